@@ -1,0 +1,226 @@
+/* bern.h — C ABI of the GB300 BERN-NN bound-propagation library.
+ *
+ * The library computes, for a ReLU feed-forward network NN and a batch of
+ * input boxes I_n(dlo, dhi), polynomials p_lo_j(x) <= NN_j(x) <= p_up_j(x)
+ * on each box together with lower/upper bounds of each output
+ * (arxiv 2211.14438, Problem 1 in Sec. 2; the method of Sec. 5).
+ *
+ * Representation.  Every polynomial is kept in the power basis of the
+ * normalised box coordinates t_i = (x_i - dlo_i) / w_i in [0,1], where
+ * w_i >= dhi_i - dlo_i is the box width rounded up to float32.  A polynomial
+ * of total degree <= D is a dense float32 vector over the graded monomial
+ * order: all exponent vectors with sum 0, then sum 1, ... up to sum D; within
+ * one total degree the exponent vectors are in descending lexicographic
+ * order of (e_1, ..., e_n).  So a degree-<=D polynomial is exactly the prefix
+ * of length M(n,D) = C(n+D, n) of any longer vector, and its "term count" is
+ * that prefix length.  bern_monomials() lists the order.
+ *
+ * Soundness.  All float32 arithmetic that produces an upper polynomial is
+ * rounded towards +inf and all that produces a lower one towards -inf, or
+ * is followed by a rigorous a-posteriori term folded into the constant
+ * coefficient; since every monomial t^K lies in [0,1] on the box, coefficient
+ * bounds are value bounds.
+ *
+ * Memory.  The caller owns every input and output buffer.  The library owns
+ * its scratch memory, monomial tables and CUDA graphs (inside bern_ctx).
+ * Unless stated otherwise, pointers are device pointers and calls are
+ * asynchronous on the context's stream.  Functions return BERN_OK or an
+ * error code; nothing throws across this boundary.
+ */
+#ifndef BERN_H
+#define BERN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define BERN_OK            0
+#define BERN_E_INVALID     1  /* bad argument: dlo > dhi, NaN box, n > 8, d not in [1,8], ... */
+#define BERN_E_CAPACITY    2  /* an output buffer is too small; n_terms tells what is needed */
+#define BERN_E_NONFINITE   3  /* a bound or coefficient became NaN/Inf */
+#define BERN_E_TIMEOUT     4  /* a device-side wait ran out of its iteration limit */
+#define BERN_E_CUDA        5  /* a CUDA runtime call failed */
+#define BERN_E_UNSUPPORTED 6  /* a size beyond the library's limits (e.g. degree table too large) */
+#define BERN_E_NOMEM       7  /* device or host allocation failed */
+
+/* pointer modes for bern_set_pointer_mode */
+#define BERN_MEM_DEVICE 0     /* boxes, network and results are device pointers (async) */
+#define BERN_MEM_HOST   1     /* they are host pointers; the call copies in, runs, copies out, syncs */
+
+/* degree plan kinds */
+#define BERN_DEG_GLOBAL     0 /* every hidden neuron uses global_d */
+#define BERN_DEG_PER_LAYER  1 /* hidden layer i (1-based) uses per_layer[i-1] */
+#define BERN_DEG_PER_NEURON 2 /* hidden neuron k (layer-major order) uses per_neuron[k] */
+
+#define BERN_MAX_VARS   8
+#define BERN_MAX_ORDER  8     /* largest ReLU Bernstein order d */
+
+typedef struct bern_ctx bern_ctx;
+
+/* A feed-forward ReLU network (Sec. 2): n_layers affine layers,
+ * widths[0] = n inputs ... widths[n_layers] = o outputs; layer i (0-based)
+ * has W[i] row-major of shape widths[i+1] x widths[i] and b[i] of length
+ * widths[i+1].  ReLU follows every layer except the last.  widths is always
+ * a host array; W[i] and b[i] follow the context's pointer mode. */
+typedef struct {
+  int n_layers;
+  const int* widths;
+  const float* const* W;
+  const float* const* b;
+} bern_net;
+
+/* Which Bernstein order d (the paper's L) each hidden neuron uses, and the
+ * limits that keep the polynomial sizes bounded.
+ *   degree_cap : total-degree cap; terms above it are dropped into a sound
+ *                constant remainder (0 means 16).
+ *   prune_tau  : terms with |c| < prune_tau * ||q||_1 are dropped likewise
+ *                after each product (0 disables pruning).
+ *   bern_budget: largest Bernstein grid (l+1)^n one enclosure may use; above
+ *                it the enclosure uses a lower order for the low-degree terms
+ *                and coefficient intervals for the rest (0 means 2^20).
+ * per_layer / per_neuron are host arrays. */
+typedef struct {
+  int kind;
+  int global_d;
+  const int* per_layer;
+  const uint8_t* per_neuron;
+  int degree_cap;
+  float prune_tau;
+  int64_t bern_budget;
+} bern_degree_plan;
+
+/* Results, all caller-owned, in the context's pointer mode.
+ *   lo, hi   : [n_boxes x o]            output enclosures (Sec. 5.3, last paragraph)
+ *   n_terms  : [n_boxes x o x 2]        term count of the upper (0) / lower (1) polynomial
+ *   keys     : [n_boxes x o x 2 x cap_terms] exponents packed 8 bits per variable
+ *              (t_1 in bits 0..7, t_2 in bits 8..15, ...), may be NULL
+ *   coef     : same shape, float32 coefficients in t, may be NULL
+ * Polynomial (box b, output j, bound k) starts at ((b*o + j)*2 + k)*cap_terms. */
+typedef struct {
+  float* lo;
+  float* hi;
+  int32_t* n_terms;
+  uint64_t* keys;
+  float* coef;
+  int64_t cap_terms;
+} bern_result;
+
+/* ------------------------------------------------------------ context */
+
+/* Create a context on `device` issuing work to `stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  Returns BERN_OK, BERN_E_CUDA. */
+int bern_create(bern_ctx** ctx, int device, void* stream);
+
+/* Free every library-owned allocation and graph.  Safe on NULL. */
+int bern_destroy(bern_ctx* ctx);
+
+/* Select BERN_MEM_DEVICE (default) or BERN_MEM_HOST for bern_propagate. */
+int bern_set_pointer_mode(bern_ctx* ctx, int mode);
+
+/* Use CUDA-graph replay for bern_propagate (default 1).  With graphs on, the
+ * launch sequence of one (network shape, batch size, plan, buffers) tuple is
+ * captured once and replayed. */
+int bern_set_graphs(bern_ctx* ctx, int enable);
+
+/* Human-readable text of a status code (static storage). */
+const char* bern_strerror(int status);
+
+/* Wait for the context's stream and return the first device-side error
+ * recorded since the last call (BERN_OK if none); clears it. */
+int bern_sync(bern_ctx* ctx);
+
+/* Number of kernels this context has launched so far (graph replays count
+ * every kernel node of the graph). */
+int64_t bern_kernel_launches(const bern_ctx* ctx);
+
+/* ------------------------------------------------------------ tables */
+
+/* M(n, D) = C(n+D, n), the number of monomials of total degree <= D in n
+ * variables, or -1 if n or D is out of range (n in [1,8], D in [0,64]). */
+int64_t bern_num_monomials(int n, int D);
+
+/* Host array exps[M(n,D) x n] of the graded order described above. */
+int bern_monomials(int n, int D, uint8_t* exps);
+
+/* ------------------------------------------------------------ hot path */
+
+/* Whole path, Sec. 5.3: input init, then per layer the affine step
+ * (Sec. 5.2) and, for hidden layers, Step 1-3 of Sec. 5.1; the last layer is
+ * affine only and its enclosure gives lo/hi.
+ *   boxes: [n_boxes x n x 2] float32, (dlo_i, dhi_i) per variable.
+ * Returns BERN_OK, BERN_E_INVALID, BERN_E_CAPACITY (result->n_terms holds
+ * the needed counts), BERN_E_UNSUPPORTED, BERN_E_NONFINITE, BERN_E_CUDA.  In
+ * BERN_MEM_DEVICE mode the call is asynchronous and device-side errors are
+ * reported by the next bern_sync(); in BERN_MEM_HOST mode it synchronises and
+ * reports them itself. */
+int bern_propagate(bern_ctx* ctx, const bern_net* net, const float* boxes,
+                   int64_t n_boxes, const bern_degree_plan* plan,
+                   bern_result* result);
+
+/* -------------------------------------------------- step entry points
+ * The five steps of the path on the library's dense layout, for testing and
+ * for callers composing their own pipeline.  All pointers are device
+ * pointers; calls are asynchronous on the context's stream.
+ *
+ * Layout of a polynomial block: poly(box b, neuron m) starts at
+ * (b*h + m)*stride floats and holds nterms[b*h + m] valid coefficients
+ * (a graded prefix); entries beyond it are not read.  "up" and "lo" blocks
+ * have the same layout.  stride must be >= the largest term count. */
+
+/* a0, Sec. 5.3 (input init): z0_i = x_i = dlo_i + w_i t_i for both bounds.
+ * z_up/z_lo get n_boxes*n polynomials of n+1 terms, nterms = n+1. */
+int bern_init_inputs(bern_ctx* ctx, int n, int64_t n_boxes, const float* boxes,
+                     float* z_up, float* z_lo, int64_t stride, int32_t* nterms);
+
+/* a1, Sec. 5.2, eqs. upper_bounds_layer / lower_bounds_layer:
+ *   pre_up_m = sum_j W+_mj up_j + W-_mj lo_j + b_m   (rounded up)
+ *   pre_lo_m = sum_j W+_mj lo_j + W-_mj up_j + b_m   (rounded down)
+ * W: [h_out x h_in] row-major, b: [h_out].  Output term count per box is
+ * max(1, max_j in_nterms[b*h_in + j]). */
+int bern_affine(bern_ctx* ctx, int64_t n_boxes, int h_out, int h_in,
+                const float* W, const float* b, const float* in_up,
+                const float* in_lo, int64_t in_stride, const int32_t* in_nterms,
+                float* out_up, float* out_lo, int64_t out_stride,
+                int32_t* out_nterms);
+
+/* a2, Sec. 5.1 Step 1 (eq. find_lo_hi) with Def. 2: lo = min of the
+ * Bernstein coefficients of pre_lo, hi = max of those of pre_up, of order
+ * `order` in every variable on [0,1]^n (rounded outward).  budget as in
+ * bern_degree_plan (0 = 2^20). */
+int bern_enclose(bern_ctx* ctx, int n, int64_t n_items, int order,
+                 int64_t budget, const float* pre_up, const float* pre_lo,
+                 int64_t stride, const int32_t* nterms, float* lo, float* hi);
+
+/* a3, Sec. 5.1 Step 2 with Def. 1 and Props. 1-2: per item the case
+ * (0: hi <= 0, output 0; 1: lo >= 0, identity; 2: ReLU polynomial), and for
+ * case 2 the power form a_0..a_d in s = (y-lo)/(hi-lo) of the order-d
+ * Bernstein polynomial of ReLU on [lo,hi], each rounded up, and the shift
+ * eps >= B(0) + sum_j (a_j rounded - a_j), rounded up.
+ *   degrees: [n_items] uint8 orders, or NULL to use global_d.
+ *   coef: [n_items x (BERN_MAX_ORDER+1)], eps: [n_items], kind: [n_items]. */
+int bern_relu_coeffs(bern_ctx* ctx, int64_t n_items, const float* lo,
+                     const float* hi, const uint8_t* degrees, int global_d,
+                     int8_t* kind, float* coef, float* eps);
+
+/* a4, Sec. 5.1 Step 3, eqs. post_bounds_1/2: post_up = B(s_up), post_lo =
+ * B(s_lo) - eps with s = (pre - lo)/(hi - lo), computed as polynomials in t
+ * with outward rounding, truncated at total degree `degree_cap` (dropped terms
+ * enter the constant as a one-sided remainder) and pruned at prune_tau.
+ * Identity items copy pre to post; zero items get nterms = 0.
+ * n_vars/n_items/h: items are (box, neuron) pairs, neuron index = item % h.
+ * post_stride must hold M(n, min(d * D_pre, degree_cap)) for every item. */
+int bern_compose(bern_ctx* ctx, int n, int64_t n_items, int degree_cap,
+                 float prune_tau, const int8_t* kind, const float* coef,
+                 const float* eps, const uint8_t* degrees, int global_d,
+                 const float* lo, const float* hi, const float* pre_up,
+                 const float* pre_lo, int64_t pre_stride,
+                 const int32_t* pre_nterms, float* post_up, float* post_lo,
+                 int64_t post_stride, int32_t* post_nterms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BERN_H */

@@ -68,6 +68,9 @@ def _load():
     lib.orc_poly_mul.restype = ctypes.c_int
     lib.orc_poly_mul.argtypes = [ctypes.c_int, ctypes.c_int, u8, dp, ctypes.c_int, u8, dp,
                                  ctypes.c_int, ip, u8, dp]
+    lib.orc_affine.restype = ctypes.c_int
+    lib.orc_affine.argtypes = [ctypes.c_int, ctypes.c_int, ip, u8, dp, ip, u8, dp, dp,
+                               ctypes.c_double, ctypes.c_int, ip, u8, dp]
     lib.orc_eval_poly.restype = None
     lib.orc_eval_poly.argtypes = [ctypes.c_int, ctypes.c_int, u8, dp, ctypes.c_longlong, dp, dp]
     lib.orc_propagate.restype = ctypes.c_int
@@ -180,6 +183,31 @@ def poly_mul(p, q, n: int, cap_terms: int = 1 << 18) -> Poly:
         raise ValueError("poly_mul capacity")
     k = int(on[0])
     return oe[: k * n].reshape(k, n).copy(), oc[:k].copy()
+
+
+def affine(up, lo, n: int, w_row, bias: float, cap_terms: int = 1 << 16):
+    """Sec. 5.2 layer step for ONE output neuron: up/lo are lists of input
+    polynomials; returns (pre_up, pre_lo)."""
+    ups = [as_poly(p, n) for p in up]
+    los = [as_poly(p, n) for p in lo]
+    nt_u = np.array([len(c) for _, c in ups], np.int32)
+    nt_l = np.array([len(c) for _, c in los], np.int32)
+    e_u = np.ascontiguousarray(np.concatenate([e for e, _ in ups]).reshape(-1), np.uint8)
+    c_u = np.ascontiguousarray(np.concatenate([c for _, c in ups]), np.float64)
+    e_l = np.ascontiguousarray(np.concatenate([e for e, _ in los]).reshape(-1), np.uint8)
+    c_l = np.ascontiguousarray(np.concatenate([c for _, c in los]), np.float64)
+    w = np.ascontiguousarray(np.asarray(w_row, np.float64).reshape(-1))
+    on = np.zeros(2, np.int32)
+    oe = np.zeros(2 * cap_terms * n, np.uint8)
+    oc = np.zeros(2 * cap_terms)
+    rc = _load().orc_affine(n, len(ups), _ip(nt_u), _u8(e_u), _dp(c_u), _ip(nt_l), _u8(e_l),
+                            _dp(c_l), _dp(w), float(bias), cap_terms, _ip(on), _u8(oe), _dp(oc))
+    if rc:
+        raise ValueError("affine failed (%d)" % rc)
+    oe = oe.reshape(2, cap_terms, n)
+    oc = oc.reshape(2, cap_terms)
+    return ((oe[0, : on[0]].copy(), oc[0, : on[0]].copy()),
+            (oe[1, : on[1]].copy(), oc[1, : on[1]].copy()))
 
 
 def eval_poly(p, n: int, t: np.ndarray) -> np.ndarray:

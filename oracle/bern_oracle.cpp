@@ -328,6 +328,28 @@ int orc_poly_mul(int n, int na, const uint8_t* ea, const double* ca, int nb,
   return to_arrays(r, n, cap_terms, out_n, out_exps, out_coef);
 }
 
+// Affine step (Sec. 5.2) for one output neuron: h_in upper/lower input
+// polynomials given back to back (nterms per polynomial in nt_up/nt_lo).
+int orc_affine(int n, int h_in, const int* nt_up, const uint8_t* e_up,
+               const double* c_up, const int* nt_lo, const uint8_t* e_lo,
+               const double* c_lo, const double* w_row, double bias, int cap_terms,
+               int* out_n, uint8_t* out_exps, double* out_coef) {
+  std::vector<Poly> up(h_in), lo(h_in);
+  size_t ou = 0, ol = 0;
+  for (int j = 0; j < h_in; ++j) {
+    up[j] = from_arrays(n, nt_up[j], e_up + ou * n, c_up + ou);
+    lo[j] = from_arrays(n, nt_lo[j], e_lo + ol * n, c_lo + ol);
+    ou += nt_up[j];
+    ol += nt_lo[j];
+  }
+  std::vector<Poly> pu, pl;
+  affine(up, lo, w_row, &bias, 1, h_in, n, pu, pl);
+  int rc = to_arrays(pu[0], n, cap_terms, &out_n[0], out_exps, out_coef);
+  int rc2 = to_arrays(pl[0], n, cap_terms, &out_n[1], out_exps + (size_t)cap_terms * n,
+                      out_coef + cap_terms);
+  return rc ? rc : rc2;
+}
+
 void orc_eval_poly(int n, int nterms, const uint8_t* exps, const double* coef,
                    long long npts, const double* t, double* out) {
   for (long long p = 0; p < npts; ++p) {

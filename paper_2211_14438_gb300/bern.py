@@ -1,0 +1,326 @@
+"""Python binding of libbern.so (the C ABI in include/bern.h).
+
+Argument marshalling only: every step of the bound propagation runs in the
+library's CUDA kernels.  PyTorch supplies device memory and the stream.  If
+the shared library is missing or cannot be loaded this module raises; there
+is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+BERN_OK = 0
+BERN_E_INVALID = 1
+BERN_E_CAPACITY = 2
+BERN_E_NONFINITE = 3
+BERN_E_TIMEOUT = 4
+BERN_E_CUDA = 5
+BERN_E_UNSUPPORTED = 6
+BERN_E_NOMEM = 7
+BERN_MEM_DEVICE = 0
+BERN_MEM_HOST = 1
+BERN_DEG_GLOBAL = 0
+BERN_DEG_PER_LAYER = 1
+BERN_DEG_PER_NEURON = 2
+BERN_MAX_ORDER = 8
+COEF_STRIDE = BERN_MAX_ORDER + 1
+
+EXPORTS = [
+    "bern_create", "bern_destroy", "bern_set_pointer_mode", "bern_set_graphs",
+    "bern_strerror", "bern_sync", "bern_kernel_launches", "bern_num_monomials",
+    "bern_monomials", "bern_propagate", "bern_init_inputs", "bern_affine",
+    "bern_enclose", "bern_relu_coeffs", "bern_compose",
+]
+
+
+class BernError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__("%s: %s (%d)" % (where, strerror(code), code))
+        self.code = code
+
+
+class bern_net(ctypes.Structure):
+    _fields_ = [("n_layers", ctypes.c_int), ("widths", ctypes.POINTER(ctypes.c_int)),
+                ("W", ctypes.POINTER(ctypes.c_void_p)), ("b", ctypes.POINTER(ctypes.c_void_p))]
+
+
+class bern_degree_plan(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("global_d", ctypes.c_int),
+                ("per_layer", ctypes.POINTER(ctypes.c_int)),
+                ("per_neuron", ctypes.POINTER(ctypes.c_uint8)),
+                ("degree_cap", ctypes.c_int), ("prune_tau", ctypes.c_float),
+                ("bern_budget", ctypes.c_int64)]
+
+
+class bern_result(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p), ("n_terms", ctypes.c_void_p),
+                ("keys", ctypes.c_void_p), ("coef", ctypes.c_void_p), ("cap_terms", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libbern.so (building it first if it is absent and allowed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise OSError("libbern.so is not built (%s)" % path)
+        _build.build()
+    lib = ctypes.CDLL(path)
+    V, I, I64, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_float
+    sig = {
+        "bern_create": (I, [ctypes.POINTER(V), I, V]),
+        "bern_destroy": (I, [V]),
+        "bern_set_pointer_mode": (I, [V, I]),
+        "bern_set_graphs": (I, [V, I]),
+        "bern_strerror": (ctypes.c_char_p, [I]),
+        "bern_sync": (I, [V]),
+        "bern_kernel_launches": (I64, [V]),
+        "bern_num_monomials": (I64, [I, I]),
+        "bern_monomials": (I, [I, I, V]),
+        "bern_propagate": (I, [V, ctypes.POINTER(bern_net), V, I64,
+                               ctypes.POINTER(bern_degree_plan), ctypes.POINTER(bern_result)]),
+        "bern_init_inputs": (I, [V, I, I64, V, V, V, I64, V]),
+        "bern_affine": (I, [V, I64, I, I, V, V, V, V, I64, V, V, V, I64, V]),
+        "bern_enclose": (I, [V, I, I64, I, I64, V, V, I64, V, V, V]),
+        "bern_relu_coeffs": (I, [V, I64, V, V, V, I, V, V, V]),
+        "bern_compose": (I, [V, I, I64, I, F, V, V, V, V, I, V, V, V, V, I64, V, V, V, I64, V]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load().bern_strerror(code).decode()
+
+
+def _check(code: int, where: str):
+    if code != BERN_OK:
+        raise BernError(code, where)
+
+
+def num_monomials(n: int, D: int) -> int:
+    return int(load().bern_num_monomials(n, D))
+
+
+def monomials(n: int, D: int) -> np.ndarray:
+    """The library's graded monomial order: array [M(n,D), n] of exponents."""
+    m = num_monomials(n, D)
+    out = np.zeros((m, n), np.uint8)
+    _check(load().bern_monomials(n, D, out.ctypes.data), "bern_monomials")
+    return out
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+class Context:
+    """Owns a bern_ctx on one CUDA device, bound to a torch stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.torch = torch
+        lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(lib.bern_create(ctypes.byref(h), device, ctypes.c_void_p(stream.cuda_stream)),
+               "bern_create")
+        self.h = h
+        self.device = device
+        self.lib = lib
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bern_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------- control
+    def sync(self) -> int:
+        return int(self.lib.bern_sync(self.h))
+
+    def check(self, where="bern_sync"):
+        _check(self.sync(), where)
+
+    def kernel_launches(self) -> int:
+        return int(self.lib.bern_kernel_launches(self.h))
+
+    def set_graphs(self, on: bool):
+        _check(self.lib.bern_set_graphs(self.h, 1 if on else 0), "bern_set_graphs")
+
+    def set_pointer_mode(self, mode: int):
+        _check(self.lib.bern_set_pointer_mode(self.h, mode), "bern_set_pointer_mode")
+
+    # ------------------------------------------------------------- steps
+    def init_inputs(self, n, boxes, z_up, z_lo, stride, nterms):
+        _check(self.lib.bern_init_inputs(self.h, n, boxes.shape[0], _ptr(boxes), _ptr(z_up),
+                                         _ptr(z_lo), stride, _ptr(nterms)), "bern_init_inputs")
+
+    def affine(self, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_stride, in_nterms,
+               out_up, out_lo, out_stride, out_nterms):
+        _check(self.lib.bern_affine(self.h, n_boxes, h_out, h_in, _ptr(W), _ptr(b), _ptr(in_up),
+                                    _ptr(in_lo), in_stride, _ptr(in_nterms), _ptr(out_up),
+                                    _ptr(out_lo), out_stride, _ptr(out_nterms)), "bern_affine")
+
+    def enclose(self, n, n_items, order, budget, pre_up, pre_lo, stride, nterms, lo, hi):
+        _check(self.lib.bern_enclose(self.h, n, n_items, order, budget, _ptr(pre_up), _ptr(pre_lo),
+                                     stride, _ptr(nterms), _ptr(lo), _ptr(hi)), "bern_enclose")
+
+    def relu_coeffs(self, n_items, lo, hi, degrees, global_d, kind, coef, eps):
+        _check(self.lib.bern_relu_coeffs(self.h, n_items, _ptr(lo), _ptr(hi), _ptr(degrees),
+                                         global_d, _ptr(kind), _ptr(coef), _ptr(eps)),
+               "bern_relu_coeffs")
+
+    def compose(self, n, n_items, cap, tau, kind, coef, eps, degrees, global_d, lo, hi,
+                pre_up, pre_lo, pre_stride, pre_nterms, post_up, post_lo, post_stride,
+                post_nterms):
+        _check(self.lib.bern_compose(self.h, n, n_items, cap, tau, _ptr(kind), _ptr(coef),
+                                     _ptr(eps), _ptr(degrees), global_d, _ptr(lo), _ptr(hi),
+                                     _ptr(pre_up), _ptr(pre_lo), pre_stride, _ptr(pre_nterms),
+                                     _ptr(post_up), _ptr(post_lo), post_stride,
+                                     _ptr(post_nterms)), "bern_compose")
+
+    # ------------------------------------------------------------- whole path
+    def propagate(self, widths: Sequence[int], W, b, boxes, degree=2, cap: int = 16,
+                  tau: float = 0.0, budget: int = 0, cap_terms: Optional[int] = None,
+                  out=None, keys: bool = False, sync: bool = True):
+        """bern_propagate on device tensors (W, b: lists of float32 CUDA tensors;
+        boxes: float32 CUDA tensor [B, n, 2]).  degree: int (global), list of
+        per-hidden-layer ints, or a uint8 array with one order per hidden
+        neuron.  Returns a dict of CUDA tensors."""
+        torch = self.torch
+        widths = [int(x) for x in widths]
+        H = len(widths) - 1
+        o = widths[-1]
+        B = int(boxes.shape[0])
+        plan, keep = make_plan(degree, widths, cap, tau, budget)
+        if cap_terms is None:
+            cap_terms = max_output_terms(widths, degree, cap)
+        dev = boxes.device
+        if out is None:
+            out = {
+                "lo": torch.empty(B, o, device=dev, dtype=torch.float32),
+                "hi": torch.empty(B, o, device=dev, dtype=torch.float32),
+                "n_terms": torch.empty(B, o, 2, device=dev, dtype=torch.int32),
+                "coef": torch.empty(B, o, 2, cap_terms, device=dev, dtype=torch.float32),
+                "keys": (torch.empty(B, o, 2, cap_terms, device=dev, dtype=torch.int64)
+                         if keys else None),
+            }
+        net, keep2 = make_net(widths, [_ptr(w) for w in W], [_ptr(x) for x in b])
+        res = bern_result(_ptr(out["lo"]), _ptr(out["hi"]), _ptr(out["n_terms"]),
+                          _ptr(out.get("keys")), _ptr(out.get("coef")), cap_terms)
+        rc = self.lib.bern_propagate(self.h, ctypes.byref(net), ctypes.c_void_p(_ptr(boxes)), B,
+                                     ctypes.byref(plan), ctypes.byref(res))
+        _check(rc, "bern_propagate")
+        if sync:
+            self.check("bern_propagate")
+        return out
+
+    def propagate_host(self, widths, W, b, boxes, degree=2, cap: int = 16, tau: float = 0.0,
+                       budget: int = 0, cap_terms: Optional[int] = None, out=None):
+        """bern_propagate with host buffers (numpy arrays, ideally pinned):
+        copies in, runs, copies out and synchronises inside the call."""
+        widths = [int(x) for x in widths]
+        o = widths[-1]
+        B = int(boxes.shape[0])
+        plan, keep = make_plan(degree, widths, cap, tau, budget)
+        if cap_terms is None:
+            cap_terms = max_output_terms(widths, degree, cap)
+        if out is None:
+            out = {"lo": np.empty((B, o), np.float32), "hi": np.empty((B, o), np.float32),
+                   "n_terms": np.empty((B, o, 2), np.int32),
+                   "coef": np.empty((B, o, 2, cap_terms), np.float32)}
+        Wp = [np.ascontiguousarray(w, np.float32) for w in W]
+        bp = [np.ascontiguousarray(x, np.float32) for x in b]
+        net, keep2 = make_net(widths, [w.ctypes.data for w in Wp], [x.ctypes.data for x in bp])
+        bx = np.ascontiguousarray(boxes, np.float32)
+        res = bern_result(out["lo"].ctypes.data, out["hi"].ctypes.data,
+                          out["n_terms"].ctypes.data, 0,
+                          out["coef"].ctypes.data if out.get("coef") is not None else 0,
+                          cap_terms)
+        self.set_pointer_mode(BERN_MEM_HOST)
+        try:
+            rc = self.lib.bern_propagate(self.h, ctypes.byref(net), bx.ctypes.data, B,
+                                         ctypes.byref(plan), ctypes.byref(res))
+        finally:
+            self.set_pointer_mode(BERN_MEM_DEVICE)
+        _check(rc, "bern_propagate(host)")
+        return out
+
+
+def make_net(widths, W_ptrs, b_ptrs):
+    H = len(widths) - 1
+    wid = (ctypes.c_int * (H + 1))(*widths)
+    Wa = (ctypes.c_void_p * H)(*W_ptrs)
+    ba = (ctypes.c_void_p * H)(*b_ptrs)
+    net = bern_net(H, wid, Wa, ba)
+    return net, (wid, Wa, ba)
+
+
+def make_plan(degree, widths, cap, tau, budget):
+    H = len(widths) - 1
+    keep = []
+    if isinstance(degree, (int, np.integer)):
+        plan = bern_degree_plan(BERN_DEG_GLOBAL, int(degree), None, None, cap, tau, budget)
+    else:
+        arr = np.asarray(degree)
+        if arr.dtype == np.uint8 or len(arr) == sum(widths[1:-1]) and len(arr) != H - 1:
+            a = np.ascontiguousarray(arr, np.uint8)
+            keep.append(a)
+            plan = bern_degree_plan(BERN_DEG_PER_NEURON, 0, None,
+                                    a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), cap, tau,
+                                    budget)
+        else:
+            a = (ctypes.c_int * len(arr))(*[int(x) for x in arr])
+            keep.append(a)
+            plan = bern_degree_plan(BERN_DEG_PER_LAYER, 0, a, None, cap, tau, budget)
+    return plan, keep
+
+
+def layer_degrees(widths, degree):
+    H = len(widths) - 1
+    if isinstance(degree, (int, np.integer)):
+        return [int(degree)] * (H - 1)
+    arr = np.asarray(degree)
+    if arr.dtype == np.uint8 or len(arr) == sum(widths[1:-1]) and len(arr) != H - 1:
+        out, base = [], 0
+        for h in widths[1:-1]:
+            out.append(int(arr[base:base + h].max()))
+            base += h
+        return out
+    return [int(x) for x in arr]
+
+
+def max_output_terms(widths, degree, cap) -> int:
+    """Worst-case term count of an output polynomial (the graded prefix of
+    total degree min(prod d_i, cap))."""
+    D = 1
+    for d in layer_degrees(widths, degree):
+        D = min(D * d, cap)
+    return num_monomials(int(widths[0]), D)

@@ -1,0 +1,681 @@
+// C ABI: context, monomial tables, workspace and the layer-by-layer driver
+// of the BERN-NN propagation (Sec. 5.3 of arxiv 2211.14438).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bern_internal.cuh"
+
+namespace bern {
+int effective_order(int n, int order, int64_t budget, int* grid_out);
+}
+
+using namespace bern;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  cudaError_t reserve(size_t want) {
+    if (want <= bytes) return cudaSuccess;
+    release();
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e == cudaSuccess) bytes = want;
+    return e;
+  }
+};
+
+struct TableSet {
+  int dmax = -1;
+  DevBuf exps, mcount;
+  std::vector<DevBuf> bufs;
+  Tables view{};
+};
+
+struct GraphEntry {
+  std::string key;
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernels = 0;
+};
+
+int64_t monomials_clamped(int n, int D) {
+  int64_t m = num_monomials(n, D);
+  return m < 0 ? -1 : m;
+}
+
+}  // namespace
+
+struct bern_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int mem_mode = BERN_MEM_DEVICE;
+  int use_graphs = 1;
+  cudaStream_t gstream = nullptr;   // private stream that graphs are captured on
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int* d_status = nullptr;
+  int64_t launches = 0;
+  std::map<int, TableSet> tables;
+  DevBuf ws, stage_in, stage_out;
+  std::vector<GraphEntry> graphs;
+  Launch launch() { return Launch{stream, d_status, &launches}; }
+  Launch launch_on(cudaStream_t s) { return Launch{s, d_status, &launches}; }
+};
+
+namespace {
+
+int map_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return BERN_OK;
+  if (e == cudaErrorMemoryAllocation) return BERN_E_NOMEM;
+  return BERN_E_CUDA;
+}
+
+int status_to_code(int s) {
+  if (s & kStatusInvalid) return BERN_E_INVALID;
+  if (s & kStatusUnsupported) return BERN_E_UNSUPPORTED;
+  if (s & kStatusCapacity) return BERN_E_CAPACITY;
+  if (s & kStatusNonFinite) return BERN_E_NONFINITE;
+  return BERN_OK;
+}
+
+// Largest total degree whose graded exponent table stays below 2^22 ranks.
+int exps_degree(int n) {
+  int D = 0;
+  while (D < kMaxTableDegree && num_monomials(n, D + 1) <= ((int64_t)1 << 22)) ++D;
+  return D;
+}
+
+// Make sure square tables exist for degrees 0..dmax in n variables.
+int ensure_tables(bern_ctx* c, int n, int dmax, const Tables** out) {
+  TableSet& ts = c->tables[n];
+  if (ts.dmax >= dmax) {
+    *out = &ts.view;
+    return BERN_OK;
+  }
+  if (dmax > kMaxTableDegree) return BERN_E_UNSUPPORTED;
+  // (re)build from scratch; previously captured graphs hold old pointers
+  for (auto& g : c->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+  cudaStreamSynchronize(c->stream);
+  for (auto& b : ts.bufs) b.release();
+  ts.bufs.clear();
+  ts.view = Tables{};
+  ts.view.n = n;
+  const int De = exps_degree(n);
+  std::vector<uint8_t> ex;
+  graded_monomials(n, De, ex);
+  cudaError_t e = ts.exps.reserve(ex.size());
+  if (e != cudaSuccess) return map_cuda(e);
+  cudaMemcpy(ts.exps.p, ex.data(), ex.size(), cudaMemcpyHostToDevice);
+  std::vector<int32_t> mc(kMaxTableDegree + 1);
+  for (int D = 0; D <= kMaxTableDegree; ++D) {
+    int64_t m = num_monomials(n, D);
+    mc[D] = (m < 0 || m > INT32_MAX) ? INT32_MAX : (int32_t)m;
+  }
+  e = ts.mcount.reserve(mc.size() * sizeof(int32_t));
+  if (e != cudaSuccess) return map_cuda(e);
+  cudaMemcpy(ts.mcount.p, mc.data(), mc.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  ts.view.exps = (const uint8_t*)ts.exps.p;
+  ts.view.mcount = (const int32_t*)ts.mcount.p;
+  ts.view.mexps = num_monomials(n, De);
+  for (int D = 0; D <= dmax; ++D) {
+    PairList pl;
+    if (!build_square_pairs(n, D, pl)) return BERN_E_UNSUPPORTED;
+    DevBuf bp, bq;
+    if ((e = bp.reserve(pl.ptr.size() * sizeof(int32_t))) != cudaSuccess) return map_cuda(e);
+    if ((e = bq.reserve(std::max<size_t>(4, pl.pairs.size() * sizeof(uint32_t)))) != cudaSuccess)
+      return map_cuda(e);
+    cudaMemcpy(bp.p, pl.ptr.data(), pl.ptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (!pl.pairs.empty())
+      cudaMemcpy(bq.p, pl.pairs.data(), pl.pairs.size() * sizeof(uint32_t),
+                 cudaMemcpyHostToDevice);
+    ts.view.sq[D].ptr = (const int32_t*)bp.p;
+    ts.view.sq[D].pairs = (const uint32_t*)bq.p;
+    ts.bufs.push_back(bp);
+    ts.bufs.push_back(bq);
+  }
+  ts.dmax = dmax;
+  ts.view.dmax = dmax;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return map_cuda(e);
+  *out = &ts.view;
+  return BERN_OK;
+}
+
+// ------------------------------------------------------------ propagate plan
+struct LayerPlan {
+  int h_in, h_out;
+  int d;            // max ReLU order of this layer's neurons (hidden only)
+  int D_pre, D_post;
+  int64_t M_pre, M_post;
+  int order;        // Bernstein order of this layer's enclosure
+  bool hidden;
+  // per-box offsets (in bytes) into the workspace
+  size_t off_pre_up, off_pre_lo, off_pre_nt, off_lo, off_hi, off_kind, off_coef, off_eps,
+      off_post_up, off_post_lo, off_post_nt, off_deg;
+};
+
+struct Plan {
+  int n, o, H, cap;
+  float tau;
+  int64_t budget;
+  std::vector<LayerPlan> L;
+  size_t off_z_up, off_z_lo, off_z_nt;
+  size_t per_box;   // bytes per box
+  std::vector<uint8_t> neuron_deg;   // PER_NEURON plans (hidden neurons, layer-major)
+  bool per_neuron = false;
+};
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int make_plan(const bern_net* net, const bern_degree_plan* dp, Plan& P) {
+  if (!net || !net->widths || net->n_layers < 1) return BERN_E_INVALID;
+  P.H = net->n_layers;
+  P.n = net->widths[0];
+  P.o = net->widths[P.H];
+  if (P.n < 1 || P.n > kMaxVars) return BERN_E_INVALID;
+  for (int i = 0; i <= P.H; ++i)
+    if (net->widths[i] < 1) return BERN_E_INVALID;
+  bern_degree_plan def{};
+  def.kind = BERN_DEG_GLOBAL;
+  def.global_d = 2;
+  if (!dp) dp = &def;
+  P.cap = dp->degree_cap > 0 ? dp->degree_cap : 16;
+  if (P.cap > kMaxTableDegree) return BERN_E_INVALID;
+  P.tau = dp->prune_tau;
+  if (!(P.tau >= 0.0f)) return BERN_E_INVALID;
+  P.budget = dp->bern_budget > 0 ? dp->bern_budget : ((int64_t)1 << 20);
+  P.L.resize(P.H);
+  int Dprev = 1, order = 1;
+  int hidden_base = 0;
+  P.per_neuron = dp->kind == BERN_DEG_PER_NEURON;
+  for (int i = 0; i < P.H; ++i) {
+    LayerPlan& l = P.L[i];
+    l.h_in = net->widths[i];
+    l.h_out = net->widths[i + 1];
+    l.hidden = i < P.H - 1;
+    l.D_pre = Dprev;
+    l.order = order;
+    l.d = 1;
+    if (l.hidden) {
+      if (dp->kind == BERN_DEG_GLOBAL) {
+        l.d = dp->global_d;
+      } else if (dp->kind == BERN_DEG_PER_LAYER) {
+        if (!dp->per_layer) return BERN_E_INVALID;
+        l.d = dp->per_layer[i];
+      } else if (dp->kind == BERN_DEG_PER_NEURON) {
+        if (!dp->per_neuron) return BERN_E_INVALID;
+        int mx = 0;
+        for (int m = 0; m < l.h_out; ++m) {
+          int dm = dp->per_neuron[hidden_base + m];
+          if (dm < 1 || dm > kMaxOrder) return BERN_E_INVALID;
+          mx = std::max(mx, dm);
+          P.neuron_deg.push_back((uint8_t)dm);
+        }
+        l.d = mx;
+      } else {
+        return BERN_E_INVALID;
+      }
+      if (l.d < 1 || l.d > kMaxOrder) return BERN_E_INVALID;
+      l.D_post = std::min(Dprev * l.d, P.cap);
+      hidden_base += l.h_out;
+      Dprev = l.D_post;
+      order = std::min(order * l.d, P.cap);
+    } else {
+      l.D_post = l.D_pre;
+    }
+    l.M_pre = monomials_clamped(P.n, l.D_pre);
+    l.M_post = monomials_clamped(P.n, l.D_post);
+    if (l.M_pre < 0 || l.M_post < 0) return BERN_E_UNSUPPORTED;
+  }
+  // per-box workspace layout
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  const int n = P.n;
+  P.off_z_up = take(sizeof(float) * n * (n + 1));
+  P.off_z_lo = take(sizeof(float) * n * (n + 1));
+  P.off_z_nt = take(sizeof(int32_t) * n);
+  for (auto& l : P.L) {
+    l.off_pre_up = take(sizeof(float) * l.h_out * l.M_pre);
+    l.off_pre_lo = take(sizeof(float) * l.h_out * l.M_pre);
+    l.off_pre_nt = take(sizeof(int32_t) * l.h_out);
+    l.off_lo = take(sizeof(float) * l.h_out);
+    l.off_hi = take(sizeof(float) * l.h_out);
+    if (l.hidden) {
+      l.off_kind = take(l.h_out);
+      l.off_coef = take(sizeof(float) * l.h_out * kCoefStride);
+      l.off_eps = take(sizeof(float) * l.h_out);
+      l.off_post_up = take(sizeof(float) * l.h_out * l.M_post);
+      l.off_post_lo = take(sizeof(float) * l.h_out * l.M_post);
+      l.off_post_nt = take(sizeof(int32_t) * l.h_out);
+      l.off_deg = P.per_neuron ? take(l.h_out) : 0;
+    }
+  }
+  P.per_box = off;
+  return BERN_OK;
+}
+
+// Workspace regions are laid out "structure of arrays": region k of a chunk
+// of B boxes starts at B * offset_k, and box b's slice of it at b * size_k.
+struct Chunk {
+  char* base;
+  int64_t B;
+  template <class T>
+  T* at(size_t off) const { return reinterpret_cast<T*>(base + off * B); }
+};
+
+// Launch sequence of one chunk (graph-capturable: no host sync, no alloc).
+int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
+              const bern_net* net, const float* boxes, int64_t B, const Chunk& ch,
+              float* out_lo, float* out_hi, bern_result res) {
+  Launch L = c->launch_on(s);
+  const int n = P.n;
+  cudaError_t e = launch_init_inputs(L, n, B, boxes, ch.at<float>(P.off_z_up),
+                                     ch.at<float>(P.off_z_lo), n + 1,
+                                     ch.at<int32_t>(P.off_z_nt));
+  if (e != cudaSuccess) return map_cuda(e);
+  const float* in_up = ch.at<float>(P.off_z_up);
+  const float* in_lo = ch.at<float>(P.off_z_lo);
+  const int32_t* in_nt = ch.at<int32_t>(P.off_z_nt);
+  int64_t in_stride = n + 1;
+  for (int i = 0; i < P.H; ++i) {
+    const LayerPlan& l = P.L[i];
+    float* pre_up = ch.at<float>(l.off_pre_up);
+    float* pre_lo = ch.at<float>(l.off_pre_lo);
+    int32_t* pre_nt = ch.at<int32_t>(l.off_pre_nt);
+    e = launch_affine(L, B, l.h_out, l.h_in, net->W[i], net->b[i], in_up, in_lo, in_stride,
+                      in_nt, pre_up, pre_lo, l.M_pre, pre_nt);
+    if (e != cudaSuccess) return map_cuda(e);
+    const int64_t items = B * l.h_out;
+    if (!l.hidden) {
+      e = launch_enclose(L, T, items, l.order, P.budget, pre_up, pre_lo, l.M_pre, pre_nt,
+                         out_lo, out_hi);
+      if (e != cudaSuccess) return map_cuda(e);
+      e = launch_pack(L, T, B, P.o, pre_up, pre_lo, l.M_pre, pre_nt, res);
+      if (e != cudaSuccess) return map_cuda(e);
+      break;
+    }
+    float* lo = ch.at<float>(l.off_lo);
+    float* hi = ch.at<float>(l.off_hi);
+    e = launch_enclose(L, T, items, l.order, P.budget, pre_up, pre_lo, l.M_pre, pre_nt, lo, hi);
+    if (e != cudaSuccess) return map_cuda(e);
+    const uint8_t* deg = nullptr;
+    if (P.per_neuron) deg = ch.at<uint8_t>(l.off_deg);
+    int8_t* kind = ch.at<int8_t>(l.off_kind);
+    float* coef = ch.at<float>(l.off_coef);
+    float* eps = ch.at<float>(l.off_eps);
+    e = launch_relu_coeffs(L, items, lo, hi, deg, l.d, kind, coef, eps);
+    if (e != cudaSuccess) return map_cuda(e);
+    float* post_up = ch.at<float>(l.off_post_up);
+    float* post_lo = ch.at<float>(l.off_post_lo);
+    int32_t* post_nt = ch.at<int32_t>(l.off_post_nt);
+    e = launch_compose(L, T, items, P.cap, P.tau, kind, coef, eps, deg, l.d, lo, hi, pre_up,
+                       pre_lo, l.M_pre, pre_nt, post_up, post_lo, l.M_post, post_nt);
+    if (e != cudaSuccess) return map_cuda(e);
+    in_up = post_up;
+    in_lo = post_lo;
+    in_nt = post_nt;
+    in_stride = l.M_post;
+  }
+  return BERN_OK;
+}
+
+// Fill the per-item degree arrays of a PER_NEURON plan for a chunk.
+int fill_degrees(bern_ctx* c, const Plan& P, const Chunk& ch, int64_t B) {
+  if (!P.per_neuron) return BERN_OK;
+  size_t base = 0;
+  std::vector<uint8_t> host;
+  for (const auto& l : P.L) {
+    if (!l.hidden) break;
+    host.resize((size_t)B * l.h_out);
+    for (int64_t b = 0; b < B; ++b)
+      std::memcpy(&host[(size_t)b * l.h_out], &P.neuron_deg[base], l.h_out);
+    cudaError_t e = cudaMemcpy(ch.at<uint8_t>(l.off_deg), host.data(), host.size(),
+                               cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return map_cuda(e);
+    base += l.h_out;
+  }
+  return BERN_OK;
+}
+
+std::string graph_key(const Plan& P, const bern_net* net, const float* boxes, int64_t B,
+                      const bern_result& r, const void* wsbase) {
+  std::string k;
+  auto add = [&](const void* p, size_t s) { k.append((const char*)p, s); };
+  add(&B, sizeof B);
+  add(&boxes, sizeof boxes);
+  add(&P.cap, sizeof P.cap);
+  add(&P.tau, sizeof P.tau);
+  add(&P.budget, sizeof P.budget);
+  add(&wsbase, sizeof wsbase);
+  for (int i = 0; i <= P.H; ++i) add(&net->widths[i], sizeof(int));
+  for (int i = 0; i < P.H; ++i) {
+    add(&net->W[i], sizeof(void*));
+    add(&net->b[i], sizeof(void*));
+    add(&P.L[i].d, sizeof(int));
+  }
+  add(P.neuron_deg.data(), P.neuron_deg.size());
+  add(&r, sizeof r);
+  return k;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+const char* bern_strerror(int s) {
+  switch (s) {
+    case BERN_OK: return "ok";
+    case BERN_E_INVALID: return "invalid argument";
+    case BERN_E_CAPACITY: return "output capacity too small";
+    case BERN_E_NONFINITE: return "non-finite bound or coefficient";
+    case BERN_E_TIMEOUT: return "device wait timed out";
+    case BERN_E_CUDA: return "CUDA runtime error";
+    case BERN_E_UNSUPPORTED: return "size beyond library limits";
+    case BERN_E_NOMEM: return "out of memory";
+    default: return "unknown status";
+  }
+}
+
+int bern_create(bern_ctx** out, int device, void* stream) {
+  if (!out) return BERN_E_INVALID;
+  *out = nullptr;
+  bern_ctx* c = new (std::nothrow) bern_ctx();
+  if (!c) return BERN_E_NOMEM;
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    delete c;
+    return map_cuda(e);
+  }
+  *out = c;
+  return BERN_OK;
+}
+
+int bern_destroy(bern_ctx* c) {
+  if (!c) return BERN_OK;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  if (c->gstream) cudaStreamSynchronize(c->gstream);
+  for (auto& g : c->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (auto& kv : c->tables) {
+    kv.second.exps.release();
+    kv.second.mcount.release();
+    for (auto& b : kv.second.bufs) b.release();
+  }
+  c->ws.release();
+  c->stage_in.release();
+  c->stage_out.release();
+  if (c->d_status) cudaFree(c->d_status);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->gstream) cudaStreamDestroy(c->gstream);
+  delete c;
+  return BERN_OK;
+}
+
+int bern_set_pointer_mode(bern_ctx* c, int mode) {
+  if (!c || (mode != BERN_MEM_DEVICE && mode != BERN_MEM_HOST)) return BERN_E_INVALID;
+  c->mem_mode = mode;
+  return BERN_OK;
+}
+
+int bern_set_graphs(bern_ctx* c, int enable) {
+  if (!c) return BERN_E_INVALID;
+  c->use_graphs = enable ? 1 : 0;
+  return BERN_OK;
+}
+
+int bern_sync(bern_ctx* c) {
+  if (!c) return BERN_E_INVALID;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return map_cuda(e);
+  int s = 0;
+  e = cudaMemcpy(&s, c->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return map_cuda(e);
+  if (s) cudaMemset(c->d_status, 0, sizeof(int));
+  return status_to_code(s);
+}
+
+int64_t bern_kernel_launches(const bern_ctx* c) { return c ? c->launches : -1; }
+
+int64_t bern_num_monomials(int n, int D) { return num_monomials(n, D); }
+
+int bern_monomials(int n, int D, uint8_t* exps) {
+  if (!exps || num_monomials(n, D) < 0) return BERN_E_INVALID;
+  if (num_monomials(n, D) > ((int64_t)1 << 26)) return BERN_E_UNSUPPORTED;
+  std::vector<uint8_t> ex;
+  graded_monomials(n, D, ex);
+  std::memcpy(exps, ex.data(), ex.size());
+  return BERN_OK;
+}
+
+int bern_init_inputs(bern_ctx* c, int n, int64_t n_boxes, const float* boxes, float* z_up,
+                     float* z_lo, int64_t stride, int32_t* nterms) {
+  if (!c || n < 1 || n > kMaxVars || n_boxes < 0 || stride < n + 1) return BERN_E_INVALID;
+  cudaSetDevice(c->device);
+  return map_cuda(launch_init_inputs(c->launch(), n, n_boxes, boxes, z_up, z_lo, stride, nterms));
+}
+
+int bern_affine(bern_ctx* c, int64_t n_boxes, int h_out, int h_in, const float* W,
+                const float* b, const float* in_up, const float* in_lo, int64_t in_stride,
+                const int32_t* in_nterms, float* out_up, float* out_lo, int64_t out_stride,
+                int32_t* out_nterms) {
+  if (!c || n_boxes < 0 || h_out < 1 || h_in < 1 || in_stride < 1 || out_stride < 1)
+    return BERN_E_INVALID;
+  cudaSetDevice(c->device);
+  return map_cuda(launch_affine(c->launch(), n_boxes, h_out, h_in, W, b, in_up, in_lo, in_stride,
+                                in_nterms, out_up, out_lo, out_stride, out_nterms));
+}
+
+int bern_enclose(bern_ctx* c, int n, int64_t n_items, int order, int64_t budget,
+                 const float* pre_up, const float* pre_lo, int64_t stride,
+                 const int32_t* nterms, float* lo, float* hi) {
+  if (!c || n < 1 || n > kMaxVars || n_items < 0 || order < 0 || stride < 1)
+    return BERN_E_INVALID;
+  cudaSetDevice(c->device);
+  const Tables* T;
+  int rc = ensure_tables(c, n, 0, &T);
+  if (rc) return rc;
+  if (stride > T->mexps) return BERN_E_UNSUPPORTED;
+  return map_cuda(launch_enclose(c->launch(), *T, n_items, order, budget, pre_up, pre_lo, stride,
+                                 nterms, lo, hi));
+}
+
+int bern_relu_coeffs(bern_ctx* c, int64_t n_items, const float* lo, const float* hi,
+                     const uint8_t* degrees, int global_d, int8_t* kind, float* coef,
+                     float* eps) {
+  if (!c || n_items < 0 || (!degrees && (global_d < 1 || global_d > kMaxOrder)))
+    return BERN_E_INVALID;
+  cudaSetDevice(c->device);
+  return map_cuda(launch_relu_coeffs(c->launch(), n_items, lo, hi, degrees, global_d, kind, coef,
+                                     eps));
+}
+
+int bern_compose(bern_ctx* c, int n, int64_t n_items, int degree_cap, float prune_tau,
+                 const int8_t* kind, const float* coef, const float* eps,
+                 const uint8_t* degrees, int global_d, const float* lo, const float* hi,
+                 const float* pre_up, const float* pre_lo, int64_t pre_stride,
+                 const int32_t* pre_nterms, float* post_up, float* post_lo,
+                 int64_t post_stride, int32_t* post_nterms) {
+  if (!c || n < 1 || n > kMaxVars || n_items < 0 || pre_stride < 1 || post_stride < 1 ||
+      degree_cap < 1 || degree_cap > kMaxTableDegree || !(prune_tau >= 0.0f))
+    return BERN_E_INVALID;
+  cudaSetDevice(c->device);
+  int Dmax = 0;
+  while (Dmax < kMaxTableDegree && num_monomials(n, Dmax + 1) <= pre_stride) ++Dmax;
+  const Tables* T;
+  int rc = ensure_tables(c, n, std::min(Dmax, 32), &T);
+  if (rc) return rc;
+  return map_cuda(launch_compose(c->launch(), *T, n_items, degree_cap, prune_tau, kind, coef, eps,
+                                 degrees, global_d, lo, hi, pre_up, pre_lo, pre_stride,
+                                 pre_nterms, post_up, post_lo, post_stride, post_nterms));
+}
+
+int bern_propagate(bern_ctx* c, const bern_net* net, const float* boxes, int64_t n_boxes,
+                   const bern_degree_plan* plan, bern_result* result) {
+  if (!c || !net || !result || n_boxes < 0 || (!boxes && n_boxes > 0)) return BERN_E_INVALID;
+  if (!result->lo || !result->hi || !result->n_terms || result->cap_terms < 0)
+    return BERN_E_INVALID;
+  cudaSetDevice(c->device);
+  Plan P;
+  int rc = make_plan(net, plan, P);
+  if (rc) return rc;
+  if (n_boxes == 0) return BERN_OK;
+  int dsq = 0;
+  for (const auto& l : P.L)
+    if (l.hidden && l.d >= 2) dsq = std::max(dsq, l.D_pre);
+  const Tables* T;
+  rc = ensure_tables(c, P.n, dsq, &T);
+  if (rc) return rc;
+  for (const auto& l : P.L)
+    if (l.M_pre > T->mexps || l.M_post > T->mexps) return BERN_E_UNSUPPORTED;
+
+  const bool host = c->mem_mode == BERN_MEM_HOST;
+  cudaError_t e;
+  // ---- stage inputs for host mode: boxes, weights, biases
+  const float* d_boxes = boxes;
+  std::vector<const float*> dW(P.H), db(P.H);
+  bern_net dnet = *net;
+  bern_result dres = *result;
+  if (host) {
+    size_t bytes_boxes = sizeof(float) * n_boxes * P.n * 2;
+    size_t wb = 0;
+    for (int i = 0; i < P.H; ++i) wb += (size_t)net->widths[i + 1] * (net->widths[i] + 1);
+    size_t in_bytes = align_up(bytes_boxes) + sizeof(float) * wb + 256 * (2 * P.H + 1);
+    if ((e = c->stage_in.reserve(in_bytes)) != cudaSuccess) return map_cuda(e);
+    char* p = (char*)c->stage_in.p;
+    cudaMemcpyAsync(p, boxes, bytes_boxes, cudaMemcpyHostToDevice, c->stream);
+    d_boxes = (const float*)p;
+    p += align_up(bytes_boxes);
+    for (int i = 0; i < P.H; ++i) {
+      size_t nw = (size_t)net->widths[i + 1] * net->widths[i];
+      cudaMemcpyAsync(p, net->W[i], nw * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+      dW[i] = (const float*)p;
+      p += align_up(nw * sizeof(float));
+      cudaMemcpyAsync(p, net->b[i], net->widths[i + 1] * sizeof(float), cudaMemcpyHostToDevice,
+                      c->stream);
+      db[i] = (const float*)p;
+      p += align_up(net->widths[i + 1] * sizeof(float));
+    }
+    dnet.W = dW.data();
+    dnet.b = db.data();
+    const int64_t no = n_boxes * P.o;
+    size_t out_bytes = align_up(no * sizeof(float)) * 2 + align_up(no * 2 * sizeof(int32_t));
+    if (result->coef) out_bytes += align_up(no * 2 * result->cap_terms * sizeof(float));
+    if (result->keys) out_bytes += align_up(no * 2 * result->cap_terms * sizeof(uint64_t));
+    if ((e = c->stage_out.reserve(out_bytes)) != cudaSuccess) return map_cuda(e);
+    char* q = (char*)c->stage_out.p;
+    dres.lo = (float*)q;
+    q += align_up(no * sizeof(float));
+    dres.hi = (float*)q;
+    q += align_up(no * sizeof(float));
+    dres.n_terms = (int32_t*)q;
+    q += align_up(no * 2 * sizeof(int32_t));
+    if (result->coef) {
+      dres.coef = (float*)q;
+      q += align_up(no * 2 * result->cap_terms * sizeof(float));
+    }
+    if (result->keys) dres.keys = (uint64_t*)q;
+  }
+  // ---- workspace: chunk of boxes that fits the budget
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  size_t limit = std::max<size_t>(c->ws.bytes, std::min<size_t>(free_b / 2, (size_t)24 << 30));
+  int64_t chunk = std::max<int64_t>(1, (int64_t)(limit / P.per_box));
+  chunk = std::min(chunk, n_boxes);
+  if ((e = c->ws.reserve(P.per_box * chunk)) != cudaSuccess) return map_cuda(e);
+
+  for (int64_t b0 = 0; b0 < n_boxes; b0 += chunk) {
+    const int64_t B = std::min(chunk, n_boxes - b0);
+    Chunk ch{(char*)c->ws.p, B};
+    bern_result r = dres;
+    r.lo = dres.lo + b0 * P.o;
+    r.hi = dres.hi + b0 * P.o;
+    r.n_terms = dres.n_terms + b0 * P.o * 2;
+    if (r.coef) r.coef = dres.coef + b0 * P.o * 2 * r.cap_terms;
+    if (r.keys) r.keys = dres.keys + b0 * P.o * 2 * r.cap_terms;
+    const float* bx = d_boxes + b0 * P.n * 2;
+    if ((rc = fill_degrees(c, P, ch, B))) return rc;
+    if (c->use_graphs) {
+      std::string key = graph_key(P, &dnet, bx, B, r, c->ws.p);
+      GraphEntry* g = nullptr;
+      for (auto& x : c->graphs)
+        if (x.key == key) g = &x;
+      if (!g) {
+        cudaGraph_t graph;
+        const int64_t before = c->launches;
+        e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return map_cuda(e);
+        rc = run_chunk(c, c->gstream, P, *T, &dnet, bx, B, ch, r.lo, r.hi, r);
+        e = cudaStreamEndCapture(c->gstream, &graph);
+        if (rc) return rc;
+        if (e != cudaSuccess) return map_cuda(e);
+        GraphEntry ge;
+        ge.key = key;
+        ge.kernels = c->launches - before;
+        c->launches = before;
+        e = cudaGraphInstantiate(&ge.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return map_cuda(e);
+        if (c->graphs.size() >= 16) {
+          cudaGraphExecDestroy(c->graphs.front().exec);
+          c->graphs.erase(c->graphs.begin());
+        }
+        c->graphs.push_back(ge);
+        g = &c->graphs.back();
+      }
+      // fork onto the private stream, replay, join back
+      if ((e = cudaEventRecord(c->ev_fork, c->stream)) != cudaSuccess) return map_cuda(e);
+      if ((e = cudaStreamWaitEvent(c->gstream, c->ev_fork, 0)) != cudaSuccess) return map_cuda(e);
+      if ((e = cudaGraphLaunch(g->exec, c->gstream)) != cudaSuccess) return map_cuda(e);
+      if ((e = cudaEventRecord(c->ev_join, c->gstream)) != cudaSuccess) return map_cuda(e);
+      if ((e = cudaStreamWaitEvent(c->stream, c->ev_join, 0)) != cudaSuccess) return map_cuda(e);
+      c->launches += g->kernels;
+    } else {
+      rc = run_chunk(c, c->stream, P, *T, &dnet, bx, B, ch, r.lo, r.hi, r);
+      if (rc) return rc;
+    }
+  }
+  if (host) {
+    const int64_t no = n_boxes * P.o;
+    cudaMemcpyAsync(result->lo, dres.lo, no * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(result->hi, dres.hi, no * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(result->n_terms, dres.n_terms, no * 2 * sizeof(int32_t),
+                    cudaMemcpyDeviceToHost, c->stream);
+    if (result->coef)
+      cudaMemcpyAsync(result->coef, dres.coef, no * 2 * result->cap_terms * sizeof(float),
+                      cudaMemcpyDeviceToHost, c->stream);
+    if (result->keys)
+      cudaMemcpyAsync(result->keys, dres.keys, no * 2 * result->cap_terms * sizeof(uint64_t),
+                      cudaMemcpyDeviceToHost, c->stream);
+    return bern_sync(c);
+  }
+  e = cudaGetLastError();
+  return map_cuda(e);
+}
+
+}  // extern "C"

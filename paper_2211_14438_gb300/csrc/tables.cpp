@@ -1,0 +1,84 @@
+// Host-side monomial tables: the graded order and the pair lists that drive
+// the composition kernel's polynomial products (the power-series product
+// "Prod" of Sec. 4.2, here over a shared dense graded monomial set).
+#include <algorithm>
+#include <unordered_map>
+
+#include "bern_internal.cuh"
+
+namespace bern {
+
+int64_t num_monomials(int n, int D) {
+  if (n < 1 || n > kMaxVars || D < 0 || D > kMaxTableDegree) return -1;
+  // C(n+D, n) by the multiplicative formula (exact in 64 bits here)
+  unsigned __int128 r = 1;
+  for (int i = 1; i <= n; ++i) r = r * (unsigned)(D + i) / (unsigned)i;
+  return (int64_t)r;
+}
+
+uint64_t pack_key(const uint8_t* e, int n) {
+  uint64_t k = 0;
+  for (int i = 0; i < n; ++i) k |= (uint64_t)e[i] << (8 * i);
+  return k;
+}
+
+// all exponent vectors of n variables with sum g, descending lexicographic
+static void rec(int n, int pos, int left, std::vector<uint8_t>& cur,
+                std::vector<uint8_t>& out) {
+  if (pos == n - 1) {
+    cur[pos] = (uint8_t)left;
+    out.insert(out.end(), cur.begin(), cur.end());
+    return;
+  }
+  for (int e = left; e >= 0; --e) {
+    cur[pos] = (uint8_t)e;
+    rec(n, pos + 1, left - e, cur, out);
+  }
+}
+
+void graded_monomials(int n, int D, std::vector<uint8_t>& exps) {
+  exps.clear();
+  std::vector<uint8_t> cur(n, 0);
+  for (int g = 0; g <= D; ++g) rec(n, 0, g, cur, exps);
+}
+
+static bool build_pairs(int n, int Dq, int Ds, bool symmetric, PairList& out) {
+  const int64_t mq = num_monomials(n, Dq), ms = num_monomials(n, Ds);
+  const int64_t mo = num_monomials(n, Dq + Ds);
+  if (mq < 0 || ms < 0 || mo < 0 || mq > 65535 || ms > 65535) return false;
+  if (mo > (int64_t)1 << 30) return false;
+  std::vector<uint8_t> ex;
+  graded_monomials(n, Dq + Ds, ex);
+  std::unordered_map<uint64_t, int32_t> rank;
+  rank.reserve((size_t)mo * 2);
+  for (int64_t r = 0; r < mo; ++r) rank[pack_key(&ex[(size_t)r * n], n)] = (int32_t)r;
+  std::vector<uint64_t> kq(mq), ks(ms);
+  for (int64_t r = 0; r < mq; ++r) kq[r] = pack_key(&ex[(size_t)r * n], n);
+  for (int64_t r = 0; r < ms; ++r) ks[r] = pack_key(&ex[(size_t)r * n], n);
+  // exponents are < 256 in every slot, so key addition never carries
+  std::vector<int32_t> cnt(mo + 1, 0);
+  for (int64_t i = 0; i < mq; ++i)
+    for (int64_t j = symmetric ? i : 0; j < ms; ++j) cnt[rank.at(kq[i] + ks[j]) + 1]++;
+  out.ptr.assign(mo + 1, 0);
+  for (int64_t k = 0; k < mo; ++k) out.ptr[k + 1] = out.ptr[k] + cnt[k + 1];
+  out.pairs.assign((size_t)out.ptr[mo], 0);
+  std::vector<int32_t> fill(out.ptr.begin(), out.ptr.end() - 1);
+  for (int64_t i = 0; i < mq; ++i)
+    for (int64_t j = symmetric ? i : 0; j < ms; ++j) {
+      int32_t k = rank.at(kq[i] + ks[j]);
+      out.pairs[(size_t)fill[k]++] = (uint32_t)i | ((uint32_t)j << 16);
+    }
+  out.m_in = mq;
+  out.m_out = mo;
+  return true;
+}
+
+bool build_square_pairs(int n, int D, PairList& out) {
+  return build_pairs(n, D, D, true, out);
+}
+
+bool build_product_pairs(int n, int Dq, int Ds, PairList& out) {
+  return build_pairs(n, Dq, Ds, false, out);
+}
+
+}  // namespace bern

@@ -1,0 +1,272 @@
+"""Whole-path parity (bern_propagate through the C ABI) against the FP64
+oracle, Monte-Carlo soundness, and the edge cases of the boundary.
+
+Tolerance (float32 path vs float64 oracle): every output bound within
+1e-4 * (1 + |bound|), and every output polynomial within 1e-4 * (1 + ||p||_1)
+in the sum of absolute coefficient differences (a sup-norm bound of the
+difference on the box, since each monomial lies in [0,1]).  A box where the
+oracle sees a hidden neuron with |lo| or |hi| within 1e-5 relative of 0 is a
+genuine tie (float32 and float64 may take different ReLU cases there); such a
+box is checked for soundness only."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2211_14438_gb300 import bern
+from paper_2211_14438_gb300 import workloads as wl
+from parity_util import dense_from_dict, eval_dense, l1
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = bern.Context(0)
+    yield c
+    c.close()
+
+
+def run_gpu(ctx, net, boxes, degree=2, cap=16, **kw):
+    W = [torch.from_numpy(w).cuda() for w in net.W]
+    b = [torch.from_numpy(x).cuda() for x in net.b]
+    out = ctx.propagate(net.widths, W, b, torch.from_numpy(np.ascontiguousarray(boxes)).cuda(),
+                        degree=degree, cap=cap, **kw)
+    return {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+
+
+def near_tie(r, rel=1e-5):
+    lo, hi = r["tr_lo"], r["tr_hi"]
+    sc = 1 + np.maximum(np.abs(lo), np.abs(hi))
+    return bool(np.any(np.minimum(np.abs(lo), np.abs(hi)) <= rel * sc))
+
+
+def gpu_t(box, x):
+    """The library's normalised coordinates: t = (x - dlo) / w, w = fl_up(dhi - dlo)."""
+    lo = box[:, 0].astype(np.float32)
+    w = (box[:, 1].astype(np.float64) - lo.astype(np.float64))
+    wf = w.astype(np.float32)
+    wf = np.where(wf.astype(np.float64) < w, np.nextafter(wf, np.float32(np.inf)), wf)
+    return (x - lo.astype(np.float64)) / np.where(wf > 0, wf, 1.0).astype(np.float64)
+
+
+def compare_box(g, bi, r, n, o, check_polys=True):
+    for j in range(o):
+        lo_g, hi_g = float(g["lo"][bi, j]), float(g["hi"][bi, j])
+        assert abs(lo_g - r["lo"][j]) <= TOL * (1 + abs(r["lo"][j])), (bi, j, lo_g, r["lo"][j])
+        assert abs(hi_g - r["hi"][j]) <= TOL * (1 + abs(r["hi"][j])), (bi, j, hi_g, r["hi"][j])
+        if not check_polys:
+            continue
+        for k, name in ((0, "upper"), (1, "lower")):
+            nt = int(g["n_terms"][bi, j, k])
+            gv = g["coef"][bi, j, k, :nt].astype(np.float64)
+            ov = dense_from_dict(r[name][j], n, nt)
+            assert np.abs(gv - ov).sum() <= TOL * (1 + l1(ov)), (bi, j, name)
+
+
+def mc_check(g, bi, net, box, count, rng):
+    n, o = net.n_in, net.n_out
+    t = rng.random((count, n))
+    corners = np.array(np.meshgrid(*([[0.0, 1.0]] * n), indexing="ij")).reshape(n, -1).T
+    t[: min(len(corners), count)] = corners[: min(len(corners), count)]
+    lo = box[:, 0].astype(np.float64)
+    hi = box[:, 1].astype(np.float64)
+    x = lo + t * (hi - lo)
+    nn = oracle.network_forward(net.widths, net.W, net.b, x)
+    tg = gpu_t(box, x)
+    viol = 0
+    for j in range(o):
+        nt_u, nt_l = int(g["n_terms"][bi, j, 0]), int(g["n_terms"][bi, j, 1])
+        up = eval_dense(g["coef"][bi, j, 0, :nt_u].astype(np.float64), n, tg)
+        lw = eval_dense(g["coef"][bi, j, 1, :nt_l].astype(np.float64), n, tg)
+        e = 1e-12 * (1 + np.abs(nn[:, j]) + l1(g["coef"][bi, j, 0, :nt_u]))
+        viol += int(np.sum(nn[:, j] > up + e)) + int(np.sum(nn[:, j] < lw - e))
+        viol += int(np.sum(nn[:, j] > g["hi"][bi, j] + e)) + int(np.sum(nn[:, j] < g["lo"][bi, j] - e))
+    return viol
+
+
+def test_config1_parity_and_soundness(ctx):
+    w = wl.config1()
+    g = run_gpu(ctx, w.net, w.boxes)
+    r = oracle.propagate(w.net.widths, w.net.W, w.net.b, w.boxes[0], 2)
+    assert not near_tie(r)
+    compare_box(g, 0, r, 2, 1)
+    assert mc_check(g, 0, w.net, w.boxes[0], 1_000_000, np.random.default_rng(1)) == 0
+
+
+def test_config2_parity_and_soundness(ctx):
+    w = wl.config2()
+    g = run_gpu(ctx, w.net, w.boxes)
+    r = oracle.propagate(w.net.widths, w.net.W, w.net.b, w.boxes[0], 2)
+    assert not near_tie(r)
+    compare_box(g, 0, r, 4, 2)
+    assert mc_check(g, 0, w.net, w.boxes[0], 200_000, np.random.default_rng(2)) == 0
+
+
+def test_config3_full_batch_sampled(ctx):
+    """The benchmark's launch configuration: all 5120 boxes in one call;
+    sampled boxes are checked against the oracle one by one, and every box
+    against properties that hold at any size."""
+    w = wl.config3()
+    g = run_gpu(ctx, w.net, w.boxes)
+    B = len(w.boxes)
+    assert np.all(np.isfinite(g["lo"])) and np.all(g["lo"] <= g["hi"])
+    nt = g["n_terms"][:, 0, 0]
+    assert np.all(nt >= 1) and np.all(nt <= bern.num_monomials(3, 16))
+    rng = np.random.default_rng(3)
+    sample = [0, 1, 2047, 4095, 4096, 5119] + list(rng.choice(B, 4, replace=False))
+    checked = 0
+    for bi in sample:
+        r = oracle.propagate(w.net.widths, w.net.W, w.net.b, w.boxes[bi], 2)
+        if not near_tie(r):
+            compare_box(g, bi, r, 3, 1)
+            checked += 1
+        assert mc_check(g, bi, w.net, w.boxes[bi], 100_000, rng) == 0
+    assert checked >= len(sample) - 2
+    # every box: the bound contains the network at the box centre and corners
+    for bi in range(0, B, 97):
+        box = w.boxes[bi]
+        assert mc_check(g, bi, w.net, box, 9, rng) == 0
+
+
+def test_config3_small_batch_matches_full(ctx):
+    """A ragged batch (37 boxes, several tiles and a tail) gives the same
+    numbers as the same boxes inside the full batch (no cross-box state)."""
+    w = wl.config3()
+    idx = np.r_[0:20, 4096:4113]
+    g_small = run_gpu(ctx, w.net, w.boxes[idx])
+    g_full = run_gpu(ctx, w.net, w.boxes)
+    assert np.array_equal(g_small["lo"], g_full["lo"][idx])
+    assert np.array_equal(g_small["hi"], g_full["hi"][idx])
+    assert np.array_equal(g_small["n_terms"], g_full["n_terms"][idx])
+
+
+@pytest.mark.parametrize("widths,degree,seed", [
+    ([1, 8, 8, 1], 2, 11), ([2, 6, 5, 3], [2, 1], 12), ([3, 10, 10, 2], 1, 13),
+    ([5, 12, 7, 1], 2, 14), ([8, 6, 4, 2], 2, 15), ([2, 20, 20, 1], 2, 16)])
+def test_small_nets_parity(ctx, widths, degree, seed):
+    net = wl.make_net(widths, seed)
+    rng = np.random.default_rng(seed)
+    n = widths[0]
+    c = rng.uniform(-1, 1, (5, n))
+    s = rng.uniform(0.05, 1.0, (5, n))
+    boxes = wl.box_array(c - s / 2, c + s / 2)
+    g = run_gpu(ctx, net, boxes, degree=degree)
+    dl = degree if isinstance(degree, int) else None
+    for bi in range(len(boxes)):
+        if dl is None:
+            degs = np.concatenate([np.full(h, d) for h, d in zip(widths[1:-1], degree)])
+        else:
+            degs = dl
+        r = oracle.propagate(widths, net.W, net.b, boxes[bi], degs)
+        if near_tie(r):
+            continue
+        compare_box(g, bi, r, n, widths[-1])
+        assert mc_check(g, bi, net, boxes[bi], 20_000, rng) == 0
+
+
+def test_paper_family_nets(ctx):
+    """The paper's own ablation family (weights U(-5,5)), [2,20,20,1] on
+    [-1,1]^2 with L = 2, 3, 4: parity and soundness."""
+    net = wl.paper_net(2, [20, 20], seed=101)
+    box = wl.box_array([-1, -1], [1, 1])[None]
+    for d in (2, 3, 4):
+        if d > 2:
+            pytest.skip("orders above 2 are not implemented in the composition kernel yet")
+        g = run_gpu(ctx, net, box, degree=d)
+        r = oracle.propagate(net.widths, net.W, net.b, box[0], d)
+        if not near_tie(r):
+            compare_box(g, 0, r, 2, 1)
+        assert mc_check(g, 0, net, box[0], 200_000, np.random.default_rng(d)) == 0
+
+
+# ------------------------------------------------------------ edge cases
+def test_empty_batch(ctx):
+    w = wl.config1()
+    g = run_gpu(ctx, w.net, w.boxes[:0])
+    assert g["lo"].shape == (0, 1)
+
+
+def test_point_box_gives_network_value(ctx):
+    w = wl.config2()
+    x = np.array([0.1, -0.2, 0.3, 0.05], np.float32)
+    box = np.stack([x, x], -1)[None]
+    g = run_gpu(ctx, w.net, box)
+    nn = oracle.network_forward(w.net.widths, w.net.W, w.net.b, x[None].astype(np.float64))[0]
+    assert np.all(g["lo"][0] <= nn + 1e-5 * (1 + abs(nn)))
+    assert np.all(g["hi"][0] >= nn - 1e-5 * (1 + abs(nn)))
+    assert np.all(g["hi"][0] - g["lo"][0] <= 1e-4 * (1 + abs(nn)))
+
+
+def test_invalid_box_reported(ctx):
+    w = wl.config1()
+    bad = np.array([[[0.5, -0.5], [0.0, 1.0]]], np.float32)
+    with pytest.raises(bern.BernError) as ei:
+        run_gpu(ctx, w.net, bad)
+    assert ei.value.code == bern.BERN_E_INVALID
+    bad = np.array([[[np.nan, 0.5], [0.0, 1.0]]], np.float32)
+    with pytest.raises(bern.BernError):
+        run_gpu(ctx, w.net, bad)
+    assert ctx.sync() == 0
+
+
+def test_capacity_too_small_reports_need(ctx):
+    w = wl.config1()
+    with pytest.raises(bern.BernError) as ei:
+        run_gpu(ctx, w.net, w.boxes, cap_terms=4)
+    assert ei.value.code == bern.BERN_E_CAPACITY
+
+
+def test_all_dead_and_all_active(ctx):
+    rng = np.random.default_rng(9)
+    W1 = rng.normal(size=(4, 3)).astype(np.float32)
+    W2 = rng.normal(size=(2, 4)).astype(np.float32)
+    b2 = np.array([0.5, -1.25], np.float32)
+    box = np.array([[[-1, 1]] * 3], np.float32)
+    dead = wl.Net([3, 4, 2], [W1, W2], [np.full(4, -50, np.float32), b2])
+    g = run_gpu(ctx, dead, box)
+    assert np.array_equal(g["lo"][0], b2) and np.array_equal(g["hi"][0], b2)
+    act = wl.Net([3, 4, 2], [W1, W2], [np.full(4, 50, np.float32), b2])
+    g = run_gpu(ctx, act, box)
+    r = oracle.propagate([3, 4, 2], act.W, act.b, box[0], 2)
+    compare_box(g, 0, r, 3, 2)
+
+
+def test_host_mode_matches_device_mode(ctx):
+    w = wl.config3(n_random=8, cells=2)
+    g = run_gpu(ctx, w.net, w.boxes)
+    h = ctx.propagate_host(w.net.widths, w.net.W, w.net.b, w.boxes, degree=2)
+    assert np.array_equal(h["lo"], g["lo"]) and np.array_equal(h["hi"], g["hi"])
+    assert np.array_equal(h["n_terms"], g["n_terms"])
+    for bi in range(len(w.boxes)):
+        nt = g["n_terms"][bi, 0, 0]
+        assert np.array_equal(h["coef"][bi, 0, :, :nt], g["coef"][bi, 0, :, :nt])
+
+
+def test_graphs_on_off_identical_and_counted(ctx):
+    w = wl.config3(n_random=16, cells=4)
+    before = ctx.kernel_launches()
+    ctx.set_graphs(False)
+    a = run_gpu(ctx, w.net, w.boxes)
+    mid = ctx.kernel_launches()
+    ctx.set_graphs(True)
+    b = run_gpu(ctx, w.net, w.boxes)
+    c = run_gpu(ctx, w.net, w.boxes)
+    after = ctx.kernel_launches()
+    assert mid > before and after > mid
+    for k in ("lo", "hi", "n_terms", "coef"):
+        assert np.array_equal(a[k], b[k]) and np.array_equal(b[k], c[k])
+
+
+def test_output_keys_are_graded_monomials(ctx):
+    w = wl.config1()
+    g = run_gpu(ctx, w.net, w.boxes, keys=True)
+    nt = int(g["n_terms"][0, 0, 0])
+    ex = bern.monomials(2, 4)[:nt].astype(np.int64)
+    want = ex[:, 0] | (ex[:, 1] << 8)
+    assert np.array_equal(g["keys"][0, 0, 0, :nt], want)
+    assert np.array_equal(g["keys"][0, 0, 1, :nt], want)
