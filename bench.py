@@ -1,0 +1,533 @@
+"""Benchmark: input boxes propagated per second (BERN-NN bounds) on GB300.
+
+Workload: the batched plain method, ReLU MLP [3, 64, 64, 64, 64, 1] (seed 2),
+5120 boxes (the 16^3 grid of [-1,1]^3 plus 1024 random boxes with sides
+U(0.01,0.5)), Bernstein ReLU order 2, total-degree cap 16.  A step is one
+bern_propagate over all 5120 boxes (init, 5 affine steps, 5 enclosures, 4
+ReLU-coefficient and composition steps, output copy-out), replayed as one CUDA
+graph.  L2 is flushed (256 MB write) before every timed step, outside the
+timed interval; each step is timed with CUDA events on the launching stream.
+
+Multi-GPU (torchrun): every rank propagates its own full batch (weak
+scaling); there is no collective on the data path, only a barrier and a max
+over ranks of the timed region.
+
+Also reported: per-kernel durations (a second K-step pass through the
+step-level C ABI, events around every launch), the roofline of the dominant
+kernel, the end-to-end rate through bern_propagate with host buffers, the
+FP64 oracle on the host cores, and SM clocks sampled during the timed region.
+
+--impl reference times the FP64 oracle (the reference for this build) on the
+host cores with the same metric and workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "input boxes propagated/sec at fixed mean output-bound width; % of HBM roofline"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+FP32_LANES_PER_SM = 128
+
+
+# ---------------------------------------------------------------- helpers
+def load_peaks():
+    if os.path.exists(PEAKS_FILE):
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def oracle_box(args):
+    """One box through the FP64 oracle (runs in a spawned worker)."""
+    import oracle as orc
+    widths, W, b, box, degree = args
+    t0 = time.perf_counter()
+    orc.propagate(widths, W, b, box, degree)
+    return time.perf_counter() - t0
+
+
+def oracle_rate(pool, cores, w, sample_idx):
+    jobs = [(w.net.widths, w.net.W, w.net.b, w.boxes[i], w.degree) for i in sample_idx]
+    t0 = time.perf_counter()
+    pool.map(oracle_box, jobs, chunksize=1)
+    wall = time.perf_counter() - t0
+    return len(sample_idx) / wall, wall
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows]
+        util = [num(r[4]) for r in rows]
+        loaded = [s for s, u in zip(sm, util) if s is not None and u is not None and u >= 50]
+        use = loaded if loaded else [s for s in sm if s is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[6:10]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(use)) if use else None,
+                "sm_max_mhz": num(rows[0][2]), "reasons": sorted(reasons),
+                "samples": len(rows), "samples_under_load": len(loaded),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+# ----------------------------------------------------- per-kernel timing pass
+class KernelPass:
+    """Drives the same kernels as bern_propagate through the step-level C ABI
+    on torch-allocated buffers, with CUDA events around every launch on the
+    launching stream; keeps the intermediates for algorithmic-work counts."""
+
+    def __init__(self, ctx, torch, w, Wd, bd, boxes_d):
+        from paper_2211_14438_gb300 import bern
+        self.bern, self.torch, self.ctx = bern, torch, ctx
+        self.w, self.Wd, self.bd, self.boxes = w, Wd, bd, boxes_d
+        widths = w.net.widths
+        self.n, self.B, self.H = widths[0], len(w.boxes), len(widths) - 1
+        dev = boxes_d.device
+        n, B = self.n, self.B
+        f32, i32 = torch.float32, torch.int32
+        self.z = [torch.empty(B * n * (n + 1), device=dev, dtype=f32) for _ in range(2)]
+        self.znt = torch.empty(B * n, device=dev, dtype=i32)
+        self.layers = []
+        D = 1
+        order = 1
+        for i in range(self.H):
+            h = widths[i + 1]
+            hidden = i < self.H - 1
+            Mpre = bern.num_monomials(n, D)
+            L = {"h_in": widths[i], "h": h, "hidden": hidden, "D": D, "order": order,
+                 "Mpre": Mpre,
+                 "pre": [torch.empty(B * h * Mpre, device=dev, dtype=f32) for _ in range(2)],
+                 "pre_nt": torch.empty(B * h, device=dev, dtype=i32),
+                 "lo": torch.empty(B * h, device=dev, dtype=f32),
+                 "hi": torch.empty(B * h, device=dev, dtype=f32)}
+            if hidden:
+                Dp = min(D * w.degree, w.degree_cap)
+                Mpost = bern.num_monomials(n, Dp)
+                L.update({"Mpost": Mpost,
+                          "kind": torch.empty(B * h, device=dev, dtype=torch.int8),
+                          "coef": torch.empty(B * h * bern.COEF_STRIDE, device=dev, dtype=f32),
+                          "eps": torch.empty(B * h, device=dev, dtype=f32),
+                          "post": [torch.empty(B * h * Mpost, device=dev, dtype=f32)
+                                   for _ in range(2)],
+                          "post_nt": torch.empty(B * h, device=dev, dtype=i32)})
+                D, order = Dp, min(order * w.degree, w.degree_cap)
+            self.layers.append(L)
+        self.times = {}
+
+    def _timed(self, name, fn):
+        t = self.torch
+        s, e = t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)
+        st = self.ctx.stream
+        s.record(st)
+        fn()
+        e.record(st)
+        self.pending.append((name, s, e))
+
+    def step(self):
+        ctx, w = self.ctx, self.w
+        n, B = self.n, self.B
+        self.pending = []
+        self._timed("init", lambda: ctx.init_inputs(n, self.boxes, self.z[0], self.z[1], n + 1,
+                                                    self.znt))
+        in_u, in_l, in_nt, in_stride = self.z[0], self.z[1], self.znt, n + 1
+        for i, L in enumerate(self.layers):
+            self._timed("affine_L%d" % (i + 1), lambda: ctx.affine(
+                B, L["h"], L["h_in"], self.Wd[i], self.bd[i], in_u, in_l, in_stride, in_nt,
+                L["pre"][0], L["pre"][1], L["Mpre"], L["pre_nt"]))
+            self._timed("enclose_L%d" % (i + 1), lambda: ctx.enclose(
+                n, B * L["h"], L["order"], 0, L["pre"][0], L["pre"][1], L["Mpre"], L["pre_nt"],
+                L["lo"], L["hi"]))
+            if not L["hidden"]:
+                break
+            self._timed("relu_L%d" % (i + 1), lambda: ctx.relu_coeffs(
+                B * L["h"], L["lo"], L["hi"], None, w.degree, L["kind"], L["coef"], L["eps"]))
+            self._timed("compose_L%d" % (i + 1), lambda: ctx.compose(
+                n, B * L["h"], w.degree_cap, 0.0, L["kind"], L["coef"], L["eps"], None, w.degree,
+                L["lo"], L["hi"], L["pre"][0], L["pre"][1], L["Mpre"], L["pre_nt"],
+                L["post"][0], L["post"][1], L["Mpost"], L["post_nt"]))
+            in_u, in_l, in_nt, in_stride = L["post"][0], L["post"][1], L["post_nt"], L["Mpost"]
+
+    def collect(self):
+        self.torch.cuda.synchronize()
+        for name, s, e in self.pending:
+            self.times.setdefault(name, []).append(s.elapsed_time(e))
+
+    def work(self):
+        """Algorithmic bytes and flops per launch of every kernel, from the
+        intermediates of the last step (actual term counts and ReLU cases)."""
+        bern = self.bern
+        n, B = self.n, self.B
+        out = {}
+        in_nt = self.znt.cpu().numpy().reshape(B, n).astype(np.int64)
+        for i, L in enumerate(self.layers):
+            h = L["h"]
+            pre_nt = L["pre_nt"].cpu().numpy().reshape(B, h).astype(np.int64)
+            Mb = pre_nt[:, 0]
+            rd = 2 * 4 * in_nt.sum()
+            wr = 2 * 4 * h * Mb.sum()
+            out["affine_L%d" % (i + 1)] = {"bytes": float(rd + wr),
+                                           "flops": float(4 * h * in_nt.sum())}
+            lb = L["order"]
+            g_lines = n * (lb + 1) ** (n - 1) * lb * (lb + 1) // 2
+            out["enclose_L%d" % (i + 1)] = {"bytes": float(2 * 4 * pre_nt.sum() + 8 * B * h),
+                                            "flops": float(2 * B * h * g_lines)}
+            if not L["hidden"]:
+                break
+            kind = L["kind"].cpu().numpy().reshape(B, h)
+            post_nt = L["post_nt"].cpu().numpy().reshape(B, h).astype(np.int64)
+            act = kind == 1
+            unst = kind == 2
+            rd = 2 * 4 * (pre_nt[act].sum() + pre_nt[unst].sum())
+            wr = 2 * 4 * (post_nt[act].sum() + post_nt[unst].sum())
+            Mp = pre_nt[unst]
+            pairs = (Mp * (Mp + 1) // 2).sum()
+            out["compose_L%d" % (i + 1)] = {"bytes": float(rd + wr),
+                                            "flops": float(2 * 2 * pairs + 2 * 2 * post_nt[unst].sum()),
+                                            "unstable": int(unst.sum()), "active": int(act.sum()),
+                                            "items": int(B * h)}
+            out["relu_L%d" % (i + 1)] = {"bytes": float(8 * B * h + 41 * unst.sum()), "flops": 0.0}
+            in_nt = post_nt
+        out["init"] = {"bytes": float(B * n * 8 + 2 * B * n * (n + 1) * 4), "flops": 0.0}
+        return out
+
+
+def source_sha(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+KERNEL_SOURCES = {"affine": "k_affine.cu", "enclose": "k_enclose.cu", "compose": "k_compose.cu",
+                  "relu": "k_enclose.cu", "init": "k_io.cu"}
+
+
+def ncu_traffic(kernel_key):
+    """DRAM bytes per launch from a committed ncu summary, if its kernel
+    source is unchanged since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    rec = d.get(kernel_key)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2211_14438_gb300", "csrc",
+                       KERNEL_SOURCES[kernel_key.split("_")[0]])
+    if rec.get("source_sha") != source_sha(src):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank, dist):
+    import torch
+    from paper_2211_14438_gb300 import bern, build
+    from paper_2211_14438_gb300 import workloads as wl
+
+    pool = None
+    cores = 0
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = min(os.cpu_count() or 1, 16)
+        pool = mp.get_context("spawn").Pool(cores)   # before the first GPU call
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = wl.config3()
+    B = len(w.boxes)
+    ctx = bern.Context(local_rank, stream=torch.cuda.current_stream(dev))
+    stream = ctx.stream
+    Wd = [torch.from_numpy(x).to(dev) for x in w.net.W]
+    bd = [torch.from_numpy(x).to(dev) for x in w.net.b]
+    boxes_d = torch.from_numpy(w.boxes).to(dev)
+    cap_terms = bern.max_output_terms(w.net.widths, w.degree, w.degree_cap)
+    o = w.net.n_out
+    out = {"lo": torch.empty(B, o, device=dev), "hi": torch.empty(B, o, device=dev),
+           "n_terms": torch.empty(B, o, 2, device=dev, dtype=torch.int32),
+           "coef": torch.empty(B, o, 2, cap_terms, device=dev), "keys": None}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        ctx.propagate(w.net.widths, Wd, bd, boxes_d, degree=w.degree, cap=w.degree_cap,
+                      cap_terms=cap_terms, out=out, sync=False)
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    for _ in range(args.warmup):
+        step()
+    rc = ctx.sync()
+    if rc != 0:
+        raise RuntimeError("propagate failed: %s" % bern.strerror(rc))
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = ctx.kernel_launches()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    launches = ctx.kernel_launches() - launches0
+    rc = ctx.sync()
+    if rc != 0:
+        raise RuntimeError("propagate failed: %s" % bern.strerror(rc))
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_local = float(np.sum(ms)) / args.steps
+    from paper_2211_14438_gb300.sharding import max_over_ranks
+    ms_step = max_over_ranks(ms_local, world, dist, dev)
+    value = world * B / (ms_step / 1e3)
+
+    lo = out["lo"].cpu().numpy()[:, 0].astype(np.float64)
+    hi = out["hi"].cpu().numpy()[:, 0].astype(np.float64)
+    nt = out["n_terms"].cpu().numpy()[:, 0, 0]
+    coef = out["coef"].cpu().numpy()[:, 0].astype(np.float64)
+    ex = bern.monomials(w.net.n_in, w.degree_cap).astype(np.float64)
+    inv = 1.0 / np.prod(ex + 1.0, axis=1)
+    vol = np.array([((coef[i, 0, :nt[i]] - coef[i, 1, :nt[i]]) * inv[:nt[i]]).sum()
+                    for i in range(B)])
+
+    # ---- per-kernel pass (same kernels through the step ABI)
+    kp = KernelPass(ctx, torch, w, Wd, bd, boxes_d)
+    for _ in range(max(1, args.warmup)):
+        kp.step()
+    kp.collect()
+    kp.times = {}
+    for _ in range(args.steps):
+        flush.zero_()
+        kp.step()
+        kp.collect()
+    rc = ctx.sync()
+    if rc != 0:
+        raise RuntimeError("kernel pass failed: %s" % bern.strerror(rc))
+    work = kp.work()
+    avg = {k: float(np.mean(v)) for k, v in kp.times.items()}
+    total_kernel_ms = sum(avg.values())
+    dom = max(avg, key=lambda k: avg[k])
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    wk = work.get(dom, {"bytes": 0.0, "flops": 0.0})
+    sec = avg[dom] / 1e3
+    gbs = wk["bytes"] / sec / 1e9
+    tfs = wk["flops"] / sec / 1e12
+    # the bound is whichever roof the kernel's arithmetic intensity hits first
+    ridge = fp32_peak * 1e12 / (hbm * 1e9)
+    inten = wk["flops"] / max(wk["bytes"], 1.0)
+    if inten < ridge:
+        roof = {"bound": "hbm", "achieved": round(gbs, 2), "peak": hbm, "unit": "GB/s",
+                "frac": round(gbs / hbm, 4)}
+    else:
+        roof = {"bound": "alu", "achieved": round(tfs, 3), "peak": round(fp32_peak, 2),
+                "unit": "TFLOP/s", "frac": round(tfs / fp32_peak, 4)}
+    roof["kernel"] = dom
+    roof["peak_source"] = ("%s (%s)" % (PEAKS_FILE.split("/")[-1], peak_kind)
+                           if roof["bound"] == "hbm" else
+                           "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz" %
+                           (sm_count, float(peaks.get("sm_max_mhz", 2070.0))))
+    roof["traffic"] = ncu_traffic(dom)
+    roof["algorithmic_bytes"] = wk["bytes"]
+    roof["algorithmic_flops"] = wk["flops"]
+    roof["avg_launch_ms"] = round(avg[dom], 4)
+    kernels = {k: {"ms": round(v, 4), "share": round(v / total_kernel_ms, 4),
+                   "GBps": round(work.get(k, {}).get("bytes", 0) / (v / 1e3) / 1e9, 1),
+                   "TFLOPs": round(work.get(k, {}).get("flops", 0) / (v / 1e3) / 1e12, 3)}
+               for k, v in sorted(avg.items(), key=lambda kv: -kv[1])}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        boxes_h = pin(w.boxes)
+        W_h = [pin(x) for x in w.net.W]
+        b_h = [pin(x) for x in w.net.b]
+        out_h = {"lo": pin(np.empty((B, o), np.float32)), "hi": pin(np.empty((B, o), np.float32)),
+                 "n_terms": pin(np.empty((B, o, 2), np.int32)),
+                 "coef": pin(np.empty((B, o, 2, cap_terms), np.float32))}
+        for _ in range(max(1, args.warmup)):
+            ctx.propagate_host(w.net.widths, W_h, b_h, boxes_h, degree=w.degree,
+                               cap=w.degree_cap, cap_terms=cap_terms, out=out_h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.propagate_host(w.net.widths, W_h, b_h, boxes_h, degree=w.degree,
+                               cap=w.degree_cap, cap_terms=cap_terms, out=out_h)
+        wall = (time.perf_counter() - t0) / args.steps
+        wall = max_over_ranks(wall, world, dist, dev)
+        h2d = boxes_h.nbytes + sum(x.nbytes for x in W_h) + sum(x.nbytes for x in b_h)
+        d2h = sum(v.nbytes for v in out_h.values())
+        e2e = {"value": round(world * B / wall, 1), "unit": "boxes/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": round(wall * 1e3, 3)}
+
+    cpu = None
+    if pool is not None:
+        idx = np.linspace(0, B - 1, 2 * cores).astype(int)
+        rate, wall = oracle_rate(pool, cores, w, idx)
+        pool.close()
+        cpu = {"value": round(rate, 4), "unit": "boxes/s", "cores": cores, "kind": "oracle",
+               "sample": "%d of the 5120 boxes (evenly strided), one per worker process, "
+                         "FP64 oracle, %.1f s wall" % (len(idx), wall)}
+
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "boxes/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded networks and boxes)",
+        "config": {"workload": "config3 batched plain method: MLP [3,64,64,64,64,1] seed 2, "
+                               "5120 boxes (16^3 grid of [-1,1]^3 + 1024 random, sides "
+                               "U(0.01,0.5)), ReLU order 2, cap 16",
+                   "n_boxes_per_gpu": B, "degree": w.degree, "degree_cap": w.degree_cap,
+                   "mean_output_width": round(float(np.mean(hi - lo)), 6),
+                   "mean_vol_relative": round(float(np.mean(vol)), 6),
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": "box-sharded dp%d (each rank its own batch)" % world,
+                   "graphs": True},
+        "roofline": roof, "kernels": kernels,
+        "kernel_pass_ms_per_step": round(total_kernel_ms, 4),
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    return line
+
+
+# ---------------------------------------------------------------- reference
+def run_reference(args, rank, world):
+    from paper_2211_14438_gb300 import workloads as wl
+    if rank != 0:
+        return None
+    cores = min(os.cpu_count() or 1, 16)
+    pool = mp.get_context("spawn").Pool(cores)
+    w = wl.config3()
+    B = len(w.boxes)
+    rng = np.random.default_rng(0)
+    for _ in range(args.warmup):
+        oracle_rate(pool, cores, w, rng.choice(B, cores, replace=False))
+    total_boxes, total_wall = 0, 0.0
+    for _ in range(args.steps):
+        idx = rng.choice(B, cores, replace=False)
+        r, wall = oracle_rate(pool, cores, w, idx)
+        total_boxes += len(idx)
+        total_wall += wall
+    pool.close()
+    value = total_boxes / total_wall
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "boxes/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * total_wall / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded networks and boxes)",
+        "config": {"workload": "config3 batched plain method: MLP [3,64,64,64,64,1] seed 2, "
+                               "5120 boxes, ReLU order 2, cap 16",
+                   "sample_per_step": "%d random boxes of the 5120, one per process" % cores},
+        "cpu_baseline": {"value": round(value, 4), "unit": "boxes/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": "%d steps x %d boxes, FP64 oracle" % (args.steps, cores)},
+        "e2e": {"value": round(value, 4), "unit": "boxes/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world, local_rank, dist)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if line is not None and rank == 0:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -57,6 +57,9 @@ extern "C" {
 
 #define BERN_MAX_VARS   8
 #define BERN_MAX_ORDER  8     /* largest ReLU Bernstein order d */
+#define BERN_MAX_GRID   24576 /* largest Bernstein grid one enclosure stages in shared memory;
+                                 bern_budget is clamped to it */
+#define BERN_MAX_ENCLOSE_ORDER 24 /* Bernstein orders above this are lowered to it */
 
 typedef struct bern_ctx bern_ctx;
 
@@ -80,7 +83,8 @@ typedef struct {
  *                after each product (0 disables pruning).
  *   bern_budget: largest Bernstein grid (l+1)^n one enclosure may use; above
  *                it the enclosure uses a lower order for the low-degree terms
- *                and coefficient intervals for the rest (0 means 2^20).
+ *                and coefficient intervals for the rest (0 means 2^20; values
+ *                above BERN_MAX_GRID act as BERN_MAX_GRID).
  * per_layer / per_neuron are host arrays. */
 typedef struct {
   int kind;

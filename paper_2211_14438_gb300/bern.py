@@ -29,7 +29,16 @@ BERN_DEG_GLOBAL = 0
 BERN_DEG_PER_LAYER = 1
 BERN_DEG_PER_NEURON = 2
 BERN_MAX_ORDER = 8
+BERN_MAX_GRID = 24576
+BERN_MAX_ENCLOSE_ORDER = 24
 COEF_STRIDE = BERN_MAX_ORDER + 1
+
+
+def effective_budget(budget: int = 0) -> int:
+    """The Bernstein-grid budget the library applies (0 means 2^20, clamped
+    to BERN_MAX_GRID)."""
+    b = budget if budget > 0 else 1 << 20
+    return min(b, BERN_MAX_GRID)
 
 EXPORTS = [
     "bern_create", "bern_destroy", "bern_set_pointer_mode", "bern_set_graphs",

@@ -538,13 +538,13 @@ int bern_compose(bern_ctx* c, int n, int64_t n_items, int degree_cap, float prun
 int bern_propagate(bern_ctx* c, const bern_net* net, const float* boxes, int64_t n_boxes,
                    const bern_degree_plan* plan, bern_result* result) {
   if (!c || !net || !result || n_boxes < 0 || (!boxes && n_boxes > 0)) return BERN_E_INVALID;
-  if (!result->lo || !result->hi || !result->n_terms || result->cap_terms < 0)
-    return BERN_E_INVALID;
-  cudaSetDevice(c->device);
   Plan P;
   int rc = make_plan(net, plan, P);
   if (rc) return rc;
   if (n_boxes == 0) return BERN_OK;
+  if (!result->lo || !result->hi || !result->n_terms || result->cap_terms < 0)
+    return BERN_E_INVALID;
+  cudaSetDevice(c->device);
   int dsq = 0;
   for (const auto& l : P.L)
     if (l.hidden && l.d >= 2) dsq = std::max(dsq, l.D_pre);

@@ -13,7 +13,7 @@ namespace bern {
 constexpr int kMaxVars = BERN_MAX_VARS;
 constexpr int kMaxOrder = BERN_MAX_ORDER;
 constexpr int kMaxTableDegree = 64;      // largest total degree with a monomial table
-constexpr int kMaxEncloseOrder = 24;     // C(24,k) is exact in float32
+constexpr int kMaxEncloseOrder = BERN_MAX_ENCLOSE_ORDER;  // C(24,k) is exact in float32
 constexpr int kCoefStride = kMaxOrder + 1;
 
 // Device-side status bits (OR-ed by kernels, read by bern_sync).

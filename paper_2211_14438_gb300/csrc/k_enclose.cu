@@ -25,7 +25,7 @@
 
 namespace bern {
 
-constexpr int kEncloseGridMax = 24576;   // floats per warp (96 KB)
+constexpr int kEncloseGridMax = BERN_MAX_GRID;   // floats per warp (96 KB)
 
 template <bool UP>
 __device__ float enclose_one(const float* __restrict__ P, int nt, int n, int lb, int G,

@@ -162,7 +162,8 @@ def test_small_nets_parity(ctx, widths, degree, seed):
             degs = np.concatenate([np.full(h, d) for h, d in zip(widths[1:-1], degree)])
         else:
             degs = dl
-        r = oracle.propagate(widths, net.W, net.b, boxes[bi], degs)
+        r = oracle.propagate(widths, net.W, net.b, boxes[bi], degs,
+                             budget=bern.effective_budget())
         if near_tie(r):
             continue
         compare_box(g, bi, r, n, widths[-1])

@@ -140,7 +140,7 @@ def test_enclose_step(ctx, n, D, order, budget):
     ctx.enclose(n, items, order, budget, dev(up), dev(lo), M, dev(nt), glo, ghi)
     assert ctx.sync() == 0
     glo, ghi = glo.cpu().numpy().astype(np.float64), ghi.cpu().numpy().astype(np.float64)
-    eff_budget = min(budget if budget > 0 else 1 << 20, 24576)
+    eff_budget = bern.effective_budget(budget)
     from parity_util import dict_from_dense
     for i in range(items):
         pu = dict_from_dense(up[i, : nt[i]].astype(np.float64), n)
