@@ -224,6 +224,33 @@ int bern_compose(bern_ctx* ctx, int n, int64_t n_items, int degree_cap,
                  const int32_t* pre_nterms, float* post_up, float* post_lo,
                  int64_t post_stride, int32_t* post_nterms);
 
+/* -------------------------------------------- allocation-free variant
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * may not allocate device memory: a host framework that owns every GPU
+ * allocation through its own pool, a latency-critical loop where cudaMalloc
+ * or cudaFree (and the synchronisation they can imply) is not allowed, or a
+ * plugin with a fixed memory budget.  It computes exactly what
+ * bern_propagate computes, but needs no bern_ctx: its workspace (32 MiB),
+ * monomial tables (4 MiB) and status word are fixed __device__ arrays of the
+ * library, present on every GPU that loads the library until the process
+ * exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ *   net, boxes, result: device pointers (layouts as for bern_propagate);
+ *   stream: a cudaStream_t (NULL = legacy default stream).
+ *   plan: BERN_DEG_GLOBAL or BERN_DEG_PER_LAYER (PER_NEURON returns
+ *   BERN_E_UNSUPPORTED); NULL means global order 2, cap 16.
+ * Boxes are processed in chunks that fit the workspace.  A network whose
+ * per-box workspace exceeds 32 MiB, or whose tables exceed 4 MiB, is rejected
+ * with BERN_E_UNSUPPORTED before any GPU work.
+ * The first call on a device (the current device) looks up the addresses of
+ * the static arrays and uploads the tables; make that first call before any
+ * stream capture.  The call synchronises `stream` at its end and returns the
+ * device-side status like bern_sync.  All calls share the one workspace:
+ * calls that overlap on the GPU (other streams or threads) race and must be
+ * serialised by the caller. */
+int bern_propagate_noalloc(const bern_net* net, const float* boxes, int64_t n_boxes,
+                           const bern_degree_plan* plan, bern_result* result, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -44,7 +44,7 @@ EXPORTS = [
     "bern_create", "bern_destroy", "bern_set_pointer_mode", "bern_set_graphs",
     "bern_strerror", "bern_sync", "bern_kernel_launches", "bern_num_monomials",
     "bern_monomials", "bern_propagate", "bern_init_inputs", "bern_affine",
-    "bern_enclose", "bern_relu_coeffs", "bern_compose",
+    "bern_enclose", "bern_relu_coeffs", "bern_compose", "bern_propagate_noalloc",
 ]
 
 
@@ -108,6 +108,9 @@ def load(build_if_missing: bool = True):
         "bern_enclose": (I, [V, I, I64, I, I64, V, V, I64, V, V, V]),
         "bern_relu_coeffs": (I, [V, I64, V, V, V, I, V, V, V]),
         "bern_compose": (I, [V, I, I64, I, F, V, V, V, V, I, V, V, V, V, I64, V, V, V, I64, V]),
+        "bern_propagate_noalloc": (I, [ctypes.POINTER(bern_net), V, I64,
+                                       ctypes.POINTER(bern_degree_plan),
+                                       ctypes.POINTER(bern_result), V]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -281,6 +284,24 @@ class Context:
             self.set_pointer_mode(BERN_MEM_DEVICE)
         _check(rc, "bern_propagate(host)")
         return out
+
+
+def propagate_noalloc(widths, W, b, boxes, out, degree=2, cap: int = 16, tau: float = 0.0,
+                      budget: int = 0, stream=None) -> int:
+    """bern_propagate_noalloc on caller-allocated CUDA tensors (W, b lists,
+    boxes [B, n, 2], out dict with 'lo', 'hi', 'n_terms', 'coef' and optional
+    'keys').  The library allocates nothing for this call; it returns the
+    status code (0 on success) after synchronising the stream."""
+    widths = [int(x) for x in widths]
+    plan, keep = make_plan(degree, widths, cap, tau, budget)
+    net, keep2 = make_net(widths, [_ptr(w) for w in W], [_ptr(x) for x in b])
+    cap_terms = int(out["coef"].shape[-1]) if out.get("coef") is not None else 0
+    res = bern_result(_ptr(out["lo"]), _ptr(out["hi"]), _ptr(out["n_terms"]),
+                      _ptr(out.get("keys")), _ptr(out.get("coef")), cap_terms)
+    h = 0 if stream is None else int(stream.cuda_stream)
+    return int(load().bern_propagate_noalloc(ctypes.byref(net), ctypes.c_void_p(_ptr(boxes)),
+                                             int(boxes.shape[0]), ctypes.byref(plan),
+                                             ctypes.byref(res), ctypes.c_void_p(h)))
 
 
 def make_net(widths, W_ptrs, b_ptrs):
