@@ -129,6 +129,16 @@ int ensure_tables(bern_ctx* c, int n, int dmax, const Tables** out) {
   ts.view.exps = (const uint8_t*)ts.exps.p;
   ts.view.mcount = (const int32_t*)ts.mcount.p;
   ts.view.mexps = num_monomials(n, De);
+  ts.view.rscale_max = max_enclose_order(n);
+  for (int l = 0; l <= ts.view.rscale_max; ++l) {
+    std::vector<float> rs;
+    build_rscale(n, l, rs);
+    DevBuf b;
+    if ((e = b.reserve(rs.size() * sizeof(float))) != cudaSuccess) return map_cuda(e);
+    cudaMemcpy(b.p, rs.data(), rs.size() * sizeof(float), cudaMemcpyHostToDevice);
+    ts.view.rscale[l] = (const float2*)b.p;
+    ts.bufs.push_back(b);
+  }
   for (int D = 0; D <= dmax; ++D) {
     PairList pl;
     if (!build_square_pairs(n, D, pl)) return BERN_E_UNSUPPORTED;
@@ -312,14 +322,13 @@ int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
     }
     float* lo = ch.at<float>(l.off_lo);
     float* hi = ch.at<float>(l.off_hi);
-    e = launch_enclose(L, T, items, l.order, P.budget, pre_up, pre_lo, l.M_pre, pre_nt, lo, hi);
-    if (e != cudaSuccess) return map_cuda(e);
     const uint8_t* deg = nullptr;
     if (P.per_neuron) deg = ch.at<uint8_t>(l.off_deg);
     int8_t* kind = ch.at<int8_t>(l.off_kind);
     float* coef = ch.at<float>(l.off_coef);
     float* eps = ch.at<float>(l.off_eps);
-    e = launch_relu_coeffs(L, items, lo, hi, deg, l.d, kind, coef, eps);
+    e = launch_enclose_relu(L, T, items, l.order, P.budget, pre_up, pre_lo, l.M_pre, pre_nt, lo,
+                            hi, deg, l.d, kind, coef, eps);
     if (e != cudaSuccess) return map_cuda(e);
     float* post_up = ch.at<float>(l.off_post_up);
     float* post_lo = ch.at<float>(l.off_post_lo);

@@ -54,7 +54,16 @@ struct Tables {
   int64_t mexps;
   const int32_t* mcount;           // M(n, D) for D = 0..64
   PairTable sq[kMaxTableDegree + 1];
+  // rscale[l][r]: float bracket (lo, hi) of 1 / prod_k C(l, e_k(r)) for the
+  // ranks r < M(n, l), for Bernstein orders l = 0..rscale_max
+  const float2* rscale[kMaxEncloseOrder + 1];
+  int rscale_max;
 };
+
+// Largest Bernstein order whose grid fits the shared-memory limit for n vars.
+int max_enclose_order(int n);
+// Host image of the reciprocal brackets for order l: 2*M(n,l) floats.
+void build_rscale(int n, int l, std::vector<float>& out);
 
 // ------------------------------------------------------------ launchers
 struct Launch {
@@ -73,6 +82,11 @@ cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
 cudaError_t launch_enclose(const Launch& L, const Tables& T, int64_t n_items, int order,
                            int64_t budget, const float* pre_up, const float* pre_lo,
                            int64_t stride, const int32_t* nterms, float* lo, float* hi);
+cudaError_t launch_enclose_relu(const Launch& L, const Tables& T, int64_t n_items, int order,
+                                int64_t budget, const float* pre_up, const float* pre_lo,
+                                int64_t stride, const int32_t* nterms, float* lo, float* hi,
+                                const uint8_t* degrees, int global_d, int8_t* kind, float* coef,
+                                float* eps);
 cudaError_t launch_relu_coeffs(const Launch& L, int64_t n_items, const float* lo,
                                const float* hi, const uint8_t* degrees, int global_d,
                                int8_t* kind, float* coef, float* eps);

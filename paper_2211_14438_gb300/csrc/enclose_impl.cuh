@@ -1,0 +1,333 @@
+// a2: Step 1 of Sec. 5.1 (eq. find_lo_hi) via the range enclosing property
+// (Def. 2):  lo = min_I b_I(pre_lo),  hi = max_I b_I(pre_up),
+// where b_I are the coefficients of the exact Bernstein expansion of order l
+// (in every variable) on [0,1]^n of a power-form polynomial a_J:
+//
+//   b_I = sum_{J <= I} prod_k C(i_k, j_k) / C(l, j_k) * a_J.
+//
+// After scaling c_J = a_J / prod_k C(l, j_k), the map factors into one
+// transform per variable, c -> (sum_{j<=i} C(i,j) c_j)_i, whose weights are
+// exact small integers.  The scaling multiplies by a float bracket of the
+// reciprocal (the end chosen by the sign of a_J and the rounding direction),
+// and the transforms use directed FMAs (round-down for the lower polynomial,
+// round-up for the upper one), so every computed coefficient is a one-sided
+// bound of the exact one.
+//
+// Work layout.  One warp per polynomial; a block holds 2*P warps = P items
+// (warp 2i: lower polynomial of item i, warp 2i+1: upper).  Each warp stages
+// the (l+1)^n grid in shared memory, indexed in mixed radix (l+1) with t_1 the
+// slowest digit.  A polynomial of total degree D <= l occupies only the
+// simplex sum_k j_k <= D, so the transforms run from the last variable to the
+// first, each over the lines whose untransformed prefix still lies in the
+// simplex, reading only in-simplex inputs (no zero fill needed).  A line is
+// loaded into registers, transformed with compile-time binomial weights and
+// written back; the first variable's transform feeds the min/max directly.
+//
+// a3 (fused): once both bounds of an item are known, one thread computes the
+// ReLU case and the order-d Bernstein polynomial of ReLU on [lo, hi]
+// (Def. 1, Prop. 1) in the power basis of s = (y-lo)/(hi-lo), plus the shift
+// B(0) of Prop. 2 (eq. max_error), in float64 rounded up to float32 with a
+// margin that covers the float64 error.
+#pragma once
+#include <math_constants.h>
+
+#include <algorithm>
+
+#include "device_util.cuh"
+
+namespace bern {
+
+constexpr int kEncloseGridMax = BERN_MAX_GRID;   // floats per warp (96 KB)
+
+constexpr float cbin(int i, int j) {
+  float r = 1.0f;
+  for (int k = 1; k <= j; ++k) r = r * (float)(i - j + k) / (float)k;
+  return r;
+}
+
+// ------------------------------------------------------------------ a3
+// C(d,k) for d <= 8, exact in float64
+static __constant__ const double c_dbin[9][9] = {
+    {1}, {1, 1}, {1, 2, 1}, {1, 3, 3, 1}, {1, 4, 6, 4, 1}, {1, 5, 10, 10, 5, 1},
+    {1, 6, 15, 20, 15, 6, 1}, {1, 7, 21, 35, 35, 21, 7, 1}, {1, 8, 28, 56, 70, 56, 28, 8, 1}};
+
+static __device__ __forceinline__ double dbin(int d, int k) { return c_dbin[d][k]; }
+
+// Order-d Bernstein polynomial of ReLU on [lo,hi], power form in s, every
+// coefficient rounded up (>= the exact one); eps >= B(0) + sum_j (a~_j - a_j).
+static __device__ void relu_power_form(float lo, float hi, int d, float* a_out, float* eps_out) {
+  const double L = lo, H = hi, w = H - L;
+  const double inv_d = 1.0 / (double)d;
+  double b[kMaxOrder + 1];
+  for (int k = 0; k <= d; ++k) {
+    double node = L + w * ((double)k * inv_d);   // Def. 1 grid point
+    b[k] = node > 0.0 ? node : 0.0;
+  }
+  double excess = 0.0;
+  for (int j = 0; j <= d; ++j) {
+    double s = 0.0, mag = 0.0;
+    for (int k = 0; k <= j; ++k) {
+      // coefficient of s^j in C(d,k) s^k (1-s)^(d-k)
+      double t = b[k] * (dbin(d, k) * dbin(d - k, j - k));
+      s += ((j - k) & 1) ? -t : t;
+      mag += t;
+    }
+    const double margin = mag * 0x1p-40;
+    const float aj = __double2float_ru(s + margin);
+    a_out[j] = aj;
+    excess += ((double)aj - s) + margin;
+  }
+  const double s0 = -L / w;
+  double e = 0.0;
+  for (int k = 0; k <= d; ++k) {
+    double t = b[k] * dbin(d, k);
+    for (int i = 0; i < k; ++i) t *= s0;
+    for (int i = 0; i < d - k; ++i) t *= (1.0 - s0);
+    e += t;
+  }
+  *eps_out = __double2float_ru((e + excess) * (1.0 + 0x1p-40) + w * 0x1p-40);
+}
+
+// Case of one item and, for case 2, its coefficients.  Returns the case.
+static __device__ int relu_item(float l, float h, int d, float* a, float* eps, int* status) {
+  if (!(isfinite(l) && isfinite(h))) {
+    atomicOr(status, kStatusNonFinite);
+    return 0;
+  }
+  if (h <= 0.0f) return 0;        // ReLU is 0 on [lo,hi]
+  if (l >= 0.0f) return 1;        // ReLU is the identity on [lo,hi]
+  if (d < 1 || d > kMaxOrder) {
+    atomicOr(status, kStatusInvalid);
+    return 0;
+  }
+  relu_power_form(l, h, d, a, eps);
+  return 2;
+}
+
+// ------------------------------------------------------------------ a2
+template <int LB, bool UP>
+__device__ __forceinline__ void line_transform(const float (&x)[LB + 1], float (&y)[LB + 1]) {
+#pragma unroll
+  for (int i = 0; i <= LB; ++i) {
+    float acc = x[0];
+#pragma unroll
+    for (int j = 1; j <= i; ++j) acc = dfma<UP>(cbin(i, j), x[j], acc);
+    y[i] = acc;
+  }
+}
+
+// Scatter the scaled coefficients of degree <= Deff into the grid; return
+// the directed sum of the one-sided ranges of all other terms.
+template <bool UP>
+__device__ float scatter_terms(const float* __restrict__ P, int nt, int n, const int* pw,
+                               const Tables& T, const float2* __restrict__ rs, int Deff,
+                               float* grid) {
+  const int lane = threadIdx.x & 31;
+  float rem = 0.0f;
+  const int m_eff = T.mcount[Deff];
+  for (int r = lane; r < nt; r += 32) {
+    const float a = P[r];
+    const uint8_t* e = T.exps + (int64_t)r * n;
+    int deg = 0, idx = 0;
+    for (int k = 0; k < n; ++k) {
+      deg += e[k];
+      idx += e[k] * pw[k];
+    }
+    if (deg <= Deff) {
+      const float2 sc = rs[r];
+      // a / C bracketed: choose the end that rounds the product the right way
+      grid[idx] = UP ? __fmul_ru(a, a >= 0.0f ? sc.y : sc.x)
+                     : __fmul_rd(a, a >= 0.0f ? sc.x : sc.y);
+    } else {
+      // the term lies in [min(0,a), max(0,a)] on the box
+      rem = UP ? __fadd_ru(rem, fmaxf(a, 0.0f)) : __fadd_rd(rem, fminf(a, 0.0f));
+    }
+  }
+  // a ragged count (not a full graded prefix): missing simplex entries are 0
+  for (int r = nt + lane; r < m_eff; r += 32) {
+    const uint8_t* e = T.exps + (int64_t)r * n;
+    int idx = 0;
+    for (int k = 0; k < n; ++k) idx += e[k] * pw[k];
+    grid[idx] = 0.0f;
+  }
+  return rem;
+}
+
+template <int LB, bool UP>
+__device__ float enclose_warp(const float* __restrict__ P, int nt, int n, const Tables& T,
+                              const float2* __restrict__ rs, float* grid) {
+  const int lane = threadIdx.x & 31;
+  constexpr int R = LB + 1;
+  int pw[kMaxVars];
+  {
+    int p = 1;
+    for (int k = n - 1; k >= 0; --k) {
+      pw[k] = p;
+      p *= R;
+    }
+  }
+  // degree actually present (the smallest graded prefix holding nt), capped at LB
+  int Dnt = 0;
+  while (Dnt < kMaxTableDegree && T.mcount[Dnt] < nt) ++Dnt;
+  const int Deff = Dnt < LB ? Dnt : LB;
+  float rem = scatter_terms<UP>(P, nt, n, pw, T, rs, Deff, grid);
+  __syncwarp();
+  float best = UP ? -CUDART_INF_F : CUDART_INF_F;
+  int nlines = 1;
+  for (int m = 0; m < n - 1; ++m) nlines *= R;
+  for (int k = n - 1; k >= 0; --k) {
+    // lines along variable k: prefix digits (variables < k) untransformed,
+    // suffix digits (variables > k) transformed
+    const int sk = pw[k];
+    for (int Ln = lane; Ln < nlines; Ln += 32) {
+      int rest = Ln, base = 0, psum = 0;
+      for (int m = n - 1; m >= 0; --m) {
+        if (m == k) continue;
+        const int dgt = rest % R;
+        rest /= R;
+        base += dgt * pw[m];
+        if (m < k) psum += dgt;
+      }
+      if (psum > Deff) continue;
+      const int p = Deff - psum;
+      float x[R], y[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) x[j] = j <= p ? grid[base + j * sk] : 0.0f;
+      line_transform<LB, UP>(x, y);
+      if (k > 0) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) grid[base + i * sk] = y[i];
+      } else {
+#pragma unroll
+        for (int i = 0; i < R; ++i) best = UP ? fmaxf(best, y[i]) : fminf(best, y[i]);
+      }
+    }
+    __syncwarp();
+  }
+  best = UP ? warp_max(best) : warp_min(best);
+  rem = warp_dsum<UP>(rem);
+  return dadd<UP>(best, rem);
+}
+
+struct ReluOut {
+  int8_t* kind;
+  float* coef;
+  float* eps;
+  const uint8_t* degrees;
+  int global_d;
+};
+
+template <int LB>
+__global__ void __launch_bounds__(512)
+k_enclose(Tables T, int G, const float2* __restrict__ rs, int64_t n_items,
+          const float* __restrict__ pre_up, const float* __restrict__ pre_lo, int64_t stride,
+          const int32_t* __restrict__ nterms, float* __restrict__ lo, float* __restrict__ hi,
+          ReluOut ro, int* status) {
+  extern __shared__ float smem[];
+  __shared__ float s_lohi[8][2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int per_block = blockDim.x >> 6;               // items per block
+  const int64_t item = (int64_t)blockIdx.x * per_block + (warp >> 1);
+  const bool up = warp & 1;
+  if (item < n_items) {
+    int nt = nterms[item];
+    if (nt < 0 || nt > stride || nt > T.mexps) {
+      if (lane == 0) atomicOr(status, kStatusInvalid);
+      nt = 0;
+    }
+    float* grid = smem + warp * G;
+    const float v = up ? enclose_warp<LB, true>(pre_up + item * stride, nt, T.n, T, rs, grid)
+                       : enclose_warp<LB, false>(pre_lo + item * stride, nt, T.n, T, rs, grid);
+    if (lane == 0) {
+      (up ? hi : lo)[item] = v;
+      s_lohi[warp >> 1][up ? 1 : 0] = v;
+      if (!isfinite(v)) atomicOr(status, kStatusNonFinite);
+    }
+  }
+  if (ro.kind == nullptr) return;
+  __syncthreads();
+  if (threadIdx.x < per_block) {
+    const int64_t it = (int64_t)blockIdx.x * per_block + threadIdx.x;
+    if (it < n_items) {
+      const int d = ro.degrees ? (int)ro.degrees[it] : ro.global_d;
+      ro.kind[it] = (int8_t)relu_item(s_lohi[threadIdx.x][0], s_lohi[threadIdx.x][1], d,
+                                      ro.coef + it * kCoefStride, ro.eps + it, status);
+    }
+  }
+}
+
+template <int LB>
+cudaError_t launch_lb(const Launch& L, const Tables& T, int G, int64_t n_items,
+                             const float* pre_up, const float* pre_lo, int64_t stride,
+                             const int32_t* nterms, float* lo, float* hi, ReluOut ro) {
+  // items per block: as many as fit 192 KB of grids, at most 8 (16 warps)
+  int items = (int)std::min<int64_t>(8, (192 * 1024) / (2 * (int64_t)G * 4));
+  if (items < 1) items = 1;
+  const size_t smem = (size_t)2 * items * G * sizeof(float);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_enclose<LB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const unsigned blocks = (unsigned)((n_items + items - 1) / items);
+  k_enclose<LB><<<blocks, 64 * items, smem, L.stream>>>(T, G, T.rscale[LB], n_items, pre_up,
+                                                        pre_lo, stride, nterms, lo, hi, ro,
+                                                        L.status);
+  ++*L.launches;
+  return cudaGetLastError();
+}
+
+// Orders above 16: one kernel with a runtime order; each line is transformed
+// in place in shared memory by l sweeps of pairwise directed additions
+// (Pascal's rule: after sweep r, c_i holds sum_j C(.,.) c_j partial sums), so
+// only non-negative integer weights are applied.
+template <bool UP>
+__device__ float enclose_warp_generic(const float* __restrict__ P, int nt, int n, int lb,
+                                      const Tables& T, const float2* __restrict__ rs,
+                                      float* grid) {
+  const int lane = threadIdx.x & 31;
+  const int R = lb + 1;
+  int pw[kMaxVars];
+  {
+    int p = 1;
+    for (int k = n - 1; k >= 0; --k) {
+      pw[k] = p;
+      p *= R;
+    }
+  }
+  int Dnt = 0;
+  while (Dnt < kMaxTableDegree && T.mcount[Dnt] < nt) ++Dnt;
+  const int Deff = Dnt < lb ? Dnt : lb;
+  float rem = scatter_terms<UP>(P, nt, n, pw, T, rs, Deff, grid);
+  __syncwarp();
+  float best = UP ? -CUDART_INF_F : CUDART_INF_F;
+  int nlines = 1;
+  for (int m = 0; m < n - 1; ++m) nlines *= R;
+  for (int k = n - 1; k >= 0; --k) {
+    const int sk = pw[k];
+    for (int Ln = lane; Ln < nlines; Ln += 32) {
+      int rest = Ln, base = 0, psum = 0;
+      for (int m = n - 1; m >= 0; --m) {
+        if (m == k) continue;
+        const int dgt = rest % R;
+        rest /= R;
+        base += dgt * pw[m];
+        if (m < k) psum += dgt;
+      }
+      if (psum > Deff) continue;
+      const int p = Deff - psum;
+      float* c = grid + base;
+      for (int j = p + 1; j <= lb; ++j) c[j * sk] = 0.0f;
+      for (int r = 1; r <= lb; ++r)
+        for (int i = lb; i >= r; --i) c[i * sk] = dadd<UP>(c[i * sk], c[(i - 1) * sk]);
+      if (k == 0)
+        for (int i = 0; i <= lb; ++i) best = UP ? fmaxf(best, c[i * sk]) : fminf(best, c[i * sk]);
+    }
+    __syncwarp();
+  }
+  best = UP ? warp_max(best) : warp_min(best);
+  rem = warp_dsum<UP>(rem);
+  return dadd<UP>(best, rem);
+}
+
+}  // namespace bern

@@ -92,6 +92,14 @@ int upload_tables(DeviceSlot& s, int n, int dmax, int deg_exps, cudaStream_t str
   std::vector<uint8_t> ex;
   bern::graded_monomials(n, deg_exps, ex);
   size_t off_ex = put(ex.data(), ex.size());
+  const int rmax = bern::max_enclose_order(n);
+  std::vector<size_t> off_rs(rmax + 1);
+  for (int l = 0; l <= rmax; ++l) {
+    std::vector<float> rs;
+    bern::build_rscale(n, l, rs);
+    off_rs[l] = put(rs.data(), rs.size() * sizeof(float));
+    if (img.size() > kNoAllocTableBytes) return BERN_E_UNSUPPORTED;
+  }
   std::vector<size_t> off_ptr(dmax + 1), off_pairs(dmax + 1);
   for (int D = 0; D <= dmax; ++D) {
     bern::PairList pl;
@@ -112,6 +120,8 @@ int upload_tables(DeviceSlot& s, int n, int dmax, int deg_exps, cudaStream_t str
   v.mcount = (const int32_t*)(s.tables + off_mc);
   v.exps = (const uint8_t*)(s.tables + off_ex);
   v.mexps = bern::num_monomials(n, deg_exps);
+  v.rscale_max = rmax;
+  for (int l = 0; l <= rmax; ++l) v.rscale[l] = (const float2*)(s.tables + off_rs[l]);
   for (int D = 0; D <= dmax; ++D) {
     v.sq[D].ptr = (const int32_t*)(s.tables + off_ptr[D]);
     v.sq[D].pairs = (const uint32_t*)(s.tables + off_pairs[D]);

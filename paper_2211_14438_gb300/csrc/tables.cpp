@@ -2,6 +2,7 @@
 // the composition kernel's polynomial products (the power-series product
 // "Prod" of Sec. 4.2, here over a shared dense graded monomial set).
 #include <algorithm>
+#include <cmath>
 #include <unordered_map>
 
 #include "bern_internal.cuh"
@@ -79,6 +80,42 @@ bool build_square_pairs(int n, int D, PairList& out) {
 
 bool build_product_pairs(int n, int Dq, int Ds, PairList& out) {
   return build_pairs(n, Dq, Ds, false, out);
+}
+
+int max_enclose_order(int n) {
+  int l = kMaxEncloseOrder;
+  for (; l > 0; --l) {
+    int64_t g = 1;
+    for (int k = 0; k < n; ++k) g *= (l + 1);
+    if (g <= BERN_MAX_GRID) break;
+  }
+  return l;
+}
+
+void build_rscale(int n, int l, std::vector<float>& out) {
+  std::vector<uint8_t> ex;
+  graded_monomials(n, l, ex);
+  const int64_t m = num_monomials(n, l);
+  out.assign((size_t)m * 2, 0.0f);
+  for (int64_t r = 0; r < m; ++r) {
+    unsigned __int128 c = 1;
+    for (int k = 0; k < n; ++k) {
+      const int e = ex[(size_t)r * n + k];
+      unsigned long long b = 1;
+      for (int i = 1; i <= e; ++i) b = b * (unsigned long long)(l - e + i) / (unsigned long long)i;
+      c *= b;
+    }
+    float lo, hi;
+    if ((c & (c - 1)) == 0) {             // a power of two: the reciprocal is exact
+      lo = hi = (float)(1.0L / (long double)c);
+    } else {
+      const float f = (float)(1.0L / (long double)c);
+      lo = std::nextafter(f, 0.0f);       // |f - 1/c| < 1 ulp, so lo < 1/c < hi
+      hi = std::nextafter(f, 1.0f);
+    }
+    out[(size_t)r * 2] = lo;
+    out[(size_t)r * 2 + 1] = hi;
+  }
 }
 
 }  // namespace bern
