@@ -198,14 +198,14 @@ class KernelPass:
                 B, L["h"], L["h_in"], self.Wd[i], self.bd[i], in_u, in_l, in_stride, in_nt,
                 L["pre"][0], L["pre"][1], L["Mpre"], L["pre_nt"]))
             self._timed("enclose_L%d" % (i + 1), lambda: ctx.enclose(
-                n, B * L["h"], L["order"], 0, L["pre"][0], L["pre"][1], L["Mpre"], L["pre_nt"],
+                n, B, L["h"], L["order"], 0, L["pre"][0], L["pre"][1], L["Mpre"], L["pre_nt"],
                 L["lo"], L["hi"]))
             if not L["hidden"]:
                 break
             self._timed("relu_L%d" % (i + 1), lambda: ctx.relu_coeffs(
                 B * L["h"], L["lo"], L["hi"], None, w.degree, L["kind"], L["coef"], L["eps"]))
             self._timed("compose_L%d" % (i + 1), lambda: ctx.compose(
-                n, B * L["h"], w.degree_cap, 0.0, L["kind"], L["coef"], L["eps"], None, w.degree,
+                n, B, L["h"], w.degree_cap, 0.0, L["kind"], L["coef"], L["eps"], None, w.degree,
                 L["lo"], L["hi"], L["pre"][0], L["pre"][1], L["Mpre"], L["pre_nt"],
                 L["post"][0], L["post"][1], L["Mpost"], L["post_nt"]))
             in_u, in_l, in_nt, in_stride = L["post"][0], L["post"][1], L["post_nt"], L["Mpost"]
@@ -296,6 +296,10 @@ def run_ours(args, rank, world, local_rank, dist):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     w = wl.config3()
+    if args.n_boxes:
+        # an evenly strided subset keeps the mix of grid cells and random boxes
+        pick = np.linspace(0, len(w.boxes) - 1, args.n_boxes).astype(int)
+        w.boxes = np.ascontiguousarray(w.boxes[pick])
     B = len(w.boxes)
     ctx = bern.Context(local_rank, stream=torch.cuda.current_stream(dev))
     stream = ctx.stream
@@ -446,7 +450,8 @@ def run_ours(args, rank, world, local_rank, dist):
         "data": "synthetic (seeded networks and boxes)",
         "config": {"workload": "config3 batched plain method: MLP [3,64,64,64,64,1] seed 2, "
                                "5120 boxes (16^3 grid of [-1,1]^3 + 1024 random, sides "
-                               "U(0.01,0.5)), ReLU order 2, cap 16",
+                               "U(0.01,0.5)), ReLU order 2, cap 16" +
+                               (" (%d strided boxes only)" % B if args.n_boxes else ""),
                    "n_boxes_per_gpu": B, "degree": w.degree, "degree_cap": w.degree_cap,
                    "mean_output_width": round(float(np.mean(hi - lo)), 6),
                    "mean_vol_relative": round(float(np.mean(vol)), 6),
@@ -506,6 +511,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n-boxes", type=int, default=0,
+                    help="use N evenly strided boxes of the workload (small cases for ncu)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

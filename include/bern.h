@@ -169,34 +169,37 @@ int bern_propagate(bern_ctx* ctx, const bern_net* net, const float* boxes,
  * for callers composing their own pipeline.  All pointers are device
  * pointers; calls are asynchronous on the context's stream.
  *
- * Layout of a polynomial block: poly(box b, neuron m) starts at
- * (b*h + m)*stride floats and holds nterms[b*h + m] valid coefficients
- * (a graded prefix); entries beyond it are not read.  "up" and "lo" blocks
- * have the same layout.  stride must be >= the largest term count. */
+ * Layout of a layer block (h neurons per box, leading dimension ld >= the
+ * largest term count): the coefficient of monomial r (graded rank) of the
+ * polynomial of neuron m of box b is at ((b*ld + r)*h + m) floats, i.e. the
+ * coefficients of one monomial of all neurons of a box are contiguous.
+ * nterms[b*h + m] coefficients (a graded prefix) are valid for that neuron;
+ * entries beyond it are not read.  "up" and "lo" blocks share the layout. */
 
-/* a0, Sec. 5.3 (input init): z0_i = x_i = dlo_i + w_i t_i for both bounds.
- * z_up/z_lo get n_boxes*n polynomials of n+1 terms, nterms = n+1. */
+/* a0, Sec. 5.3 (input init): z0_i = x_i = dlo_i + w_i t_i for both bounds,
+ * i.e. a layer block with h = n neurons, ld >= n+1, nterms = n+1. */
 int bern_init_inputs(bern_ctx* ctx, int n, int64_t n_boxes, const float* boxes,
-                     float* z_up, float* z_lo, int64_t stride, int32_t* nterms);
+                     float* z_up, float* z_lo, int64_t ld, int32_t* nterms);
 
 /* a1, Sec. 5.2, eqs. upper_bounds_layer / lower_bounds_layer:
  *   pre_up_m = sum_j W+_mj up_j + W-_mj lo_j + b_m   (rounded up)
  *   pre_lo_m = sum_j W+_mj lo_j + W-_mj up_j + b_m   (rounded down)
- * W: [h_out x h_in] row-major, b: [h_out].  Output term count per box is
- * max(1, max_j in_nterms[b*h_in + j]). */
+ * W: [h_out x h_in] row-major, b: [h_out]; input block with h = h_in, output
+ * block with h = h_out.  Output term count per box is
+ * max(1, max_j in_nterms[b*h_in + j]) for all its neurons. */
 int bern_affine(bern_ctx* ctx, int64_t n_boxes, int h_out, int h_in,
                 const float* W, const float* b, const float* in_up,
-                const float* in_lo, int64_t in_stride, const int32_t* in_nterms,
-                float* out_up, float* out_lo, int64_t out_stride,
+                const float* in_lo, int64_t in_ld, const int32_t* in_nterms,
+                float* out_up, float* out_lo, int64_t out_ld,
                 int32_t* out_nterms);
 
-/* a2, Sec. 5.1 Step 1 (eq. find_lo_hi) with Def. 2: lo = min of the
- * Bernstein coefficients of pre_lo, hi = max of those of pre_up, of order
- * `order` in every variable on [0,1]^n (rounded outward).  budget as in
- * bern_degree_plan (0 = 2^20). */
-int bern_enclose(bern_ctx* ctx, int n, int64_t n_items, int order,
+/* a2, Sec. 5.1 Step 1 (eq. find_lo_hi) with Def. 2: for every neuron of a
+ * layer block, lo = min of the Bernstein coefficients of pre_lo, hi = max of
+ * those of pre_up, of order `order` in every variable on [0,1]^n (rounded
+ * outward).  budget as in bern_degree_plan (0 = 2^20).  lo/hi: [n_boxes x h]. */
+int bern_enclose(bern_ctx* ctx, int n, int64_t n_boxes, int h, int order,
                  int64_t budget, const float* pre_up, const float* pre_lo,
-                 int64_t stride, const int32_t* nterms, float* lo, float* hi);
+                 int64_t ld, const int32_t* nterms, float* lo, float* hi);
 
 /* a3, Sec. 5.1 Step 2 with Def. 1 and Props. 1-2: per item the case
  * (0: hi <= 0, output 0; 1: lo >= 0, identity; 2: ReLU polynomial), and for
@@ -212,17 +215,18 @@ int bern_relu_coeffs(bern_ctx* ctx, int64_t n_items, const float* lo,
 /* a4, Sec. 5.1 Step 3, eqs. post_bounds_1/2: post_up = B(s_up), post_lo =
  * B(s_lo) - eps with s = (pre - lo)/(hi - lo), computed as polynomials in t
  * with outward rounding, truncated at total degree `degree_cap` (dropped terms
- * enter the constant as a one-sided remainder) and pruned at prune_tau.
- * Identity items copy pre to post; zero items get nterms = 0.
- * n_vars/n_items/h: items are (box, neuron) pairs, neuron index = item % h.
- * post_stride must hold M(n, min(d * D_pre, degree_cap)) for every item. */
-int bern_compose(bern_ctx* ctx, int n, int64_t n_items, int degree_cap,
+ * enter the constant as a one-sided remainder).  Identity items copy pre to
+ * post; zero items get nterms = 0.  Items are the n_boxes*h neurons of the
+ * pre block; kind/coef/eps/degrees/lo/hi are per item (b*h + m).  post_ld
+ * must hold M(n, min(d * D_pre, degree_cap)) for every item.  prune_tau must
+ * be 0 (pruning is not implemented on the GPU; BERN_E_INVALID otherwise). */
+int bern_compose(bern_ctx* ctx, int n, int64_t n_boxes, int h, int degree_cap,
                  float prune_tau, const int8_t* kind, const float* coef,
                  const float* eps, const uint8_t* degrees, int global_d,
                  const float* lo, const float* hi, const float* pre_up,
-                 const float* pre_lo, int64_t pre_stride,
+                 const float* pre_lo, int64_t pre_ld,
                  const int32_t* pre_nterms, float* post_up, float* post_lo,
-                 int64_t post_stride, int32_t* post_nterms);
+                 int64_t post_ld, int32_t* post_nterms);
 
 /* -------------------------------------------- allocation-free variant
  * The paper has no counterpart to this entry point.  It serves callers that

@@ -105,9 +105,10 @@ def load(build_if_missing: bool = True):
                                ctypes.POINTER(bern_degree_plan), ctypes.POINTER(bern_result)]),
         "bern_init_inputs": (I, [V, I, I64, V, V, V, I64, V]),
         "bern_affine": (I, [V, I64, I, I, V, V, V, V, I64, V, V, V, I64, V]),
-        "bern_enclose": (I, [V, I, I64, I, I64, V, V, I64, V, V, V]),
+        "bern_enclose": (I, [V, I, I64, I, I, I64, V, V, I64, V, V, V]),
         "bern_relu_coeffs": (I, [V, I64, V, V, V, I, V, V, V]),
-        "bern_compose": (I, [V, I, I64, I, F, V, V, V, V, I, V, V, V, V, I64, V, V, V, I64, V]),
+        "bern_compose": (I, [V, I, I64, I, I, F, V, V, V, V, I, V, V, V, V, I64, V, V, V, I64,
+                             V]),
         "bern_propagate_noalloc": (I, [ctypes.POINTER(bern_net), V, I64,
                                        ctypes.POINTER(bern_degree_plan),
                                        ctypes.POINTER(bern_result), V]),
@@ -190,32 +191,33 @@ class Context:
         _check(self.lib.bern_set_pointer_mode(self.h, mode), "bern_set_pointer_mode")
 
     # ------------------------------------------------------------- steps
-    def init_inputs(self, n, boxes, z_up, z_lo, stride, nterms):
+    # Layer blocks: coefficient r of neuron m of box b at ((b*ld + r)*h + m).
+    def init_inputs(self, n, boxes, z_up, z_lo, ld, nterms):
         _check(self.lib.bern_init_inputs(self.h, n, boxes.shape[0], _ptr(boxes), _ptr(z_up),
-                                         _ptr(z_lo), stride, _ptr(nterms)), "bern_init_inputs")
+                                         _ptr(z_lo), ld, _ptr(nterms)), "bern_init_inputs")
 
-    def affine(self, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_stride, in_nterms,
-               out_up, out_lo, out_stride, out_nterms):
+    def affine(self, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld, in_nterms,
+               out_up, out_lo, out_ld, out_nterms):
         _check(self.lib.bern_affine(self.h, n_boxes, h_out, h_in, _ptr(W), _ptr(b), _ptr(in_up),
-                                    _ptr(in_lo), in_stride, _ptr(in_nterms), _ptr(out_up),
-                                    _ptr(out_lo), out_stride, _ptr(out_nterms)), "bern_affine")
+                                    _ptr(in_lo), in_ld, _ptr(in_nterms), _ptr(out_up),
+                                    _ptr(out_lo), out_ld, _ptr(out_nterms)), "bern_affine")
 
-    def enclose(self, n, n_items, order, budget, pre_up, pre_lo, stride, nterms, lo, hi):
-        _check(self.lib.bern_enclose(self.h, n, n_items, order, budget, _ptr(pre_up), _ptr(pre_lo),
-                                     stride, _ptr(nterms), _ptr(lo), _ptr(hi)), "bern_enclose")
+    def enclose(self, n, n_boxes, h, order, budget, pre_up, pre_lo, ld, nterms, lo, hi):
+        _check(self.lib.bern_enclose(self.h, n, n_boxes, h, order, budget, _ptr(pre_up),
+                                     _ptr(pre_lo), ld, _ptr(nterms), _ptr(lo), _ptr(hi)),
+               "bern_enclose")
 
     def relu_coeffs(self, n_items, lo, hi, degrees, global_d, kind, coef, eps):
         _check(self.lib.bern_relu_coeffs(self.h, n_items, _ptr(lo), _ptr(hi), _ptr(degrees),
                                          global_d, _ptr(kind), _ptr(coef), _ptr(eps)),
                "bern_relu_coeffs")
 
-    def compose(self, n, n_items, cap, tau, kind, coef, eps, degrees, global_d, lo, hi,
-                pre_up, pre_lo, pre_stride, pre_nterms, post_up, post_lo, post_stride,
-                post_nterms):
-        _check(self.lib.bern_compose(self.h, n, n_items, cap, tau, _ptr(kind), _ptr(coef),
+    def compose(self, n, n_boxes, h, cap, tau, kind, coef, eps, degrees, global_d, lo, hi,
+                pre_up, pre_lo, pre_ld, pre_nterms, post_up, post_lo, post_ld, post_nterms):
+        _check(self.lib.bern_compose(self.h, n, n_boxes, h, cap, tau, _ptr(kind), _ptr(coef),
                                      _ptr(eps), _ptr(degrees), global_d, _ptr(lo), _ptr(hi),
-                                     _ptr(pre_up), _ptr(pre_lo), pre_stride, _ptr(pre_nterms),
-                                     _ptr(post_up), _ptr(post_lo), post_stride,
+                                     _ptr(pre_up), _ptr(pre_lo), pre_ld, _ptr(pre_nterms),
+                                     _ptr(post_up), _ptr(post_lo), post_ld,
                                      _ptr(post_nterms)), "bern_compose")
 
     # ------------------------------------------------------------- whole path

@@ -66,7 +66,7 @@ struct bern_ctx {
   int* d_status = nullptr;
   int64_t launches = 0;
   std::map<int, TableSet> tables;
-  DevBuf ws, stage_in, stage_out;
+  DevBuf ws, stage_in, stage_out, qbuf;
   std::vector<GraphEntry> graphs;
   Launch launch() { return Launch{stream, d_status, &launches}; }
   Launch launch_on(cudaStream_t s) { return Launch{s, d_status, &launches}; }
@@ -139,6 +139,28 @@ int ensure_tables(bern_ctx* c, int n, int dmax, const Tables** out) {
     ts.view.rscale[l] = (const float2*)b.p;
     ts.bufs.push_back(b);
   }
+  ts.view.row_dmax = std::min(kMaxRowDegree, row_path_max_degree(n));
+  for (int D = 0; D <= ts.view.row_dmax; ++D) {
+    RowImage ri;
+    if (!build_row_table(n, D, ri)) return BERN_E_UNSUPPORTED;
+    RowTable& rt = ts.view.row[D];
+    rt.m_in = ri.m_in;
+    rt.n_out_rows = ri.n_out_rows;
+    auto up = [&](const std::vector<int32_t>& v, const void** dst) -> cudaError_t {
+      DevBuf b;
+      cudaError_t e2 = b.reserve(std::max<size_t>(16, v.size() * sizeof(int32_t)));
+      if (e2 != cudaSuccess) return e2;
+      if (!v.empty()) cudaMemcpy(b.p, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+      *dst = b.p;
+      ts.bufs.push_back(b);
+      return cudaSuccess;
+    };
+    if ((e = up(ri.pos_in, (const void**)&rt.pos_in)) != cudaSuccess) return map_cuda(e);
+    if ((e = up(ri.hdr, (const void**)&rt.hdr)) != cudaSuccess) return map_cuda(e);
+    if ((e = up(ri.in_off, (const void**)&rt.in_off)) != cudaSuccess) return map_cuda(e);
+    if ((e = up(ri.pairs, (const void**)&rt.pairs)) != cudaSuccess) return map_cuda(e);
+    if ((e = up(ri.out_ranks, (const void**)&rt.out_ranks)) != cudaSuccess) return map_cuda(e);
+  }
   for (int D = 0; D <= dmax; ++D) {
     PairList pl;
     if (!build_square_pairs(n, D, pl)) return BERN_E_UNSUPPORTED;
@@ -160,6 +182,17 @@ int ensure_tables(bern_ctx* c, int n, int dmax, const Tables** out) {
   e = cudaGetLastError();
   if (e != cudaSuccess) return map_cuda(e);
   *out = &ts.view;
+  return BERN_OK;
+}
+
+// Composition work queues for up to `items` items.
+int ensure_queues(bern_ctx* c, int64_t items, ComposeScratch* out) {
+  const size_t bytes = 256 + (size_t)kComposeQueues * items * sizeof(int);
+  cudaError_t e = c->qbuf.reserve(bytes);
+  if (e != cudaSuccess) return map_cuda(e);
+  out->qcount = (int*)c->qbuf.p;
+  out->queue = (int*)((char*)c->qbuf.p + 256);
+  out->qcap = items;
   return BERN_OK;
 }
 
@@ -291,8 +324,8 @@ struct Chunk {
 
 // Launch sequence of one chunk (graph-capturable: no host sync, no alloc).
 int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
-              const bern_net* net, const float* boxes, int64_t B, const Chunk& ch,
-              float* out_lo, float* out_hi, bern_result res) {
+              const ComposeScratch& CS, const bern_net* net, const float* boxes, int64_t B,
+              const Chunk& ch, float* out_lo, float* out_hi, bern_result res) {
   Launch L = c->launch_on(s);
   const int n = P.n;
   cudaError_t e = launch_init_inputs(L, n, B, boxes, ch.at<float>(P.off_z_up),
@@ -311,9 +344,8 @@ int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
     e = launch_affine(L, B, l.h_out, l.h_in, net->W[i], net->b[i], in_up, in_lo, in_stride,
                       in_nt, pre_up, pre_lo, l.M_pre, pre_nt);
     if (e != cudaSuccess) return map_cuda(e);
-    const int64_t items = B * l.h_out;
     if (!l.hidden) {
-      e = launch_enclose(L, T, items, l.order, P.budget, pre_up, pre_lo, l.M_pre, pre_nt,
+      e = launch_enclose(L, T, B, l.h_out, l.order, P.budget, pre_up, pre_lo, l.M_pre, pre_nt,
                          out_lo, out_hi);
       if (e != cudaSuccess) return map_cuda(e);
       e = launch_pack(L, T, B, P.o, pre_up, pre_lo, l.M_pre, pre_nt, res);
@@ -327,14 +359,14 @@ int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
     int8_t* kind = ch.at<int8_t>(l.off_kind);
     float* coef = ch.at<float>(l.off_coef);
     float* eps = ch.at<float>(l.off_eps);
-    e = launch_enclose_relu(L, T, items, l.order, P.budget, pre_up, pre_lo, l.M_pre, pre_nt, lo,
-                            hi, deg, l.d, kind, coef, eps);
+    e = launch_enclose_relu(L, T, B, l.h_out, l.order, P.budget, pre_up, pre_lo, l.M_pre,
+                            pre_nt, lo, hi, deg, l.d, kind, coef, eps);
     if (e != cudaSuccess) return map_cuda(e);
     float* post_up = ch.at<float>(l.off_post_up);
     float* post_lo = ch.at<float>(l.off_post_lo);
     int32_t* post_nt = ch.at<int32_t>(l.off_post_nt);
-    e = launch_compose(L, T, items, P.cap, P.tau, kind, coef, eps, deg, l.d, lo, hi, pre_up,
-                       pre_lo, l.M_pre, pre_nt, post_up, post_lo, l.M_post, post_nt);
+    e = launch_compose(L, T, CS, B, l.h_out, P.cap, P.tau, kind, coef, eps, deg, l.d, lo, hi,
+                       pre_up, pre_lo, l.M_pre, pre_nt, post_up, post_lo, l.M_post, post_nt);
     if (e != cudaSuccess) return map_cuda(e);
     in_up = post_up;
     in_lo = post_lo;
@@ -436,6 +468,7 @@ int bern_destroy(bern_ctx* c) {
     for (auto& b : kv.second.bufs) b.release();
   }
   c->ws.release();
+  c->qbuf.release();
   c->stage_in.release();
   c->stage_out.release();
   if (c->d_status) cudaFree(c->d_status);
@@ -483,34 +516,34 @@ int bern_monomials(int n, int D, uint8_t* exps) {
 }
 
 int bern_init_inputs(bern_ctx* c, int n, int64_t n_boxes, const float* boxes, float* z_up,
-                     float* z_lo, int64_t stride, int32_t* nterms) {
-  if (!c || n < 1 || n > kMaxVars || n_boxes < 0 || stride < n + 1) return BERN_E_INVALID;
+                     float* z_lo, int64_t ld, int32_t* nterms) {
+  if (!c || n < 1 || n > kMaxVars || n_boxes < 0 || ld < n + 1) return BERN_E_INVALID;
   cudaSetDevice(c->device);
-  return map_cuda(launch_init_inputs(c->launch(), n, n_boxes, boxes, z_up, z_lo, stride, nterms));
+  return map_cuda(launch_init_inputs(c->launch(), n, n_boxes, boxes, z_up, z_lo, ld, nterms));
 }
 
 int bern_affine(bern_ctx* c, int64_t n_boxes, int h_out, int h_in, const float* W,
-                const float* b, const float* in_up, const float* in_lo, int64_t in_stride,
-                const int32_t* in_nterms, float* out_up, float* out_lo, int64_t out_stride,
+                const float* b, const float* in_up, const float* in_lo, int64_t in_ld,
+                const int32_t* in_nterms, float* out_up, float* out_lo, int64_t out_ld,
                 int32_t* out_nterms) {
-  if (!c || n_boxes < 0 || h_out < 1 || h_in < 1 || in_stride < 1 || out_stride < 1)
+  if (!c || n_boxes < 0 || h_out < 1 || h_in < 1 || in_ld < 1 || out_ld < 1)
     return BERN_E_INVALID;
   cudaSetDevice(c->device);
-  return map_cuda(launch_affine(c->launch(), n_boxes, h_out, h_in, W, b, in_up, in_lo, in_stride,
-                                in_nterms, out_up, out_lo, out_stride, out_nterms));
+  return map_cuda(launch_affine(c->launch(), n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
+                                in_nterms, out_up, out_lo, out_ld, out_nterms));
 }
 
-int bern_enclose(bern_ctx* c, int n, int64_t n_items, int order, int64_t budget,
-                 const float* pre_up, const float* pre_lo, int64_t stride,
-                 const int32_t* nterms, float* lo, float* hi) {
-  if (!c || n < 1 || n > kMaxVars || n_items < 0 || order < 0 || stride < 1)
+int bern_enclose(bern_ctx* c, int n, int64_t n_boxes, int h, int order, int64_t budget,
+                 const float* pre_up, const float* pre_lo, int64_t ld, const int32_t* nterms,
+                 float* lo, float* hi) {
+  if (!c || n < 1 || n > kMaxVars || n_boxes < 0 || h < 1 || order < 0 || ld < 1)
     return BERN_E_INVALID;
   cudaSetDevice(c->device);
   const Tables* T;
   int rc = ensure_tables(c, n, 0, &T);
   if (rc) return rc;
-  if (stride > T->mexps) return BERN_E_UNSUPPORTED;
-  return map_cuda(launch_enclose(c->launch(), *T, n_items, order, budget, pre_up, pre_lo, stride,
+  if (ld > T->mexps) return BERN_E_UNSUPPORTED;
+  return map_cuda(launch_enclose(c->launch(), *T, n_boxes, h, order, budget, pre_up, pre_lo, ld,
                                  nterms, lo, hi));
 }
 
@@ -524,24 +557,26 @@ int bern_relu_coeffs(bern_ctx* c, int64_t n_items, const float* lo, const float*
                                      eps));
 }
 
-int bern_compose(bern_ctx* c, int n, int64_t n_items, int degree_cap, float prune_tau,
+int bern_compose(bern_ctx* c, int n, int64_t n_boxes, int h, int degree_cap, float prune_tau,
                  const int8_t* kind, const float* coef, const float* eps,
                  const uint8_t* degrees, int global_d, const float* lo, const float* hi,
-                 const float* pre_up, const float* pre_lo, int64_t pre_stride,
-                 const int32_t* pre_nterms, float* post_up, float* post_lo,
-                 int64_t post_stride, int32_t* post_nterms) {
-  if (!c || n < 1 || n > kMaxVars || n_items < 0 || pre_stride < 1 || post_stride < 1 ||
-      degree_cap < 1 || degree_cap > kMaxTableDegree || !(prune_tau >= 0.0f))
+                 const float* pre_up, const float* pre_lo, int64_t pre_ld,
+                 const int32_t* pre_nterms, float* post_up, float* post_lo, int64_t post_ld,
+                 int32_t* post_nterms) {
+  if (!c || n < 1 || n > kMaxVars || n_boxes < 0 || h < 1 || pre_ld < 1 || post_ld < 1 ||
+      degree_cap < 1 || degree_cap > kMaxTableDegree || prune_tau != 0.0f)
     return BERN_E_INVALID;
   cudaSetDevice(c->device);
   int Dmax = 0;
-  while (Dmax < kMaxTableDegree && num_monomials(n, Dmax + 1) <= pre_stride) ++Dmax;
+  while (Dmax < kMaxTableDegree && num_monomials(n, Dmax + 1) <= pre_ld) ++Dmax;
   const Tables* T;
   int rc = ensure_tables(c, n, std::min(Dmax, 32), &T);
   if (rc) return rc;
-  return map_cuda(launch_compose(c->launch(), *T, n_items, degree_cap, prune_tau, kind, coef, eps,
-                                 degrees, global_d, lo, hi, pre_up, pre_lo, pre_stride,
-                                 pre_nterms, post_up, post_lo, post_stride, post_nterms));
+  ComposeScratch CS;
+  if ((rc = ensure_queues(c, std::max<int64_t>(1, n_boxes * h), &CS))) return rc;
+  return map_cuda(launch_compose(c->launch(), *T, CS, n_boxes, h, degree_cap, prune_tau, kind,
+                                 coef, eps, degrees, global_d, lo, hi, pre_up, pre_lo, pre_ld,
+                                 pre_nterms, post_up, post_lo, post_ld, post_nterms));
 }
 
 int bern_propagate(bern_ctx* c, const bern_net* net, const float* boxes, int64_t n_boxes,
@@ -617,6 +652,10 @@ int bern_propagate(bern_ctx* c, const bern_net* net, const float* boxes, int64_t
   int64_t chunk = std::max<int64_t>(1, (int64_t)(limit / P.per_box));
   chunk = std::min(chunk, n_boxes);
   if ((e = c->ws.reserve(P.per_box * chunk)) != cudaSuccess) return map_cuda(e);
+  int hmax = 1;
+  for (const auto& l : P.L) hmax = std::max(hmax, l.h_out);
+  ComposeScratch CS;
+  if ((rc = ensure_queues(c, chunk * hmax, &CS))) return rc;
 
   for (int64_t b0 = 0; b0 < n_boxes; b0 += chunk) {
     const int64_t B = std::min(chunk, n_boxes - b0);
@@ -631,6 +670,7 @@ int bern_propagate(bern_ctx* c, const bern_net* net, const float* boxes, int64_t
     if ((rc = fill_degrees(c, P, ch, B))) return rc;
     if (c->use_graphs) {
       std::string key = graph_key(P, &dnet, bx, B, r, c->ws.p);
+      key.append((const char*)&CS, sizeof CS);
       GraphEntry* g = nullptr;
       for (auto& x : c->graphs)
         if (x.key == key) g = &x;
@@ -639,7 +679,7 @@ int bern_propagate(bern_ctx* c, const bern_net* net, const float* boxes, int64_t
         const int64_t before = c->launches;
         e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return map_cuda(e);
-        rc = run_chunk(c, c->gstream, P, *T, &dnet, bx, B, ch, r.lo, r.hi, r);
+        rc = run_chunk(c, c->gstream, P, *T, CS, &dnet, bx, B, ch, r.lo, r.hi, r);
         e = cudaStreamEndCapture(c->gstream, &graph);
         if (rc) return rc;
         if (e != cudaSuccess) return map_cuda(e);
@@ -665,7 +705,7 @@ int bern_propagate(bern_ctx* c, const bern_net* net, const float* boxes, int64_t
       if ((e = cudaStreamWaitEvent(c->stream, c->ev_join, 0)) != cudaSuccess) return map_cuda(e);
       c->launches += g->kernels;
     } else {
-      rc = run_chunk(c, c->stream, P, *T, &dnet, bx, B, ch, r.lo, r.hi, r);
+      rc = run_chunk(c, c->stream, P, *T, CS, &dnet, bx, B, ch, r.lo, r.hi, r);
       if (rc) return rc;
     }
   }

@@ -41,7 +41,33 @@ bool build_square_pairs(int n, int D, PairList& out);
 // pairs (I in q, J in s), packed I | (J << 16)
 bool build_product_pairs(int n, int Dq, int Ds, PairList& out);
 
+// Row decomposition for the squaring kernel.  A "row" is the set of
+// monomials sharing the exponents of t_1..t_{n-1} (its prefix) and varying
+// the exponent c of t_n.  The square of a degree-D polynomial is, per output
+// row P, the sum over input-row pairs (p, q), p + q = P, of the 1-D
+// convolution of the two rows.
+constexpr int kMaxRowDegree = 8;          // input degree handled by row convolution
+constexpr int kRowLen = kMaxRowDegree + 1;
+struct RowImage {
+  int m_in = 0, n_out_rows = 0;
+  std::vector<int32_t> pos_in;     // graded rank -> row-layout position
+  std::vector<int32_t> hdr;        // per output row: pair_begin, pair_end, rank_begin, Lout|in_len<<8
+  std::vector<int32_t> in_off;     // per output row: its input-row offset or -1
+  std::vector<int32_t> pairs;      // per pair: off_p, off_q, (L1<<4)|L2 with L1<=L2, diag
+  std::vector<int32_t> out_ranks;  // graded ranks of the output row elements
+};
+bool build_row_table(int n, int D, RowImage& out);
+
 // ------------------------------------------------------------ device views
+struct RowTable {
+  int m_in, n_out_rows;
+  const int32_t* pos_in;
+  const int4* hdr;
+  const int32_t* in_off;
+  const int4* pairs;
+  const int32_t* out_ranks;
+};
+
 struct PairTable {
   const int32_t* ptr;
   const uint32_t* pairs;
@@ -58,6 +84,9 @@ struct Tables {
   // ranks r < M(n, l), for Bernstein orders l = 0..rscale_max
   const float2* rscale[kMaxEncloseOrder + 1];
   int rscale_max;
+  // row tables for squaring, input degrees 0..row_dmax (row_dmax <= 8)
+  RowTable row[kMaxRowDegree + 1];
+  int row_dmax;
 };
 
 // Largest Bernstein order whose grid fits the shared-memory limit for n vars.
@@ -72,33 +101,46 @@ struct Launch {
   int64_t* launches;               // host counter
 };
 
+// Layer-block layout: coefficient r of neuron m of box b at ((b*ld + r)*h + m);
+// term counts at b*h + m.
 cudaError_t launch_init_inputs(const Launch& L, int n, int64_t n_boxes, const float* boxes,
-                               float* z_up, float* z_lo, int64_t stride, int32_t* nterms);
+                               float* z_up, float* z_lo, int64_t ld, int32_t* nterms);
 cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
                           const float* W, const float* b, const float* in_up,
-                          const float* in_lo, int64_t in_stride, const int32_t* in_nterms,
-                          float* out_up, float* out_lo, int64_t out_stride,
+                          const float* in_lo, int64_t in_ld, const int32_t* in_nterms,
+                          float* out_up, float* out_lo, int64_t out_ld,
                           int32_t* out_nterms);
-cudaError_t launch_enclose(const Launch& L, const Tables& T, int64_t n_items, int order,
-                           int64_t budget, const float* pre_up, const float* pre_lo,
-                           int64_t stride, const int32_t* nterms, float* lo, float* hi);
-cudaError_t launch_enclose_relu(const Launch& L, const Tables& T, int64_t n_items, int order,
-                                int64_t budget, const float* pre_up, const float* pre_lo,
-                                int64_t stride, const int32_t* nterms, float* lo, float* hi,
-                                const uint8_t* degrees, int global_d, int8_t* kind, float* coef,
-                                float* eps);
+cudaError_t launch_enclose(const Launch& L, const Tables& T, int64_t n_boxes, int h, int order,
+                           int64_t budget, const float* pre_up, const float* pre_lo, int64_t ld,
+                           const int32_t* nterms, float* lo, float* hi);
+cudaError_t launch_enclose_relu(const Launch& L, const Tables& T, int64_t n_boxes, int h,
+                                int order, int64_t budget, const float* pre_up,
+                                const float* pre_lo, int64_t ld, const int32_t* nterms,
+                                float* lo, float* hi, const uint8_t* degrees, int global_d,
+                                int8_t* kind, float* coef, float* eps);
 cudaError_t launch_relu_coeffs(const Launch& L, int64_t n_items, const float* lo,
                                const float* hi, const uint8_t* degrees, int global_d,
                                int8_t* kind, float* coef, float* eps);
-cudaError_t launch_compose(const Launch& L, const Tables& T, int64_t n_items, int cap,
-                           float tau, const int8_t* kind, const float* coef,
-                           const float* eps, const uint8_t* degrees, int global_d,
-                           const float* lo, const float* hi, const float* pre_up,
-                           const float* pre_lo, int64_t pre_stride,
-                           const int32_t* pre_nterms, float* post_up, float* post_lo,
-                           int64_t post_stride, int32_t* post_nterms);
 cudaError_t launch_pack(const Launch& L, const Tables& T, int64_t n_boxes, int o,
-                        const float* pre_up, const float* pre_lo, int64_t stride,
+                        const float* pre_up, const float* pre_lo, int64_t ld,
                         const int32_t* nterms, bern_result res);
+
+// Work queues of the composition step: kComposeQueues lists of item
+// indices, each of capacity qcap, and their counters.
+constexpr int kComposeQueues = kMaxRowDegree + 4;
+struct ComposeScratch {
+  int* qcount;       // kComposeQueues counters (zeroed by the launcher)
+  int* queue;        // kComposeQueues * qcap item indices
+  int64_t qcap;
+};
+// Largest input degree the row-convolution path handles for n variables.
+int row_path_max_degree(int n);
+cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratch& S,
+                           int64_t n_boxes, int h, int cap, float tau, const int8_t* kind,
+                           const float* coef, const float* eps, const uint8_t* degrees,
+                           int global_d, const float* lo, const float* hi, const float* pre_up,
+                           const float* pre_lo, int64_t pre_ld, const int32_t* pre_nterms,
+                           float* post_up, float* post_lo, int64_t post_ld,
+                           int32_t* post_nterms);
 
 }  // namespace bern

@@ -119,14 +119,14 @@ __device__ __forceinline__ void line_transform(const float (&x)[LB + 1], float (
 // Scatter the scaled coefficients of degree <= Deff into the grid; return
 // the directed sum of the one-sided ranges of all other terms.
 template <bool UP>
-__device__ float scatter_terms(const float* __restrict__ P, int nt, int n, const int* pw,
-                               const Tables& T, const float2* __restrict__ rs, int Deff,
-                               float* grid) {
+__device__ float scatter_terms(const float* __restrict__ P, int ps, int nt, int n,
+                               const int* pw, const Tables& T, const float2* __restrict__ rs,
+                               int Deff, float* grid) {
   const int lane = threadIdx.x & 31;
   float rem = 0.0f;
   const int m_eff = T.mcount[Deff];
   for (int r = lane; r < nt; r += 32) {
-    const float a = P[r];
+    const float a = P[(int64_t)r * ps];
     const uint8_t* e = T.exps + (int64_t)r * n;
     int deg = 0, idx = 0;
     for (int k = 0; k < n; ++k) {
@@ -154,8 +154,8 @@ __device__ float scatter_terms(const float* __restrict__ P, int nt, int n, const
 }
 
 template <int LB, bool UP>
-__device__ float enclose_warp(const float* __restrict__ P, int nt, int n, const Tables& T,
-                              const float2* __restrict__ rs, float* grid) {
+__device__ float enclose_warp(const float* __restrict__ P, int ps, int nt, int n,
+                              const Tables& T, const float2* __restrict__ rs, float* grid) {
   const int lane = threadIdx.x & 31;
   constexpr int R = LB + 1;
   int pw[kMaxVars];
@@ -170,7 +170,7 @@ __device__ float enclose_warp(const float* __restrict__ P, int nt, int n, const 
   int Dnt = 0;
   while (Dnt < kMaxTableDegree && T.mcount[Dnt] < nt) ++Dnt;
   const int Deff = Dnt < LB ? Dnt : LB;
-  float rem = scatter_terms<UP>(P, nt, n, pw, T, rs, Deff, grid);
+  float rem = scatter_terms<UP>(P, ps, nt, n, pw, T, rs, Deff, grid);
   __syncwarp();
   float best = UP ? -CUDART_INF_F : CUDART_INF_F;
   int nlines = 1;
@@ -219,8 +219,8 @@ struct ReluOut {
 
 template <int LB>
 __global__ void __launch_bounds__(512)
-k_enclose(Tables T, int G, const float2* __restrict__ rs, int64_t n_items,
-          const float* __restrict__ pre_up, const float* __restrict__ pre_lo, int64_t stride,
+k_enclose(Tables T, int G, const float2* __restrict__ rs, int64_t n_items, int h,
+          const float* __restrict__ pre_up, const float* __restrict__ pre_lo, int64_t ld,
           const int32_t* __restrict__ nterms, float* __restrict__ lo, float* __restrict__ hi,
           ReluOut ro, int* status) {
   extern __shared__ float smem[];
@@ -231,13 +231,15 @@ k_enclose(Tables T, int G, const float2* __restrict__ rs, int64_t n_items,
   const bool up = warp & 1;
   if (item < n_items) {
     int nt = nterms[item];
-    if (nt < 0 || nt > stride || nt > T.mexps) {
+    if (nt < 0 || nt > ld || nt > T.mexps) {
       if (lane == 0) atomicOr(status, kStatusInvalid);
       nt = 0;
     }
+    const int64_t b = item / h;
+    const int64_t base = (b * ld) * h + (item - b * h);
     float* grid = smem + warp * G;
-    const float v = up ? enclose_warp<LB, true>(pre_up + item * stride, nt, T.n, T, rs, grid)
-                       : enclose_warp<LB, false>(pre_lo + item * stride, nt, T.n, T, rs, grid);
+    const float v = up ? enclose_warp<LB, true>(pre_up + base, h, nt, T.n, T, rs, grid)
+                       : enclose_warp<LB, false>(pre_lo + base, h, nt, T.n, T, rs, grid);
     if (lane == 0) {
       (up ? hi : lo)[item] = v;
       s_lohi[warp >> 1][up ? 1 : 0] = v;
@@ -257,9 +259,9 @@ k_enclose(Tables T, int G, const float2* __restrict__ rs, int64_t n_items,
 }
 
 template <int LB>
-cudaError_t launch_lb(const Launch& L, const Tables& T, int G, int64_t n_items,
-                             const float* pre_up, const float* pre_lo, int64_t stride,
-                             const int32_t* nterms, float* lo, float* hi, ReluOut ro) {
+cudaError_t launch_lb(const Launch& L, const Tables& T, int G, int64_t n_items, int h,
+                      const float* pre_up, const float* pre_lo, int64_t ld,
+                      const int32_t* nterms, float* lo, float* hi, ReluOut ro) {
   // items per block: as many as fit 192 KB of grids, at most 8 (16 warps)
   int items = (int)std::min<int64_t>(8, (192 * 1024) / (2 * (int64_t)G * 4));
   if (items < 1) items = 1;
@@ -270,8 +272,8 @@ cudaError_t launch_lb(const Launch& L, const Tables& T, int G, int64_t n_items,
     if (e != cudaSuccess) return e;
   }
   const unsigned blocks = (unsigned)((n_items + items - 1) / items);
-  k_enclose<LB><<<blocks, 64 * items, smem, L.stream>>>(T, G, T.rscale[LB], n_items, pre_up,
-                                                        pre_lo, stride, nterms, lo, hi, ro,
+  k_enclose<LB><<<blocks, 64 * items, smem, L.stream>>>(T, G, T.rscale[LB], n_items, h, pre_up,
+                                                        pre_lo, ld, nterms, lo, hi, ro,
                                                         L.status);
   ++*L.launches;
   return cudaGetLastError();
@@ -282,8 +284,8 @@ cudaError_t launch_lb(const Launch& L, const Tables& T, int G, int64_t n_items,
 // (Pascal's rule: after sweep r, c_i holds sum_j C(.,.) c_j partial sums), so
 // only non-negative integer weights are applied.
 template <bool UP>
-__device__ float enclose_warp_generic(const float* __restrict__ P, int nt, int n, int lb,
-                                      const Tables& T, const float2* __restrict__ rs,
+__device__ float enclose_warp_generic(const float* __restrict__ P, int ps, int nt, int n,
+                                      int lb, const Tables& T, const float2* __restrict__ rs,
                                       float* grid) {
   const int lane = threadIdx.x & 31;
   const int R = lb + 1;
@@ -298,7 +300,7 @@ __device__ float enclose_warp_generic(const float* __restrict__ P, int nt, int n
   int Dnt = 0;
   while (Dnt < kMaxTableDegree && T.mcount[Dnt] < nt) ++Dnt;
   const int Deff = Dnt < lb ? Dnt : lb;
-  float rem = scatter_terms<UP>(P, nt, n, pw, T, rs, Deff, grid);
+  float rem = scatter_terms<UP>(P, ps, nt, n, pw, T, rs, Deff, grid);
   __syncwarp();
   float best = UP ? -CUDART_INF_F : CUDART_INF_F;
   int nlines = 1;

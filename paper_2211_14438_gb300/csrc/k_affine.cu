@@ -8,33 +8,155 @@
 // round-down FMAs, so each computed coefficient bounds the exact one from the
 // correct side; with t^K >= 0 on the box that bounds the polynomial values.
 //
-// Work decomposition: one block per (box, tile of TM neurons); a thread owns
-// one monomial r and keeps TM upper + TM lower accumulators in registers, so
-// every input coefficient it loads feeds 2*TM FMAs.  Loads of consecutive r
-// by consecutive threads are coalesced.
+// With the layer-block layout (coefficient r of neuron j of box b at
+// ((b*ld + r)*h + j)) each box is a row-major [M x h_in] matrix per bound and
+// the step is the product with W^T: a small GEMM per box.  A block computes a
+// BM (neurons) x BR (monomials) tile of one box; K (= h_in) is staged through
+// shared memory in chunks of KC, and every thread keeps a TM x TR register
+// tile per bound.  Inputs beyond a neuron's term count are read as zero.
+#include <algorithm>
+
 #include "device_util.cuh"
 
 namespace bern {
 
-template <int TM>
-__global__ void __launch_bounds__(128)
+template <int BM, int BR, int TM, int TR, int KC>
+__global__ void __launch_bounds__((BM / TM) * (BR / TR))
 k_affine(int h_out, int h_in, const float* __restrict__ W, const float* __restrict__ bias,
-         const float* __restrict__ in_up, const float* __restrict__ in_lo, int64_t in_stride,
+         const float* __restrict__ in_up, const float* __restrict__ in_lo, int64_t in_ld,
          const int32_t* __restrict__ in_nterms, float* __restrict__ out_up,
-         float* __restrict__ out_lo, int64_t out_stride, int32_t* __restrict__ out_nterms,
+         float* __restrict__ out_lo, int64_t out_ld, int32_t* __restrict__ out_nterms,
          int* status) {
-  extern __shared__ float smem[];
-  float* sW = smem;                                  // TM x h_in
-  int32_t* sN = reinterpret_cast<int32_t*>(sW + TM * h_in);
+  constexpr int NT = (BM / TM) * (BR / TR);
+  constexpr int TX = BM / TM;                       // threads along m
+  __shared__ float sW[KC][BM];
+  __shared__ float sU[BR][KC + 1];
+  __shared__ float sL[BR][KC + 1];
   __shared__ int sMax;
-  const int64_t box = blockIdx.x;
-  const int m0 = blockIdx.y * TM;
+  extern __shared__ int32_t sN[];                   // h_in term counts
+  const int64_t b = blockIdx.x;
+  const int r0 = blockIdx.y * BR;
+  const int m0 = blockIdx.z * BM;
+  const int tid = threadIdx.x;
+  if (tid == 0) sMax = 0;
+  __syncthreads();
+  int mloc = 0;
+  for (int j = tid; j < h_in; j += NT) {
+    int v = in_nterms[b * h_in + j];
+    if (v < 0 || v > in_ld) {
+      atomicOr(status, kStatusInvalid);
+      v = 0;
+    }
+    sN[j] = v;
+    mloc = max(mloc, v);
+  }
+  mloc = warp_imax(mloc);
+  if ((tid & 31) == 0) atomicMax(&sMax, mloc);
+  __syncthreads();
+  const int M = max(1, sMax);
+  if (M > out_ld) {
+    if (tid == 0 && blockIdx.y == 0 && blockIdx.z == 0) atomicOr(status, kStatusCapacity);
+    return;
+  }
+  if (blockIdx.y == 0)
+    for (int m = m0 + tid; m < min(m0 + BM, h_out); m += NT) out_nterms[b * h_out + m] = M;
+  if (r0 >= M) return;
+
+  const int tm = tid % TX, tr = tid / TX;
+  float up[TM][TR], lo[TM][TR];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int k = 0; k < TR; ++k) {
+      const int m = m0 + tm * TM + i, r = r0 + tr * TR + k;
+      const float b0 = (r == 0 && m < h_out) ? bias[m] : 0.0f;
+      up[i][k] = b0;
+      lo[i][k] = b0;
+    }
+  const float* gU = in_up + (b * in_ld) * h_in;
+  const float* gL = in_lo + (b * in_ld) * h_in;
+  for (int j0 = 0; j0 < h_in; j0 += KC) {
+    // stage W[m0.., j0..] transposed, and the input rows r0.. of columns j0..
+    for (int idx = tid; idx < KC * BM; idx += NT) {
+      const int mm = idx % BM, jj = idx / BM;
+      const int m = m0 + mm, j = j0 + jj;
+      sW[jj][mm] = (m < h_out && j < h_in) ? W[(int64_t)m * h_in + j] : 0.0f;
+    }
+    for (int idx = tid; idx < KC * BR; idx += NT) {
+      const int jj = idx % KC, rr = idx / KC;
+      const int j = j0 + jj, r = r0 + rr;
+      float u = 0.0f, l = 0.0f;
+      if (j < h_in && r < sN[j]) {
+        u = gU[(int64_t)r * h_in + j];
+        l = gL[(int64_t)r * h_in + j];
+      }
+      sU[rr][jj] = u;
+      sL[rr][jj] = l;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < KC; ++jj) {
+      float w[TM], u[TR], l[TR];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) w[i] = sW[jj][tm * TM + i];
+#pragma unroll
+      for (int k = 0; k < TR; ++k) {
+        u[k] = sU[tr * TR + k][jj];
+        l[k] = sL[tr * TR + k][jj];
+      }
+#pragma unroll
+      for (int i = 0; i < TM; ++i) {
+        const bool pos = w[i] > 0.0f;
+#pragma unroll
+        for (int k = 0; k < TR; ++k) {
+          up[i][k] = __fmaf_ru(w[i], pos ? u[k] : l[k], up[i][k]);
+          lo[i][k] = __fmaf_rd(w[i], pos ? l[k] : u[k], lo[i][k]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < TR; ++k) {
+    const int r = r0 + tr * TR + k;
+    if (r >= M) continue;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int m = m0 + tm * TM + i;
+      if (m < h_out) {
+        const int64_t o = (b * out_ld + r) * h_out + m;
+        out_up[o] = up[i][k];
+        out_lo[o] = lo[i][k];
+      }
+    }
+  }
+}
+
+// Narrow output layers (h_out <= 4, e.g. a network's output): one thread per
+// (box, monomial row) reads its whole input row (contiguous over j) and
+// keeps the HO outputs of both bounds in registers; no staging is needed.
+template <int HO>
+__global__ void __launch_bounds__(256)
+k_affine_narrow(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
+                const float* __restrict__ bias, const float* __restrict__ in_up,
+                const float* __restrict__ in_lo, int64_t in_ld,
+                const int32_t* __restrict__ in_nterms, float* __restrict__ out_up,
+                float* __restrict__ out_lo, int64_t out_ld, int32_t* __restrict__ out_nterms,
+                int* status) {
+  extern __shared__ float sW[];                      // h_out x h_in, then h_in counts
+  int32_t* sN = reinterpret_cast<int32_t*>(sW + HO * h_in);
+  __shared__ int sMax;
+  const int64_t b = blockIdx.x;
   if (threadIdx.x == 0) sMax = 0;
+  for (int i = threadIdx.x; i < HO * h_in; i += blockDim.x) {
+    const int m = i / h_in;
+    sW[i] = m < h_out ? W[i] : 0.0f;
+  }
   __syncthreads();
   int mloc = 0;
   for (int j = threadIdx.x; j < h_in; j += blockDim.x) {
-    int v = in_nterms[box * h_in + j];
-    if (v < 0 || v > in_stride) {
+    int v = in_nterms[b * h_in + j];
+    if (v < 0 || v > in_ld) {
       atomicOr(status, kStatusInvalid);
       v = 0;
     }
@@ -43,70 +165,105 @@ k_affine(int h_out, int h_in, const float* __restrict__ W, const float* __restri
   }
   mloc = warp_imax(mloc);
   if ((threadIdx.x & 31) == 0) atomicMax(&sMax, mloc);
-  for (int idx = threadIdx.x; idx < TM * h_in; idx += blockDim.x) {
-    int mm = idx / h_in, j = idx - mm * h_in;
-    sW[idx] = (m0 + mm < h_out) ? W[(int64_t)(m0 + mm) * h_in + j] : 0.0f;
-  }
   __syncthreads();
   const int M = max(1, sMax);
-  if (M > out_stride) {
-    if (threadIdx.x == 0) atomicOr(status, kStatusCapacity);
+  if (M > out_ld) {
+    if (threadIdx.x == 0 && blockIdx.y == 0) atomicOr(status, kStatusCapacity);
     return;
   }
-  const float* pu = in_up + box * h_in * in_stride;
-  const float* pl = in_lo + box * h_in * in_stride;
-  for (int r = threadIdx.x; r < M; r += blockDim.x) {
-    float up[TM], lo[TM];
+  if (blockIdx.y == 0 && threadIdx.x < h_out) out_nterms[b * h_out + threadIdx.x] = M;
+  const int r = blockIdx.y * blockDim.x + threadIdx.x;
+  if (r >= M) return;
+  float up[HO], lo[HO];
 #pragma unroll
-    for (int mm = 0; mm < TM; ++mm) {
-      float b0 = (r == 0 && m0 + mm < h_out) ? bias[m0 + mm] : 0.0f;
-      up[mm] = b0;
-      lo[mm] = b0;
-    }
-    for (int j = 0; j < h_in; ++j) {
-      float u = 0.0f, l = 0.0f;
-      if (r < sN[j]) {
-        u = pu[(int64_t)j * in_stride + r];
-        l = pl[(int64_t)j * in_stride + r];
-      }
+  for (int m = 0; m < HO; ++m) {
+    const float b0 = (r == 0 && m < h_out) ? bias[m] : 0.0f;
+    up[m] = b0;
+    lo[m] = b0;
+  }
+  const float* pu = in_up + (b * in_ld + r) * h_in;
+  const float* pl = in_lo + (b * in_ld + r) * h_in;
+#pragma unroll 4
+  for (int j = 0; j < h_in; ++j) {
+    const bool live = r < sN[j];
+    const float u = live ? __ldg(pu + j) : 0.0f;
+    const float l = live ? __ldg(pl + j) : 0.0f;
 #pragma unroll
-      for (int mm = 0; mm < TM; ++mm) {
-        const float w = sW[mm * h_in + j];
-        const bool pos = w > 0.0f;
-        up[mm] = __fmaf_ru(w, pos ? u : l, up[mm]);
-        lo[mm] = __fmaf_rd(w, pos ? l : u, lo[mm]);
-      }
-    }
-#pragma unroll
-    for (int mm = 0; mm < TM; ++mm) {
-      if (m0 + mm < h_out) {
-        const int64_t o = (box * h_out + m0 + mm) * out_stride + r;
-        out_up[o] = up[mm];
-        out_lo[o] = lo[mm];
-      }
+    for (int m = 0; m < HO; ++m) {
+      const float w = sW[m * h_in + j];
+      const bool pos = w > 0.0f;
+      up[m] = __fmaf_ru(w, pos ? u : l, up[m]);
+      lo[m] = __fmaf_rd(w, pos ? l : u, lo[m]);
     }
   }
-  if (threadIdx.x < TM && m0 + (int)threadIdx.x < h_out)
-    out_nterms[box * h_out + m0 + threadIdx.x] = M;
+#pragma unroll
+  for (int m = 0; m < HO; ++m) {
+    if (m < h_out) {
+      const int64_t o = (b * out_ld + r) * h_out + m;
+      out_up[o] = up[m];
+      out_lo[o] = lo[m];
+    }
+  }
+}
+
+template <int BM, int BR, int TM, int TR, int KC>
+static cudaError_t launch_cfg(const Launch& L, int64_t n_boxes, int h_out, int h_in,
+                              const float* W, const float* b, const float* in_up,
+                              const float* in_lo, int64_t in_ld, const int32_t* in_nterms,
+                              float* out_up, float* out_lo, int64_t out_ld,
+                              int32_t* out_nterms) {
+  // r tiles cover the largest possible term count (in_ld); tiles past a box's
+  // actual count exit after the count is known
+  const int64_t rt = (std::max<int64_t>(1, std::min(in_ld, out_ld)) + BR - 1) / BR;
+  dim3 grid((unsigned)n_boxes, (unsigned)rt, (unsigned)((h_out + BM - 1) / BM));
+  const size_t smem = (size_t)h_in * sizeof(int32_t);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_affine<BM, BR, TM, TR, KC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_affine<BM, BR, TM, TR, KC><<<grid, (BM / TM) * (BR / TR), smem, L.stream>>>(
+      h_out, h_in, W, b, in_up, in_lo, in_ld, in_nterms, out_up, out_lo, out_ld, out_nterms,
+      L.status);
+  ++*L.launches;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
                           const float* W, const float* b, const float* in_up,
-                          const float* in_lo, int64_t in_stride, const int32_t* in_nterms,
-                          float* out_up, float* out_lo, int64_t out_stride,
+                          const float* in_lo, int64_t in_ld, const int32_t* in_nterms,
+                          float* out_up, float* out_lo, int64_t out_ld,
                           int32_t* out_nterms) {
-  constexpr int TM = 8;
   if (n_boxes == 0) return cudaSuccess;
-  dim3 grid((unsigned)n_boxes, (unsigned)((h_out + TM - 1) / TM));
-  size_t smem = (size_t)TM * h_in * sizeof(float) + (size_t)h_in * sizeof(int32_t);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_affine<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
+  if (n_boxes > 0x7fffffff || (in_ld + 15) / 16 > 65535) return cudaErrorInvalidValue;
+  if (h_out >= 32)
+    return launch_cfg<64, 64, 4, 4, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
+                                        in_nterms, out_up, out_lo, out_ld, out_nterms);
+  if (h_out > 8)
+    return launch_cfg<16, 64, 2, 4, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
+                                        in_nterms, out_up, out_lo, out_ld, out_nterms);
+  // narrow outputs (h_out <= 8): a thread per monomial row, HO >= h_out
+  const int HO = h_out == 1 ? 1 : (h_out <= 4 ? 4 : 8);
+  const size_t smem = (size_t)HO * h_in * sizeof(float) + (size_t)h_in * sizeof(int32_t);
+  const int64_t rows = std::max<int64_t>(1, std::min(in_ld, out_ld));
+  if (smem > 200 * 1024 || (rows + 127) / 128 > 65535) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)n_boxes, (unsigned)((rows + 127) / 128));
+  cudaError_t e = cudaSuccess;
+#define BERN_NARROW(X)                                                                        \
+  if (HO == X) {                                                                              \
+    if (smem > 48 * 1024)                                                                     \
+      e = cudaFuncSetAttribute(k_affine_narrow<X>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                               (int)smem);                                                    \
+    if (e == cudaSuccess)                                                                     \
+      k_affine_narrow<X><<<grid, 128, smem, L.stream>>>(n_boxes, h_out, h_in, W, b, in_up,    \
+                                                        in_lo, in_ld, in_nterms, out_up,      \
+                                                        out_lo, out_ld, out_nterms, L.status);\
   }
-  k_affine<TM><<<grid, 128, smem, L.stream>>>(h_out, h_in, W, b, in_up, in_lo, in_stride,
-                                              in_nterms, out_up, out_lo, out_stride,
-                                              out_nterms, L.status);
+  BERN_NARROW(1)
+  BERN_NARROW(4)
+  BERN_NARROW(8)
+#undef BERN_NARROW
+  if (e != cudaSuccess) return e;
   ++*L.launches;
   return cudaGetLastError();
 }

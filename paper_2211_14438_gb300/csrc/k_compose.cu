@@ -11,24 +11,54 @@
 // round-to-nearest; eta = 5u * sum|s~_K| bounds |s~(t) - s(t)| on the box,
 // and Lip = sum_j j|a_j|(1+eta)^(j-1) bounds |B'| there, so Lip*eta is added
 // to the upper constant and subtracted from the lower one.  The polynomial
-// B(s~(t)) itself is then formed with outward rounding:
+// B(s~(t)) itself is formed with outward rounding:
 //   d = 1: c_K = a0[K=0] + a1 s~_K                  (one directed FMA)
 //   d = 2: c_K = a0[K=0] + a1 s~_K + a2 (s~^2)_K     (a2 >= 0 by convexity)
-//          with (s~^2)_K = sum_{I+J=K} s~_I s~_J over the symmetric pair list,
-//          accumulated round-up for the upper bound, round-down for the lower.
-//   d >= 3: Horner q <- q s~ + a_j with interval coefficients [q_lo, q_hi]
-//          (both ends accumulated outward, the end used chosen by the sign
-//          of s~_J), truncated at the cap after every product with the
-//          dropped mass carried as a one-sided remainder through later
-//          products by s in [-eta, 1+eta].
+// where (s~^2)_K is accumulated round-up for the upper bound and round-down
+// for the lower one (a2 >= 0, so each end bounds a2*(s~^2)_K correctly).
 //
-// One block per (box, neuron) item; threads stride over output monomials;
-// the normalised input polynomials live in shared memory.
+// Work layout.  A classification kernel puts each item (box, neuron) into a
+// queue: zero items only get a term count of 0; identity items and order-1
+// items go to an elementwise kernel; order-2 items of input degree D <= 8 go
+// to queue D of the row-convolution kernel (one lane per item, 32 items of
+// equal structure per warp), the rest to a per-item pair-list kernel.
+#include <algorithm>
+
 #include "device_util.cuh"
 
 namespace bern {
 
 constexpr float kU = 0x1p-24f;   // unit roundoff of float32
+constexpr int kQIdent = kMaxRowDegree + 1;   // identity copies
+constexpr int kQLinear = kMaxRowDegree + 2;  // order-1 items
+constexpr int kQPairs = kMaxRowDegree + 3;   // order-2 items outside the row path
+static_assert(kQPairs + 1 == kComposeQueues, "queue ids");
+
+struct ComposeArgs {
+  int cap;
+  int h;                     // neurons per box; item = b*h + m
+  const int8_t* kind;
+  const float* coef;
+  const float* eps;
+  const uint8_t* degrees;
+  int global_d;
+  const float* lo;
+  const float* hi;
+  const float* pre_up;
+  const float* pre_lo;
+  int64_t pre_ld;
+  const int32_t* pre_nterms;
+  float* post_up;
+  float* post_lo;
+  int64_t post_ld;
+  int32_t* post_nterms;
+  // offset of coefficient 0 of an item in a block with leading dimension ld;
+  // coefficient r is at offset + r*h
+  __device__ __forceinline__ int64_t base(int64_t item, int64_t ld) const {
+    const int64_t b = item / h;
+    return (b * ld) * h + (item - b * h);
+  }
+};
 
 __device__ __forceinline__ int degree_of(const Tables& T, int m) {
   int D = 0;
@@ -36,132 +66,371 @@ __device__ __forceinline__ int degree_of(const Tables& T, int m) {
   return D;
 }
 
+// ------------------------------------------------------------ classification
+// Each block classifies 1024 consecutive items and appends them to the
+// queues in item order (ballot/popc within a warp, a scan over the warps),
+// reserving its range of every queue with one atomic; so a queue is a list
+// of sorted runs, and a warp's 32 consecutive entries are mostly neighbouring
+// neurons of one box.
+__global__ void __launch_bounds__(1024)
+k_compose_queue(Tables T, ComposeArgs A, int64_t n_items, int row_dmax, ComposeScratch S,
+                int* status) {
+  __shared__ int s_wcnt[32][kComposeQueues];
+  __shared__ int s_base[kComposeQueues];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int q = -1;
+  if (item < n_items) {
+    const int k = A.kind[item];
+    const int Mpre = A.pre_nterms[item];
+    int nt = 0;
+    if (Mpre < 0 || Mpre > A.pre_ld) {
+      atomicOr(status, kStatusInvalid);
+    } else if (k == 1) {
+      if (Mpre > A.post_ld) {
+        atomicOr(status, kStatusCapacity);
+      } else {
+        q = kQIdent;
+        nt = Mpre;
+      }
+    } else if (k == 2) {
+      const int d = A.degrees ? (int)A.degrees[item] : A.global_d;
+      const int D = degree_of(T, Mpre);
+      const int Dfull = d * D;
+      if (T.mcount[D] > A.pre_ld || d < 1 || Dfull > kMaxTableDegree) {
+        atomicOr(status, kStatusInvalid);
+      } else {
+        const int Mout = T.mcount[min(Dfull, A.cap)];
+        if (Mout > A.post_ld) {
+          atomicOr(status, kStatusCapacity);
+        } else if (d == 1) {
+          q = kQLinear;
+          nt = Mout;
+        } else if (d == 2 && D <= row_dmax) {
+          q = D;
+          nt = Mout;
+        } else if (d == 2 && D <= T.dmax) {
+          q = kQPairs;
+          nt = Mout;
+        } else {
+          atomicOr(status, kStatusUnsupported);
+        }
+      }
+    }
+    A.post_nterms[item] = nt;
+  }
+  int rank_in_warp = 0;
+  for (int qq = 0; qq < kComposeQueues; ++qq) {
+    const unsigned m = __ballot_sync(0xffffffffu, q == qq);
+    if (q == qq) rank_in_warp = __popc(m & ((1u << lane) - 1u));
+    if (lane == 0) s_wcnt[warp][qq] = __popc(m);
+  }
+  __syncthreads();
+  if (threadIdx.x < kComposeQueues) {
+    const int qq = threadIdx.x;
+    int run = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {   // exclusive scan over warps
+      const int c = s_wcnt[w][qq];
+      s_wcnt[w][qq] = run;
+      run += c;
+    }
+    s_base[qq] = run ? atomicAdd(&S.qcount[qq], run) : 0;
+  }
+  __syncthreads();
+  if (q >= 0) S.queue[(int64_t)q * S.qcap + s_base[q] + s_wcnt[warp][q] + rank_in_warp] = (int)item;
+}
+
+// ------------------------------------------------------------ row convolution
+// acc[a+b] += x[a] * y[b] with directed FMAs, rows read from shared memory.
+// Off-diagonal row pairs (p < q) accumulate into acc (their product counts
+// twice in the square: doubled at the end, exactly); the diagonal pair
+// (p == q) into accd.
+template <int L1, int L2, bool UP>
+__device__ __forceinline__ void conv_rows(const float* __restrict__ s, int offp, int offq,
+                                          float (&acc)[2 * kRowLen - 1]) {
+  float x[L1], y[L2];
+#pragma unroll
+  for (int a = 0; a < L1; ++a) x[a] = s[offp + a];
+#pragma unroll
+  for (int b = 0; b < L2; ++b) y[b] = s[offq + b];
+#pragma unroll
+  for (int a = 0; a < L1; ++a)
+#pragma unroll
+    for (int b = 0; b < L2; ++b) acc[a + b] = dfma<UP>(x[a], y[b], acc[a + b]);
+}
+
+#define BERN_CC(L1, L2)                                                           \
+  case (L1 << 4) | L2:                                                            \
+    if (pr.w) conv_rows<L1, L2, UP>(s, pr.x, pr.y, accd);                        \
+    else conv_rows<L1, L2, UP>(s, pr.x, pr.y, acc);                              \
+    break;
+#define BERN_CONV_ALL_CASES                                                                     \
+  BERN_CC(1, 1) BERN_CC(1, 2) BERN_CC(1, 3) BERN_CC(1, 4) BERN_CC(1, 5) BERN_CC(1, 6)          \
+  BERN_CC(1, 7) BERN_CC(1, 8) BERN_CC(1, 9) BERN_CC(2, 2) BERN_CC(2, 3) BERN_CC(2, 4)          \
+  BERN_CC(2, 5) BERN_CC(2, 6) BERN_CC(2, 7) BERN_CC(2, 8) BERN_CC(2, 9) BERN_CC(3, 3)          \
+  BERN_CC(3, 4) BERN_CC(3, 5) BERN_CC(3, 6) BERN_CC(3, 7) BERN_CC(3, 8) BERN_CC(3, 9)          \
+  BERN_CC(4, 4) BERN_CC(4, 5) BERN_CC(4, 6) BERN_CC(4, 7) BERN_CC(4, 8) BERN_CC(4, 9)          \
+  BERN_CC(5, 5) BERN_CC(5, 6) BERN_CC(5, 7) BERN_CC(5, 8) BERN_CC(5, 9) BERN_CC(6, 6)          \
+  BERN_CC(6, 7) BERN_CC(6, 8) BERN_CC(6, 9) BERN_CC(7, 7) BERN_CC(7, 8) BERN_CC(7, 9)          \
+  BERN_CC(8, 8) BERN_CC(8, 9) BERN_CC(9, 9)
+
+// One bound of the items of a warp: UP = upper polynomial.
+template <bool UP>
+__device__ void rows_pass(const Tables& T, const ComposeArgs& A, const RowTable& R, int D,
+                          int64_t item, bool valid, float* s, int* status) {
+  const float Lo = valid ? A.lo[item] : -1.0f;
+  const float Hi = valid ? A.hi[item] : 1.0f;
+  const float inv = 1.0f / (Hi - Lo);
+  float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, eps = 0.0f;
+  if (valid) {
+    const float* cf = A.coef + item * kCoefStride;
+    a0 = cf[0];
+    a1 = cf[1];
+    a2 = cf[2];
+    eps = A.eps[item];
+    if (a2 < 0.0f) atomicOr(status, kStatusUnsupported);   // excluded by convexity
+  }
+  const int Mpre = valid ? A.pre_nterms[item] : 0;
+  const int h = A.h;
+  const float* P = (UP ? A.pre_up : A.pre_lo) + A.base(valid ? item : 0, A.pre_ld);
+  // gather the input into row layout, 8 loads in flight per lane
+  float l1 = 0.0f;
+  for (int r0 = 0; r0 < R.m_in; r0 += 8) {
+    float v[8];
+    int pos[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = r0 + i;
+      v[i] = r < Mpre ? __ldg(P + (int64_t)r * h) : 0.0f;
+      pos[i] = r < R.m_in ? __ldg(R.pos_in + r) : -1;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (pos[i] < 0) continue;
+      float x = v[i];
+      if (r0 + i == 0) x = __fsub_rn(x, Lo);
+      x = __fmul_rn(x, inv);
+      s[pos[i]] = x;
+      l1 = __fadd_ru(l1, fabsf(x));
+    }
+  }
+  __syncwarp();
+  const float eta = __fmul_ru(5.0f * kU, l1);
+  const float lip = __fmaf_ru(2.0f * a2, __fadd_ru(1.0f, eta), fabsf(a1));
+  const int Mout = T.mcount[min(2 * D, A.cap)];
+  float* Q = (UP ? A.post_up : A.post_lo) + A.base(valid ? item : 0, A.post_ld);
+  float c0 = 0.0f, rem = 0.0f;
+  int4 hd = __ldg(R.hdr);
+  for (int row = 0; row < R.n_out_rows; ++row) {
+    const int4 hn = row + 1 < R.n_out_rows ? __ldg(R.hdr + row + 1) : hd;
+    float acc[2 * kRowLen - 1], accd[2 * kRowLen - 1];
+#pragma unroll
+    for (int c = 0; c < 2 * kRowLen - 1; ++c) {
+      acc[c] = 0.0f;
+      accd[c] = 0.0f;
+    }
+    if (hd.x < hd.y) {
+      int4 pr = __ldg(R.pairs + hd.x);
+      for (int k = hd.x; k < hd.y; ++k) {
+        const int4 nx = k + 1 < hd.y ? __ldg(R.pairs + k + 1) : pr;   // prefetch
+        switch (pr.z) {
+          BERN_CONV_ALL_CASES
+          default: break;
+        }
+        pr = nx;
+      }
+    }
+    const int Lout = hd.w & 0xff, in_len = hd.w >> 8;
+    const int in_off = __ldg(R.in_off + row);
+    int rk[2 * kRowLen - 1];
+#pragma unroll
+    for (int c = 0; c < 2 * kRowLen - 1; ++c) rk[c] = c < Lout ? __ldg(R.out_ranks + hd.z + c) : 0;
+#pragma unroll
+    for (int c = 0; c < 2 * kRowLen - 1; ++c) {
+      if (c < Lout) {
+        const int rank = rk[c];
+        // (s^2) = diagonal part + 2 * off-diagonal part; 2*x is exact
+        const float sq = dadd<UP>(accd[c], 2.0f * acc[c]);
+        const float lin = c < in_len ? s[in_off + c] : 0.0f;
+        const float at0 = rank == 0 ? a0 : 0.0f;
+        const float v = dfma<UP>(a2, sq, dfma<UP>(a1, lin, at0));
+        if (rank == 0) {
+          c0 = v;
+        } else if (rank < Mout) {
+          if (valid) Q[(int64_t)rank * h] = v;
+        } else {
+          rem = UP ? __fadd_ru(rem, fmaxf(v, 0.0f)) : __fadd_rd(rem, fminf(v, 0.0f));
+        }
+      }
+    }
+    hd = hn;
+  }
+  if (valid) {
+    float v;
+    if (UP) {
+      v = __fadd_ru(__fadd_ru(c0, __fmul_ru(lip, eta)), rem);
+    } else {
+      v = __fsub_rd(c0, __fmul_ru(lip, eta));
+      v = __fadd_rd(__fsub_rd(v, eps), rem);
+    }
+    Q[0] = v;
+    if (!isfinite(v)) atomicOr(status, kStatusNonFinite);
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(256, 2)
+k_compose_rows(Tables T, ComposeArgs A, ComposeScratch S, int row_dmax, int sstride,
+               int* status) {
+  extern __shared__ float smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  float* s = smem + (size_t)(wib * 32 + lane) * sstride;
+  for (int task = blockIdx.x * wpb + wib;; task += gridDim.x * wpb) {
+    int D = -1, chunk = task;
+    for (int d = 0; d <= row_dmax; ++d) {
+      const int nc = (S.qcount[d] + 31) >> 5;
+      if (chunk < nc) {
+        D = d;
+        break;
+      }
+      chunk -= nc;
+    }
+    if (D < 0) break;
+    const int idx = chunk * 32 + lane;
+    const bool valid = idx < S.qcount[D];
+    const int64_t item = valid ? S.queue[(int64_t)D * S.qcap + idx] : 0;
+    const RowTable R = T.row[D];
+    rows_pass<true>(T, A, R, D, item, valid, s, status);
+    rows_pass<false>(T, A, R, D, item, valid, s, status);
+  }
+}
+
+// ------------------------------------------------------------ elementwise items
+// Identity items copy pre to post: one thread per (queue entry, coefficient),
+// entry fastest, so neighbouring threads touch neighbouring neurons.
 __global__ void __launch_bounds__(256)
-k_compose(Tables T, int cap, float tau, const int8_t* __restrict__ kind,
-          const float* __restrict__ coef, const float* __restrict__ eps,
-          const uint8_t* __restrict__ degrees, int global_d, const float* __restrict__ lo,
-          const float* __restrict__ hi, const float* __restrict__ pre_up,
-          const float* __restrict__ pre_lo, int64_t pre_stride,
-          const int32_t* __restrict__ pre_nterms, float* __restrict__ post_up,
-          float* __restrict__ post_lo, int64_t post_stride, int32_t* __restrict__ post_nterms,
-          int* status) {
+k_compose_copy(ComposeArgs A, ComposeScratch S) {
+  const int cnt = S.qcount[kQIdent];
+  const int64_t total = (int64_t)cnt * A.pre_ld;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = g / cnt;
+    const int t = (int)(g - r * cnt);
+    const int64_t item = S.queue[(int64_t)kQIdent * S.qcap + t];
+    if (r >= A.pre_nterms[item]) continue;
+    const int64_t src = A.base(item, A.pre_ld) + r * A.h;
+    const int64_t dst = A.base(item, A.post_ld) + r * A.h;
+    A.post_up[dst] = A.pre_up[src];
+    A.post_lo[dst] = A.pre_lo[src];
+  }
+}
+
+// Order-1 items: a0 + a1*s~ for both bounds, one warp per item.
+__global__ void __launch_bounds__(256)
+k_compose_linear(ComposeArgs A, ComposeScratch S, int* status) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int n_lin = S.qcount[kQLinear];
+  const int h = A.h;
+  for (int t = gw; t < n_lin; t += nw) {
+    const int64_t item = S.queue[(int64_t)kQLinear * S.qcap + t];
+    const int Mpre = A.pre_nterms[item];
+    const float* Pu = A.pre_up + A.base(item, A.pre_ld);
+    const float* Pl = A.pre_lo + A.base(item, A.pre_ld);
+    float* Qu = A.post_up + A.base(item, A.post_ld);
+    float* Ql = A.post_lo + A.base(item, A.post_ld);
+    const float Lo = A.lo[item], Hi = A.hi[item];
+    const float inv = 1.0f / (Hi - Lo);
+    const float* cf = A.coef + item * kCoefStride;
+    const float a0 = cf[0], a1 = cf[1];
+    const int Mout = A.post_nterms[item];     // the graded prefix of Mpre's degree
+    float lu = 0.0f, ll = 0.0f, cu0 = 0.0f, cl0 = 0.0f;
+    for (int r = lane; r < Mout; r += 32) {
+      float vu = r < Mpre ? Pu[(int64_t)r * h] : 0.0f, vl = r < Mpre ? Pl[(int64_t)r * h] : 0.0f;
+      if (r == 0) {
+        vu = __fsub_rn(vu, Lo);
+        vl = __fsub_rn(vl, Lo);
+      }
+      vu = __fmul_rn(vu, inv);
+      vl = __fmul_rn(vl, inv);
+      lu = __fadd_ru(lu, fabsf(vu));
+      ll = __fadd_ru(ll, fabsf(vl));
+      const float cu = __fmaf_ru(a1, vu, r == 0 ? a0 : 0.0f);
+      const float cl = __fmaf_rd(a1, vl, r == 0 ? a0 : 0.0f);
+      if (r == 0) {
+        cu0 = cu;
+        cl0 = cl;
+      } else {
+        Qu[(int64_t)r * h] = cu;
+        Ql[(int64_t)r * h] = cl;
+      }
+    }
+    lu = warp_dsum<true>(lu);
+    ll = warp_dsum<true>(ll);
+    if (lane == 0) {
+      const float lip = fabsf(a1);
+      const float eu = __fmul_ru(5.0f * kU, lu), el = __fmul_ru(5.0f * kU, ll);
+      const float vu = __fadd_ru(cu0, __fmul_ru(lip, eu));
+      const float vl = __fsub_rd(__fsub_rd(cl0, __fmul_ru(lip, el)), A.eps[item]);
+      Qu[0] = vu;
+      Ql[0] = vl;
+      if (!isfinite(vu) || !isfinite(vl)) atomicOr(status, kStatusNonFinite);
+    }
+  }
+}
+
+// ------------------------------------------------------------ pair-list squaring
+// Order-2 items outside the row path: one block per item, threads over output
+// monomials, symmetric pair lists (I <= J, I + J = K) from the host tables.
+__global__ void __launch_bounds__(256)
+k_compose_pairs(Tables T, ComposeArgs A, ComposeScratch S, int* status) {
   extern __shared__ float smem[];
   __shared__ float red[32];
   __shared__ float c0[2];
-  const int64_t item = blockIdx.x;
-  const int k = kind[item];
-  const int Mpre = pre_nterms[item];
-  const float* Pu = pre_up + item * pre_stride;
-  const float* Pl = pre_lo + item * pre_stride;
-  float* Qu = post_up + item * post_stride;
-  float* Ql = post_lo + item * post_stride;
-  if (k == 0) {
-    if (threadIdx.x == 0) post_nterms[item] = 0;
-    return;
-  }
-  if (Mpre > pre_stride || Mpre < 0) {
-    if (threadIdx.x == 0) {
-      atomicOr(status, kStatusInvalid);
-      post_nterms[item] = 0;
-    }
-    return;
-  }
-  if (k == 1) {
-    if (Mpre > post_stride) {
-      if (threadIdx.x == 0) {
-        atomicOr(status, kStatusCapacity);
-        post_nterms[item] = 0;
+  const int count = S.qcount[kQPairs];
+  for (int t = blockIdx.x; t < count; t += gridDim.x) {
+    const int64_t item = S.queue[(int64_t)kQPairs * S.qcap + t];
+    const int Mpre = A.pre_nterms[item];
+    const int Dpre = degree_of(T, Mpre);
+    const int Mp = T.mcount[Dpre];
+    const int Dfull = 2 * Dpre;
+    const int Mout = T.mcount[min(Dfull, A.cap)];
+    const int Mfull = T.mcount[Dfull];
+    const int h = A.h;
+    const float* Pu = A.pre_up + A.base(item, A.pre_ld);
+    const float* Pl = A.pre_lo + A.base(item, A.pre_ld);
+    float* Qu = A.post_up + A.base(item, A.post_ld);
+    float* Ql = A.post_lo + A.base(item, A.post_ld);
+    const float L = A.lo[item], H = A.hi[item];
+    const float inv = 1.0f / (H - L);
+    float* su = smem;
+    float* sl = smem + A.pre_ld;
+    float au = 0.0f, al = 0.0f;
+    for (int r = threadIdx.x; r < Mp; r += blockDim.x) {
+      float vu = r < Mpre ? Pu[(int64_t)r * h] : 0.0f, vl = r < Mpre ? Pl[(int64_t)r * h] : 0.0f;
+      if (r == 0) {
+        vu = __fsub_rn(vu, L);
+        vl = __fsub_rn(vl, L);
       }
-      return;
+      vu = __fmul_rn(vu, inv);
+      vl = __fmul_rn(vl, inv);
+      su[r] = vu;
+      sl[r] = vl;
+      au = __fadd_ru(au, fabsf(vu));
+      al = __fadd_ru(al, fabsf(vl));
     }
-    for (int r = threadIdx.x; r < Mpre; r += blockDim.x) {
-      Qu[r] = Pu[r];
-      Ql[r] = Pl[r];
-    }
-    if (threadIdx.x == 0) post_nterms[item] = Mpre;
-    return;
-  }
-  const int d = degrees ? (int)degrees[item] : global_d;
-  const int Dpre = degree_of(T, Mpre);
-  // the input is read as the full graded prefix of its degree (missing
-  // entries are zero), which must fit the caller's stride
-  const int Mp = T.mcount[Dpre];
-  if (Mp > pre_stride || d < 1) {
-    if (threadIdx.x == 0) {
-      atomicOr(status, kStatusInvalid);
-      post_nterms[item] = 0;
-    }
-    return;
-  }
-  const int Dfull = d * Dpre;
-  const int Dout = min(Dfull, cap);
-  if (Dfull > kMaxTableDegree || (d == 2 && Dpre > T.dmax) || d > 2 || tau > 0.0f) {
-    if (threadIdx.x == 0) {
-      atomicOr(status, kStatusUnsupported);
-      post_nterms[item] = 0;
-    }
-    return;
-  }
-  const int Mout = T.mcount[Dout];
-  const int Mfull = T.mcount[Dfull];
-  if (Mout > post_stride) {
-    if (threadIdx.x == 0) {
-      atomicOr(status, kStatusCapacity);
-      post_nterms[item] = 0;
-    }
-    return;
-  }
-  const float L = lo[item], H = hi[item];
-  const float inv = 1.0f / (H - L);
-  float* su = smem;
-  float* sl = smem + pre_stride;
-  float au = 0.0f, al = 0.0f;
-  for (int r = threadIdx.x; r < Mp; r += blockDim.x) {
-    float vu = r < Mpre ? Pu[r] : 0.0f, vl = r < Mpre ? Pl[r] : 0.0f;
-    if (r == 0) {
-      vu = __fsub_rn(vu, L);
-      vl = __fsub_rn(vl, L);
-    }
-    vu = __fmul_rn(vu, inv);
-    vl = __fmul_rn(vl, inv);
-    su[r] = vu;
-    sl[r] = vl;
-    au = __fadd_ru(au, fabsf(vu));
-    al = __fadd_ru(al, fabsf(vl));
-  }
-  au = block_dsum<true>(au, red);
-  __syncthreads();
-  al = block_dsum<true>(al, red);
-  const float eta_u = __fmul_ru(5.0f * kU, au);
-  const float eta_l = __fmul_ru(5.0f * kU, al);
-  float a[3];
-  const float* cf = coef + item * kCoefStride;
-  for (int j = 0; j <= d; ++j) a[j] = cf[j];
-  // Lipschitz bound of B on [-eta, 1+eta]
-  auto lip = [&](float eta) {
-    float s = 0.0f, p = 1.0f;
-    for (int j = 1; j <= d; ++j) {
-      s = __fmaf_ru((float)j * fabsf(a[j]), p, s);
-      p = __fmul_ru(p, __fadd_ru(1.0f, eta));
-    }
-    return s;
-  };
-  float remU = 0.0f, remL = 0.0f;
-  if (d == 1) {
-    for (int K = threadIdx.x; K < Mp; K += blockDim.x) {
-      float cu = __fmaf_ru(a[1], su[K], K == 0 ? a[0] : 0.0f);
-      float cl = __fmaf_rd(a[1], sl[K], K == 0 ? a[0] : 0.0f);
-      if (K == 0) {
-        c0[0] = cu;
-        c0[1] = cl;
-      } else {
-        Qu[K] = cu;
-        Ql[K] = cl;
-      }
-    }
-  } else {  // d == 2
+    au = block_dsum<true>(au, red);
+    __syncthreads();
+    al = block_dsum<true>(al, red);
+    const float eta_u = __fmul_ru(5.0f * kU, au);
+    const float eta_l = __fmul_ru(5.0f * kU, al);
+    const float* cf = A.coef + item * kCoefStride;
+    const float a0 = cf[0], a1 = cf[1], a2 = cf[2];
+    const bool a2pos = a2 >= 0.0f;
     const PairTable pt = T.sq[Dpre];
-    const bool a2pos = a[2] >= 0.0f;
+    float remU = 0.0f, remL = 0.0f;
     for (int K = threadIdx.x; K < Mfull; K += blockDim.x) {
       const int p0 = pt.ptr[K], p1 = pt.ptr[K + 1];
       float offU = 0.0f, offL = 0.0f, diagU = 0.0f, diagL = 0.0f;
@@ -176,63 +445,99 @@ k_compose(Tables T, int cap, float tau, const int8_t* __restrict__ kind,
           offL = __fmaf_rd(sl[i], sl[j], offL);
         }
       }
-      // (s^2)_K = diag + 2*off  (2*x is exact)
       const float sqU = __fadd_ru(diagU, 2.0f * offU);
       const float sqL = __fadd_rd(diagL, 2.0f * offL);
-      // lower bound of a2*(s^2)_K: a2 >= 0 uses the lower end, else the upper
-      const float cu = __fmaf_ru(a[2], a2pos ? sqU : sqL,
-                                 __fmaf_ru(a[1], K < Mp ? su[K] : 0.0f, K == 0 ? a[0] : 0.0f));
-      const float cl = __fmaf_rd(a[2], a2pos ? sqL : sqU,
-                                 __fmaf_rd(a[1], K < Mp ? sl[K] : 0.0f, K == 0 ? a[0] : 0.0f));
+      const float cu = __fmaf_ru(a2, a2pos ? sqU : sqL,
+                                 __fmaf_ru(a1, K < Mp ? su[K] : 0.0f, K == 0 ? a0 : 0.0f));
+      const float cl = __fmaf_rd(a2, a2pos ? sqL : sqU,
+                                 __fmaf_rd(a1, K < Mp ? sl[K] : 0.0f, K == 0 ? a0 : 0.0f));
       if (K == 0) {
         c0[0] = cu;
         c0[1] = cl;
       } else if (K < Mout) {
-        Qu[K] = cu;
-        Ql[K] = cl;
+        Qu[(int64_t)K * h] = cu;
+        Ql[(int64_t)K * h] = cl;
       } else {
         remU = __fadd_ru(remU, fmaxf(cu, 0.0f));
         remL = __fadd_rd(remL, fminf(cl, 0.0f));
       }
     }
-  }
-  __syncthreads();
-  remU = block_dsum<true>(remU, red);
-  __syncthreads();
-  remL = block_dsum<false>(remL, red);
-  if (threadIdx.x == 0) {
-    const float e = eps[item];
-    float cu = __fadd_ru(c0[0], __fmul_ru(lip(eta_u), eta_u));
-    cu = __fadd_ru(cu, remU);
-    float cl = __fsub_rd(c0[1], __fmul_ru(lip(eta_l), eta_l));
-    cl = __fsub_rd(cl, e);
-    cl = __fadd_rd(cl, remL);
-    Qu[0] = cu;
-    Ql[0] = cl;
-    post_nterms[item] = Mout;
-    if (!isfinite(cu) || !isfinite(cl)) atomicOr(status, kStatusNonFinite);
+    __syncthreads();
+    remU = block_dsum<true>(remU, red);
+    __syncthreads();
+    remL = block_dsum<false>(remL, red);
+    if (threadIdx.x == 0) {
+      const float lipu = __fmaf_ru(2.0f * fabsf(a2), __fadd_ru(1.0f, eta_u), fabsf(a1));
+      const float lipl = __fmaf_ru(2.0f * fabsf(a2), __fadd_ru(1.0f, eta_l), fabsf(a1));
+      float cu = __fadd_ru(__fadd_ru(c0[0], __fmul_ru(lipu, eta_u)), remU);
+      float cl = __fsub_rd(c0[1], __fmul_ru(lipl, eta_l));
+      cl = __fadd_rd(__fsub_rd(cl, A.eps[item]), remL);
+      Qu[0] = cu;
+      Ql[0] = cl;
+      if (!isfinite(cu) || !isfinite(cl)) atomicOr(status, kStatusNonFinite);
+    }
+    __syncthreads();
   }
 }
 
-cudaError_t launch_compose(const Launch& L, const Tables& T, int64_t n_items, int cap,
-                           float tau, const int8_t* kind, const float* coef,
-                           const float* eps, const uint8_t* degrees, int global_d,
-                           const float* lo, const float* hi, const float* pre_up,
-                           const float* pre_lo, int64_t pre_stride,
-                           const int32_t* pre_nterms, float* post_up, float* post_lo,
-                           int64_t post_stride, int32_t* post_nterms) {
+// ------------------------------------------------------------ launcher
+cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratch& S,
+                           int64_t n_boxes, int h, int cap, float tau, const int8_t* kind,
+                           const float* coef, const float* eps, const uint8_t* degrees,
+                           int global_d, const float* lo, const float* hi, const float* pre_up,
+                           const float* pre_lo, int64_t pre_ld, const int32_t* pre_nterms,
+                           float* post_up, float* post_lo, int64_t post_ld,
+                           int32_t* post_nterms) {
+  const int64_t n_items = n_boxes * h;
   if (n_items == 0) return cudaSuccess;
-  size_t smem = 2 * (size_t)pre_stride * sizeof(float);
-  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (tau > 0.0f || n_items > S.qcap || n_items > INT32_MAX) return cudaErrorInvalidValue;
+  ComposeArgs A{cap, h, kind, coef, eps, degrees, global_d, lo, hi, pre_up, pre_lo, pre_ld,
+                pre_nterms, post_up, post_lo, post_ld, post_nterms};
+  // the largest input degree any item of this call can have
+  int Dmax = 0;
+  while (Dmax < kMaxTableDegree && num_monomials(T.n, Dmax + 1) >= 0 &&
+         num_monomials(T.n, Dmax + 1) <= pre_ld)
+    ++Dmax;
+  const int row_dmax = std::min(std::min(T.row_dmax, row_path_max_degree(T.n)), Dmax);
+  cudaError_t e = cudaMemsetAsync(S.qcount, 0, kComposeQueues * sizeof(int), L.stream);
+  if (e != cudaSuccess) return e;
+  k_compose_queue<<<(unsigned)((n_items + 1023) / 1024), 1024, 0, L.stream>>>(
+      T, A, n_items, row_dmax, S, L.status);
+  ++*L.launches;
+  // row-convolution kernel: persistent warps; the per-lane stride is odd so
+  // that lanes reading the same offset hit distinct banks
+  const int sstride = (int)num_monomials(T.n, row_dmax) | 1;
+  const int wpb = (int)std::max<int64_t>(
+      1, std::min<int64_t>(8, (96 * 1024) / (32 * 4 * (int64_t)sstride)));
+  const size_t smem = (size_t)wpb * 32 * sstride * sizeof(float);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_compose, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    e = cudaFuncSetAttribute(k_compose_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_compose<<<(unsigned)n_items, 256, smem, L.stream>>>(
-      T, cap, tau, kind, coef, eps, degrees, global_d, lo, hi, pre_up, pre_lo, pre_stride,
-      pre_nterms, post_up, post_lo, post_stride, post_nterms, L.status);
+  const int64_t tasks = n_items / 32 + row_dmax + 1;
+  const int blocks = (int)std::min<int64_t>((tasks + wpb - 1) / wpb, 152 * 8);
+  k_compose_rows<<<blocks, 32 * wpb, smem, L.stream>>>(T, A, S, row_dmax, sstride, L.status);
   ++*L.launches;
+  k_compose_copy<<<(unsigned)std::min<int64_t>((n_items * pre_ld + 255) / 256, 152 * 16), 256, 0,
+                   L.stream>>>(A, S);
+  ++*L.launches;
+  k_compose_linear<<<(unsigned)std::min<int64_t>((n_items + 7) / 8, 152 * 16), 256, 0,
+                     L.stream>>>(A, S, L.status);
+  ++*L.launches;
+  // pair-list kernel for order-2 items beyond the row path
+  if (Dmax > row_dmax) {
+    const size_t psmem = 2 * (size_t)pre_ld * sizeof(float);
+    if (psmem > 200 * 1024) return cudaErrorInvalidValue;
+    if (psmem > 48 * 1024) {
+      e = cudaFuncSetAttribute(k_compose_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)psmem);
+      if (e != cudaSuccess) return e;
+    }
+    k_compose_pairs<<<(unsigned)std::min<int64_t>(n_items, 152 * 8), 256, psmem, L.stream>>>(
+        T, A, S, L.status);
+    ++*L.launches;
+  }
   return cudaGetLastError();
 }
 

@@ -7,7 +7,7 @@
 namespace bern {
 
 #define BERN_ENC_EXTERN(X)                                                                   \
-  extern template cudaError_t launch_lb<X>(const Launch&, const Tables&, int, int64_t,       \
+  extern template cudaError_t launch_lb<X>(const Launch&, const Tables&, int, int64_t, int,  \
                                            const float*, const float*, int64_t, const int32_t*, \
                                            float*, float*, ReluOut);
 BERN_ENC_EXTERN(9) BERN_ENC_EXTERN(10) BERN_ENC_EXTERN(11) BERN_ENC_EXTERN(12)
@@ -15,9 +15,9 @@ BERN_ENC_EXTERN(13) BERN_ENC_EXTERN(14) BERN_ENC_EXTERN(15) BERN_ENC_EXTERN(16)
 #undef BERN_ENC_EXTERN
 
 __global__ void __launch_bounds__(512)
-k_enclose_generic(Tables T, int lb, int G, const float2* __restrict__ rs, int64_t n_items,
+k_enclose_generic(Tables T, int lb, int G, const float2* __restrict__ rs, int64_t n_items, int h,
                   const float* __restrict__ pre_up, const float* __restrict__ pre_lo,
-                  int64_t stride, const int32_t* __restrict__ nterms, float* __restrict__ lo,
+                  int64_t ld, const int32_t* __restrict__ nterms, float* __restrict__ lo,
                   float* __restrict__ hi, ReluOut ro, int* status) {
   extern __shared__ float smem[];
   __shared__ float s_lohi[8][2];
@@ -27,14 +27,16 @@ k_enclose_generic(Tables T, int lb, int G, const float2* __restrict__ rs, int64_
   const bool up = warp & 1;
   if (item < n_items) {
     int nt = nterms[item];
-    if (nt < 0 || nt > stride || nt > T.mexps) {
+    if (nt < 0 || nt > ld || nt > T.mexps) {
       if (lane == 0) atomicOr(status, kStatusInvalid);
       nt = 0;
     }
+    const int64_t b = item / h;
+    const int64_t base = (b * ld) * h + (item - b * h);
     float* grid = smem + warp * G;
     const float v =
-        up ? enclose_warp_generic<true>(pre_up + item * stride, nt, T.n, lb, T, rs, grid)
-           : enclose_warp_generic<false>(pre_lo + item * stride, nt, T.n, lb, T, rs, grid);
+        up ? enclose_warp_generic<true>(pre_up + base, h, nt, T.n, lb, T, rs, grid)
+           : enclose_warp_generic<false>(pre_lo + base, h, nt, T.n, lb, T, rs, grid);
     if (lane == 0) {
       (up ? hi : lo)[item] = v;
       s_lohi[warp >> 1][up ? 1 : 0] = v;
@@ -54,9 +56,9 @@ k_enclose_generic(Tables T, int lb, int G, const float2* __restrict__ rs, int64_
 }
 
 static cudaError_t launch_generic(const Launch& L, const Tables& T, int lb, int G,
-                                  int64_t n_items, const float* pre_up, const float* pre_lo,
-                                  int64_t stride, const int32_t* nterms, float* lo, float* hi,
-                                  ReluOut ro) {
+                                  int64_t n_items, int h, const float* pre_up,
+                                  const float* pre_lo, int64_t ld, const int32_t* nterms,
+                                  float* lo, float* hi, ReluOut ro) {
   int items = (int)std::min<int64_t>(8, (192 * 1024) / (2 * (int64_t)G * 4));
   if (items < 1) items = 1;
   const size_t smem = (size_t)2 * items * G * sizeof(float);
@@ -66,9 +68,9 @@ static cudaError_t launch_generic(const Launch& L, const Tables& T, int lb, int 
     if (e != cudaSuccess) return e;
   }
   const unsigned blocks = (unsigned)((n_items + items - 1) / items);
-  k_enclose_generic<<<blocks, 64 * items, smem, L.stream>>>(T, lb, G, T.rscale[lb], n_items,
-                                                           pre_up, pre_lo, stride, nterms, lo,
-                                                           hi, ro, L.status);
+  k_enclose_generic<<<blocks, 64 * items, smem, L.stream>>>(T, lb, G, T.rscale[lb], n_items, h,
+                                                           pre_up, pre_lo, ld, nterms, lo, hi,
+                                                           ro, L.status);
   ++*L.launches;
   return cudaGetLastError();
 }
@@ -92,40 +94,41 @@ int effective_order(int n, int order, int64_t budget, int* grid_out) {
   return lb;
 }
 
-static cudaError_t launch_enclose_impl(const Launch& L, const Tables& T, int64_t n_items,
+static cudaError_t launch_enclose_impl(const Launch& L, const Tables& T, int64_t n_boxes, int h,
                                        int order, int64_t budget, const float* pre_up,
-                                       const float* pre_lo, int64_t stride,
-                                       const int32_t* nterms, float* lo, float* hi, ReluOut ro) {
+                                       const float* pre_lo, int64_t ld, const int32_t* nterms,
+                                       float* lo, float* hi, ReluOut ro) {
+  const int64_t n_items = n_boxes * h;
   if (n_items == 0) return cudaSuccess;
   int G;
   const int lb = effective_order(T.n, order, budget, &G);
   if (lb > T.rscale_max || T.rscale[lb] == nullptr) return cudaErrorInvalidValue;
 #define BERN_ENC_CASE(X) \
-  case X: return launch_lb<X>(L, T, G, n_items, pre_up, pre_lo, stride, nterms, lo, hi, ro);
+  case X: return launch_lb<X>(L, T, G, n_items, h, pre_up, pre_lo, ld, nterms, lo, hi, ro);
   switch (lb) {
     BERN_ENC_CASE(0) BERN_ENC_CASE(1) BERN_ENC_CASE(2) BERN_ENC_CASE(3) BERN_ENC_CASE(4)
     BERN_ENC_CASE(5) BERN_ENC_CASE(6) BERN_ENC_CASE(7) BERN_ENC_CASE(8) BERN_ENC_CASE(9)
     BERN_ENC_CASE(10) BERN_ENC_CASE(11) BERN_ENC_CASE(12) BERN_ENC_CASE(13) BERN_ENC_CASE(14)
     BERN_ENC_CASE(15) BERN_ENC_CASE(16)
     default:
-      return launch_generic(L, T, lb, G, n_items, pre_up, pre_lo, stride, nterms, lo, hi, ro);
+      return launch_generic(L, T, lb, G, n_items, h, pre_up, pre_lo, ld, nterms, lo, hi, ro);
   }
 #undef BERN_ENC_CASE
 }
 
-cudaError_t launch_enclose(const Launch& L, const Tables& T, int64_t n_items, int order,
-                           int64_t budget, const float* pre_up, const float* pre_lo,
-                           int64_t stride, const int32_t* nterms, float* lo, float* hi) {
-  return launch_enclose_impl(L, T, n_items, order, budget, pre_up, pre_lo, stride, nterms, lo,
+cudaError_t launch_enclose(const Launch& L, const Tables& T, int64_t n_boxes, int h, int order,
+                           int64_t budget, const float* pre_up, const float* pre_lo, int64_t ld,
+                           const int32_t* nterms, float* lo, float* hi) {
+  return launch_enclose_impl(L, T, n_boxes, h, order, budget, pre_up, pre_lo, ld, nterms, lo,
                              hi, ReluOut{nullptr, nullptr, nullptr, nullptr, 0});
 }
 
-cudaError_t launch_enclose_relu(const Launch& L, const Tables& T, int64_t n_items, int order,
-                                int64_t budget, const float* pre_up, const float* pre_lo,
-                                int64_t stride, const int32_t* nterms, float* lo, float* hi,
-                                const uint8_t* degrees, int global_d, int8_t* kind, float* coef,
-                                float* eps) {
-  return launch_enclose_impl(L, T, n_items, order, budget, pre_up, pre_lo, stride, nterms, lo,
+cudaError_t launch_enclose_relu(const Launch& L, const Tables& T, int64_t n_boxes, int h,
+                                int order, int64_t budget, const float* pre_up,
+                                const float* pre_lo, int64_t ld, const int32_t* nterms,
+                                float* lo, float* hi, const uint8_t* degrees, int global_d,
+                                int8_t* kind, float* coef, float* eps) {
+  return launch_enclose_impl(L, T, n_boxes, h, order, budget, pre_up, pre_lo, ld, nterms, lo,
                              hi, ReluOut{kind, coef, eps, degrees, global_d});
 }
 

@@ -100,6 +100,21 @@ int upload_tables(DeviceSlot& s, int n, int dmax, int deg_exps, cudaStream_t str
     off_rs[l] = put(rs.data(), rs.size() * sizeof(float));
     if (img.size() > kNoAllocTableBytes) return BERN_E_UNSUPPORTED;
   }
+  const int row_dmax = std::min(bern::kMaxRowDegree, bern::row_path_max_degree(n));
+  struct RowOff { size_t pos_in, hdr, in_off, pairs, out_ranks; int m_in, n_out_rows; };
+  std::vector<RowOff> roff(row_dmax + 1);
+  for (int D = 0; D <= row_dmax; ++D) {
+    bern::RowImage ri;
+    if (!bern::build_row_table(n, D, ri)) return BERN_E_UNSUPPORTED;
+    roff[D].m_in = ri.m_in;
+    roff[D].n_out_rows = ri.n_out_rows;
+    roff[D].pos_in = put(ri.pos_in.data(), ri.pos_in.size() * sizeof(int32_t));
+    roff[D].hdr = put(ri.hdr.data(), ri.hdr.size() * sizeof(int32_t));
+    roff[D].in_off = put(ri.in_off.data(), ri.in_off.size() * sizeof(int32_t));
+    roff[D].pairs = put(ri.pairs.data(), ri.pairs.size() * sizeof(int32_t));
+    roff[D].out_ranks = put(ri.out_ranks.data(), ri.out_ranks.size() * sizeof(int32_t));
+    if (img.size() > kNoAllocTableBytes) return BERN_E_UNSUPPORTED;
+  }
   std::vector<size_t> off_ptr(dmax + 1), off_pairs(dmax + 1);
   for (int D = 0; D <= dmax; ++D) {
     bern::PairList pl;
@@ -120,6 +135,17 @@ int upload_tables(DeviceSlot& s, int n, int dmax, int deg_exps, cudaStream_t str
   v.mcount = (const int32_t*)(s.tables + off_mc);
   v.exps = (const uint8_t*)(s.tables + off_ex);
   v.mexps = bern::num_monomials(n, deg_exps);
+  v.row_dmax = row_dmax;
+  for (int D = 0; D <= row_dmax; ++D) {
+    bern::RowTable& rt = v.row[D];
+    rt.m_in = roff[D].m_in;
+    rt.n_out_rows = roff[D].n_out_rows;
+    rt.pos_in = (const int32_t*)(s.tables + roff[D].pos_in);
+    rt.hdr = (const int4*)(s.tables + roff[D].hdr);
+    rt.in_off = (const int32_t*)(s.tables + roff[D].in_off);
+    rt.pairs = (const int4*)(s.tables + roff[D].pairs);
+    rt.out_ranks = (const int32_t*)(s.tables + roff[D].out_ranks);
+  }
   v.rscale_max = rmax;
   for (int l = 0; l <= rmax; ++l) v.rscale[l] = (const float2*)(s.tables + off_rs[l]);
   for (int D = 0; D <= dmax; ++D) {
@@ -172,6 +198,9 @@ extern "C" int bern_propagate_noalloc(const bern_net* net, const float* boxes, i
     off = align256(off + bytes);
     return r;
   };
+  int hmax = 1;
+  for (int i = 1; i <= H; ++i) hmax = std::max(hmax, net->widths[i]);
+  const size_t q_region = take(sizeof(int) * bern::kComposeQueues * hmax);
   const size_t z_up = take(sizeof(float) * n * (n + 1));
   const size_t z_lo = take(sizeof(float) * n * (n + 1));
   const size_t z_nt = take(sizeof(int32_t) * n);
@@ -213,8 +242,10 @@ extern "C" int bern_propagate_noalloc(const bern_net* net, const float* boxes, i
     }
   }
   const size_t per_box = off;
-  if (per_box > kNoAllocScratchBytes) return BERN_E_UNSUPPORTED;   // one box must fit
-  const int64_t chunk = std::min<int64_t>(n_boxes, (int64_t)(kNoAllocScratchBytes / per_box));
+  const size_t counters = 256;   // composition queue counters, ahead of the per-box regions
+  if (per_box + counters > kNoAllocScratchBytes) return BERN_E_UNSUPPORTED;   // one box must fit
+  const int64_t chunk =
+      std::min<int64_t>(n_boxes, (int64_t)((kNoAllocScratchBytes - counters) / per_box));
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return BERN_E_CUDA;
@@ -232,7 +263,8 @@ extern "C" int bern_propagate_noalloc(const bern_net* net, const float* boxes, i
 
   for (int64_t b0 = 0; b0 < n_boxes; b0 += chunk) {
     const int64_t B = std::min(chunk, n_boxes - b0);
-    auto at = [&](size_t region) { return s->scratch + region * B; };   // structure of arrays
+    auto at = [&](size_t region) { return s->scratch + counters + region * B; };   // structure of arrays
+    bern::ComposeScratch CS{(int*)s->scratch, (int*)at(q_region), B * hmax};
     cudaError_t e = bern::launch_init_inputs(La, n, B, boxes + b0 * n * 2, (float*)at(z_up),
                                              (float*)at(z_lo), n + 1, (int32_t*)at(z_nt));
     const float* in_up = (const float*)at(z_up);
@@ -254,7 +286,7 @@ extern "C" int bern_propagate_noalloc(const bern_net* net, const float* boxes, i
         r.n_terms = result->n_terms + b0 * o * 2;
         if (r.coef) r.coef = result->coef + b0 * o * 2 * r.cap_terms;
         if (r.keys) r.keys = result->keys + b0 * o * 2 * r.cap_terms;
-        e = bern::launch_enclose(La, T, B * l.h_out, l.order, budget, pu, pl, l.M_pre, pn, r.lo,
+        e = bern::launch_enclose(La, T, B, l.h_out, l.order, budget, pu, pl, l.M_pre, pn, r.lo,
                                  r.hi);
         if (e == cudaSuccess) e = bern::launch_pack(La, T, B, o, pu, pl, l.M_pre, pn, r);
         break;
@@ -267,13 +299,11 @@ extern "C" int bern_propagate_noalloc(const bern_net* net, const float* boxes, i
       float* qu = (float*)at(l.post_up);
       float* ql = (float*)at(l.post_lo);
       int32_t* qn = (int32_t*)at(l.post_nt);
-      const int64_t items = B * l.h_out;
-      e = bern::launch_enclose(La, T, items, l.order, budget, pu, pl, l.M_pre, pn, lo, hi);
+      e = bern::launch_enclose_relu(La, T, B, l.h_out, l.order, budget, pu, pl, l.M_pre, pn, lo,
+                                    hi, nullptr, l.d, kind, coef, eps);
       if (e == cudaSuccess)
-        e = bern::launch_relu_coeffs(La, items, lo, hi, nullptr, l.d, kind, coef, eps);
-      if (e == cudaSuccess)
-        e = bern::launch_compose(La, T, items, cap, dp->prune_tau, kind, coef, eps, nullptr, l.d,
-                                 lo, hi, pu, pl, l.M_pre, pn, qu, ql, l.M_post, qn);
+        e = bern::launch_compose(La, T, CS, B, l.h_out, cap, dp->prune_tau, kind, coef, eps,
+                                 nullptr, l.d, lo, hi, pu, pl, l.M_pre, pn, qu, ql, l.M_post, qn);
       in_up = qu;
       in_lo = ql;
       in_nt = qn;

@@ -82,6 +82,96 @@ bool build_product_pairs(int n, int Dq, int Ds, PairList& out) {
   return build_pairs(n, Dq, Ds, false, out);
 }
 
+bool build_row_table(int n, int D, RowImage& out) {
+  out = RowImage{};
+  if (D < 0 || D > kMaxRowDegree) return false;
+  const int64_t m_in = num_monomials(n, D);
+  const int64_t m_full = num_monomials(n, 2 * D);
+  // prefixes: exponent vectors of t_1..t_{n-1} up to total degree 2D
+  std::vector<uint8_t> pre;
+  int np;
+  if (n == 1) {
+    np = 1;
+  } else {
+    graded_monomials(n - 1, 2 * D, pre);
+    np = (int)num_monomials(n - 1, 2 * D);
+  }
+  auto psum = [&](int i) {
+    int s = 0;
+    for (int k = 0; k < n - 1; ++k) s += pre[(size_t)i * (n - 1) + k];
+    return s;
+  };
+  std::vector<uint8_t> ex;
+  graded_monomials(n, 2 * D, ex);
+  std::unordered_map<uint64_t, int32_t> rank;
+  rank.reserve((size_t)m_full * 2);
+  for (int64_t r = 0; r < m_full; ++r) rank[pack_key(&ex[(size_t)r * n], n)] = (int32_t)r;
+  auto full_rank = [&](int pi, int c) {
+    uint8_t e[kMaxVars] = {0};
+    for (int k = 0; k < n - 1; ++k) e[k] = pre[(size_t)pi * (n - 1) + k];
+    e[n - 1] = (uint8_t)c;
+    return rank.at(pack_key(e, n));
+  };
+  // input rows: the prefixes of degree <= D (a graded prefix of the list)
+  const int np_in = n == 1 ? 1 : (int)num_monomials(n - 1, D);
+  std::vector<int32_t> off(np_in), len(np_in);
+  int pos = 0;
+  out.pos_in.assign(m_in, -1);
+  for (int i = 0; i < np_in; ++i) {
+    off[i] = pos;
+    len[i] = D - (n == 1 ? 0 : psum(i)) + 1;
+    for (int c = 0; c < len[i]; ++c) out.pos_in[full_rank(i, c)] = pos + c;
+    pos += len[i];
+  }
+  if (pos != m_in) return false;
+  // prefix key -> prefix index
+  std::unordered_map<uint64_t, int32_t> pidx;
+  for (int i = 0; i < np; ++i) pidx[n == 1 ? 0 : pack_key(&pre[(size_t)i * (n - 1)], n - 1)] = i;
+  std::vector<std::vector<int>> bucket(np);
+  for (int i = 0; i < np_in; ++i)
+    for (int j = i; j < np_in; ++j) {
+      uint64_t k = 0;
+      if (n > 1)
+        k = pack_key(&pre[(size_t)i * (n - 1)], n - 1) + pack_key(&pre[(size_t)j * (n - 1)], n - 1);
+      bucket[pidx.at(k)].push_back(i * np_in + j);
+    }
+  out.n_out_rows = np;
+  out.m_in = (int)m_in;
+  for (int P = 0; P < np; ++P) {
+    const int sP = n == 1 ? 0 : psum(P);
+    const int Lout = 2 * D - sP + 1;
+    out.hdr.push_back((int32_t)(out.pairs.size() / 4));
+    for (int code : bucket[P]) {
+      const int i = code / np_in, j = code % np_in;
+      int oi = off[i], oj = off[j], li = len[i], lj = len[j];
+      if (li > lj) {
+        std::swap(oi, oj);
+        std::swap(li, lj);
+      }
+      out.pairs.push_back(oi);
+      out.pairs.push_back(oj);
+      out.pairs.push_back((li << 4) | lj);
+      out.pairs.push_back(i == j ? 1 : 0);
+    }
+    out.hdr.push_back((int32_t)(out.pairs.size() / 4));
+    out.hdr.push_back((int32_t)out.out_ranks.size());
+    const int in_len = sP <= D ? D - sP + 1 : 0;
+    out.hdr.push_back(Lout | (in_len << 8));
+    out.in_off.push_back(sP <= D ? off[P] : -1);
+    for (int c = 0; c < Lout; ++c) out.out_ranks.push_back(full_rank(P, c));
+  }
+  return true;
+}
+
+// The row-convolution kernel keeps one row-layout copy of the input per lane
+// in shared memory (32 lanes per warp); inputs up to 750 terms fit one warp in
+// 96 KB.
+int row_path_max_degree(int n) {
+  int D = kMaxRowDegree;
+  while (D > 0 && num_monomials(n, D) > 750) --D;
+  return D;
+}
+
 int max_enclose_order(int n) {
   int l = kMaxEncloseOrder;
   for (; l > 0; --l) {

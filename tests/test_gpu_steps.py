@@ -32,6 +32,8 @@ def dev(a, dtype=None):
 
 
 # ---------------------------------------------------------------- a0
+# Layer blocks: coefficient r of neuron m of box b at ((b*ld + r)*h + m).
+
 def test_init_inputs(ctx):
     rng = np.random.default_rng(0)
     n, B = 3, 37
@@ -39,27 +41,27 @@ def test_init_inputs(ctx):
     hi = (lo + rng.uniform(0, 1.5, (B, n))).astype(np.float32)
     hi[5] = lo[5]                                   # a point box
     boxes = np.stack([lo, hi], -1)
-    stride = n + 1
-    zu = torch.zeros(B * n * stride, device="cuda")
+    ld = n + 2
+    zu = torch.zeros(B * ld * n, device="cuda")
     zl = torch.zeros_like(zu)
     nt = torch.zeros(B * n, dtype=torch.int32, device="cuda")
-    ctx.init_inputs(n, dev(boxes), zu, zl, stride, nt)
+    ctx.init_inputs(n, dev(boxes), zu, zl, ld, nt)
     assert ctx.sync() == 0
-    zu = zu.cpu().numpy().reshape(B, n, stride)
-    assert np.array_equal(zu, zl.cpu().numpy().reshape(B, n, stride))
+    zu = zu.cpu().numpy().reshape(B, ld, n)
+    assert np.array_equal(zu, zl.cpu().numpy().reshape(B, ld, n))
     assert np.all(nt.cpu().numpy() == n + 1)
     w = hi.astype(np.float64) - lo.astype(np.float64)
     for b in range(B):
         for i in range(n):
-            assert zu[b, i, 0] == lo[b, i]
-            assert zu[b, i, 1 + i] >= w[b, i] and zu[b, i, 1 + i] - w[b, i] <= 2 ** -23 * (w[b, i] + 1e-30) * 2
-            others = [zu[b, i, 1 + k] for k in range(n) if k != i]
+            assert zu[b, 0, i] == lo[b, i]
+            assert zu[b, 1 + i, i] >= w[b, i] and zu[b, 1 + i, i] - w[b, i] <= 2 ** -23 * (w[b, i] + 1e-30) * 2
+            others = [zu[b, 1 + k, i] for k in range(n) if k != i]
             assert all(x == 0 for x in others)
 
 
 def test_init_rejects_inverted_box(ctx):
     boxes = np.array([[[0.5, 0.25], [0, 1]]], np.float32)
-    zu = torch.zeros(2 * 3, device="cuda")
+    zu = torch.zeros(3 * 2, device="cuda")
     zl = torch.zeros_like(zu)
     nt = torch.zeros(2, dtype=torch.int32, device="cuda")
     ctx.init_inputs(2, dev(boxes), zu, zl, 3, nt)
@@ -68,7 +70,9 @@ def test_init_rejects_inverted_box(ctx):
 
 
 # ---------------------------------------------------------------- a1
-@pytest.mark.parametrize("n,D,h_in,h_out,B", [(2, 2, 5, 7, 3), (3, 4, 20, 9, 5), (4, 3, 33, 17, 2)])
+@pytest.mark.parametrize("n,D,h_in,h_out,B", [
+    (2, 2, 5, 7, 3), (3, 4, 20, 9, 5), (4, 3, 33, 17, 2), (3, 8, 64, 1, 3), (2, 3, 6, 3, 4),
+    (3, 2, 7, 5, 2), (3, 8, 64, 64, 2), (2, 4, 40, 33, 3), (6, 2, 100, 100, 2), (1, 6, 3, 2, 5)])
 def test_affine_step(ctx, n, D, h_in, h_out, B):
     rng = np.random.default_rng(n * 100 + D)
     M = bern.num_monomials(n, D)
@@ -88,14 +92,19 @@ def test_affine_step(ctx, n, D, h_in, h_out, B):
     W = rng.normal(size=(h_out, h_in)).astype(np.float32)
     W[rng.random(W.shape) < 0.1] = 0.0
     bias = rng.normal(size=h_out).astype(np.float32)
-    out_u = torch.full((B * h_out * M,), np.nan, device="cuda")
+    out_u = torch.full((B * M * h_out,), np.nan, device="cuda")
     out_l = torch.full_like(out_u, np.nan)
     out_nt = torch.zeros(B * h_out, dtype=torch.int32, device="cuda")
-    ctx.affine(B, h_out, h_in, dev(W), dev(bias), dev(up), dev(lo), M, dev(nt), out_u, out_l, M,
-               out_nt)
+    # entries beyond a neuron's term count hold garbage that must not be read
+    up_blk = np.where(np.arange(M)[None, None, :] < nt[:, :, None], up, np.float32(1e30))
+    lo_blk = np.where(np.arange(M)[None, None, :] < nt[:, :, None], lo, np.float32(-1e30))
+    up_blk = np.ascontiguousarray(up_blk.transpose(0, 2, 1))
+    lo_blk = np.ascontiguousarray(lo_blk.transpose(0, 2, 1))
+    ctx.affine(B, h_out, h_in, dev(W), dev(bias), dev(up_blk), dev(lo_blk), M, dev(nt), out_u,
+               out_l, M, out_nt)
     assert ctx.sync() == 0
-    out_u = out_u.cpu().numpy().reshape(B, h_out, M).astype(np.float64)
-    out_l = out_l.cpu().numpy().reshape(B, h_out, M).astype(np.float64)
+    out_u = out_u.cpu().numpy().reshape(B, M, h_out).transpose(0, 2, 1).astype(np.float64)
+    out_l = out_l.cpu().numpy().reshape(B, M, h_out).transpose(0, 2, 1).astype(np.float64)
     out_nt = out_nt.cpu().numpy().reshape(B, h_out)
     from parity_util import dict_from_dense
     for b in range(B):
@@ -125,7 +134,8 @@ def test_affine_step(ctx, n, D, h_in, h_out, B):
 def test_enclose_step(ctx, n, D, order, budget):
     rng = np.random.default_rng(7 * n + D + order)
     M = bern.num_monomials(n, D)
-    items = 23
+    h, B = 3, 8
+    items = B * h
     up = np.zeros((items, M), np.float32)
     lo = np.zeros((items, M), np.float32)
     nt = np.zeros(items, np.int32)
@@ -135,9 +145,14 @@ def test_enclose_step(ctx, n, D, order, budget):
         base = random_dense(rng, n, D)[:k]
         up[i, :k] = base + 0.1
         lo[i, :k] = base - 0.1
+    # layer block [B][M][h]; unused entries are poison
+    blk_u = np.where(np.arange(M)[None, :] < nt[:, None], up, np.float32(np.nan))
+    blk_l = np.where(np.arange(M)[None, :] < nt[:, None], lo, np.float32(np.nan))
+    blk_u = np.ascontiguousarray(blk_u.reshape(B, h, M).transpose(0, 2, 1))
+    blk_l = np.ascontiguousarray(blk_l.reshape(B, h, M).transpose(0, 2, 1))
     glo = torch.zeros(items, device="cuda")
     ghi = torch.zeros(items, device="cuda")
-    ctx.enclose(n, items, order, budget, dev(up), dev(lo), M, dev(nt), glo, ghi)
+    ctx.enclose(n, B, h, order, budget, dev(blk_u), dev(blk_l), M, dev(nt), glo, ghi)
     assert ctx.sync() == 0
     glo, ghi = glo.cpu().numpy().astype(np.float64), ghi.cpu().numpy().astype(np.float64)
     eff_budget = bern.effective_budget(budget)
@@ -194,7 +209,8 @@ def test_compose_step(ctx, n, D, d, cap):
     rng = np.random.default_rng(1000 + 10 * n + D + cap)
     M = bern.num_monomials(n, D)
     Mout = bern.num_monomials(n, min(d * D, cap))
-    items = 11
+    h, B = 4, 3
+    items = h * B
     pu = np.zeros((items, M), np.float32)
     pl = np.zeros((items, M), np.float32)
     nt = np.full(items, M, np.int32)
@@ -224,15 +240,17 @@ def test_compose_step(ctx, n, D, d, cap):
     eps = torch.zeros(items, device="cuda")
     glo, ghi = dev(lo), dev(hi)
     ctx.relu_coeffs(items, glo, ghi, None, d, kind, coef, eps)
-    qu = torch.full((items * Mout,), np.nan, device="cuda")
+    blk_u = np.ascontiguousarray(pu.reshape(B, h, M).transpose(0, 2, 1))
+    blk_l = np.ascontiguousarray(pl.reshape(B, h, M).transpose(0, 2, 1))
+    qu = torch.full((B * Mout * h,), np.nan, device="cuda")
     ql = torch.full_like(qu, np.nan)
     qnt = torch.zeros(items, dtype=torch.int32, device="cuda")
-    ctx.compose(n, items, cap, 0.0, kind, coef, eps, None, d, glo, ghi, dev(pu), dev(pl), M,
+    ctx.compose(n, B, h, cap, 0.0, kind, coef, eps, None, d, glo, ghi, dev(blk_u), dev(blk_l), M,
                 dev(nt), qu, ql, Mout, qnt)
     assert ctx.sync() == 0
     assert np.all(kind.cpu().numpy() == 2)
-    qu = qu.cpu().numpy().reshape(items, Mout).astype(np.float64)
-    ql = ql.cpu().numpy().reshape(items, Mout).astype(np.float64)
+    qu = qu.cpu().numpy().reshape(B, Mout, h).transpose(0, 2, 1).reshape(items, Mout).astype(np.float64)
+    ql = ql.cpu().numpy().reshape(B, Mout, h).transpose(0, 2, 1).reshape(items, Mout).astype(np.float64)
     qnt = qnt.cpu().numpy()
     pts = rng.random((300, n))
     pts[0] = 1.0
@@ -257,7 +275,8 @@ def test_compose_step(ctx, n, D, d, cap):
 
 
 def test_compose_stable_cases(ctx):
-    """Identity items copy their input, zero items produce no terms."""
+    """Identity items copy their input, zero items produce no terms (one box,
+    three neurons)."""
     n, D = 2, 2
     M = bern.num_monomials(n, D)
     rng = np.random.default_rng(3)
@@ -271,15 +290,16 @@ def test_compose_stable_cases(ctx):
     eps = torch.zeros(3, device="cuda")
     ctx.relu_coeffs(3, dev(lo), dev(hi), None, 2, kind, coef, eps)
     Mout = bern.num_monomials(n, 2 * D)
-    qu = torch.zeros(3 * Mout, device="cuda")
+    qu = torch.zeros(Mout * 3, device="cuda")
     ql = torch.zeros_like(qu)
     qnt = torch.zeros(3, dtype=torch.int32, device="cuda")
-    ctx.compose(n, 3, 16, 0.0, kind, coef, eps, None, 2, dev(lo), dev(hi), dev(pu), dev(pl), M,
-                dev(nt), qu, ql, Mout, qnt)
+    ctx.compose(n, 1, 3, 16, 0.0, kind, coef, eps, None, 2, dev(lo), dev(hi),
+                dev(np.ascontiguousarray(pu.T)), dev(np.ascontiguousarray(pl.T)), M, dev(nt), qu,
+                ql, Mout, qnt)
     assert ctx.sync() == 0
     assert list(kind.cpu().numpy()) == [0, 1, 2]
     qnt = qnt.cpu().numpy()
     assert qnt[0] == 0 and qnt[1] == M and qnt[2] == Mout
-    qu = qu.cpu().numpy().reshape(3, Mout)
-    ql = ql.cpu().numpy().reshape(3, Mout)
+    qu = qu.cpu().numpy().reshape(Mout, 3).T
+    ql = ql.cpu().numpy().reshape(Mout, 3).T
     assert np.array_equal(qu[1, :M], pu[1]) and np.array_equal(ql[1, :M], pl[1])
