@@ -146,6 +146,7 @@ int ensure_tables(bern_ctx* c, int n, int dmax, const Tables** out) {
     RowTable& rt = ts.view.row[D];
     rt.m_in = ri.m_in;
     rt.n_out_rows = ri.n_out_rows;
+    rt.row_split = ri.row_split;
     auto up = [&](const std::vector<int32_t>& v, const void** dst) -> cudaError_t {
       DevBuf b;
       cudaError_t e2 = b.reserve(std::max<size_t>(16, v.size() * sizeof(int32_t)));

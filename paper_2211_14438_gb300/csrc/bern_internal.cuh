@@ -50,8 +50,10 @@ constexpr int kMaxRowDegree = 8;          // input degree handled by row convolu
 constexpr int kRowLen = kMaxRowDegree + 1;
 struct RowImage {
   int m_in = 0, n_out_rows = 0;
+  int row_split = 0;               // output rows [0, split) hold about half the work
   std::vector<int32_t> pos_in;     // graded rank -> row-layout position
-  std::vector<int32_t> hdr;        // per output row: pair_begin, pair_end, rank_begin, Lout|in_len<<8
+  std::vector<int32_t> hdr;        // per output row: pair_begin, pair_end, rank_begin,
+                                   // Lout | in_len<<8 | has_diag<<16 (diagonal pair last)
   std::vector<int32_t> in_off;     // per output row: its input-row offset or -1
   std::vector<int32_t> pairs;      // per pair: off_p, off_q, (L1<<4)|L2 with L1<=L2, diag
   std::vector<int32_t> out_ranks;  // graded ranks of the output row elements
@@ -60,7 +62,7 @@ bool build_row_table(int n, int D, RowImage& out);
 
 // ------------------------------------------------------------ device views
 struct RowTable {
-  int m_in, n_out_rows;
+  int m_in, n_out_rows, row_split;
   const int32_t* pos_in;
   const int4* hdr;
   const int32_t* in_off;

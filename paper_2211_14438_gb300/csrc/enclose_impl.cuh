@@ -279,6 +279,138 @@ cudaError_t launch_lb(const Launch& L, const Tables& T, int G, int64_t n_items, 
   return cudaGetLastError();
 }
 
+// Tiny grids ((l+1)^n <= 64): one lane per polynomial, the lane's grid
+// interleaved with its warp's (element g of lane L at grid[g*32 + L]); a warp
+// takes 32 items of one bound, a block 4 groups of 32 items (both bounds).
+constexpr int kSmallGrid = 64;
+template <int LB, bool UP>
+__device__ float enclose_lane(const float* __restrict__ P, int ps, int nt, int n,
+                              const Tables& T, const float2* __restrict__ rs, float* grid) {
+  constexpr int R = LB + 1;
+  int pw[kMaxVars];
+  {
+    int p = 1;
+    for (int k = n - 1; k >= 0; --k) {
+      pw[k] = p;
+      p *= R;
+    }
+  }
+  int Dnt = 0;
+  while (Dnt < kMaxTableDegree && T.mcount[Dnt] < nt) ++Dnt;
+  const int Deff = Dnt < LB ? Dnt : LB;
+  float rem = 0.0f;
+  for (int r = 0; r < nt; ++r) {
+    const float a = P[(int64_t)r * ps];
+    const uint8_t* e = T.exps + (int64_t)r * n;
+    int deg = 0, idx = 0;
+    for (int k = 0; k < n; ++k) {
+      deg += e[k];
+      idx += e[k] * pw[k];
+    }
+    if (deg <= Deff) {
+      const float2 sc = rs[r];
+      grid[idx * 32] = UP ? __fmul_ru(a, a >= 0.0f ? sc.y : sc.x)
+                          : __fmul_rd(a, a >= 0.0f ? sc.x : sc.y);
+    } else {
+      rem = UP ? __fadd_ru(rem, fmaxf(a, 0.0f)) : __fadd_rd(rem, fminf(a, 0.0f));
+    }
+  }
+  for (int r = nt; r < T.mcount[Deff]; ++r) {
+    const uint8_t* e = T.exps + (int64_t)r * n;
+    int idx = 0;
+    for (int k = 0; k < n; ++k) idx += e[k] * pw[k];
+    grid[idx * 32] = 0.0f;
+  }
+  float best = UP ? -CUDART_INF_F : CUDART_INF_F;
+  int nlines = 1;
+  for (int m = 0; m < n - 1; ++m) nlines *= R;
+  for (int k = n - 1; k >= 0; --k) {
+    const int sk = pw[k];
+    for (int Ln = 0; Ln < nlines; ++Ln) {
+      int rest = Ln, base = 0, psum = 0;
+      for (int m = n - 1; m >= 0; --m) {
+        if (m == k) continue;
+        const int dgt = rest % R;
+        rest /= R;
+        base += dgt * pw[m];
+        if (m < k) psum += dgt;
+      }
+      if (psum > Deff) continue;
+      const int p = Deff - psum;
+      float x[R], y[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) x[j] = j <= p ? grid[(base + j * sk) * 32] : 0.0f;
+      line_transform<LB, UP>(x, y);
+      if (k > 0) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) grid[(base + i * sk) * 32] = y[i];
+      } else {
+#pragma unroll
+        for (int i = 0; i < R; ++i) best = UP ? fmaxf(best, y[i]) : fminf(best, y[i]);
+      }
+    }
+  }
+  return dadd<UP>(best, rem);
+}
+
+template <int LB>
+__global__ void __launch_bounds__(256)
+k_enclose_small(Tables T, int G, const float2* __restrict__ rs, int64_t n_items, int h,
+                const float* __restrict__ pre_up, const float* __restrict__ pre_lo, int64_t ld,
+                const int32_t* __restrict__ nterms, float* __restrict__ lo,
+                float* __restrict__ hi, ReluOut ro, int* status) {
+  extern __shared__ float smem[];
+  __shared__ float s_lohi[128][2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int group = warp >> 1;
+  const bool up = warp & 1;
+  const int64_t item = (int64_t)blockIdx.x * 128 + group * 32 + lane;
+  float v = 0.0f;
+  if (item < n_items) {
+    int nt = nterms[item];
+    if (nt < 0 || nt > ld || nt > T.mexps) {
+      atomicOr(status, kStatusInvalid);
+      nt = 0;
+    }
+    const int64_t b = item / h;
+    const int64_t base = (b * ld) * h + (item - b * h);
+    float* grid = smem + (size_t)warp * G * 32 + lane;
+    v = up ? enclose_lane<LB, true>(pre_up + base, h, nt, T.n, T, rs, grid)
+           : enclose_lane<LB, false>(pre_lo + base, h, nt, T.n, T, rs, grid);
+    (up ? hi : lo)[item] = v;
+    if (!isfinite(v)) atomicOr(status, kStatusNonFinite);
+  }
+  s_lohi[group * 32 + lane][up ? 1 : 0] = v;
+  if (ro.kind == nullptr) return;
+  __syncthreads();
+  if (threadIdx.x < 128) {
+    const int64_t it = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    if (it < n_items) {
+      const int d = ro.degrees ? (int)ro.degrees[it] : ro.global_d;
+      ro.kind[it] = (int8_t)relu_item(s_lohi[threadIdx.x][0], s_lohi[threadIdx.x][1], d,
+                                      ro.coef + it * kCoefStride, ro.eps + it, status);
+    }
+  }
+}
+
+template <int LB>
+cudaError_t launch_small(const Launch& L, const Tables& T, int G, int64_t n_items, int h,
+                         const float* pre_up, const float* pre_lo, int64_t ld,
+                         const int32_t* nterms, float* lo, float* hi, ReluOut ro) {
+  const size_t smem = (size_t)8 * G * 32 * sizeof(float);   // <= 64 KB
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_enclose_small<LB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const unsigned blocks = (unsigned)((n_items + 127) / 128);
+  k_enclose_small<LB><<<blocks, 256, smem, L.stream>>>(T, G, T.rscale[LB], n_items, h, pre_up,
+                                                       pre_lo, ld, nterms, lo, hi, ro,
+                                                       L.status);
+  ++*L.launches;
+  return cudaGetLastError();
+}
+
 // Orders above 16: one kernel with a runtime order; each line is transformed
 // in place in shared memory by l sweeps of pairwise directed additions
 // (Pascal's rule: after sweep r, c_i holds sum_j C(.,.) c_j partial sums), so

@@ -183,11 +183,10 @@ k_affine_narrow(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ 
   }
   const float* pu = in_up + (b * in_ld + r) * h_in;
   const float* pl = in_lo + (b * in_ld + r) * h_in;
-#pragma unroll 4
-  for (int j = 0; j < h_in; ++j) {
+  auto step = [&](int j, float u, float l) {
     const bool live = r < sN[j];
-    const float u = live ? __ldg(pu + j) : 0.0f;
-    const float l = live ? __ldg(pl + j) : 0.0f;
+    u = live ? u : 0.0f;
+    l = live ? l : 0.0f;
 #pragma unroll
     for (int m = 0; m < HO; ++m) {
       const float w = sW[m * h_in + j];
@@ -195,6 +194,22 @@ k_affine_narrow(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ 
       up[m] = __fmaf_ru(w, pos ? u : l, up[m]);
       lo[m] = __fmaf_rd(w, pos ? l : u, lo[m]);
     }
+  };
+  if ((h_in & 3) == 0 && ((reinterpret_cast<uintptr_t>(pu) | reinterpret_cast<uintptr_t>(pl)) & 15) == 0) {
+    // rows are 16-byte aligned: read them as float4
+    const float4* pu4 = reinterpret_cast<const float4*>(pu);
+    const float4* pl4 = reinterpret_cast<const float4*>(pl);
+#pragma unroll 2
+    for (int j4 = 0; j4 < (h_in >> 2); ++j4) {
+      const float4 u = __ldg(pu4 + j4), l = __ldg(pl4 + j4);
+      step(4 * j4, u.x, l.x);
+      step(4 * j4 + 1, u.y, l.y);
+      step(4 * j4 + 2, u.z, l.z);
+      step(4 * j4 + 3, u.w, l.w);
+    }
+  } else {
+#pragma unroll 4
+    for (int j = 0; j < h_in; ++j) step(j, __ldg(pu + j), __ldg(pl + j));
   }
 #pragma unroll
   for (int m = 0; m < HO; ++m) {
@@ -235,9 +250,17 @@ cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
                           float* out_up, float* out_lo, int64_t out_ld,
                           int32_t* out_nterms) {
   if (n_boxes == 0) return cudaSuccess;
-  if (n_boxes > 0x7fffffff || (in_ld + 15) / 16 > 65535) return cudaErrorInvalidValue;
+  if (n_boxes > 0x7fffffff || (std::min(in_ld, out_ld) + 15) / 16 > 65535)
+    return cudaErrorInvalidValue;
+  const bool few_rows = std::min(in_ld, out_ld) <= 16;     // short polynomials: short tiles
+  if (h_out >= 32 && few_rows)
+    return launch_cfg<64, 16, 4, 1, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
+                                        in_nterms, out_up, out_lo, out_ld, out_nterms);
   if (h_out >= 32)
     return launch_cfg<64, 64, 4, 4, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
+                                        in_nterms, out_up, out_lo, out_ld, out_nterms);
+  if (h_out > 8 && few_rows)
+    return launch_cfg<16, 16, 2, 1, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
                                         in_nterms, out_up, out_lo, out_ld, out_nterms);
   if (h_out > 8)
     return launch_cfg<16, 64, 2, 4, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,

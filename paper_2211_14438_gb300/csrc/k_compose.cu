@@ -159,11 +159,8 @@ __device__ __forceinline__ void conv_rows(const float* __restrict__ s, int offp,
     for (int b = 0; b < L2; ++b) acc[a + b] = dfma<UP>(x[a], y[b], acc[a + b]);
 }
 
-#define BERN_CC(L1, L2)                                                           \
-  case (L1 << 4) | L2:                                                            \
-    if (pr.w) conv_rows<L1, L2, UP>(s, pr.x, pr.y, accd);                        \
-    else conv_rows<L1, L2, UP>(s, pr.x, pr.y, acc);                              \
-    break;
+#define BERN_CC(L1, L2) \
+  case (L1 << 4) | L2: conv_rows<L1, L2, UP>(s, pr.x, pr.y, acc); break;
 #define BERN_CONV_ALL_CASES                                                                     \
   BERN_CC(1, 1) BERN_CC(1, 2) BERN_CC(1, 3) BERN_CC(1, 4) BERN_CC(1, 5) BERN_CC(1, 6)          \
   BERN_CC(1, 7) BERN_CC(1, 8) BERN_CC(1, 9) BERN_CC(2, 2) BERN_CC(2, 3) BERN_CC(2, 4)          \
@@ -173,29 +170,20 @@ __device__ __forceinline__ void conv_rows(const float* __restrict__ s, int offp,
   BERN_CC(5, 5) BERN_CC(5, 6) BERN_CC(5, 7) BERN_CC(5, 8) BERN_CC(5, 9) BERN_CC(6, 6)          \
   BERN_CC(6, 7) BERN_CC(6, 8) BERN_CC(6, 9) BERN_CC(7, 7) BERN_CC(7, 8) BERN_CC(7, 9)          \
   BERN_CC(8, 8) BERN_CC(8, 9) BERN_CC(9, 9)
+#define BERN_CD(L) \
+  case L: conv_rows<L, L, UP>(s, pr.x, pr.x, accd); break;
+#define BERN_DIAG_CASES \
+  BERN_CD(1) BERN_CD(2) BERN_CD(3) BERN_CD(4) BERN_CD(5) BERN_CD(6) BERN_CD(7) BERN_CD(8) BERN_CD(9)
 
-// One bound of the items of a warp: UP = upper polynomial.
-template <bool UP>
-__device__ void rows_pass(const Tables& T, const ComposeArgs& A, const RowTable& R, int D,
-                          int64_t item, bool valid, float* s, int* status) {
-  const float Lo = valid ? A.lo[item] : -1.0f;
-  const float Hi = valid ? A.hi[item] : 1.0f;
-  const float inv = 1.0f / (Hi - Lo);
-  float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, eps = 0.0f;
-  if (valid) {
-    const float* cf = A.coef + item * kCoefStride;
-    a0 = cf[0];
-    a1 = cf[1];
-    a2 = cf[2];
-    eps = A.eps[item];
-    if (a2 < 0.0f) atomicOr(status, kStatusUnsupported);   // excluded by convexity
-  }
-  const int Mpre = valid ? A.pre_nterms[item] : 0;
+// Load one bound of the 32 items of a lane group into row layout:
+// s = (pre - lo*[K=0]) / (hi - lo) in round-to-nearest; returns this warp's
+// share of sum|s| (rounded up).  Warp `half` (0/1) takes every other group
+// of 8 input monomials.
+__device__ float load_rows(const ComposeArgs& A, const RowTable& R, const float* P, int Mpre,
+                           float Lo, float inv, int half, float* s) {
   const int h = A.h;
-  const float* P = (UP ? A.pre_up : A.pre_lo) + A.base(valid ? item : 0, A.pre_ld);
-  // gather the input into row layout, 8 loads in flight per lane
   float l1 = 0.0f;
-  for (int r0 = 0; r0 < R.m_in; r0 += 8) {
+  for (int r0 = 8 * half; r0 < R.m_in; r0 += 16) {
     float v[8];
     int pos[8];
 #pragma unroll
@@ -214,25 +202,40 @@ __device__ void rows_pass(const Tables& T, const ComposeArgs& A, const RowTable&
       l1 = __fadd_ru(l1, fabsf(x));
     }
   }
-  __syncwarp();
-  const float eta = __fmul_ru(5.0f * kU, l1);
-  const float lip = __fmaf_ru(2.0f * a2, __fadd_ru(1.0f, eta), fabsf(a1));
+  return l1;
+}
+
+// Output rows [row_b, row_e) of one bound (UP: upper polynomial) of the
+// items of a warp: per row, the row-pair convolutions, then the coefficients
+// a1*s + a2*s^2 of the row's monomials (the constant term only in c0).
+template <bool UP>
+__device__ void rows_range(const Tables& T, const ComposeArgs& A, const RowTable& R, int D,
+                           int row_b, int row_e, bool valid, float a1, float a2,
+                           const float* s, float* Q, float* c0_out, float* rem_out) {
+  const int h = A.h;
   const int Mout = T.mcount[min(2 * D, A.cap)];
-  float* Q = (UP ? A.post_up : A.post_lo) + A.base(valid ? item : 0, A.post_ld);
-  float c0 = 0.0f, rem = 0.0f;
-  int4 hd = __ldg(R.hdr);
-  for (int row = 0; row < R.n_out_rows; ++row) {
-    const int4 hn = row + 1 < R.n_out_rows ? __ldg(R.hdr + row + 1) : hd;
+  const bool no_trunc = 2 * D <= A.cap;   // every output monomial is kept
+  float rem = 0.0f;
+  for (int row = row_b; row < row_e; ++row) {
+    const int4 hd = __ldg(R.hdr + row);
+    const int Lout = hd.w & 0xff, in_len = (hd.w >> 8) & 0xff;
+    const int in_off = __ldg(R.in_off + row);
+    // fetch the row's output ranks now; they are used after the convolutions
+    int rk[2 * kRowLen - 1];
+#pragma unroll
+    for (int c = 0; c < 2 * kRowLen - 1; ++c) rk[c] = c < Lout ? __ldg(R.out_ranks + hd.z + c) : 0;
     float acc[2 * kRowLen - 1], accd[2 * kRowLen - 1];
 #pragma unroll
     for (int c = 0; c < 2 * kRowLen - 1; ++c) {
       acc[c] = 0.0f;
       accd[c] = 0.0f;
     }
-    if (hd.x < hd.y) {
+    const int has_diag = (hd.w >> 16) & 1;
+    const int off_end = hd.y - has_diag;
+    if (hd.x < off_end) {
       int4 pr = __ldg(R.pairs + hd.x);
-      for (int k = hd.x; k < hd.y; ++k) {
-        const int4 nx = k + 1 < hd.y ? __ldg(R.pairs + k + 1) : pr;   // prefetch
+      for (int k = hd.x; k < off_end; ++k) {
+        const int4 nx = k + 1 < off_end ? __ldg(R.pairs + k + 1) : pr;   // prefetch
         switch (pr.z) {
           BERN_CONV_ALL_CASES
           default: break;
@@ -240,53 +243,46 @@ __device__ void rows_pass(const Tables& T, const ComposeArgs& A, const RowTable&
         pr = nx;
       }
     }
-    const int Lout = hd.w & 0xff, in_len = hd.w >> 8;
-    const int in_off = __ldg(R.in_off + row);
-    int rk[2 * kRowLen - 1];
-#pragma unroll
-    for (int c = 0; c < 2 * kRowLen - 1; ++c) rk[c] = c < Lout ? __ldg(R.out_ranks + hd.z + c) : 0;
-#pragma unroll
-    for (int c = 0; c < 2 * kRowLen - 1; ++c) {
-      if (c < Lout) {
-        const int rank = rk[c];
-        // (s^2) = diagonal part + 2 * off-diagonal part; 2*x is exact
-        const float sq = dadd<UP>(accd[c], 2.0f * acc[c]);
-        const float lin = c < in_len ? s[in_off + c] : 0.0f;
-        const float at0 = rank == 0 ? a0 : 0.0f;
-        const float v = dfma<UP>(a2, sq, dfma<UP>(a1, lin, at0));
-        if (rank == 0) {
-          c0 = v;
-        } else if (rank < Mout) {
-          if (valid) Q[(int64_t)rank * h] = v;
-        } else {
-          rem = UP ? __fadd_ru(rem, fmaxf(v, 0.0f)) : __fadd_rd(rem, fminf(v, 0.0f));
-        }
+    if (has_diag) {
+      const int4 pr = __ldg(R.pairs + off_end);
+      switch (pr.z & 15) {
+        BERN_DIAG_CASES
+        default: break;
       }
     }
-    hd = hn;
-  }
-  if (valid) {
-    float v;
-    if (UP) {
-      v = __fadd_ru(__fadd_ru(c0, __fmul_ru(lip, eta)), rem);
-    } else {
-      v = __fsub_rd(c0, __fmul_ru(lip, eta));
-      v = __fadd_rd(__fsub_rd(v, eps), rem);
+#pragma unroll
+    for (int c = 0; c < 2 * kRowLen - 1; ++c) {
+      if (c >= Lout) break;
+      // (s^2) = diagonal part + 2 * off-diagonal part; 2*x is exact
+      const float sq = dadd<UP>(accd[c], 2.0f * acc[c]);
+      const float lin = c < in_len ? s[in_off + c] : 0.0f;
+      const float v = dfma<UP>(a2, sq, UP ? __fmul_ru(a1, lin) : __fmul_rd(a1, lin));
+      if (row == 0 && c == 0) {
+        *c0_out = v;                      // the constant term is finished by the caller
+      } else if (no_trunc || rk[c] < Mout) {
+        if (valid) Q[(int64_t)rk[c] * h] = v;
+      } else {
+        rem = UP ? __fadd_ru(rem, fmaxf(v, 0.0f)) : __fadd_rd(rem, fminf(v, 0.0f));
+      }
     }
-    Q[0] = v;
-    if (!isfinite(v)) atomicOr(status, kStatusNonFinite);
   }
-  __syncwarp();
+  *rem_out = rem;
 }
 
-__global__ void __launch_bounds__(256, 2)
+// A block of four warps squares 32 queued items (one lane per item): warps
+// 0-1 compute the upper polynomials, warps 2-3 the lower ones, each pair
+// splitting the output rows in two ranges of about equal work.  The two
+// bounds' inputs of the 32 items sit in shared memory once.
+__global__ void __launch_bounds__(128, 4)
 k_compose_rows(Tables T, ComposeArgs A, ComposeScratch S, int row_dmax, int sstride,
                int* status) {
   extern __shared__ float smem[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int wpb = blockDim.x >> 5;
-  float* s = smem + (size_t)(wib * 32 + lane) * sstride;
-  for (int task = blockIdx.x * wpb + wib;; task += gridDim.x * wpb) {
+  __shared__ float s_l1[4][32], s_rem[4][32], s_c0[2][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool up = warp < 2;
+  const int half = warp & 1;
+  float* s = smem + (size_t)((up ? 0 : 32) + lane) * sstride;
+  for (int task = blockIdx.x;; task += gridDim.x) {
     int D = -1, chunk = task;
     for (int d = 0; d <= row_dmax; ++d) {
       const int nc = (S.qcount[d] + 31) >> 5;
@@ -301,8 +297,51 @@ k_compose_rows(Tables T, ComposeArgs A, ComposeScratch S, int row_dmax, int sstr
     const bool valid = idx < S.qcount[D];
     const int64_t item = valid ? S.queue[(int64_t)D * S.qcap + idx] : 0;
     const RowTable R = T.row[D];
-    rows_pass<true>(T, A, R, D, item, valid, s, status);
-    rows_pass<false>(T, A, R, D, item, valid, s, status);
+    const float Lo = valid ? A.lo[item] : -1.0f;
+    const float Hi = valid ? A.hi[item] : 1.0f;
+    const float inv = 1.0f / (Hi - Lo);
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+    if (valid) {
+      const float* cf = A.coef + item * kCoefStride;
+      a0 = cf[0];
+      a1 = cf[1];
+      a2 = cf[2];
+      if (a2 < 0.0f) atomicOr(status, kStatusUnsupported);   // excluded by convexity
+    }
+    const int Mpre = valid ? A.pre_nterms[item] : 0;
+    const float* P = (up ? A.pre_up : A.pre_lo) + A.base(valid ? item : 0, A.pre_ld);
+    s_l1[warp][lane] = load_rows(A, R, P, Mpre, Lo, inv, half, s);
+    __syncthreads();
+    const int row_b = half ? R.row_split : 0;
+    const int row_e = half ? R.n_out_rows : R.row_split;
+    float* Q = (up ? A.post_up : A.post_lo) + A.base(valid ? item : 0, A.post_ld);
+    float c0 = 0.0f, rem = 0.0f;
+    if (up)
+      rows_range<true>(T, A, R, D, row_b, row_e, valid, a1, a2, s, Q, &c0, &rem);
+    else
+      rows_range<false>(T, A, R, D, row_b, row_e, valid, a1, a2, s, Q, &c0, &rem);
+    s_rem[warp][lane] = rem;
+    if (!half) s_c0[up ? 0 : 1][lane] = c0;
+    __syncthreads();
+    if (!half && valid) {
+      // constant term: a0 + (the row-0 value without a0) + Lip*eta + remainder
+      const int w0 = up ? 0 : 2;
+      const float l1 = __fadd_ru(s_l1[w0][lane], s_l1[w0 + 1][lane]);
+      const float eta = __fmul_ru(5.0f * kU, l1);
+      const float lip = __fmaf_ru(2.0f * a2, __fadd_ru(1.0f, eta), fabsf(a1));
+      float v;
+      if (up) {
+        const float remt = __fadd_ru(s_rem[0][lane], s_rem[1][lane]);
+        v = __fadd_ru(__fadd_ru(__fadd_ru(c0, a0), __fmul_ru(lip, eta)), remt);
+      } else {
+        const float remt = __fadd_rd(s_rem[2][lane], s_rem[3][lane]);
+        v = __fsub_rd(__fadd_rd(c0, a0), __fmul_ru(lip, eta));
+        v = __fadd_rd(__fsub_rd(v, A.eps[item]), remt);
+      }
+      Q[0] = v;
+      if (!isfinite(v)) atomicOr(status, kStatusNonFinite);
+    }
+    __syncthreads();   // the next task reuses the shared inputs
   }
 }
 
@@ -504,20 +543,19 @@ cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratc
   k_compose_queue<<<(unsigned)((n_items + 1023) / 1024), 1024, 0, L.stream>>>(
       T, A, n_items, row_dmax, S, L.status);
   ++*L.launches;
-  // row-convolution kernel: persistent warps; the per-lane stride is odd so
-  // that lanes reading the same offset hit distinct banks
+  // row-convolution kernel: persistent blocks of 4 warps per 32 items; the
+  // per-lane stride is odd so that lanes reading the same offset hit
+  // distinct banks
   const int sstride = (int)num_monomials(T.n, row_dmax) | 1;
-  const int wpb = (int)std::max<int64_t>(
-      1, std::min<int64_t>(8, (96 * 1024) / (32 * 4 * (int64_t)sstride)));
-  const size_t smem = (size_t)wpb * 32 * sstride * sizeof(float);
+  const size_t smem = (size_t)2 * 32 * sstride * sizeof(float);
   if (smem > 48 * 1024) {
     e = cudaFuncSetAttribute(k_compose_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
   }
   const int64_t tasks = n_items / 32 + row_dmax + 1;
-  const int blocks = (int)std::min<int64_t>((tasks + wpb - 1) / wpb, 152 * 8);
-  k_compose_rows<<<blocks, 32 * wpb, smem, L.stream>>>(T, A, S, row_dmax, sstride, L.status);
+  const int blocks = (int)std::min<int64_t>(tasks, 152 * 8);
+  k_compose_rows<<<blocks, 128, smem, L.stream>>>(T, A, S, row_dmax, sstride, L.status);
   ++*L.launches;
   k_compose_copy<<<(unsigned)std::min<int64_t>((n_items * pre_ld + 255) / 256, 152 * 16), 256, 0,
                    L.stream>>>(A, S);

@@ -103,6 +103,16 @@ static cudaError_t launch_enclose_impl(const Launch& L, const Tables& T, int64_t
   int G;
   const int lb = effective_order(T.n, order, budget, &G);
   if (lb > T.rscale_max || T.rscale[lb] == nullptr) return cudaErrorInvalidValue;
+  if (G <= kSmallGrid && lb <= 7) {
+#define BERN_SMALL_CASE(X) \
+  case X: return launch_small<X>(L, T, G, n_items, h, pre_up, pre_lo, ld, nterms, lo, hi, ro);
+    switch (lb) {
+      BERN_SMALL_CASE(0) BERN_SMALL_CASE(1) BERN_SMALL_CASE(2) BERN_SMALL_CASE(3)
+      BERN_SMALL_CASE(4) BERN_SMALL_CASE(5) BERN_SMALL_CASE(6) BERN_SMALL_CASE(7)
+      default: break;
+    }
+#undef BERN_SMALL_CASE
+  }
 #define BERN_ENC_CASE(X) \
   case X: return launch_lb<X>(L, T, G, n_items, h, pre_up, pre_lo, ld, nterms, lo, hi, ro);
   switch (lb) {

@@ -101,13 +101,14 @@ int upload_tables(DeviceSlot& s, int n, int dmax, int deg_exps, cudaStream_t str
     if (img.size() > kNoAllocTableBytes) return BERN_E_UNSUPPORTED;
   }
   const int row_dmax = std::min(bern::kMaxRowDegree, bern::row_path_max_degree(n));
-  struct RowOff { size_t pos_in, hdr, in_off, pairs, out_ranks; int m_in, n_out_rows; };
+  struct RowOff { size_t pos_in, hdr, in_off, pairs, out_ranks; int m_in, n_out_rows, row_split; };
   std::vector<RowOff> roff(row_dmax + 1);
   for (int D = 0; D <= row_dmax; ++D) {
     bern::RowImage ri;
     if (!bern::build_row_table(n, D, ri)) return BERN_E_UNSUPPORTED;
     roff[D].m_in = ri.m_in;
     roff[D].n_out_rows = ri.n_out_rows;
+    roff[D].row_split = ri.row_split;
     roff[D].pos_in = put(ri.pos_in.data(), ri.pos_in.size() * sizeof(int32_t));
     roff[D].hdr = put(ri.hdr.data(), ri.hdr.size() * sizeof(int32_t));
     roff[D].in_off = put(ri.in_off.data(), ri.in_off.size() * sizeof(int32_t));
@@ -140,6 +141,7 @@ int upload_tables(DeviceSlot& s, int n, int dmax, int deg_exps, cudaStream_t str
     bern::RowTable& rt = v.row[D];
     rt.m_in = roff[D].m_in;
     rt.n_out_rows = roff[D].n_out_rows;
+    rt.row_split = roff[D].row_split;
     rt.pos_in = (const int32_t*)(s.tables + roff[D].pos_in);
     rt.hdr = (const int4*)(s.tables + roff[D].hdr);
     rt.in_off = (const int32_t*)(s.tables + roff[D].in_off);

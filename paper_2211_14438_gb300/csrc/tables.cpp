@@ -141,25 +141,52 @@ bool build_row_table(int n, int D, RowImage& out) {
     const int sP = n == 1 ? 0 : psum(P);
     const int Lout = 2 * D - sP + 1;
     out.hdr.push_back((int32_t)(out.pairs.size() / 4));
-    for (int code : bucket[P]) {
-      const int i = code / np_in, j = code % np_in;
-      int oi = off[i], oj = off[j], li = len[i], lj = len[j];
-      if (li > lj) {
-        std::swap(oi, oj);
-        std::swap(li, lj);
+    // off-diagonal pairs first, then the diagonal pair (p == q) if P = 2p
+    int has_diag = 0;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int code : bucket[P]) {
+        const int i = code / np_in, j = code % np_in;
+        if ((i == j) != (pass == 1)) continue;
+        has_diag |= (i == j);
+        int oi = off[i], oj = off[j], li = len[i], lj = len[j];
+        if (li > lj) {
+          std::swap(oi, oj);
+          std::swap(li, lj);
+        }
+        out.pairs.push_back(oi);
+        out.pairs.push_back(oj);
+        out.pairs.push_back((li << 4) | lj);
+        out.pairs.push_back(i == j ? 1 : 0);
       }
-      out.pairs.push_back(oi);
-      out.pairs.push_back(oj);
-      out.pairs.push_back((li << 4) | lj);
-      out.pairs.push_back(i == j ? 1 : 0);
-    }
     out.hdr.push_back((int32_t)(out.pairs.size() / 4));
     out.hdr.push_back((int32_t)out.out_ranks.size());
     const int in_len = sP <= D ? D - sP + 1 : 0;
-    out.hdr.push_back(Lout | (in_len << 8));
+    out.hdr.push_back(Lout | (in_len << 8) | (has_diag << 16));
     out.in_off.push_back(sP <= D ? off[P] : -1);
     for (int c = 0; c < Lout; ++c) out.out_ranks.push_back(full_rank(P, c));
   }
+  // split the output rows into two ranges of about equal work (products of
+  // row lengths plus a cost per output element)
+  std::vector<int64_t> work(np, 0);
+  for (int P = 0; P < np; ++P) {
+    for (int k = out.hdr[4 * P]; k < out.hdr[4 * P + 1]; ++k) {
+      const int code = out.pairs[4 * k + 2];
+      work[P] += (int64_t)(code >> 4) * (code & 15) + 6;
+    }
+    work[P] += 8 * (out.hdr[4 * P + 3] & 0xff);
+  }
+  int64_t total = 0;
+  for (int64_t w : work) total += w;
+  int64_t run = 0;
+  out.row_split = np;
+  for (int P = 0; P < np; ++P) {
+    if (2 * run >= total) {
+      out.row_split = P;
+      break;
+    }
+    run += work[P];
+  }
+  if (out.row_split == 0) out.row_split = std::min(1, np);
   return true;
 }
 
