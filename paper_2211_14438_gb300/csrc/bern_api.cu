@@ -129,6 +129,15 @@ int ensure_tables(bern_ctx* c, int n, int dmax, const Tables** out) {
   ts.view.exps = (const uint8_t*)ts.exps.p;
   ts.view.mcount = (const int32_t*)ts.mcount.p;
   ts.view.mexps = num_monomials(n, De);
+  {
+    std::vector<uint8_t> dof;
+    build_degree_of(n, De, dof);
+    DevBuf b;
+    if ((e = b.reserve(dof.size())) != cudaSuccess) return map_cuda(e);
+    cudaMemcpy(b.p, dof.data(), dof.size(), cudaMemcpyHostToDevice);
+    ts.view.deg_of = (const uint8_t*)b.p;
+    ts.bufs.push_back(b);
+  }
   ts.view.rscale_max = max_enclose_order(n);
   for (int l = 0; l <= ts.view.rscale_max; ++l) {
     std::vector<float> rs;

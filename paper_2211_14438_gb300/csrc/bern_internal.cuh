@@ -80,6 +80,7 @@ struct Tables {
   int dmax;                        // degrees 0..dmax have square tables
   const uint8_t* exps;             // graded exponents, mexps ranks
   int64_t mexps;
+  const uint8_t* deg_of;           // deg_of[c] = smallest D with M(n,D) >= c, c <= mexps
   const int32_t* mcount;           // M(n, D) for D = 0..64
   PairTable sq[kMaxTableDegree + 1];
   // rscale[l][r]: float bracket (lo, hi) of 1 / prod_k C(l, e_k(r)) for the
@@ -93,6 +94,8 @@ struct Tables {
 
 // Largest Bernstein order whose grid fits the shared-memory limit for n vars.
 int max_enclose_order(int n);
+// deg_of[c] for c = 0..M(n,De): the smallest D with M(n,D) >= c.
+void build_degree_of(int n, int De, std::vector<uint8_t>& out);
 // Host image of the reciprocal brackets for order l: 2*M(n,l) floats.
 void build_rscale(int n, int l, std::vector<float>& out);
 

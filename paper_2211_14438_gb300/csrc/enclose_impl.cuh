@@ -116,23 +116,64 @@ __device__ __forceinline__ void line_transform(const float (&x)[LB + 1], float (
   }
 }
 
+// Mixed-radix strides of the grid: pw[k] = R^(n-1-k) (loops over the 8
+// variable slots are unrolled so the array stays in registers).
+template <int R>
+__device__ __forceinline__ void grid_strides(int n, int (&pw)[kMaxVars]) {
+  int p = 1;
+#pragma unroll
+  for (int k = kMaxVars - 1; k >= 0; --k) {
+    pw[k] = k < n ? p : 0;
+    if (k < n) p *= R;
+  }
+}
+
+// Line Ln along variable k: its base offset and the digit sum of the
+// untransformed prefix (variables < k).
+template <int R>
+__device__ __forceinline__ void line_base(int Ln, int k, int n, const int (&pw)[kMaxVars],
+                                          int* base, int* psum) {
+  int rest = Ln, b = 0, ps = 0;
+#pragma unroll
+  for (int m = kMaxVars - 1; m >= 0; --m) {
+    if (m >= n || m == k) continue;
+    const int dgt = rest % R;
+    rest /= R;
+    b += dgt * pw[m];
+    if (m < k) ps += dgt;
+  }
+  *base = b;
+  *psum = ps;
+}
+
+// Grid index and total degree of graded rank r.
+__device__ __forceinline__ void term_index(const uint8_t* __restrict__ e, int n,
+                                           const int (&pw)[kMaxVars], int* idx, int* deg) {
+  int d = 0, ix = 0;
+#pragma unroll
+  for (int k = 0; k < kMaxVars; ++k) {
+    if (k < n) {
+      d += e[k];
+      ix += e[k] * pw[k];
+    }
+  }
+  *idx = ix;
+  *deg = d;
+}
+
 // Scatter the scaled coefficients of degree <= Deff into the grid; return
 // the directed sum of the one-sided ranges of all other terms.
 template <bool UP>
 __device__ float scatter_terms(const float* __restrict__ P, int ps, int nt, int n,
-                               const int* pw, const Tables& T, const float2* __restrict__ rs,
-                               int Deff, float* grid) {
+                               const int (&pw)[kMaxVars], const Tables& T,
+                               const float2* __restrict__ rs, int Deff, float* grid) {
   const int lane = threadIdx.x & 31;
   float rem = 0.0f;
   const int m_eff = T.mcount[Deff];
   for (int r = lane; r < nt; r += 32) {
     const float a = P[(int64_t)r * ps];
-    const uint8_t* e = T.exps + (int64_t)r * n;
-    int deg = 0, idx = 0;
-    for (int k = 0; k < n; ++k) {
-      deg += e[k];
-      idx += e[k] * pw[k];
-    }
+    int deg, idx;
+    term_index(T.exps + (int64_t)r * n, n, pw, &idx, &deg);
     if (deg <= Deff) {
       const float2 sc = rs[r];
       // a / C bracketed: choose the end that rounds the product the right way
@@ -145,12 +186,16 @@ __device__ float scatter_terms(const float* __restrict__ P, int ps, int nt, int 
   }
   // a ragged count (not a full graded prefix): missing simplex entries are 0
   for (int r = nt + lane; r < m_eff; r += 32) {
-    const uint8_t* e = T.exps + (int64_t)r * n;
-    int idx = 0;
-    for (int k = 0; k < n; ++k) idx += e[k] * pw[k];
+    int deg, idx;
+    term_index(T.exps + (int64_t)r * n, n, pw, &idx, &deg);
     grid[idx] = 0.0f;
   }
   return rem;
+}
+
+// Total degree of a graded prefix of nt terms (the smallest D with M(n,D) >= nt).
+__device__ __forceinline__ int prefix_degree(const Tables& T, int nt) {
+  return nt <= T.mexps ? (int)T.deg_of[nt] : kMaxTableDegree;
 }
 
 template <int LB, bool UP>
@@ -159,16 +204,8 @@ __device__ float enclose_warp(const float* __restrict__ P, int ps, int nt, int n
   const int lane = threadIdx.x & 31;
   constexpr int R = LB + 1;
   int pw[kMaxVars];
-  {
-    int p = 1;
-    for (int k = n - 1; k >= 0; --k) {
-      pw[k] = p;
-      p *= R;
-    }
-  }
-  // degree actually present (the smallest graded prefix holding nt), capped at LB
-  int Dnt = 0;
-  while (Dnt < kMaxTableDegree && T.mcount[Dnt] < nt) ++Dnt;
+  grid_strides<R>(n, pw);
+  const int Dnt = prefix_degree(T, nt);
   const int Deff = Dnt < LB ? Dnt : LB;
   float rem = scatter_terms<UP>(P, ps, nt, n, pw, T, rs, Deff, grid);
   __syncwarp();
@@ -178,16 +215,13 @@ __device__ float enclose_warp(const float* __restrict__ P, int ps, int nt, int n
   for (int k = n - 1; k >= 0; --k) {
     // lines along variable k: prefix digits (variables < k) untransformed,
     // suffix digits (variables > k) transformed
-    const int sk = pw[k];
+    int sk = 1;
+#pragma unroll
+    for (int m = 0; m < kMaxVars; ++m)
+      if (m == k) sk = pw[m];
     for (int Ln = lane; Ln < nlines; Ln += 32) {
-      int rest = Ln, base = 0, psum = 0;
-      for (int m = n - 1; m >= 0; --m) {
-        if (m == k) continue;
-        const int dgt = rest % R;
-        rest /= R;
-        base += dgt * pw[m];
-        if (m < k) psum += dgt;
-      }
+      int base, psum;
+      line_base<R>(Ln, k, n, pw, &base, &psum);
       if (psum > Deff) continue;
       const int p = Deff - psum;
       float x[R], y[R];
@@ -288,25 +322,14 @@ __device__ float enclose_lane(const float* __restrict__ P, int ps, int nt, int n
                               const Tables& T, const float2* __restrict__ rs, float* grid) {
   constexpr int R = LB + 1;
   int pw[kMaxVars];
-  {
-    int p = 1;
-    for (int k = n - 1; k >= 0; --k) {
-      pw[k] = p;
-      p *= R;
-    }
-  }
-  int Dnt = 0;
-  while (Dnt < kMaxTableDegree && T.mcount[Dnt] < nt) ++Dnt;
+  grid_strides<R>(n, pw);
+  const int Dnt = prefix_degree(T, nt);
   const int Deff = Dnt < LB ? Dnt : LB;
   float rem = 0.0f;
   for (int r = 0; r < nt; ++r) {
     const float a = P[(int64_t)r * ps];
-    const uint8_t* e = T.exps + (int64_t)r * n;
-    int deg = 0, idx = 0;
-    for (int k = 0; k < n; ++k) {
-      deg += e[k];
-      idx += e[k] * pw[k];
-    }
+    int deg, idx;
+    term_index(T.exps + (int64_t)r * n, n, pw, &idx, &deg);
     if (deg <= Deff) {
       const float2 sc = rs[r];
       grid[idx * 32] = UP ? __fmul_ru(a, a >= 0.0f ? sc.y : sc.x)
@@ -316,25 +339,21 @@ __device__ float enclose_lane(const float* __restrict__ P, int ps, int nt, int n
     }
   }
   for (int r = nt; r < T.mcount[Deff]; ++r) {
-    const uint8_t* e = T.exps + (int64_t)r * n;
-    int idx = 0;
-    for (int k = 0; k < n; ++k) idx += e[k] * pw[k];
+    int deg, idx;
+    term_index(T.exps + (int64_t)r * n, n, pw, &idx, &deg);
     grid[idx * 32] = 0.0f;
   }
   float best = UP ? -CUDART_INF_F : CUDART_INF_F;
   int nlines = 1;
   for (int m = 0; m < n - 1; ++m) nlines *= R;
   for (int k = n - 1; k >= 0; --k) {
-    const int sk = pw[k];
+    int sk = 1;
+#pragma unroll
+    for (int m = 0; m < kMaxVars; ++m)
+      if (m == k) sk = pw[m];
     for (int Ln = 0; Ln < nlines; ++Ln) {
-      int rest = Ln, base = 0, psum = 0;
-      for (int m = n - 1; m >= 0; --m) {
-        if (m == k) continue;
-        const int dgt = rest % R;
-        rest /= R;
-        base += dgt * pw[m];
-        if (m < k) psum += dgt;
-      }
+      int base, psum;
+      line_base<R>(Ln, k, n, pw, &base, &psum);
       if (psum > Deff) continue;
       const int p = Deff - psum;
       float x[R], y[R];
@@ -424,13 +443,13 @@ __device__ float enclose_warp_generic(const float* __restrict__ P, int ps, int n
   int pw[kMaxVars];
   {
     int p = 1;
-    for (int k = n - 1; k >= 0; --k) {
-      pw[k] = p;
-      p *= R;
+#pragma unroll
+    for (int k = kMaxVars - 1; k >= 0; --k) {
+      pw[k] = k < n ? p : 0;
+      if (k < n) p *= R;
     }
   }
-  int Dnt = 0;
-  while (Dnt < kMaxTableDegree && T.mcount[Dnt] < nt) ++Dnt;
+  const int Dnt = prefix_degree(T, nt);
   const int Deff = Dnt < lb ? Dnt : lb;
   float rem = scatter_terms<UP>(P, ps, nt, n, pw, T, rs, Deff, grid);
   __syncwarp();
@@ -438,11 +457,15 @@ __device__ float enclose_warp_generic(const float* __restrict__ P, int ps, int n
   int nlines = 1;
   for (int m = 0; m < n - 1; ++m) nlines *= R;
   for (int k = n - 1; k >= 0; --k) {
-    const int sk = pw[k];
+    int sk = 1;
+#pragma unroll
+    for (int m = 0; m < kMaxVars; ++m)
+      if (m == k) sk = pw[m];
     for (int Ln = lane; Ln < nlines; Ln += 32) {
       int rest = Ln, base = 0, psum = 0;
-      for (int m = n - 1; m >= 0; --m) {
-        if (m == k) continue;
+#pragma unroll
+      for (int m = kMaxVars - 1; m >= 0; --m) {
+        if (m >= n || m == k) continue;
         const int dgt = rest % R;
         rest /= R;
         base += dgt * pw[m];

@@ -92,6 +92,9 @@ int upload_tables(DeviceSlot& s, int n, int dmax, int deg_exps, cudaStream_t str
   std::vector<uint8_t> ex;
   bern::graded_monomials(n, deg_exps, ex);
   size_t off_ex = put(ex.data(), ex.size());
+  std::vector<uint8_t> dof;
+  bern::build_degree_of(n, deg_exps, dof);
+  size_t off_dof = put(dof.data(), dof.size());
   const int rmax = bern::max_enclose_order(n);
   std::vector<size_t> off_rs(rmax + 1);
   for (int l = 0; l <= rmax; ++l) {
@@ -136,6 +139,7 @@ int upload_tables(DeviceSlot& s, int n, int dmax, int deg_exps, cudaStream_t str
   v.mcount = (const int32_t*)(s.tables + off_mc);
   v.exps = (const uint8_t*)(s.tables + off_ex);
   v.mexps = bern::num_monomials(n, deg_exps);
+  v.deg_of = (const uint8_t*)(s.tables + off_dof);
   v.row_dmax = row_dmax;
   for (int D = 0; D <= row_dmax; ++D) {
     bern::RowTable& rt = v.row[D];

@@ -199,6 +199,16 @@ int row_path_max_degree(int n) {
   return D;
 }
 
+void build_degree_of(int n, int De, std::vector<uint8_t>& out) {
+  const int64_t m = num_monomials(n, De);
+  out.assign((size_t)m + 1, 0);
+  int D = 0;
+  for (int64_t c = 0; c <= m; ++c) {
+    while (num_monomials(n, D) < c) ++D;
+    out[(size_t)c] = (uint8_t)D;
+  }
+}
+
 int max_enclose_order(int n) {
   int l = kMaxEncloseOrder;
   for (; l > 0; --l) {
