@@ -210,13 +210,13 @@ __device__ float load_rows(const ComposeArgs& A, const RowTable& R, const float*
 // a1*s + a2*s^2 of the row's monomials (the constant term only in c0).
 template <bool UP>
 __device__ void rows_range(const Tables& T, const ComposeArgs& A, const RowTable& R, int D,
-                           int row_b, int row_e, bool valid, float a1, float a2,
+                           int row_b, int row_e, int row_step, bool valid, float a1, float a2,
                            const float* s, float* Q, float* c0_out, float* rem_out) {
   const int h = A.h;
   const int Mout = T.mcount[min(2 * D, A.cap)];
   const bool no_trunc = 2 * D <= A.cap;   // every output monomial is kept
   float rem = 0.0f;
-  for (int row = row_b; row < row_e; ++row) {
+  for (int row = row_b; row < row_e; row += row_step) {
     const int4 hd = __ldg(R.hdr + row);
     const int Lout = hd.w & 0xff, in_len = (hd.w >> 8) & 0xff;
     const int in_off = __ldg(R.in_off + row);
@@ -253,8 +253,8 @@ __device__ void rows_range(const Tables& T, const ComposeArgs& A, const RowTable
 #pragma unroll
     for (int c = 0; c < 2 * kRowLen - 1; ++c) {
       if (c >= Lout) break;
-      // (s^2) = diagonal part + 2 * off-diagonal part; 2*x is exact
-      const float sq = dadd<UP>(accd[c], 2.0f * acc[c]);
+      // (s^2) = diagonal part + 2 * off-diagonal part (2*x is exact)
+      const float sq = dfma<UP>(2.0f, acc[c], accd[c]);
       const float lin = c < in_len ? s[in_off + c] : 0.0f;
       const float v = dfma<UP>(a2, sq, UP ? __fmul_ru(a1, lin) : __fmul_rd(a1, lin));
       if (row == 0 && c == 0) {
@@ -269,19 +269,17 @@ __device__ void rows_range(const Tables& T, const ComposeArgs& A, const RowTable
   *rem_out = rem;
 }
 
-// A block of four warps squares 32 queued items (one lane per item): warps
-// 0-1 compute the upper polynomials, warps 2-3 the lower ones, each pair
-// splitting the output rows in two ranges of about equal work.  The two
-// bounds' inputs of the 32 items sit in shared memory once.
-__global__ void __launch_bounds__(128, 4)
+// A block of two warps squares one bound (UP: upper) of 32 queued items (one
+// lane per item); the two warps share the items' inputs in shared memory and
+// take alternate output rows.
+template <bool UP>
+__global__ void __launch_bounds__(64, 10)
 k_compose_rows(Tables T, ComposeArgs A, ComposeScratch S, int row_dmax, int sstride,
                int* status) {
   extern __shared__ float smem[];
-  __shared__ float s_l1[4][32], s_rem[4][32], s_c0[2][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool up = warp < 2;
-  const int half = warp & 1;
-  float* s = smem + (size_t)((up ? 0 : 32) + lane) * sstride;
+  __shared__ float s_l1[2][32], s_rem[2][32], s_c0[32];
+  const int lane = threadIdx.x & 31, half = threadIdx.x >> 5;
+  float* s = smem + (size_t)lane * sstride;
   for (int task = blockIdx.x;; task += gridDim.x) {
     int D = -1, chunk = task;
     for (int d = 0; d <= row_dmax; ++d) {
@@ -309,33 +307,27 @@ k_compose_rows(Tables T, ComposeArgs A, ComposeScratch S, int row_dmax, int sstr
       if (a2 < 0.0f) atomicOr(status, kStatusUnsupported);   // excluded by convexity
     }
     const int Mpre = valid ? A.pre_nterms[item] : 0;
-    const float* P = (up ? A.pre_up : A.pre_lo) + A.base(valid ? item : 0, A.pre_ld);
-    s_l1[warp][lane] = load_rows(A, R, P, Mpre, Lo, inv, half, s);
+    const float* P = (UP ? A.pre_up : A.pre_lo) + A.base(valid ? item : 0, A.pre_ld);
+    s_l1[half][lane] = load_rows(A, R, P, Mpre, Lo, inv, half, s);
     __syncthreads();
-    const int row_b = half ? R.row_split : 0;
-    const int row_e = half ? R.n_out_rows : R.row_split;
-    float* Q = (up ? A.post_up : A.post_lo) + A.base(valid ? item : 0, A.post_ld);
+    float* Q = (UP ? A.post_up : A.post_lo) + A.base(valid ? item : 0, A.post_ld);
     float c0 = 0.0f, rem = 0.0f;
-    if (up)
-      rows_range<true>(T, A, R, D, row_b, row_e, valid, a1, a2, s, Q, &c0, &rem);
-    else
-      rows_range<false>(T, A, R, D, row_b, row_e, valid, a1, a2, s, Q, &c0, &rem);
-    s_rem[warp][lane] = rem;
-    if (!half) s_c0[up ? 0 : 1][lane] = c0;
+    rows_range<UP>(T, A, R, D, half, R.n_out_rows, 2, valid, a1, a2, s, Q, &c0, &rem);
+    s_rem[half][lane] = rem;
+    if (!half) s_c0[lane] = c0;
     __syncthreads();
     if (!half && valid) {
       // constant term: a0 + (the row-0 value without a0) + Lip*eta + remainder
-      const int w0 = up ? 0 : 2;
-      const float l1 = __fadd_ru(s_l1[w0][lane], s_l1[w0 + 1][lane]);
+      const float l1 = __fadd_ru(s_l1[0][lane], s_l1[1][lane]);
       const float eta = __fmul_ru(5.0f * kU, l1);
       const float lip = __fmaf_ru(2.0f * a2, __fadd_ru(1.0f, eta), fabsf(a1));
       float v;
-      if (up) {
+      if (UP) {
         const float remt = __fadd_ru(s_rem[0][lane], s_rem[1][lane]);
-        v = __fadd_ru(__fadd_ru(__fadd_ru(c0, a0), __fmul_ru(lip, eta)), remt);
+        v = __fadd_ru(__fadd_ru(__fadd_ru(s_c0[lane], a0), __fmul_ru(lip, eta)), remt);
       } else {
-        const float remt = __fadd_rd(s_rem[2][lane], s_rem[3][lane]);
-        v = __fsub_rd(__fadd_rd(c0, a0), __fmul_ru(lip, eta));
+        const float remt = __fadd_rd(s_rem[0][lane], s_rem[1][lane]);
+        v = __fsub_rd(__fadd_rd(s_c0[lane], a0), __fmul_ru(lip, eta));
         v = __fadd_rd(__fsub_rd(v, A.eps[item]), remt);
       }
       Q[0] = v;
@@ -543,20 +535,24 @@ cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratc
   k_compose_queue<<<(unsigned)((n_items + 1023) / 1024), 1024, 0, L.stream>>>(
       T, A, n_items, row_dmax, S, L.status);
   ++*L.launches;
-  // row-convolution kernel: persistent blocks of 4 warps per 32 items; the
-  // per-lane stride is odd so that lanes reading the same offset hit
-  // distinct banks
+  // row-convolution kernels (one per bound): persistent blocks of 2 warps
+  // per 32 items; the per-lane stride is odd so that lanes reading the same
+  // offset hit distinct banks
   const int sstride = (int)num_monomials(T.n, row_dmax) | 1;
-  const size_t smem = (size_t)2 * 32 * sstride * sizeof(float);
+  const size_t smem = (size_t)32 * sstride * sizeof(float);
   if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_compose_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_compose_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_compose_rows<false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   const int64_t tasks = n_items / 32 + row_dmax + 1;
-  const int blocks = (int)std::min<int64_t>(tasks, 152 * 8);
-  k_compose_rows<<<blocks, 128, smem, L.stream>>>(T, A, S, row_dmax, sstride, L.status);
-  ++*L.launches;
+  const int blocks = (int)std::min<int64_t>(tasks, 152 * 10);
+  k_compose_rows<true><<<blocks, 64, smem, L.stream>>>(T, A, S, row_dmax, sstride, L.status);
+  k_compose_rows<false><<<blocks, 64, smem, L.stream>>>(T, A, S, row_dmax, sstride, L.status);
+  *L.launches += 2;
   k_compose_copy<<<(unsigned)std::min<int64_t>((n_items * pre_ld + 255) / 256, 152 * 16), 256, 0,
                    L.stream>>>(A, S);
   ++*L.launches;
