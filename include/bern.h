@@ -218,8 +218,18 @@ int bern_relu_coeffs(bern_ctx* ctx, int64_t n_items, const float* lo,
  * enter the constant as a one-sided remainder).  Identity items copy pre to
  * post; zero items get nterms = 0.  Items are the n_boxes*h neurons of the
  * pre block; kind/coef/eps/degrees/lo/hi are per item (b*h + m).  post_ld
- * must hold M(n, min(d * D_pre, degree_cap)) for every item.  prune_tau must
- * be 0 (pruning is not implemented on the GPU; BERN_E_INVALID otherwise). */
+ * must hold M(n, min(d * D_pre, degree_cap)) for every item.
+ *   global_d: the order of every item when degrees is NULL; otherwise an
+ *     upper bound of the entries of degrees (an entry above it sets
+ *     BERN_E_INVALID at bern_sync).
+ *   prune_tau >= 0: with prune_tau > 0, after every Horner product the terms
+ *     of positive degree with |c| < prune_tau * ||q||_1 are dropped into the
+ *     remainder as well, and post_nterms becomes the graded prefix up to the
+ *     highest degree with a kept term.
+ * Orders 1 and 2 use closed forms (c = a0 + a1 s, a0 + a1 s + a2 s^2); orders
+ * >= 3, and every order when prune_tau > 0, use Horner's rule with interval
+ * coefficients.  Shapes whose Horner buffers exceed shared memory return
+ * BERN_E_UNSUPPORTED. */
 int bern_compose(bern_ctx* ctx, int n, int64_t n_boxes, int h, int degree_cap,
                  float prune_tau, const int8_t* kind, const float* coef,
                  const float* eps, const uint8_t* degrees, int global_d,

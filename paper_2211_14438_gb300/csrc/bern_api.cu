@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "bern_internal.cuh"
+#include "compose_common.cuh"
 
 namespace bern {
 int effective_order(int n, int order, int64_t budget, int* grid_out);
@@ -41,6 +42,11 @@ struct TableSet {
   DevBuf exps, mcount;
   std::vector<DevBuf> bufs;
   Tables view{};
+  // product tables of the Horner kernel, built on demand; prod_arr is the
+  // device array of kProdStride^2 entries the kernels index
+  std::map<std::pair<int, int>, std::pair<DevBuf, DevBuf>> prod;
+  std::vector<ProdTable> prod_host;
+  DevBuf prod_arr;
 };
 
 struct GraphEntry {
@@ -187,11 +193,58 @@ int ensure_tables(bern_ctx* c, int n, int dmax, const Tables** out) {
     ts.bufs.push_back(bp);
     ts.bufs.push_back(bq);
   }
+  if (!ts.prod_arr.p) {
+    ts.prod_host.assign((size_t)kProdStride * kProdStride, ProdTable{nullptr, nullptr});
+    if ((e = ts.prod_arr.reserve(ts.prod_host.size() * sizeof(ProdTable))) != cudaSuccess)
+      return map_cuda(e);
+    cudaMemcpy(ts.prod_arr.p, ts.prod_host.data(), ts.prod_host.size() * sizeof(ProdTable),
+               cudaMemcpyHostToDevice);
+  }
+  ts.view.prod = (const ProdTable*)ts.prod_arr.p;
   ts.dmax = dmax;
   ts.view.dmax = dmax;
   e = cudaGetLastError();
   if (e != cudaSuccess) return map_cuda(e);
   *out = &ts.view;
+  return BERN_OK;
+}
+
+// Product tables for Horner items of input degree <= Dmax and order <= dmax
+// under degree cap `cap`: (min(cap, k*D), D) for D <= Dmax, k < dmax.
+int ensure_prod_tables(bern_ctx* c, int n, int Dmax, int dmax, int cap) {
+  const Tables* T;
+  int rc = ensure_tables(c, n, 0, &T);
+  if (rc) return rc;
+  TableSet& ts = c->tables[n];
+  bool changed = false;
+  for (int D = 0; D <= Dmax; ++D)
+    for (int k = 0; k < std::max(1, dmax); ++k) {
+      const int Dq = std::min(cap, k * D);
+      if (Dq + D > kMaxTableDegree) return BERN_E_UNSUPPORTED;
+      const auto key = std::make_pair(Dq, D);
+      if (ts.prod.count(key)) continue;
+      std::vector<int32_t> ptr, pairs;
+      if (!build_product_table(n, Dq, D, (int64_t)1 << 24, ptr, pairs)) return BERN_E_UNSUPPORTED;
+      DevBuf bp, bq;
+      cudaError_t e = bp.reserve(ptr.size() * sizeof(int32_t));
+      if (e == cudaSuccess) e = bq.reserve(std::max<size_t>(8, pairs.size() * sizeof(int32_t)));
+      if (e != cudaSuccess) {
+        bp.release();
+        bq.release();
+        return map_cuda(e);
+      }
+      cudaMemcpy(bp.p, ptr.data(), ptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+      if (!pairs.empty())
+        cudaMemcpy(bq.p, pairs.data(), pairs.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+      ts.prod[key] = std::make_pair(bp, bq);
+      ts.prod_host[(size_t)Dq * kProdStride + D] = ProdTable{(const int32_t*)bp.p, (const int2*)bq.p};
+      changed = true;
+    }
+  if (changed) {
+    cudaError_t e = cudaMemcpy(ts.prod_arr.p, ts.prod_host.data(),
+                               ts.prod_host.size() * sizeof(ProdTable), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return map_cuda(e);
+  }
   return BERN_OK;
 }
 
@@ -476,6 +529,11 @@ int bern_destroy(bern_ctx* c) {
     kv.second.exps.release();
     kv.second.mcount.release();
     for (auto& b : kv.second.bufs) b.release();
+    for (auto& p : kv.second.prod) {
+      p.second.first.release();
+      p.second.second.release();
+    }
+    kv.second.prod_arr.release();
   }
   c->ws.release();
   c->qbuf.release();
@@ -574,7 +632,8 @@ int bern_compose(bern_ctx* c, int n, int64_t n_boxes, int h, int degree_cap, flo
                  const int32_t* pre_nterms, float* post_up, float* post_lo, int64_t post_ld,
                  int32_t* post_nterms) {
   if (!c || n < 1 || n > kMaxVars || n_boxes < 0 || h < 1 || pre_ld < 1 || post_ld < 1 ||
-      degree_cap < 1 || degree_cap > kMaxTableDegree || prune_tau != 0.0f)
+      degree_cap < 1 || degree_cap > kMaxTableDegree || !(prune_tau >= 0.0f) ||
+      global_d < 1 || global_d > kMaxOrder)
     return BERN_E_INVALID;
   cudaSetDevice(c->device);
   int Dmax = 0;
@@ -582,6 +641,12 @@ int bern_compose(bern_ctx* c, int n, int64_t n_boxes, int h, int degree_cap, flo
   const Tables* T;
   int rc = ensure_tables(c, n, std::min(Dmax, 32), &T);
   if (rc) return rc;
+  if (global_d >= 3 || prune_tau > 0.0f) {
+    if ((rc = ensure_prod_tables(c, n, Dmax, global_d, degree_cap))) return rc;
+    const int Dout = std::min(degree_cap, global_d * Dmax);
+    if (horner_smem_floats(*T, Dmax, Dout) * sizeof(float) > 200 * 1024)
+      return BERN_E_UNSUPPORTED;
+  }
   ComposeScratch CS;
   if ((rc = ensure_queues(c, std::max<int64_t>(1, n_boxes * h), &CS))) return rc;
   return map_cuda(launch_compose(c->launch(), *T, CS, n_boxes, h, degree_cap, prune_tau, kind,
@@ -607,6 +672,12 @@ int bern_propagate(bern_ctx* c, const bern_net* net, const float* boxes, int64_t
   if (rc) return rc;
   for (const auto& l : P.L)
     if (l.M_pre > T->mexps || l.M_post > T->mexps) return BERN_E_UNSUPPORTED;
+  for (const auto& l : P.L) {
+    if (!l.hidden || (l.d < 3 && P.tau == 0.0f)) continue;
+    if ((rc = ensure_prod_tables(c, P.n, l.D_pre, l.d, P.cap))) return rc;
+    if (horner_smem_floats(*T, l.D_pre, l.D_post) * sizeof(float) > 200 * 1024)
+      return BERN_E_UNSUPPORTED;
+  }
 
   const bool host = c->mem_mode == BERN_MEM_HOST;
   cudaError_t e;

@@ -41,6 +41,12 @@ bool build_square_pairs(int n, int D, PairList& out);
 // pairs (I in q, J in s), packed I | (J << 16)
 bool build_product_pairs(int n, int Dq, int Ds, PairList& out);
 
+// Product table of a degree-Dq polynomial q by a degree-Ds polynomial s, for
+// the Horner kernel: for every output rank K < M(n, Dq + Ds), the pairs
+// (I, J), I + J = K, stored as two int32 (I then J) from pairs[2*ptr[K]].
+bool build_product_table(int n, int Dq, int Ds, int64_t max_pairs, std::vector<int32_t>& ptr,
+                         std::vector<int32_t>& pairs);
+
 // Row decomposition for the squaring kernel.  A "row" is the set of
 // monomials sharing the exponents of t_1..t_{n-1} (its prefix) and varying
 // the exponent c of t_n.  The square of a degree-D polynomial is, per output
@@ -75,6 +81,12 @@ struct PairTable {
   const uint32_t* pairs;
 };
 
+struct ProdTable {
+  const int32_t* ptr;              // null: not built
+  const int2* pairs;
+};
+constexpr int kProdStride = kMaxTableDegree + 1;   // prod[Dq * kProdStride + Ds]
+
 struct Tables {
   int n;
   int dmax;                        // degrees 0..dmax have square tables
@@ -90,6 +102,8 @@ struct Tables {
   // row tables for squaring, input degrees 0..row_dmax (row_dmax <= 8)
   RowTable row[kMaxRowDegree + 1];
   int row_dmax;
+  // product tables of the Horner kernel (device array of kProdStride^2)
+  const ProdTable* prod;
 };
 
 // Largest Bernstein order whose grid fits the shared-memory limit for n vars.
@@ -132,7 +146,7 @@ cudaError_t launch_pack(const Launch& L, const Tables& T, int64_t n_boxes, int o
 
 // Work queues of the composition step: kComposeQueues lists of item
 // indices, each of capacity qcap, and their counters.
-constexpr int kComposeQueues = kMaxRowDegree + 4;
+constexpr int kComposeQueues = kMaxRowDegree + 5;
 struct ComposeScratch {
   int* qcount;       // kComposeQueues counters (zeroed by the launcher)
   int* queue;        // kComposeQueues * qcap item indices

@@ -24,47 +24,9 @@
 // equal structure per warp), the rest to a per-item pair-list kernel.
 #include <algorithm>
 
-#include "device_util.cuh"
+#include "compose_common.cuh"
 
 namespace bern {
-
-constexpr float kU = 0x1p-24f;   // unit roundoff of float32
-constexpr int kQIdent = kMaxRowDegree + 1;   // identity copies
-constexpr int kQLinear = kMaxRowDegree + 2;  // order-1 items
-constexpr int kQPairs = kMaxRowDegree + 3;   // order-2 items outside the row path
-static_assert(kQPairs + 1 == kComposeQueues, "queue ids");
-
-struct ComposeArgs {
-  int cap;
-  int h;                     // neurons per box; item = b*h + m
-  const int8_t* kind;
-  const float* coef;
-  const float* eps;
-  const uint8_t* degrees;
-  int global_d;
-  const float* lo;
-  const float* hi;
-  const float* pre_up;
-  const float* pre_lo;
-  int64_t pre_ld;
-  const int32_t* pre_nterms;
-  float* post_up;
-  float* post_lo;
-  int64_t post_ld;
-  int32_t* post_nterms;
-  // offset of coefficient 0 of an item in a block with leading dimension ld;
-  // coefficient r is at offset + r*h
-  __device__ __forceinline__ int64_t base(int64_t item, int64_t ld) const {
-    const int64_t b = item / h;
-    return (b * ld) * h + (item - b * h);
-  }
-};
-
-__device__ __forceinline__ int degree_of(const Tables& T, int m) {
-  int D = 0;
-  while (D < kMaxTableDegree && T.mcount[D] < m) ++D;
-  return D;
-}
 
 // ------------------------------------------------------------ classification
 // Each block classifies 1024 consecutive items and appends them to the
@@ -96,20 +58,22 @@ k_compose_queue(Tables T, ComposeArgs A, int64_t n_items, int row_dmax, ComposeS
     } else if (k == 2) {
       const int d = A.degrees ? (int)A.degrees[item] : A.global_d;
       const int D = degree_of(T, Mpre);
-      const int Dfull = d * D;
-      if (T.mcount[D] > A.pre_ld || d < 1 || Dfull > kMaxTableDegree) {
+      if (T.mcount[D] > A.pre_ld || d < 1 || d > kMaxOrder || (A.degrees && d > A.global_d)) {
         atomicOr(status, kStatusInvalid);
       } else {
-        const int Mout = T.mcount[min(Dfull, A.cap)];
+        const int Mout = T.mcount[min(d * D, A.cap)];
         if (Mout > A.post_ld) {
           atomicOr(status, kStatusCapacity);
+        } else if (A.tau > 0.0f || d >= 3) {
+          q = kQHorner;
+          nt = A.tau > 0.0f ? 0 : Mout;   // with pruning the Horner kernel sets it
         } else if (d == 1) {
           q = kQLinear;
           nt = Mout;
-        } else if (d == 2 && D <= row_dmax) {
+        } else if (D <= row_dmax) {
           q = D;
           nt = Mout;
-        } else if (d == 2 && D <= T.dmax) {
+        } else if (D <= T.dmax) {
           q = kQPairs;
           nt = Mout;
         } else {
@@ -521,8 +485,8 @@ cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratc
                            int32_t* post_nterms) {
   const int64_t n_items = n_boxes * h;
   if (n_items == 0) return cudaSuccess;
-  if (tau > 0.0f || n_items > S.qcap || n_items > INT32_MAX) return cudaErrorInvalidValue;
-  ComposeArgs A{cap, h, kind, coef, eps, degrees, global_d, lo, hi, pre_up, pre_lo, pre_ld,
+  if (!(tau >= 0.0f) || n_items > S.qcap || n_items > INT32_MAX) return cudaErrorInvalidValue;
+  ComposeArgs A{cap, tau, h, kind, coef, eps, degrees, global_d, lo, hi, pre_up, pre_lo, pre_ld,
                 pre_nterms, post_up, post_lo, post_ld, post_nterms};
   // the largest input degree any item of this call can have
   int Dmax = 0;
@@ -571,6 +535,12 @@ cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratc
     k_compose_pairs<<<(unsigned)std::min<int64_t>(n_items, 152 * 8), 256, psmem, L.stream>>>(
         T, A, S, L.status);
     ++*L.launches;
+  }
+  // Horner kernel for orders >= 3, and for every order when pruning
+  if (tau > 0.0f || global_d >= 3) {
+    const int Dout = std::min(cap, std::max(1, global_d) * Dmax);
+    e = launch_compose_horner(L, T, S, A, Dmax, Dout);
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }

@@ -191,6 +191,9 @@ extern "C" int bern_propagate_noalloc(const bern_net* net, const float* boxes, i
   if (dp->kind == BERN_DEG_PER_LAYER && !dp->per_layer) return BERN_E_INVALID;
   const int cap = dp->degree_cap > 0 ? dp->degree_cap : 16;
   if (cap > bern::kMaxTableDegree || !(dp->prune_tau >= 0.0f)) return BERN_E_INVALID;
+  // the static tables hold the order-1/2 kernels' tables only: no Horner
+  // items (orders >= 3, pruning) on this path
+  if (dp->prune_tau > 0.0f) return BERN_E_UNSUPPORTED;
   const int64_t budget = dp->bern_budget > 0 ? dp->bern_budget : ((int64_t)1 << 20);
   if (n_boxes == 0) return BERN_OK;
   if (!result->lo || !result->hi || !result->n_terms || result->cap_terms < 0)
@@ -222,6 +225,7 @@ extern "C" int bern_propagate_noalloc(const bern_net* net, const float* boxes, i
     if (l.hidden) {
       l.d = dp->kind == BERN_DEG_GLOBAL ? dp->global_d : dp->per_layer[i];
       if (l.d < 1 || l.d > bern::kMaxOrder) return BERN_E_INVALID;
+      if (l.d >= 3) return BERN_E_UNSUPPORTED;
       l.D_post = std::min(D * l.d, cap);
       if (l.d >= 2) dsq = std::max(dsq, l.D_pre);
       D = l.D_post;

@@ -82,6 +82,41 @@ bool build_product_pairs(int n, int Dq, int Ds, PairList& out) {
   return build_pairs(n, Dq, Ds, false, out);
 }
 
+bool build_product_table(int n, int Dq, int Ds, int64_t max_pairs, std::vector<int32_t>& ptr,
+                         std::vector<int32_t>& pairs) {
+  const int64_t mq = num_monomials(n, Dq), ms = num_monomials(n, Ds);
+  const int64_t mo = num_monomials(n, Dq + Ds);
+  if (mq < 0 || ms < 0 || mo < 0 || mq * ms > max_pairs || mo > INT32_MAX - 1) return false;
+  std::vector<uint8_t> ex;
+  graded_monomials(n, Dq + Ds, ex);
+  std::unordered_map<uint64_t, int32_t> rank;
+  rank.reserve((size_t)mo * 2);
+  for (int64_t r = 0; r < mo; ++r) rank[pack_key(&ex[(size_t)r * n], n)] = (int32_t)r;
+  // the graded order of degree <= D is a prefix of the list, so the ranks of
+  // q's and s's monomials are their ranks in ex
+  std::vector<int32_t> code((size_t)mq * ms);
+  std::vector<int32_t> cnt(mo + 1, 0);
+  for (int64_t i = 0; i < mq; ++i) {
+    const uint64_t ki = pack_key(&ex[(size_t)i * n], n);
+    for (int64_t j = 0; j < ms; ++j) {
+      const int32_t k = rank.at(ki + pack_key(&ex[(size_t)j * n], n));
+      code[(size_t)i * ms + j] = k;
+      cnt[k + 1]++;
+    }
+  }
+  ptr.assign(mo + 1, 0);
+  for (int64_t k = 0; k < mo; ++k) ptr[k + 1] = ptr[k] + cnt[k + 1];
+  pairs.assign((size_t)ptr[mo] * 2, 0);
+  std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+  for (int64_t i = 0; i < mq; ++i)
+    for (int64_t j = 0; j < ms; ++j) {
+      const int32_t p = fill[code[(size_t)i * ms + j]]++;
+      pairs[(size_t)p * 2] = (int32_t)i;
+      pairs[(size_t)p * 2 + 1] = (int32_t)j;
+    }
+  return true;
+}
+
 bool build_row_table(int n, int D, RowImage& out) {
   out = RowImage{};
   if (D < 0 || D > kMaxRowDegree) return false;

@@ -1,0 +1,152 @@
+"""Composition by Horner's rule on the GPU (ReLU orders 3 and 4, mixed
+per-layer and per-neuron orders, degree-cap truncation and pruning) against
+the FP64 oracle, plus Monte-Carlo soundness.  Same tolerances as the other
+whole-path tests: bounds within 1e-4 * (1 + |bound|), polynomials within
+1e-4 * (1 + ||p||_1) in summed absolute coefficient difference."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2211_14438_gb300 import bern
+from paper_2211_14438_gb300 import workloads as wl
+from parity_util import dense_from_dict, l1
+from test_gpu_propagate import compare_box, mc_check, near_tie, run_gpu
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = bern.Context(0)
+    yield c
+    c.close()
+
+
+def random_boxes(n, k, seed, lo=0.05, hi=1.0):
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-1, 1, (k, n))
+    s = rng.uniform(lo, hi, (k, n))
+    return wl.box_array(c - s / 2, c + s / 2)
+
+
+def check_all(ctx, net, boxes, degree, cap=16, tau=0.0, mc=20_000, seed=0):
+    g = run_gpu(ctx, net, boxes, degree=degree, cap=cap, tau=tau)
+    widths = net.widths
+    if isinstance(degree, (int, np.integer)):
+        degs = int(degree)
+    else:
+        arr = np.asarray(degree)
+        if len(arr) == len(widths) - 2 and arr.dtype != np.uint8:
+            degs = np.concatenate([np.full(h, d) for h, d in zip(widths[1:-1], arr)])
+        else:
+            degs = arr.astype(np.int64)
+    rng = np.random.default_rng(seed)
+    checked = 0
+    for bi in range(len(boxes)):
+        r = oracle.propagate(widths, net.W, net.b, boxes[bi], degs, cap=cap, tau=tau,
+                             budget=bern.effective_budget())
+        if not near_tie(r):
+            compare_box(g, bi, r, widths[0], widths[-1])
+            checked += 1
+        assert mc_check(g, bi, net, boxes[bi], mc, rng) == 0
+    assert checked >= max(1, len(boxes) - 1)
+    return g
+
+
+@pytest.mark.parametrize("d", [3, 4, 5])
+def test_config1_orders_above_two(ctx, d):
+    w = wl.config1()
+    check_all(ctx, w.net, w.boxes, d, mc=200_000, seed=d)
+
+
+@pytest.mark.parametrize("widths,degree,seed", [
+    ([2, 6, 5, 3], [3, 2], 21), ([3, 10, 10, 2], [1, 4], 22), ([1, 8, 8, 1], 4, 23),
+    ([4, 8, 8, 1], [2, 3], 24), ([3, 7, 6, 5, 1], [3, 3, 2], 25)])
+def test_per_layer_orders(ctx, widths, degree, seed):
+    net = wl.make_net(widths, seed)
+    check_all(ctx, net, random_boxes(widths[0], 4, seed), degree, seed=seed)
+
+
+def test_per_neuron_orders(ctx):
+    widths = [2, 8, 8, 1]
+    net = wl.make_net(widths, 31)
+    degs = np.random.default_rng(31).integers(1, 5, sum(widths[1:-1])).astype(np.uint8)
+    check_all(ctx, net, random_boxes(2, 4, 31, 0.3, 1.5), degs, seed=31)
+
+
+@pytest.mark.parametrize("cap", [3, 5, 7])
+def test_degree_cap_truncation_with_horner(ctx, cap):
+    """Low caps force truncation (and remainder carrying) inside Horner."""
+    widths = [2, 6, 6, 1]
+    net = wl.make_net(widths, 41)
+    check_all(ctx, net, random_boxes(2, 4, 41, 0.5, 2.0), 3, cap=cap, seed=cap)
+
+
+@pytest.mark.parametrize("tau,degree", [(1e-3, 2), (1e-2, 2), (1e-3, 3), (3e-3, 1)])
+def test_pruning(ctx, tau, degree):
+    widths = [3, 10, 10, 2]
+    net = wl.make_net(widths, 51)
+    boxes = random_boxes(3, 4, 51, 0.3, 1.5)
+    g = check_all(ctx, net, boxes, degree, tau=tau, seed=52)
+    # pruning only ever removes terms: term counts never exceed the unpruned ones
+    g0 = run_gpu(ctx, net, boxes, degree=degree)
+    assert np.all(g["n_terms"] <= g0["n_terms"])
+
+
+def test_pruning_shrinks_terms_on_small_boxes(ctx):
+    """On small boxes the high-degree terms are tiny and pruning drops whole
+    degrees: the term count falls below the unpruned graded prefix."""
+    w = wl.config3()
+    idx = np.arange(0, 4096, 512)
+    g0 = run_gpu(ctx, w.net, w.boxes[idx])
+    g = run_gpu(ctx, w.net, w.boxes[idx], tau=1e-4)
+    assert np.all(g["n_terms"] <= g0["n_terms"])
+    assert np.any(g["n_terms"] < g0["n_terms"])
+    for k, bi in enumerate(idx):
+        r = oracle.propagate(w.net.widths, w.net.W, w.net.b, w.boxes[bi], 2, tau=1e-4)
+        if not near_tie(r):
+            compare_box(g, k, r, 3, 1)
+
+
+def test_step_compose_order3_matches_oracle(ctx):
+    """bern_compose (step ABI) on order-3 items against the oracle's compose
+    of each item's polynomial."""
+    n, h, B = 2, 3, 2
+    D = 3
+    Mpre = bern.num_monomials(n, D)
+    cap = 8
+    Mpost = bern.num_monomials(n, min(3 * D, cap))
+    rng = np.random.default_rng(61)
+    pre = rng.normal(0, 0.3, (B, Mpre, h)).astype(np.float32)
+    # bracket each item's range loosely so that s lies in [0,1]
+    mag = np.abs(pre).sum(1)
+    lo = (pre[:, 0, :] - mag - 0.1).astype(np.float32)
+    hi = (pre[:, 0, :] + mag + 0.2).astype(np.float32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    kind = torch.full((B * h,), 2, dtype=torch.int8, device="cuda")
+    coef = torch.zeros((B * h, bern.COEF_STRIDE), dtype=torch.float32, device="cuda")
+    eps = torch.zeros(B * h, dtype=torch.float32, device="cuda")
+    lo_d, hi_d = dev(lo.reshape(-1)), dev(hi.reshape(-1))
+    ctx.relu_coeffs(B * h, lo_d, hi_d, None, 3, kind, coef, eps)
+    nt = torch.full((B * h,), Mpre, dtype=torch.int32, device="cuda")
+    pu, pl = dev(pre), dev(pre)
+    qu = torch.zeros((B, Mpost, h), dtype=torch.float32, device="cuda")
+    ql = torch.zeros_like(qu)
+    qn = torch.zeros(B * h, dtype=torch.int32, device="cuda")
+    ctx.compose(n, B, h, cap, 0.0, kind, coef, eps, None, 3, lo_d, hi_d, pu, pl, Mpre, nt,
+                qu, ql, Mpost, qn)
+    assert ctx.sync() == 0
+    qu, ql, qn = qu.cpu().numpy(), ql.cpu().numpy(), qn.cpu().numpy()
+    ex = bern.monomials(n, D)
+    for b in range(B):
+        for m in range(h):
+            assert qn[b * h + m] == Mpost
+            for name, arr, upper in (("u", qu, True), ("l", ql, False)):
+                ref = oracle.compose((ex, pre[b, :, m].astype(np.float64)), n, float(lo[b, m]),
+                                     float(hi[b, m]), 3, upper, cap=cap)
+                ov = dense_from_dict(oracle.to_dict(ref), n, Mpost)
+                gv = arr[b, :, m].astype(np.float64)
+                assert np.abs(gv - ov).sum() <= 1e-4 * (1 + l1(ov)), (b, m, name)

@@ -176,8 +176,6 @@ def test_paper_family_nets(ctx):
     net = wl.paper_net(2, [20, 20], seed=101)
     box = wl.box_array([-1, -1], [1, 1])[None]
     for d in (2, 3, 4):
-        if d > 2:
-            pytest.skip("orders above 2 are not implemented in the composition kernel yet")
         g = run_gpu(ctx, net, box, degree=d)
         r = oracle.propagate(net.widths, net.W, net.b, box[0], d)
         if not near_tie(r):

@@ -81,3 +81,19 @@ def test_noalloc_rejects_oversized_network():
     out = _out(1, 1, 16)
     rc = bern.propagate_noalloc(widths, W, b, bx, out, degree=2, cap=16)
     assert rc == bern.BERN_E_UNSUPPORTED
+
+
+def test_noalloc_rejects_horner_plans():
+    """Orders >= 3 and pruning need the Horner product tables, which the
+    static table area does not hold: rejected before any GPU work."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    w = wl.config1()
+    W = [torch.from_numpy(x).cuda() for x in w.net.W]
+    b = [torch.from_numpy(x).cuda() for x in w.net.b]
+    bx = torch.from_numpy(w.boxes).cuda()
+    out = _out(1, 1, 256)
+    assert bern.propagate_noalloc(w.net.widths, W, b, bx, out, degree=3, cap=16) == \
+        bern.BERN_E_UNSUPPORTED
+    assert bern.propagate_noalloc(w.net.widths, W, b, bx, out, degree=2, cap=16, tau=1e-3) == \
+        bern.BERN_E_UNSUPPORTED
