@@ -54,12 +54,21 @@ extern "C" {
 #define BERN_DEG_GLOBAL     0 /* every hidden neuron uses global_d */
 #define BERN_DEG_PER_LAYER  1 /* hidden layer i (1-based) uses per_layer[i-1] */
 #define BERN_DEG_PER_NEURON 2 /* hidden neuron k (layer-major order) uses per_neuron[k] */
+#define BERN_DEG_LEARNED    3 /* the order of every (box, hidden neuron) is proposed at run
+                                 time by the plan's degree MLP (see bern_mlp) */
 
 #define BERN_MAX_VARS   8
 #define BERN_MAX_ORDER  8     /* largest ReLU Bernstein order d */
 #define BERN_MAX_GRID   24576 /* largest Bernstein grid one enclosure stages in shared memory;
                                  bern_budget is clamped to it */
 #define BERN_MAX_ENCLOSE_ORDER 24 /* Bernstein orders above this are lowered to it */
+
+/* the learned component's MLP */
+#define BERN_MLP_HIDDEN       64  /* hidden width */
+#define BERN_MLP_MAX_FEATURES 16
+#define BERN_MLP_MAX_CLASSES  8
+#define BERN_DEGREE_FEATURES  8   /* features of one (box, neuron) for degree proposals */
+#define BERN_DEGREE_CLASSES   4   /* class c proposes ReLU order c + 1 */
 
 typedef struct bern_ctx bern_ctx;
 
@@ -86,6 +95,23 @@ typedef struct {
  *                and coefficient intervals for the rest (0 means 2^20; values
  *                above BERN_MAX_GRID act as BERN_MAX_GRID).
  * per_layer / per_neuron are host arrays. */
+/* The learned component (not part of the paper's method): a two-layer MLP
+ * with BF16 weights and activations and FP32 accumulation,
+ *   a = relu(W1 bf16(x) + b1) rounded to bf16   (BERN_MLP_HIDDEN units)
+ *   z = W2 a + b2                               (n_classes logits)
+ * Device pointers: W1 bf16 bits [HIDDEN x n_features] row-major, b1 fp32
+ * [HIDDEN], W2 bf16 bits [n_classes x HIDDEN], b2 fp32 [n_classes].
+ * The flat FP32 parameter vector used by training keeps the same four
+ * blocks in this order: W1, b1, W2, b2 (bern_mlp_num_params entries). */
+typedef struct {
+  int n_features;
+  int n_classes;
+  const uint16_t* W1;
+  const float* b1;
+  const uint16_t* W2;
+  const float* b2;
+} bern_mlp;
+
 typedef struct {
   int kind;
   int global_d;
@@ -94,6 +120,12 @@ typedef struct {
   int degree_cap;
   float prune_tau;
   int64_t bern_budget;
+  /* BERN_DEG_LEARNED: the degree MLP (n_features = BERN_DEGREE_FEATURES,
+   * n_classes = BERN_DEGREE_CLASSES, host struct, device weights) and the
+   * fallback: a neuron whose largest class probability is below min_conf
+   * uses global_d (the plain method's order). */
+  const bern_mlp* mlp;
+  float min_conf;
 } bern_degree_plan;
 
 /* Results, all caller-owned, in the context's pointer mode.
@@ -264,6 +296,45 @@ int bern_compose(bern_ctx* ctx, int n, int64_t n_boxes, int h, int degree_cap,
  * serialised by the caller. */
 int bern_propagate_noalloc(const bern_net* net, const float* boxes, int64_t n_boxes,
                            const bern_degree_plan* plan, bern_result* result, void* stream);
+
+/* ------------------------------------------------------------ learned component
+ * The proposals only choose orders; bern_propagate computes sound bounds for
+ * whatever order it is given, so the MLP never affects soundness. */
+
+/* Number of FP32 parameters of an MLP (W1, b1, W2, b2). */
+int64_t bern_mlp_num_params(int n_features, int n_classes);
+
+/* Features of n_items (box, neuron) items for degree proposals, from the
+ * pre-activation enclosure [lo, hi], the pre-activation term count and the
+ * hidden layer index (1-based):  with s = max(|lo|, |hi|, 1e-30),
+ *   x0 = lo/s, x1 = hi/s, x2 = log2(max(hi-lo, 1e-30))/8, x3 = layer/8,
+ *   x4 = log2(max(nterms, 1))/16, x5 = [lo >= 0], x6 = [hi <= 0],
+ *   x7 = -lo/(hi-lo) clipped to [0, 1] (the kink position, 0 if lo >= 0).
+ * x: [n_items x BERN_DEGREE_FEATURES] fp32. */
+int bern_degree_features(bern_ctx* ctx, int64_t n_items, const float* lo, const float* hi,
+                         const int32_t* nterms, int layer, float* x);
+
+/* Inference: logits [n x n_classes] fp32 for features x [n x n_features]. */
+int bern_mlp_forward(bern_ctx* ctx, const bern_mlp* mlp, int64_t n, const float* x,
+                     float* logits);
+
+/* Training step, part 1: the gradient of the mean weighted softmax
+ * cross-entropy  L = (1/n) sum_s w_s * (-log softmax(z_s)[label_s])
+ * with respect to the flat parameter vector (W1, b1, W2, b2), through the
+ * BF16 forward above (the bf16 roundings of x and a are treated as the
+ * identity in the derivative).  labels: [n] int32 in [0, n_classes);
+ * w: [n] fp32 or NULL (all 1).  grad: [num_params] fp32, loss: [1] fp32.
+ * Deterministic (fixed summation order).  Uses library scratch. */
+int bern_mlp_backward(bern_ctx* ctx, const bern_mlp* mlp, int64_t n, const float* x,
+                      const int32_t* labels, const float* w, float* grad, float* loss);
+
+/* Training step, part 2: one Adam update (Kingma & Ba, with bias
+ * correction for step t >= 1) of the FP32 master parameters `param`
+ * (with moments m, v, all [num_params]), then the BF16 copies of W1 and W2
+ * (round to nearest even) into W1_bf16 / W2_bf16. */
+int bern_mlp_adam(bern_ctx* ctx, int n_features, int n_classes, float* param, float* m,
+                  float* v, const float* grad, float lr, float beta1, float beta2, float eps,
+                  int t, uint16_t* W1_bf16, uint16_t* W2_bf16);
 
 #ifdef __cplusplus
 }

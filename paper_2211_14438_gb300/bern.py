@@ -28,6 +28,10 @@ BERN_MEM_HOST = 1
 BERN_DEG_GLOBAL = 0
 BERN_DEG_PER_LAYER = 1
 BERN_DEG_PER_NEURON = 2
+BERN_DEG_LEARNED = 3
+BERN_MLP_HIDDEN = 64
+BERN_DEGREE_FEATURES = 8
+BERN_DEGREE_CLASSES = 4
 BERN_MAX_ORDER = 8
 BERN_MAX_GRID = 24576
 BERN_MAX_ENCLOSE_ORDER = 24
@@ -45,6 +49,8 @@ EXPORTS = [
     "bern_strerror", "bern_sync", "bern_kernel_launches", "bern_num_monomials",
     "bern_monomials", "bern_propagate", "bern_init_inputs", "bern_affine",
     "bern_enclose", "bern_relu_coeffs", "bern_compose", "bern_propagate_noalloc",
+    "bern_mlp_num_params", "bern_degree_features", "bern_mlp_forward", "bern_mlp_backward",
+    "bern_mlp_adam",
 ]
 
 
@@ -59,12 +65,19 @@ class bern_net(ctypes.Structure):
                 ("W", ctypes.POINTER(ctypes.c_void_p)), ("b", ctypes.POINTER(ctypes.c_void_p))]
 
 
+class bern_mlp(ctypes.Structure):
+    _fields_ = [("n_features", ctypes.c_int), ("n_classes", ctypes.c_int),
+                ("W1", ctypes.c_void_p), ("b1", ctypes.c_void_p),
+                ("W2", ctypes.c_void_p), ("b2", ctypes.c_void_p)]
+
+
 class bern_degree_plan(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("global_d", ctypes.c_int),
                 ("per_layer", ctypes.POINTER(ctypes.c_int)),
                 ("per_neuron", ctypes.POINTER(ctypes.c_uint8)),
                 ("degree_cap", ctypes.c_int), ("prune_tau", ctypes.c_float),
-                ("bern_budget", ctypes.c_int64)]
+                ("bern_budget", ctypes.c_int64),
+                ("mlp", ctypes.POINTER(bern_mlp)), ("min_conf", ctypes.c_float)]
 
 
 class bern_result(ctypes.Structure):
@@ -112,6 +125,11 @@ def load(build_if_missing: bool = True):
         "bern_propagate_noalloc": (I, [ctypes.POINTER(bern_net), V, I64,
                                        ctypes.POINTER(bern_degree_plan),
                                        ctypes.POINTER(bern_result), V]),
+        "bern_mlp_num_params": (I64, [I, I]),
+        "bern_degree_features": (I, [V, I64, V, V, V, I, V]),
+        "bern_mlp_forward": (I, [V, ctypes.POINTER(bern_mlp), I64, V, V]),
+        "bern_mlp_backward": (I, [V, ctypes.POINTER(bern_mlp), I64, V, V, V, V, V]),
+        "bern_mlp_adam": (I, [V, I, I, V, V, V, V, F, F, F, F, I, V, V]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -220,6 +238,26 @@ class Context:
                                      _ptr(post_up), _ptr(post_lo), post_ld,
                                      _ptr(post_nterms)), "bern_compose")
 
+    # ------------------------------------------------------------- learned component
+    def degree_features(self, n_items, lo, hi, nterms, layer, x):
+        _check(self.lib.bern_degree_features(self.h, n_items, _ptr(lo), _ptr(hi), _ptr(nterms),
+                                             int(layer), _ptr(x)), "bern_degree_features")
+
+    def mlp_forward(self, mlp: "Mlp", x, logits):
+        _check(self.lib.bern_mlp_forward(self.h, ctypes.byref(mlp.struct()), int(x.shape[0]),
+                                         _ptr(x), _ptr(logits)), "bern_mlp_forward")
+
+    def mlp_backward(self, mlp: "Mlp", x, labels, w, grad, loss):
+        _check(self.lib.bern_mlp_backward(self.h, ctypes.byref(mlp.struct()), int(x.shape[0]),
+                                          _ptr(x), _ptr(labels), _ptr(w), _ptr(grad),
+                                          _ptr(loss)), "bern_mlp_backward")
+
+    def mlp_adam(self, mlp: "Mlp", grad, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        mlp.t += 1
+        _check(self.lib.bern_mlp_adam(self.h, mlp.F, mlp.C, _ptr(mlp.param), _ptr(mlp.m),
+                                      _ptr(mlp.v), _ptr(grad), lr, beta1, beta2, eps, mlp.t,
+                                      _ptr(mlp.W1), _ptr(mlp.W2)), "bern_mlp_adam")
+
     # ------------------------------------------------------------- whole path
     def propagate(self, widths: Sequence[int], W, b, boxes, degree=2, cap: int = 16,
                   tau: float = 0.0, budget: int = 0, cap_terms: Optional[int] = None,
@@ -306,6 +344,43 @@ def propagate_noalloc(widths, W, b, boxes, out, degree=2, cap: int = 16, tau: fl
                                              ctypes.byref(res), ctypes.c_void_p(h)))
 
 
+class Mlp:
+    """Device state of one MLP of the learned component: the FP32 master
+    parameter vector (W1, b1, W2, b2), its Adam moments and the BF16 copies
+    of W1 and W2 that the kernels read.  Tensors are torch CUDA tensors."""
+
+    def __init__(self, torch, n_features: int, n_classes: int, theta=None, device="cuda"):
+        self.F, self.C = int(n_features), int(n_classes)
+        P = int(load().bern_mlp_num_params(self.F, self.C))
+        if P < 0:
+            raise ValueError("unsupported MLP shape")
+        H = BERN_MLP_HIDDEN
+        if theta is None:
+            theta = np.zeros(P, np.float32)
+        theta = np.asarray(theta, np.float32)
+        self.param = torch.from_numpy(theta.copy()).to(device)
+        self.m = torch.zeros_like(self.param)
+        self.v = torch.zeros_like(self.param)
+        self.t = 0
+        oW1, ob1, oW2 = H * self.F, H * self.F + H, H * self.F + H + self.C * H
+        self.b1 = self.param[oW1:ob1]
+        self.b2 = self.param[oW2:]
+        # bf16 copies (round to nearest even), as raw 16-bit words
+        self.W1 = self.param[:oW1].to(torch.bfloat16).view(torch.int16).contiguous()
+        self.W2 = self.param[ob1:oW2].to(torch.bfloat16).view(torch.int16).contiguous()
+        self.n_params = P
+        self._s = None
+
+    def struct(self):
+        if self._s is None:
+            self._s = bern_mlp(self.F, self.C, _ptr(self.W1), _ptr(self.b1), _ptr(self.W2),
+                               _ptr(self.b2))
+        return self._s
+
+    def theta(self) -> np.ndarray:
+        return self.param.detach().cpu().numpy().astype(np.float64)
+
+
 def make_net(widths, W_ptrs, b_ptrs):
     H = len(widths) - 1
     wid = (ctypes.c_int * (H + 1))(*widths)
@@ -315,10 +390,24 @@ def make_net(widths, W_ptrs, b_ptrs):
     return net, (wid, Wa, ba)
 
 
+class Learned:
+    """A learned degree plan: the degree MLP (an Mlp with BERN_DEGREE_FEATURES
+    features and BERN_DEGREE_CLASSES classes), the confidence below which a
+    neuron falls back to the plain order, and that order."""
+
+    def __init__(self, mlp: "Mlp", min_conf: float = 0.0, fallback: int = 2):
+        self.mlp, self.min_conf, self.fallback = mlp, float(min_conf), int(fallback)
+
+
 def make_plan(degree, widths, cap, tau, budget):
     H = len(widths) - 1
     keep = []
-    if isinstance(degree, (int, np.integer)):
+    if isinstance(degree, Learned):
+        ms = degree.mlp.struct()
+        keep.append(ms)
+        plan = bern_degree_plan(BERN_DEG_LEARNED, degree.fallback, None, None, cap, tau, budget,
+                                ctypes.pointer(ms), degree.min_conf)
+    elif isinstance(degree, (int, np.integer)):
         plan = bern_degree_plan(BERN_DEG_GLOBAL, int(degree), None, None, cap, tau, budget)
     else:
         arr = np.asarray(degree)
@@ -337,6 +426,8 @@ def make_plan(degree, widths, cap, tau, budget):
 
 def layer_degrees(widths, degree):
     H = len(widths) - 1
+    if isinstance(degree, Learned):
+        return [max(BERN_DEGREE_CLASSES, degree.fallback)] * (H - 1)
     if isinstance(degree, (int, np.integer)):
         return [int(degree)] * (H - 1)
     arr = np.asarray(degree)

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <new>
@@ -11,6 +12,7 @@
 
 #include "bern_internal.cuh"
 #include "compose_common.cuh"
+#include "mlp.cuh"
 
 namespace bern {
 int effective_order(int n, int order, int64_t budget, int* grid_out);
@@ -72,7 +74,7 @@ struct bern_ctx {
   int* d_status = nullptr;
   int64_t launches = 0;
   std::map<int, TableSet> tables;
-  DevBuf ws, stage_in, stage_out, qbuf;
+  DevBuf ws, stage_in, stage_out, qbuf, mlp_ws;
   std::vector<GraphEntry> graphs;
   Launch launch() { return Launch{stream, d_status, &launches}; }
   Launch launch_on(cudaStream_t s) { return Launch{s, d_status, &launches}; }
@@ -250,7 +252,7 @@ int ensure_prod_tables(bern_ctx* c, int n, int Dmax, int dmax, int cap) {
 
 // Composition work queues for up to `items` items.
 int ensure_queues(bern_ctx* c, int64_t items, ComposeScratch* out) {
-  const size_t bytes = 256 + (size_t)kComposeQueues * items * sizeof(int);
+  const size_t bytes = 256 + (size_t)kQueueLists * items * sizeof(int);
   cudaError_t e = c->qbuf.reserve(bytes);
   if (e != cudaSuccess) return map_cuda(e);
   out->qcount = (int*)c->qbuf.p;
@@ -270,6 +272,10 @@ struct LayerPlan {
   // per-box offsets (in bytes) into the workspace
   size_t off_pre_up, off_pre_lo, off_pre_nt, off_lo, off_hi, off_kind, off_coef, off_eps,
       off_post_up, off_post_lo, off_post_nt, off_deg;
+  // learned plans: the per-box Bernstein order of this layer's enclosure and
+  // every value it can take
+  size_t off_order = 0;
+  std::vector<int> orders;
 };
 
 struct Plan {
@@ -281,6 +287,11 @@ struct Plan {
   size_t per_box;   // bytes per box
   std::vector<uint8_t> neuron_deg;   // PER_NEURON plans (hidden neurons, layer-major)
   bool per_neuron = false;
+  // LEARNED plans
+  bool learned = false;
+  bern_mlp mlp{};
+  float min_conf = 0.0f;
+  int fallback_d = 2;
 };
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -306,6 +317,18 @@ int make_plan(const bern_net* net, const bern_degree_plan* dp, Plan& P) {
   int Dprev = 1, order = 1;
   int hidden_base = 0;
   P.per_neuron = dp->kind == BERN_DEG_PER_NEURON;
+  P.learned = dp->kind == BERN_DEG_LEARNED;
+  if (P.learned) {
+    const bern_mlp* m = dp->mlp;
+    if (!m || m->n_features != kDegFeatures || m->n_classes != kDegClasses || !m->W1 || !m->b1 ||
+        !m->W2 || !m->b2 || !(dp->min_conf >= 0.0f && dp->min_conf <= 1.0f))
+      return BERN_E_INVALID;
+    P.mlp = *m;
+    P.min_conf = dp->min_conf;
+    P.fallback_d = dp->global_d > 0 ? dp->global_d : 2;
+    if (P.fallback_d > kMaxOrder) return BERN_E_INVALID;
+  }
+  std::vector<int> reach{1};   // learned plans: the order values a box can have
   for (int i = 0; i < P.H; ++i) {
     LayerPlan& l = P.L[i];
     l.h_in = net->widths[i];
@@ -320,6 +343,8 @@ int make_plan(const bern_net* net, const bern_degree_plan* dp, Plan& P) {
       } else if (dp->kind == BERN_DEG_PER_LAYER) {
         if (!dp->per_layer) return BERN_E_INVALID;
         l.d = dp->per_layer[i];
+      } else if (dp->kind == BERN_DEG_LEARNED) {
+        l.d = std::max(kDegClasses, P.fallback_d);
       } else if (dp->kind == BERN_DEG_PER_NEURON) {
         if (!dp->per_neuron) return BERN_E_INVALID;
         int mx = 0;
@@ -344,6 +369,20 @@ int make_plan(const bern_net* net, const bern_degree_plan* dp, Plan& P) {
     l.M_pre = monomials_clamped(P.n, l.D_pre);
     l.M_post = monomials_clamped(P.n, l.D_post);
     if (l.M_pre < 0 || l.M_post < 0) return BERN_E_UNSUPPORTED;
+    if (P.learned) {
+      l.orders = reach;
+      if (l.hidden) {
+        std::vector<int> next;
+        for (int o : reach)
+          for (int d = 1; d <= l.d; ++d) {
+            const int v = std::min(o * d, P.cap);
+            if (std::find(next.begin(), next.end(), v) == next.end()) next.push_back(v);
+          }
+        std::sort(next.begin(), next.end());
+        reach = next;
+      }
+      if ((int)l.orders.size() > kOrderQueues) return BERN_E_UNSUPPORTED;
+    }
   }
   // per-box workspace layout
   size_t off = 0;
@@ -369,8 +408,9 @@ int make_plan(const bern_net* net, const bern_degree_plan* dp, Plan& P) {
       l.off_post_up = take(sizeof(float) * l.h_out * l.M_post);
       l.off_post_lo = take(sizeof(float) * l.h_out * l.M_post);
       l.off_post_nt = take(sizeof(int32_t) * l.h_out);
-      l.off_deg = P.per_neuron ? take(l.h_out) : 0;
+      l.off_deg = (P.per_neuron || P.learned) ? take(l.h_out) : 0;
     }
+    if (P.learned) l.off_order = take(sizeof(int32_t));
   }
   P.per_box = off;
   return BERN_OK;
@@ -399,6 +439,12 @@ int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
   const float* in_lo = ch.at<float>(P.off_z_lo);
   const int32_t* in_nt = ch.at<int32_t>(P.off_z_nt);
   int64_t in_stride = n + 1;
+  const MlpView mv{P.mlp.n_features, P.mlp.n_classes, (const __nv_bfloat16*)P.mlp.W1, P.mlp.b1,
+                   (const __nv_bfloat16*)P.mlp.W2, P.mlp.b2};
+  if (P.learned) {
+    e = launch_fill_i32(L, ch.at<int32_t>(P.L[0].off_order), B, 1);
+    if (e != cudaSuccess) return map_cuda(e);
+  }
   for (int i = 0; i < P.H; ++i) {
     const LayerPlan& l = P.L[i];
     float* pre_up = ch.at<float>(l.off_pre_up);
@@ -408,8 +454,12 @@ int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
                       in_nt, pre_up, pre_lo, l.M_pre, pre_nt);
     if (e != cudaSuccess) return map_cuda(e);
     if (!l.hidden) {
-      e = launch_enclose(L, T, B, l.h_out, l.order, P.budget, pre_up, pre_lo, l.M_pre, pre_nt,
-                         out_lo, out_hi);
+      if (P.learned)
+        e = launch_enclose_by_order(L, T, CS, B, l.h_out, ch.at<int32_t>(l.off_order), l.orders,
+                                    P.budget, pre_up, pre_lo, l.M_pre, pre_nt, out_lo, out_hi);
+      else
+        e = launch_enclose(L, T, B, l.h_out, l.order, P.budget, pre_up, pre_lo, l.M_pre, pre_nt,
+                           out_lo, out_hi);
       if (e != cudaSuccess) return map_cuda(e);
       e = launch_pack(L, T, B, P.o, pre_up, pre_lo, l.M_pre, pre_nt, res);
       if (e != cudaSuccess) return map_cuda(e);
@@ -418,12 +468,23 @@ int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
     float* lo = ch.at<float>(l.off_lo);
     float* hi = ch.at<float>(l.off_hi);
     const uint8_t* deg = nullptr;
-    if (P.per_neuron) deg = ch.at<uint8_t>(l.off_deg);
+    if (P.per_neuron || P.learned) deg = ch.at<uint8_t>(l.off_deg);
     int8_t* kind = ch.at<int8_t>(l.off_kind);
     float* coef = ch.at<float>(l.off_coef);
     float* eps = ch.at<float>(l.off_eps);
-    e = launch_enclose_relu(L, T, B, l.h_out, l.order, P.budget, pre_up, pre_lo, l.M_pre,
-                            pre_nt, lo, hi, deg, l.d, kind, coef, eps);
+    if (P.learned) {
+      // enclosure at each box's order, then the MLP's orders and the a3 step
+      int32_t* ord = ch.at<int32_t>(l.off_order);
+      e = launch_enclose_by_order(L, T, CS, B, l.h_out, ord, l.orders, P.budget, pre_up, pre_lo,
+                                  l.M_pre, pre_nt, lo, hi);
+      if (e != cudaSuccess) return map_cuda(e);
+      e = launch_learned_degrees(L, mv, B, l.h_out, i + 1, lo, hi, pre_nt, P.min_conf,
+                                 P.fallback_d, P.cap, ord, ch.at<int32_t>(P.L[i + 1].off_order),
+                                 ch.at<uint8_t>(l.off_deg), kind, coef, eps);
+    } else {
+      e = launch_enclose_relu(L, T, B, l.h_out, l.order, P.budget, pre_up, pre_lo, l.M_pre,
+                              pre_nt, lo, hi, deg, l.d, kind, coef, eps);
+    }
     if (e != cudaSuccess) return map_cuda(e);
     float* post_up = ch.at<float>(l.off_post_up);
     float* post_lo = ch.at<float>(l.off_post_lo);
@@ -466,6 +527,12 @@ std::string graph_key(const Plan& P, const bern_net* net, const float* boxes, in
   add(&P.cap, sizeof P.cap);
   add(&P.tau, sizeof P.tau);
   add(&P.budget, sizeof P.budget);
+  add(&P.learned, sizeof P.learned);
+  if (P.learned) {
+    add(&P.mlp, sizeof P.mlp);
+    add(&P.min_conf, sizeof P.min_conf);
+    add(&P.fallback_d, sizeof P.fallback_d);
+  }
   add(&wsbase, sizeof wsbase);
   for (int i = 0; i <= P.H; ++i) add(&net->widths[i], sizeof(int));
   for (int i = 0; i < P.H; ++i) {
@@ -539,6 +606,7 @@ int bern_destroy(bern_ctx* c) {
   c->qbuf.release();
   c->stage_in.release();
   c->stage_out.release();
+  c->mlp_ws.release();
   if (c->d_status) cudaFree(c->d_status);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -806,6 +874,68 @@ int bern_propagate(bern_ctx* c, const bern_net* net, const float* boxes, int64_t
   }
   e = cudaGetLastError();
   return map_cuda(e);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ learned component
+namespace {
+bool mlp_shape_ok(int F, int C) {
+  return F >= 1 && F <= kMlpMaxF && C >= 2 && C <= kMlpMaxC;
+}
+bool mlp_ok(const bern_mlp* m) {
+  return m && mlp_shape_ok(m->n_features, m->n_classes) && m->W1 && m->b1 && m->W2 && m->b2;
+}
+MlpView view_of(const bern_mlp* m) {
+  return MlpView{m->n_features, m->n_classes, (const __nv_bfloat16*)m->W1, m->b1,
+                 (const __nv_bfloat16*)m->W2, m->b2};
+}
+}  // namespace
+
+extern "C" {
+
+int64_t bern_mlp_num_params(int n_features, int n_classes) {
+  if (!mlp_shape_ok(n_features, n_classes)) return -1;
+  return mlp_num_params(n_features, n_classes);
+}
+
+int bern_degree_features(bern_ctx* c, int64_t n_items, const float* lo, const float* hi,
+                         const int32_t* nterms, int layer, float* x) {
+  if (!c || n_items < 0 || (n_items > 0 && (!lo || !hi || !x))) return BERN_E_INVALID;
+  cudaSetDevice(c->device);
+  return map_cuda(launch_degree_features(c->launch(), n_items, lo, hi, nterms, layer, x));
+}
+
+int bern_mlp_forward(bern_ctx* c, const bern_mlp* mlp, int64_t n, const float* x,
+                     float* logits) {
+  if (!c || !mlp_ok(mlp) || n < 0 || (n > 0 && (!x || !logits))) return BERN_E_INVALID;
+  cudaSetDevice(c->device);
+  return map_cuda(launch_mlp_forward(c->launch(), view_of(mlp), n, x, logits));
+}
+
+int bern_mlp_backward(bern_ctx* c, const bern_mlp* mlp, int64_t n, const float* x,
+                      const int32_t* labels, const float* w, float* grad, float* loss) {
+  if (!c || !mlp_ok(mlp) || n < 1 || !x || !labels || !grad || !loss) return BERN_E_INVALID;
+  cudaSetDevice(c->device);
+  cudaError_t e = c->mlp_ws.reserve(mlp_backward_scratch(n, mlp->n_features, mlp->n_classes));
+  if (e != cudaSuccess) return map_cuda(e);
+  return map_cuda(launch_mlp_backward(c->launch(), view_of(mlp), n, x, labels, w, c->mlp_ws.p,
+                                      grad, loss));
+}
+
+int bern_mlp_adam(bern_ctx* c, int n_features, int n_classes, float* param, float* m, float* v,
+                  const float* grad, float lr, float beta1, float beta2, float eps, int t,
+                  uint16_t* W1_bf16, uint16_t* W2_bf16) {
+  if (!c || !mlp_shape_ok(n_features, n_classes) || !param || !m || !v || !grad || !W1_bf16 ||
+      !W2_bf16 || t < 1 || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
+      !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+    return BERN_E_INVALID;
+  cudaSetDevice(c->device);
+  const float c1 = (float)(1.0 - std::pow((double)beta1, (double)t));
+  const float c2 = (float)(1.0 - std::pow((double)beta2, (double)t));
+  return map_cuda(launch_mlp_adam(c->launch(), n_features, n_classes, param, m, v, grad, lr,
+                                  beta1, beta2, eps, c1, c2, (__nv_bfloat16*)W1_bf16,
+                                  (__nv_bfloat16*)W2_bf16));
 }
 
 }  // extern "C"

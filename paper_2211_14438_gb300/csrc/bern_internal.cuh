@@ -147,11 +147,23 @@ cudaError_t launch_pack(const Launch& L, const Tables& T, int64_t n_boxes, int o
 // Work queues of the composition step: kComposeQueues lists of item
 // indices, each of capacity qcap, and their counters.
 constexpr int kComposeQueues = kMaxRowDegree + 5;
+// Lists for the per-box Bernstein orders of learned plans (one per order value).
+constexpr int kOrderQueues = 32;
+constexpr int kQueueLists = kComposeQueues > kOrderQueues ? kComposeQueues : kOrderQueues;
 struct ComposeScratch {
   int* qcount;       // kComposeQueues counters (zeroed by the launcher)
   int* queue;        // kComposeQueues * qcap item indices
   int64_t qcap;
 };
+// Enclosure with a Bernstein order per box (box_order[b]); `orders` lists
+// every value box_order may take (at most kOrderQueues).  Items are sorted
+// into one list per order in S, then each order runs on its list.
+cudaError_t launch_enclose_by_order(const Launch& L, const Tables& T, const ComposeScratch& S,
+                                    int64_t n_boxes, int h, const int32_t* box_order,
+                                    const std::vector<int>& orders, int64_t budget,
+                                    const float* pre_up, const float* pre_lo, int64_t ld,
+                                    const int32_t* nterms, float* lo, float* hi);
+
 // Largest input degree the row-convolution path handles for n variables.
 int row_path_max_degree(int n);
 cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratch& S,

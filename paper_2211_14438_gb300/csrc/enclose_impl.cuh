@@ -243,27 +243,38 @@ __device__ float enclose_warp(const float* __restrict__ P, int ps, int nt, int n
   return dadd<UP>(best, rem);
 }
 
-struct ReluOut {
+// Options of one enclosure launch: the fused a3 outputs (kind == nullptr:
+// enclosure only) and an optional item list (list != nullptr: the launch
+// covers items list[0 .. *count), a device-side count; otherwise items
+// 0 .. n_items).
+struct EncloseOpts {
   int8_t* kind;
   float* coef;
   float* eps;
   const uint8_t* degrees;
   int global_d;
+  const int* list = nullptr;
+  const int* count = nullptr;
 };
+
+__device__ __forceinline__ int64_t map_item(const EncloseOpts& o, int64_t idx, int64_t n_items) {
+  if (o.list) return idx < *o.count ? (int64_t)o.list[idx] : -1;
+  return idx < n_items ? idx : -1;
+}
 
 template <int LB>
 __global__ void __launch_bounds__(512)
 k_enclose(Tables T, int G, const float2* __restrict__ rs, int64_t n_items, int h,
           const float* __restrict__ pre_up, const float* __restrict__ pre_lo, int64_t ld,
           const int32_t* __restrict__ nterms, float* __restrict__ lo, float* __restrict__ hi,
-          ReluOut ro, int* status) {
+          EncloseOpts ro, int* status) {
   extern __shared__ float smem[];
   __shared__ float s_lohi[8][2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int per_block = blockDim.x >> 6;               // items per block
-  const int64_t item = (int64_t)blockIdx.x * per_block + (warp >> 1);
+  const int64_t item = map_item(ro, (int64_t)blockIdx.x * per_block + (warp >> 1), n_items);
   const bool up = warp & 1;
-  if (item < n_items) {
+  if (item >= 0) {
     int nt = nterms[item];
     if (nt < 0 || nt > ld || nt > T.mexps) {
       if (lane == 0) atomicOr(status, kStatusInvalid);
@@ -283,8 +294,8 @@ k_enclose(Tables T, int G, const float2* __restrict__ rs, int64_t n_items, int h
   if (ro.kind == nullptr) return;
   __syncthreads();
   if (threadIdx.x < per_block) {
-    const int64_t it = (int64_t)blockIdx.x * per_block + threadIdx.x;
-    if (it < n_items) {
+    const int64_t it = map_item(ro, (int64_t)blockIdx.x * per_block + threadIdx.x, n_items);
+    if (it >= 0) {
       const int d = ro.degrees ? (int)ro.degrees[it] : ro.global_d;
       ro.kind[it] = (int8_t)relu_item(s_lohi[threadIdx.x][0], s_lohi[threadIdx.x][1], d,
                                       ro.coef + it * kCoefStride, ro.eps + it, status);
@@ -295,7 +306,7 @@ k_enclose(Tables T, int G, const float2* __restrict__ rs, int64_t n_items, int h
 template <int LB>
 cudaError_t launch_lb(const Launch& L, const Tables& T, int G, int64_t n_items, int h,
                       const float* pre_up, const float* pre_lo, int64_t ld,
-                      const int32_t* nterms, float* lo, float* hi, ReluOut ro) {
+                      const int32_t* nterms, float* lo, float* hi, EncloseOpts ro) {
   // items per block: as many as fit 192 KB of grids, at most 8 (16 warps)
   int items = (int)std::min<int64_t>(8, (192 * 1024) / (2 * (int64_t)G * 4));
   if (items < 1) items = 1;
@@ -377,15 +388,15 @@ __global__ void __launch_bounds__(256)
 k_enclose_small(Tables T, int G, const float2* __restrict__ rs, int64_t n_items, int h,
                 const float* __restrict__ pre_up, const float* __restrict__ pre_lo, int64_t ld,
                 const int32_t* __restrict__ nterms, float* __restrict__ lo,
-                float* __restrict__ hi, ReluOut ro, int* status) {
+                float* __restrict__ hi, EncloseOpts ro, int* status) {
   extern __shared__ float smem[];
   __shared__ float s_lohi[128][2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int group = warp >> 1;
   const bool up = warp & 1;
-  const int64_t item = (int64_t)blockIdx.x * 128 + group * 32 + lane;
+  const int64_t item = map_item(ro, (int64_t)blockIdx.x * 128 + group * 32 + lane, n_items);
   float v = 0.0f;
-  if (item < n_items) {
+  if (item >= 0) {
     int nt = nterms[item];
     if (nt < 0 || nt > ld || nt > T.mexps) {
       atomicOr(status, kStatusInvalid);
@@ -403,8 +414,8 @@ k_enclose_small(Tables T, int G, const float2* __restrict__ rs, int64_t n_items,
   if (ro.kind == nullptr) return;
   __syncthreads();
   if (threadIdx.x < 128) {
-    const int64_t it = (int64_t)blockIdx.x * 128 + threadIdx.x;
-    if (it < n_items) {
+    const int64_t it = map_item(ro, (int64_t)blockIdx.x * 128 + threadIdx.x, n_items);
+    if (it >= 0) {
       const int d = ro.degrees ? (int)ro.degrees[it] : ro.global_d;
       ro.kind[it] = (int8_t)relu_item(s_lohi[threadIdx.x][0], s_lohi[threadIdx.x][1], d,
                                       ro.coef + it * kCoefStride, ro.eps + it, status);
@@ -415,7 +426,7 @@ k_enclose_small(Tables T, int G, const float2* __restrict__ rs, int64_t n_items,
 template <int LB>
 cudaError_t launch_small(const Launch& L, const Tables& T, int G, int64_t n_items, int h,
                          const float* pre_up, const float* pre_lo, int64_t ld,
-                         const int32_t* nterms, float* lo, float* hi, ReluOut ro) {
+                         const int32_t* nterms, float* lo, float* hi, EncloseOpts ro) {
   const size_t smem = (size_t)8 * G * 32 * sizeof(float);   // <= 64 KB
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_enclose_small<LB>,

@@ -9,7 +9,7 @@ namespace bern {
 #define BERN_ENC_EXTERN(X)                                                                   \
   extern template cudaError_t launch_lb<X>(const Launch&, const Tables&, int, int64_t, int,  \
                                            const float*, const float*, int64_t, const int32_t*, \
-                                           float*, float*, ReluOut);
+                                           float*, float*, EncloseOpts);
 BERN_ENC_EXTERN(9) BERN_ENC_EXTERN(10) BERN_ENC_EXTERN(11) BERN_ENC_EXTERN(12)
 BERN_ENC_EXTERN(13) BERN_ENC_EXTERN(14) BERN_ENC_EXTERN(15) BERN_ENC_EXTERN(16)
 #undef BERN_ENC_EXTERN
@@ -18,14 +18,14 @@ __global__ void __launch_bounds__(512)
 k_enclose_generic(Tables T, int lb, int G, const float2* __restrict__ rs, int64_t n_items, int h,
                   const float* __restrict__ pre_up, const float* __restrict__ pre_lo,
                   int64_t ld, const int32_t* __restrict__ nterms, float* __restrict__ lo,
-                  float* __restrict__ hi, ReluOut ro, int* status) {
+                  float* __restrict__ hi, EncloseOpts ro, int* status) {
   extern __shared__ float smem[];
   __shared__ float s_lohi[8][2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int per_block = blockDim.x >> 6;
-  const int64_t item = (int64_t)blockIdx.x * per_block + (warp >> 1);
+  const int64_t item = map_item(ro, (int64_t)blockIdx.x * per_block + (warp >> 1), n_items);
   const bool up = warp & 1;
-  if (item < n_items) {
+  if (item >= 0) {
     int nt = nterms[item];
     if (nt < 0 || nt > ld || nt > T.mexps) {
       if (lane == 0) atomicOr(status, kStatusInvalid);
@@ -46,8 +46,8 @@ k_enclose_generic(Tables T, int lb, int G, const float2* __restrict__ rs, int64_
   if (ro.kind == nullptr) return;
   __syncthreads();
   if (threadIdx.x < per_block) {
-    const int64_t it = (int64_t)blockIdx.x * per_block + threadIdx.x;
-    if (it < n_items) {
+    const int64_t it = map_item(ro, (int64_t)blockIdx.x * per_block + threadIdx.x, n_items);
+    if (it >= 0) {
       const int d = ro.degrees ? (int)ro.degrees[it] : ro.global_d;
       ro.kind[it] = (int8_t)relu_item(s_lohi[threadIdx.x][0], s_lohi[threadIdx.x][1], d,
                                       ro.coef + it * kCoefStride, ro.eps + it, status);
@@ -58,7 +58,7 @@ k_enclose_generic(Tables T, int lb, int G, const float2* __restrict__ rs, int64_
 static cudaError_t launch_generic(const Launch& L, const Tables& T, int lb, int G,
                                   int64_t n_items, int h, const float* pre_up,
                                   const float* pre_lo, int64_t ld, const int32_t* nterms,
-                                  float* lo, float* hi, ReluOut ro) {
+                                  float* lo, float* hi, EncloseOpts ro) {
   int items = (int)std::min<int64_t>(8, (192 * 1024) / (2 * (int64_t)G * 4));
   if (items < 1) items = 1;
   const size_t smem = (size_t)2 * items * G * sizeof(float);
@@ -97,8 +97,8 @@ int effective_order(int n, int order, int64_t budget, int* grid_out) {
 static cudaError_t launch_enclose_impl(const Launch& L, const Tables& T, int64_t n_boxes, int h,
                                        int order, int64_t budget, const float* pre_up,
                                        const float* pre_lo, int64_t ld, const int32_t* nterms,
-                                       float* lo, float* hi, ReluOut ro) {
-  const int64_t n_items = n_boxes * h;
+                                       float* lo, float* hi, EncloseOpts ro) {
+  const int64_t n_items = n_boxes * h;   // with a list: its largest possible length
   if (n_items == 0) return cudaSuccess;
   int G;
   const int lb = effective_order(T.n, order, budget, &G);
@@ -130,7 +130,7 @@ cudaError_t launch_enclose(const Launch& L, const Tables& T, int64_t n_boxes, in
                            int64_t budget, const float* pre_up, const float* pre_lo, int64_t ld,
                            const int32_t* nterms, float* lo, float* hi) {
   return launch_enclose_impl(L, T, n_boxes, h, order, budget, pre_up, pre_lo, ld, nterms, lo,
-                             hi, ReluOut{nullptr, nullptr, nullptr, nullptr, 0});
+                             hi, EncloseOpts{nullptr, nullptr, nullptr, nullptr, 0});
 }
 
 cudaError_t launch_enclose_relu(const Launch& L, const Tables& T, int64_t n_boxes, int h,
@@ -139,7 +139,79 @@ cudaError_t launch_enclose_relu(const Launch& L, const Tables& T, int64_t n_boxe
                                 float* lo, float* hi, const uint8_t* degrees, int global_d,
                                 int8_t* kind, float* coef, float* eps) {
   return launch_enclose_impl(L, T, n_boxes, h, order, budget, pre_up, pre_lo, ld, nterms, lo,
-                             hi, ReluOut{kind, coef, eps, degrees, global_d});
+                             hi, EncloseOpts{kind, coef, eps, degrees, global_d});
+}
+
+// ------------------------------------------------------------------ per-box orders
+struct OrderKeys {
+  int8_t key[kMaxTableDegree + 1];   // order value -> list index, -1 if absent
+};
+
+// Stable classification of the items by their box's order (same scheme as
+// the composition queues: ballot/popc in a warp, a scan over the warps, one
+// atomic per list and block).
+__global__ void __launch_bounds__(1024)
+k_order_queue(int64_t n_items, int h, const int32_t* __restrict__ box_order, OrderKeys K,
+              ComposeScratch S, int* status) {
+  __shared__ int s_wcnt[32][kOrderQueues];
+  __shared__ int s_base[kOrderQueues];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int q = -1;
+  if (item < n_items) {
+    const int o = box_order[item / h];
+    q = (o >= 0 && o <= kMaxTableDegree) ? K.key[o] : -1;
+    if (q < 0) atomicOr(status, kStatusInvalid);
+  }
+  int rank_in_warp = 0;
+  for (int qq = 0; qq < kOrderQueues; ++qq) {
+    const unsigned m = __ballot_sync(0xffffffffu, q == qq);
+    if (q == qq) rank_in_warp = __popc(m & ((1u << lane) - 1u));
+    if (lane == 0) s_wcnt[warp][qq] = __popc(m);
+  }
+  __syncthreads();
+  if (threadIdx.x < kOrderQueues) {
+    const int qq = threadIdx.x;
+    int run = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      const int c = s_wcnt[w][qq];
+      s_wcnt[w][qq] = run;
+      run += c;
+    }
+    s_base[qq] = run ? atomicAdd(&S.qcount[qq], run) : 0;
+  }
+  __syncthreads();
+  if (q >= 0) S.queue[(int64_t)q * S.qcap + s_base[q] + s_wcnt[warp][q] + rank_in_warp] = (int)item;
+}
+
+cudaError_t launch_enclose_by_order(const Launch& L, const Tables& T, const ComposeScratch& S,
+                                    int64_t n_boxes, int h, const int32_t* box_order,
+                                    const std::vector<int>& orders, int64_t budget,
+                                    const float* pre_up, const float* pre_lo, int64_t ld,
+                                    const int32_t* nterms, float* lo, float* hi) {
+  const int64_t n_items = n_boxes * h;
+  if (n_items == 0) return cudaSuccess;
+  if ((int)orders.size() > kOrderQueues || n_items > S.qcap) return cudaErrorInvalidValue;
+  OrderKeys K;
+  for (auto& k : K.key) k = -1;
+  for (size_t i = 0; i < orders.size(); ++i) {
+    if (orders[i] < 0 || orders[i] > kMaxTableDegree) return cudaErrorInvalidValue;
+    K.key[orders[i]] = (int8_t)i;
+  }
+  cudaError_t e = cudaMemsetAsync(S.qcount, 0, kOrderQueues * sizeof(int), L.stream);
+  if (e != cudaSuccess) return e;
+  k_order_queue<<<(unsigned)((n_items + 1023) / 1024), 1024, 0, L.stream>>>(n_items, h, box_order,
+                                                                          K, S, L.status);
+  ++*L.launches;
+  for (size_t i = 0; i < orders.size(); ++i) {
+    EncloseOpts o{nullptr, nullptr, nullptr, nullptr, 0};
+    o.list = S.queue + (int64_t)i * S.qcap;
+    o.count = S.qcount + i;
+    e = launch_enclose_impl(L, T, n_boxes, h, orders[i], budget, pre_up, pre_lo, ld, nterms, lo,
+                            hi, o);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ a3 alone
