@@ -123,7 +123,8 @@ typedef struct {
   /* BERN_DEG_LEARNED: the degree MLP (n_features = BERN_DEGREE_FEATURES,
    * n_classes = BERN_DEGREE_CLASSES, host struct, device weights) and the
    * fallback: a neuron whose largest class probability is below min_conf
-   * uses global_d (the plain method's order). */
+   * (>= 0; above 1 every neuron falls back) uses global_d (the plain
+   * method's order, 0 means 2). */
   const bern_mlp* mlp;
   float min_conf;
 } bern_degree_plan;
@@ -195,6 +196,24 @@ int bern_monomials(int n, int D, uint8_t* exps);
 int bern_propagate(bern_ctx* ctx, const bern_net* net, const float* boxes,
                    int64_t n_boxes, const bern_degree_plan* plan,
                    bern_result* result);
+
+/* Per hidden neuron trace of a propagation (device pointers, caller-owned,
+ * [n_boxes x N_hidden], hidden neurons layer-major within a box): the
+ * pre-activation enclosure lo/hi (Step 1 of Sec. 5.1), the pre-activation
+ * term count, and the ReLU order the neuron used (plan or proposal).  Any
+ * pointer may be NULL.  Used to build training data for the learned
+ * component and to inspect learned plans. */
+typedef struct {
+  float* lo;
+  float* hi;
+  int32_t* nterms;
+  uint8_t* degree;
+} bern_trace;
+
+/* bern_propagate plus the trace (device pointer mode only). */
+int bern_propagate_traced(bern_ctx* ctx, const bern_net* net, const float* boxes,
+                          int64_t n_boxes, const bern_degree_plan* plan,
+                          bern_result* result, const bern_trace* trace);
 
 /* -------------------------------------------------- step entry points
  * The five steps of the path on the library's dense layout, for testing and

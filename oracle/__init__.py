@@ -77,8 +77,17 @@ def _load():
     lib.orc_propagate.argtypes = [ctypes.c_int, ip, dp, dp, dp, ip, ctypes.c_int,
                                   ctypes.c_double, ctypes.c_longlong, dp, dp, ctypes.c_int,
                                   ip, u8, dp, dp, dp, ip, ip]
+    lib.orc_propagate_cb.restype = ctypes.c_int
+    lib.orc_propagate_cb.argtypes = [ctypes.c_int, ip, dp, dp, dp, DEGREE_FN, ctypes.c_void_p,
+                                     ctypes.c_int, ctypes.c_double, ctypes.c_longlong, dp, dp,
+                                     ctypes.c_int, ip, u8, dp, dp, dp, ip, ip, ip]
     _lib = lib
     return lib
+
+
+# order chooser callback: (user, layer, neuron, lo, hi, nterms) -> order
+DEGREE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                             ctypes.c_double, ctypes.c_double, ctypes.c_longlong)
 
 
 def _dp(a):
@@ -224,11 +233,14 @@ def propagate(widths: Sequence[int], W, b, box, degrees, cap: int = 16,
     """Whole-network bounds for ONE box.
 
     widths: [n, h_1, ..., o]; W, b: per-layer float arrays (float32 values are
-    taken exactly); box: array (n, 2); degrees: an int (every hidden neuron) or
-    an array with one ReLU order per hidden neuron.
+    taken exactly); box: array (n, 2); degrees: an int (every hidden neuron),
+    an array with one ReLU order per hidden neuron, or a callable
+    choose(layer, neuron, lo, hi, nterms) -> order called for every hidden
+    neuron once its pre-activation enclosure is known (layer is 1-based;
+    nterms is the dense term count M(n, D) of its pre-activation polynomials).
     Returns a dict with 'lo', 'hi' (o,), 'upper'/'lower' (lists of polys),
-    and the per-hidden-neuron trace 'tr_lo', 'tr_hi', 'tr_case' and the
-    per-layer Bernstein order 'order'.
+    and the per-hidden-neuron trace 'tr_lo', 'tr_hi', 'tr_case', 'degree' and
+    the per-layer Bernstein order 'order'.
     """
     widths = [int(w) for w in widths]
     H = len(widths) - 1
@@ -237,14 +249,6 @@ def propagate(widths: Sequence[int], W, b, box, degrees, cap: int = 16,
     ba = np.concatenate([np.asarray(x, dtype=np.float64).reshape(-1) for x in b])
     bx = np.ascontiguousarray(np.asarray(box, dtype=np.float64).reshape(n, 2))
     n_hidden = sum(widths[1:-1])
-    if np.isscalar(degrees):
-        deg = np.full(max(n_hidden, 1), int(degrees), np.int32)
-    else:
-        deg = np.ascontiguousarray(np.asarray(degrees, dtype=np.int32).reshape(-1))
-        if len(deg) < n_hidden:
-            raise ValueError("need one degree per hidden neuron")
-        if len(deg) == 0:
-            deg = np.ones(1, np.int32)
     wid = np.array(widths, np.int32)
     out_lo = np.zeros(o)
     out_hi = np.zeros(o)
@@ -254,11 +258,39 @@ def propagate(widths: Sequence[int], W, b, box, degrees, cap: int = 16,
     nh = max(n_hidden, 1)
     tr_lo, tr_hi = np.zeros(nh), np.zeros(nh)
     tr_case = np.zeros(nh, np.int32)
+    tr_deg = np.zeros(nh, np.int32)
     tr_order = np.zeros(H, np.int32)
-    rc = _load().orc_propagate(H, _ip(wid), _dp(Wa), _dp(ba), _dp(bx), _ip(deg), cap, tau,
-                               budget, _dp(out_lo), _dp(out_hi), cap_terms, _ip(nterms),
-                               _u8(exps), _dp(coef), _dp(tr_lo), _dp(tr_hi), _ip(tr_case),
-                               _ip(tr_order))
+    if callable(degrees):
+        err = []
+
+        def _cb(user, layer, m, lo, hi, nt):
+            try:
+                return int(degrees(int(layer), int(m), float(lo), float(hi), int(nt)))
+            except Exception as ex:   # report, never raise through C
+                err.append(ex)
+                return 0
+
+        fn = DEGREE_FN(_cb)
+        rc = _load().orc_propagate_cb(H, _ip(wid), _dp(Wa), _dp(ba), _dp(bx), fn, None, cap, tau,
+                                      budget, _dp(out_lo), _dp(out_hi), cap_terms, _ip(nterms),
+                                      _u8(exps), _dp(coef), _dp(tr_lo), _dp(tr_hi),
+                                      _ip(tr_case), _ip(tr_order), _ip(tr_deg))
+        if err:
+            raise err[0]
+    else:
+        if np.isscalar(degrees):
+            deg = np.full(nh, int(degrees), np.int32)
+        else:
+            deg = np.ascontiguousarray(np.asarray(degrees, dtype=np.int32).reshape(-1))
+            if len(deg) < n_hidden:
+                raise ValueError("need one degree per hidden neuron")
+            if len(deg) == 0:
+                deg = np.ones(1, np.int32)
+        tr_deg[:n_hidden] = deg[:n_hidden]
+        rc = _load().orc_propagate(H, _ip(wid), _dp(Wa), _dp(ba), _dp(bx), _ip(deg), cap, tau,
+                                   budget, _dp(out_lo), _dp(out_hi), cap_terms, _ip(nterms),
+                                   _u8(exps), _dp(coef), _dp(tr_lo), _dp(tr_hi), _ip(tr_case),
+                                   _ip(tr_order))
     if rc:
         raise ValueError("oracle propagate failed (%d)" % rc)
     exps = exps.reshape(o, 2, cap_terms, n)
@@ -268,7 +300,7 @@ def propagate(widths: Sequence[int], W, b, box, degrees, cap: int = 16,
     lower = [(exps[j, 1, : nterms[j, 1]].copy(), coef[j, 1, : nterms[j, 1]].copy()) for j in range(o)]
     return {"lo": out_lo, "hi": out_hi, "upper": upper, "lower": lower,
             "tr_lo": tr_lo[:n_hidden], "tr_hi": tr_hi[:n_hidden],
-            "tr_case": tr_case[:n_hidden], "order": tr_order}
+            "tr_case": tr_case[:n_hidden], "degree": tr_deg[:n_hidden], "order": tr_order}
 
 
 def network_forward(widths: Sequence[int], W, b, x: np.ndarray) -> np.ndarray:

@@ -51,6 +51,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <vector>
 
@@ -376,12 +377,31 @@ void orc_eval_poly(int n, int nterms, const uint8_t* exps, const double* coef,
 //   and per layer (H entries) the Bernstein order used by the enclosure.
 // Returns 0, 1 (order exceeds grid), 2 (output capacity too small),
 // 3 (invalid input).
-int orc_propagate(int H, const int* widths, const double* W_all,
-                  const double* b_all, const double* box, const int* degrees,
-                  int cap, double tau, long long budget, double* out_lo,
-                  double* out_hi, int cap_terms, int* out_nterms,
-                  uint8_t* out_exps, double* out_coef, double* tr_lo,
-                  double* tr_hi, int* tr_case, int* tr_order) {
+}  // extern "C"
+
+namespace {
+
+// Choice of the ReLU order of hidden neuron m of hidden layer `layer`
+// (1-based; hidden_idx counts hidden neurons layer-major) from its
+// pre-activation enclosure and the dense term count M(n, D) of its
+// pre-activation polynomials (D = their largest total degree).
+using DegreeChoice = std::function<int(int layer, int m, int hidden_idx, double lo, double hi,
+                                       long long nterms)>;
+
+long long dense_terms(const Poly& p, int n) {
+  int D = 0;
+  for (const auto& t : p) D = std::max(D, total_degree(t.first));
+  double m = 1.0;
+  for (int i = 1; i <= n; ++i) m = m * (double)(D + i) / (double)i;
+  return (long long)std::llround(m);
+}
+
+int propagate_core(int H, const int* widths, const double* W_all,
+                   const double* b_all, const double* box, const DegreeChoice& choose,
+                   int cap, double tau, long long budget, double* out_lo,
+                   double* out_hi, int cap_terms, int* out_nterms,
+                   uint8_t* out_exps, double* out_coef, double* tr_lo,
+                   double* tr_hi, int* tr_case, int* tr_order, int* tr_degree) {
   const int n = widths[0];
   if (H < 1 || n < 1 || n > 8 || cap < 1) return 3;
   std::vector<Poly> up(n), lo(n);
@@ -429,8 +449,9 @@ int orc_propagate(int H, const int* widths, const double* W_all,
       double lom, him, dummy;
       if (!enclosure(pl[m], n, order, budget, &lom, &dummy)) return 1;
       if (!enclosure(pu[m], n, order, budget, &dummy, &him)) return 1;
-      int d = degrees[hidden_idx];
+      int d = choose(layer, m, hidden_idx, lom, him, dense_terms(pu[m], n));
       if (d < 1) return 3;
+      if (tr_degree) tr_degree[hidden_idx] = d;
       dmax = std::max(dmax, d);
       tr_lo[hidden_idx] = lom;
       tr_hi[hidden_idx] = him;
@@ -457,6 +478,43 @@ int orc_propagate(int H, const int* widths, const double* W_all,
     order = std::min(order * dmax, cap);
   }
   return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int orc_propagate(int H, const int* widths, const double* W_all,
+                  const double* b_all, const double* box, const int* degrees,
+                  int cap, double tau, long long budget, double* out_lo,
+                  double* out_hi, int cap_terms, int* out_nterms,
+                  uint8_t* out_exps, double* out_coef, double* tr_lo,
+                  double* tr_hi, int* tr_case, int* tr_order) {
+  DegreeChoice fixed = [degrees](int, int, int k, double, double, long long) {
+    return degrees[k];
+  };
+  return propagate_core(H, widths, W_all, b_all, box, fixed, cap, tau, budget, out_lo, out_hi,
+                        cap_terms, out_nterms, out_exps, out_coef, tr_lo, tr_hi, tr_case,
+                        tr_order, nullptr);
+}
+
+// Same, with the order of every hidden neuron chosen at run time by a
+// callback (the learned component's proposals); the chosen orders are
+// written to tr_degree.
+typedef int (*orc_degree_fn)(void* user, int layer, int m, double lo, double hi,
+                             long long nterms);
+int orc_propagate_cb(int H, const int* widths, const double* W_all,
+                     const double* b_all, const double* box, orc_degree_fn fn, void* user,
+                     int cap, double tau, long long budget, double* out_lo,
+                     double* out_hi, int cap_terms, int* out_nterms,
+                     uint8_t* out_exps, double* out_coef, double* tr_lo,
+                     double* tr_hi, int* tr_case, int* tr_order, int* tr_degree) {
+  DegreeChoice cb = [fn, user](int layer, int m, int, double lo, double hi, long long nt) {
+    return fn(user, layer, m, lo, hi, nt);
+  };
+  return propagate_core(H, widths, W_all, b_all, box, cb, cap, tau, budget, out_lo, out_hi,
+                        cap_terms, out_nterms, out_exps, out_coef, tr_lo, tr_hi, tr_case,
+                        tr_order, tr_degree);
 }
 
 }  // extern "C"

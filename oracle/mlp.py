@@ -114,3 +114,33 @@ def degree_features(lo, hi, nterms, layer: int) -> np.ndarray:
                   np.full_like(lo, layer / 8.0), np.log2(nt) / 16,
                   (lo >= 0).astype(np.float64), (hi <= 0).astype(np.float64), kink], axis=-1)
     return f.astype(np.float32)
+
+
+class DegreeChooser:
+    """Order proposals of a degree MLP for the oracle's propagation (a
+    callable for oracle.propagate): features -> bf16-emulated forward ->
+    the first maximum of the softmax; below min_conf the fallback order.
+    Records the smallest decision margin seen (the gap between the two
+    largest probabilities, and the distance of the largest from min_conf),
+    so that a caller can tell a genuine near-tie from a disagreement."""
+
+    def __init__(self, theta, min_conf: float = 0.0, fallback: int = 2, classes: int = 4):
+        self.theta = np.asarray(theta, dtype=np.float64)
+        self.min_conf, self.fallback, self.C = float(min_conf), int(fallback), int(classes)
+        self.margin = np.inf
+        self.chosen = []
+
+    def __call__(self, layer, m, lo, hi, nterms):
+        x = degree_features([lo], [hi], [nterms], layer)
+        z, _ = forward(self.theta, x.shape[1], self.C, x, emulate=True)
+        z = z[0]
+        p = np.exp(z - z.max())
+        p /= p.sum()
+        order = np.argsort(-p, kind="stable")
+        best, second = p[order[0]], p[order[1]]
+        self.margin = min(self.margin, best - second)
+        if self.min_conf > 0:
+            self.margin = min(self.margin, abs(best - self.min_conf))
+        d = int(order[0]) + 1 if best >= self.min_conf else self.fallback
+        self.chosen.append(d)
+        return d

@@ -50,7 +50,7 @@ EXPORTS = [
     "bern_monomials", "bern_propagate", "bern_init_inputs", "bern_affine",
     "bern_enclose", "bern_relu_coeffs", "bern_compose", "bern_propagate_noalloc",
     "bern_mlp_num_params", "bern_degree_features", "bern_mlp_forward", "bern_mlp_backward",
-    "bern_mlp_adam",
+    "bern_mlp_adam", "bern_propagate_traced",
 ]
 
 
@@ -78,6 +78,11 @@ class bern_degree_plan(ctypes.Structure):
                 ("degree_cap", ctypes.c_int), ("prune_tau", ctypes.c_float),
                 ("bern_budget", ctypes.c_int64),
                 ("mlp", ctypes.POINTER(bern_mlp)), ("min_conf", ctypes.c_float)]
+
+
+class bern_trace(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p), ("nterms", ctypes.c_void_p),
+                ("degree", ctypes.c_void_p)]
 
 
 class bern_result(ctypes.Structure):
@@ -125,6 +130,9 @@ def load(build_if_missing: bool = True):
         "bern_propagate_noalloc": (I, [ctypes.POINTER(bern_net), V, I64,
                                        ctypes.POINTER(bern_degree_plan),
                                        ctypes.POINTER(bern_result), V]),
+        "bern_propagate_traced": (I, [V, ctypes.POINTER(bern_net), V, I64,
+                                      ctypes.POINTER(bern_degree_plan),
+                                      ctypes.POINTER(bern_result), ctypes.POINTER(bern_trace)]),
         "bern_mlp_num_params": (I64, [I, I]),
         "bern_degree_features": (I, [V, I64, V, V, V, I, V]),
         "bern_mlp_forward": (I, [V, ctypes.POINTER(bern_mlp), I64, V, V]),
@@ -261,7 +269,7 @@ class Context:
     # ------------------------------------------------------------- whole path
     def propagate(self, widths: Sequence[int], W, b, boxes, degree=2, cap: int = 16,
                   tau: float = 0.0, budget: int = 0, cap_terms: Optional[int] = None,
-                  out=None, keys: bool = False, sync: bool = True):
+                  out=None, keys: bool = False, sync: bool = True, trace: bool = False):
         """bern_propagate on device tensors (W, b: lists of float32 CUDA tensors;
         boxes: float32 CUDA tensor [B, n, 2]).  degree: int (global), list of
         per-hidden-layer ints, or a uint8 array with one order per hidden
@@ -287,8 +295,21 @@ class Context:
         net, keep2 = make_net(widths, [_ptr(w) for w in W], [_ptr(x) for x in b])
         res = bern_result(_ptr(out["lo"]), _ptr(out["hi"]), _ptr(out["n_terms"]),
                           _ptr(out.get("keys")), _ptr(out.get("coef")), cap_terms)
-        rc = self.lib.bern_propagate(self.h, ctypes.byref(net), ctypes.c_void_p(_ptr(boxes)), B,
-                                     ctypes.byref(plan), ctypes.byref(res))
+        if trace:
+            nh = sum(widths[1:-1])
+            out["tr_lo"] = torch.empty(B, nh, device=dev, dtype=torch.float32)
+            out["tr_hi"] = torch.empty(B, nh, device=dev, dtype=torch.float32)
+            out["tr_nterms"] = torch.empty(B, nh, device=dev, dtype=torch.int32)
+            out["tr_degree"] = torch.empty(B, nh, device=dev, dtype=torch.uint8)
+            tr = bern_trace(_ptr(out["tr_lo"]), _ptr(out["tr_hi"]), _ptr(out["tr_nterms"]),
+                            _ptr(out["tr_degree"]))
+            rc = self.lib.bern_propagate_traced(self.h, ctypes.byref(net),
+                                                ctypes.c_void_p(_ptr(boxes)), B,
+                                                ctypes.byref(plan), ctypes.byref(res),
+                                                ctypes.byref(tr))
+        else:
+            rc = self.lib.bern_propagate(self.h, ctypes.byref(net), ctypes.c_void_p(_ptr(boxes)),
+                                         B, ctypes.byref(plan), ctypes.byref(res))
         _check(rc, "bern_propagate")
         if sync:
             self.check("bern_propagate")

@@ -321,7 +321,7 @@ int make_plan(const bern_net* net, const bern_degree_plan* dp, Plan& P) {
   if (P.learned) {
     const bern_mlp* m = dp->mlp;
     if (!m || m->n_features != kDegFeatures || m->n_classes != kDegClasses || !m->W1 || !m->b1 ||
-        !m->W2 || !m->b2 || !(dp->min_conf >= 0.0f && dp->min_conf <= 1.0f))
+        !m->W2 || !m->b2 || !(dp->min_conf >= 0.0f))
       return BERN_E_INVALID;
     P.mlp = *m;
     P.min_conf = dp->min_conf;
@@ -428,7 +428,11 @@ struct Chunk {
 // Launch sequence of one chunk (graph-capturable: no host sync, no alloc).
 int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
               const ComposeScratch& CS, const bern_net* net, const float* boxes, int64_t B,
-              const Chunk& ch, float* out_lo, float* out_hi, bern_result res) {
+              const Chunk& ch, float* out_lo, float* out_hi, bern_result res,
+              const bern_trace* trace) {
+  int64_t n_hidden = 0, hidden_off = 0;
+  for (const auto& l : P.L)
+    if (l.hidden) n_hidden += l.h_out;
   Launch L = c->launch_on(s);
   const int n = P.n;
   cudaError_t e = launch_init_inputs(L, n, B, boxes, ch.at<float>(P.off_z_up),
@@ -486,6 +490,11 @@ int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
                               pre_nt, lo, hi, deg, l.d, kind, coef, eps);
     }
     if (e != cudaSuccess) return map_cuda(e);
+    if (trace) {
+      e = launch_trace(L, B, l.h_out, n_hidden, hidden_off, lo, hi, pre_nt, deg, l.d, *trace);
+      if (e != cudaSuccess) return map_cuda(e);
+    }
+    hidden_off += l.h_out;
     float* post_up = ch.at<float>(l.off_post_up);
     float* post_lo = ch.at<float>(l.off_post_lo);
     int32_t* post_nt = ch.at<int32_t>(l.off_post_nt);
@@ -724,7 +733,14 @@ int bern_compose(bern_ctx* c, int n, int64_t n_boxes, int h, int degree_cap, flo
 
 int bern_propagate(bern_ctx* c, const bern_net* net, const float* boxes, int64_t n_boxes,
                    const bern_degree_plan* plan, bern_result* result) {
+  return bern_propagate_traced(c, net, boxes, n_boxes, plan, result, nullptr);
+}
+
+int bern_propagate_traced(bern_ctx* c, const bern_net* net, const float* boxes,
+                          int64_t n_boxes, const bern_degree_plan* plan, bern_result* result,
+                          const bern_trace* trace) {
   if (!c || !net || !result || n_boxes < 0 || (!boxes && n_boxes > 0)) return BERN_E_INVALID;
+  if (trace && c->mem_mode == BERN_MEM_HOST) return BERN_E_INVALID;
   Plan P;
   int rc = make_plan(net, plan, P);
   if (rc) return rc;
@@ -817,8 +833,22 @@ int bern_propagate(bern_ctx* c, const bern_net* net, const float* boxes, int64_t
     if (r.keys) r.keys = dres.keys + b0 * P.o * 2 * r.cap_terms;
     const float* bx = d_boxes + b0 * P.n * 2;
     if ((rc = fill_degrees(c, P, ch, B))) return rc;
+    bern_trace tr{};
+    const bern_trace* tr_ptr = nullptr;
+    if (trace) {
+      int64_t nh = 0;
+      for (const auto& l : P.L)
+        if (l.hidden) nh += l.h_out;
+      tr = *trace;
+      if (tr.lo) tr.lo += b0 * nh;
+      if (tr.hi) tr.hi += b0 * nh;
+      if (tr.nterms) tr.nterms += b0 * nh;
+      if (tr.degree) tr.degree += b0 * nh;
+      tr_ptr = &tr;
+    }
     if (c->use_graphs) {
       std::string key = graph_key(P, &dnet, bx, B, r, c->ws.p);
+      key.append((const char*)&tr, sizeof tr);
       key.append((const char*)&CS, sizeof CS);
       GraphEntry* g = nullptr;
       for (auto& x : c->graphs)
@@ -828,7 +858,7 @@ int bern_propagate(bern_ctx* c, const bern_net* net, const float* boxes, int64_t
         const int64_t before = c->launches;
         e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return map_cuda(e);
-        rc = run_chunk(c, c->gstream, P, *T, CS, &dnet, bx, B, ch, r.lo, r.hi, r);
+        rc = run_chunk(c, c->gstream, P, *T, CS, &dnet, bx, B, ch, r.lo, r.hi, r, tr_ptr);
         e = cudaStreamEndCapture(c->gstream, &graph);
         if (rc) return rc;
         if (e != cudaSuccess) return map_cuda(e);
@@ -854,7 +884,7 @@ int bern_propagate(bern_ctx* c, const bern_net* net, const float* boxes, int64_t
       if ((e = cudaStreamWaitEvent(c->stream, c->ev_join, 0)) != cudaSuccess) return map_cuda(e);
       c->launches += g->kernels;
     } else {
-      rc = run_chunk(c, c->stream, P, *T, CS, &dnet, bx, B, ch, r.lo, r.hi, r);
+      rc = run_chunk(c, c->stream, P, *T, CS, &dnet, bx, B, ch, r.lo, r.hi, r, tr_ptr);
       if (rc) return rc;
     }
   }

@@ -5,6 +5,8 @@
 // t_i = (x_i - dlo_i)/w_i that is the polynomial dlo_i + w_i t_i.  The width
 // is rounded up (w_i >= dhi_i - dlo_i), so t in [0,1]^n covers the whole box.
 // Layer-block layout: coefficient r of neuron i of box b at ((b*ld + r)*n + i).
+#include <algorithm>
+
 #include "device_util.cuh"
 
 namespace bern {
@@ -77,6 +79,35 @@ cudaError_t launch_pack(const Launch& L, const Tables& T, int64_t n_boxes, int o
   if (n_boxes == 0) return cudaSuccess;
   k_pack<<<(unsigned)(n_boxes * o), 128, 0, L.stream>>>(T, o, pre_up, pre_lo, ld, nterms, res,
                                                         L.status);
+  ++*L.launches;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ trace
+__global__ void k_trace(int64_t n_boxes, int h, int64_t n_hidden, int64_t off,
+                        const float* __restrict__ lo, const float* __restrict__ hi,
+                        const int32_t* __restrict__ nt, const uint8_t* __restrict__ deg,
+                        int global_d, bern_trace tr) {
+  const int64_t n = n_boxes * h;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = i / h, m = i - b * h;
+    const int64_t o = b * n_hidden + off + m;
+    if (tr.lo) tr.lo[o] = lo[i];
+    if (tr.hi) tr.hi[o] = hi[i];
+    if (tr.nterms) tr.nterms[o] = nt[i];
+    if (tr.degree) tr.degree[o] = deg ? deg[i] : (uint8_t)global_d;
+  }
+}
+
+cudaError_t launch_trace(const Launch& L, int64_t n_boxes, int h, int64_t n_hidden, int64_t off,
+                         const float* lo, const float* hi, const int32_t* nt,
+                         const uint8_t* deg, int global_d, const bern_trace& tr) {
+  const int64_t n = n_boxes * h;
+  if (n == 0) return cudaSuccess;
+  const int64_t g = std::min<int64_t>((n + 255) / 256, 152 * 8);
+  k_trace<<<(unsigned)g, 256, 0, L.stream>>>(n_boxes, h, n_hidden, off, lo, hi, nt, deg,
+                                              global_d, tr);
   ++*L.launches;
   return cudaGetLastError();
 }
