@@ -432,6 +432,56 @@ def run_ours(args, rank, world, local_rank, dist):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": round(wall * 1e3, 3)}
 
+    # ---- the learned form: degree MLP trained on the GPU, then timed like the plain form
+    learned = None
+    if not args.no_learned:
+        from paper_2211_14438_gb300 import learned as lm
+        tr_boxes = wl.config3_training_boxes(800)
+        info = lm.fit(ctx, w.net.widths, w.net.W, w.net.b, tr_boxes, cap=w.degree_cap)
+        plan = bern.Learned(info["mlp"], 0.0, w.degree)
+        out_l = {k: (torch.empty_like(v) if v is not None else None) for k, v in out.items()}
+
+        def lstep():
+            ctx.propagate(w.net.widths, Wd, bd, boxes_d, degree=plan, cap=w.degree_cap,
+                          cap_terms=cap_terms, out=out_l, sync=False)
+
+        for _ in range(args.warmup):
+            lstep()
+        if ctx.sync() != 0:
+            raise RuntimeError("learned propagate failed")
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            lstep()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        if ctx.sync() != 0:
+            raise RuntimeError("learned propagate failed")
+        ms_l = max_over_ranks(float(np.mean([s_.elapsed_time(e_) for s_, e_ in
+                                             zip(starts, ends)])), world, dist, dev)
+        width_l = float((out_l["hi"] - out_l["lo"]).float().mean().item())
+        tr = ctx.propagate(w.net.widths, Wd, bd, boxes_d, degree=plan, cap=w.degree_cap,
+                           cap_terms=cap_terms, trace=True)
+        hist = np.bincount(tr["tr_degree"].cpu().numpy().reshape(-1), minlength=5)[1:]
+        ch = info["chosen"]
+        learned = {
+            "value": round(world * B / (ms_l / 1e3), 1), "unit": "boxes/s",
+            "ms_per_step": round(ms_l, 4),
+            "mean_output_width": round(width_l, 6),
+            "plain_mean_output_width": round(float(np.mean(hi - lo)), 6),
+            "speedup_vs_plain": round(ms_step / ms_l, 4),
+            "order_histogram_1_to_4": hist.tolist(),
+            "train": {"boxes": int(len(tr_boxes)), "neurons": info["n_samples"],
+                      "seconds": round(info["seconds"], 2), "label_margin": ch["margin"],
+                      "train_acc": round(ch["train_acc"], 4),
+                      "learned_width_on_training_boxes": round(ch["learned_width"], 6),
+                      "plain_width_on_training_boxes": round(info["base_width"], 6)},
+            "plan": "BERN_DEG_LEARNED, fallback order 2, min_conf 0",
+        }
+
     cpu = None
     if pool is not None:
         idx = np.linspace(0, B - 1, 2 * cores).astype(int)
@@ -461,6 +511,7 @@ def run_ours(args, rank, world, local_rank, dist):
         "roofline": roof, "kernels": kernels,
         "kernel_pass_ms_per_step": round(total_kernel_ms, 4),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "learned": learned,
         "clocks": clocks,
     }
     return line
@@ -511,6 +562,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip training and timing the learned-degree form")
     ap.add_argument("--n-boxes", type=int, default=0,
                     help="use N evenly strided boxes of the workload (small cases for ncu)")
     args = ap.parse_args()

@@ -8,7 +8,8 @@ Labels (the method has no learned part; this is the project's reading of
 * A family of per-layer order plans (every layer in {1, 2}, plus order 3 or
   4 at the first hidden layer with {1, 2} after it) runs with the plain
   method over all training boxes: W[b, p] is box b's mean output-bound width
-  under plan p and cost[p] the plan's measured GPU time per box.
+  under plan p and cost[p] the plan's arithmetic work per box (plan_cost: a
+  deterministic count, so the labels do not depend on timing noise).
 * Each box takes the plan minimising  cost[p] + lam * W[b, p];  lam is the
   smallest value for which the mean of the chosen widths does not exceed
   (1 - margin) times the base plan's mean width, so boxes buy speed with
@@ -88,9 +89,41 @@ def plan_family(n_hidden: int) -> List[Tuple[int, ...]]:
     return fam
 
 
+def _monomials(n: int, D: int) -> int:
+    r = 1
+    for i in range(1, n + 1):
+        r = r * (D + i) // i
+    return r
+
+
+def plan_cost(widths, plan, cap=16) -> float:
+    """Fused multiply-adds per box of a per-layer order plan when every hidden
+    neuron is unstable: the affine steps (h_i h_{i-1} M_pre), the Bernstein
+    enclosures (h_i n (l+1)^n (l+2)/2 at order l = the pre-activation degree)
+    and the compositions (order 1: M_pre; order 2: M_pre^2 / 2; order d >= 3:
+    4 M_pre sum_k M(n, min(k D, cap)) for the interval Horner products)."""
+    n = int(widths[0])
+    D = 1
+    total = 0.0
+    for i in range(1, len(widths)):
+        h_in, h = int(widths[i - 1]), int(widths[i])
+        M = _monomials(n, D)
+        total += h * h_in * M + h * n * (D + 1) ** n * (D + 2) / 2.0
+        if i < len(widths) - 1:
+            d = int(plan[i - 1])
+            if d == 1:
+                total += h * M
+            elif d == 2:
+                total += h * M * M / 2.0
+            else:
+                total += h * 4.0 * M * sum(_monomials(n, min(k * D, cap)) for k in range(1, d))
+            D = min(D * d, cap)
+    return total
+
+
 def width_table(ctx, widths, W, b, boxes, plans, cap=16):
-    """W[b, p] (mean output width of box b under plan p) and cost[p] (ms per
-    box of plan p over the whole batch)."""
+    """W[b, p] (mean output width of box b under plan p) and the plan's
+    measured GPU time per box (ms, for reporting)."""
     torch = _torch()
     Wd, bd = _dev_net(widths, W, b)
     boxes_d = torch.as_tensor(np.ascontiguousarray(boxes, np.float32)).cuda()
@@ -198,11 +231,13 @@ def evaluate(ctx, widths, W, b, boxes, degree, cap=16, reps=3):
 
 
 def fit(ctx, widths, W, b, boxes, cap=16, base=2, steps=600, lr=3e-3, seed=0,
-        margins=(0.02, 0.05, 0.08, 0.12, 0.16, 0.24), slack=0.01) -> Dict:
+        margins=(0.02, 0.03, 0.04, 0.05, 0.065, 0.08, 0.1, 0.12, 0.16, 0.24),
+        slack=0.005) -> Dict:
     """Labels from the plain method on `boxes`, GPU training, and a check of
     the trained MLP driving the propagation on the same boxes.  The label
     margin grows until the learned plan's measured mean width is at most
-    (1 - slack) times the base plan's; among those the fastest is kept.
+    (1 - slack) times the base plan's (the smallest such margin buys the
+    least tightness, so it keeps the most speed).
     Returns a dict with the trained Mlp and what was learned from."""
     torch = _torch()
     t0 = time.time()
@@ -212,7 +247,8 @@ def fit(ctx, widths, W, b, boxes, cap=16, base=2, steps=600, lr=3e-3, seed=0,
     if base_plan not in plans:
         plans.append(base_plan)
     base_idx = plans.index(base_plan)
-    table, cost = width_table(ctx, widths, W, b, boxes, plans, cap)
+    table, ms_per_box = width_table(ctx, widths, W, b, boxes, plans, cap)
+    cost = np.array([plan_cost(widths, p, cap) for p in plans])
     base_w = float(table[:, base_idx].mean())
     tried, best = [], None
     for margin in margins:
@@ -224,15 +260,13 @@ def fit(ctx, widths, W, b, boxes, cap=16, base=2, steps=600, lr=3e-3, seed=0,
         acc = float((z.argmax(1).cpu().numpy() == y).mean())
         w_l, c_l = evaluate(ctx, widths, W, b, boxes, bern.Learned(m, 0.0, base), cap)
         rec = {"margin": margin, "lam": lam, "label_width": float(mean_w),
-               "label_cost": float(cost[idx].mean()), "learned_width": w_l,
-               "learned_cost": c_l, "train_acc": acc, "loss": hist,
+               "label_work": float(cost[idx].mean() / cost[base_idx]), "learned_width": w_l,
+               "learned_ms_per_box": c_l, "train_acc": acc, "loss": hist,
                "label_hist": np.bincount(y, minlength=CLASSES).tolist(),
                "plan_of_box": idx}
         tried.append(rec)
-        ok = w_l <= (1.0 - slack) * base_w
-        if ok and (best is None or c_l < best[0]["learned_cost"]):
+        if w_l <= (1.0 - slack) * base_w:   # the smallest margin that meets the target
             best = (rec, m)
-        if ok:
             break
     if best is None:    # no margin met the width target: keep the tightest one
         k = int(np.argmin([r["learned_width"] for r in tried]))
@@ -241,6 +275,7 @@ def fit(ctx, widths, W, b, boxes, cap=16, base=2, steps=600, lr=3e-3, seed=0,
         m, _ = train(ctx, Xf, torch.as_tensor(y).cuda(), steps, lr, seed)
         best = (tried[k], m)
     rec, m = best
-    return {"mlp": m, "plans": plans, "base_width": base_w, "base_cost": float(cost[base_idx]),
-            "table": table, "cost": cost, "tried": tried, "chosen": rec,
+    return {"mlp": m, "plans": plans, "base_width": base_w, "base_work": float(cost[base_idx]),
+            "table": table, "cost": cost, "ms_per_box": ms_per_box, "tried": tried,
+            "chosen": rec,
             "n_samples": int(Xf.shape[0]), "seconds": time.time() - t0}

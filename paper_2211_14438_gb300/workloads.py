@@ -142,11 +142,11 @@ def config3(n_random: int = 1024, cells: int = 16) -> Workload:
 
 def config3_training_boxes(count: int = 800, seed: int = 1002) -> np.ndarray:
     """Training boxes for the learned component on the config-3 network, drawn
-    like the benchmark's boxes but from their own seed: half are cells of the
-    16^3 grid's size (side 0.125) at random centres, half have sides
-    U(0.01, 0.5); all clipped to [-1,1]^3."""
+    like the benchmark's boxes (4/5 grid-cell sized, 1/5 random sized) but from
+    their own seed: cells of the 16^3 grid's size (side 0.125) at random
+    centres, and boxes with sides U(0.01, 0.5); all clipped to [-1,1]^3."""
     rng = np.random.default_rng(seed)
-    k = count // 2
+    k = (count * 4) // 5
     c = rng.uniform(-1 + 0.0625, 1 - 0.0625, (k, 3))
     cells = box_array(c - 0.0625, c + 0.0625)
     return np.concatenate([cells, random_boxes(rng, count - k, 3, 0.01, 0.5)], 0)
