@@ -320,6 +320,20 @@ int bern_propagate_noalloc(const bern_net* net, const float* boxes, int64_t n_bo
  * The proposals only choose orders; bern_propagate computes sound bounds for
  * whatever order it is given, so the MLP never affects soundness. */
 
+/* Features of n_boxes boxes for split-dimension proposals (2n + 2 per box,
+ * so n <= 7 for a BERN_MLP_MAX_FEATURES input), from the boxes, the root
+ * box the search started from, and a bern_result of those boxes (device
+ * pointers, coef required), for output j:  with c_up / c_lo the output's
+ * upper / lower polynomial and e_k(r) the exponent of t_k in monomial r,
+ *   x[k]      = log2(side_k / root_side_k) / 16              (k < n)
+ *   x[n + k]  = s_k / sum_i s_i,  s_k = sum_r |c_up_r| e_k(r)  (k < n)
+ *   x[2n]     = log2(max(hi_j - lo_j, 1e-30)) / 8
+ *   x[2n + 1] = log2(max(sum_r |c_up_r - c_lo_r|, 1e-30)) / 8
+ * x: [n_boxes x (2n + 2)] fp32. */
+int bern_split_features(bern_ctx* ctx, int n, int64_t n_boxes, const float* boxes,
+                        const float* root_box, const bern_result* result, int n_outputs,
+                        int output, float* x);
+
 /* Number of FP32 parameters of an MLP (W1, b1, W2, b2). */
 int64_t bern_mlp_num_params(int n_features, int n_classes);
 

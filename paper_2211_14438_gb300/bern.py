@@ -50,7 +50,7 @@ EXPORTS = [
     "bern_monomials", "bern_propagate", "bern_init_inputs", "bern_affine",
     "bern_enclose", "bern_relu_coeffs", "bern_compose", "bern_propagate_noalloc",
     "bern_mlp_num_params", "bern_degree_features", "bern_mlp_forward", "bern_mlp_backward",
-    "bern_mlp_adam", "bern_propagate_traced",
+    "bern_mlp_adam", "bern_propagate_traced", "bern_split_features",
 ]
 
 
@@ -133,6 +133,7 @@ def load(build_if_missing: bool = True):
         "bern_propagate_traced": (I, [V, ctypes.POINTER(bern_net), V, I64,
                                       ctypes.POINTER(bern_degree_plan),
                                       ctypes.POINTER(bern_result), ctypes.POINTER(bern_trace)]),
+        "bern_split_features": (I, [V, I, I64, V, V, ctypes.POINTER(bern_result), I, I, V]),
         "bern_mlp_num_params": (I64, [I, I]),
         "bern_degree_features": (I, [V, I64, V, V, V, I, V]),
         "bern_mlp_forward": (I, [V, ctypes.POINTER(bern_mlp), I64, V, V]),
@@ -250,6 +251,17 @@ class Context:
     def degree_features(self, n_items, lo, hi, nterms, layer, x):
         _check(self.lib.bern_degree_features(self.h, n_items, _ptr(lo), _ptr(hi), _ptr(nterms),
                                              int(layer), _ptr(x)), "bern_degree_features")
+
+    def split_features(self, n, boxes, root, out, output, x):
+        """Split-dimension features (bern_split_features) of the boxes of a
+        propagate() result `out` (device tensors; out must hold coef)."""
+        B = int(boxes.shape[0])
+        o = int(out["lo"].shape[1])
+        res = bern_result(_ptr(out["lo"]), _ptr(out["hi"]), _ptr(out["n_terms"]), None,
+                          _ptr(out["coef"]), int(out["coef"].shape[-1]))
+        _check(self.lib.bern_split_features(self.h, n, B, _ptr(boxes), _ptr(root),
+                                            ctypes.byref(res), o, int(output), _ptr(x)),
+               "bern_split_features")
 
     def mlp_forward(self, mlp: "Mlp", x, logits):
         _check(self.lib.bern_mlp_forward(self.h, ctypes.byref(mlp.struct()), int(x.shape[0]),

@@ -936,6 +936,23 @@ int bern_degree_features(bern_ctx* c, int64_t n_items, const float* lo, const fl
   return map_cuda(launch_degree_features(c->launch(), n_items, lo, hi, nterms, layer, x));
 }
 
+int bern_split_features(bern_ctx* c, int n, int64_t n_boxes, const float* boxes,
+                        const float* root_box, const bern_result* result, int n_outputs,
+                        int output, float* x) {
+  if (!c || n < 1 || n > kMaxVars || 2 * n + 2 > kMlpMaxF || n_boxes < 0 || !result ||
+      n_outputs < 1 || output < 0 || output >= n_outputs)
+    return BERN_E_INVALID;
+  if (n_boxes > 0 && (!boxes || !root_box || !x || !result->coef || !result->n_terms ||
+                      !result->lo || !result->hi))
+    return BERN_E_INVALID;
+  cudaSetDevice(c->device);
+  const Tables* T;
+  int rc = ensure_tables(c, n, 0, &T);
+  if (rc) return rc;
+  return map_cuda(launch_split_features(c->launch(), *T, n_boxes, n_outputs, output, boxes,
+                                        root_box, *result, x));
+}
+
 int bern_mlp_forward(bern_ctx* c, const bern_mlp* mlp, int64_t n, const float* x,
                      float* logits) {
   if (!c || !mlp_ok(mlp) || n < 0 || (n > 0 && (!x || !logits))) return BERN_E_INVALID;

@@ -143,6 +143,9 @@ cudaError_t launch_relu_coeffs(const Launch& L, int64_t n_items, const float* lo
 cudaError_t launch_trace(const Launch& L, int64_t n_boxes, int h, int64_t n_hidden, int64_t off,
                          const float* lo, const float* hi, const int32_t* nt,
                          const uint8_t* deg, int global_d, const bern_trace& tr);
+cudaError_t launch_split_features(const Launch& L, const Tables& T, int64_t n_boxes, int o, int j,
+                                  const float* boxes, const float* root, const bern_result& res,
+                                  float* x);
 cudaError_t launch_pack(const Launch& L, const Tables& T, int64_t n_boxes, int o,
                         const float* pre_up, const float* pre_lo, int64_t ld,
                         const int32_t* nterms, bern_result res);

@@ -112,4 +112,71 @@ cudaError_t launch_trace(const Launch& L, int64_t n_boxes, int h, int64_t n_hidd
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ split features
+// One block per box.  Features of output `j` (see bern_split_features).
+__global__ void __launch_bounds__(128)
+k_split_features(Tables T, int64_t n_boxes, int o, int j, const float* __restrict__ boxes,
+                 const float* __restrict__ root, bern_result res, float* __restrict__ x,
+                 int* status) {
+  __shared__ float s_part[4][kMaxVars + 1];
+  const int n = T.n, F = 2 * n + 2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t b = blockIdx.x; b < n_boxes; b += gridDim.x) {
+    const int64_t p = (b * o + j) * 2;
+    int ntu = res.n_terms[p], ntl = res.n_terms[p + 1];
+    if (ntu < 0 || ntl < 0 || ntu > res.cap_terms || ntl > res.cap_terms || ntu > T.mexps ||
+        ntl > T.mexps) {
+      if (threadIdx.x == 0) atomicOr(status, kStatusInvalid);
+      ntu = ntl = 0;
+    }
+    const float* cu = res.coef + p * res.cap_terms;
+    const float* cl = cu + res.cap_terms;
+    float sk[kMaxVars + 1];
+#pragma unroll
+    for (int k = 0; k <= kMaxVars; ++k) sk[k] = 0.0f;
+    for (int r = threadIdx.x; r < max(ntu, ntl); r += blockDim.x) {
+      const float u = r < ntu ? cu[r] : 0.0f, l = r < ntl ? cl[r] : 0.0f;
+      sk[kMaxVars] += fabsf(u - l);
+      const uint8_t* e = T.exps + (int64_t)r * n;
+#pragma unroll
+      for (int k = 0; k < kMaxVars; ++k)
+        if (k < n) sk[k] += fabsf(u) * (float)e[k];
+    }
+#pragma unroll
+    for (int k = 0; k <= kMaxVars; ++k) {
+      float v = sk[k];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (lane == 0) s_part[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float tot[kMaxVars + 1];
+      for (int k = 0; k <= kMaxVars; ++k)
+        tot[k] = s_part[0][k] + s_part[1][k] + s_part[2][k] + s_part[3][k];
+      float ssum = 0.0f;
+      for (int k = 0; k < n; ++k) ssum += tot[k];
+      float* xo = x + b * F;
+      for (int k = 0; k < n; ++k) {
+        const float side = boxes[(b * n + k) * 2 + 1] - boxes[(b * n + k) * 2];
+        const float rside = root[k * 2 + 1] - root[k * 2];
+        xo[k] = log2f(fmaxf(side, 1e-30f) / fmaxf(rside, 1e-30f)) * 0.0625f;
+        xo[n + k] = tot[k] / fmaxf(ssum, 1e-30f);
+      }
+      xo[2 * n] = log2f(fmaxf(res.hi[b * o + j] - res.lo[b * o + j], 1e-30f)) * 0.125f;
+      xo[2 * n + 1] = log2f(fmaxf(tot[kMaxVars], 1e-30f)) * 0.125f;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_split_features(const Launch& L, const Tables& T, int64_t n_boxes, int o, int j,
+                                  const float* boxes, const float* root, const bern_result& res,
+                                  float* x) {
+  if (n_boxes == 0) return cudaSuccess;
+  const unsigned g = (unsigned)std::min<int64_t>(n_boxes, 152 * 16);
+  k_split_features<<<g, 128, 0, L.stream>>>(T, n_boxes, o, j, boxes, root, res, x, L.status);
+  ++*L.launches;
+  return cudaGetLastError();
+}
+
 }  // namespace bern
