@@ -157,6 +157,12 @@ int bern_destroy(bern_ctx* ctx);
 /* Select BERN_MEM_DEVICE (default) or BERN_MEM_HOST for bern_propagate. */
 int bern_set_pointer_mode(bern_ctx* ctx, int mode);
 
+/* Largest shared-memory footprint (bytes, at most 200 KB) the Horner
+ * composition kernel may use per block before it keeps its buffers in a
+ * global workspace instead; the default is 200 KB.  Both placements compute
+ * the same values in the same order (a setting for tests and tuning). */
+int bern_set_horner_smem_limit(bern_ctx* ctx, int64_t bytes);
+
 /* Use CUDA-graph replay for bern_propagate (default 1).  With graphs on, the
  * launch sequence of one (network shape, batch size, plan, buffers) tuple is
  * captured once and replayed. */

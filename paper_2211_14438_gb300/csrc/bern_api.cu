@@ -68,13 +68,14 @@ struct bern_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   int mem_mode = BERN_MEM_DEVICE;
+  int64_t horner_smem_limit = 200 * 1024;
   int use_graphs = 1;
   cudaStream_t gstream = nullptr;   // private stream that graphs are captured on
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int* d_status = nullptr;
   int64_t launches = 0;
   std::map<int, TableSet> tables;
-  DevBuf ws, stage_in, stage_out, qbuf, mlp_ws;
+  DevBuf ws, stage_in, stage_out, qbuf, mlp_ws, hbuf;
   std::vector<GraphEntry> graphs;
   Launch launch() { return Launch{stream, d_status, &launches}; }
   Launch launch_on(cudaStream_t s) { return Launch{s, d_status, &launches}; }
@@ -251,13 +252,21 @@ int ensure_prod_tables(bern_ctx* c, int n, int Dmax, int dmax, int cap) {
 }
 
 // Composition work queues for up to `items` items.
-int ensure_queues(bern_ctx* c, int64_t items, ComposeScratch* out) {
+int ensure_queues(bern_ctx* c, int64_t items, ComposeScratch* out, size_t horner_floats = 0) {
   const size_t bytes = 256 + (size_t)kQueueLists * items * sizeof(int);
   cudaError_t e = c->qbuf.reserve(bytes);
   if (e != cudaSuccess) return map_cuda(e);
   out->qcount = (int*)c->qbuf.p;
   out->queue = (int*)((char*)c->qbuf.p + 256);
   out->qcap = items;
+  out->hws = nullptr;
+  out->hws_floats = 0;
+  out->horner_smem_limit = c->horner_smem_limit;
+  if (horner_floats) {
+    if ((e = c->hbuf.reserve(horner_floats * sizeof(float))) != cudaSuccess) return map_cuda(e);
+    out->hws = (float*)c->hbuf.p;
+    out->hws_floats = (int64_t)(c->hbuf.bytes / sizeof(float));
+  }
   return BERN_OK;
 }
 
@@ -616,6 +625,7 @@ int bern_destroy(bern_ctx* c) {
   c->stage_in.release();
   c->stage_out.release();
   c->mlp_ws.release();
+  c->hbuf.release();
   if (c->d_status) cudaFree(c->d_status);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -627,6 +637,12 @@ int bern_destroy(bern_ctx* c) {
 int bern_set_pointer_mode(bern_ctx* c, int mode) {
   if (!c || (mode != BERN_MEM_DEVICE && mode != BERN_MEM_HOST)) return BERN_E_INVALID;
   c->mem_mode = mode;
+  return BERN_OK;
+}
+
+int bern_set_horner_smem_limit(bern_ctx* c, int64_t bytes) {
+  if (!c || bytes < 0) return BERN_E_INVALID;
+  c->horner_smem_limit = bytes;
   return BERN_OK;
 }
 
@@ -718,14 +734,16 @@ int bern_compose(bern_ctx* c, int n, int64_t n_boxes, int h, int degree_cap, flo
   const Tables* T;
   int rc = ensure_tables(c, n, std::min(Dmax, 32), &T);
   if (rc) return rc;
+  size_t horner_floats = 0;
   if (global_d >= 3 || prune_tau > 0.0f) {
     if ((rc = ensure_prod_tables(c, n, Dmax, global_d, degree_cap))) return rc;
     const int Dout = std::min(degree_cap, global_d * Dmax);
-    if (horner_smem_floats(*T, Dmax, Dout) * sizeof(float) > 200 * 1024)
-      return BERN_E_UNSUPPORTED;
+    const size_t per_block = horner_smem_floats(*T, Dmax, Dout);
+    if (per_block == SIZE_MAX || per_block > ((size_t)64 << 20)) return BERN_E_UNSUPPORTED;
+    horner_floats = horner_global_floats(*T, Dmax, Dout, c->horner_smem_limit);
   }
   ComposeScratch CS;
-  if ((rc = ensure_queues(c, std::max<int64_t>(1, n_boxes * h), &CS))) return rc;
+  if ((rc = ensure_queues(c, std::max<int64_t>(1, n_boxes * h), &CS, horner_floats))) return rc;
   return map_cuda(launch_compose(c->launch(), *T, CS, n_boxes, h, degree_cap, prune_tau, kind,
                                  coef, eps, degrees, global_d, lo, hi, pre_up, pre_lo, pre_ld,
                                  pre_nterms, post_up, post_lo, post_ld, post_nterms));
@@ -756,11 +774,14 @@ int bern_propagate_traced(bern_ctx* c, const bern_net* net, const float* boxes,
   if (rc) return rc;
   for (const auto& l : P.L)
     if (l.M_pre > T->mexps || l.M_post > T->mexps) return BERN_E_UNSUPPORTED;
+  size_t horner_floats = 0;
   for (const auto& l : P.L) {
     if (!l.hidden || (l.d < 3 && P.tau == 0.0f)) continue;
     if ((rc = ensure_prod_tables(c, P.n, l.D_pre, l.d, P.cap))) return rc;
-    if (horner_smem_floats(*T, l.D_pre, l.D_post) * sizeof(float) > 200 * 1024)
-      return BERN_E_UNSUPPORTED;
+    const size_t per_block = horner_smem_floats(*T, l.D_pre, l.D_post);
+    if (per_block == SIZE_MAX || per_block > ((size_t)64 << 20)) return BERN_E_UNSUPPORTED;
+    horner_floats = std::max(horner_floats, horner_global_floats(*T, l.D_pre, l.D_post,
+                                                                 c->horner_smem_limit));
   }
 
   const bool host = c->mem_mode == BERN_MEM_HOST;
@@ -820,7 +841,7 @@ int bern_propagate_traced(bern_ctx* c, const bern_net* net, const float* boxes,
   int hmax = 1;
   for (const auto& l : P.L) hmax = std::max(hmax, l.h_out);
   ComposeScratch CS;
-  if ((rc = ensure_queues(c, chunk * hmax, &CS))) return rc;
+  if ((rc = ensure_queues(c, chunk * hmax, &CS, horner_floats))) return rc;
 
   for (int64_t b0 = 0; b0 < n_boxes; b0 += chunk) {
     const int64_t B = std::min(chunk, n_boxes - b0);

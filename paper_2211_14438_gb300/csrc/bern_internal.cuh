@@ -160,7 +160,11 @@ struct ComposeScratch {
   int* qcount;       // kComposeQueues counters (zeroed by the launcher)
   int* queue;        // kComposeQueues * qcap item indices
   int64_t qcap;
+  float* hws = nullptr;      // Horner buffers in global memory (polynomials too
+  int64_t hws_floats = 0;    // large for shared memory), kHornerGlobalBlocks slices
+  int64_t horner_smem_limit = 200 * 1024;   // bytes of shared memory before hws is used
 };
+constexpr int kHornerGlobalBlocks = 152 * 2;
 // Enclosure with a Bernstein order per box (box_order[b]); `orders` lists
 // every value box_order may take (at most kOrderQueues).  Items are sorted
 // into one list per order in S, then each order runs on its list.

@@ -26,6 +26,8 @@
 // Work layout.  One block of 256 threads per (item, bound): s~ and the two
 // ends of q (current and next) sit in shared memory; threads take output
 // monomials K of a product and walk the host-built pair list of K (I + J = K).
+// Polynomials too large for shared memory keep the same buffers in a slice
+// of a global workspace per block (same arithmetic, same order).
 #include <stdint.h>
 
 #include <algorithm>
@@ -51,8 +53,10 @@ __device__ float horner_lip(const float* a, int d, float eta) {
 
 __global__ void __launch_bounds__(kHornerThreads)
 k_compose_horner(Tables T, ComposeArgs A, ComposeScratch S, int ms_cap, int mq_cap,
-                 int* status) {
-  extern __shared__ float smem[];
+                 float* gws, int64_t gstride, int* status) {
+  extern __shared__ float smem_dyn[];
+  // the buffers: shared memory, or this block's slice of the global workspace
+  float* smem = gws ? gws + (int64_t)blockIdx.x * gstride : smem_dyn;
   __shared__ float red[32];
   __shared__ int s_nz;
   const int tid = threadIdx.x;
@@ -205,19 +209,34 @@ k_compose_horner(Tables T, ComposeArgs A, ComposeScratch S, int ms_cap, int mq_c
 
 }  // namespace
 
-// Shared-memory floats the Horner kernel needs for inputs of degree <= Dmax
-// and outputs of degree <= Dout.
+// Buffer floats (per block) the Horner kernel needs for inputs of degree
+// <= Dmax and outputs of degree <= Dout; above kHornerSmemLimit bytes the
+// buffers live in global memory.
 size_t horner_smem_floats(const Tables& T, int Dmax, int Dout) {
   const int64_t ms = num_monomials(T.n, Dmax), mq = num_monomials(T.n, Dout);
   if (ms < 0 || mq < 0) return SIZE_MAX;
   return (size_t)ms + 4 * (size_t)mq;
 }
 
+size_t horner_global_floats(const Tables& T, int Dmax, int Dout, int64_t smem_limit) {
+  const size_t f = horner_smem_floats(T, Dmax, Dout);
+  if (f == SIZE_MAX || (int64_t)(f * sizeof(float)) <= smem_limit) return 0;
+  return f * kHornerGlobalBlocks;
+}
+
 cudaError_t launch_compose_horner(const Launch& L, const Tables& T, const ComposeScratch& S,
                                   const ComposeArgs& A, int Dmax, int Dout) {
   const size_t floats = horner_smem_floats(T, Dmax, Dout);
-  if (floats > 200 * 1024 / sizeof(float)) return cudaErrorInvalidValue;
+  if (floats == SIZE_MAX) return cudaErrorInvalidValue;
   const int ms_cap = (int)num_monomials(T.n, Dmax), mq_cap = (int)num_monomials(T.n, Dout);
+  if ((int64_t)(floats * sizeof(float)) > std::min<int64_t>(S.horner_smem_limit, 200 * 1024)) {
+    if (!S.hws || S.hws_floats < (int64_t)(floats * kHornerGlobalBlocks))
+      return cudaErrorInvalidValue;
+    k_compose_horner<<<kHornerGlobalBlocks, kHornerThreads, 0, L.stream>>>(
+        T, A, S, ms_cap, mq_cap, S.hws, (int64_t)floats, L.status);
+    ++*L.launches;
+    return cudaGetLastError();
+  }
   const size_t smem = floats * sizeof(float);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_compose_horner,
@@ -226,7 +245,7 @@ cudaError_t launch_compose_horner(const Launch& L, const Tables& T, const Compos
   }
   const int per_sm = std::max(1, std::min(8, (int)((228 * 1024) / (smem + 1024))));
   k_compose_horner<<<152 * per_sm, kHornerThreads, smem, L.stream>>>(T, A, S, ms_cap, mq_cap,
-                                                                      L.status);
+                                                                      nullptr, 0, L.status);
   ++*L.launches;
   return cudaGetLastError();
 }

@@ -150,3 +150,41 @@ def test_step_compose_order3_matches_oracle(ctx):
                 ov = dense_from_dict(oracle.to_dict(ref), n, Mpost)
                 gv = arr[b, :, m].astype(np.float64)
                 assert np.abs(gv - ov).sum() <= 1e-4 * (1 + l1(ov)), (b, m, name)
+
+
+@pytest.mark.parametrize("degree,tau", [(3, 0.0), (2, 1e-3), (4, 0.0)])
+def test_global_workspace_path_matches_shared(ctx, degree, tau):
+    """The Horner kernel with its buffers in the global workspace computes
+    the same bits as with them in shared memory."""
+    widths = [3, 10, 10, 2]
+    net = wl.make_net(widths, 91)
+    boxes = random_boxes(3, 5, 91, 0.3, 1.5)
+    a = run_gpu(ctx, net, boxes, degree=degree, tau=tau)
+    ctx.set_horner_smem_limit(0)
+    try:
+        b = run_gpu(ctx, net, boxes, degree=degree, tau=tau)
+    finally:
+        ctx.set_horner_smem_limit(200 * 1024)
+    for k in ("lo", "hi", "n_terms", "coef"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_six_inputs_cap16_pruned(ctx):
+    """The branch-and-bound network shape ([6, 64 x 4, 1], cap 16) with
+    pruning: the order-2 items of the last hidden layer (3003-term inputs,
+    74613-term outputs) run in the global-workspace Horner path.  Bounds are
+    sound, term counts never exceed the unpruned ones, and the pruned bounds
+    stay close to the unpruned ones on small boxes."""
+    w = wl.config5()
+    rng = np.random.default_rng(101)
+    c = rng.uniform(-0.8, 0.8, (3, 6))
+    boxes = wl.box_array(c - 0.06, c + 0.06)
+    g0 = run_gpu(ctx, w.net, boxes, degree=2, cap=16)
+    g1 = run_gpu(ctx, w.net, boxes, degree=2, cap=16, tau=1e-7)
+    assert np.all(g1["n_terms"] <= g0["n_terms"])
+    assert np.all(g1["lo"] <= g1["hi"])
+    scale = 1 + np.abs(g0["hi"]) + np.abs(g0["lo"])
+    assert np.all(np.abs(g1["hi"] - g0["hi"]) <= 1e-3 * scale)
+    assert np.all(np.abs(g1["lo"] - g0["lo"]) <= 1e-3 * scale)
+    for bi in range(len(boxes)):
+        assert mc_check(g1, bi, w.net, boxes[bi], 5_000, rng) == 0
