@@ -156,6 +156,20 @@ int ensure_tables(bern_ctx* c, int n, int dmax, const Tables** out) {
     cudaMemcpy(b.p, rs.data(), rs.size() * sizeof(float), cudaMemcpyHostToDevice);
     ts.view.rscale[l] = (const float2*)b.p;
     ts.bufs.push_back(b);
+    std::vector<int32_t> gi, li;
+    build_enclose_tables(n, l, gi, li);
+    DevBuf bg, bl;
+    if ((e = bg.reserve(gi.size() * sizeof(int32_t))) != cudaSuccess) return map_cuda(e);
+    if ((e = bl.reserve(li.size() * sizeof(int32_t))) != cudaSuccess) {
+      bg.release();
+      return map_cuda(e);
+    }
+    cudaMemcpy(bg.p, gi.data(), gi.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(bl.p, li.data(), li.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    ts.view.gidx[l] = (const int32_t*)bg.p;
+    ts.view.lines[l] = (const int2*)bl.p;
+    ts.bufs.push_back(bg);
+    ts.bufs.push_back(bl);
   }
   ts.view.row_dmax = std::min(kMaxRowDegree, row_path_max_degree(n));
   for (int D = 0; D <= ts.view.row_dmax; ++D) {

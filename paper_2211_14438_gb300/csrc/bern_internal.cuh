@@ -99,6 +99,10 @@ struct Tables {
   // ranks r < M(n, l), for Bernstein orders l = 0..rscale_max
   const float2* rscale[kMaxEncloseOrder + 1];
   int rscale_max;
+  // per order l <= rscale_max: grid index of every graded rank < M(n, l),
+  // and per (variable k, line) the line's (base offset, prefix digit sum)
+  const int32_t* gidx[kMaxEncloseOrder + 1];
+  const int2* lines[kMaxEncloseOrder + 1];
   // row tables for squaring, input degrees 0..row_dmax (row_dmax <= 8)
   RowTable row[kMaxRowDegree + 1];
   int row_dmax;
@@ -112,6 +116,9 @@ int max_enclose_order(int n);
 void build_degree_of(int n, int De, std::vector<uint8_t>& out);
 // Host image of the reciprocal brackets for order l: 2*M(n,l) floats.
 void build_rscale(int n, int l, std::vector<float>& out);
+// Enclosure index tables for order l (grid indices of the graded ranks, and
+// the lines' base offsets and prefix digit sums; two int32 per line).
+void build_enclose_tables(int n, int l, std::vector<int32_t>& gidx, std::vector<int32_t>& lines);
 
 // ------------------------------------------------------------ launchers
 struct Launch {

@@ -16,7 +16,9 @@
 // Work layout.  One warp per polynomial; a block holds 2*P warps = P items
 // (warp 2i: lower polynomial of item i, warp 2i+1: upper).  Each warp stages
 // the (l+1)^n grid in shared memory, indexed in mixed radix (l+1) with t_1 the
-// slowest digit.  A polynomial of total degree D <= l occupies only the
+// slowest digit; host-built tables per order give each graded rank's grid
+// index and each line's base offset and prefix digit sum, so the kernels do
+// no mixed-radix arithmetic.  A polynomial of total degree D <= l occupies only the
 // simplex sum_k j_k <= D, so the transforms run from the last variable to the
 // first, each over the lines whose untransformed prefix still lies in the
 // simplex, reading only in-simplex inputs (no zero fill needed).  A line is
@@ -116,81 +118,37 @@ __device__ __forceinline__ void line_transform(const float (&x)[LB + 1], float (
   }
 }
 
-// Mixed-radix strides of the grid: pw[k] = R^(n-1-k) (loops over the 8
-// variable slots are unrolled so the array stays in registers).
-template <int R>
-__device__ __forceinline__ void grid_strides(int n, int (&pw)[kMaxVars]) {
-  int p = 1;
-#pragma unroll
-  for (int k = kMaxVars - 1; k >= 0; --k) {
-    pw[k] = k < n ? p : 0;
-    if (k < n) p *= R;
-  }
-}
-
-// Line Ln along variable k: its base offset and the digit sum of the
-// untransformed prefix (variables < k).
-template <int R>
-__device__ __forceinline__ void line_base(int Ln, int k, int n, const int (&pw)[kMaxVars],
-                                          int* base, int* psum) {
-  int rest = Ln, b = 0, ps = 0;
-#pragma unroll
-  for (int m = kMaxVars - 1; m >= 0; --m) {
-    if (m >= n || m == k) continue;
-    const int dgt = rest % R;
-    rest /= R;
-    b += dgt * pw[m];
-    if (m < k) ps += dgt;
-  }
-  *base = b;
-  *psum = ps;
-}
-
-// Grid index and total degree of graded rank r.
-__device__ __forceinline__ void term_index(const uint8_t* __restrict__ e, int n,
-                                           const int (&pw)[kMaxVars], int* idx, int* deg) {
-  int d = 0, ix = 0;
-#pragma unroll
-  for (int k = 0; k < kMaxVars; ++k) {
-    if (k < n) {
-      d += e[k];
-      ix += e[k] * pw[k];
-    }
-  }
-  *idx = ix;
-  *deg = d;
-}
-
-// Scatter the scaled coefficients of degree <= Deff into the grid; return
-// the directed sum of the one-sided ranges of all other terms.
+// Scatter the scaled coefficients of the first m_eff graded ranks (degree
+// <= Deff) into the grid at their precomputed grid indices; return the
+// directed sum of the one-sided ranges of all other terms.
 template <bool UP>
-__device__ float scatter_terms(const float* __restrict__ P, int ps, int nt, int n,
-                               const int (&pw)[kMaxVars], const Tables& T,
-                               const float2* __restrict__ rs, int Deff, float* grid) {
+__device__ float scatter_terms(const float* __restrict__ P, int ps, int nt,
+                               const int32_t* __restrict__ gidx, const float2* __restrict__ rs,
+                               int m_eff, float* grid) {
   const int lane = threadIdx.x & 31;
   float rem = 0.0f;
-  const int m_eff = T.mcount[Deff];
   for (int r = lane; r < nt; r += 32) {
     const float a = P[(int64_t)r * ps];
-    int deg, idx;
-    term_index(T.exps + (int64_t)r * n, n, pw, &idx, &deg);
-    if (deg <= Deff) {
+    if (r < m_eff) {
       const float2 sc = rs[r];
       // a / C bracketed: choose the end that rounds the product the right way
-      grid[idx] = UP ? __fmul_ru(a, a >= 0.0f ? sc.y : sc.x)
-                     : __fmul_rd(a, a >= 0.0f ? sc.x : sc.y);
+      grid[__ldg(gidx + r)] = UP ? __fmul_ru(a, a >= 0.0f ? sc.y : sc.x)
+                                 : __fmul_rd(a, a >= 0.0f ? sc.x : sc.y);
     } else {
       // the term lies in [min(0,a), max(0,a)] on the box
       rem = UP ? __fadd_ru(rem, fmaxf(a, 0.0f)) : __fadd_rd(rem, fminf(a, 0.0f));
     }
   }
   // a ragged count (not a full graded prefix): missing simplex entries are 0
-  for (int r = nt + lane; r < m_eff; r += 32) {
-    int deg, idx;
-    term_index(T.exps + (int64_t)r * n, n, pw, &idx, &deg);
-    grid[idx] = 0.0f;
-  }
+  for (int r = nt + lane; r < m_eff; r += 32) grid[__ldg(gidx + r)] = 0.0f;
   return rem;
+}
+
+// R^e for small e
+__device__ __forceinline__ int ipow(int R, int e) {
+  int p = 1;
+  for (int i = 0; i < e; ++i) p *= R;
+  return p;
 }
 
 // Total degree of a graded prefix of nt terms (the smallest D with M(n,D) >= nt).
@@ -203,25 +161,20 @@ __device__ float enclose_warp(const float* __restrict__ P, int ps, int nt, int n
                               const Tables& T, const float2* __restrict__ rs, float* grid) {
   const int lane = threadIdx.x & 31;
   constexpr int R = LB + 1;
-  int pw[kMaxVars];
-  grid_strides<R>(n, pw);
   const int Dnt = prefix_degree(T, nt);
   const int Deff = Dnt < LB ? Dnt : LB;
-  float rem = scatter_terms<UP>(P, ps, nt, n, pw, T, rs, Deff, grid);
+  float rem = scatter_terms<UP>(P, ps, nt, T.gidx[LB], rs, T.mcount[Deff], grid);
   __syncwarp();
   float best = UP ? -CUDART_INF_F : CUDART_INF_F;
-  int nlines = 1;
-  for (int m = 0; m < n - 1; ++m) nlines *= R;
+  const int nlines = ipow(R, n - 1);
+  const int2* __restrict__ lines = T.lines[LB];
   for (int k = n - 1; k >= 0; --k) {
     // lines along variable k: prefix digits (variables < k) untransformed,
     // suffix digits (variables > k) transformed
-    int sk = 1;
-#pragma unroll
-    for (int m = 0; m < kMaxVars; ++m)
-      if (m == k) sk = pw[m];
+    const int sk = ipow(R, n - 1 - k);
     for (int Ln = lane; Ln < nlines; Ln += 32) {
-      int base, psum;
-      line_base<R>(Ln, k, n, pw, &base, &psum);
+      const int2 ln = __ldg(lines + (int64_t)k * nlines + Ln);
+      const int base = ln.x, psum = ln.y;
       if (psum > Deff) continue;
       const int p = Deff - psum;
       float x[R], y[R];
@@ -263,7 +216,7 @@ __device__ __forceinline__ int64_t map_item(const EncloseOpts& o, int64_t idx, i
 }
 
 template <int LB>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, 3)
 k_enclose(Tables T, int G, const float2* __restrict__ rs, int64_t n_items, int h,
           const float* __restrict__ pre_up, const float* __restrict__ pre_lo, int64_t ld,
           const int32_t* __restrict__ nterms, float* __restrict__ lo, float* __restrict__ hi,
@@ -332,39 +285,30 @@ template <int LB, bool UP>
 __device__ float enclose_lane(const float* __restrict__ P, int ps, int nt, int n,
                               const Tables& T, const float2* __restrict__ rs, float* grid) {
   constexpr int R = LB + 1;
-  int pw[kMaxVars];
-  grid_strides<R>(n, pw);
+  const int32_t* __restrict__ gidx = T.gidx[LB];
+  const int2* __restrict__ lines = T.lines[LB];
   const int Dnt = prefix_degree(T, nt);
   const int Deff = Dnt < LB ? Dnt : LB;
+  const int m_eff = T.mcount[Deff];
   float rem = 0.0f;
   for (int r = 0; r < nt; ++r) {
     const float a = P[(int64_t)r * ps];
-    int deg, idx;
-    term_index(T.exps + (int64_t)r * n, n, pw, &idx, &deg);
-    if (deg <= Deff) {
+    if (r < m_eff) {
       const float2 sc = rs[r];
-      grid[idx * 32] = UP ? __fmul_ru(a, a >= 0.0f ? sc.y : sc.x)
-                          : __fmul_rd(a, a >= 0.0f ? sc.x : sc.y);
+      grid[__ldg(gidx + r) * 32] = UP ? __fmul_ru(a, a >= 0.0f ? sc.y : sc.x)
+                                      : __fmul_rd(a, a >= 0.0f ? sc.x : sc.y);
     } else {
       rem = UP ? __fadd_ru(rem, fmaxf(a, 0.0f)) : __fadd_rd(rem, fminf(a, 0.0f));
     }
   }
-  for (int r = nt; r < T.mcount[Deff]; ++r) {
-    int deg, idx;
-    term_index(T.exps + (int64_t)r * n, n, pw, &idx, &deg);
-    grid[idx * 32] = 0.0f;
-  }
+  for (int r = nt; r < m_eff; ++r) grid[__ldg(gidx + r) * 32] = 0.0f;
   float best = UP ? -CUDART_INF_F : CUDART_INF_F;
-  int nlines = 1;
-  for (int m = 0; m < n - 1; ++m) nlines *= R;
+  const int nlines = ipow(R, n - 1);
   for (int k = n - 1; k >= 0; --k) {
-    int sk = 1;
-#pragma unroll
-    for (int m = 0; m < kMaxVars; ++m)
-      if (m == k) sk = pw[m];
+    const int sk = ipow(R, n - 1 - k);
     for (int Ln = 0; Ln < nlines; ++Ln) {
-      int base, psum;
-      line_base<R>(Ln, k, n, pw, &base, &psum);
+      const int2 ln = __ldg(lines + (int64_t)k * nlines + Ln);
+      const int base = ln.x, psum = ln.y;
       if (psum > Deff) continue;
       const int p = Deff - psum;
       float x[R], y[R];
@@ -451,37 +395,18 @@ __device__ float enclose_warp_generic(const float* __restrict__ P, int ps, int n
                                       float* grid) {
   const int lane = threadIdx.x & 31;
   const int R = lb + 1;
-  int pw[kMaxVars];
-  {
-    int p = 1;
-#pragma unroll
-    for (int k = kMaxVars - 1; k >= 0; --k) {
-      pw[k] = k < n ? p : 0;
-      if (k < n) p *= R;
-    }
-  }
   const int Dnt = prefix_degree(T, nt);
   const int Deff = Dnt < lb ? Dnt : lb;
-  float rem = scatter_terms<UP>(P, ps, nt, n, pw, T, rs, Deff, grid);
+  float rem = scatter_terms<UP>(P, ps, nt, T.gidx[lb], rs, T.mcount[Deff], grid);
   __syncwarp();
   float best = UP ? -CUDART_INF_F : CUDART_INF_F;
-  int nlines = 1;
-  for (int m = 0; m < n - 1; ++m) nlines *= R;
+  const int nlines = ipow(R, n - 1);
+  const int2* __restrict__ lines = T.lines[lb];
   for (int k = n - 1; k >= 0; --k) {
-    int sk = 1;
-#pragma unroll
-    for (int m = 0; m < kMaxVars; ++m)
-      if (m == k) sk = pw[m];
+    const int sk = ipow(R, n - 1 - k);
     for (int Ln = lane; Ln < nlines; Ln += 32) {
-      int rest = Ln, base = 0, psum = 0;
-#pragma unroll
-      for (int m = kMaxVars - 1; m >= 0; --m) {
-        if (m >= n || m == k) continue;
-        const int dgt = rest % R;
-        rest /= R;
-        base += dgt * pw[m];
-        if (m < k) psum += dgt;
-      }
+      const int2 ln = __ldg(lines + (int64_t)k * nlines + Ln);
+      const int base = ln.x, psum = ln.y;
       if (psum > Deff) continue;
       const int p = Deff - psum;
       float* c = grid + base;

@@ -96,11 +96,15 @@ int upload_tables(DeviceSlot& s, int n, int dmax, int deg_exps, cudaStream_t str
   bern::build_degree_of(n, deg_exps, dof);
   size_t off_dof = put(dof.data(), dof.size());
   const int rmax = bern::max_enclose_order(n);
-  std::vector<size_t> off_rs(rmax + 1);
+  std::vector<size_t> off_rs(rmax + 1), off_gi(rmax + 1), off_li(rmax + 1);
   for (int l = 0; l <= rmax; ++l) {
     std::vector<float> rs;
     bern::build_rscale(n, l, rs);
     off_rs[l] = put(rs.data(), rs.size() * sizeof(float));
+    std::vector<int32_t> gi, li;
+    bern::build_enclose_tables(n, l, gi, li);
+    off_gi[l] = put(gi.data(), gi.size() * sizeof(int32_t));
+    off_li[l] = put(li.data(), li.size() * sizeof(int32_t));
     if (img.size() > kNoAllocTableBytes) return BERN_E_UNSUPPORTED;
   }
   const int row_dmax = std::min(bern::kMaxRowDegree, bern::row_path_max_degree(n));
@@ -153,7 +157,11 @@ int upload_tables(DeviceSlot& s, int n, int dmax, int deg_exps, cudaStream_t str
     rt.out_ranks = (const int32_t*)(s.tables + roff[D].out_ranks);
   }
   v.rscale_max = rmax;
-  for (int l = 0; l <= rmax; ++l) v.rscale[l] = (const float2*)(s.tables + off_rs[l]);
+  for (int l = 0; l <= rmax; ++l) {
+    v.rscale[l] = (const float2*)(s.tables + off_rs[l]);
+    v.gidx[l] = (const int32_t*)(s.tables + off_gi[l]);
+    v.lines[l] = (const int2*)(s.tables + off_li[l]);
+  }
   for (int D = 0; D <= dmax; ++D) {
     v.sq[D].ptr = (const int32_t*)(s.tables + off_ptr[D]);
     v.sq[D].pairs = (const uint32_t*)(s.tables + off_pairs[D]);

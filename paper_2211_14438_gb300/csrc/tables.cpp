@@ -281,3 +281,48 @@ void build_rscale(int n, int l, std::vector<float>& out) {
 }
 
 }  // namespace bern
+
+namespace bern {
+
+// Enclosure index tables for order l (grid radix R = l + 1, variable 0 the
+// slowest digit): gidx[r] = grid index of graded rank r < M(n, l); lines
+// holds, for each variable k and each line Ln along k (Ln enumerates the
+// digits of the other variables, the highest variable first), the pair
+// (base offset, digit sum of the variables before k).
+void build_enclose_tables(int n, int l, std::vector<int32_t>& gidx, std::vector<int32_t>& lines) {
+  const int R = l + 1;
+  std::vector<int64_t> pw(n);
+  int64_t p = 1;
+  for (int k = n - 1; k >= 0; --k) {
+    pw[k] = p;
+    p *= R;
+  }
+  std::vector<uint8_t> ex;
+  graded_monomials(n, l, ex);
+  const int64_t m = num_monomials(n, l);
+  gidx.assign((size_t)m, 0);
+  for (int64_t r = 0; r < m; ++r) {
+    int64_t ix = 0;
+    for (int k = 0; k < n; ++k) ix += ex[(size_t)r * n + k] * pw[k];
+    gidx[(size_t)r] = (int32_t)ix;
+  }
+  int64_t nlines = 1;
+  for (int k = 0; k < n - 1; ++k) nlines *= R;
+  lines.assign((size_t)(2 * n * nlines), 0);
+  for (int k = 0; k < n; ++k)
+    for (int64_t Ln = 0; Ln < nlines; ++Ln) {
+      int64_t rest = Ln, base = 0;
+      int psum = 0;
+      for (int mm = n - 1; mm >= 0; --mm) {
+        if (mm == k) continue;
+        const int dgt = (int)(rest % R);
+        rest /= R;
+        base += dgt * pw[mm];
+        if (mm < k) psum += dgt;
+      }
+      lines[(size_t)(2 * (k * nlines + Ln))] = (int32_t)base;
+      lines[(size_t)(2 * (k * nlines + Ln)) + 1] = psum;
+    }
+}
+
+}  // namespace bern
