@@ -8,6 +8,16 @@
 // round-down FMAs, so each computed coefficient bounds the exact one from the
 // correct side; with t^K >= 0 on the box that bounds the polynomial values.
 //
+// The tiled kernel uses the midpoint-radius form of the same step: with
+// c = fl((up + lo) / 2) and r >= max(up - c, c - lo) (rounded up), every
+// input coefficient lies in [c - r, c + r], and for any weight w
+//   w+ up + w- lo = w c + |w| r  (exactly, when c, r are exact),
+//   w x <= w c + |w| r  for every x in [c - r, c + r];
+// so pre_up = RU(b + sum_j w c) + RU(sum_j |w| r) and pre_lo = RD(b + sum_j
+// w c) - RU(sum_j |w| r) bound the sign-split sums from the correct side
+// (r exceeds (up - lo)/2 by at most an ulp of c).  This needs three FMAs per
+// product and no per-product select of the operand by the sign of w.
+//
 // With the layer-block layout (coefficient r of neuron j of box b at
 // ((b*ld + r)*h + j)) each box is a row-major [M x h_in] matrix per bound and
 // the step is the product with W^T: a small GEMM per box.  A block computes a
@@ -30,8 +40,9 @@ k_affine(int h_out, int h_in, const float* __restrict__ W, const float* __restri
   constexpr int NT = (BM / TM) * (BR / TR);
   constexpr int TX = BM / TM;                       // threads along m
   __shared__ float sW[KC][BM];
-  __shared__ float sU[BR][KC + 1];
-  __shared__ float sL[BR][KC + 1];
+  __shared__ float sA[KC][BM];        // |W|
+  __shared__ float sU[BR][KC + 1];    // midpoints c
+  __shared__ float sL[BR][KC + 1];    // radii r
   __shared__ int sMax;
   extern __shared__ int32_t sN[];                   // h_in term counts
   const int64_t b = blockIdx.x;
@@ -63,56 +74,64 @@ k_affine(int h_out, int h_in, const float* __restrict__ W, const float* __restri
   if (r0 >= M) return;
 
   const int tm = tid % TX, tr = tid / TX;
-  float up[TM][TR], lo[TM][TR];
+  float uc[TM][TR], lc[TM][TR], rad[TM][TR];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int k = 0; k < TR; ++k) {
       const int m = m0 + tm * TM + i, r = r0 + tr * TR + k;
       const float b0 = (r == 0 && m < h_out) ? bias[m] : 0.0f;
-      up[i][k] = b0;
-      lo[i][k] = b0;
+      uc[i][k] = b0;
+      lc[i][k] = b0;
+      rad[i][k] = 0.0f;
     }
   const float* gU = in_up + (b * in_ld) * h_in;
   const float* gL = in_lo + (b * in_ld) * h_in;
   for (int j0 = 0; j0 < h_in; j0 += KC) {
-    // stage W[m0.., j0..] transposed, and the input rows r0.. of columns j0..
+    // stage W[m0.., j0..] transposed (and |W|), and the midpoints and radii
+    // of the input rows r0.. of columns j0..
     for (int idx = tid; idx < KC * BM; idx += NT) {
       const int mm = idx % BM, jj = idx / BM;
       const int m = m0 + mm, j = j0 + jj;
-      sW[jj][mm] = (m < h_out && j < h_in) ? W[(int64_t)m * h_in + j] : 0.0f;
+      const float w = (m < h_out && j < h_in) ? W[(int64_t)m * h_in + j] : 0.0f;
+      sW[jj][mm] = w;
+      sA[jj][mm] = fabsf(w);
     }
     for (int idx = tid; idx < KC * BR; idx += NT) {
       const int jj = idx % KC, rr = idx / KC;
       const int j = j0 + jj, r = r0 + rr;
-      float u = 0.0f, l = 0.0f;
+      float c = 0.0f, rd = 0.0f;
       if (j < h_in && r < sN[j]) {
-        u = gU[(int64_t)r * h_in + j];
-        l = gL[(int64_t)r * h_in + j];
+        const float u = gU[(int64_t)r * h_in + j];
+        const float l = gL[(int64_t)r * h_in + j];
+        c = __fmaf_rn(0.5f, u, 0.5f * l);
+        rd = fmaxf(__fsub_ru(u, c), __fsub_ru(c, l));
       }
-      sU[rr][jj] = u;
-      sL[rr][jj] = l;
+      sU[rr][jj] = c;
+      sL[rr][jj] = rd;
     }
     __syncthreads();
 #pragma unroll 4
     for (int jj = 0; jj < KC; ++jj) {
-      float w[TM], u[TR], l[TR];
-#pragma unroll
-      for (int i = 0; i < TM; ++i) w[i] = sW[jj][tm * TM + i];
-#pragma unroll
-      for (int k = 0; k < TR; ++k) {
-        u[k] = sU[tr * TR + k][jj];
-        l[k] = sL[tr * TR + k][jj];
-      }
+      float w[TM], a[TM], c[TR], rd[TR];
 #pragma unroll
       for (int i = 0; i < TM; ++i) {
-        const bool pos = w[i] > 0.0f;
+        w[i] = sW[jj][tm * TM + i];
+        a[i] = sA[jj][tm * TM + i];
+      }
+#pragma unroll
+      for (int k = 0; k < TR; ++k) {
+        c[k] = sU[tr * TR + k][jj];
+        rd[k] = sL[tr * TR + k][jj];
+      }
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int k = 0; k < TR; ++k) {
-          up[i][k] = __fmaf_ru(w[i], pos ? u[k] : l[k], up[i][k]);
-          lo[i][k] = __fmaf_rd(w[i], pos ? l[k] : u[k], lo[i][k]);
+          uc[i][k] = __fmaf_ru(w[i], c[k], uc[i][k]);
+          lc[i][k] = __fmaf_rd(w[i], c[k], lc[i][k]);
+          rad[i][k] = __fmaf_ru(a[i], rd[k], rad[i][k]);
         }
-      }
     }
     __syncthreads();
   }
@@ -125,11 +144,144 @@ k_affine(int h_out, int h_in, const float* __restrict__ W, const float* __restri
       const int m = m0 + tm * TM + i;
       if (m < h_out) {
         const int64_t o = (b * out_ld + r) * h_out + m;
-        out_up[o] = up[i][k];
-        out_lo[o] = lo[i][k];
+        out_up[o] = __fadd_ru(uc[i][k], rad[i][k]);
+        out_lo[o] = __fsub_rd(lc[i][k], rad[i][k]);
       }
     }
   }
+}
+
+// Persistent form for the wide layers: a block keeps W and |W| (all h_out x
+// h_in, k-major) in shared memory for the whole launch and walks boxes; per
+// box it stages 64-row tiles of the input as midpoints and radii, and every
+// thread accumulates a 4 (neurons) x 4 (rows) tile of the three sums per
+// 64-neuron slice of the layer.
+constexpr int kPRows = 64;
+constexpr int kPThreads = 256;
+
+__global__ void __launch_bounds__(kPThreads, 3)
+k_affine_persistent(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
+                    const float* __restrict__ bias, const float* __restrict__ in_up,
+                    const float* __restrict__ in_lo, int64_t in_ld,
+                    const int32_t* __restrict__ in_nterms, float* __restrict__ out_up,
+                    float* __restrict__ out_lo, int64_t out_ld, int32_t* __restrict__ out_nterms,
+                    int* status) {
+  extern __shared__ float smem[];
+  const int hp = (h_out + 63) & ~63;                 // neurons padded to 64
+  float* sW = smem;                                  // [h_in][hp]
+  float* sA = sW + (size_t)h_in * hp;                // |W|
+  float* sC = sA + (size_t)h_in * hp;                // [kPRows][h_in + 1] midpoints
+  float* sR = sC + (size_t)kPRows * (h_in + 1);      // radii
+  int* sN = reinterpret_cast<int*>(sR + (size_t)kPRows * (h_in + 1));   // [h_in]
+  __shared__ int sMax;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < h_in * hp; idx += kPThreads) {
+    const int j = idx / hp, m = idx - j * hp;
+    const float w = m < h_out ? W[(int64_t)m * h_in + j] : 0.0f;
+    sW[idx] = w;
+    sA[idx] = fabsf(w);
+  }
+  const int tm = tid & 15, tr = tid >> 4;            // 16 x 16 threads
+  const int ldx = h_in + 1;
+  for (int64_t b = blockIdx.x; b < n_boxes; b += gridDim.x) {
+    if (tid == 0) sMax = 0;
+    __syncthreads();                                 // also: W staged, previous box done
+    int mloc = 0;
+    for (int j = tid; j < h_in; j += kPThreads) {
+      int v = in_nterms[b * h_in + j];
+      if (v < 0 || v > in_ld) {
+        atomicOr(status, kStatusInvalid);
+        v = 0;
+      }
+      sN[j] = v;
+      mloc = max(mloc, v);
+    }
+    mloc = warp_imax(mloc);
+    if ((tid & 31) == 0) atomicMax(&sMax, mloc);
+    __syncthreads();
+    const int M = max(1, sMax);
+    if (M > out_ld) {
+      if (tid == 0) atomicOr(status, kStatusCapacity);
+      continue;
+    }
+    for (int m = tid; m < h_out; m += kPThreads) out_nterms[b * h_out + m] = M;
+    const float* gU = in_up + (b * in_ld) * h_in;
+    const float* gL = in_lo + (b * in_ld) * h_in;
+    for (int r0 = 0; r0 < M; r0 += kPRows) {
+      __syncthreads();                               // the previous tile is consumed
+      for (int idx = tid; idx < kPRows * h_in; idx += kPThreads) {
+        const int rr = idx / h_in, j = idx - rr * h_in;
+        const int r = r0 + rr;
+        float c = 0.0f, rd = 0.0f;
+        if (r < M && r < sN[j]) {
+          const float u = gU[(int64_t)r * h_in + j];
+          const float l = gL[(int64_t)r * h_in + j];
+          c = __fmaf_rn(0.5f, u, 0.5f * l);
+          rd = fmaxf(__fsub_ru(u, c), __fsub_ru(c, l));
+        }
+        sC[rr * ldx + j] = c;
+        sR[rr * ldx + j] = rd;
+      }
+      __syncthreads();
+      for (int m0 = 0; m0 < h_out; m0 += 64) {
+        float uc[4][4], lc[4][4], rad[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int m = m0 + tm * 4 + i, r = r0 + tr * 4 + k;
+            const float b0 = (r == 0 && m < h_out) ? bias[m] : 0.0f;
+            uc[i][k] = b0;
+            lc[i][k] = b0;
+            rad[i][k] = 0.0f;
+          }
+        const float* pw = sW + m0 + tm * 4;
+        const float* pa = sA + m0 + tm * 4;
+        const float* pc = sC + (tr * 4) * ldx;
+        const float* pr = sR + (tr * 4) * ldx;
+#pragma unroll 4
+        for (int j = 0; j < h_in; ++j) {
+          const float4 w4 = *reinterpret_cast<const float4*>(pw + (size_t)j * hp);
+          const float4 a4 = *reinterpret_cast<const float4*>(pa + (size_t)j * hp);
+          const float w[4] = {w4.x, w4.y, w4.z, w4.w}, a[4] = {a4.x, a4.y, a4.z, a4.w};
+          float c[4], rd[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            c[k] = pc[k * ldx + j];
+            rd[k] = pr[k * ldx + j];
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              uc[i][k] = __fmaf_ru(w[i], c[k], uc[i][k]);
+              lc[i][k] = __fmaf_rd(w[i], c[k], lc[i][k]);
+              rad[i][k] = __fmaf_ru(a[i], rd[k], rad[i][k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int r = r0 + tr * 4 + k;
+          if (r >= M) continue;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int m = m0 + tm * 4 + i;
+            if (m < h_out) {
+              const int64_t o = (b * out_ld + r) * h_out + m;
+              out_up[o] = __fadd_ru(uc[i][k], rad[i][k]);
+              out_lo[o] = __fsub_rd(lc[i][k], rad[i][k]);
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+static size_t persistent_smem(int h_out, int h_in) {
+  const size_t hp = (size_t)((h_out + 63) & ~63);
+  return (2 * hp * h_in + 2 * (size_t)kPRows * (h_in + 1)) * sizeof(float) +
+         (size_t)h_in * sizeof(int);
 }
 
 // Narrow output layers (h_out <= 4, e.g. a network's output): one thread per
@@ -199,7 +351,7 @@ k_affine_narrow(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ 
     // rows are 16-byte aligned: read them as float4
     const float4* pu4 = reinterpret_cast<const float4*>(pu);
     const float4* pl4 = reinterpret_cast<const float4*>(pl);
-#pragma unroll 2
+#pragma unroll 4
     for (int j4 = 0; j4 < (h_in >> 2); ++j4) {
       const float4 u = __ldg(pu4 + j4), l = __ldg(pl4 + j4);
       step(4 * j4, u.x, l.x);
@@ -217,6 +369,100 @@ k_affine_narrow(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ 
       const int64_t o = (b * out_ld + r) * h_out + m;
       out_up[o] = up[m];
       out_lo[o] = lo[m];
+    }
+  }
+}
+
+// Narrow layers (h_out <= 4), warp form: a block takes one box and 64
+// monomial rows, a warp one row at a time with its lanes over the inputs j
+// (coalesced row reads; each lane keeps its inputs' weights and term counts
+// in registers); the per-lane partial sums are combined by a directed warp
+// reduction (round-up for the upper sum, round-down for the lower one), which
+// bounds the exact sum from the correct side in any order.
+constexpr int kNarrowMaxJ = 8;                       // h_in <= 256
+
+template <int HO, int JQ>
+__global__ void __launch_bounds__(256)
+k_affine_narrow_warp(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
+                     const float* __restrict__ bias, const float* __restrict__ in_up,
+                     const float* __restrict__ in_lo, int64_t in_ld,
+                     const int32_t* __restrict__ in_nterms, float* __restrict__ out_up,
+                     float* __restrict__ out_lo, int64_t out_ld, int32_t* __restrict__ out_nterms,
+                     int* status) {
+  __shared__ int sMax;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t b = blockIdx.x;
+  if (threadIdx.x == 0) sMax = 0;
+  __syncthreads();
+  float w[HO][JQ];
+  int nt[JQ];
+  int mloc = 0;
+#pragma unroll
+  for (int q = 0; q < JQ; ++q) {
+    const int j = lane + 32 * q;
+    int v = 0;
+    if (j < h_in) {
+      v = in_nterms[b * h_in + j];
+      if (v < 0 || v > in_ld) {
+        atomicOr(status, kStatusInvalid);
+        v = 0;
+      }
+    }
+    nt[q] = v;
+    mloc = max(mloc, v);
+#pragma unroll
+    for (int m = 0; m < HO; ++m) w[m][q] = (j < h_in && m < h_out) ? W[(int64_t)m * h_in + j] : 0.0f;
+  }
+  mloc = warp_imax(mloc);
+  if (lane == 0) atomicMax(&sMax, mloc);
+  __syncthreads();
+  const int M = max(1, sMax);
+  if (M > out_ld) {
+    if (threadIdx.x == 0 && blockIdx.y == 0) atomicOr(status, kStatusCapacity);
+    return;
+  }
+  if (blockIdx.y == 0 && threadIdx.x < h_out) out_nterms[b * h_out + threadIdx.x] = M;
+  const int r_end = min(M, (int)(blockIdx.y + 1) * 64);
+  for (int r = blockIdx.y * 64 + warp; r < r_end; r += 8) {
+    const float* pu = in_up + (b * in_ld + r) * h_in;
+    const float* pl = in_lo + (b * in_ld + r) * h_in;
+    float u[JQ], l[JQ];
+#pragma unroll
+    for (int q = 0; q < JQ; ++q) {
+      const int j = lane + 32 * q;
+      const bool live = j < h_in && r < nt[q];
+      u[q] = live ? __ldg(pu + j) : 0.0f;
+      l[q] = live ? __ldg(pl + j) : 0.0f;
+    }
+    float up[HO], lo[HO];
+#pragma unroll
+    for (int m = 0; m < HO; ++m) {
+      up[m] = 0.0f;
+      lo[m] = 0.0f;
+#pragma unroll
+      for (int q = 0; q < JQ; ++q) {
+        const bool pos = w[m][q] > 0.0f;
+        up[m] = __fmaf_ru(w[m][q], pos ? u[q] : l[q], up[m]);
+        lo[m] = __fmaf_rd(w[m][q], pos ? l[q] : u[q], lo[m]);
+      }
+      up[m] = warp_dsum<true>(up[m]);
+      lo[m] = warp_dsum<false>(lo[m]);
+    }
+    if (lane < h_out) {
+      float vu = 0.0f, vl = 0.0f;
+#pragma unroll
+      for (int m = 0; m < HO; ++m)
+        if (m == lane) {
+          vu = up[m];
+          vl = lo[m];
+        }
+      if (r == 0) {
+        vu = __fadd_ru(vu, bias[lane]);
+        vl = __fadd_rd(vl, bias[lane]);
+      }
+      const int64_t o = (b * out_ld + r) * h_out + lane;
+      out_up[o] = vu;
+      out_lo[o] = vl;
     }
   }
 }
@@ -253,11 +499,23 @@ cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
   if (n_boxes > 0x7fffffff || (std::min(in_ld, out_ld) + 15) / 16 > 65535)
     return cudaErrorInvalidValue;
   const bool few_rows = std::min(in_ld, out_ld) <= 16;     // short polynomials: short tiles
+  const size_t psmem = persistent_smem(h_out, h_in);
+  if (h_out >= 32 && !few_rows && psmem <= 72 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_affine_persistent,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = std::min<int64_t>(n_boxes, 152 * 3);
+    k_affine_persistent<<<(unsigned)blocks, kPThreads, psmem, L.stream>>>(
+        n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld, in_nterms, out_up, out_lo, out_ld,
+        out_nterms, L.status);
+    ++*L.launches;
+    return cudaGetLastError();
+  }
   if (h_out >= 32 && few_rows)
     return launch_cfg<64, 16, 4, 1, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
                                         in_nterms, out_up, out_lo, out_ld, out_nterms);
   if (h_out >= 32)
-    return launch_cfg<64, 64, 4, 4, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
+    return launch_cfg<64, 32, 4, 2, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
                                         in_nterms, out_up, out_lo, out_ld, out_nterms);
   if (h_out > 8 && few_rows)
     return launch_cfg<16, 16, 2, 1, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
@@ -265,6 +523,23 @@ cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
   if (h_out > 8)
     return launch_cfg<16, 64, 2, 4, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
                                         in_nterms, out_up, out_lo, out_ld, out_nterms);
+  // narrow outputs (h_out <= 4, h_in <= 256): a warp per monomial row
+  if (h_out <= 4 && h_in <= 32 * kNarrowMaxJ) {
+    const int64_t rows = std::max<int64_t>(1, std::min(in_ld, out_ld));
+    if ((rows + 63) / 64 > 65535) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)n_boxes, (unsigned)((rows + 63) / 64));
+    const int jq = h_in <= 32 ? 1 : (h_in <= 64 ? 2 : (h_in <= 128 ? 4 : 8));
+#define BERN_NW(HO, JQ)                                                                       \
+  if ((HO == 1) == (h_out == 1) && jq == JQ)                                                  \
+    k_affine_narrow_warp<HO, JQ><<<grid, 256, 0, L.stream>>>(                                 \
+        n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld, in_nterms, out_up, out_lo, out_ld,   \
+        out_nterms, L.status);
+    BERN_NW(1, 1) BERN_NW(1, 2) BERN_NW(1, 4) BERN_NW(1, 8)
+    BERN_NW(4, 1) BERN_NW(4, 2) BERN_NW(4, 4) BERN_NW(4, 8)
+#undef BERN_NW
+    ++*L.launches;
+    return cudaGetLastError();
+  }
   // narrow outputs (h_out <= 8): a thread per monomial row, HO >= h_out
   const int HO = h_out == 1 ? 1 : (h_out <= 4 ? 4 : 8);
   const size_t smem = (size_t)HO * h_in * sizeof(float) + (size_t)h_in * sizeof(int32_t);
