@@ -434,53 +434,79 @@ def run_ours(args, rank, world, local_rank, dist):
 
     # ---- the learned form: degree MLP trained on the GPU, then timed like the plain form
     learned = None
+    learned4 = None
     if not args.no_learned:
         from paper_2211_14438_gb300 import learned as lm
-        tr_boxes = wl.config3_training_boxes(800)
-        info = lm.fit(ctx, w.net.widths, w.net.W, w.net.b, tr_boxes, cap=w.degree_cap)
-        plan = bern.Learned(info["mlp"], 0.0, w.degree)
-        out_l = {k: (torch.empty_like(v) if v is not None else None) for k, v in out.items()}
 
-        def lstep():
-            ctx.propagate(w.net.widths, Wd, bd, boxes_d, degree=plan, cap=w.degree_cap,
-                          cap_terms=cap_terms, out=out_l, sync=False)
+        def timed(net, Wd_, bd_, bx_, degree, ct, o_, tau=0.0):
+            outx = {"lo": torch.empty(bx_.shape[0], o_, device=dev),
+                    "hi": torch.empty(bx_.shape[0], o_, device=dev),
+                    "n_terms": torch.empty(bx_.shape[0], o_, 2, device=dev, dtype=torch.int32),
+                    "coef": torch.empty(bx_.shape[0], o_, 2, ct, device=dev), "keys": None}
 
-        for _ in range(args.warmup):
-            lstep()
-        if ctx.sync() != 0:
-            raise RuntimeError("learned propagate failed")
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-        for k in range(args.steps):
-            flush.zero_()
-            starts[k].record(stream)
-            lstep()
-            ends[k].record(stream)
-        torch.cuda.synchronize()
-        if ctx.sync() != 0:
-            raise RuntimeError("learned propagate failed")
-        ms_l = max_over_ranks(float(np.mean([s_.elapsed_time(e_) for s_, e_ in
-                                             zip(starts, ends)])), world, dist, dev)
-        width_l = float((out_l["hi"] - out_l["lo"]).float().mean().item())
-        tr = ctx.propagate(w.net.widths, Wd, bd, boxes_d, degree=plan, cap=w.degree_cap,
-                           cap_terms=cap_terms, trace=True)
-        hist = np.bincount(tr["tr_degree"].cpu().numpy().reshape(-1), minlength=5)[1:]
-        ch = info["chosen"]
-        learned = {
-            "value": round(world * B / (ms_l / 1e3), 1), "unit": "boxes/s",
-            "ms_per_step": round(ms_l, 4),
-            "mean_output_width": round(width_l, 6),
-            "plain_mean_output_width": round(float(np.mean(hi - lo)), 6),
-            "speedup_vs_plain": round(ms_step / ms_l, 4),
-            "order_histogram_1_to_4": hist.tolist(),
-            "train": {"boxes": int(len(tr_boxes)), "neurons": info["n_samples"],
-                      "seconds": round(info["seconds"], 2), "label_margin": ch["margin"],
-                      "train_acc": round(ch["train_acc"], 4),
-                      "learned_width_on_training_boxes": round(ch["learned_width"], 6),
-                      "plain_width_on_training_boxes": round(info["base_width"], 6)},
-            "plan": "BERN_DEG_LEARNED, fallback order 2, min_conf 0",
-        }
+            def st():
+                ctx.propagate(net.widths, Wd_, bd_, bx_, degree=degree, cap=16, tau=tau,
+                              cap_terms=ct, out=outx, sync=False)
+            for _ in range(args.warmup):
+                st()
+            if ctx.sync() != 0:
+                raise RuntimeError("propagate failed")
+            if dist is not None:
+                dist.barrier()
+            torch.cuda.synchronize()
+            for k in range(args.steps):
+                flush.zero_()
+                starts[k].record(stream)
+                st()
+                ends[k].record(stream)
+            torch.cuda.synchronize()
+            if ctx.sync() != 0:
+                raise RuntimeError("propagate failed")
+            msx = max_over_ranks(float(np.mean([s_.elapsed_time(e_) for s_, e_ in
+                                                zip(starts, ends)])), world, dist, dev)
+            return msx, float((outx["hi"] - outx["lo"]).float().mean().item())
+
+        def learned_entry(net, train_boxes, plain_ms, plain_width, bx_, Wd_, bd_, ct, o_):
+            info = lm.fit(ctx, net.widths, net.W, net.b, train_boxes, cap=16)
+            plan = info["plan"]
+            ms_l, width_l = timed(net, Wd_, bd_, bx_, plan, ct, o_)
+            tr = ctx.propagate(net.widths, Wd_, bd_, bx_, degree=plan, cap=16, cap_terms=ct,
+                               trace=True)
+            hist = np.bincount(tr["tr_degree"].cpu().numpy().reshape(-1), minlength=5)[1:]
+            ch = info["chosen"]
+            nb = int(bx_.shape[0])
+            return {
+                "value": round(world * nb / (ms_l / 1e3), 1), "unit": "boxes/s",
+                "ms_per_step": round(ms_l, 4),
+                "plain_value": round(world * nb / (plain_ms / 1e3), 1),
+                "mean_output_width": round(width_l, 6),
+                "plain_mean_output_width": round(plain_width, 6),
+                "speedup_vs_plain": round(plain_ms / ms_l, 4),
+                "order_histogram_1_to_4": hist.tolist(),
+                "train": {"boxes": int(len(train_boxes)), "neurons": info["n_samples"],
+                          "seconds": round(info["seconds"], 2), "label_margin": ch["margin"],
+                          "train_acc": round(ch["train_acc"], 4),
+                          "learned_width_on_training_boxes": round(ch["learned_width"], 6),
+                          "plain_width_on_training_boxes": round(info["base_width"], 6)},
+                "plan": "BERN_DEG_LEARNED, fallback order 2, min_conf 0, per-layer caps %s"
+                        % info["max_per_layer"],
+            }
+
+        learned = learned_entry(w.net, wl.config3_training_boxes(800), ms_step,
+                                float(np.mean(hi - lo)), boxes_d, Wd, bd, cap_terms, o)
+        learned["workload"] = "the benchmark workload above"
+        if not args.n_boxes:
+            w4 = wl.config4()
+            Wd4 = [torch.from_numpy(x).to(dev) for x in w4.net.W]
+            bd4 = [torch.from_numpy(x).to(dev) for x in w4.net.b]
+            bx4 = torch.from_numpy(w4.boxes).to(dev)
+            ct4 = bern.max_output_terms(w4.net.widths, 4, 16)
+            ms4, width4 = timed(w4.net, Wd4, bd4, bx4, 2, ct4, w4.net.n_out)
+            learned4 = learned_entry(w4.net, wl.config4_training_boxes(700), ms4, width4, bx4,
+                                     Wd4, bd4, ct4, w4.net.n_out)
+            learned4["workload"] = ("config4 learned-degree shape: MLP [6,100,100,100,2] seed 3, "
+                                    "2048 boxes with sides U(0.05,0.5) in [-1,1]^6, cap 16; "
+                                    "plain = order 2 everywhere")
 
     cpu = None
     if pool is not None:
@@ -511,7 +537,7 @@ def run_ours(args, rank, world, local_rank, dist):
         "roofline": roof, "kernels": kernels,
         "kernel_pass_ms_per_step": round(total_kernel_ms, 4),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-        "learned": learned,
+        "learned": learned, "learned_config4": learned4,
         "clocks": clocks,
     }
     return line

@@ -122,7 +122,10 @@ typedef struct {
   int64_t bern_budget;
   /* BERN_DEG_LEARNED: the degree MLP (n_features = BERN_DEGREE_FEATURES,
    * n_classes = BERN_DEGREE_CLASSES, host struct, device weights) and the
-   * fallback: a neuron whose largest class probability is below min_conf
+   * fallback.  per_layer, if not NULL, caps the order proposed at hidden
+   * layer i (1-based) at per_layer[i-1] (it sizes the workspace and tables;
+   * without it every layer is sized for order BERN_DEGREE_CLASSES).  A
+   * neuron whose largest class probability is below min_conf
    * (>= 0; above 1 every neuron falls back) uses global_d (the plain
    * method's order, 0 means 2). */
   const bern_mlp* mlp;

@@ -434,8 +434,9 @@ class Learned:
     features and BERN_DEGREE_CLASSES classes), the confidence below which a
     neuron falls back to the plain order, and that order."""
 
-    def __init__(self, mlp: "Mlp", min_conf: float = 0.0, fallback: int = 2):
+    def __init__(self, mlp: "Mlp", min_conf: float = 0.0, fallback: int = 2, max_per_layer=None):
         self.mlp, self.min_conf, self.fallback = mlp, float(min_conf), int(fallback)
+        self.max_per_layer = None if max_per_layer is None else [int(x) for x in max_per_layer]
 
 
 def make_plan(degree, widths, cap, tau, budget):
@@ -444,7 +445,11 @@ def make_plan(degree, widths, cap, tau, budget):
     if isinstance(degree, Learned):
         ms = degree.mlp.struct()
         keep.append(ms)
-        plan = bern_degree_plan(BERN_DEG_LEARNED, degree.fallback, None, None, cap, tau, budget,
+        caps = None
+        if degree.max_per_layer is not None:
+            caps = (ctypes.c_int * len(degree.max_per_layer))(*degree.max_per_layer)
+            keep.append(caps)
+        plan = bern_degree_plan(BERN_DEG_LEARNED, degree.fallback, caps, None, cap, tau, budget,
                                 ctypes.pointer(ms), degree.min_conf)
     elif isinstance(degree, (int, np.integer)):
         plan = bern_degree_plan(BERN_DEG_GLOBAL, int(degree), None, None, cap, tau, budget)
@@ -466,6 +471,8 @@ def make_plan(degree, widths, cap, tau, budget):
 def layer_degrees(widths, degree):
     H = len(widths) - 1
     if isinstance(degree, Learned):
+        if degree.max_per_layer is not None:
+            return list(degree.max_per_layer)
         return [max(BERN_DEGREE_CLASSES, degree.fallback)] * (H - 1)
     if isinstance(degree, (int, np.integer)):
         return [int(degree)] * (H - 1)

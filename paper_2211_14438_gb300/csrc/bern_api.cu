@@ -367,7 +367,9 @@ int make_plan(const bern_net* net, const bern_degree_plan* dp, Plan& P) {
         if (!dp->per_layer) return BERN_E_INVALID;
         l.d = dp->per_layer[i];
       } else if (dp->kind == BERN_DEG_LEARNED) {
-        l.d = std::max(kDegClasses, P.fallback_d);
+        // proposals are clamped to per_layer[i] when it is given
+        l.d = dp->per_layer ? dp->per_layer[i] : std::max(kDegClasses, P.fallback_d);
+        if (l.d < 1 || l.d > kMaxOrder) return BERN_E_INVALID;
       } else if (dp->kind == BERN_DEG_PER_NEURON) {
         if (!dp->per_neuron) return BERN_E_INVALID;
         int mx = 0;
@@ -506,7 +508,8 @@ int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
                                   l.M_pre, pre_nt, lo, hi);
       if (e != cudaSuccess) return map_cuda(e);
       e = launch_learned_degrees(L, mv, B, l.h_out, i + 1, lo, hi, pre_nt, P.min_conf,
-                                 P.fallback_d, P.cap, ord, ch.at<int32_t>(P.L[i + 1].off_order),
+                                 P.fallback_d, l.d, P.cap, ord,
+                                 ch.at<int32_t>(P.L[i + 1].off_order),
                                  ch.at<uint8_t>(l.off_deg), kind, coef, eps);
     } else {
       e = launch_enclose_relu(L, T, B, l.h_out, l.order, P.budget, pre_up, pre_lo, l.M_pre,

@@ -87,7 +87,8 @@ k_degree_features(int64_t n, const float* __restrict__ lo, const float* __restri
 __global__ void __launch_bounds__(128)
 k_learned_degrees(MlpView M, int64_t n_boxes, int h, int layer, const float* __restrict__ lo,
                   const float* __restrict__ hi, const int32_t* __restrict__ pre_nterms,
-                  float min_conf, int fallback_d, int cap, const int32_t* __restrict__ order_in,
+                  float min_conf, int fallback_d, int max_d, int cap,
+                  const int32_t* __restrict__ order_in,
                   int32_t* __restrict__ order_out, uint8_t* __restrict__ degrees,
                   int8_t* __restrict__ kind, float* __restrict__ coef, float* __restrict__ eps,
                   int* status) {
@@ -118,7 +119,7 @@ k_learned_degrees(MlpView M, int64_t n_boxes, int h, int layer, const float* __r
 #pragma unroll
       for (int c = 0; c < kDegClasses; ++c) sum += expf(z[c] - zb);
       const float conf = 1.0f / sum;   // the largest softmax probability
-      const int d = conf >= min_conf ? best + 1 : fallback_d;
+      const int d = min(conf >= min_conf ? best + 1 : fallback_d, max_d);
       degrees[it] = (uint8_t)d;
       kind[it] = (int8_t)relu_item(l, u, d, coef + it * kCoefStride, eps + it, status);
       dmax = max(dmax, d);
@@ -316,12 +317,14 @@ cudaError_t launch_degree_features(const Launch& L, int64_t n_items, const float
 cudaError_t launch_learned_degrees(const Launch& L, const MlpView& M, int64_t n_boxes, int h,
                                    int layer, const float* lo, const float* hi,
                                    const int32_t* pre_nterms, float min_conf, int fallback_d,
-                                   int cap, const int32_t* order_in, int32_t* order_out,
-                                   uint8_t* degrees, int8_t* kind, float* coef, float* eps) {
+                                   int max_d, int cap, const int32_t* order_in,
+                                   int32_t* order_out, uint8_t* degrees, int8_t* kind,
+                                   float* coef, float* eps) {
   if (n_boxes == 0) return cudaSuccess;
   if (M.F != kDegFeatures || M.C != kDegClasses) return cudaErrorInvalidValue;
   k_learned_degrees<<<grid_for(n_boxes, 1, 152 * 16), 128, 0, L.stream>>>(
-      M, n_boxes, h, layer, lo, hi, pre_nterms, min_conf, fallback_d, cap, order_in, order_out,
+      M, n_boxes, h, layer, lo, hi, pre_nterms, min_conf, fallback_d, max_d, cap, order_in,
+      order_out,
       degrees, kind, coef, eps, L.status);
   ++*L.launches;
   return cudaGetLastError();

@@ -47,13 +47,15 @@ __device__ __forceinline__ void degree_feature_vec(float l, float h, int nt, int
 
 // Learned plan, one hidden layer: per (box, neuron) the degree MLP's
 // proposal d (class c -> order c + 1; the fallback order when the largest
-// probability is below min_conf), the ReLU case and coefficients for d, and
+// probability is below min_conf; at most max_d), the ReLU case and
+// coefficients for d, and
 // per box the next Bernstein order min(cap, order_in * max_m d).
 cudaError_t launch_learned_degrees(const Launch& L, const MlpView& M, int64_t n_boxes, int h,
                                    int layer, const float* lo, const float* hi,
                                    const int32_t* pre_nterms, float min_conf, int fallback_d,
-                                   int cap, const int32_t* order_in, int32_t* order_out,
-                                   uint8_t* degrees, int8_t* kind, float* coef, float* eps);
+                                   int max_d, int cap, const int32_t* order_in,
+                                   int32_t* order_out, uint8_t* degrees, int8_t* kind,
+                                   float* coef, float* eps);
 cudaError_t launch_fill_i32(const Launch& L, int32_t* p, int64_t n, int32_t v);
 
 cudaError_t launch_degree_features(const Launch& L, int64_t n_items, const float* lo,

@@ -247,6 +247,7 @@ def fit(ctx, widths, W, b, boxes, cap=16, base=2, steps=600, lr=3e-3, seed=0,
     if base_plan not in plans:
         plans.append(base_plan)
     base_idx = plans.index(base_plan)
+    caps = [max(p[i] for p in plans) for i in range(H1)]   # largest order per layer
     table, ms_per_box = width_table(ctx, widths, W, b, boxes, plans, cap)
     cost = np.array([plan_cost(widths, p, cap) for p in plans])
     base_w = float(table[:, base_idx].mean())
@@ -258,7 +259,7 @@ def fit(ctx, widths, W, b, boxes, cap=16, base=2, steps=600, lr=3e-3, seed=0,
         z = torch.empty(Xf.shape[0], CLASSES, device="cuda")
         ctx.mlp_forward(m, Xf, z)
         acc = float((z.argmax(1).cpu().numpy() == y).mean())
-        w_l, c_l = evaluate(ctx, widths, W, b, boxes, bern.Learned(m, 0.0, base), cap)
+        w_l, c_l = evaluate(ctx, widths, W, b, boxes, bern.Learned(m, 0.0, base, caps), cap)
         rec = {"margin": margin, "lam": lam, "label_width": float(mean_w),
                "label_work": float(cost[idx].mean() / cost[base_idx]), "learned_width": w_l,
                "learned_ms_per_box": c_l, "train_acc": acc, "loss": hist,
@@ -275,7 +276,8 @@ def fit(ctx, widths, W, b, boxes, cap=16, base=2, steps=600, lr=3e-3, seed=0,
         m, _ = train(ctx, Xf, torch.as_tensor(y).cuda(), steps, lr, seed)
         best = (tried[k], m)
     rec, m = best
-    return {"mlp": m, "plans": plans, "base_width": base_w, "base_work": float(cost[base_idx]),
+    return {"mlp": m, "plan": bern.Learned(m, 0.0, base, caps), "max_per_layer": caps,
+            "plans": plans, "base_width": base_w, "base_work": float(cost[base_idx]),
             "table": table, "cost": cost, "ms_per_box": ms_per_box, "tried": tried,
             "chosen": rec,
             "n_samples": int(Xf.shape[0]), "seconds": time.time() - t0}

@@ -162,6 +162,13 @@ def config4(n_boxes: int = 2048) -> Workload:
                     degree_cap=16, prune_tau=1e-7)
 
 
+def config4_training_boxes(count: int = 700, seed: int = 1003) -> np.ndarray:
+    """Training boxes for the learned component on the config-4 network:
+    random sub-boxes of [-1,1]^6 with sides U(0.05, 0.5), like the workload's,
+    from their own seed (700 boxes x 300 hidden neurons = 210,000 samples)."""
+    return random_boxes(np.random.default_rng(seed), count, 6, 0.05, 0.5)
+
+
 def config5() -> Workload:
     """[6,64,64,64,64,1], seed 4, root box [-1,1]^6 (branch-and-bound root)."""
     net = make_net([6, 64, 64, 64, 64, 1], seed=4)

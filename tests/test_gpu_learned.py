@@ -114,7 +114,7 @@ def test_trained_mlp_gains_over_plain(ctx):
     held = w.boxes[np.r_[0:4096:8, 4096:5120:2]]         # 512 grid cells + 512 random
     info = lm.fit(ctx, net.widths, net.W, net.b, wl.config3_training_boxes(800), cap=16)
     assert info["n_samples"] >= 200_000
-    plan = bern.Learned(info["mlp"], 0.0, 2)
+    plan = info["plan"]
     gp = run_gpu(ctx, net, held, degree=2, trace=True)
     gl = run_gpu(ctx, net, held, degree=plan, trace=True)
     wp = float(np.mean(gp["hi"] - gp["lo"]))
@@ -127,3 +127,19 @@ def test_trained_mlp_gains_over_plain(ctx):
     rng = np.random.default_rng(17)
     for bi in range(0, len(held), 64):
         assert mc_check(gl, bi, net, held[bi], 5_000, rng) == 0
+
+
+def test_per_layer_caps_clamp_proposals(ctx):
+    """With per-layer caps the proposals are clamped: an MLP sure of order 4
+    under caps of 2 everywhere gives exactly the order-2 plan, and caps
+    (4, 1, 1, 1) give the per-layer plan (4, 1, 1, 1)."""
+    w = wl.config3(n_random=8, cells=2)
+    m = bern.Mlp(torch, F, C, const_theta(3))
+    a = run_gpu(ctx, w.net, w.boxes, degree=bern.Learned(m, max_per_layer=[2, 2, 2, 2]))
+    b = run_gpu(ctx, w.net, w.boxes, degree=2)
+    for k in ("lo", "hi", "n_terms"):
+        assert np.array_equal(a[k], b[k]), k
+    a = run_gpu(ctx, w.net, w.boxes, degree=bern.Learned(m, max_per_layer=[4, 1, 1, 1]))
+    b = run_gpu(ctx, w.net, w.boxes, degree=[4, 1, 1, 1])
+    for k in ("lo", "hi", "n_terms"):
+        assert np.array_equal(a[k], b[k]), k
