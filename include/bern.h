@@ -160,6 +160,14 @@ int bern_destroy(bern_ctx* ctx);
 /* Select BERN_MEM_DEVICE (default) or BERN_MEM_HOST for bern_propagate. */
 int bern_set_pointer_mode(bern_ctx* ctx, int mode);
 
+/* Autotuning (on by default): the first bern_propagate of each plan shape
+ * (network widths, plan, batch size) times every variant of the tunable
+ * kernels (the wide-layer affine kernel: persistent or two tile shapes; the
+ * Bernstein enclosure: 8, 4 or 2 items per block) on its first chunk and
+ * keeps the fastest per shape.  All variants compute identical results.
+ * enable = 0 uses the built-in defaults. */
+int bern_set_autotune(bern_ctx* ctx, int enable);
+
 /* Largest shared-memory footprint (bytes, at most 200 KB) the Horner
  * composition kernel may use per block before it keeps its buffers in a
  * global workspace instead; the default is 200 KB.  Both placements compute

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <set>
 #include <new>
 #include <string>
 #include <vector>
@@ -77,8 +78,11 @@ struct bern_ctx {
   std::map<int, TableSet> tables;
   DevBuf ws, stage_in, stage_out, qbuf, mlp_ws, hbuf;
   std::vector<GraphEntry> graphs;
-  Launch launch() { return Launch{stream, d_status, &launches}; }
-  Launch launch_on(cudaStream_t s) { return Launch{s, d_status, &launches}; }
+  Tuner tuner;
+  int autotune = 1;
+  std::set<std::string> tuned;     // plan signatures already tuned
+  Launch launch() { return Launch{stream, d_status, &launches, &tuner}; }
+  Launch launch_on(cudaStream_t s) { return Launch{s, d_status, &launches, &tuner}; }
 };
 
 namespace {
@@ -657,6 +661,12 @@ int bern_set_pointer_mode(bern_ctx* c, int mode) {
   return BERN_OK;
 }
 
+int bern_set_autotune(bern_ctx* c, int enable) {
+  if (!c) return BERN_E_INVALID;
+  c->autotune = enable ? 1 : 0;
+  return BERN_OK;
+}
+
 int bern_set_horner_smem_limit(bern_ctx* c, int64_t bytes) {
   if (!c || bytes < 0) return BERN_E_INVALID;
   c->horner_smem_limit = bytes;
@@ -860,6 +870,51 @@ int bern_propagate_traced(bern_ctx* c, const bern_net* net, const float* boxes,
   ComposeScratch CS;
   if ((rc = ensure_queues(c, chunk * hmax, &CS, horner_floats))) return rc;
 
+  // autotune once per plan shape: probe every variant of every tunable kind
+  // on the first chunk (plain launches, timed per launch), keep the fastest
+  if (c->autotune) {
+    std::string sig;
+    {
+      auto add = [&](const void* p, size_t sz) { sig.append((const char*)p, sz); };
+      const int64_t B0 = std::min(chunk, n_boxes);
+      add(&B0, sizeof B0);
+      add(&P.cap, sizeof P.cap);
+      add(&P.tau, sizeof P.tau);
+      add(&P.budget, sizeof P.budget);
+      add(&P.learned, sizeof P.learned);
+      for (int i = 0; i <= P.H; ++i) add(&net->widths[i], sizeof(int));
+      for (const auto& l : P.L) add(&l.d, sizeof l.d);
+    }
+    if (!c->tuned.count(sig)) {
+      const int64_t B = std::min(chunk, n_boxes);
+      Chunk ch{(char*)c->ws.p, B};
+      if ((rc = fill_degrees(c, P, ch, B))) return rc;
+      const char* kinds[] = {"affine", "enclose"};
+      const int nvar[] = {3, 3};
+      for (int k = 0; k < 2; ++k) {
+        for (int v = 0; v < nvar[k]; ++v) {
+          c->tuner.probe_kind = kinds[k];
+          c->tuner.probe_variant = v;
+          rc = run_chunk(c, c->stream, P, *T, CS, &dnet, d_boxes, B, ch, dres.lo, dres.hi, dres,
+                         nullptr);
+          if (rc) {
+            c->tuner.probe_kind.clear();
+            return rc;
+          }
+        }
+        c->tuner.probe_kind.clear();
+        for (auto& kv : c->tuner.probe_ms) {
+          int best = -1;
+          for (int v = 0; v < (int)kv.second.size(); ++v)
+            if (kv.second[v] >= 0.0f && (best < 0 || kv.second[v] < kv.second[best])) best = v;
+          if (best >= 0) c->tuner.best[kv.first] = best;
+        }
+        c->tuner.probe_ms.clear();
+      }
+      if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return map_cuda(e);
+      c->tuned.insert(sig);
+    }
+  }
   for (int64_t b0 = 0; b0 < n_boxes; b0 += chunk) {
     const int64_t B = std::min(chunk, n_boxes - b0);
     Chunk ch{(char*)c->ws.p, B};

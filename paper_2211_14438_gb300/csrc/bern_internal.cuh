@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <string>
 #include <vector>
 
 #include "../../include/bern.h"
@@ -121,11 +123,35 @@ void build_rscale(int n, int l, std::vector<float>& out);
 void build_enclose_tables(int n, int l, std::vector<int32_t>& gidx, std::vector<int32_t>& lines);
 
 // ------------------------------------------------------------ launchers
+// Autotuning.  Launchers that have several valid variants for a shape ask
+// the tuner which one to run (by a key naming the kernel kind and shape).  In
+// a probe pass the tuner forces one variant of one kind and times every
+// launch of that kind with CUDA events; afterwards each key keeps its fastest
+// variant.  Every variant computes the same values in the same order.
+struct Tuner {
+  std::map<std::string, int> best;                        // key -> variant
+  std::string probe_kind;                                 // empty: no probe pass
+  int probe_variant = -1;
+  std::map<std::string, std::vector<float>> probe_ms;     // key -> ms per variant
+};
+
 struct Launch {
   cudaStream_t stream;
   int* status;                     // device status word
   int64_t* launches;               // host counter
+  Tuner* tuner = nullptr;
 };
+
+// Variant of `kind` to run for `key` (dflt when untuned).
+int tune_variant(const Launch& L, const char* kind, const std::string& key, int dflt);
+// Probe timing around one launch of `kind`: tune_begin records the start event
+// when this kind is being probed; tune_end records, waits and adds the time.
+struct TuneTimer {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool on = false;
+};
+void tune_begin(const Launch& L, const char* kind, TuneTimer& t);
+void tune_end(const Launch& L, const char* kind, const std::string& key, TuneTimer& t);
 
 // Layer-block layout: coefficient r of neuron m of box b at ((b*ld + r)*h + m);
 // term counts at b*h + m.

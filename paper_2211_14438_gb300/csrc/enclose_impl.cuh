@@ -34,6 +34,7 @@
 #include <math_constants.h>
 
 #include <algorithm>
+#include <string>
 
 #include "device_util.cuh"
 
@@ -260,9 +261,16 @@ template <int LB>
 cudaError_t launch_lb(const Launch& L, const Tables& T, int G, int64_t n_items, int h,
                       const float* pre_up, const float* pre_lo, int64_t ld,
                       const int32_t* nterms, float* lo, float* hi, EncloseOpts ro) {
-  // items per block: as many as fit 192 KB of grids, at most 8 (16 warps)
+  // items per block: as many as fit 192 KB of grids, at most 8 (16 warps);
+  // autotuned among 8, 4 and 2 (variants 0, 1, 2)
   int items = (int)std::min<int64_t>(8, (192 * 1024) / (2 * (int64_t)G * 4));
+  const std::string key = "enclose/" + std::to_string(LB) + "/" + std::to_string(T.n) + "/" +
+                          std::to_string(n_items);
+  const int v = tune_variant(L, "enclose", key, 0);
+  items = std::min(items, 8 >> std::min(v, 2));
   if (items < 1) items = 1;
+  TuneTimer tt;
+  tune_begin(L, "enclose", tt);
   const size_t smem = (size_t)2 * items * G * sizeof(float);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_enclose<LB>,
@@ -274,7 +282,9 @@ cudaError_t launch_lb(const Launch& L, const Tables& T, int G, int64_t n_items, 
                                                         pre_lo, ld, nterms, lo, hi, ro,
                                                         L.status);
   ++*L.launches;
-  return cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
+  tune_end(L, "enclose", key, tt);
+  return e;
 }
 
 // Tiny grids ((l+1)^n <= 64): one lane per polynomial, the lane's grid

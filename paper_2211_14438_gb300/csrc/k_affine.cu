@@ -25,6 +25,7 @@
 // shared memory in chunks of KC, and every thread keeps a TM x TR register
 // tile per bound.  Inputs beyond a neuron's term count are read as zero.
 #include <algorithm>
+#include <string>
 
 #include "device_util.cuh"
 
@@ -500,22 +501,38 @@ cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
     return cudaErrorInvalidValue;
   const bool few_rows = std::min(in_ld, out_ld) <= 16;     // short polynomials: short tiles
   const size_t psmem = persistent_smem(h_out, h_in);
-  if (h_out >= 32 && !few_rows && psmem <= 72 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_affine_persistent,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
-    if (e != cudaSuccess) return e;
-    const int64_t blocks = std::min<int64_t>(n_boxes, 152 * 3);
-    k_affine_persistent<<<(unsigned)blocks, kPThreads, psmem, L.stream>>>(
-        n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld, in_nterms, out_up, out_lo, out_ld,
-        out_nterms, L.status);
-    ++*L.launches;
-    return cudaGetLastError();
+  if (h_out >= 32 && !few_rows) {
+    // wide layers: autotuned among the persistent kernel (0, when its
+    // weights fit shared memory) and two tile shapes (1: 64 x 32, 2: 64 x 64)
+    const std::string key = "affine/" + std::to_string(h_out) + "/" + std::to_string(h_in) +
+                            "/" + std::to_string(in_ld) + "/" + std::to_string(n_boxes);
+    int v = tune_variant(L, "affine", key, psmem <= 72 * 1024 ? 0 : 1);
+    if (v == 0 && psmem > 72 * 1024) v = 1;
+    TuneTimer tt;
+    tune_begin(L, "affine", tt);
+    cudaError_t e;
+    if (v == 0) {
+      e = cudaFuncSetAttribute(k_affine_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)psmem);
+      if (e != cudaSuccess) return e;
+      const int64_t blocks = std::min<int64_t>(n_boxes, 152 * 3);
+      k_affine_persistent<<<(unsigned)blocks, kPThreads, psmem, L.stream>>>(
+          n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld, in_nterms, out_up, out_lo, out_ld,
+          out_nterms, L.status);
+      ++*L.launches;
+      e = cudaGetLastError();
+    } else if (v == 2) {
+      e = launch_cfg<64, 64, 4, 4, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
+                                       in_nterms, out_up, out_lo, out_ld, out_nterms);
+    } else {
+      e = launch_cfg<64, 32, 4, 2, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
+                                       in_nterms, out_up, out_lo, out_ld, out_nterms);
+    }
+    tune_end(L, "affine", key, tt);
+    return e;
   }
   if (h_out >= 32 && few_rows)
     return launch_cfg<64, 16, 4, 1, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
-                                        in_nterms, out_up, out_lo, out_ld, out_nterms);
-  if (h_out >= 32)
-    return launch_cfg<64, 32, 4, 2, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
                                         in_nterms, out_up, out_lo, out_ld, out_nterms);
   if (h_out > 8 && few_rows)
     return launch_cfg<16, 16, 2, 1, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,

@@ -326,3 +326,38 @@ void build_enclose_tables(int n, int l, std::vector<int32_t>& gidx, std::vector<
 }
 
 }  // namespace bern
+
+namespace bern {
+
+int tune_variant(const Launch& L, const char* kind, const std::string& key, int dflt) {
+  if (!L.tuner) return dflt;
+  if (!L.tuner->probe_kind.empty())
+    return L.tuner->probe_kind == kind ? L.tuner->probe_variant : dflt;
+  auto it = L.tuner->best.find(key);
+  return it == L.tuner->best.end() ? dflt : it->second;
+}
+
+void tune_begin(const Launch& L, const char* kind, TuneTimer& t) {
+  t.on = L.tuner && L.tuner->probe_kind == kind;
+  if (!t.on) return;
+  cudaEventCreate(&t.e0);
+  cudaEventCreate(&t.e1);
+  cudaEventRecord(t.e0, L.stream);
+}
+
+void tune_end(const Launch& L, const char* kind, const std::string& key, TuneTimer& t) {
+  if (!t.on) return;
+  cudaEventRecord(t.e1, L.stream);
+  cudaEventSynchronize(t.e1);
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, t.e0, t.e1);
+  cudaEventDestroy(t.e0);
+  cudaEventDestroy(t.e1);
+  auto& v = L.tuner->probe_ms[key];
+  const int var = L.tuner->probe_variant;
+  if ((int)v.size() <= var) v.resize(var + 1, -1.0f);
+  v[var] = (v[var] < 0.0f ? 0.0f : v[var]) + ms;
+  (void)kind;
+}
+
+}  // namespace bern

@@ -269,3 +269,18 @@ def test_output_keys_are_graded_monomials(ctx):
     want = ex[:, 0] | (ex[:, 1] << 8)
     assert np.array_equal(g["keys"][0, 0, 0, :nt], want)
     assert np.array_equal(g["keys"][0, 0, 1, :nt], want)
+
+
+def test_autotune_on_off_identical(ctx):
+    """Every tunable variant computes the same values: results with the
+    autotuner's choices equal those with the built-in defaults, bit for bit."""
+    w = wl.config3(n_random=40, cells=4)
+    ctx.set_autotune(False)
+    try:
+        a = run_gpu(ctx, w.net, w.boxes)
+    finally:
+        ctx.set_autotune(True)
+    b = run_gpu(ctx, w.net, w.boxes)
+    c = run_gpu(ctx, w.net, w.boxes)
+    for k in ("lo", "hi", "n_terms", "coef"):
+        assert np.array_equal(a[k], b[k]) and np.array_equal(b[k], c[k]), k
