@@ -266,7 +266,7 @@ KERNEL_SOURCES = {"affine": "k_affine.cu", "enclose": "k_enclose.cu", "compose":
 def ncu_traffic(kernel_key):
     """DRAM bytes per launch from a committed ncu summary, if its kernel
     source is unchanged since the counters were taken."""
-    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(p):
         return None
     with open(p) as f:
