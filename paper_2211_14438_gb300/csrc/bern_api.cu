@@ -793,6 +793,15 @@ int bern_propagate_traced(bern_ctx* c, const bern_net* net, const float* boxes,
   if (!result->lo || !result->hi || !result->n_terms || result->cap_terms < 0)
     return BERN_E_INVALID;
   cudaSetDevice(c->device);
+  // order-2 items beyond the row path use the pair-list kernel: its inputs
+  // (both bounds) must fit shared memory and its square pair list must stay
+  // below 2^26 entries (checked before any table is built)
+  const int row_dmax_n = std::min(kMaxRowDegree, row_path_max_degree(P.n));
+  for (const auto& l : P.L)
+    if (l.hidden && l.d == 2 && P.tau == 0.0f && l.D_pre > row_dmax_n &&
+        (2 * (size_t)l.M_pre * sizeof(float) > 200 * 1024 ||
+         (double)l.M_pre * (double)(l.M_pre + 1) / 2.0 > (double)(1 << 26)))
+      return BERN_E_UNSUPPORTED;
   int dsq = 0;
   for (const auto& l : P.L)
     if (l.hidden && l.d >= 2) dsq = std::max(dsq, l.D_pre);

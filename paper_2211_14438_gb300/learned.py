@@ -6,10 +6,15 @@ Labels (the method has no learned part; this is the project's reading of
 "labelled by plain-method bound widths"):
 
 * A family of per-layer order plans (every layer in {1, 2}, plus order 3 or
-  4 at the first hidden layer with {1, 2} after it) runs with the plain
-  method over all training boxes: W[b, p] is box b's mean output-bound width
-  under plan p and cost[p] the plan's arithmetic work per box (plan_cost: a
-  deterministic count, so the labels do not depend on timing noise).
+  4 at the first hidden layer with {1, 2} after it; plans with more than four
+  times the base plan's counted work, or beyond the library's limits, are
+  left out) runs with the plain method over all training boxes: W[b, p] is
+  box b's mean output-bound width under plan p and cost[p] the plan's
+  arithmetic work per box (plan_cost: a deterministic count, so the labels do
+  not depend on timing noise).
+* The learned plan caps each layer's proposals; the caps must form a plan the
+  library runs, and among such cap vectors the one whose plans reach the
+  width target at the least work is kept.
 * Each box takes the plan minimising  cost[p] + lam * W[b, p];  lam is the
   smallest value for which the mean of the chosen widths does not exceed
   (1 - margin) times the base plan's mean width, so boxes buy speed with
@@ -27,6 +32,7 @@ min_conf uses the base order (the fallback).
 """
 from __future__ import annotations
 
+import itertools
 import time
 from typing import Dict, List, Sequence, Tuple
 
@@ -121,9 +127,10 @@ def plan_cost(widths, plan, cap=16) -> float:
     return total
 
 
-def width_table(ctx, widths, W, b, boxes, plans, cap=16):
+def width_table(ctx, widths, W, b, boxes, plans, cap=16, skip=None):
     """W[b, p] (mean output width of box b under plan p) and the plan's
-    measured GPU time per box (ms, for reporting)."""
+    measured GPU time per box (ms, for reporting); plans in `skip`, and plans
+    the library rejects, get infinite width and time."""
     torch = _torch()
     Wd, bd = _dev_net(widths, W, b)
     boxes_d = torch.as_tensor(np.ascontiguousarray(boxes, np.float32)).cuda()
@@ -131,16 +138,28 @@ def width_table(ctx, widths, W, b, boxes, plans, cap=16):
     table = np.zeros((B, len(plans)))
     cost = np.zeros(len(plans))
     for k, plan in enumerate(plans):
-        out, ms = timed_propagate(ctx, widths, Wd, bd, boxes_d, list(plan), cap)
+        if skip is not None and skip[k]:
+            table[:, k] = np.inf
+            cost[k] = np.inf
+            continue
+        try:
+            out, ms = timed_propagate(ctx, widths, Wd, bd, boxes_d, list(plan), cap)
+        except bern.BernError:
+            ctx.sync()                       # clear any device-side status of the attempt
+            table[:, k] = np.inf             # beyond the library's limits: never chosen
+            cost[k] = np.inf
+            continue
         table[:, k] = mean_width(out)
         cost[k] = ms / B
     return table, cost
 
 
-def choose_plans(table, cost, base_idx, margin=0.0, iters=60):
+def choose_plans(table, cost, base_idx, margin=0.0, iters=60, base_mean=None):
     """Per box the plan index minimising cost + lam * width, with the
-    smallest lam that keeps the mean chosen width <= (1 - margin) * base."""
-    target = (1.0 - margin) * table[:, base_idx].mean()
+    smallest lam that keeps the mean chosen width <= (1 - margin) * base
+    (base: the mean width of plan base_idx, or base_mean when given)."""
+    bm = table[:, base_idx].mean() if base_mean is None else base_mean
+    target = (1.0 - margin) * bm
 
     def pick(lam):
         idx = np.argmin(cost[None, :] + lam * table, axis=1)
@@ -221,6 +240,18 @@ def _labels_and_features(ctx, widths, W, b, boxes, plans, idx, cap):
     return X.reshape(-1, FEATURES).contiguous(), y
 
 
+def _runnable(ctx, widths, W, b, boxes, plan, cap):
+    torch = _torch()
+    Wd, bd = _dev_net(widths, W, b)
+    try:
+        ctx.propagate(widths, Wd, bd, torch.as_tensor(np.ascontiguousarray(boxes)).cuda(),
+                      degree=list(plan), cap=cap)
+        return True
+    except bern.BernError:
+        ctx.sync()
+        return False
+
+
 def evaluate(ctx, widths, W, b, boxes, degree, cap=16, reps=3):
     """(mean output width, ms per box) of a plan over `boxes`."""
     torch = _torch()
@@ -232,7 +263,7 @@ def evaluate(ctx, widths, W, b, boxes, degree, cap=16, reps=3):
 
 def fit(ctx, widths, W, b, boxes, cap=16, base=2, steps=600, lr=3e-3, seed=0,
         margins=(0.02, 0.03, 0.04, 0.05, 0.065, 0.08, 0.1, 0.12, 0.16, 0.24),
-        slack=0.005) -> Dict:
+        slack=0.005, max_work=4.0) -> Dict:
     """Labels from the plain method on `boxes`, GPU training, and a check of
     the trained MLP driving the propagation on the same boxes.  The label
     margin grows until the learned plan's measured mean width is at most
@@ -247,13 +278,42 @@ def fit(ctx, widths, W, b, boxes, cap=16, base=2, steps=600, lr=3e-3, seed=0,
     if base_plan not in plans:
         plans.append(base_plan)
     base_idx = plans.index(base_plan)
-    caps = [max(p[i] for p in plans) for i in range(H1)]   # largest order per layer
-    table, ms_per_box = width_table(ctx, widths, W, b, boxes, plans, cap)
-    cost = np.array([plan_cost(widths, p, cap) for p in plans])
-    base_w = float(table[:, base_idx].mean())
+    # plans with more than max_work times the base plan's counted work are not
+    # run at all (they would never be chosen, and the largest need tables of
+    # hundreds of millions of entries on six inputs)
+    work = np.array([plan_cost(widths, p, cap) for p in plans])
+    skip = work > max_work * work[base_idx]
+    table, ms_per_box = width_table(ctx, widths, W, b, boxes, plans, cap, skip)
+    cost = np.where(np.isfinite(ms_per_box), work, np.inf)
+    base_mean = float(table[:, base_idx].mean())
+    # the per-layer caps size the learned plan and must form a runnable plan;
+    # among the runnable cap vectors keep the one whose plans reach the width
+    # target at the least work (or, if none does, the tightest)
+    feasible = [p for k, p in enumerate(plans) if np.isfinite(cost[k])]
+    top = [max(p[i] for p in feasible) for i in range(H1)]
+    best_key, caps = None, None
+    for c in itertools.product(*[range(1, t + 1) for t in top]):
+        sel = np.array([np.isfinite(cost[k]) and all(p[i] <= c[i] for i in range(H1))
+                        for k, p in enumerate(plans)])
+        if not sel.any() or not _runnable(ctx, widths, W, b, boxes[:1], c, cap):
+            continue
+        t2 = np.where(sel[None, :], table, np.inf)
+        c2 = np.where(sel, cost, np.inf)
+        idx, _, mw = choose_plans(t2, c2, base_idx, margins[0], base_mean=base_mean)
+        ok = mw <= (1.0 - margins[0]) * base_mean
+        key = (0, float(c2[idx].mean())) if ok else (1, float(mw))
+        if best_key is None or key < best_key:
+            best_key, caps = key, list(c)
+    if caps is None:
+        raise RuntimeError("no runnable order plan")
+    for k, p in enumerate(plans):
+        if any(p[i] > caps[i] for i in range(H1)):
+            cost[k] = np.inf
+            table[:, k] = np.inf
+    base_w = base_mean
     tried, best = [], None
     for margin in margins:
-        idx, lam, mean_w = choose_plans(table, cost, base_idx, margin)
+        idx, lam, mean_w = choose_plans(table, cost, base_idx, margin, base_mean=base_mean)
         Xf, y = _labels_and_features(ctx, widths, W, b, boxes, plans, idx, cap)
         m, hist = train(ctx, Xf, torch.as_tensor(y).cuda(), steps, lr, seed)
         z = torch.empty(Xf.shape[0], CLASSES, device="cuda")
@@ -261,7 +321,7 @@ def fit(ctx, widths, W, b, boxes, cap=16, base=2, steps=600, lr=3e-3, seed=0,
         acc = float((z.argmax(1).cpu().numpy() == y).mean())
         w_l, c_l = evaluate(ctx, widths, W, b, boxes, bern.Learned(m, 0.0, base, caps), cap)
         rec = {"margin": margin, "lam": lam, "label_width": float(mean_w),
-               "label_work": float(cost[idx].mean() / cost[base_idx]), "learned_width": w_l,
+               "label_work": float(cost[idx].mean() / work[base_idx]), "learned_width": w_l,
                "learned_ms_per_box": c_l, "train_acc": acc, "loss": hist,
                "label_hist": np.bincount(y, minlength=CLASSES).tolist(),
                "plan_of_box": idx}
@@ -271,13 +331,14 @@ def fit(ctx, widths, W, b, boxes, cap=16, base=2, steps=600, lr=3e-3, seed=0,
             break
     if best is None:    # no margin met the width target: keep the tightest one
         k = int(np.argmin([r["learned_width"] for r in tried]))
-        idx, lam, _ = choose_plans(table, cost, base_idx, tried[k]["margin"])
+        idx, lam, _ = choose_plans(table, cost, base_idx, tried[k]["margin"],
+                                   base_mean=base_mean)
         Xf, y = _labels_and_features(ctx, widths, W, b, boxes, plans, idx, cap)
         m, _ = train(ctx, Xf, torch.as_tensor(y).cuda(), steps, lr, seed)
         best = (tried[k], m)
     rec, m = best
     return {"mlp": m, "plan": bern.Learned(m, 0.0, base, caps), "max_per_layer": caps,
-            "plans": plans, "base_width": base_w, "base_work": float(cost[base_idx]),
+            "plans": plans, "base_width": base_w, "base_work": float(work[base_idx]),
             "table": table, "cost": cost, "ms_per_box": ms_per_box, "tried": tried,
             "chosen": rec,
             "n_samples": int(Xf.shape[0]), "seconds": time.time() - t0}
