@@ -508,6 +508,40 @@ def run_ours(args, rank, world, local_rank, dist):
                                     "2048 boxes with sides U(0.05,0.5) in [-1,1]^6, cap 16; "
                                     "plain = order 2 everywhere")
 
+    # ---- branch-and-bound refinement of the config-5 root box (wall clock,
+    # host work included), plain orders against the learned form
+    bnb5 = None
+    if not args.no_learned and not args.no_bnb and not args.n_boxes and world == 1:
+        from paper_2211_14438_gb300 import bnb
+        from paper_2211_14438_gb300 import learned as lm
+        w5 = wl.config5()
+        root5 = w5.boxes[0]
+        rng5 = np.random.default_rng(1005)
+        c5 = rng5.uniform(-1, 1, (400, 6))
+        s5 = rng5.uniform(0.1, 0.7, (400, 6))
+        tr5 = wl.box_array(np.clip(c5 - s5 / 2, -1, 1), np.clip(c5 + s5 / 2, -1, 1))
+        t0 = time.time()
+        info5 = lm.fit(ctx, w5.net.widths, w5.net.W, w5.net.b, tr5, cap=16)
+        train5 = time.time() - t0
+        bnb5 = {"workload": "config5 network [6,64x4,1] seed 4, root [-1,1]^6, best-first "
+                            "refinement of output 0 in rounds of 1024 splits (widest side) "
+                            "until 4096 leaves; boxes/s counts every bounded child, wall "
+                            "clock with host work",
+                "learned_caps": info5["max_per_layer"], "train_seconds": round(train5, 2)}
+        for name, deg in (("plain", 2), ("learned", info5["plan"])):
+            fn = bnb.gpu_bound_fn(ctx, w5.net.widths, w5.net.W, w5.net.b, root5, deg, 16, 0.0)
+            fn(root5[None])                                   # warm-up (tuning, graphs)
+            bb = bnb.BranchAndBound(fn, root5, batch=1024, max_leaves=4096)
+            torch.cuda.synchronize()
+            t0 = time.time()
+            bb.run(64)
+            torch.cuda.synchronize()
+            dt = time.time() - t0
+            bnb5[name] = {"boxes_per_s": round((bb.propagated - 1) / dt, 1),
+                          "leaves": bb.count(), "rounds": len(bb.history),
+                          "U": round(bb.upper(), 5), "L": round(bb.lower(), 5),
+                          "seconds": round(dt, 3)}
+
     cpu = None
     if pool is not None:
         idx = np.linspace(0, B - 1, 2 * cores).astype(int)
@@ -537,7 +571,7 @@ def run_ours(args, rank, world, local_rank, dist):
         "roofline": roof, "kernels": kernels,
         "kernel_pass_ms_per_step": round(total_kernel_ms, 4),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-        "learned": learned, "learned_config4": learned4,
+        "learned": learned, "learned_config4": learned4, "bnb_config5": bnb5,
         "clocks": clocks,
     }
     return line
@@ -588,6 +622,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-bnb", action="store_true",
+                    help="skip the branch-and-bound refinement of the config-5 root box")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip training and timing the learned-degree form")
     ap.add_argument("--n-boxes", type=int, default=0,
