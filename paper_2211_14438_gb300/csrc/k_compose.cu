@@ -105,22 +105,46 @@ k_compose_queue(Tables T, ComposeArgs A, int64_t n_items, int row_dmax, ComposeS
 }
 
 // ------------------------------------------------------------ row convolution
-// acc[a+b] += x[a] * y[b] with directed FMAs, rows read from shared memory.
-// Off-diagonal row pairs (p < q) accumulate into acc (their product counts
-// twice in the square: doubled at the end, exactly); the diagonal pair
-// (p == q) into accd.
+constexpr int kRowWarps = 4;    // warps sharing one 32-item group
+constexpr int kRowBlocks = 6;   // resident blocks per SM (registers and shared memory)
+
+// One accumulator per output slot holds the square directly: an off-diagonal
+// row pair (p < q) counts twice in the square, so it multiplies 2*x[a]
+// (exact) by y[b]; the diagonal pair (p == q) is the row's own square,
+// sum_a x[a]^2 t^(2a) + sum_(a<b) 2 x[a] x[b] t^(a+b), taken as a triangle.
+// Every product is accumulated with a directed FMA.
 template <int L1, int L2, bool UP>
 __device__ __forceinline__ void conv_rows(const float* __restrict__ s, int offp, int offq,
                                           float (&acc)[2 * kRowLen - 1]) {
   float x[L1], y[L2];
 #pragma unroll
-  for (int a = 0; a < L1; ++a) x[a] = s[offp + a];
+  for (int a = 0; a < L1; ++a) {
+    const float v = s[offp + a];
+    x[a] = v + v;
+  }
 #pragma unroll
   for (int b = 0; b < L2; ++b) y[b] = s[offq + b];
 #pragma unroll
   for (int a = 0; a < L1; ++a)
 #pragma unroll
     for (int b = 0; b < L2; ++b) acc[a + b] = dfma<UP>(x[a], y[b], acc[a + b]);
+}
+
+template <int L, bool UP>
+__device__ __forceinline__ void conv_diag(const float* __restrict__ s, int off,
+                                          float (&acc)[2 * kRowLen - 1]) {
+  float x[L], x2[L];
+#pragma unroll
+  for (int a = 0; a < L; ++a) {
+    x[a] = s[off + a];
+    x2[a] = x[a] + x[a];
+  }
+#pragma unroll
+  for (int a = 0; a < L; ++a) {
+    acc[2 * a] = dfma<UP>(x[a], x[a], acc[2 * a]);
+#pragma unroll
+    for (int b = a + 1; b < L; ++b) acc[a + b] = dfma<UP>(x2[a], x[b], acc[a + b]);
+  }
 }
 
 #define BERN_CC(L1, L2) \
@@ -135,19 +159,20 @@ __device__ __forceinline__ void conv_rows(const float* __restrict__ s, int offp,
   BERN_CC(6, 7) BERN_CC(6, 8) BERN_CC(6, 9) BERN_CC(7, 7) BERN_CC(7, 8) BERN_CC(7, 9)          \
   BERN_CC(8, 8) BERN_CC(8, 9) BERN_CC(9, 9)
 #define BERN_CD(L) \
-  case L: conv_rows<L, L, UP>(s, pr.x, pr.x, accd); break;
+  case L: conv_diag<L, UP>(s, pr.x, acc); break;
 #define BERN_DIAG_CASES \
   BERN_CD(1) BERN_CD(2) BERN_CD(3) BERN_CD(4) BERN_CD(5) BERN_CD(6) BERN_CD(7) BERN_CD(8) BERN_CD(9)
 
 // Load one bound of the 32 items of a lane group into row layout:
 // s = (pre - lo*[K=0]) / (hi - lo) in round-to-nearest; returns this warp's
-// share of sum|s| (rounded up).  Warp `half` (0/1) takes every other group
+// share of sum|s| (rounded up).  Warp `half` (of kRowWarps) takes every
+// kRowWarps-th group
 // of 8 input monomials.
 __device__ float load_rows(const ComposeArgs& A, const RowTable& R, const float* P, int Mpre,
                            float Lo, float inv, int half, float* s) {
   const int h = A.h;
   float l1 = 0.0f;
-  for (int r0 = 8 * half; r0 < R.m_in; r0 += 16) {
+  for (int r0 = 8 * half; r0 < R.m_in; r0 += 8 * kRowWarps) {
     float v[8];
     int pos[8];
 #pragma unroll
@@ -188,12 +213,9 @@ __device__ void rows_range(const Tables& T, const ComposeArgs& A, const RowTable
     int rk[2 * kRowLen - 1];
 #pragma unroll
     for (int c = 0; c < 2 * kRowLen - 1; ++c) rk[c] = c < Lout ? __ldg(R.out_ranks + hd.z + c) : 0;
-    float acc[2 * kRowLen - 1], accd[2 * kRowLen - 1];
+    float acc[2 * kRowLen - 1];
 #pragma unroll
-    for (int c = 0; c < 2 * kRowLen - 1; ++c) {
-      acc[c] = 0.0f;
-      accd[c] = 0.0f;
-    }
+    for (int c = 0; c < 2 * kRowLen - 1; ++c) acc[c] = 0.0f;
     const int has_diag = (hd.w >> 16) & 1;
     const int off_end = hd.y - has_diag;
     if (hd.x < off_end) {
@@ -217,8 +239,7 @@ __device__ void rows_range(const Tables& T, const ComposeArgs& A, const RowTable
 #pragma unroll
     for (int c = 0; c < 2 * kRowLen - 1; ++c) {
       if (c >= Lout) break;
-      // (s^2) = diagonal part + 2 * off-diagonal part (2*x is exact)
-      const float sq = dfma<UP>(2.0f, acc[c], accd[c]);
+      const float sq = acc[c];            // (s^2)_K, directed
       const float lin = c < in_len ? s[in_off + c] : 0.0f;
       const float v = dfma<UP>(a2, sq, UP ? __fmul_ru(a1, lin) : __fmul_rd(a1, lin));
       if (row == 0 && c == 0) {
@@ -233,15 +254,15 @@ __device__ void rows_range(const Tables& T, const ComposeArgs& A, const RowTable
   *rem_out = rem;
 }
 
-// A block of two warps squares one bound (UP: upper) of 32 queued items (one
-// lane per item); the two warps share the items' inputs in shared memory and
-// take alternate output rows.
+// A block of kRowWarps warps squares one bound (UP: upper) of 32 queued items
+// (one lane per item); the warps share the items' inputs in shared memory and
+// take the output rows in turn.
 template <bool UP>
-__global__ void __launch_bounds__(64, 10)
+__global__ void __launch_bounds__(32 * kRowWarps, kRowBlocks)
 k_compose_rows(Tables T, ComposeArgs A, ComposeScratch S, int row_dmax, int sstride,
                int* status) {
   extern __shared__ float smem[];
-  __shared__ float s_l1[2][32], s_rem[2][32], s_c0[32];
+  __shared__ float s_l1[kRowWarps][32], s_rem[kRowWarps][32], s_c0[32];
   const int lane = threadIdx.x & 31, half = threadIdx.x >> 5;
   float* s = smem + (size_t)lane * sstride;
   for (int task = blockIdx.x;; task += gridDim.x) {
@@ -276,21 +297,24 @@ k_compose_rows(Tables T, ComposeArgs A, ComposeScratch S, int row_dmax, int sstr
     __syncthreads();
     float* Q = (UP ? A.post_up : A.post_lo) + A.base(valid ? item : 0, A.post_ld);
     float c0 = 0.0f, rem = 0.0f;
-    rows_range<UP>(T, A, R, D, half, R.n_out_rows, 2, valid, a1, a2, s, Q, &c0, &rem);
+    rows_range<UP>(T, A, R, D, half, R.n_out_rows, kRowWarps, valid, a1, a2, s, Q, &c0, &rem);
     s_rem[half][lane] = rem;
     if (!half) s_c0[lane] = c0;
     __syncthreads();
     if (!half && valid) {
       // constant term: a0 + (the row-0 value without a0) + Lip*eta + remainder
-      const float l1 = __fadd_ru(s_l1[0][lane], s_l1[1][lane]);
+      float l1 = s_l1[0][lane], remt = s_rem[0][lane];
+#pragma unroll
+      for (int w = 1; w < kRowWarps; ++w) {
+        l1 = __fadd_ru(l1, s_l1[w][lane]);
+        remt = UP ? __fadd_ru(remt, s_rem[w][lane]) : __fadd_rd(remt, s_rem[w][lane]);
+      }
       const float eta = __fmul_ru(5.0f * kU, l1);
       const float lip = __fmaf_ru(2.0f * a2, __fadd_ru(1.0f, eta), fabsf(a1));
       float v;
       if (UP) {
-        const float remt = __fadd_ru(s_rem[0][lane], s_rem[1][lane]);
         v = __fadd_ru(__fadd_ru(__fadd_ru(s_c0[lane], a0), __fmul_ru(lip, eta)), remt);
       } else {
-        const float remt = __fadd_rd(s_rem[0][lane], s_rem[1][lane]);
         v = __fsub_rd(__fadd_rd(s_c0[lane], a0), __fmul_ru(lip, eta));
         v = __fadd_rd(__fsub_rd(v, A.eps[item]), remt);
       }
@@ -513,9 +537,11 @@ cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratc
     if (e != cudaSuccess) return e;
   }
   const int64_t tasks = n_items / 32 + row_dmax + 1;
-  const int blocks = (int)std::min<int64_t>(tasks, 152 * 10);
-  k_compose_rows<true><<<blocks, 64, smem, L.stream>>>(T, A, S, row_dmax, sstride, L.status);
-  k_compose_rows<false><<<blocks, 64, smem, L.stream>>>(T, A, S, row_dmax, sstride, L.status);
+  const int blocks = (int)std::min<int64_t>(tasks, 152 * kRowBlocks);
+  k_compose_rows<true><<<blocks, 32 * kRowWarps, smem, L.stream>>>(T, A, S, row_dmax, sstride,
+                                                                   L.status);
+  k_compose_rows<false><<<blocks, 32 * kRowWarps, smem, L.stream>>>(T, A, S, row_dmax, sstride,
+                                                                    L.status);
   *L.launches += 2;
   k_compose_copy<<<(unsigned)std::min<int64_t>((n_items * pre_ld + 255) / 256, 152 * 16), 256, 0,
                    L.stream>>>(A, S);
