@@ -221,37 +221,13 @@ __global__ void __launch_bounds__(512, 3)
 k_enclose(Tables T, int G, const float2* __restrict__ rs, int64_t n_items, int h,
           const float* __restrict__ pre_up, const float* __restrict__ pre_lo, int64_t ld,
           const int32_t* __restrict__ nterms, float* __restrict__ lo, float* __restrict__ hi,
-          EncloseOpts ro, int* status, int stage_ld) {
+          EncloseOpts ro, int* status) {
   extern __shared__ float smem[];
   __shared__ float s_lohi[8][2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int per_block = blockDim.x >> 6;               // items per block
   const int64_t item = map_item(ro, (int64_t)blockIdx.x * per_block + (warp >> 1), n_items);
   const bool up = warp & 1;
-  // With stage_ld > 0 (consecutive items, no list) the block first copies its
-  // items' coefficients of both bounds into shared memory, neighbouring
-  // neurons together, so the global reads cover whole sectors.
-  float* stage = smem + (size_t)2 * per_block * G;    // [bound][slot][stage_ld]
-  if (stage_ld > 0) {
-    const int64_t first = (int64_t)blockIdx.x * per_block;
-    const int total = 2 * per_block * stage_ld;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-      const int bnd = idx / (per_block * stage_ld);
-      const int rem = idx - bnd * per_block * stage_ld;
-      const int r = rem / per_block, k = rem - r * per_block;
-      const int64_t it = first + k;
-      float v = 0.0f;
-      if (it < n_items) {
-        const int nt = nterms[it];
-        if (r < nt && nt <= ld) {
-          const int64_t b = it / h;
-          v = (bnd ? pre_up : pre_lo)[(b * ld + r) * h + (it - b * h)];
-        }
-      }
-      stage[((size_t)bnd * per_block + k) * stage_ld + r] = v;
-    }
-    __syncthreads();
-  }
   if (item >= 0) {
     int nt = nterms[item];
     if (nt < 0 || nt > ld || nt > T.mexps) {
@@ -261,17 +237,8 @@ k_enclose(Tables T, int G, const float2* __restrict__ rs, int64_t n_items, int h
     const int64_t b = item / h;
     const int64_t base = (b * ld) * h + (item - b * h);
     float* grid = smem + warp * G;
-    const float* pu = pre_up + base;
-    const float* pl = pre_lo + base;
-    int ps = h;
-    if (stage_ld > 0) {
-      const int slot = warp >> 1;
-      pu = stage + ((size_t)per_block + slot) * stage_ld;
-      pl = stage + (size_t)slot * stage_ld;
-      ps = 1;
-    }
-    const float v = up ? enclose_warp<LB, true>(pu, ps, nt, T.n, T, rs, grid)
-                       : enclose_warp<LB, false>(pl, ps, nt, T.n, T, rs, grid);
+    const float v = up ? enclose_warp<LB, true>(pre_up + base, h, nt, T.n, T, rs, grid)
+                       : enclose_warp<LB, false>(pre_lo + base, h, nt, T.n, T, rs, grid);
     if (lane == 0) {
       (up ? hi : lo)[item] = v;
       s_lohi[warp >> 1][up ? 1 : 0] = v;
@@ -304,15 +271,7 @@ cudaError_t launch_lb(const Launch& L, const Tables& T, int G, int64_t n_items, 
   if (items < 1) items = 1;
   TuneTimer tt;
   tune_begin(L, "enclose", tt);
-  size_t smem = (size_t)2 * items * G * sizeof(float);
-  // stage the inputs in shared memory when the items are consecutive and the
-  // copy is small
-  const size_t stage_bytes = (size_t)2 * items * ld * sizeof(float);
-  const int stage_ld =
-      (ro.list == nullptr && stage_bytes <= 32 * 1024 && smem + stage_bytes <= 200 * 1024)
-          ? (int)ld
-          : 0;
-  if (stage_ld) smem += stage_bytes;
+  const size_t smem = (size_t)2 * items * G * sizeof(float);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_enclose<LB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -321,7 +280,7 @@ cudaError_t launch_lb(const Launch& L, const Tables& T, int G, int64_t n_items, 
   const unsigned blocks = (unsigned)((n_items + items - 1) / items);
   k_enclose<LB><<<blocks, 64 * items, smem, L.stream>>>(T, G, T.rscale[LB], n_items, h, pre_up,
                                                         pre_lo, ld, nterms, lo, hi, ro,
-                                                        L.status, stage_ld);
+                                                        L.status);
   ++*L.launches;
   const cudaError_t e = cudaGetLastError();
   tune_end(L, "enclose", key, tt);
