@@ -23,6 +23,7 @@ host cores with the same metric and workload.
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import multiprocessing as mp
@@ -70,16 +71,20 @@ def oracle_rate(pool, cores, w, sample_idx):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,"
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms; the samples
+    whose timestamps fall inside the timed region (marked by begin()/end())
+    give the reported median clock and the reasons."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,"
               "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 50
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def start(self):
         fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
@@ -87,16 +92,23 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+        time.sleep(0.3)                     # first sample before the timed region
+
+    def begin(self):
+        self.t0 = datetime.datetime.now()
+
+    def end(self):
+        self.t1 = datetime.datetime.now()
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
                     "samples": 0}
-        time.sleep(0.25)
+        time.sleep(2.5 * self.PERIOD_MS / 1000.0)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -106,6 +118,10 @@ class ClockSampler:
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 10:
+                continue
+            try:
+                parts[0] = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+            except ValueError:
                 continue
             rows.append(parts)
         os.unlink(self.path)
@@ -117,20 +133,24 @@ class ClockSampler:
                 return float(x)
             except ValueError:
                 return None
-        sm = [num(r[1]) for r in rows]
-        util = [num(r[4]) for r in rows]
-        loaded = [s for s, u in zip(sm, util) if s is not None and u is not None and u >= 50]
-        use = loaded if loaded else [s for s in sm if s is not None]
+        t0, t1 = self.t0 or rows[0][0], self.t1 or rows[-1][0]
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        # a timed region shorter than the sampling period: the samples nearest to it
+        half = datetime.timedelta(milliseconds=self.PERIOD_MS)
+        window = inside or [r for r in rows if t0 - half <= r[0] <= t1 + half]
+        sm = [num(r[2]) for r in window if num(r[2]) is not None]
         reasons = set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
+        for r in window:
             for name, v in zip(names, r[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(name)
-        return {"sm_mhz": float(np.median(use)) if use else None,
-                "sm_max_mhz": num(rows[0][2]), "reasons": sorted(reasons),
-                "samples": len(rows), "samples_under_load": len(loaded),
-                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": num(rows[0][3]), "reasons": sorted(reasons),
+                "samples": len(rows), "samples_in_timed_region": len(inside),
+                "samples_used": len(window),
+                "timed_region_ms": round((t1 - t0).total_seconds() * 1000.0, 1),
+                "power_w_max": max((num(r[4]) or 0.0) for r in window) if window else None}
 
 
 # ----------------------------------------------------- per-kernel timing pass
@@ -330,12 +350,14 @@ def run_ours(args, rank, world, local_rank, dist):
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = ctx.kernel_launches()
+    sampler.begin()
     for k in range(args.steps):
         flush.zero_()
         starts[k].record(stream)
         step()
         ends[k].record(stream)
     torch.cuda.synchronize()
+    sampler.end()
     if dist is not None:
         dist.barrier()
     clocks = sampler.stop()
