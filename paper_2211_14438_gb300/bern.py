@@ -51,7 +51,7 @@ EXPORTS = [
     "bern_enclose", "bern_relu_coeffs", "bern_compose", "bern_propagate_noalloc",
     "bern_mlp_num_params", "bern_degree_features", "bern_mlp_forward", "bern_mlp_backward",
     "bern_mlp_adam", "bern_propagate_traced", "bern_split_features",
-    "bern_set_horner_smem_limit", "bern_set_autotune",
+    "bern_set_horner_smem_limit", "bern_set_autotune", "bern_force_variant",
 ]
 
 
@@ -117,6 +117,7 @@ def load(build_if_missing: bool = True):
         "bern_set_graphs": (I, [V, I]),
         "bern_set_horner_smem_limit": (I, [V, I64]),
         "bern_set_autotune": (I, [V, I]),
+        "bern_force_variant": (I, [V, ctypes.c_char_p, I]),
         "bern_strerror": (ctypes.c_char_p, [I]),
         "bern_sync": (I, [V]),
         "bern_kernel_launches": (I64, [V]),
@@ -219,6 +220,12 @@ class Context:
 
     def set_autotune(self, on: bool):
         _check(self.lib.bern_set_autotune(self.h, 1 if on else 0), "bern_set_autotune")
+
+    def force_variant(self, kind: str, variant: int):
+        """Force variant `variant` (-1: none) of kernel family `kind`
+        ("affine" or "enclose") for later launches (tests and tuning)."""
+        _check(self.lib.bern_force_variant(self.h, kind.encode(), int(variant)),
+               "bern_force_variant")
 
     def set_horner_smem_limit(self, nbytes: int):
         _check(self.lib.bern_set_horner_smem_limit(self.h, int(nbytes)),

@@ -667,6 +667,22 @@ int bern_set_autotune(bern_ctx* c, int enable) {
   return BERN_OK;
 }
 
+int bern_force_variant(bern_ctx* c, const char* kind, int variant) {
+  if (!c || !kind) return BERN_E_INVALID;
+  const std::string k(kind);
+  const int nvar = k == "affine" ? 4 : (k == "enclose" ? 3 : 0);
+  if (nvar == 0 || variant < -1 || variant >= nvar) return BERN_E_INVALID;
+  cudaStreamSynchronize(c->stream);
+  for (auto& g : c->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+  if (variant < 0)
+    c->tuner.forced.erase(k);
+  else
+    c->tuner.forced[k] = variant;
+  return BERN_OK;
+}
+
 int bern_set_horner_smem_limit(bern_ctx* c, int64_t bytes) {
   if (!c || bytes < 0) return BERN_E_INVALID;
   c->horner_smem_limit = bytes;
@@ -899,7 +915,7 @@ int bern_propagate_traced(bern_ctx* c, const bern_net* net, const float* boxes,
       Chunk ch{(char*)c->ws.p, B};
       if ((rc = fill_degrees(c, P, ch, B))) return rc;
       const char* kinds[] = {"affine", "enclose"};
-      const int nvar[] = {3, 3};
+      const int nvar[] = {4, 3};
       for (int k = 0; k < 2; ++k) {
         for (int v = 0; v < nvar[k]; ++v) {
           c->tuner.probe_kind = kinds[k];

@@ -133,6 +133,7 @@ struct Tuner {
   std::string probe_kind;                                 // empty: no probe pass
   int probe_variant = -1;
   std::map<std::string, std::vector<float>> probe_ms;     // key -> ms per variant
+  std::map<std::string, int> forced;                      // kind -> variant (tests)
 };
 
 struct Launch {

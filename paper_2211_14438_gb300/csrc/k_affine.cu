@@ -279,6 +279,148 @@ k_affine_persistent(int64_t n_boxes, int h_out, int h_in, const float* __restric
   }
 }
 
+// Persistent, register-blocked form for the wide layers: a block of four
+// warps keeps W (h_in x h_out, k-major, neurons padded to 64) in shared
+// memory for the whole launch and walks boxes; per box it stages 64-row tiles
+// of the input as (midpoint, radius) pairs, and every thread accumulates an
+// 8 (neurons) x 4 (rows) tile of the three sums per 64-neuron slice, reading
+// 8 weights as two float4 and 4 pairs as float2 per input j (|w| is taken in
+// the radius FMA itself).  A warp covers 16 rows of the tile and skips the
+// tile when all of them are at or past the box's term count.
+constexpr int kWRows = 64;
+constexpr int kWThreads = 128;
+
+__global__ void __launch_bounds__(kWThreads, 3)
+k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
+              const float* __restrict__ bias, const float* __restrict__ in_up,
+              const float* __restrict__ in_lo, int64_t in_ld,
+              const int32_t* __restrict__ in_nterms, float* __restrict__ out_up,
+              float* __restrict__ out_lo, int64_t out_ld, int32_t* __restrict__ out_nterms,
+              int* status) {
+  extern __shared__ float4 smem4[];
+  const int hp = (h_out + 63) & ~63;                 // neurons padded to 64
+  float* sW = reinterpret_cast<float*>(smem4);       // [h_in][hp]
+  float2* sCR = reinterpret_cast<float2*>(sW + (size_t)h_in * hp);   // [kWRows][h_in + 1]
+  int* sN = reinterpret_cast<int*>(sCR + (size_t)kWRows * (h_in + 1));   // [h_in]
+  __shared__ int sMax;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int idx = tid; idx < h_in * hp; idx += kWThreads) {
+    const int j = idx / hp, m = idx - j * hp;
+    sW[idx] = m < h_out ? W[(int64_t)m * h_in + j] : 0.0f;
+  }
+  const int tm = tid & 7, tr = tid >> 3;             // 8 x 16 threads
+  const int ldx = h_in + 1;
+  const bool vec_out =
+      (h_out & 3) == 0 &&
+      ((reinterpret_cast<uintptr_t>(out_up) | reinterpret_cast<uintptr_t>(out_lo)) & 15) == 0;
+  for (int64_t b = blockIdx.x; b < n_boxes; b += gridDim.x) {
+    if (tid == 0) sMax = 0;
+    __syncthreads();                                 // also: W staged, previous box done
+    int mloc = 0;
+    for (int j = tid; j < h_in; j += kWThreads) {
+      int v = in_nterms[b * h_in + j];
+      if (v < 0 || v > in_ld) {
+        atomicOr(status, kStatusInvalid);
+        v = 0;
+      }
+      sN[j] = v;
+      mloc = max(mloc, v);
+    }
+    mloc = warp_imax(mloc);
+    if ((tid & 31) == 0) atomicMax(&sMax, mloc);
+    __syncthreads();
+    const int M = max(1, sMax);
+    if (M > out_ld) {
+      if (tid == 0) atomicOr(status, kStatusCapacity);
+      continue;
+    }
+    for (int m = tid; m < h_out; m += kWThreads) out_nterms[b * h_out + m] = M;
+    const float* gU = in_up + (b * in_ld) * h_in;
+    const float* gL = in_lo + (b * in_ld) * h_in;
+    for (int r0 = 0; r0 < M; r0 += kWRows) {
+      __syncthreads();                               // the previous tile is consumed
+      for (int idx = tid; idx < kWRows * h_in; idx += kWThreads) {
+        const int rr = idx / h_in, j = idx - rr * h_in;
+        const int r = r0 + rr;
+        float c = 0.0f, rd = 0.0f;
+        if (r < sN[j]) {                             // sN[j] <= M <= in_ld
+          const float u = gU[(int64_t)r * h_in + j];
+          const float l = gL[(int64_t)r * h_in + j];
+          c = __fmaf_rn(0.5f, u, 0.5f * l);
+          rd = fmaxf(__fsub_ru(u, c), __fsub_ru(c, l));
+        }
+        sCR[rr * ldx + j] = make_float2(c, rd);
+      }
+      __syncthreads();
+      if (r0 + warp * 16 >= M) continue;             // warp-uniform; no barrier follows
+      for (int m0 = 0; m0 < h_out; m0 += 64) {
+        float uc[4][8], lc[4][8], rad[4][8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int m = m0 + tm * 8 + i, r = r0 + tr * 4 + k;
+            const float b0 = (r == 0 && m < h_out) ? bias[m] : 0.0f;
+            uc[k][i] = b0;
+            lc[k][i] = b0;
+            rad[k][i] = 0.0f;
+          }
+        const float* pw = sW + m0 + tm * 8;
+        const float2* pcr = sCR + (tr * 4) * ldx;
+#pragma unroll 2
+        for (int j = 0; j < h_in; ++j) {
+          const float4 wa = *reinterpret_cast<const float4*>(pw + (size_t)j * hp);
+          const float4 wb = *reinterpret_cast<const float4*>(pw + (size_t)j * hp + 4);
+          const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+          float2 cr[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) cr[k] = pcr[k * ldx + j];
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              uc[k][i] = __fmaf_ru(w[i], cr[k].x, uc[k][i]);
+              lc[k][i] = __fmaf_rd(w[i], cr[k].x, lc[k][i]);
+              rad[k][i] = __fmaf_ru(fabsf(w[i]), cr[k].y, rad[k][i]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int r = r0 + tr * 4 + k;
+          if (r >= M) continue;
+          const int mb = m0 + tm * 8;
+          float vu[8], vl[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            vu[i] = __fadd_ru(uc[k][i], rad[k][i]);
+            vl[i] = __fsub_rd(lc[k][i], rad[k][i]);
+          }
+          const int64_t o = (b * out_ld + r) * h_out + mb;
+          if (vec_out && mb + 8 <= h_out) {
+            *reinterpret_cast<float4*>(out_up + o) = make_float4(vu[0], vu[1], vu[2], vu[3]);
+            *reinterpret_cast<float4*>(out_up + o + 4) = make_float4(vu[4], vu[5], vu[6], vu[7]);
+            *reinterpret_cast<float4*>(out_lo + o) = make_float4(vl[0], vl[1], vl[2], vl[3]);
+            *reinterpret_cast<float4*>(out_lo + o + 4) = make_float4(vl[4], vl[5], vl[6], vl[7]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+              if (mb + i < h_out) {
+                out_up[o + i] = vu[i];
+                out_lo[o + i] = vl[i];
+              }
+          }
+        }
+      }
+    }
+  }
+}
+
+static size_t wide_smem(int h_out, int h_in) {
+  const size_t hp = (size_t)((h_out + 63) & ~63);
+  return hp * h_in * sizeof(float) + (size_t)kWRows * (h_in + 1) * sizeof(float2) +
+         (size_t)h_in * sizeof(int);
+}
+
 static size_t persistent_smem(int h_out, int h_in) {
   const size_t hp = (size_t)((h_out + 63) & ~63);
   return (2 * hp * h_in + 2 * (size_t)kPRows * (h_in + 1)) * sizeof(float) +
@@ -468,6 +610,121 @@ k_affine_narrow_warp(int64_t n_boxes, int h_out, int h_in, const float* __restri
   }
 }
 
+// Narrow layers (h_out <= 4) with h_in a multiple of 4 and 16-byte aligned
+// rows, quad form: G lanes share one monomial row, each lane reading four
+// consecutive inputs j as one float4, so a warp reads 32 / G whole rows per
+// load; U such loads are issued before any is used.  Each lane keeps the
+// weights and term counts of its four inputs in registers; the G partial sums
+// of a row are combined by a directed shuffle reduction (round-up for the
+// upper sum, round-down for the lower one), which bounds the exact sum from
+// the correct side in any order.  A block takes one box and kQRows rows.
+constexpr int kQRows = 256;
+
+template <int HO, int G>
+__global__ void __launch_bounds__(256)
+k_affine_narrow_quad(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
+                     const float* __restrict__ bias, const float* __restrict__ in_up,
+                     const float* __restrict__ in_lo, int64_t in_ld,
+                     const int32_t* __restrict__ in_nterms, float* __restrict__ out_up,
+                     float* __restrict__ out_lo, int64_t out_ld, int32_t* __restrict__ out_nterms,
+                     int* status) {
+  constexpr int R = 32 / G;                          // rows per warp load
+  constexpr int U = 4;                               // loads in flight per warp
+  __shared__ int sMax;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int q = lane % G, s = lane / G;
+  const int64_t b = blockIdx.x;
+  if (threadIdx.x == 0) sMax = 0;
+  __syncthreads();
+  int mloc = 0;
+  for (int j = threadIdx.x; j < h_in; j += blockDim.x) {
+    int v = in_nterms[b * h_in + j];
+    if (v < 0 || v > in_ld) {
+      atomicOr(status, kStatusInvalid);
+      v = 0;
+    }
+    mloc = max(mloc, v);
+  }
+  mloc = warp_imax(mloc);
+  if (lane == 0) atomicMax(&sMax, mloc);
+  __syncthreads();
+  const int M = max(1, sMax);
+  if (M > out_ld) {
+    if (threadIdx.x == 0 && blockIdx.y == 0) atomicOr(status, kStatusCapacity);
+    return;
+  }
+  if (blockIdx.y == 0 && threadIdx.x < h_out) out_nterms[b * h_out + threadIdx.x] = M;
+  const bool qlive = 4 * q < h_in;
+  float w[HO][4];
+  int nt[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int j = 4 * q + i;
+    int v = qlive ? in_nterms[b * h_in + j] : 0;
+    nt[i] = (v < 0 || v > in_ld) ? 0 : v;
+#pragma unroll
+    for (int m = 0; m < HO; ++m) w[m][i] = (qlive && m < h_out) ? W[(int64_t)m * h_in + j] : 0.0f;
+  }
+  const float4* pu = reinterpret_cast<const float4*>(in_up + (b * in_ld) * h_in) + q;
+  const float4* pl = reinterpret_cast<const float4*>(in_lo + (b * in_ld) * h_in) + q;
+  const int h4 = h_in >> 2;
+  const int r_end = min(M, (int)(blockIdx.y + 1) * kQRows);
+  for (int r0 = blockIdx.y * kQRows + warp * R * U; r0 < r_end; r0 += 8 * R * U) {
+    float4 u[U], l[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int r = r0 + k * R + s;
+      if (qlive && r < r_end) {
+        u[k] = __ldg(pu + (int64_t)r * h4);
+        l[k] = __ldg(pl + (int64_t)r * h4);
+      } else {
+        u[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        l[k] = u[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int r = r0 + k * R + s;
+      const float uu[4] = {r < nt[0] ? u[k].x : 0.0f, r < nt[1] ? u[k].y : 0.0f,
+                           r < nt[2] ? u[k].z : 0.0f, r < nt[3] ? u[k].w : 0.0f};
+      const float ll[4] = {r < nt[0] ? l[k].x : 0.0f, r < nt[1] ? l[k].y : 0.0f,
+                           r < nt[2] ? l[k].z : 0.0f, r < nt[3] ? l[k].w : 0.0f};
+      float up[HO], lo[HO];
+#pragma unroll
+      for (int m = 0; m < HO; ++m) {
+        up[m] = 0.0f;
+        lo[m] = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const bool pos = w[m][i] > 0.0f;
+          up[m] = __fmaf_ru(w[m][i], pos ? uu[i] : ll[i], up[m]);
+          lo[m] = __fmaf_rd(w[m][i], pos ? ll[i] : uu[i], lo[m]);
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+          up[m] = __fadd_ru(up[m], __shfl_xor_sync(0xffffffffu, up[m], o));
+          lo[m] = __fadd_rd(lo[m], __shfl_xor_sync(0xffffffffu, lo[m], o));
+        }
+      }
+      if (q == 0 && r < r_end) {
+#pragma unroll
+        for (int m = 0; m < HO; ++m) {
+          if (m < h_out) {
+            float vu = up[m], vl = lo[m];
+            if (r == 0) {
+              vu = __fadd_ru(vu, bias[m]);
+              vl = __fadd_rd(vl, bias[m]);
+            }
+            const int64_t o = (b * out_ld + r) * h_out + m;
+            out_up[o] = vu;
+            out_lo[o] = vl;
+          }
+        }
+      }
+    }
+  }
+}
+
 template <int BM, int BR, int TM, int TR, int KC>
 static cudaError_t launch_cfg(const Launch& L, int64_t n_boxes, int h_out, int h_in,
                               const float* W, const float* b, const float* in_up,
@@ -502,16 +759,31 @@ cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
   const bool few_rows = std::min(in_ld, out_ld) <= 16;     // short polynomials: short tiles
   const size_t psmem = persistent_smem(h_out, h_in);
   if (h_out >= 32 && !few_rows) {
-    // wide layers: autotuned among the persistent kernel (0, when its
-    // weights fit shared memory) and two tile shapes (1: 64 x 32, 2: 64 x 64)
+    // wide layers: autotuned among the persistent kernels (0: 4 x 4 tiles,
+    // 3: register-blocked 8 x 4 tiles; each when its weights fit shared
+    // memory) and two tile shapes (1: 64 x 32, 2: 64 x 64)
     const std::string key = "affine/" + std::to_string(h_out) + "/" + std::to_string(h_in) +
                             "/" + std::to_string(in_ld) + "/" + std::to_string(n_boxes);
-    int v = tune_variant(L, "affine", key, psmem <= 72 * 1024 ? 0 : 1);
+    const size_t wsmem = wide_smem(h_out, h_in);
+    const bool wide_ok = wsmem <= 200 * 1024;
+    int v = tune_variant(L, "affine", key, wide_ok ? 3 : (psmem <= 72 * 1024 ? 0 : 1));
     if (v == 0 && psmem > 72 * 1024) v = 1;
+    if (v == 3 && !wide_ok) v = 1;
     TuneTimer tt;
     tune_begin(L, "affine", tt);
     cudaError_t e;
-    if (v == 0) {
+    if (v == 3) {
+      e = cudaFuncSetAttribute(k_affine_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)wsmem);
+      if (e != cudaSuccess) return e;
+      const int per_sm = wsmem <= 72 * 1024 ? 3 : (wsmem <= 110 * 1024 ? 2 : 1);
+      const int64_t blocks = std::min<int64_t>(n_boxes, 152 * per_sm);
+      k_affine_wide<<<(unsigned)blocks, kWThreads, wsmem, L.stream>>>(
+          n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld, in_nterms, out_up, out_lo, out_ld,
+          out_nterms, L.status);
+      ++*L.launches;
+      e = cudaGetLastError();
+    } else if (v == 0) {
       e = cudaFuncSetAttribute(k_affine_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)psmem);
       if (e != cudaSuccess) return e;
@@ -540,6 +812,26 @@ cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
   if (h_out > 8)
     return launch_cfg<16, 64, 2, 4, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
                                         in_nterms, out_up, out_lo, out_ld, out_nterms);
+  // narrow outputs (h_out <= 4, h_in <= 128 a multiple of 4, aligned rows):
+  // lanes over float4 quads of a row
+  if (h_out <= 4 && (h_in & 3) == 0 && h_in <= 128 &&
+      ((reinterpret_cast<uintptr_t>(in_up) | reinterpret_cast<uintptr_t>(in_lo)) & 15) == 0) {
+    const int64_t rows = std::max<int64_t>(1, std::min(in_ld, out_ld));
+    if ((rows + kQRows - 1) / kQRows > 65535) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)n_boxes, (unsigned)((rows + kQRows - 1) / kQRows));
+    const int q4 = h_in >> 2;
+    const int g = q4 <= 4 ? 4 : (q4 <= 8 ? 8 : (q4 <= 16 ? 16 : 32));
+#define BERN_NQ(HO, G)                                                                        \
+  if ((HO == 1) == (h_out == 1) && g == G)                                                    \
+    k_affine_narrow_quad<HO, G><<<grid, 256, 0, L.stream>>>(                                  \
+        n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld, in_nterms, out_up, out_lo, out_ld,   \
+        out_nterms, L.status);
+    BERN_NQ(1, 4) BERN_NQ(1, 8) BERN_NQ(1, 16) BERN_NQ(1, 32)
+    BERN_NQ(4, 4) BERN_NQ(4, 8) BERN_NQ(4, 16) BERN_NQ(4, 32)
+#undef BERN_NQ
+    ++*L.launches;
+    return cudaGetLastError();
+  }
   // narrow outputs (h_out <= 4, h_in <= 256): a warp per monomial row
   if (h_out <= 4 && h_in <= 32 * kNarrowMaxJ) {
     const int64_t rows = std::max<int64_t>(1, std::min(in_ld, out_ld));

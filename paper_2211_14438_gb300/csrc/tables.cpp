@@ -333,6 +333,8 @@ int tune_variant(const Launch& L, const char* kind, const std::string& key, int 
   if (!L.tuner) return dflt;
   if (!L.tuner->probe_kind.empty())
     return L.tuner->probe_kind == kind ? L.tuner->probe_variant : dflt;
+  auto f = L.tuner->forced.find(kind);
+  if (f != L.tuner->forced.end()) return f->second;
   auto it = L.tuner->best.find(key);
   return it == L.tuner->best.end() ? dflt : it->second;
 }

@@ -271,6 +271,38 @@ def test_output_keys_are_graded_monomials(ctx):
     assert np.array_equal(g["keys"][0, 0, 1, :nt], want)
 
 
+@pytest.mark.parametrize("widths,seed", [([3, 64, 64, 64, 64, 1], 2), ([6, 100, 100, 2], 3),
+                                        ([3, 40, 72, 48, 4], 5)])
+def test_forced_variants_identical(ctx, widths, seed):
+    """Every variant of the wide-layer affine kernel (persistent 4x4 tiles,
+    64x32 and 64x64 tiles, persistent register-blocked 8x4 tiles) and of the
+    enclosure (8, 4, 2 items per block) gives the same bits, on layers 64 and
+    100 wide and on widths that are not multiples of 64."""
+    net = wl.make_net(widths, seed)
+    rng = np.random.default_rng(seed)
+    n = widths[0]
+    c = rng.uniform(-1, 1, (24, n))
+    s = rng.uniform(0.05, 0.6, (24, n))
+    boxes = wl.box_array(c - s / 2, c + s / 2)
+    ref = None
+    try:
+        for kind, nv in (("affine", 4), ("enclose", 3)):
+            for v in range(nv):
+                ctx.force_variant(kind, v)
+                g = run_gpu(ctx, net, boxes)
+                ctx.force_variant(kind, -1)
+                if ref is None:
+                    ref = g
+                for k in ("lo", "hi", "n_terms", "coef"):
+                    assert np.array_equal(g[k], ref[k]), (kind, v, k)
+    finally:
+        ctx.force_variant("affine", -1)
+        ctx.force_variant("enclose", -1)
+    r = oracle.propagate(widths, net.W, net.b, boxes[0], 2)
+    if not near_tie(r):
+        compare_box(ref, 0, r, n, widths[-1])
+
+
 def test_autotune_on_off_identical(ctx):
     """Every tunable variant computes the same values: results with the
     autotuner's choices equal those with the built-in defaults, bit for bit."""
