@@ -283,12 +283,16 @@ k_affine_persistent(int64_t n_boxes, int h_out, int h_in, const float* __restric
 // warps keeps W (h_in x h_out, k-major, neurons padded to 64) in shared
 // memory for the whole launch and walks boxes; per box it stages 64-row tiles
 // of the input as (midpoint, radius) pairs, and every thread accumulates an
-// 8 (neurons) x 4 (rows) tile of the three sums per 64-neuron slice, reading
-// 8 weights as two float4 and 4 pairs as float2 per input j (|w| is taken in
-// the radius FMA itself).  A warp covers 16 rows of the tile and skips the
-// tile when all of them are at or past the box's term count.
+// 8 (neurons) x 4 (rows) tile of the three sums per 64-neuron slice: neurons
+// 4 tm .. 4 tm + 3 and 32 + 4 tm .. 32 + 4 tm + 3, so the eight lanes of a
+// row read each half of the slice's weights as one contiguous 128-byte float4
+// load; 4 pairs are read as float2 per input j, and |w| is taken in the
+// radius FMA itself.  The staging issues kWBatch loads of each bound per
+// thread before converting any.  A warp covers 16 rows of the tile and skips
+// the tile when all of them are at or past the box's term count.
 constexpr int kWRows = 64;
 constexpr int kWThreads = 128;
+constexpr int kWBatch = 8;
 
 __global__ void __launch_bounds__(kWThreads, 3)
 k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
@@ -310,6 +314,7 @@ k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
   }
   const int tm = tid & 7, tr = tid >> 3;             // 8 x 16 threads
   const int ldx = h_in + 1;
+  const int step_r = kWThreads / h_in, step_j = kWThreads - step_r * h_in;
   const bool vec_out =
       (h_out & 3) == 0 &&
       ((reinterpret_cast<uintptr_t>(out_up) | reinterpret_cast<uintptr_t>(out_lo)) & 15) == 0;
@@ -339,17 +344,33 @@ k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
     const float* gL = in_lo + (b * in_ld) * h_in;
     for (int r0 = 0; r0 < M; r0 += kWRows) {
       __syncthreads();                               // the previous tile is consumed
-      for (int idx = tid; idx < kWRows * h_in; idx += kWThreads) {
-        const int rr = idx / h_in, j = idx - rr * h_in;
-        const int r = r0 + rr;
-        float c = 0.0f, rd = 0.0f;
-        if (r < sN[j]) {                             // sN[j] <= M <= in_ld
-          const float u = gU[(int64_t)r * h_in + j];
-          const float l = gL[(int64_t)r * h_in + j];
-          c = __fmaf_rn(0.5f, u, 0.5f * l);
-          rd = fmaxf(__fsub_ru(u, c), __fsub_ru(c, l));
+      // element idx = rr * h_in + j of the tile; (rr, j) advance by
+      // (step_r, step_j) per kWThreads elements
+      int rr = tid / h_in, j = tid - (tid / h_in) * h_in;
+      for (int idx = tid; idx < kWRows * h_in; idx += kWThreads * kWBatch) {
+        float u[kWBatch], l[kWBatch];
+        int at[kWBatch];
+#pragma unroll
+        for (int q = 0; q < kWBatch; ++q) {
+          const bool in = idx + q * kWThreads < kWRows * h_in;
+          const int r = r0 + rr;
+          const bool live = in && r < sN[j];         // sN[j] <= M <= in_ld
+          u[q] = live ? gU[(int64_t)r * h_in + j] : 0.0f;
+          l[q] = live ? gL[(int64_t)r * h_in + j] : 0.0f;
+          at[q] = in ? rr * ldx + j : -1;
+          rr += step_r;
+          j += step_j;
+          if (j >= h_in) {
+            j -= h_in;
+            ++rr;
+          }
         }
-        sCR[rr * ldx + j] = make_float2(c, rd);
+#pragma unroll
+        for (int q = 0; q < kWBatch; ++q) {
+          const float c = __fmaf_rn(0.5f, u[q], 0.5f * l[q]);
+          const float rd = fmaxf(__fsub_ru(u[q], c), __fsub_ru(c, l[q]));
+          if (at[q] >= 0) sCR[at[q]] = make_float2(c, rd);
+        }
       }
       __syncthreads();
       if (r0 + warp * 16 >= M) continue;             // warp-uniform; no barrier follows
@@ -359,18 +380,18 @@ k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
         for (int k = 0; k < 4; ++k)
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            const int m = m0 + tm * 8 + i, r = r0 + tr * 4 + k;
+            const int m = m0 + (i < 4 ? 4 * tm + i : 28 + 4 * tm + i), r = r0 + tr * 4 + k;
             const float b0 = (r == 0 && m < h_out) ? bias[m] : 0.0f;
             uc[k][i] = b0;
             lc[k][i] = b0;
             rad[k][i] = 0.0f;
           }
-        const float* pw = sW + m0 + tm * 8;
+        const float* pw = sW + m0 + tm * 4;
         const float2* pcr = sCR + (tr * 4) * ldx;
 #pragma unroll 2
         for (int j = 0; j < h_in; ++j) {
           const float4 wa = *reinterpret_cast<const float4*>(pw + (size_t)j * hp);
-          const float4 wb = *reinterpret_cast<const float4*>(pw + (size_t)j * hp + 4);
+          const float4 wb = *reinterpret_cast<const float4*>(pw + (size_t)j * hp + 32);
           const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
           float2 cr[4];
 #pragma unroll
@@ -388,26 +409,30 @@ k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
         for (int k = 0; k < 4; ++k) {
           const int r = r0 + tr * 4 + k;
           if (r >= M) continue;
-          const int mb = m0 + tm * 8;
           float vu[8], vl[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             vu[i] = __fadd_ru(uc[k][i], rad[k][i]);
             vl[i] = __fsub_rd(lc[k][i], rad[k][i]);
           }
-          const int64_t o = (b * out_ld + r) * h_out + mb;
-          if (vec_out && mb + 8 <= h_out) {
-            *reinterpret_cast<float4*>(out_up + o) = make_float4(vu[0], vu[1], vu[2], vu[3]);
-            *reinterpret_cast<float4*>(out_up + o + 4) = make_float4(vu[4], vu[5], vu[6], vu[7]);
-            *reinterpret_cast<float4*>(out_lo + o) = make_float4(vl[0], vl[1], vl[2], vl[3]);
-            *reinterpret_cast<float4*>(out_lo + o + 4) = make_float4(vl[4], vl[5], vl[6], vl[7]);
-          } else {
+          const int64_t o = (b * out_ld + r) * h_out + m0;
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-              if (mb + i < h_out) {
-                out_up[o + i] = vu[i];
-                out_lo[o + i] = vl[i];
-              }
+          for (int half = 0; half < 2; ++half) {
+            const int mb = m0 + 32 * half + 4 * tm;
+            const int64_t oh = o + 32 * half + 4 * tm;
+            const float* pu = vu + 4 * half;
+            const float* pl = vl + 4 * half;
+            if (vec_out && mb + 4 <= h_out) {
+              *reinterpret_cast<float4*>(out_up + oh) = make_float4(pu[0], pu[1], pu[2], pu[3]);
+              *reinterpret_cast<float4*>(out_lo + oh) = make_float4(pl[0], pl[1], pl[2], pl[3]);
+            } else {
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+                if (mb + i < h_out) {
+                  out_up[oh + i] = pu[i];
+                  out_lo[oh + i] = pl[i];
+                }
+            }
           }
         }
       }
