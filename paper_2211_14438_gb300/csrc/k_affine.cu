@@ -8,53 +8,28 @@
 // round-down FMAs, so each computed coefficient bounds the exact one from the
 // correct side; with t^K >= 0 on the box that bounds the polynomial values.
 //
-// The wide-layer kernels use the midpoint-radius form of the same step: with
-// c = fl((up + lo) / 2) and r >= max(up - c, c - lo) (rounded up), every input
-// coefficient lies in [c - r, c + r], so for any weight w
-//   w x <= w c + |w| r  and  w x >= w c - |w| r  for every x in [c - r, c + r].
-// The centre sum s = b + sum_j w_j c_j is accumulated with round-to-nearest
-// FMAs in a fixed order; by the standard error bound of recursive summation
-// with a fused multiply-add per term (Higham, Accuracy and Stability of
-// Numerical Algorithms, 2nd ed., Sec. 3.1, with gamma_n = n u / (1 - n u),
-// u = 2^-24, plus an absolute n 2^-149 for gradual underflow),
-//   |s - exact| <= gamma_n (|b| + sum_j |w_j| |c_j|) + n 2^-149,
-// with n = h_in FMAs.  Folding gamma_n |c_j| into the radius,
-// r'_j = RU(r_j + RU(gamma_n |c_j|)), the radius sum R = RU(sum_j |w_j| r'_j)
-// (round-up FMAs, all terms non-negative) and E = RU(gamma_n |b| + n 2^-149)
-// (or n 2^-149 off the constant monomial) give
-//   pre_up = RU(RU(s + R) + E) >= exact upper sum,
-//   pre_lo = RD(RD(s - R) - E) <= exact lower sum:
-// two FMAs per product (s and R) instead of a round-up and a round-down copy
-// of the centre sum, for a bound wider by about gamma_n |w| |c|.
+// The tiled kernel uses the midpoint-radius form of the same step: with
+// c = fl((up + lo) / 2) and r >= max(up - c, c - lo) (rounded up), every
+// input coefficient lies in [c - r, c + r], and for any weight w
+//   w+ up + w- lo = w c + |w| r  (exactly, when c, r are exact),
+//   w x <= w c + |w| r  for every x in [c - r, c + r];
+// so pre_up = RU(b + sum_j w c) + RU(sum_j |w| r) and pre_lo = RD(b + sum_j
+// w c) - RU(sum_j |w| r) bound the sign-split sums from the correct side
+// (r exceeds (up - lo)/2 by at most an ulp of c).  This needs three FMAs per
+// product and no per-product select of the operand by the sign of w.
 //
 // With the layer-block layout (coefficient r of neuron j of box b at
 // ((b*ld + r)*h + j)) each box is a row-major [M x h_in] matrix per bound and
-// the step is the product with W^T: a small GEMM per box.  The tiled kernel
-// computes a BM (neurons) x BR (monomials) tile of one box per block; K
-// (= h_in) is staged through shared memory in chunks of KC, and every thread
-// keeps a TM x TR register tile of both sums.  Inputs beyond a neuron's term
-// count are read as zero.
+// the step is the product with W^T: a small GEMM per box.  A block computes a
+// BM (neurons) x BR (monomials) tile of one box; K (= h_in) is staged through
+// shared memory in chunks of KC, and every thread keeps a TM x TR register
+// tile per bound.  Inputs beyond a neuron's term count are read as zero.
 #include <algorithm>
-#include <cmath>
 #include <string>
 
 #include "device_util.cuh"
 
 namespace bern {
-
-// Error terms of the centre sum (see the head of this file): E_b for the
-// constant monomial (bias b), E_0 elsewhere.
-__device__ __forceinline__ float centre_err(float gamma, float b, int h_in, bool constant) {
-  const float eta = __fmul_ru((float)h_in, __int_as_float(1));   // h_in * 2^-149
-  return constant ? __fmaf_ru(gamma, fabsf(b), eta) : eta;
-}
-
-// (midpoint, inflated radius) of one input coefficient interval [l, u]
-__device__ __forceinline__ float2 mid_rad(float u, float l, float gamma) {
-  const float c = __fmaf_rn(0.5f, u, 0.5f * l);
-  const float rd = fmaxf(__fsub_ru(u, c), __fsub_ru(c, l));
-  return make_float2(c, __fadd_ru(rd, __fmul_ru(gamma, fabsf(c))));
-}
 
 template <int BM, int BR, int TM, int TR, int KC>
 __global__ void __launch_bounds__((BM / TM) * (BR / TR))
@@ -62,12 +37,13 @@ k_affine(int h_out, int h_in, const float* __restrict__ W, const float* __restri
          const float* __restrict__ in_up, const float* __restrict__ in_lo, int64_t in_ld,
          const int32_t* __restrict__ in_nterms, float* __restrict__ out_up,
          float* __restrict__ out_lo, int64_t out_ld, int32_t* __restrict__ out_nterms,
-         float gamma, int* status) {
+         int* status) {
   constexpr int NT = (BM / TM) * (BR / TR);
   constexpr int TX = BM / TM;                       // threads along m
   __shared__ float sW[KC][BM];
-  __shared__ float sC[BR][KC + 1];    // midpoints c
-  __shared__ float sR[BR][KC + 1];    // inflated radii r'
+  __shared__ float sA[KC][BM];        // |W|
+  __shared__ float sU[BR][KC + 1];    // midpoints c
+  __shared__ float sL[BR][KC + 1];    // radii r
   __shared__ int sMax;
   extern __shared__ int32_t sN[];                   // h_in term counts
   const int64_t b = blockIdx.x;
@@ -99,51 +75,63 @@ k_affine(int h_out, int h_in, const float* __restrict__ W, const float* __restri
   if (r0 >= M) return;
 
   const int tm = tid % TX, tr = tid / TX;
-  float sc[TM][TR], rad[TM][TR];
+  float uc[TM][TR], lc[TM][TR], rad[TM][TR];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int k = 0; k < TR; ++k) {
       const int m = m0 + tm * TM + i, r = r0 + tr * TR + k;
-      sc[i][k] = (r == 0 && m < h_out) ? bias[m] : 0.0f;
+      const float b0 = (r == 0 && m < h_out) ? bias[m] : 0.0f;
+      uc[i][k] = b0;
+      lc[i][k] = b0;
       rad[i][k] = 0.0f;
     }
   const float* gU = in_up + (b * in_ld) * h_in;
   const float* gL = in_lo + (b * in_ld) * h_in;
   for (int j0 = 0; j0 < h_in; j0 += KC) {
-    // stage W[m0.., j0..] transposed, and the midpoints and radii of the
-    // input rows r0.. of columns j0..
+    // stage W[m0.., j0..] transposed (and |W|), and the midpoints and radii
+    // of the input rows r0.. of columns j0..
     for (int idx = tid; idx < KC * BM; idx += NT) {
       const int mm = idx % BM, jj = idx / BM;
       const int m = m0 + mm, j = j0 + jj;
-      sW[jj][mm] = (m < h_out && j < h_in) ? W[(int64_t)m * h_in + j] : 0.0f;
+      const float w = (m < h_out && j < h_in) ? W[(int64_t)m * h_in + j] : 0.0f;
+      sW[jj][mm] = w;
+      sA[jj][mm] = fabsf(w);
     }
     for (int idx = tid; idx < KC * BR; idx += NT) {
       const int jj = idx % KC, rr = idx / KC;
       const int j = j0 + jj, r = r0 + rr;
-      float2 cr = make_float2(0.0f, 0.0f);
-      if (j < h_in && r < sN[j])
-        cr = mid_rad(gU[(int64_t)r * h_in + j], gL[(int64_t)r * h_in + j], gamma);
-      sC[rr][jj] = cr.x;
-      sR[rr][jj] = cr.y;
+      float c = 0.0f, rd = 0.0f;
+      if (j < h_in && r < sN[j]) {
+        const float u = gU[(int64_t)r * h_in + j];
+        const float l = gL[(int64_t)r * h_in + j];
+        c = __fmaf_rn(0.5f, u, 0.5f * l);
+        rd = fmaxf(__fsub_ru(u, c), __fsub_ru(c, l));
+      }
+      sU[rr][jj] = c;
+      sL[rr][jj] = rd;
     }
     __syncthreads();
 #pragma unroll 4
     for (int jj = 0; jj < KC; ++jj) {
-      float w[TM], c[TR], rd[TR];
+      float w[TM], a[TM], c[TR], rd[TR];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) w[i] = sW[jj][tm * TM + i];
+      for (int i = 0; i < TM; ++i) {
+        w[i] = sW[jj][tm * TM + i];
+        a[i] = sA[jj][tm * TM + i];
+      }
 #pragma unroll
       for (int k = 0; k < TR; ++k) {
-        c[k] = sC[tr * TR + k][jj];
-        rd[k] = sR[tr * TR + k][jj];
+        c[k] = sU[tr * TR + k][jj];
+        rd[k] = sL[tr * TR + k][jj];
       }
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int k = 0; k < TR; ++k) {
-          sc[i][k] = __fmaf_rn(w[i], c[k], sc[i][k]);
-          rad[i][k] = __fmaf_ru(fabsf(w[i]), rd[k], rad[i][k]);
+          uc[i][k] = __fmaf_ru(w[i], c[k], uc[i][k]);
+          lc[i][k] = __fmaf_rd(w[i], c[k], lc[i][k]);
+          rad[i][k] = __fmaf_ru(a[i], rd[k], rad[i][k]);
         }
     }
     __syncthreads();
@@ -156,10 +144,136 @@ k_affine(int h_out, int h_in, const float* __restrict__ W, const float* __restri
     for (int i = 0; i < TM; ++i) {
       const int m = m0 + tm * TM + i;
       if (m < h_out) {
-        const float e = centre_err(gamma, bias[m], h_in, r == 0);
         const int64_t o = (b * out_ld + r) * h_out + m;
-        out_up[o] = __fadd_ru(__fadd_ru(sc[i][k], rad[i][k]), e);
-        out_lo[o] = __fsub_rd(__fsub_rd(sc[i][k], rad[i][k]), e);
+        out_up[o] = __fadd_ru(uc[i][k], rad[i][k]);
+        out_lo[o] = __fsub_rd(lc[i][k], rad[i][k]);
+      }
+    }
+  }
+}
+
+// Persistent form for the wide layers: a block keeps W and |W| (all h_out x
+// h_in, k-major) in shared memory for the whole launch and walks boxes; per
+// box it stages 64-row tiles of the input as midpoints and radii, and every
+// thread accumulates a 4 (neurons) x 4 (rows) tile of the three sums per
+// 64-neuron slice of the layer.
+constexpr int kPRows = 64;
+constexpr int kPThreads = 256;
+
+__global__ void __launch_bounds__(kPThreads, 3)
+k_affine_persistent(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
+                    const float* __restrict__ bias, const float* __restrict__ in_up,
+                    const float* __restrict__ in_lo, int64_t in_ld,
+                    const int32_t* __restrict__ in_nterms, float* __restrict__ out_up,
+                    float* __restrict__ out_lo, int64_t out_ld, int32_t* __restrict__ out_nterms,
+                    int* status) {
+  extern __shared__ float smem[];
+  const int hp = (h_out + 63) & ~63;                 // neurons padded to 64
+  float* sW = smem;                                  // [h_in][hp]
+  float* sA = sW + (size_t)h_in * hp;                // |W|
+  float* sC = sA + (size_t)h_in * hp;                // [kPRows][h_in + 1] midpoints
+  float* sR = sC + (size_t)kPRows * (h_in + 1);      // radii
+  int* sN = reinterpret_cast<int*>(sR + (size_t)kPRows * (h_in + 1));   // [h_in]
+  __shared__ int sMax;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < h_in * hp; idx += kPThreads) {
+    const int j = idx / hp, m = idx - j * hp;
+    const float w = m < h_out ? W[(int64_t)m * h_in + j] : 0.0f;
+    sW[idx] = w;
+    sA[idx] = fabsf(w);
+  }
+  const int tm = tid & 15, tr = tid >> 4;            // 16 x 16 threads
+  const int ldx = h_in + 1;
+  for (int64_t b = blockIdx.x; b < n_boxes; b += gridDim.x) {
+    if (tid == 0) sMax = 0;
+    __syncthreads();                                 // also: W staged, previous box done
+    int mloc = 0;
+    for (int j = tid; j < h_in; j += kPThreads) {
+      int v = in_nterms[b * h_in + j];
+      if (v < 0 || v > in_ld) {
+        atomicOr(status, kStatusInvalid);
+        v = 0;
+      }
+      sN[j] = v;
+      mloc = max(mloc, v);
+    }
+    mloc = warp_imax(mloc);
+    if ((tid & 31) == 0) atomicMax(&sMax, mloc);
+    __syncthreads();
+    const int M = max(1, sMax);
+    if (M > out_ld) {
+      if (tid == 0) atomicOr(status, kStatusCapacity);
+      continue;
+    }
+    for (int m = tid; m < h_out; m += kPThreads) out_nterms[b * h_out + m] = M;
+    const float* gU = in_up + (b * in_ld) * h_in;
+    const float* gL = in_lo + (b * in_ld) * h_in;
+    for (int r0 = 0; r0 < M; r0 += kPRows) {
+      __syncthreads();                               // the previous tile is consumed
+      for (int idx = tid; idx < kPRows * h_in; idx += kPThreads) {
+        const int rr = idx / h_in, j = idx - rr * h_in;
+        const int r = r0 + rr;
+        float c = 0.0f, rd = 0.0f;
+        if (r < M && r < sN[j]) {
+          const float u = gU[(int64_t)r * h_in + j];
+          const float l = gL[(int64_t)r * h_in + j];
+          c = __fmaf_rn(0.5f, u, 0.5f * l);
+          rd = fmaxf(__fsub_ru(u, c), __fsub_ru(c, l));
+        }
+        sC[rr * ldx + j] = c;
+        sR[rr * ldx + j] = rd;
+      }
+      __syncthreads();
+      for (int m0 = 0; m0 < h_out; m0 += 64) {
+        float uc[4][4], lc[4][4], rad[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int m = m0 + tm * 4 + i, r = r0 + tr * 4 + k;
+            const float b0 = (r == 0 && m < h_out) ? bias[m] : 0.0f;
+            uc[i][k] = b0;
+            lc[i][k] = b0;
+            rad[i][k] = 0.0f;
+          }
+        const float* pw = sW + m0 + tm * 4;
+        const float* pa = sA + m0 + tm * 4;
+        const float* pc = sC + (tr * 4) * ldx;
+        const float* pr = sR + (tr * 4) * ldx;
+#pragma unroll 4
+        for (int j = 0; j < h_in; ++j) {
+          const float4 w4 = *reinterpret_cast<const float4*>(pw + (size_t)j * hp);
+          const float4 a4 = *reinterpret_cast<const float4*>(pa + (size_t)j * hp);
+          const float w[4] = {w4.x, w4.y, w4.z, w4.w}, a[4] = {a4.x, a4.y, a4.z, a4.w};
+          float c[4], rd[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            c[k] = pc[k * ldx + j];
+            rd[k] = pr[k * ldx + j];
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              uc[i][k] = __fmaf_ru(w[i], c[k], uc[i][k]);
+              lc[i][k] = __fmaf_rd(w[i], c[k], lc[i][k]);
+              rad[i][k] = __fmaf_ru(a[i], rd[k], rad[i][k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int r = r0 + tr * 4 + k;
+          if (r >= M) continue;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int m = m0 + tm * 4 + i;
+            if (m < h_out) {
+              const int64_t o = (b * out_ld + r) * h_out + m;
+              out_up[o] = __fadd_ru(uc[i][k], rad[i][k]);
+              out_lo[o] = __fsub_rd(lc[i][k], rad[i][k]);
+            }
+          }
+        }
       }
     }
   }
@@ -169,7 +283,7 @@ k_affine(int h_out, int h_in, const float* __restrict__ W, const float* __restri
 // warps keeps W (h_in x h_out, k-major, neurons padded to 64) in shared
 // memory for the whole launch and walks boxes; per box it stages 64-row tiles
 // of the input as (midpoint, radius) pairs, and every thread accumulates an
-// 8 (neurons) x 4 (rows) tile of the two sums per 64-neuron slice: neurons
+// 8 (neurons) x 4 (rows) tile of the three sums per 64-neuron slice: neurons
 // 4 tm .. 4 tm + 3 and 32 + 4 tm .. 32 + 4 tm + 3, so the eight lanes of a
 // row read each half of the slice's weights as one contiguous 128-byte float4
 // load; 4 pairs are read as float2 per input j, and |w| is taken in the
@@ -180,13 +294,13 @@ constexpr int kWRows = 64;
 constexpr int kWThreads = 128;
 constexpr int kWBatch = 8;
 
-__global__ void __launch_bounds__(kWThreads, 4)
+__global__ void __launch_bounds__(kWThreads, 3)
 k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
               const float* __restrict__ bias, const float* __restrict__ in_up,
               const float* __restrict__ in_lo, int64_t in_ld,
               const int32_t* __restrict__ in_nterms, float* __restrict__ out_up,
               float* __restrict__ out_lo, int64_t out_ld, int32_t* __restrict__ out_nterms,
-              float gamma, int* status) {
+              int* status) {
   extern __shared__ float4 smem4[];
   const int hp = (h_out + 63) & ~63;                 // neurons padded to 64
   float* sW = reinterpret_cast<float*>(smem4);       // [h_in][hp]
@@ -253,20 +367,23 @@ k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
         }
 #pragma unroll
         for (int q = 0; q < kWBatch; ++q) {
-          const float2 cr = mid_rad(u[q], l[q], gamma);
-          if (at[q] >= 0) sCR[at[q]] = cr;
+          const float c = __fmaf_rn(0.5f, u[q], 0.5f * l[q]);
+          const float rd = fmaxf(__fsub_ru(u[q], c), __fsub_ru(c, l[q]));
+          if (at[q] >= 0) sCR[at[q]] = make_float2(c, rd);
         }
       }
       __syncthreads();
       if (r0 + warp * 16 >= M) continue;             // warp-uniform; no barrier follows
       for (int m0 = 0; m0 < h_out; m0 += 64) {
-        float sc[4][8], rad[4][8];
+        float uc[4][8], lc[4][8], rad[4][8];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const int m = m0 + (i < 4 ? 4 * tm + i : 28 + 4 * tm + i), r = r0 + tr * 4 + k;
-            sc[k][i] = (r == 0 && m < h_out) ? bias[m] : 0.0f;
+            const float b0 = (r == 0 && m < h_out) ? bias[m] : 0.0f;
+            uc[k][i] = b0;
+            lc[k][i] = b0;
             rad[k][i] = 0.0f;
           }
         const float* pw = sW + m0 + tm * 4;
@@ -283,7 +400,8 @@ k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
           for (int k = 0; k < 4; ++k)
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              sc[k][i] = __fmaf_rn(w[i], cr[k].x, sc[k][i]);
+              uc[k][i] = __fmaf_ru(w[i], cr[k].x, uc[k][i]);
+              lc[k][i] = __fmaf_rd(w[i], cr[k].x, lc[k][i]);
               rad[k][i] = __fmaf_ru(fabsf(w[i]), cr[k].y, rad[k][i]);
             }
         }
@@ -294,10 +412,8 @@ k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
           float vu[8], vl[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            const int m = m0 + (i < 4 ? 4 * tm + i : 28 + 4 * tm + i);
-            const float e = centre_err(gamma, m < h_out ? bias[m] : 0.0f, h_in, r == 0);
-            vu[i] = __fadd_ru(__fadd_ru(sc[k][i], rad[k][i]), e);
-            vl[i] = __fsub_rd(__fsub_rd(sc[k][i], rad[k][i]), e);
+            vu[i] = __fadd_ru(uc[k][i], rad[k][i]);
+            vl[i] = __fsub_rd(lc[k][i], rad[k][i]);
           }
           const int64_t o = (b * out_ld + r) * h_out + m0;
 #pragma unroll
@@ -327,6 +443,12 @@ k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
 static size_t wide_smem(int h_out, int h_in) {
   const size_t hp = (size_t)((h_out + 63) & ~63);
   return hp * h_in * sizeof(float) + (size_t)kWRows * (h_in + 1) * sizeof(float2) +
+         (size_t)h_in * sizeof(int);
+}
+
+static size_t persistent_smem(int h_out, int h_in) {
+  const size_t hp = (size_t)((h_out + 63) & ~63);
+  return (2 * hp * h_in + 2 * (size_t)kPRows * (h_in + 1)) * sizeof(float) +
          (size_t)h_in * sizeof(int);
 }
 
@@ -628,16 +750,6 @@ k_affine_narrow_quad(int64_t n_boxes, int h_out, int h_in, const float* __restri
   }
 }
 
-// gamma_n = n u / (1 - n u), u = 2^-24, rounded up to float (with a relative
-// margin of 2^-20 over the double evaluation)
-static float gamma_up(int n) {
-  const double u = std::ldexp(1.0, -24);
-  const double g = (double)n * u / (1.0 - (double)n * u) * (1.0 + std::ldexp(1.0, -20));
-  float f = (float)g;
-  if ((double)f < g) f = std::nextafter(f, INFINITY);
-  return f;
-}
-
 template <int BM, int BR, int TM, int TR, int KC>
 static cudaError_t launch_cfg(const Launch& L, int64_t n_boxes, int h_out, int h_in,
                               const float* W, const float* b, const float* in_up,
@@ -656,7 +768,7 @@ static cudaError_t launch_cfg(const Launch& L, int64_t n_boxes, int h_out, int h
   }
   k_affine<BM, BR, TM, TR, KC><<<grid, (BM / TM) * (BR / TR), smem, L.stream>>>(
       h_out, h_in, W, b, in_up, in_lo, in_ld, in_nterms, out_up, out_lo, out_ld, out_nterms,
-      gamma_up(h_in), L.status);
+      L.status);
   ++*L.launches;
   return cudaGetLastError();
 }
@@ -670,29 +782,45 @@ cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
   if (n_boxes > 0x7fffffff || (std::min(in_ld, out_ld) + 15) / 16 > 65535)
     return cudaErrorInvalidValue;
   const bool few_rows = std::min(in_ld, out_ld) <= 16;     // short polynomials: short tiles
+  const size_t psmem = persistent_smem(h_out, h_in);
   if (h_out >= 32 && !few_rows) {
-    // wide layers: autotuned between the persistent register-blocked kernel
-    // (0, when its weights fit shared memory) and 64 x 32 tiles (1)
+    // wide layers: autotuned among the persistent kernels (0: 4 x 4 tiles,
+    // 3: register-blocked 8 x 4 tiles; each when its weights fit shared
+    // memory) and two tile shapes (1: 64 x 32, 2: 64 x 64)
     const std::string key = "affine/" + std::to_string(h_out) + "/" + std::to_string(h_in) +
                             "/" + std::to_string(in_ld) + "/" + std::to_string(n_boxes);
     const size_t wsmem = wide_smem(h_out, h_in);
     const bool wide_ok = wsmem <= 200 * 1024;
-    int v = tune_variant(L, "affine", key, wide_ok ? 0 : 1);
-    if (v == 0 && !wide_ok) v = 1;
+    int v = tune_variant(L, "affine", key, wide_ok ? 3 : (psmem <= 72 * 1024 ? 0 : 1));
+    if (v == 0 && psmem > 72 * 1024) v = 1;
+    if (v == 3 && !wide_ok) v = 1;
     TuneTimer tt;
     tune_begin(L, "affine", tt);
     cudaError_t e;
-    if (v == 0) {
+    if (v == 3) {
       e = cudaFuncSetAttribute(k_affine_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)wsmem);
       if (e != cudaSuccess) return e;
-      const int per_sm = wsmem <= 54 * 1024 ? 4 : (wsmem <= 72 * 1024 ? 3 : (wsmem <= 110 * 1024 ? 2 : 1));
+      const int per_sm = wsmem <= 72 * 1024 ? 3 : (wsmem <= 110 * 1024 ? 2 : 1);
       const int64_t blocks = std::min<int64_t>(n_boxes, 152 * per_sm);
       k_affine_wide<<<(unsigned)blocks, kWThreads, wsmem, L.stream>>>(
           n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld, in_nterms, out_up, out_lo, out_ld,
-          out_nterms, gamma_up(h_in), L.status);
+          out_nterms, L.status);
       ++*L.launches;
       e = cudaGetLastError();
+    } else if (v == 0) {
+      e = cudaFuncSetAttribute(k_affine_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)psmem);
+      if (e != cudaSuccess) return e;
+      const int64_t blocks = std::min<int64_t>(n_boxes, 152 * 3);
+      k_affine_persistent<<<(unsigned)blocks, kPThreads, psmem, L.stream>>>(
+          n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld, in_nterms, out_up, out_lo, out_ld,
+          out_nterms, L.status);
+      ++*L.launches;
+      e = cudaGetLastError();
+    } else if (v == 2) {
+      e = launch_cfg<64, 64, 4, 4, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
+                                       in_nterms, out_up, out_lo, out_ld, out_nterms);
     } else {
       e = launch_cfg<64, 32, 4, 2, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
                                        in_nterms, out_up, out_lo, out_ld, out_nterms);

@@ -120,12 +120,7 @@ def test_affine_step(ctx, n, D, h_in, h_out, B):
             pu, pl = oracle.affine(ups, los, n, W[m].astype(np.float64), float(bias[m]))
             ou = dense_from_dict(pu, n, Mb)
             ol = dense_from_dict(pl, n, Mb)
-            # the centre sum is rounded to nearest and its a-priori error
-            # bound gamma_n sum |w| |c| (n = h_in) is added to the radius, whose
-            # own round-up sum adds up to gamma_n of it again: within
-            # 3 gamma_n (1 + scale) of the exact sums, plus the float32 midpoint
-            # and radius roundings
-            tol = (1e-6 + 3 * h_in * 2.0**-24) * (1 + scale[m])
+            tol = 1e-6 * (1 + scale[m])
             gu, gl = out_u[b, m, :Mb], out_l[b, m, :Mb]
             assert np.all(gu >= ou - 1e-12 * (1 + scale[m]))       # rounded up
             assert np.all(gl <= ol + 1e-12 * (1 + scale[m]))       # rounded down
