@@ -152,133 +152,6 @@ k_affine(int h_out, int h_in, const float* __restrict__ W, const float* __restri
   }
 }
 
-// Persistent form for the wide layers: a block keeps W and |W| (all h_out x
-// h_in, k-major) in shared memory for the whole launch and walks boxes; per
-// box it stages 64-row tiles of the input as midpoints and radii, and every
-// thread accumulates a 4 (neurons) x 4 (rows) tile of the three sums per
-// 64-neuron slice of the layer.
-constexpr int kPRows = 64;
-constexpr int kPThreads = 256;
-
-__global__ void __launch_bounds__(kPThreads, 3)
-k_affine_persistent(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
-                    const float* __restrict__ bias, const float* __restrict__ in_up,
-                    const float* __restrict__ in_lo, int64_t in_ld,
-                    const int32_t* __restrict__ in_nterms, float* __restrict__ out_up,
-                    float* __restrict__ out_lo, int64_t out_ld, int32_t* __restrict__ out_nterms,
-                    int* status) {
-  extern __shared__ float smem[];
-  const int hp = (h_out + 63) & ~63;                 // neurons padded to 64
-  float* sW = smem;                                  // [h_in][hp]
-  float* sA = sW + (size_t)h_in * hp;                // |W|
-  float* sC = sA + (size_t)h_in * hp;                // [kPRows][h_in + 1] midpoints
-  float* sR = sC + (size_t)kPRows * (h_in + 1);      // radii
-  int* sN = reinterpret_cast<int*>(sR + (size_t)kPRows * (h_in + 1));   // [h_in]
-  __shared__ int sMax;
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < h_in * hp; idx += kPThreads) {
-    const int j = idx / hp, m = idx - j * hp;
-    const float w = m < h_out ? W[(int64_t)m * h_in + j] : 0.0f;
-    sW[idx] = w;
-    sA[idx] = fabsf(w);
-  }
-  const int tm = tid & 15, tr = tid >> 4;            // 16 x 16 threads
-  const int ldx = h_in + 1;
-  for (int64_t b = blockIdx.x; b < n_boxes; b += gridDim.x) {
-    if (tid == 0) sMax = 0;
-    __syncthreads();                                 // also: W staged, previous box done
-    int mloc = 0;
-    for (int j = tid; j < h_in; j += kPThreads) {
-      int v = in_nterms[b * h_in + j];
-      if (v < 0 || v > in_ld) {
-        atomicOr(status, kStatusInvalid);
-        v = 0;
-      }
-      sN[j] = v;
-      mloc = max(mloc, v);
-    }
-    mloc = warp_imax(mloc);
-    if ((tid & 31) == 0) atomicMax(&sMax, mloc);
-    __syncthreads();
-    const int M = max(1, sMax);
-    if (M > out_ld) {
-      if (tid == 0) atomicOr(status, kStatusCapacity);
-      continue;
-    }
-    for (int m = tid; m < h_out; m += kPThreads) out_nterms[b * h_out + m] = M;
-    const float* gU = in_up + (b * in_ld) * h_in;
-    const float* gL = in_lo + (b * in_ld) * h_in;
-    for (int r0 = 0; r0 < M; r0 += kPRows) {
-      __syncthreads();                               // the previous tile is consumed
-      for (int idx = tid; idx < kPRows * h_in; idx += kPThreads) {
-        const int rr = idx / h_in, j = idx - rr * h_in;
-        const int r = r0 + rr;
-        float c = 0.0f, rd = 0.0f;
-        if (r < M && r < sN[j]) {
-          const float u = gU[(int64_t)r * h_in + j];
-          const float l = gL[(int64_t)r * h_in + j];
-          c = __fmaf_rn(0.5f, u, 0.5f * l);
-          rd = fmaxf(__fsub_ru(u, c), __fsub_ru(c, l));
-        }
-        sC[rr * ldx + j] = c;
-        sR[rr * ldx + j] = rd;
-      }
-      __syncthreads();
-      for (int m0 = 0; m0 < h_out; m0 += 64) {
-        float uc[4][4], lc[4][4], rad[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int m = m0 + tm * 4 + i, r = r0 + tr * 4 + k;
-            const float b0 = (r == 0 && m < h_out) ? bias[m] : 0.0f;
-            uc[i][k] = b0;
-            lc[i][k] = b0;
-            rad[i][k] = 0.0f;
-          }
-        const float* pw = sW + m0 + tm * 4;
-        const float* pa = sA + m0 + tm * 4;
-        const float* pc = sC + (tr * 4) * ldx;
-        const float* pr = sR + (tr * 4) * ldx;
-#pragma unroll 4
-        for (int j = 0; j < h_in; ++j) {
-          const float4 w4 = *reinterpret_cast<const float4*>(pw + (size_t)j * hp);
-          const float4 a4 = *reinterpret_cast<const float4*>(pa + (size_t)j * hp);
-          const float w[4] = {w4.x, w4.y, w4.z, w4.w}, a[4] = {a4.x, a4.y, a4.z, a4.w};
-          float c[4], rd[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            c[k] = pc[k * ldx + j];
-            rd[k] = pr[k * ldx + j];
-          }
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              uc[i][k] = __fmaf_ru(w[i], c[k], uc[i][k]);
-              lc[i][k] = __fmaf_rd(w[i], c[k], lc[i][k]);
-              rad[i][k] = __fmaf_ru(a[i], rd[k], rad[i][k]);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int r = r0 + tr * 4 + k;
-          if (r >= M) continue;
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int m = m0 + tm * 4 + i;
-            if (m < h_out) {
-              const int64_t o = (b * out_ld + r) * h_out + m;
-              out_up[o] = __fadd_ru(uc[i][k], rad[i][k]);
-              out_lo[o] = __fsub_rd(lc[i][k], rad[i][k]);
-            }
-          }
-        }
-      }
-    }
-  }
-}
-
 // Persistent, register-blocked form for the wide layers: a block of four
 // warps keeps W (h_in x h_out, k-major, neurons padded to 64) in shared
 // memory for the whole launch and walks boxes; per box it stages 64-row tiles
@@ -294,7 +167,7 @@ constexpr int kWRows = 64;
 constexpr int kWThreads = 128;
 constexpr int kWBatch = 8;
 
-__global__ void __launch_bounds__(kWThreads, 3)
+__global__ void __launch_bounds__(kWThreads, 4)
 k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
               const float* __restrict__ bias, const float* __restrict__ in_up,
               const float* __restrict__ in_lo, int64_t in_ld,
@@ -390,20 +263,23 @@ k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
         const float2* pcr = sCR + (tr * 4) * ldx;
 #pragma unroll 2
         for (int j = 0; j < h_in; ++j) {
-          const float4 wa = *reinterpret_cast<const float4*>(pw + (size_t)j * hp);
-          const float4 wb = *reinterpret_cast<const float4*>(pw + (size_t)j * hp + 32);
-          const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
           float2 cr[4];
 #pragma unroll
           for (int k = 0; k < 4; ++k) cr[k] = pcr[k * ldx + j];
 #pragma unroll
-          for (int k = 0; k < 4; ++k)
+          for (int half = 0; half < 2; ++half) {
+            const float4 w4 = *reinterpret_cast<const float4*>(pw + (size_t)j * hp + 32 * half);
+            const float w[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              uc[k][i] = __fmaf_ru(w[i], cr[k].x, uc[k][i]);
-              lc[k][i] = __fmaf_rd(w[i], cr[k].x, lc[k][i]);
-              rad[k][i] = __fmaf_ru(fabsf(w[i]), cr[k].y, rad[k][i]);
-            }
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const int ii = 4 * half + i;
+                uc[k][ii] = __fmaf_ru(w[i], cr[k].x, uc[k][ii]);
+                lc[k][ii] = __fmaf_rd(w[i], cr[k].x, lc[k][ii]);
+                rad[k][ii] = __fmaf_ru(fabsf(w[i]), cr[k].y, rad[k][ii]);
+              }
+          }
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -443,12 +319,6 @@ k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
 static size_t wide_smem(int h_out, int h_in) {
   const size_t hp = (size_t)((h_out + 63) & ~63);
   return hp * h_in * sizeof(float) + (size_t)kWRows * (h_in + 1) * sizeof(float2) +
-         (size_t)h_in * sizeof(int);
-}
-
-static size_t persistent_smem(int h_out, int h_in) {
-  const size_t hp = (size_t)((h_out + 63) & ~63);
-  return (2 * hp * h_in + 2 * (size_t)kPRows * (h_in + 1)) * sizeof(float) +
          (size_t)h_in * sizeof(int);
 }
 
@@ -782,45 +652,29 @@ cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
   if (n_boxes > 0x7fffffff || (std::min(in_ld, out_ld) + 15) / 16 > 65535)
     return cudaErrorInvalidValue;
   const bool few_rows = std::min(in_ld, out_ld) <= 16;     // short polynomials: short tiles
-  const size_t psmem = persistent_smem(h_out, h_in);
   if (h_out >= 32 && !few_rows) {
-    // wide layers: autotuned among the persistent kernels (0: 4 x 4 tiles,
-    // 3: register-blocked 8 x 4 tiles; each when its weights fit shared
-    // memory) and two tile shapes (1: 64 x 32, 2: 64 x 64)
+    // wide layers: autotuned between the persistent register-blocked kernel
+    // (0, when its weights fit shared memory) and 64 x 32 tiles (1)
     const std::string key = "affine/" + std::to_string(h_out) + "/" + std::to_string(h_in) +
                             "/" + std::to_string(in_ld) + "/" + std::to_string(n_boxes);
     const size_t wsmem = wide_smem(h_out, h_in);
     const bool wide_ok = wsmem <= 200 * 1024;
-    int v = tune_variant(L, "affine", key, wide_ok ? 3 : (psmem <= 72 * 1024 ? 0 : 1));
-    if (v == 0 && psmem > 72 * 1024) v = 1;
-    if (v == 3 && !wide_ok) v = 1;
+    int v = tune_variant(L, "affine", key, wide_ok ? 0 : 1);
+    if (v == 0 && !wide_ok) v = 1;
     TuneTimer tt;
     tune_begin(L, "affine", tt);
     cudaError_t e;
-    if (v == 3) {
+    if (v == 0) {
       e = cudaFuncSetAttribute(k_affine_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)wsmem);
       if (e != cudaSuccess) return e;
-      const int per_sm = wsmem <= 72 * 1024 ? 3 : (wsmem <= 110 * 1024 ? 2 : 1);
+      const int per_sm = wsmem <= 54 * 1024 ? 4 : (wsmem <= 72 * 1024 ? 3 : (wsmem <= 110 * 1024 ? 2 : 1));
       const int64_t blocks = std::min<int64_t>(n_boxes, 152 * per_sm);
       k_affine_wide<<<(unsigned)blocks, kWThreads, wsmem, L.stream>>>(
           n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld, in_nterms, out_up, out_lo, out_ld,
           out_nterms, L.status);
       ++*L.launches;
       e = cudaGetLastError();
-    } else if (v == 0) {
-      e = cudaFuncSetAttribute(k_affine_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)psmem);
-      if (e != cudaSuccess) return e;
-      const int64_t blocks = std::min<int64_t>(n_boxes, 152 * 3);
-      k_affine_persistent<<<(unsigned)blocks, kPThreads, psmem, L.stream>>>(
-          n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld, in_nterms, out_up, out_lo, out_ld,
-          out_nterms, L.status);
-      ++*L.launches;
-      e = cudaGetLastError();
-    } else if (v == 2) {
-      e = launch_cfg<64, 64, 4, 4, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
-                                       in_nterms, out_up, out_lo, out_ld, out_nterms);
     } else {
       e = launch_cfg<64, 32, 4, 2, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
                                        in_nterms, out_up, out_lo, out_ld, out_nterms);
