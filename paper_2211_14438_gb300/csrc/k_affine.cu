@@ -316,6 +316,164 @@ k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
   }
 }
 
+// Short polynomials (at most 16 monomial rows per box) in wide layers: the
+// same register tiles as k_affine_wide, but each warp takes a whole box (its
+// 16 rows x 64 neurons per slice), so a block of four warps works on four
+// boxes at a time with only warp-level synchronisation after W is staged.
+constexpr int kSRows = 16;
+
+__global__ void __launch_bounds__(kWThreads, 4)
+k_affine_short(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
+               const float* __restrict__ bias, const float* __restrict__ in_up,
+               const float* __restrict__ in_lo, int64_t in_ld,
+               const int32_t* __restrict__ in_nterms, float* __restrict__ out_up,
+               float* __restrict__ out_lo, int64_t out_ld, int32_t* __restrict__ out_nterms,
+               int* status) {
+  extern __shared__ float4 smem4[];
+  const int hp = (h_out + 63) & ~63;
+  const int ldx = h_in + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* sW = reinterpret_cast<float*>(smem4);                        // [h_in][hp]
+  float2* sCR = reinterpret_cast<float2*>(sW + (size_t)h_in * hp) +
+                (size_t)warp * kSRows * ldx;                          // [kSRows][ldx] per warp
+  int* sN = reinterpret_cast<int*>(reinterpret_cast<float2*>(sW + (size_t)h_in * hp) +
+                                   (size_t)4 * kSRows * ldx) +
+            warp * h_in;                                              // [h_in] per warp
+  for (int idx = threadIdx.x; idx < h_in * hp; idx += kWThreads) {
+    const int j = idx / hp, m = idx - j * hp;
+    sW[idx] = m < h_out ? W[(int64_t)m * h_in + j] : 0.0f;
+  }
+  __syncthreads();
+  const int tm = lane & 7, tr = lane >> 3;           // 8 x 4 lanes
+  const int step_r = 32 / h_in, step_j = 32 - step_r * h_in;
+  const bool vec_out =
+      (h_out & 3) == 0 &&
+      ((reinterpret_cast<uintptr_t>(out_up) | reinterpret_cast<uintptr_t>(out_lo)) & 15) == 0;
+  for (int64_t b = (int64_t)blockIdx.x * 4 + warp; b < n_boxes; b += (int64_t)gridDim.x * 4) {
+    int mloc = 0;
+    for (int j = lane; j < h_in; j += 32) {
+      int v = in_nterms[b * h_in + j];
+      if (v < 0 || v > in_ld) {
+        atomicOr(status, kStatusInvalid);
+        v = 0;
+      }
+      sN[j] = v;
+      mloc = max(mloc, v);
+    }
+    const int M = max(1, warp_imax(mloc));
+    if (M > out_ld || M > kSRows) {
+      if (lane == 0) atomicOr(status, kStatusCapacity);
+      __syncwarp();
+      continue;
+    }
+    for (int m = lane; m < h_out; m += 32) out_nterms[b * h_out + m] = M;
+    __syncwarp();                                    // sN visible to the warp
+    const float* gU = in_up + (b * in_ld) * h_in;
+    const float* gL = in_lo + (b * in_ld) * h_in;
+    int rr = lane / h_in, j = lane - (lane / h_in) * h_in;
+    for (int idx = lane; idx < M * h_in; idx += 32 * kWBatch) {
+      float u[kWBatch], l[kWBatch];
+      int at[kWBatch];
+#pragma unroll
+      for (int q = 0; q < kWBatch; ++q) {
+        const bool in = idx + q * 32 < M * h_in;
+        const bool live = in && rr < sN[j];
+        u[q] = live ? gU[(int64_t)rr * h_in + j] : 0.0f;
+        l[q] = live ? gL[(int64_t)rr * h_in + j] : 0.0f;
+        at[q] = in ? rr * ldx + j : -1;
+        rr += step_r;
+        j += step_j;
+        if (j >= h_in) {
+          j -= h_in;
+          ++rr;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kWBatch; ++q) {
+        const float c = __fmaf_rn(0.5f, u[q], 0.5f * l[q]);
+        const float rd = fmaxf(__fsub_ru(u[q], c), __fsub_ru(c, l[q]));
+        if (at[q] >= 0) sCR[at[q]] = make_float2(c, rd);
+      }
+    }
+    __syncwarp();
+    if (tr * 4 < M) {
+      for (int m0 = 0; m0 < h_out; m0 += 64) {
+        float uc[4][8], lc[4][8], rad[4][8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int m = m0 + (i < 4 ? 4 * tm + i : 28 + 4 * tm + i), r = tr * 4 + k;
+            const float b0 = (r == 0 && m < h_out) ? bias[m] : 0.0f;
+            uc[k][i] = b0;
+            lc[k][i] = b0;
+            rad[k][i] = 0.0f;
+          }
+        const float* pw = sW + m0 + tm * 4;
+        const float2* pcr = sCR + (tr * 4) * ldx;
+#pragma unroll 2
+        for (int jj = 0; jj < h_in; ++jj) {
+          float2 cr[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            cr[k] = tr * 4 + k < M ? pcr[k * ldx + jj] : make_float2(0.0f, 0.0f);
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            const float4 w4 = *reinterpret_cast<const float4*>(pw + (size_t)jj * hp + 32 * half);
+            const float w[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const int ii = 4 * half + i;
+                uc[k][ii] = __fmaf_ru(w[i], cr[k].x, uc[k][ii]);
+                lc[k][ii] = __fmaf_rd(w[i], cr[k].x, lc[k][ii]);
+                rad[k][ii] = __fmaf_ru(fabsf(w[i]), cr[k].y, rad[k][ii]);
+              }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int r = tr * 4 + k;
+          if (r >= M) continue;
+          float vu[8], vl[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            vu[i] = __fadd_ru(uc[k][i], rad[k][i]);
+            vl[i] = __fsub_rd(lc[k][i], rad[k][i]);
+          }
+          const int64_t o = (b * out_ld + r) * h_out + m0;
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            const int mb = m0 + 32 * half + 4 * tm;
+            const int64_t oh = o + 32 * half + 4 * tm;
+            const float* pu = vu + 4 * half;
+            const float* pl = vl + 4 * half;
+            if (vec_out && mb + 4 <= h_out) {
+              *reinterpret_cast<float4*>(out_up + oh) = make_float4(pu[0], pu[1], pu[2], pu[3]);
+              *reinterpret_cast<float4*>(out_lo + oh) = make_float4(pl[0], pl[1], pl[2], pl[3]);
+            } else {
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+                if (mb + i < h_out) {
+                  out_up[oh + i] = pu[i];
+                  out_lo[oh + i] = pl[i];
+                }
+            }
+          }
+        }
+      }
+    }
+    __syncwarp();                                    // sCR and sN consumed
+  }
+}
+
+static size_t short_smem(int h_out, int h_in) {
+  const size_t hp = (size_t)((h_out + 63) & ~63);
+  return hp * h_in * sizeof(float) + (size_t)4 * kSRows * (h_in + 1) * sizeof(float2) +
+         (size_t)4 * h_in * sizeof(int);
+}
+
 static size_t wide_smem(int h_out, int h_in) {
   const size_t hp = (size_t)((h_out + 63) & ~63);
   return hp * h_in * sizeof(float) + (size_t)kWRows * (h_in + 1) * sizeof(float2) +
@@ -682,9 +840,24 @@ cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
     tune_end(L, "affine", key, tt);
     return e;
   }
-  if (h_out >= 32 && few_rows)
+  if (h_out >= 32 && few_rows) {
+    // short polynomials: a warp per box where the weights fit shared memory
+    const size_t ssmem = short_smem(h_out, h_in);
+    if (ssmem <= 200 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(
+          k_affine_short, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem);
+      if (e != cudaSuccess) return e;
+      const int per_sm = ssmem <= 54 * 1024 ? 4 : (ssmem <= 72 * 1024 ? 3 : (ssmem <= 110 * 1024 ? 2 : 1));
+      const int64_t blocks = std::min<int64_t>((n_boxes + 3) / 4, 152 * per_sm);
+      k_affine_short<<<(unsigned)blocks, kWThreads, ssmem, L.stream>>>(
+          n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld, in_nterms, out_up, out_lo, out_ld,
+          out_nterms, L.status);
+      ++*L.launches;
+      return cudaGetLastError();
+    }
     return launch_cfg<64, 16, 4, 1, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
                                         in_nterms, out_up, out_lo, out_ld, out_nterms);
+  }
   if (h_out > 8 && few_rows)
     return launch_cfg<16, 16, 2, 1, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
                                         in_nterms, out_up, out_lo, out_ld, out_nterms);
