@@ -127,17 +127,32 @@ __device__ float scatter_terms(const float* __restrict__ P, int ps, int nt,
                                const int32_t* __restrict__ gidx, const float2* __restrict__ rs,
                                int m_eff, float* grid) {
   const int lane = threadIdx.x & 31;
+  constexpr int kB = 4;                              // rounds of loads in flight
   float rem = 0.0f;
-  for (int r = lane; r < nt; r += 32) {
-    const float a = P[(int64_t)r * ps];
-    if (r < m_eff) {
-      const float2 sc = rs[r];
-      // a / C bracketed: choose the end that rounds the product the right way
-      grid[__ldg(gidx + r)] = UP ? __fmul_ru(a, a >= 0.0f ? sc.y : sc.x)
-                                 : __fmul_rd(a, a >= 0.0f ? sc.x : sc.y);
-    } else {
-      // the term lies in [min(0,a), max(0,a)] on the box
-      rem = UP ? __fadd_ru(rem, fmaxf(a, 0.0f)) : __fadd_rd(rem, fminf(a, 0.0f));
+  for (int r0 = lane; r0 < nt; r0 += 32 * kB) {
+    float a[kB];
+    int gi[kB];
+    float2 sc[kB];
+#pragma unroll
+    for (int q = 0; q < kB; ++q) {
+      const int r = r0 + 32 * q;
+      a[q] = r < nt ? P[(int64_t)r * ps] : 0.0f;
+      const bool in = r < nt && r < m_eff;
+      gi[q] = in ? __ldg(gidx + r) : 0;
+      sc[q] = in ? rs[r] : make_float2(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int q = 0; q < kB; ++q) {
+      const int r = r0 + 32 * q;
+      if (r >= nt) continue;
+      if (r < m_eff) {
+        // a / C bracketed: choose the end that rounds the product the right way
+        grid[gi[q]] = UP ? __fmul_ru(a[q], a[q] >= 0.0f ? sc[q].y : sc[q].x)
+                         : __fmul_rd(a[q], a[q] >= 0.0f ? sc[q].x : sc[q].y);
+      } else {
+        // the term lies in [min(0,a), max(0,a)] on the box
+        rem = UP ? __fadd_ru(rem, fmaxf(a[q], 0.0f)) : __fadd_rd(rem, fminf(a[q], 0.0f));
+      }
     }
   }
   // a ragged count (not a full graded prefix): missing simplex entries are 0
@@ -197,70 +212,6 @@ __device__ float enclose_warp(const float* __restrict__ P, int ps, int nt, int n
   return dadd<UP>(best, rem);
 }
 
-__host__ __device__ constexpr int cpow(int R, int e) { return e == 0 ? 1 : R * cpow(R, e - 1); }
-
-// The same transforms with the number of variables N known at compile time:
-// the stages are unrolled, so every line stride is a constant, and a line's
-// base offset and prefix digit sum are decoded from its index by constant
-// divisions instead of being read from the per-order line table.
-template <int LB, int N, bool UP>
-__device__ float enclose_warp_n(const float* __restrict__ P, int ps, int nt, const Tables& T,
-                                const float2* __restrict__ rs, float* grid) {
-  const int lane = threadIdx.x & 31;
-  constexpr int R = LB + 1;
-  constexpr int NL = cpow(R, N - 1);                 // lines along one variable
-  const int Dnt = prefix_degree(T, nt);
-  const int Deff = Dnt < LB ? Dnt : LB;
-  float rem = scatter_terms<UP>(P, ps, nt, T.gidx[LB], rs, T.mcount[Deff], grid);
-  __syncwarp();
-  float best = UP ? -CUDART_INF_F : CUDART_INF_F;
-#pragma unroll
-  for (int k = N - 1; k >= 0; --k) {
-    const int sk = cpow(R, N - 1 - k);
-#pragma unroll
-    for (int L0 = 0; L0 < NL; L0 += 32) {
-      const int Ln = L0 + lane;
-      if (Ln >= NL) continue;
-      // digits of the other variables, the last variable fastest
-      int q = Ln, base = 0, psum = 0;
-#pragma unroll
-      for (int v = N - 1; v >= 0; --v) {
-        if (v == k) continue;
-        const int dg = q % R;
-        q /= R;
-        base += dg * cpow(R, N - 1 - v);
-        if (v < k) psum += dg;
-      }
-      if (psum > Deff) continue;
-      const int p = Deff - psum;
-      float x[R], y[R];
-#pragma unroll
-      for (int j = 0; j < R; ++j) x[j] = j <= p ? grid[base + j * sk] : 0.0f;
-      line_transform<LB, UP>(x, y);
-      if (k > 0) {
-#pragma unroll
-        for (int i = 0; i < R; ++i) grid[base + i * sk] = y[i];
-      } else {
-#pragma unroll
-        for (int i = 0; i < R; ++i) best = UP ? fmaxf(best, y[i]) : fminf(best, y[i]);
-      }
-    }
-    __syncwarp();
-  }
-  best = UP ? warp_max(best) : warp_min(best);
-  rem = warp_dsum<UP>(rem);
-  return dadd<UP>(best, rem);
-}
-
-template <int LB, bool UP>
-__device__ __forceinline__ float enclose_dispatch(const float* __restrict__ P, int ps, int nt,
-                                                  const Tables& T, const float2* __restrict__ rs,
-                                                  float* grid) {
-  if (T.n == 3) return enclose_warp_n<LB, 3, UP>(P, ps, nt, T, rs, grid);
-  if (T.n == 2) return enclose_warp_n<LB, 2, UP>(P, ps, nt, T, rs, grid);
-  return enclose_warp<LB, UP>(P, ps, nt, T.n, T, rs, grid);
-}
-
 // Options of one enclosure launch: the fused a3 outputs (kind == nullptr:
 // enclosure only) and an optional item list (list != nullptr: the launch
 // covers items list[0 .. *count), a device-side count; otherwise items
@@ -301,8 +252,8 @@ k_enclose(Tables T, int G, const float2* __restrict__ rs, int64_t n_items, int h
     const int64_t b = item / h;
     const int64_t base = (b * ld) * h + (item - b * h);
     float* grid = smem + warp * G;
-    const float v = up ? enclose_dispatch<LB, true>(pre_up + base, h, nt, T, rs, grid)
-                       : enclose_dispatch<LB, false>(pre_lo + base, h, nt, T, rs, grid);
+    const float v = up ? enclose_warp<LB, true>(pre_up + base, h, nt, T.n, T, rs, grid)
+                       : enclose_warp<LB, false>(pre_lo + base, h, nt, T.n, T, rs, grid);
     if (lane == 0) {
       (up ? hi : lo)[item] = v;
       s_lohi[warp >> 1][up ? 1 : 0] = v;

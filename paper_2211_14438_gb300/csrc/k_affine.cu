@@ -667,7 +667,8 @@ k_affine_narrow_warp(int64_t n_boxes, int h_out, int h_in, const float* __restri
 // rows, quad form: G lanes share one monomial row, each lane reading four
 // consecutive inputs j as one float4, so a warp reads 32 / G whole rows per
 // load; U such loads are issued before any is used.  Each lane keeps the
-// weights and term counts of its four inputs in registers; the G partial sums
+// weights and term counts of its four inputs in registers (and skips the
+// loads of rows past all four counts); the G partial sums
 // of a row are combined by a directed shuffle reduction (round-up for the
 // upper sum, round-down for the lower one), which bounds the exact sum from
 // the correct side in any order.  A block takes one box and kQRows rows.
@@ -721,13 +722,14 @@ k_affine_narrow_quad(int64_t n_boxes, int h_out, int h_in, const float* __restri
   const float4* pu = reinterpret_cast<const float4*>(in_up + (b * in_ld) * h_in) + q;
   const float4* pl = reinterpret_cast<const float4*>(in_lo + (b * in_ld) * h_in) + q;
   const int h4 = h_in >> 2;
+  const int ntq = max(max(nt[0], nt[1]), max(nt[2], nt[3]));   // rows this quad holds
   const int r_end = min(M, (int)(blockIdx.y + 1) * kQRows);
   for (int r0 = blockIdx.y * kQRows + warp * R * U; r0 < r_end; r0 += 8 * R * U) {
     float4 u[U], l[U];
 #pragma unroll
     for (int k = 0; k < U; ++k) {
       const int r = r0 + k * R + s;
-      if (qlive && r < r_end) {
+      if (qlive && r < r_end && r < ntq) {
         u[k] = __ldg(pu + (int64_t)r * h4);
         l[k] = __ldg(pl + (int64_t)r * h4);
       } else {
