@@ -127,32 +127,17 @@ __device__ float scatter_terms(const float* __restrict__ P, int ps, int nt,
                                const int32_t* __restrict__ gidx, const float2* __restrict__ rs,
                                int m_eff, float* grid) {
   const int lane = threadIdx.x & 31;
-  constexpr int kB = 4;                              // rounds of loads in flight
   float rem = 0.0f;
-  for (int r0 = lane; r0 < nt; r0 += 32 * kB) {
-    float a[kB];
-    int gi[kB];
-    float2 sc[kB];
-#pragma unroll
-    for (int q = 0; q < kB; ++q) {
-      const int r = r0 + 32 * q;
-      a[q] = r < nt ? P[(int64_t)r * ps] : 0.0f;
-      const bool in = r < nt && r < m_eff;
-      gi[q] = in ? __ldg(gidx + r) : 0;
-      sc[q] = in ? rs[r] : make_float2(0.0f, 0.0f);
-    }
-#pragma unroll
-    for (int q = 0; q < kB; ++q) {
-      const int r = r0 + 32 * q;
-      if (r >= nt) continue;
-      if (r < m_eff) {
-        // a / C bracketed: choose the end that rounds the product the right way
-        grid[gi[q]] = UP ? __fmul_ru(a[q], a[q] >= 0.0f ? sc[q].y : sc[q].x)
-                         : __fmul_rd(a[q], a[q] >= 0.0f ? sc[q].x : sc[q].y);
-      } else {
-        // the term lies in [min(0,a), max(0,a)] on the box
-        rem = UP ? __fadd_ru(rem, fmaxf(a[q], 0.0f)) : __fadd_rd(rem, fminf(a[q], 0.0f));
-      }
+  for (int r = lane; r < nt; r += 32) {
+    const float a = P[(int64_t)r * ps];
+    if (r < m_eff) {
+      const float2 sc = rs[r];
+      // a / C bracketed: choose the end that rounds the product the right way
+      grid[__ldg(gidx + r)] = UP ? __fmul_ru(a, a >= 0.0f ? sc.y : sc.x)
+                                 : __fmul_rd(a, a >= 0.0f ? sc.x : sc.y);
+    } else {
+      // the term lies in [min(0,a), max(0,a)] on the box
+      rem = UP ? __fadd_ru(rem, fmaxf(a, 0.0f)) : __fadd_rd(rem, fminf(a, 0.0f));
     }
   }
   // a ragged count (not a full graded prefix): missing simplex entries are 0
