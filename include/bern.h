@@ -38,7 +38,7 @@ extern "C" {
 
 /* ------------------------------------------------------------ status codes */
 #define BERN_OK            0
-#define BERN_E_INVALID     1  /* bad argument: dlo > dhi, NaN box, n > 8, d not in [1,8], ... */
+#define BERN_E_INVALID     1  /* bad argument: dlo > dhi, NaN box, n > 8, d not in [1,16], ... */
 #define BERN_E_CAPACITY    2  /* an output buffer is too small; n_terms tells what is needed */
 #define BERN_E_NONFINITE   3  /* a bound or coefficient became NaN/Inf */
 #define BERN_E_TIMEOUT     4  /* a device-side wait ran out of its iteration limit */
@@ -58,7 +58,7 @@ extern "C" {
                                  time by the plan's degree MLP (see bern_mlp) */
 
 #define BERN_MAX_VARS   8
-#define BERN_MAX_ORDER  8     /* largest ReLU Bernstein order d */
+#define BERN_MAX_ORDER  16    /* largest ReLU Bernstein order d */
 #define BERN_MAX_GRID   24576 /* largest Bernstein grid one enclosure stages in shared memory;
                                  bern_budget is clamped to it */
 #define BERN_MAX_ENCLOSE_ORDER 24 /* Bernstein orders above this are lowered to it */

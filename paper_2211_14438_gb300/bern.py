@@ -32,7 +32,7 @@ BERN_DEG_LEARNED = 3
 BERN_MLP_HIDDEN = 64
 BERN_DEGREE_FEATURES = 8
 BERN_DEGREE_CLASSES = 4
-BERN_MAX_ORDER = 8
+BERN_MAX_ORDER = 16
 BERN_MAX_GRID = 24576
 BERN_MAX_ENCLOSE_ORDER = 24
 COEF_STRIDE = BERN_MAX_ORDER + 1

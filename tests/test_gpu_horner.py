@@ -56,7 +56,7 @@ def check_all(ctx, net, boxes, degree, cap=16, tau=0.0, mc=20_000, seed=0):
     return g
 
 
-@pytest.mark.parametrize("d", [3, 4, 5])
+@pytest.mark.parametrize("d", [3, 4, 5, 8, 12, 16])
 def test_config1_orders_above_two(ctx, d):
     w = wl.config1()
     check_all(ctx, w.net, w.boxes, d, mc=200_000, seed=d)

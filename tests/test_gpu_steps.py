@@ -168,7 +168,7 @@ def test_enclose_step(ctx, n, D, order, budget):
 
 
 # ---------------------------------------------------------------- a3
-@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 8])
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 8, 12, 16])
 def test_relu_coeffs_step(ctx, d):
     rng = np.random.default_rng(d)
     N = 64

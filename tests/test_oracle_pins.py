@@ -54,7 +54,7 @@ def test_table1_band_area():
 
 
 @pytest.mark.parametrize("lo,hi", [(-6, 10), (-1, 1), (-0.3, 2.5), (-7.5, 0.2)])
-@pytest.mark.parametrize("d", [1, 2, 3, 4, 8])
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 8, 12, 16])
 def test_prop1_prop2(lo, hi, d):
     """Prop. 1: B >= relu on [lo,hi]. Prop. 2: max(B - relu) = B(0), so
     B - B(0) <= relu."""
@@ -90,6 +90,23 @@ def test_power_form_matches_definition(d):
     assert eps == pytest.approx(oracle.relu_bern_eval(lo, hi, d, 0.0), abs=1e-14)
     # a_0 = B(lo) = relu(lo) = 0 and sum a_j = B(hi) = hi (end-point interpolation)
     assert abs(a[0]) < 1e-14 and a.sum() == pytest.approx(hi, abs=1e-12)
+
+
+@pytest.mark.parametrize("d", [8, 10, 13, 16])
+def test_power_form_high_orders(d):
+    """At orders up to 16 (Fig. 1's range) the power form in s still equals
+    Def. 1 evaluated directly at random points (a Vandermonde fit is too
+    ill-conditioned here), interpolates the end points, and its shift is
+    B(0)."""
+    lo, hi = -2.3, 3.1
+    a, eps = oracle.relu_coeffs(lo, hi, d)
+    rng = np.random.default_rng(d)
+    for sv in np.r_[0.0, 1.0, rng.random(40)]:
+        direct = oracle.relu_bern_eval(lo, hi, d, lo + sv * (hi - lo))
+        power = sum(a[j] * sv ** j for j in range(d + 1))
+        assert abs(power - direct) <= 1e-12 * (1 + np.abs(a).sum())
+    assert abs(a[0]) < 1e-12 and a.sum() == pytest.approx(hi, abs=1e-10)
+    assert eps == pytest.approx(oracle.relu_bern_eval(lo, hi, d, 0.0), abs=1e-14)
 
 
 # ------------------------------------------------------------------- Step 1
