@@ -174,17 +174,11 @@ __device__ __forceinline__ int prefix_degree(const Tables& T, int nt) {
 
 template <int LB, bool UP>
 __device__ float enclose_warp(const float* __restrict__ P, int ps, int nt, int n,
-                              const Tables& T, const float2* __restrict__ rs, float* grid,
-                              int G) {
+                              const Tables& T, const float2* __restrict__ rs, float* grid) {
   const int lane = threadIdx.x & 31;
   constexpr int R = LB + 1;
   const int Dnt = prefix_degree(T, nt);
   const int Deff = Dnt < LB ? Dnt : LB;
-  // the grid starts at zero (G is a multiple of 4 and the grid 16-byte
-  // aligned), so entries outside the degree simplex read as zero below
-  float4* g4 = reinterpret_cast<float4*>(grid);
-  for (int i = lane; i < (G >> 2); i += 32) g4[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  __syncwarp();
   float rem = scatter_terms<UP>(P, ps, nt, T.gidx[LB], rs, T.mcount[Deff], grid);
   __syncwarp();
   float best = UP ? -CUDART_INF_F : CUDART_INF_F;
@@ -192,17 +186,16 @@ __device__ float enclose_warp(const float* __restrict__ P, int ps, int nt, int n
   const int2* __restrict__ lines = T.lines[LB];
   for (int k = n - 1; k >= 0; --k) {
     // lines along variable k: prefix digits (variables < k) untransformed,
-    // suffix digits (variables > k) transformed; the lines are sorted by
-    // prefix digit sum, and the first C(Deff + k, k) R^(n-1-k) of them have
-    // their prefix in the simplex
+    // suffix digits (variables > k) transformed
     const int sk = ipow(R, n - 1 - k);
-    int cnt = sk;
-    for (int i = 1; i <= k; ++i) cnt = cnt * (Deff + i) / i;   // exact at every step
-    for (int Ln = lane; Ln < cnt; Ln += 32) {
-      const int base = __ldg(lines + (int64_t)k * nlines + Ln).x;
+    for (int Ln = lane; Ln < nlines; Ln += 32) {
+      const int2 ln = __ldg(lines + (int64_t)k * nlines + Ln);
+      const int base = ln.x, psum = ln.y;
+      if (psum > Deff) continue;
+      const int p = Deff - psum;
       float x[R], y[R];
 #pragma unroll
-      for (int j = 0; j < R; ++j) x[j] = grid[base + j * sk];
+      for (int j = 0; j < R; ++j) x[j] = j <= p ? grid[base + j * sk] : 0.0f;
       line_transform<LB, UP>(x, y);
       if (k > 0) {
 #pragma unroll
@@ -259,8 +252,8 @@ k_enclose(Tables T, int G, const float2* __restrict__ rs, int64_t n_items, int h
     const int64_t b = item / h;
     const int64_t base = (b * ld) * h + (item - b * h);
     float* grid = smem + warp * G;
-    const float v = up ? enclose_warp<LB, true>(pre_up + base, h, nt, T.n, T, rs, grid, G)
-                       : enclose_warp<LB, false>(pre_lo + base, h, nt, T.n, T, rs, grid, G);
+    const float v = up ? enclose_warp<LB, true>(pre_up + base, h, nt, T.n, T, rs, grid)
+                       : enclose_warp<LB, false>(pre_lo + base, h, nt, T.n, T, rs, grid);
     if (lane == 0) {
       (up ? hi : lo)[item] = v;
       s_lohi[warp >> 1][up ? 1 : 0] = v;
@@ -285,7 +278,6 @@ cudaError_t launch_lb(const Launch& L, const Tables& T, int G, int64_t n_items, 
                       const int32_t* nterms, float* lo, float* hi, EncloseOpts ro) {
   // items per block: as many as fit 192 KB of grids, at most 8 (16 warps);
   // autotuned among 8, 4 and 2 (variants 0, 1, 2)
-  G = (G + 3) & ~3;                    // per-warp grid stride: 16-byte aligned grids
   int items = (int)std::min<int64_t>(8, (192 * 1024) / (2 * (int64_t)G * 4));
   const std::string key = "enclose/" + std::to_string(LB) + "/" + std::to_string(T.n) + "/" +
                           std::to_string(n_items);

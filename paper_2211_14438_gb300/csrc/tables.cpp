@@ -323,22 +323,6 @@ void build_enclose_tables(int n, int l, std::vector<int32_t>& gidx, std::vector<
       lines[(size_t)(2 * (k * nlines + Ln))] = (int32_t)base;
       lines[(size_t)(2 * (k * nlines + Ln)) + 1] = psum;
     }
-  // each variable's lines in ascending prefix digit sum (stable), so the lines
-  // whose prefix lies in the degree-D simplex are the first C(D + k, k) R^(n-1-k)
-  for (int k = 0; k < n; ++k) {
-    std::vector<std::pair<int32_t, int32_t>> v((size_t)nlines);
-    for (int64_t Ln = 0; Ln < nlines; ++Ln)
-      v[(size_t)Ln] = {lines[(size_t)(2 * (k * nlines + Ln)) + 1],
-                       lines[(size_t)(2 * (k * nlines + Ln))]};
-    std::stable_sort(v.begin(), v.end(),
-                     [](const std::pair<int32_t, int32_t>& a, const std::pair<int32_t, int32_t>& b) {
-                       return a.first < b.first;
-                     });
-    for (int64_t Ln = 0; Ln < nlines; ++Ln) {
-      lines[(size_t)(2 * (k * nlines + Ln))] = v[(size_t)Ln].second;
-      lines[(size_t)(2 * (k * nlines + Ln)) + 1] = v[(size_t)Ln].first;
-    }
-  }
 }
 
 }  // namespace bern
