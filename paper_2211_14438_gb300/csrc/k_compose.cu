@@ -106,7 +106,7 @@ k_compose_queue(Tables T, ComposeArgs A, int64_t n_items, int row_dmax, ComposeS
 
 // ------------------------------------------------------------ row convolution
 constexpr int kRowWarps = 4;    // warps sharing one 32-item group
-constexpr int kRowBlocks = 7;   // resident blocks per SM (registers and shared memory)
+constexpr int kRowBlocks = 8;   // resident blocks per SM (registers and shared memory)
 
 // One accumulator per output slot holds the square directly: an off-diagonal
 // row pair (p < q) counts twice in the square, so it multiplies 2*x[a]
@@ -209,10 +209,6 @@ __device__ void rows_range(const Tables& T, const ComposeArgs& A, const RowTable
     const int4 hd = __ldg(R.hdr + row);
     const int Lout = hd.w & 0xff, in_len = (hd.w >> 8) & 0xff;
     const int in_off = __ldg(R.in_off + row);
-    // fetch the row's output ranks now; they are used after the convolutions
-    int rk[2 * kRowLen - 1];
-#pragma unroll
-    for (int c = 0; c < 2 * kRowLen - 1; ++c) rk[c] = c < Lout ? __ldg(R.out_ranks + hd.z + c) : 0;
     float acc[2 * kRowLen - 1];
 #pragma unroll
     for (int c = 0; c < 2 * kRowLen - 1; ++c) acc[c] = 0.0f;
@@ -236,6 +232,7 @@ __device__ void rows_range(const Tables& T, const ComposeArgs& A, const RowTable
         default: break;
       }
     }
+    const int* __restrict__ rk = R.out_ranks + hd.z;   // the row's output ranks
 #pragma unroll
     for (int c = 0; c < 2 * kRowLen - 1; ++c) {
       if (c >= Lout) break;
@@ -244,8 +241,8 @@ __device__ void rows_range(const Tables& T, const ComposeArgs& A, const RowTable
       const float v = dfma<UP>(a2, sq, UP ? __fmul_ru(a1, lin) : __fmul_rd(a1, lin));
       if (row == 0 && c == 0) {
         *c0_out = v;                      // the constant term is finished by the caller
-      } else if (no_trunc || rk[c] < Mout) {
-        if (valid) Q[(int64_t)rk[c] * h] = v;
+      } else if (no_trunc || __ldg(rk + c) < Mout) {
+        if (valid) Q[(int64_t)__ldg(rk + c) * h] = v;
       } else {
         rem = UP ? __fadd_ru(rem, fmaxf(v, 0.0f)) : __fadd_rd(rem, fminf(v, 0.0f));
       }
