@@ -323,22 +323,27 @@ k_compose_rows(Tables T, ComposeArgs A, ComposeScratch S, int row_dmax, int sstr
 }
 
 // ------------------------------------------------------------ elementwise items
-// Identity items copy pre to post: one thread per (queue entry, coefficient),
-// entry fastest, so neighbouring threads touch neighbouring neurons.
+// Identity items copy pre to post: a lane per queue entry (32 consecutive
+// entries per warp, so neighbouring lanes touch neighbouring neurons), the
+// warps of a block over the coefficient rows.
 __global__ void __launch_bounds__(256)
 k_compose_copy(ComposeArgs A, ComposeScratch S) {
   const int cnt = S.qcount[kQIdent];
-  const int64_t total = (int64_t)cnt * A.pre_ld;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = g / cnt;
-    const int t = (int)(g - r * cnt);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t h = A.h;
+  for (int64_t t0 = (int64_t)blockIdx.x * 32; t0 < cnt; t0 += (int64_t)gridDim.x * 32) {
+    const int64_t t = t0 + lane;
+    if (t >= cnt) continue;
     const int64_t item = S.queue[(int64_t)kQIdent * S.qcap + t];
-    if (r >= A.pre_nterms[item]) continue;
-    const int64_t src = A.base(item, A.pre_ld) + r * A.h;
-    const int64_t dst = A.base(item, A.post_ld) + r * A.h;
-    A.post_up[dst] = A.pre_up[src];
-    A.post_lo[dst] = A.pre_lo[src];
+    const int nt = A.pre_nterms[item];
+    const float* su = A.pre_up + A.base(item, A.pre_ld);
+    const float* sl = A.pre_lo + A.base(item, A.pre_ld);
+    float* du = A.post_up + A.base(item, A.post_ld);
+    float* dl = A.post_lo + A.base(item, A.post_ld);
+    for (int r = warp; r < nt; r += nw) {
+      du[r * h] = su[r * h];
+      dl[r * h] = sl[r * h];
+    }
   }
 }
 
@@ -540,7 +545,7 @@ cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratc
   k_compose_rows<false><<<blocks, 32 * kRowWarps, smem, L.stream>>>(T, A, S, row_dmax, sstride,
                                                                     L.status);
   *L.launches += 2;
-  k_compose_copy<<<(unsigned)std::min<int64_t>((n_items * pre_ld + 255) / 256, 152 * 16), 256, 0,
+  k_compose_copy<<<(unsigned)std::min<int64_t>((n_items + 31) / 32, 152 * 16), 256, 0,
                    L.stream>>>(A, S);
   ++*L.launches;
   k_compose_linear<<<(unsigned)std::min<int64_t>((n_items + 7) / 8, 152 * 16), 256, 0,
