@@ -106,7 +106,7 @@ k_compose_queue(Tables T, ComposeArgs A, int64_t n_items, int row_dmax, ComposeS
 
 // ------------------------------------------------------------ row convolution
 constexpr int kRowWarps = 4;    // warps sharing one 32-item group
-constexpr int kRowBlocks = 10;  // resident blocks per SM (registers and shared memory)
+constexpr int kRowBlocks = 8;   // resident blocks per SM (registers and shared memory)
 
 // One accumulator per output slot holds the square directly: an off-diagonal
 // row pair (p < q) counts twice in the square, so it multiplies 2*x[a]
