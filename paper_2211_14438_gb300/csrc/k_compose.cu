@@ -105,27 +105,6 @@ k_compose_queue(Tables T, ComposeArgs A, int64_t n_items, int row_dmax, ComposeS
 }
 
 // ------------------------------------------------------------ row convolution
-// Read-only loads with an L1 eviction priority: the row tables, which every
-// warp of every block walks, are kept (evict_last); the items' streamed
-// coefficients are dropped first (evict_first).
-__device__ __forceinline__ int ld_keep(const int* p) {
-  int v;
-  asm("ld.global.nc.L1::evict_last.s32 %0, [%1];" : "=r"(v) : "l"(p));
-  return v;
-}
-__device__ __forceinline__ int4 ld_keep(const int4* p) {
-  int4 v;
-  asm("ld.global.nc.L1::evict_last.v4.s32 {%0, %1, %2, %3}, [%4];"
-      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-      : "l"(p));
-  return v;
-}
-__device__ __forceinline__ float ld_stream(const float* p) {
-  float v;
-  asm("ld.global.nc.L1::evict_first.f32 %0, [%1];" : "=f"(v) : "l"(p));
-  return v;
-}
-
 constexpr int kRowWarps = 4;    // warps sharing one 32-item group
 constexpr int kRowBlocks = 8;   // resident blocks per SM (registers and shared memory)
 
@@ -199,8 +178,8 @@ __device__ float load_rows(const ComposeArgs& A, const RowTable& R, const float*
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int r = r0 + i;
-      v[i] = r < Mpre ? ld_stream(P + (int64_t)r * h) : 0.0f;
-      pos[i] = r < R.m_in ? ld_keep(R.pos_in + r) : -1;
+      v[i] = r < Mpre ? __ldg(P + (int64_t)r * h) : 0.0f;
+      pos[i] = r < R.m_in ? __ldg(R.pos_in + r) : -1;
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -227,18 +206,18 @@ __device__ void rows_range(const Tables& T, const ComposeArgs& A, const RowTable
   const bool no_trunc = 2 * D <= A.cap;   // every output monomial is kept
   float rem = 0.0f;
   for (int row = row_b; row < row_e; row += row_step) {
-    const int4 hd = ld_keep(R.hdr + row);
+    const int4 hd = __ldg(R.hdr + row);
     const int Lout = hd.w & 0xff, in_len = (hd.w >> 8) & 0xff;
-    const int in_off = ld_keep(R.in_off + row);
+    const int in_off = __ldg(R.in_off + row);
     float acc[2 * kRowLen - 1];
 #pragma unroll
     for (int c = 0; c < 2 * kRowLen - 1; ++c) acc[c] = 0.0f;
     const int has_diag = (hd.w >> 16) & 1;
     const int off_end = hd.y - has_diag;
     if (hd.x < off_end) {
-      int4 pr = ld_keep(R.pairs + hd.x);
+      int4 pr = __ldg(R.pairs + hd.x);
       for (int k = hd.x; k < off_end; ++k) {
-        const int4 nx = k + 1 < off_end ? ld_keep(R.pairs + k + 1) : pr;   // prefetch
+        const int4 nx = k + 1 < off_end ? __ldg(R.pairs + k + 1) : pr;   // prefetch
         switch (pr.z) {
           BERN_CONV_ALL_CASES
           default: break;
@@ -247,7 +226,7 @@ __device__ void rows_range(const Tables& T, const ComposeArgs& A, const RowTable
       }
     }
     if (has_diag) {
-      const int4 pr = ld_keep(R.pairs + off_end);
+      const int4 pr = __ldg(R.pairs + off_end);
       switch (pr.z & 15) {
         BERN_DIAG_CASES
         default: break;
@@ -262,8 +241,8 @@ __device__ void rows_range(const Tables& T, const ComposeArgs& A, const RowTable
       const float v = dfma<UP>(a2, sq, UP ? __fmul_ru(a1, lin) : __fmul_rd(a1, lin));
       if (row == 0 && c == 0) {
         *c0_out = v;                      // the constant term is finished by the caller
-      } else if (no_trunc || ld_keep(rk + c) < Mout) {
-        if (valid) Q[(int64_t)ld_keep(rk + c) * h] = v;
+      } else if (no_trunc || __ldg(rk + c) < Mout) {
+        if (valid) Q[(int64_t)__ldg(rk + c) * h] = v;
       } else {
         rem = UP ? __fadd_ru(rem, fmaxf(v, 0.0f)) : __fadd_rd(rem, fminf(v, 0.0f));
       }
