@@ -231,8 +231,10 @@ __device__ __forceinline__ int64_t map_item(const EncloseOpts& o, int64_t idx, i
   return idx < n_items ? idx : -1;
 }
 
+// Orders up to 6 fit 32 registers without spills: four 512-thread blocks per
+// SM (64 warps); higher orders keep three.
 template <int LB>
-__global__ void __launch_bounds__(512, 3)
+__global__ void __launch_bounds__(512, (LB <= 6 ? 4 : 3))
 k_enclose(Tables T, int G, const float2* __restrict__ rs, int64_t n_items, int h,
           const float* __restrict__ pre_up, const float* __restrict__ pre_lo, int64_t ld,
           const int32_t* __restrict__ nterms, float* __restrict__ lo, float* __restrict__ hi,
