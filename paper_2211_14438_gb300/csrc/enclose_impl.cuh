@@ -123,6 +123,19 @@ static __device__ int relu_item(float l, float h, int d, float* a, float* eps, i
 }
 
 // ------------------------------------------------------------------ a2
+// In place, from the top: y_i needs x_0 .. x_i only, so x_i can take y_i
+// once it is formed (same FMAs in the same order as line_transform).
+template <int LB, bool UP>
+__device__ __forceinline__ void line_transform_inplace(float (&x)[LB + 1]) {
+#pragma unroll
+  for (int i = LB; i >= 1; --i) {
+    float acc = x[0];
+#pragma unroll
+    for (int j = 1; j <= i; ++j) acc = dfma<UP>(cbin(i, j), x[j], acc);
+    x[i] = acc;
+  }
+}
+
 template <int LB, bool UP>
 __device__ __forceinline__ void line_transform(const float (&x)[LB + 1], float (&y)[LB + 1]) {
 #pragma unroll
@@ -193,16 +206,16 @@ __device__ float enclose_warp(const float* __restrict__ P, int ps, int nt, int n
       const int base = ln.x, psum = ln.y;
       if (psum > Deff) continue;
       const int p = Deff - psum;
-      float x[R], y[R];
+      float x[R];
 #pragma unroll
       for (int j = 0; j < R; ++j) x[j] = j <= p ? grid[base + j * sk] : 0.0f;
-      line_transform<LB, UP>(x, y);
+      line_transform_inplace<LB, UP>(x);
       if (k > 0) {
 #pragma unroll
-        for (int i = 0; i < R; ++i) grid[base + i * sk] = y[i];
+        for (int i = 0; i < R; ++i) grid[base + i * sk] = x[i];
       } else {
 #pragma unroll
-        for (int i = 0; i < R; ++i) best = UP ? fmaxf(best, y[i]) : fminf(best, y[i]);
+        for (int i = 0; i < R; ++i) best = UP ? fmaxf(best, x[i]) : fminf(best, x[i]);
       }
     }
     __syncwarp();
