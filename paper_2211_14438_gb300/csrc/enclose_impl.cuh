@@ -206,16 +206,24 @@ __device__ float enclose_warp(const float* __restrict__ P, int ps, int nt, int n
       const int base = ln.x, psum = ln.y;
       if (psum > Deff) continue;
       const int p = Deff - psum;
-      float x[R];
+      float x[R], y[R];
 #pragma unroll
       for (int j = 0; j < R; ++j) x[j] = j <= p ? grid[base + j * sk] : 0.0f;
-      line_transform_inplace<LB, UP>(x);
+      // in place up to order 8 (fewer live registers); above, the separate
+      // output array schedules better (measured)
+      if constexpr (LB <= 8) {
+        line_transform_inplace<LB, UP>(x);
+#pragma unroll
+        for (int i = 0; i < R; ++i) y[i] = x[i];
+      } else {
+        line_transform<LB, UP>(x, y);
+      }
       if (k > 0) {
 #pragma unroll
-        for (int i = 0; i < R; ++i) grid[base + i * sk] = x[i];
+        for (int i = 0; i < R; ++i) grid[base + i * sk] = y[i];
       } else {
 #pragma unroll
-        for (int i = 0; i < R; ++i) best = UP ? fmaxf(best, x[i]) : fminf(best, x[i]);
+        for (int i = 0; i < R; ++i) best = UP ? fmaxf(best, y[i]) : fminf(best, y[i]);
       }
     }
     __syncwarp();
