@@ -311,10 +311,9 @@ __device__ __forceinline__ void row_task(const Tables& T, const ComposeArgs& A,
 
 // A block of kRowWarps warps squares one bound of 32 queued items (one lane
 // per item); the warps share the items' inputs in shared memory and take the
-// output rows in turn.  One launch covers both bounds: all upper-bound tasks,
-// then all lower-bound ones (so an SM runs one bound's code at a time), each
-// from the highest input degree down, so the last round of the persistent
-// blocks holds the cheapest tasks.
+// output rows in turn.  One launch covers both bounds: the tasks run from the
+// highest input degree down (upper and lower bound of a chunk next to each
+// other), so the last round of the persistent blocks holds the cheapest tasks.
 __global__ void __launch_bounds__(32 * kRowWarps, kRowBlocks)
 k_compose_rows(Tables T, ComposeArgs A, ComposeScratch S, int row_dmax, int sstride,
                int* status) {
@@ -322,23 +321,21 @@ k_compose_rows(Tables T, ComposeArgs A, ComposeScratch S, int row_dmax, int sstr
   __shared__ float s_l1[kRowWarps][32], s_rem[kRowWarps][32], s_c0[32];
   const int lane = threadIdx.x & 31;
   float* s = smem + (size_t)lane * sstride;
-  int total = 0;
-  for (int d = 0; d <= row_dmax; ++d) total += (S.qcount[d] + 31) >> 5;
-  for (int task = blockIdx.x; task < 2 * total; task += gridDim.x) {
-    const bool up = task < total;
-    int D = -1, chunk = up ? task : task - total;
+  for (int task = blockIdx.x;; task += gridDim.x) {
+    int D = -1, chunk = task;
     for (int d = row_dmax; d >= 0; --d) {
       const int nc = (S.qcount[d] + 31) >> 5;
-      if (chunk < nc) {
+      if (chunk < 2 * nc) {
         D = d;
         break;
       }
-      chunk -= nc;
+      chunk -= 2 * nc;
     }
-    if (up)
-      row_task<true>(T, A, S, D, chunk, s, s_l1, s_rem, s_c0, status);
+    if (D < 0) break;
+    if ((chunk & 1) == 0)
+      row_task<true>(T, A, S, D, chunk >> 1, s, s_l1, s_rem, s_c0, status);
     else
-      row_task<false>(T, A, S, D, chunk, s, s_l1, s_rem, s_c0, status);
+      row_task<false>(T, A, S, D, chunk >> 1, s, s_l1, s_rem, s_c0, status);
     __syncthreads();   // the next task reuses the shared inputs
   }
 }
