@@ -254,88 +254,70 @@ __device__ void rows_range(const Tables& T, const ComposeArgs& A, const RowTable
 // A block of kRowWarps warps squares one bound (UP: upper) of 32 queued items
 // (one lane per item); the warps share the items' inputs in shared memory and
 // take the output rows in turn.
-// One task: one bound (UP: upper) of the 32 queued items of chunk `chunk` of
-// queue D.
 template <bool UP>
-__device__ __forceinline__ void row_task(const Tables& T, const ComposeArgs& A,
-                                         const ComposeScratch& S, int D, int chunk, float* s,
-                                         float (*s_l1)[32], float (*s_rem)[32], float* s_c0,
-                                         int* status) {
-  const int lane = threadIdx.x & 31, half = threadIdx.x >> 5;
-  const int idx = chunk * 32 + lane;
-  const bool valid = idx < S.qcount[D];
-  const int64_t item = valid ? S.queue[(int64_t)D * S.qcap + idx] : 0;
-  const RowTable R = T.row[D];
-  const float Lo = valid ? A.lo[item] : -1.0f;
-  const float Hi = valid ? A.hi[item] : 1.0f;
-  const float inv = 1.0f / (Hi - Lo);
-  float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
-  if (valid) {
-    const float* cf = A.coef + item * kCoefStride;
-    a0 = cf[0];
-    a1 = cf[1];
-    a2 = cf[2];
-    if (a2 < 0.0f) atomicOr(status, kStatusUnsupported);   // excluded by convexity
-  }
-  const int Mpre = valid ? A.pre_nterms[item] : 0;
-  const float* P = (UP ? A.pre_up : A.pre_lo) + A.base(valid ? item : 0, A.pre_ld);
-  s_l1[half][lane] = load_rows(A, R, P, Mpre, Lo, inv, half, s);
-  __syncthreads();
-  float* Q = (UP ? A.post_up : A.post_lo) + A.base(valid ? item : 0, A.post_ld);
-  float c0 = 0.0f, rem = 0.0f;
-  rows_range<UP>(T, A, R, D, half, R.n_out_rows, kRowWarps, valid, a1, a2, s, Q, &c0, &rem);
-  s_rem[half][lane] = rem;
-  if (!half) s_c0[lane] = c0;
-  __syncthreads();
-  if (!half && valid) {
-    // constant term: a0 + (the row-0 value without a0) + Lip*eta + remainder
-    float l1 = s_l1[0][lane], remt = s_rem[0][lane];
-#pragma unroll
-    for (int w = 1; w < kRowWarps; ++w) {
-      l1 = __fadd_ru(l1, s_l1[w][lane]);
-      remt = UP ? __fadd_ru(remt, s_rem[w][lane]) : __fadd_rd(remt, s_rem[w][lane]);
-    }
-    const float eta = __fmul_ru(5.0f * kU, l1);
-    const float lip = __fmaf_ru(2.0f * a2, __fadd_ru(1.0f, eta), fabsf(a1));
-    float v;
-    if (UP) {
-      v = __fadd_ru(__fadd_ru(__fadd_ru(s_c0[lane], a0), __fmul_ru(lip, eta)), remt);
-    } else {
-      v = __fsub_rd(__fadd_rd(s_c0[lane], a0), __fmul_ru(lip, eta));
-      v = __fadd_rd(__fsub_rd(v, A.eps[item]), remt);
-    }
-    Q[0] = v;
-    if (!isfinite(v)) atomicOr(status, kStatusNonFinite);
-  }
-}
-
-// A block of kRowWarps warps squares one bound of 32 queued items (one lane
-// per item); the warps share the items' inputs in shared memory and take the
-// output rows in turn.  One launch covers both bounds: the tasks run from the
-// highest input degree down (upper and lower bound of a chunk next to each
-// other), so the last round of the persistent blocks holds the cheapest tasks.
 __global__ void __launch_bounds__(32 * kRowWarps, kRowBlocks)
 k_compose_rows(Tables T, ComposeArgs A, ComposeScratch S, int row_dmax, int sstride,
                int* status) {
   extern __shared__ float smem[];
   __shared__ float s_l1[kRowWarps][32], s_rem[kRowWarps][32], s_c0[32];
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, half = threadIdx.x >> 5;
   float* s = smem + (size_t)lane * sstride;
   for (int task = blockIdx.x;; task += gridDim.x) {
     int D = -1, chunk = task;
-    for (int d = row_dmax; d >= 0; --d) {
+    for (int d = 0; d <= row_dmax; ++d) {
       const int nc = (S.qcount[d] + 31) >> 5;
-      if (chunk < 2 * nc) {
+      if (chunk < nc) {
         D = d;
         break;
       }
-      chunk -= 2 * nc;
+      chunk -= nc;
     }
     if (D < 0) break;
-    if ((chunk & 1) == 0)
-      row_task<true>(T, A, S, D, chunk >> 1, s, s_l1, s_rem, s_c0, status);
-    else
-      row_task<false>(T, A, S, D, chunk >> 1, s, s_l1, s_rem, s_c0, status);
+    const int idx = chunk * 32 + lane;
+    const bool valid = idx < S.qcount[D];
+    const int64_t item = valid ? S.queue[(int64_t)D * S.qcap + idx] : 0;
+    const RowTable R = T.row[D];
+    const float Lo = valid ? A.lo[item] : -1.0f;
+    const float Hi = valid ? A.hi[item] : 1.0f;
+    const float inv = 1.0f / (Hi - Lo);
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+    if (valid) {
+      const float* cf = A.coef + item * kCoefStride;
+      a0 = cf[0];
+      a1 = cf[1];
+      a2 = cf[2];
+      if (a2 < 0.0f) atomicOr(status, kStatusUnsupported);   // excluded by convexity
+    }
+    const int Mpre = valid ? A.pre_nterms[item] : 0;
+    const float* P = (UP ? A.pre_up : A.pre_lo) + A.base(valid ? item : 0, A.pre_ld);
+    s_l1[half][lane] = load_rows(A, R, P, Mpre, Lo, inv, half, s);
+    __syncthreads();
+    float* Q = (UP ? A.post_up : A.post_lo) + A.base(valid ? item : 0, A.post_ld);
+    float c0 = 0.0f, rem = 0.0f;
+    rows_range<UP>(T, A, R, D, half, R.n_out_rows, kRowWarps, valid, a1, a2, s, Q, &c0, &rem);
+    s_rem[half][lane] = rem;
+    if (!half) s_c0[lane] = c0;
+    __syncthreads();
+    if (!half && valid) {
+      // constant term: a0 + (the row-0 value without a0) + Lip*eta + remainder
+      float l1 = s_l1[0][lane], remt = s_rem[0][lane];
+#pragma unroll
+      for (int w = 1; w < kRowWarps; ++w) {
+        l1 = __fadd_ru(l1, s_l1[w][lane]);
+        remt = UP ? __fadd_ru(remt, s_rem[w][lane]) : __fadd_rd(remt, s_rem[w][lane]);
+      }
+      const float eta = __fmul_ru(5.0f * kU, l1);
+      const float lip = __fmaf_ru(2.0f * a2, __fadd_ru(1.0f, eta), fabsf(a1));
+      float v;
+      if (UP) {
+        v = __fadd_ru(__fadd_ru(__fadd_ru(s_c0[lane], a0), __fmul_ru(lip, eta)), remt);
+      } else {
+        v = __fsub_rd(__fadd_rd(s_c0[lane], a0), __fmul_ru(lip, eta));
+        v = __fadd_rd(__fsub_rd(v, A.eps[item]), remt);
+      }
+      Q[0] = v;
+      if (!isfinite(v)) atomicOr(status, kStatusNonFinite);
+    }
     __syncthreads();   // the next task reuses the shared inputs
   }
 }
@@ -543,21 +525,26 @@ cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratc
   k_compose_queue<<<(unsigned)((n_items + 1023) / 1024), 1024, 0, L.stream>>>(
       T, A, n_items, row_dmax, S, L.status);
   ++*L.launches;
-  // row-convolution kernel (both bounds): persistent blocks of kRowWarps
-  // warps per 32 items; the per-lane stride is odd so that lanes reading the
-  // same offset hit distinct banks
+  // row-convolution kernels (one per bound): persistent blocks of 2 warps
+  // per 32 items; the per-lane stride is odd so that lanes reading the same
+  // offset hit distinct banks
   const int sstride = (int)num_monomials(T.n, row_dmax) | 1;
   const size_t smem = (size_t)32 * sstride * sizeof(float);
   if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_compose_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_compose_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_compose_rows<false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  const int64_t tasks = 2 * (n_items / 32 + row_dmax + 1);
+  const int64_t tasks = n_items / 32 + row_dmax + 1;
   const int blocks = (int)std::min<int64_t>(tasks, 152 * kRowBlocks);
-  k_compose_rows<<<blocks, 32 * kRowWarps, smem, L.stream>>>(T, A, S, row_dmax, sstride,
-                                                             L.status);
-  ++*L.launches;
+  k_compose_rows<true><<<blocks, 32 * kRowWarps, smem, L.stream>>>(T, A, S, row_dmax, sstride,
+                                                                   L.status);
+  k_compose_rows<false><<<blocks, 32 * kRowWarps, smem, L.stream>>>(T, A, S, row_dmax, sstride,
+                                                                    L.status);
+  *L.launches += 2;
   k_compose_copy<<<(unsigned)std::min<int64_t>((n_items + 31) / 32, 152 * 16), 256, 0,
                    L.stream>>>(A, S);
   ++*L.launches;
