@@ -8,7 +8,8 @@
 // round-down FMAs, so each computed coefficient bounds the exact one from the
 // correct side; with t^K >= 0 on the box that bounds the polynomial values.
 //
-// The tiled kernel uses the midpoint-radius form of the same step: with
+// The kernels for layers of more than 8 neurons (tiled, persistent wide and
+// short) use the midpoint-radius form of the same step: with
 // c = fl((up + lo) / 2) and r >= max(up - c, c - lo) (rounded up), every
 // input coefficient lies in [c - r, c + r], and for any weight w
 //   w+ up + w- lo = w c + |w| r  (exactly, when c, r are exact),
@@ -20,10 +21,11 @@
 //
 // With the layer-block layout (coefficient r of neuron j of box b at
 // ((b*ld + r)*h + j)) each box is a row-major [M x h_in] matrix per bound and
-// the step is the product with W^T: a small GEMM per box.  A block computes a
-// BM (neurons) x BR (monomials) tile of one box; K (= h_in) is staged through
-// shared memory in chunks of KC, and every thread keeps a TM x TR register
-// tile per bound.  Inputs beyond a neuron's term count are read as zero.
+// the step is the product with W^T: a small GEMM per box.  In the tiled
+// kernel a block computes a BM (neurons) x BR (monomials) tile of one box; K
+// (= h_in) is staged through shared memory in chunks of KC, and every thread
+// keeps a TM x TR register tile per bound.  Inputs beyond a neuron's term
+// count are read as zero.
 #include <algorithm>
 #include <string>
 

@@ -72,7 +72,10 @@ def test_init_rejects_inverted_box(ctx):
 # ---------------------------------------------------------------- a1
 @pytest.mark.parametrize("n,D,h_in,h_out,B", [
     (2, 2, 5, 7, 3), (3, 4, 20, 9, 5), (4, 3, 33, 17, 2), (3, 8, 64, 1, 3), (2, 3, 6, 3, 4),
-    (3, 2, 7, 5, 2), (3, 8, 64, 64, 2), (2, 4, 40, 33, 3), (6, 2, 100, 100, 2), (1, 6, 3, 2, 5)])
+    (3, 2, 7, 5, 2), (3, 8, 64, 64, 2), (2, 4, 40, 33, 3), (6, 2, 100, 100, 2), (1, 6, 3, 2, 5),
+    # a warp per box at exactly 16 rows; the register-blocked kernel with
+    # h_in > 128 and a ragged neuron slice; the quad kernel at G = 4 and 32
+    (1, 15, 20, 40, 3), (3, 4, 150, 70, 2), (2, 4, 4, 1, 3), (2, 3, 128, 2, 3)])
 def test_affine_step(ctx, n, D, h_in, h_out, B):
     rng = np.random.default_rng(n * 100 + D)
     M = bern.num_monomials(n, D)
