@@ -242,6 +242,28 @@ int bern_propagate_traced(bern_ctx* ctx, const bern_net* net, const float* boxes
                           int64_t n_boxes, const bern_degree_plan* plan,
                           bern_result* result, const bern_trace* trace);
 
+/* Output polynomials in the input coordinates x (the change of variables of
+ * Sec. 5.3 undone: bern_propagate returns them in t in [0,1]^n with
+ * x_i = dlo_i + w_i t_i, w_i = dhi_i - dlo_i rounded up).  For every box b,
+ * output j and bound k (0 upper, 1 lower) the polynomial
+ *   coef_t[((b*o + j)*2 + k)*cap_terms + r], r < n_terms[(b*o + j)*2 + k]
+ * (graded monomial order, bern_result's layout) is rewritten as a polynomial
+ * in x over the same graded monomials, into coef_x (same layout; entries past
+ * the term count are not written).  The float64 expansion's rounding and the
+ * rounding to float are bounded on the box and folded into the constant term
+ * (added for upper polynomials, subtracted for lower ones), so the converted
+ * upper (lower) polynomial is >= (<=) the original everywhere on the box.
+ *   boxes: [n_boxes x n x 2] (dlo, dhi), the boxes the polynomials were
+ *   computed on.  All pointers are device pointers; the call is asynchronous
+ *   on the context's stream and a term count outside [0, cap_terms], an
+ *   invalid box or a non-finite constant is reported by the next bern_sync.
+ * Returns BERN_E_INVALID for bad sizes, BERN_E_UNSUPPORTED when cap_terms
+ * needs per-variable tables above 200 KB of shared memory (total degree above
+ * about 40 for n = 2). */
+int bern_poly_to_x(bern_ctx* ctx, int n, int64_t n_boxes, int o, const float* boxes,
+                   const int32_t* n_terms, const float* coef_t, int64_t cap_terms,
+                   float* coef_x);
+
 /* -------------------------------------------------- step entry points
  * The five steps of the path on the library's dense layout, for testing and
  * for callers composing their own pipeline.  All pointers are device

@@ -52,6 +52,7 @@ EXPORTS = [
     "bern_mlp_num_params", "bern_degree_features", "bern_mlp_forward", "bern_mlp_backward",
     "bern_mlp_adam", "bern_propagate_traced", "bern_split_features",
     "bern_set_horner_smem_limit", "bern_set_autotune", "bern_force_variant",
+    "bern_poly_to_x",
 ]
 
 
@@ -118,6 +119,7 @@ def load(build_if_missing: bool = True):
         "bern_set_horner_smem_limit": (I, [V, I64]),
         "bern_set_autotune": (I, [V, I]),
         "bern_force_variant": (I, [V, ctypes.c_char_p, I]),
+        "bern_poly_to_x": (I, [V, I, I64, I, V, V, V, I64, V]),
         "bern_strerror": (ctypes.c_char_p, [I]),
         "bern_sync": (I, [V]),
         "bern_kernel_launches": (I64, [V]),
@@ -245,6 +247,19 @@ class Context:
         _check(self.lib.bern_affine(self.h, n_boxes, h_out, h_in, _ptr(W), _ptr(b), _ptr(in_up),
                                     _ptr(in_lo), in_ld, _ptr(in_nterms), _ptr(out_up),
                                     _ptr(out_lo), out_ld, _ptr(out_nterms)), "bern_affine")
+
+    def poly_to_x(self, boxes, n_terms, coef, out=None):
+        """Output polynomials of ``propagate`` (``n_terms`` [B, o, 2], ``coef``
+        [B, o, 2, cap]) rewritten in the input coordinates x of their boxes
+        (``boxes`` [B, n, 2]); the constant terms carry the rounding remainder
+        outward.  Returns ``out`` (a tensor shaped like ``coef``)."""
+        B, n = int(boxes.shape[0]), int(boxes.shape[1])
+        o, cap = int(coef.shape[1]), int(coef.shape[3])
+        if out is None:
+            out = coef.new_zeros(coef.shape)
+        _check(self.lib.bern_poly_to_x(self.h, n, B, o, _ptr(boxes), _ptr(n_terms), _ptr(coef),
+                                       cap, _ptr(out)), "bern_poly_to_x")
+        return out
 
     def enclose(self, n, n_boxes, h, order, budget, pre_up, pre_lo, ld, nterms, lo, hi):
         _check(self.lib.bern_enclose(self.h, n, n_boxes, h, order, budget, _ptr(pre_up),

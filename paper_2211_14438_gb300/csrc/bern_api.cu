@@ -737,6 +737,24 @@ int bern_affine(bern_ctx* c, int64_t n_boxes, int h_out, int h_in, const float* 
                                 in_nterms, out_up, out_lo, out_ld, out_nterms));
 }
 
+int bern_poly_to_x(bern_ctx* c, int n, int64_t n_boxes, int o, const float* boxes,
+                   const int32_t* n_terms, const float* coef_t, int64_t cap_terms,
+                   float* coef_x) {
+  if (!c || n < 1 || n > kMaxVars || n_boxes < 0 || o < 1 || cap_terms < 1 || !boxes ||
+      !n_terms || !coef_t || !coef_x)
+    return BERN_E_INVALID;
+  cudaSetDevice(c->device);
+  const Tables* T;
+  int rc = ensure_tables(c, n, 0, &T);
+  if (rc) return rc;
+  // the degree of the longest graded prefix the buffers can hold
+  int D = 0;
+  while (D < kMaxTableDegree && num_monomials(n, D) < std::min<int64_t>(cap_terms, T->mexps)) ++D;
+  if (poly_to_x_smem(n, D) > 200 * 1024) return BERN_E_UNSUPPORTED;
+  return map_cuda(launch_poly_to_x(c->launch(), *T, n, n_boxes, o, boxes, n_terms, coef_t,
+                                   cap_terms, coef_x, D));
+}
+
 int bern_enclose(bern_ctx* c, int n, int64_t n_boxes, int h, int order, int64_t budget,
                  const float* pre_up, const float* pre_lo, int64_t ld, const int32_t* nterms,
                  float* lo, float* hi) {

@@ -158,6 +158,10 @@ void tune_end(const Launch& L, const char* kind, const std::string& key, TuneTim
 // term counts at b*h + m.
 cudaError_t launch_init_inputs(const Launch& L, int n, int64_t n_boxes, const float* boxes,
                                float* z_up, float* z_lo, int64_t ld, int32_t* nterms);
+size_t poly_to_x_smem(int n, int D);
+cudaError_t launch_poly_to_x(const Launch& L, const Tables& T, int n, int64_t n_boxes, int o,
+                             const float* boxes, const int32_t* nterms, const float* coef_t,
+                             int64_t cap, float* coef_x, int D);
 cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
                           const float* W, const float* b, const float* in_up,
                           const float* in_lo, int64_t in_ld, const int32_t* in_nterms,
