@@ -29,10 +29,13 @@ import numpy as np
 Poly = Dict[Tuple[int, ...], float]
 
 
-def poly_to_x(p: Poly, dlo: Sequence[float], w: Sequence[float]) -> Poly:
-    """P(t) as a polynomial in x, with t_i = (x_i - dlo_i) / w_i."""
+def poly_to_x(p: Poly, dlo: Sequence[float], w: Sequence[float], magnitudes: bool = False):
+    """P(t) as a polynomial in x, with t_i = (x_i - dlo_i) / w_i.  With
+    ``magnitudes`` also the sum of the absolute values of the terms that make
+    up each coefficient (the scale of its cancellation)."""
     n = len(dlo)
     out: Poly = {}
+    mag: Poly = {}
     for K, c in p.items():
         if c == 0.0:
             continue
@@ -51,7 +54,8 @@ def poly_to_x(p: Poly, dlo: Sequence[float], w: Sequence[float]) -> Poly:
             for _, f in combo:
                 v *= f
             out[J] = out.get(J, 0.0) + v
-    return out
+            mag[J] = mag.get(J, 0.0) + abs(v)
+    return (out, mag) if magnitudes else out
 
 
 def eval_x(p: Poly, x: np.ndarray) -> np.ndarray:

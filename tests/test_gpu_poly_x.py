@@ -3,11 +3,14 @@ oracle's float64 binomial expansion of the same t-polynomials, its outward
 constant terms, Monte-Carlo soundness of the converted bounds in x, a box
 with a zero-width side, and the term-count check.
 
-Tolerances: every coefficient but the constant is the float rounding of a
-float64 sum, so it lies within 2^-23 |e_J| (plus the float64 error, far
-below 1e-12 of the term magnitudes) of the oracle's; the constant term is
-outward (>= the oracle's for an upper polynomial, <= for a lower one) by at
-most 1e-6 of the polynomial's magnitude on the box."""
+Tolerances follow the kernel's own bound.  With E_J the sum of the
+magnitudes of the terms behind coefficient J (from the oracle) and
+g = 2 (n (4D + 3) + nt + 4) 2^-53, each coefficient but the constant lies
+within 2^-24 |e_J| + 2 g E_J of the oracle's; the constant is outward (>= the
+oracle's for an upper polynomial, <= for a lower one) by at most twice
+R = sum_{J != 0} (2^-24 |e_J| + g E_J) X^J + g E_0, X_i = max |x_i| on the
+box.  In x the monomial basis is badly conditioned on small boxes far from
+the origin (E_J can exceed |e_J| by many orders), which R reflects."""
 import numpy as np
 import pytest
 
@@ -67,18 +70,23 @@ def check_box(net, box, g, cx, bi, rng, n_mc=4000):
         for k in (0, 1):
             nt = int(g["n_terms"][bi, j, k])
             pt = dict_from_dense(g["coef"][bi, j, k, :nt].astype(np.float64), n)
-            e = poly_x.poly_to_x(pt, dlo, w)
+            e, E = poly_x.poly_to_x(pt, dlo, w, magnitudes=True)
             exps = exps_of(n, nt)
-            mag = sum(abs(v) * np.prod(X ** np.asarray(J, np.float64)) for J, v in e.items())
+            D = int(max(sum(int(v) for v in ex) for ex in exps))
+            gam = 2.0 * (n * (4 * D + 3) + nt + 4) * 2.0 ** -53
+            R = gam * E.get((0,) * n, 0.0)
             for r in range(1, nt):
-                want = e.get(tuple(int(v) for v in exps[r]), 0.0)
-                assert abs(cx[bi, j, k, r] - want) <= 2.0 ** -23 * abs(want) + 1e-12 * (1 + mag)
+                J = tuple(int(v) for v in exps[r])
+                want, EJ = e.get(J, 0.0), E.get(J, 0.0)
+                assert abs(cx[bi, j, k, r] - want) <= 2.0 ** -24 * abs(want) + 2 * gam * EJ
+                R += (2.0 ** -24 * abs(want) + gam * EJ) * np.prod(X ** np.asarray(J, np.float64))
             e0 = e.get((0,) * n, 0.0)
             c0 = cx[bi, j, k, 0]
             if k == 0:
-                assert c0 >= e0 and c0 - e0 <= 1e-6 * (1 + mag)
+                assert c0 >= e0 and c0 - e0 <= 2 * R + 1e-30
             else:
-                assert c0 <= e0 and e0 - c0 <= 1e-6 * (1 + mag)
+                assert c0 <= e0 and e0 - c0 <= 2 * R + 1e-30
+            mag = sum(abs(v) * np.prod(X ** np.asarray(J, np.float64)) for J, v in e.items())
             px = {tuple(int(v) for v in exps[r]): cx[bi, j, k, r] for r in range(nt)}
             vals = poly_x.eval_x(px, x)
             tol = 1e-9 * (1 + mag + np.abs(nn[:, j]))
