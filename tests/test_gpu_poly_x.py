@@ -9,7 +9,7 @@ g = 2 (n (4D + 3) + nt + 4) 2^-53, each coefficient but the constant lies
 within 2^-24 |e_J| + 2 g E_J of the oracle's; the constant is outward (>= the
 oracle's for an upper polynomial, <= for a lower one) by at most twice
 R = sum_{J != 0} (2^-24 |e_J| + g E_J) X^J + g E_0, X_i = max |x_i| on the
-box.  In x the monomial basis is badly conditioned on small boxes far from
+box, plus one float ulp of its own directed rounding.  In x the monomial basis is badly conditioned on small boxes far from
 the origin (E_J can exceed |e_J| by many orders), which R reflects."""
 import numpy as np
 import pytest
@@ -82,10 +82,11 @@ def check_box(net, box, g, cx, bi, rng, n_mc=4000):
                 R += (2.0 ** -24 * abs(want) + gam * EJ) * np.prod(X ** np.asarray(J, np.float64))
             e0 = e.get((0,) * n, 0.0)
             c0 = cx[bi, j, k, 0]
+            ulp = 2.0 ** -23 * abs(c0) + 1e-44            # the constant's directed rounding
             if k == 0:
-                assert c0 >= e0 and c0 - e0 <= 2 * R + 1e-30
+                assert c0 >= e0 and c0 - e0 <= 2 * R + ulp
             else:
-                assert c0 <= e0 and e0 - c0 <= 2 * R + 1e-30
+                assert c0 <= e0 and e0 - c0 <= 2 * R + ulp
             mag = sum(abs(v) * np.prod(X ** np.asarray(J, np.float64)) for J, v in e.items())
             px = {tuple(int(v) for v in exps[r]): cx[bi, j, k, r] for r in range(nt)}
             vals = poly_x.eval_x(px, x)
