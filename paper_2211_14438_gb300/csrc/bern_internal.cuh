@@ -56,6 +56,11 @@ bool build_product_table(int n, int Dq, int Ds, int64_t max_pairs, std::vector<i
 // convolution of the two rows.
 constexpr int kMaxRowDegree = 8;          // input degree handled by row convolution
 constexpr int kRowLen = kMaxRowDegree + 1;
+// Dense index 0..44 of a pair of row lengths 1 <= l1 <= l2 <= kRowLen (the
+// case of the squaring kernel's dispatch; dense cases make a jump table).
+__host__ __device__ constexpr int row_pair_case(int l1, int l2) {
+  return (l1 - 1) * kRowLen - (l1 - 1) * (l1 - 2) / 2 + (l2 - l1);
+}
 struct RowImage {
   int m_in = 0, n_out_rows = 0;
   int row_split = 0;               // output rows [0, split) hold about half the work
@@ -63,7 +68,7 @@ struct RowImage {
   std::vector<int32_t> hdr;        // per output row: pair_begin, pair_end, rank_begin,
                                    // Lout | in_len<<8 | has_diag<<16 (diagonal pair last)
   std::vector<int32_t> in_off;     // per output row: its input-row offset or -1
-  std::vector<int32_t> pairs;      // per pair: off_p, off_q, (L1<<4)|L2 with L1<=L2, diag
+  std::vector<int32_t> pairs;      // per pair: off_p, off_q, (L1<<4)|L2 with L1<=L2, row_pair_case
   std::vector<int32_t> out_ranks;  // graded ranks of the output row elements
 };
 bool build_row_table(int n, int D, RowImage& out);

@@ -148,7 +148,7 @@ __device__ __forceinline__ void conv_diag(const float* __restrict__ s, int off,
 }
 
 #define BERN_CC(L1, L2) \
-  case (L1 << 4) | L2: conv_rows<L1, L2, UP>(s, pr.x, pr.y, acc); break;
+  case row_pair_case(L1, L2): conv_rows<L1, L2, UP>(s, pr.x, pr.y, acc); break;
 #define BERN_CONV_ALL_CASES                                                                     \
   BERN_CC(1, 1) BERN_CC(1, 2) BERN_CC(1, 3) BERN_CC(1, 4) BERN_CC(1, 5) BERN_CC(1, 6)          \
   BERN_CC(1, 7) BERN_CC(1, 8) BERN_CC(1, 9) BERN_CC(2, 2) BERN_CC(2, 3) BERN_CC(2, 4)          \
@@ -218,7 +218,7 @@ __device__ void rows_range(const Tables& T, const ComposeArgs& A, const RowTable
       int4 pr = __ldg(R.pairs + hd.x);
       for (int k = hd.x; k < off_end; ++k) {
         const int4 nx = k + 1 < off_end ? __ldg(R.pairs + k + 1) : pr;   // prefetch
-        switch (pr.z) {
+        switch (pr.w) {
           BERN_CONV_ALL_CASES
           default: break;
         }

@@ -191,7 +191,7 @@ bool build_row_table(int n, int D, RowImage& out) {
         out.pairs.push_back(oi);
         out.pairs.push_back(oj);
         out.pairs.push_back((li << 4) | lj);
-        out.pairs.push_back(i == j ? 1 : 0);
+        out.pairs.push_back(row_pair_case(li, lj));
       }
     out.hdr.push_back((int32_t)(out.pairs.size() / 4));
     out.hdr.push_back((int32_t)out.out_ranks.size());
