@@ -515,6 +515,12 @@ int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
                                  P.fallback_d, l.d, P.cap, ord,
                                  ch.at<int32_t>(P.L[i + 1].off_order),
                                  ch.at<uint8_t>(l.off_deg), kind, coef, eps);
+    } else if (!trace) {
+      // stable items decided by their coefficient signs skip the enclosure
+      // (their lo/hi are read by nothing downstream; a trace reports the
+      // Bernstein bounds of every item, so traced runs enclose all of them)
+      e = launch_enclose_relu_screened(L, T, CS, B, l.h_out, l.order, P.budget, pre_up, pre_lo,
+                                       l.M_pre, pre_nt, lo, hi, deg, l.d, kind, coef, eps);
     } else {
       e = launch_enclose_relu(L, T, B, l.h_out, l.order, P.budget, pre_up, pre_lo, l.M_pre,
                               pre_nt, lo, hi, deg, l.d, kind, coef, eps);

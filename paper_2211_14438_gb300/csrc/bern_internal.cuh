@@ -180,6 +180,17 @@ cudaError_t launch_enclose_relu(const Launch& L, const Tables& T, int64_t n_boxe
                                 const float* pre_lo, int64_t ld, const int32_t* nterms,
                                 float* lo, float* hi, const uint8_t* degrees, int global_d,
                                 int8_t* kind, float* coef, float* eps);
+struct ComposeScratch;
+// The same after a stability screen: items that a coefficient-sign interval
+// shows stable get their case (and that interval as lo/hi) without the
+// enclosure; the rest go through it as an item list in S's first queue.
+cudaError_t launch_enclose_relu_screened(const Launch& L, const Tables& T,
+                                         const ComposeScratch& S, int64_t n_boxes, int h,
+                                         int order, int64_t budget, const float* pre_up,
+                                         const float* pre_lo, int64_t ld,
+                                         const int32_t* nterms, float* lo, float* hi,
+                                         const uint8_t* degrees, int global_d, int8_t* kind,
+                                         float* coef, float* eps);
 cudaError_t launch_relu_coeffs(const Launch& L, int64_t n_items, const float* lo,
                                const float* hi, const uint8_t* degrees, int global_d,
                                int8_t* kind, float* coef, float* eps);

@@ -142,6 +142,79 @@ cudaError_t launch_enclose_relu(const Launch& L, const Tables& T, int64_t n_boxe
                              hi, EncloseOpts{kind, coef, eps, degrees, global_d});
 }
 
+// Stability screen of a hidden layer's items before the enclosure.  On the box
+// every monomial t^K lies in [0,1], so a polynomial p lies in
+//   [c_0 + sum_{K>0} min(0, c_K),  c_0 + sum_{K>0} max(0, c_K)]
+// (summed rounding down, resp. up), an interval that contains the range of
+// its Bernstein coefficients (each is c_0 plus the other coefficients with
+// weights in [0,1]).  An item whose upper polynomial is <= 0 or whose lower
+// polynomial is >= 0 on this interval is stable (the cases of Sec. 5.1 Step
+// 2): it gets its case, the interval as lo/hi, and no enclosure or ReLU
+// coefficients (nothing downstream reads them).  The other items are appended
+// to `list` (one atomic per warp) for the enclosure.  One thread per item, so
+// a warp reads one coefficient of 32 neighbouring neurons at a time.
+__global__ void __launch_bounds__(256)
+k_stable_screen(int64_t n_items, int h, const float* __restrict__ pre_up,
+                const float* __restrict__ pre_lo, int64_t ld, const int32_t* __restrict__ nterms,
+                float* __restrict__ lo, float* __restrict__ hi, int8_t* __restrict__ kind,
+                int* __restrict__ list, int* __restrict__ count) {
+  const int lane = threadIdx.x & 31;
+  const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool need = false;
+  if (it < n_items) {
+    const int nt = nterms[it];
+    if (nt < 0 || nt > ld) {
+      need = true;                                  // the enclosure reports it
+    } else {
+      const int64_t b = it / h;
+      const int64_t base = (b * ld) * h + (it - b * h);
+      float l = 0.0f, u = 0.0f;
+      if (nt > 0) {
+        l = pre_lo[base];
+        u = pre_up[base];
+        for (int r = 1; r < nt; ++r) {
+          l = __fadd_rd(l, fminf(pre_lo[base + (int64_t)r * h], 0.0f));
+          u = __fadd_ru(u, fmaxf(pre_up[base + (int64_t)r * h], 0.0f));
+        }
+      }
+      if (!(isfinite(l) && isfinite(u)) || (u > 0.0f && l < 0.0f)) {
+        need = true;
+      } else {
+        kind[it] = u <= 0.0f ? 0 : 1;
+        lo[it] = l;
+        hi[it] = u;
+      }
+    }
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, need);
+  int at = 0;
+  if (lane == 0 && m) at = atomicAdd(count, __popc(m));
+  at = __shfl_sync(0xffffffffu, at, 0);
+  if (need) list[at + __popc(m & ((1u << lane) - 1u))] = (int)it;
+}
+
+cudaError_t launch_enclose_relu_screened(const Launch& L, const Tables& T,
+                                         const ComposeScratch& S, int64_t n_boxes, int h,
+                                         int order, int64_t budget, const float* pre_up,
+                                         const float* pre_lo, int64_t ld,
+                                         const int32_t* nterms, float* lo, float* hi,
+                                         const uint8_t* degrees, int global_d, int8_t* kind,
+                                         float* coef, float* eps) {
+  const int64_t n_items = n_boxes * h;
+  if (n_items == 0) return cudaSuccess;
+  if (n_items > S.qcap || n_items > 0x7fffffff) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(S.qcount, 0, sizeof(int), L.stream);
+  if (e != cudaSuccess) return e;
+  k_stable_screen<<<(unsigned)((n_items + 255) / 256), 256, 0, L.stream>>>(
+      n_items, h, pre_up, pre_lo, ld, nterms, lo, hi, kind, S.queue, S.qcount);
+  ++*L.launches;
+  EncloseOpts o{kind, coef, eps, degrees, global_d};
+  o.list = S.queue;
+  o.count = S.qcount;
+  return launch_enclose_impl(L, T, n_boxes, h, order, budget, pre_up, pre_lo, ld, nterms, lo,
+                             hi, o);
+}
+
 // ------------------------------------------------------------------ per-box orders
 struct OrderKeys {
   int8_t key[kMaxTableDegree + 1];   // order value -> list index, -1 if absent
