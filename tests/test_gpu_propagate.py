@@ -316,3 +316,20 @@ def test_autotune_on_off_identical(ctx):
     c = run_gpu(ctx, w.net, w.boxes)
     for k in ("lo", "hi", "n_terms", "coef"):
         assert np.array_equal(a[k], b[k]) and np.array_equal(b[k], c[k]), k
+
+
+def test_stability_screen_matches_full_enclosure(ctx):
+    """Untraced plain runs decide the hidden items whose coefficient signs
+    show them stable without enclosing them; traced runs enclose every item.
+    The outputs agree: bit for bit on (nearly) every box, and within the
+    parity tolerance where a Bernstein bound within rounding of 0 takes the
+    other ReLU case."""
+    w = wl.config3(n_random=64, cells=4)
+    a = run_gpu(ctx, w.net, w.boxes)
+    b = run_gpu(ctx, w.net, w.boxes, trace=True)
+    same = np.all(a["lo"] == b["lo"], axis=1) & np.all(a["hi"] == b["hi"], axis=1)
+    assert same.mean() >= 0.95
+    assert np.all(np.abs(a["lo"] - b["lo"]) <= TOL * (1 + np.abs(b["lo"])))
+    assert np.all(np.abs(a["hi"] - b["hi"]) <= TOL * (1 + np.abs(b["hi"])))
+    # the traced run's Bernstein bounds confirm every hidden case the screen decided
+    assert np.array_equal(a["n_terms"][same], b["n_terms"][same])
