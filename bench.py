@@ -636,6 +636,81 @@ def run_reference(args, rank, world):
     }
 
 
+# ------------------------------------------------- paper-shaped sweeps (context)
+def run_paper_sweeps(args):
+    """Context runs on the shapes of the paper's ablations (Figs. 4-7): weights
+    and biases U(-5,5) (seeded here, unseeded in the paper), box [-1,1]^n,
+    degree cap 64.  Per setting: the latency of one box per call (the paper's
+    unit: graph replay, CUDA events, median of 20 calls after warm-up), the
+    throughput of 4096 random sub-boxes per call (sides U(0.05,0.5)), and the
+    mean over the box of upper minus lower polynomial (Vol_relative).  Not the
+    headline metric; one JSON line."""
+    import torch
+    from paper_2211_14438_gb300 import bern
+    from paper_2211_14438_gb300 import workloads as wl
+    dev = torch.device("cuda:0")
+    ctx = bern.Context(0, stream=torch.cuda.current_stream(dev))
+    settings = [("fig4", 2, [20, 20], L) for L in (2, 3, 4, 5, 6)]
+    settings += [("fig5", n, [20, 20], 2) for n in range(2, 9)]
+    settings += [("fig6", 2, [ne, ne], 2) for ne in (10, 20, 40, 60, 80, 100)]
+    settings += [("fig7", 2, [20] * k, 2) for k in range(1, 6)]
+    cap = 64
+    rows = []
+    for si, (fig, n, hidden, L) in enumerate(settings):
+        net = wl.paper_net(n, hidden, seed=500 + si)
+        Wd = [torch.from_numpy(x).to(dev) for x in net.W]
+        bd = [torch.from_numpy(x).to(dev) for x in net.b]
+        ct = bern.max_output_terms(net.widths, L, cap)
+
+        def timed(boxes_d, reps):
+            B = int(boxes_d.shape[0])
+            out = {"lo": torch.empty(B, 1, device=dev), "hi": torch.empty(B, 1, device=dev),
+                   "n_terms": torch.empty(B, 1, 2, device=dev, dtype=torch.int32),
+                   "coef": torch.empty(B, 1, 2, ct, device=dev), "keys": None}
+            for _ in range(3):
+                ctx.propagate(net.widths, Wd, bd, boxes_d, degree=L, cap=cap, cap_terms=ct,
+                              out=out, sync=False)
+            if ctx.sync() != 0:
+                raise RuntimeError("propagate failed on %s %s" % (fig, net.widths))
+            ms = []
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(ctx.stream)
+                ctx.propagate(net.widths, Wd, bd, boxes_d, degree=L, cap=cap, cap_terms=ct,
+                              out=out, sync=False)
+                e1.record(ctx.stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            if ctx.sync() != 0:
+                raise RuntimeError("propagate failed on %s %s" % (fig, net.widths))
+            return float(np.median(ms)), out
+
+        one = torch.from_numpy(wl.box_array([-1.0] * n, [1.0] * n)[None]).to(dev)
+        t1, out = timed(one, 20)
+        nt = int(out["n_terms"][0, 0, 0])
+        D = 0
+        while bern.num_monomials(n, D) < nt:
+            D += 1
+        ex = bern.monomials(n, D)[:nt].astype(np.float64)
+        cf = out["coef"][0, 0].cpu().numpy().astype(np.float64)
+        vol = float(((cf[0, :nt] - cf[1, :nt]) / np.prod(ex + 1.0, axis=1)).sum())
+        rng = np.random.default_rng(900 + si)
+        c = rng.uniform(-1, 1, (4096, n))
+        sd = rng.uniform(0.05, 0.5, (4096, n))
+        many = torch.from_numpy(wl.box_array(np.clip(c - sd / 2, -1, 1),
+                                             np.clip(c + sd / 2, -1, 1))).to(dev)
+        tb, _ = timed(many, 5)
+        rows.append({"setting": fig, "widths": net.widths, "relu_order": L,
+                     "one_box_ms": round(t1, 4), "boxes_per_s_4096": round(4096 / (tb / 1e3), 1),
+                     "vol_relative": round(vol, 3),
+                     "lo": round(float(out["lo"][0, 0]), 4), "hi": round(float(out["hi"][0, 0]), 4)})
+    return {"metric": "paper-shaped sweeps (context, not the headline metric)",
+            "data": "synthetic: paper ablation shapes, weights and biases U(-5,5) seeded 500+i, "
+                    "box [-1,1]^n; throughput on 4096 random sub-boxes",
+            "degree_cap": cap, "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -650,7 +725,12 @@ def main():
                     help="skip training and timing the learned-degree form")
     ap.add_argument("--n-boxes", type=int, default=0,
                     help="use N evenly strided boxes of the workload (small cases for ncu)")
+    ap.add_argument("--paper-sweeps", action="store_true",
+                    help="instead of the benchmark, time the paper's ablation shapes (context)")
     args = ap.parse_args()
+    if args.paper_sweeps:
+        print(json.dumps(run_paper_sweeps(args)))
+        return
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
