@@ -232,11 +232,7 @@ __device__ void rows_range(const Tables& T, const ComposeArgs& A, const RowTable
         default: break;
       }
     }
-    // the row's output ranks, all loads issued together (predicated)
-    const int* __restrict__ rkp = R.out_ranks + hd.z;
-    int rk[2 * kRowLen - 1];
-#pragma unroll
-    for (int c = 0; c < 2 * kRowLen - 1; ++c) rk[c] = c < Lout ? __ldg(rkp + c) : 0;
+    const int* __restrict__ rk = R.out_ranks + hd.z;   // the row's output ranks
 #pragma unroll
     for (int c = 0; c < 2 * kRowLen - 1; ++c) {
       if (c >= Lout) break;
@@ -245,8 +241,8 @@ __device__ void rows_range(const Tables& T, const ComposeArgs& A, const RowTable
       const float v = dfma<UP>(a2, sq, UP ? __fmul_ru(a1, lin) : __fmul_rd(a1, lin));
       if (row == 0 && c == 0) {
         *c0_out = v;                      // the constant term is finished by the caller
-      } else if (no_trunc || rk[c] < Mout) {
-        if (valid) Q[(int64_t)rk[c] * h] = v;
+      } else if (no_trunc || __ldg(rk + c) < Mout) {
+        if (valid) Q[(int64_t)__ldg(rk + c) * h] = v;
       } else {
         rem = UP ? __fadd_ru(rem, fmaxf(v, 0.0f)) : __fadd_rd(rem, fminf(v, 0.0f));
       }
