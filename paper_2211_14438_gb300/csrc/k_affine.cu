@@ -165,22 +165,23 @@ k_affine(int h_out, int h_in, const float* __restrict__ W, const float* __restri
 // radius FMA itself.  The staging issues kWBatch loads of each bound per
 // thread before converting any.  A warp covers 16 rows of the tile and skips
 // the tile when all of them are at or past the box's term count.
-constexpr int kWRows = 64;
 constexpr int kWThreads = 128;
 constexpr int kWBatch = 8;
 
-__global__ void __launch_bounds__(kWThreads, 4)
+template <int TR, int MINB>
+__global__ void __launch_bounds__(kWThreads, MINB)
 k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
               const float* __restrict__ bias, const float* __restrict__ in_up,
               const float* __restrict__ in_lo, int64_t in_ld,
               const int32_t* __restrict__ in_nterms, float* __restrict__ out_up,
               float* __restrict__ out_lo, int64_t out_ld, int32_t* __restrict__ out_nterms,
               int* status) {
+  constexpr int ROWS = 16 * TR;                      // rows per tile
   extern __shared__ float4 smem4[];
   const int hp = (h_out + 63) & ~63;                 // neurons padded to 64
   float* sW = reinterpret_cast<float*>(smem4);       // [h_in][hp]
-  float2* sCR = reinterpret_cast<float2*>(sW + (size_t)h_in * hp);   // [kWRows][h_in + 1]
-  int* sN = reinterpret_cast<int*>(sCR + (size_t)kWRows * (h_in + 1));   // [h_in]
+  float2* sCR = reinterpret_cast<float2*>(sW + (size_t)h_in * hp);   // [ROWS][h_in + 1]
+  int* sN = reinterpret_cast<int*>(sCR + (size_t)ROWS * (h_in + 1));   // [h_in]
   __shared__ int sMax;
   const int tid = threadIdx.x, warp = tid >> 5;
   for (int idx = tid; idx < h_in * hp; idx += kWThreads) {
@@ -217,17 +218,17 @@ k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
     for (int m = tid; m < h_out; m += kWThreads) out_nterms[b * h_out + m] = M;
     const float* gU = in_up + (b * in_ld) * h_in;
     const float* gL = in_lo + (b * in_ld) * h_in;
-    for (int r0 = 0; r0 < M; r0 += kWRows) {
+    for (int r0 = 0; r0 < M; r0 += ROWS) {
       __syncthreads();                               // the previous tile is consumed
       // element idx = rr * h_in + j of the tile; (rr, j) advance by
       // (step_r, step_j) per kWThreads elements
       int rr = tid / h_in, j = tid - (tid / h_in) * h_in;
-      for (int idx = tid; idx < kWRows * h_in; idx += kWThreads * kWBatch) {
+      for (int idx = tid; idx < ROWS * h_in; idx += kWThreads * kWBatch) {
         float u[kWBatch], l[kWBatch];
         int at[kWBatch];
 #pragma unroll
         for (int q = 0; q < kWBatch; ++q) {
-          const bool in = idx + q * kWThreads < kWRows * h_in;
+          const bool in = idx + q * kWThreads < ROWS * h_in;
           const int r = r0 + rr;
           const bool live = in && r < sN[j];         // sN[j] <= M <= in_ld
           u[q] = live ? gU[(int64_t)r * h_in + j] : 0.0f;
@@ -248,32 +249,32 @@ k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
         }
       }
       __syncthreads();
-      if (r0 + warp * 16 >= M) continue;             // warp-uniform; no barrier follows
+      if (r0 + warp * 4 * TR >= M) continue;         // warp-uniform; no barrier follows
       for (int m0 = 0; m0 < h_out; m0 += 64) {
-        float uc[4][8], lc[4][8], rad[4][8];
+        float uc[TR][8], lc[TR][8], rad[TR][8];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < TR; ++k)
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            const int m = m0 + (i < 4 ? 4 * tm + i : 28 + 4 * tm + i), r = r0 + tr * 4 + k;
+            const int m = m0 + (i < 4 ? 4 * tm + i : 28 + 4 * tm + i), r = r0 + tr * TR + k;
             const float b0 = (r == 0 && m < h_out) ? bias[m] : 0.0f;
             uc[k][i] = b0;
             lc[k][i] = b0;
             rad[k][i] = 0.0f;
           }
         const float* pw = sW + m0 + tm * 4;
-        const float2* pcr = sCR + (tr * 4) * ldx;
+        const float2* pcr = sCR + (tr * TR) * ldx;
 #pragma unroll 2
         for (int j = 0; j < h_in; ++j) {
-          float2 cr[4];
+          float2 cr[TR];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) cr[k] = pcr[k * ldx + j];
+          for (int k = 0; k < TR; ++k) cr[k] = pcr[k * ldx + j];
 #pragma unroll
           for (int half = 0; half < 2; ++half) {
             const float4 w4 = *reinterpret_cast<const float4*>(pw + (size_t)j * hp + 32 * half);
             const float w[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < TR; ++k)
 #pragma unroll
               for (int i = 0; i < 4; ++i) {
                 const int ii = 4 * half + i;
@@ -284,8 +285,8 @@ k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
           }
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int r = r0 + tr * 4 + k;
+        for (int k = 0; k < TR; ++k) {
+          const int r = r0 + tr * TR + k;
           if (r >= M) continue;
           float vu[8], vl[8];
 #pragma unroll
@@ -476,9 +477,9 @@ static size_t short_smem(int h_out, int h_in) {
          (size_t)4 * h_in * sizeof(int);
 }
 
-static size_t wide_smem(int h_out, int h_in) {
+static size_t wide_smem(int h_out, int h_in, int rows) {
   const size_t hp = (size_t)((h_out + 63) & ~63);
-  return hp * h_in * sizeof(float) + (size_t)kWRows * (h_in + 1) * sizeof(float2) +
+  return hp * h_in * sizeof(float) + (size_t)rows * (h_in + 1) * sizeof(float2) +
          (size_t)h_in * sizeof(int);
 }
 
@@ -815,24 +816,28 @@ cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
     return cudaErrorInvalidValue;
   const bool few_rows = std::min(in_ld, out_ld) <= 16;     // short polynomials: short tiles
   if (h_out >= 32 && !few_rows) {
-    // wide layers: autotuned between the persistent register-blocked kernel
-    // (0, when its weights fit shared memory) and 64 x 32 tiles (1)
+    // wide layers: autotuned among the persistent register-blocked kernel with
+    // 4-row (0) or 2-row (2) thread tiles, when its weights fit shared memory,
+    // and 64 x 32 block tiles (1)
     const std::string key = "affine/" + std::to_string(h_out) + "/" + std::to_string(h_in) +
                             "/" + std::to_string(in_ld) + "/" + std::to_string(n_boxes);
-    const size_t wsmem = wide_smem(h_out, h_in);
-    const bool wide_ok = wsmem <= 200 * 1024;
+    const bool wide_ok = wide_smem(h_out, h_in, 64) <= 200 * 1024;
     int v = tune_variant(L, "affine", key, wide_ok ? 0 : 1);
-    if (v == 0 && !wide_ok) v = 1;
+    if (v != 1 && !wide_ok) v = 1;
     TuneTimer tt;
     tune_begin(L, "affine", tt);
     cudaError_t e;
-    if (v == 0) {
-      e = cudaFuncSetAttribute(k_affine_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)wsmem);
+    if (v == 0 || v == 2) {
+      const int rows = v == 0 ? 64 : 32;
+      const size_t wsmem = wide_smem(h_out, h_in, rows);
+      auto kern = v == 0 ? k_affine_wide<4, 4> : k_affine_wide<2, 6>;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
       if (e != cudaSuccess) return e;
-      const int per_sm = wsmem <= 54 * 1024 ? 4 : (wsmem <= 72 * 1024 ? 3 : (wsmem <= 110 * 1024 ? 2 : 1));
+      const int max_sm = v == 0 ? 4 : 6;
+      int per_sm = (int)std::min<size_t>(max_sm, (220 * 1024) / (wsmem + 1024));
+      if (per_sm < 1) per_sm = 1;
       const int64_t blocks = std::min<int64_t>(n_boxes, 152 * per_sm);
-      k_affine_wide<<<(unsigned)blocks, kWThreads, wsmem, L.stream>>>(
+      kern<<<(unsigned)blocks, kWThreads, wsmem, L.stream>>>(
           n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld, in_nterms, out_up, out_lo, out_ld,
           out_nterms, L.status);
       ++*L.launches;
