@@ -163,18 +163,18 @@ int bern_set_pointer_mode(bern_ctx* ctx, int mode);
 /* Autotuning (on by default): the first bern_propagate of each plan shape
  * (network widths, plan, batch size) times every variant of the tunable
  * kernels (the wide-layer affine kernel: persistent register-blocked with
- * 4- or 2-row thread tiles, or 64x32 block tiles; the Bernstein enclosure: 8,
- * 4 or 2 items per block) on its first
+ * 4-, 2- or 1-row thread tiles, or 64x32 block tiles; the Bernstein
+ * enclosure: 8, 4 or 2 items per block) on its first
  * chunk and keeps the fastest per shape.  All variants compute identical
  * results.  enable = 0 uses the built-in defaults. */
 int bern_set_autotune(bern_ctx* ctx, int enable);
 
 /* Force one variant of a tunable kernel family for every later launch on
  * this context (a setting for tests and tuning; the paper has no
- * counterpart).  kind: "affine" (variants 0-2: persistent register-blocked
- * 8x4 thread tiles, 64x32 block tiles, persistent register-blocked 8x2
- * thread tiles; 0 and 2 fall back to 1 where the layer's weights do not fit
- * shared memory) or "enclose"
+ * counterpart).  kind: "affine" (variants 0-3: persistent register-blocked
+ * 8x4 thread tiles, 64x32 block tiles, persistent register-blocked 8x2 and
+ * 8x1 thread tiles; 0, 2 and 3 fall back to 1 where the layer's weights do
+ * not fit shared memory) or "enclose"
  * (variants 0-2: 8, 4 or 2 items per block).  variant = -1 clears the force.
  * Drops captured graphs.  Returns BERN_E_INVALID for an unknown kind or a
  * variant out of range. */

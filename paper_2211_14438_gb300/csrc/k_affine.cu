@@ -817,23 +817,23 @@ cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
   const bool few_rows = std::min(in_ld, out_ld) <= 16;     // short polynomials: short tiles
   if (h_out >= 32 && !few_rows) {
     // wide layers: autotuned among the persistent register-blocked kernel with
-    // 4-row (0) or 2-row (2) thread tiles, when its weights fit shared memory,
-    // and 64 x 32 block tiles (1)
+    // 4-row (0), 2-row (2, the default) or 1-row (3) thread tiles, when its
+    // weights fit shared memory, and 64 x 32 block tiles (1)
     const std::string key = "affine/" + std::to_string(h_out) + "/" + std::to_string(h_in) +
                             "/" + std::to_string(in_ld) + "/" + std::to_string(n_boxes);
     const bool wide_ok = wide_smem(h_out, h_in, 64) <= 200 * 1024;
-    int v = tune_variant(L, "affine", key, wide_ok ? 0 : 1);
+    int v = tune_variant(L, "affine", key, wide_ok ? 2 : 1);
     if (v != 1 && !wide_ok) v = 1;
     TuneTimer tt;
     tune_begin(L, "affine", tt);
     cudaError_t e;
-    if (v == 0 || v == 2) {
-      const int rows = v == 0 ? 64 : 32;
+    if (v == 0 || v == 2 || v == 3) {
+      const int rows = v == 0 ? 64 : (v == 2 ? 32 : 16);
       const size_t wsmem = wide_smem(h_out, h_in, rows);
-      auto kern = v == 0 ? k_affine_wide<4, 4> : k_affine_wide<2, 6>;
+      auto kern = v == 0 ? k_affine_wide<4, 4> : (v == 2 ? k_affine_wide<2, 6> : k_affine_wide<1, 8>);
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
       if (e != cudaSuccess) return e;
-      const int max_sm = v == 0 ? 4 : 6;
+      const int max_sm = v == 0 ? 4 : (v == 2 ? 6 : 8);
       int per_sm = (int)std::min<size_t>(max_sm, (220 * 1024) / (wsmem + 1024));
       if (per_sm < 1) per_sm = 1;
       const int64_t blocks = std::min<int64_t>(n_boxes, 152 * per_sm);

@@ -275,7 +275,7 @@ def test_output_keys_are_graded_monomials(ctx):
                                         ([3, 40, 72, 48, 4], 5)])
 def test_forced_variants_identical(ctx, widths, seed):
     """Every variant of the wide-layer affine kernel (persistent
-    register-blocked 8x4 and 8x2 thread tiles, 64x32 block tiles) and of the
+    register-blocked 8x4, 8x2 and 8x1 thread tiles, 64x32 block tiles) and of the
     enclosure (8, 4, 2 items per block) gives the same bits, on layers 64 and
     100 wide and on widths that are not multiples of 64."""
     net = wl.make_net(widths, seed)
@@ -286,7 +286,7 @@ def test_forced_variants_identical(ctx, widths, seed):
     boxes = wl.box_array(c - s / 2, c + s / 2)
     ref = None
     try:
-        for kind, nv in (("affine", 3), ("enclose", 3)):
+        for kind, nv in (("affine", 4), ("enclose", 3)):
             for v in range(nv):
                 ctx.force_variant(kind, v)
                 g = run_gpu(ctx, net, boxes)
