@@ -315,7 +315,7 @@ def run_ours(args, rank, world, local_rank, dist):
     build.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    w = wl.config3()
+    w = wl.batch_3in()
     if args.n_boxes:
         # an evenly strided subset keeps the mix of grid cells and random boxes
         pick = np.linspace(0, len(w.boxes) - 1, args.n_boxes).astype(int)
@@ -514,29 +514,29 @@ def run_ours(args, rank, world, local_rank, dist):
                         % info["max_per_layer"],
             }
 
-        learned = learned_entry(w.net, wl.config3_training_boxes(800), ms_step,
+        learned = learned_entry(w.net, wl.batch_3in_training_boxes(800), ms_step,
                                 float(np.mean(hi - lo)), boxes_d, Wd, bd, cap_terms, o)
         learned["workload"] = "the benchmark workload above"
         if not args.n_boxes:
-            w4 = wl.config4()
+            w4 = wl.batch_6in()
             Wd4 = [torch.from_numpy(x).to(dev) for x in w4.net.W]
             bd4 = [torch.from_numpy(x).to(dev) for x in w4.net.b]
             bx4 = torch.from_numpy(w4.boxes).to(dev)
             ct4 = bern.max_output_terms(w4.net.widths, 4, 16)
             ms4, width4 = timed(w4.net, Wd4, bd4, bx4, 2, ct4, w4.net.n_out)
-            learned4 = learned_entry(w4.net, wl.config4_training_boxes(700), ms4, width4, bx4,
+            learned4 = learned_entry(w4.net, wl.batch_6in_training_boxes(700), ms4, width4, bx4,
                                      Wd4, bd4, ct4, w4.net.n_out)
-            learned4["workload"] = ("config4 learned-degree shape: MLP [6,100,100,100,2] seed 3, "
+            learned4["workload"] = ("learned-degree shape: MLP [6,100,100,100,2] seed 3, "
                                     "2048 boxes with sides U(0.05,0.5) in [-1,1]^6, cap 16; "
                                     "plain = order 2 everywhere")
 
-    # ---- branch-and-bound refinement of the config-5 root box (wall clock,
+    # ---- branch-and-bound refinement of the [6,64x4,1] root box [-1,1]^6 (wall clock,
     # host work included), plain orders against the learned form
     bnb5 = None
     if not args.no_learned and not args.no_bnb and not args.n_boxes and world == 1:
         from paper_2211_14438_gb300 import bnb
         from paper_2211_14438_gb300 import learned as lm
-        w5 = wl.config5()
+        w5 = wl.bnb_root_6in()
         root5 = w5.boxes[0]
         rng5 = np.random.default_rng(1005)
         c5 = rng5.uniform(-1, 1, (400, 6))
@@ -545,7 +545,7 @@ def run_ours(args, rank, world, local_rank, dist):
         t0 = time.time()
         info5 = lm.fit(ctx, w5.net.widths, w5.net.W, w5.net.b, tr5, cap=16)
         train5 = time.time() - t0
-        bnb5 = {"workload": "config5 network [6,64x4,1] seed 4, root [-1,1]^6, best-first "
+        bnb5 = {"workload": "branch-and-bound network [6,64x4,1] seed 4, root [-1,1]^6, best-first "
                             "refinement of output 0 in rounds of 1024 splits (widest side) "
                             "until 4096 leaves; boxes/s counts every bounded child, wall "
                             "clock with host work",
@@ -580,7 +580,7 @@ def run_ours(args, rank, world, local_rank, dist):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded networks and boxes)",
-        "config": {"workload": "config3 batched plain method: MLP [3,64,64,64,64,1] seed 2, "
+        "config": {"workload": "batched plain method: MLP [3,64,64,64,64,1] seed 2, "
                                "5120 boxes (16^3 grid of [-1,1]^3 + 1024 random, sides "
                                "U(0.01,0.5)), ReLU order 2, cap 16" +
                                (" (%d strided boxes only)" % B if args.n_boxes else ""),
@@ -593,7 +593,7 @@ def run_ours(args, rank, world, local_rank, dist):
         "roofline": roof, "kernels": kernels,
         "kernel_pass_ms_per_step": round(total_kernel_ms, 4),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-        "learned": learned, "learned_config4": learned4, "bnb_config5": bnb5,
+        "learned": learned, "learned_6in": learned4, "bnb_6in": bnb5,
         "clocks": clocks,
     }
     return line
@@ -606,7 +606,7 @@ def run_reference(args, rank, world):
         return None
     cores = min(os.cpu_count() or 1, 16)
     pool = mp.get_context("spawn").Pool(cores)
-    w = wl.config3()
+    w = wl.batch_3in()
     B = len(w.boxes)
     rng = np.random.default_rng(0)
     for _ in range(args.warmup):
@@ -625,7 +625,7 @@ def run_reference(args, rank, world):
         "ms_per_step": round(1e3 * total_wall / args.steps, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded networks and boxes)",
-        "config": {"workload": "config3 batched plain method: MLP [3,64,64,64,64,1] seed 2, "
+        "config": {"workload": "batched plain method: MLP [3,64,64,64,64,1] seed 2, "
                                "5120 boxes, ReLU order 2, cap 16",
                    "sample_per_step": "%d random boxes of the 5120, one per process" % cores},
         "cpu_baseline": {"value": round(value, 4), "unit": "boxes/s", "cores": cores,
@@ -720,7 +720,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-bnb", action="store_true",
-                    help="skip the branch-and-bound refinement of the config-5 root box")
+                    help="skip the branch-and-bound refinement of the [6,64x4,1] root box [-1,1]^6")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip training and timing the learned-degree form")
     ap.add_argument("--n-boxes", type=int, default=0,

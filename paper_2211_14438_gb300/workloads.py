@@ -116,20 +116,20 @@ def random_boxes(rng: np.random.Generator, count: int, n: int, side_lo: float,
 # experiments (Sec. 6) widened to batches of sub-boxes.
 # --------------------------------------------------------------------------
 
-def config1() -> Workload:
+def single_box_2in() -> Workload:
     """[2,20,20,1], seed 0, one box [-1,1]^2, degree 2 (shape of Fig. 4)."""
     net = make_net([2, 20, 20, 1], seed=0)
     return Workload("mlp2-20-20-1_box1_d2", net, box_array([-1, -1], [1, 1])[None], degree=2)
 
 
-def config2() -> Workload:
+def single_box_4in() -> Workload:
     """[4,50,50,50,2], seed 1, one box [-0.5,0.5]^4, degree 2."""
     net = make_net([4, 50, 50, 50, 2], seed=1)
     return Workload("mlp4-50x3-2_box1_d2", net,
                     box_array([-0.5] * 4, [0.5] * 4)[None], degree=2)
 
 
-def config3(n_random: int = 1024, cells: int = 16) -> Workload:
+def batch_3in(n_random: int = 1024, cells: int = 16) -> Workload:
     """[3,64,64,64,64,1], seed 2: the cells^3 grid over [-1,1]^3 plus n_random
     boxes with centres U(-1,1)^3 and sides U(0.01,0.5), clipped."""
     rng = np.random.default_rng(2)
@@ -140,8 +140,8 @@ def config3(n_random: int = 1024, cells: int = 16) -> Workload:
                     np.concatenate([g, r], 0), degree=2)
 
 
-def config3_training_boxes(count: int = 800, seed: int = 1002) -> np.ndarray:
-    """Training boxes for the learned component on the config-3 network, drawn
+def batch_3in_training_boxes(count: int = 800, seed: int = 1002) -> np.ndarray:
+    """Training boxes for the learned component on the [3,64x4,1] network, drawn
     like the benchmark's boxes (4/5 grid-cell sized, 1/5 random sized) but from
     their own seed: cells of the 16^3 grid's size (side 0.125) at random
     centres, and boxes with sides U(0.01, 0.5); all clipped to [-1,1]^3."""
@@ -152,7 +152,7 @@ def config3_training_boxes(count: int = 800, seed: int = 1002) -> np.ndarray:
     return np.concatenate([cells, random_boxes(rng, count - k, 3, 0.01, 0.5)], 0)
 
 
-def config4(n_boxes: int = 2048) -> Workload:
+def batch_6in(n_boxes: int = 2048) -> Workload:
     """[6,100,100,100,2], seed 3, random sub-boxes of [-1,1]^6 with sides
     U(0.05,0.5); degrees in {1..4} with total-degree cap 16."""
     rng = np.random.default_rng(3)
@@ -162,14 +162,14 @@ def config4(n_boxes: int = 2048) -> Workload:
                     degree_cap=16, prune_tau=1e-7)
 
 
-def config4_training_boxes(count: int = 700, seed: int = 1003) -> np.ndarray:
-    """Training boxes for the learned component on the config-4 network:
+def batch_6in_training_boxes(count: int = 700, seed: int = 1003) -> np.ndarray:
+    """Training boxes for the learned component on the [6,100x3,2] network:
     random sub-boxes of [-1,1]^6 with sides U(0.05, 0.5), like the workload's,
     from their own seed (700 boxes x 300 hidden neurons = 210,000 samples)."""
     return random_boxes(np.random.default_rng(seed), count, 6, 0.05, 0.5)
 
 
-def config5() -> Workload:
+def bnb_root_6in() -> Workload:
     """[6,64,64,64,64,1], seed 4, root box [-1,1]^6 (branch-and-bound root)."""
     net = make_net([6, 64, 64, 64, 64, 1], seed=4)
     return Workload("mlp6-64x4-1_root", net, box_array([-1] * 6, [1] * 6)[None],
@@ -181,5 +181,5 @@ def paper_net(n: int, hidden: List[int], seed: int) -> Net:
     return make_net([n] + list(hidden) + [1], seed=seed, dist="paper")
 
 
-WORKLOADS = {"config1": config1, "config2": config2, "config3": config3,
-             "config4": config4, "config5": config5}
+WORKLOADS = {"single_box_2in": single_box_2in, "single_box_4in": single_box_4in, "batch_3in": batch_3in,
+             "batch_6in": batch_6in, "bnb_root_6in": bnb_root_6in}

@@ -57,8 +57,8 @@ def check_all(ctx, net, boxes, degree, cap=16, tau=0.0, mc=20_000, seed=0):
 
 
 @pytest.mark.parametrize("d", [3, 4, 5])
-def test_config1_orders_above_two(ctx, d):
-    w = wl.config1()
+def test_single_box_2in_orders_above_two(ctx, d):
+    w = wl.single_box_2in()
     check_all(ctx, w.net, w.boxes, d, mc=200_000, seed=d)
 
 
@@ -86,11 +86,11 @@ def test_orders_above_8_sound(ctx, widths, d, cap, seed):
 
 
 @pytest.mark.parametrize("d", [8, 16])
-def test_config1_high_orders_sound(ctx, d):
+def test_single_box_2in_high_orders_sound(ctx, d):
     """Two hidden layers at orders 8 and 16 with cap 16: the truncated
     power-form remainders make the bounds very loose in both float32 and
     float64 (parity is not meaningful there), but they stay sound."""
-    w = wl.config1()
+    w = wl.single_box_2in()
     g = run_gpu(ctx, w.net, w.boxes, degree=d, cap=16)
     assert np.all(np.isfinite(g["lo"])) and np.all(g["lo"] <= g["hi"])
     assert mc_check(g, 0, w.net, w.boxes[0], 200_000, np.random.default_rng(d)) == 0
@@ -133,7 +133,7 @@ def test_pruning(ctx, tau, degree):
 def test_pruning_shrinks_terms_on_small_boxes(ctx):
     """On small boxes the high-degree terms are tiny and pruning drops whole
     degrees: the term count falls below the unpruned graded prefix."""
-    w = wl.config3()
+    w = wl.batch_3in()
     idx = np.arange(0, 4096, 512)
     g0 = run_gpu(ctx, w.net, w.boxes[idx])
     g = run_gpu(ctx, w.net, w.boxes[idx], tau=1e-4)
@@ -209,7 +209,7 @@ def test_six_inputs_cap16_pruned(ctx):
     74613-term outputs) run in the global-workspace Horner path.  Bounds are
     sound, term counts never exceed the unpruned ones, and the pruned bounds
     stay close to the unpruned ones on small boxes."""
-    w = wl.config5()
+    w = wl.bnb_root_6in()
     rng = np.random.default_rng(101)
     c = rng.uniform(-0.8, 0.8, (3, 6))
     boxes = wl.box_array(c - 0.06, c + 0.06)

@@ -70,7 +70,7 @@ def test_learned_plan_matches_oracle(ctx, widths, seed, tseed):
 @pytest.mark.parametrize("cls", [0, 1, 2, 3])
 def test_sure_proposal_equals_global_plan(ctx, cls):
     """An MLP that always proposes order cls+1 gives exactly the global plan."""
-    w = wl.config3(n_random=8, cells=2)
+    w = wl.batch_3in(n_random=8, cells=2)
     m = bern.Mlp(torch, F, C, const_theta(cls))
     a = run_gpu(ctx, w.net, w.boxes, degree=bern.Learned(m), cap=16)
     b = run_gpu(ctx, w.net, w.boxes, degree=cls + 1, cap=16)
@@ -82,7 +82,7 @@ def test_sure_proposal_equals_global_plan(ctx, cls):
 
 
 def test_low_confidence_falls_back_to_plain(ctx):
-    w = wl.config3(n_random=8, cells=2)
+    w = wl.batch_3in(n_random=8, cells=2)
     m = bern.Mlp(torch, F, C, random_theta(5))
     a = run_gpu(ctx, w.net, w.boxes, degree=bern.Learned(m, min_conf=1.01, fallback=2))
     b = run_gpu(ctx, w.net, w.boxes, degree=2)
@@ -92,7 +92,7 @@ def test_low_confidence_falls_back_to_plain(ctx):
 
 def test_any_proposal_is_sound(ctx):
     """Random MLPs propose arbitrary mixed orders: the bounds stay sound."""
-    w = wl.config3(n_random=24, cells=2)
+    w = wl.batch_3in(n_random=24, cells=2)
     rng = np.random.default_rng(7)
     for seed in (11, 12):
         m = bern.Mlp(torch, F, C, random_theta(seed, 2.0))
@@ -109,10 +109,10 @@ def test_trained_mlp_gains_over_plain(ctx):
     held-out generalisation) and much less polynomial work (the term counts
     every hidden layer and the output carry)."""
     from paper_2211_14438_gb300 import learned as lm
-    w = wl.config3()
+    w = wl.batch_3in()
     net = w.net
     held = w.boxes[np.r_[0:4096:8, 4096:5120:2]]         # 512 grid cells + 512 random
-    info = lm.fit(ctx, net.widths, net.W, net.b, wl.config3_training_boxes(800), cap=16)
+    info = lm.fit(ctx, net.widths, net.W, net.b, wl.batch_3in_training_boxes(800), cap=16)
     assert info["n_samples"] >= 200_000
     plan = info["plan"]
     gp = run_gpu(ctx, net, held, degree=2, trace=True)
@@ -133,7 +133,7 @@ def test_per_layer_caps_clamp_proposals(ctx):
     """With per-layer caps the proposals are clamped: an MLP sure of order 4
     under caps of 2 everywhere gives exactly the order-2 plan, and caps
     (4, 1, 1, 1) give the per-layer plan (4, 1, 1, 1)."""
-    w = wl.config3(n_random=8, cells=2)
+    w = wl.batch_3in(n_random=8, cells=2)
     m = bern.Mlp(torch, F, C, const_theta(3))
     a = run_gpu(ctx, w.net, w.boxes, degree=bern.Learned(m, max_per_layer=[2, 2, 2, 2]))
     b = run_gpu(ctx, w.net, w.boxes, degree=2)

@@ -97,8 +97,8 @@ def check_box(net, box, g, cx, bi, rng, n_mc=4000):
                 assert np.all(nn[:, j] >= vals - tol)
 
 
-def test_config3_boxes(ctx):
-    w = wl.config3(n_random=8, cells=2)
+def test_batch_3in_boxes(ctx):
+    w = wl.batch_3in(n_random=8, cells=2)
     g = run_gpu(ctx, w.net, w.boxes)
     cx = convert(ctx, w.boxes, g)
     rng = np.random.default_rng(3)
@@ -106,8 +106,8 @@ def test_config3_boxes(ctx):
         check_box(w.net, w.boxes[bi], g, cx, bi, rng)
 
 
-def test_config1_and_orders(ctx):
-    w = wl.config1()
+def test_single_box_2in_and_orders(ctx):
+    w = wl.single_box_2in()
     for d in (1, 2, 3):
         g = run_gpu(ctx, w.net, w.boxes, degree=d)
         cx = convert(ctx, w.boxes, g)
@@ -126,7 +126,7 @@ def test_zero_width_side(ctx):
 
 
 def test_term_count_above_capacity_is_reported(ctx):
-    w = wl.config1()
+    w = wl.single_box_2in()
     g = run_gpu(ctx, w.net, w.boxes)
     nt = g["n_terms"].copy()
     nt[0, 0, 0] = g["coef"].shape[3] + 1

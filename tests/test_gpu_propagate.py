@@ -89,8 +89,8 @@ def mc_check(g, bi, net, box, count, rng):
     return viol
 
 
-def test_config1_parity_and_soundness(ctx):
-    w = wl.config1()
+def test_single_box_2in_parity_and_soundness(ctx):
+    w = wl.single_box_2in()
     g = run_gpu(ctx, w.net, w.boxes)
     r = oracle.propagate(w.net.widths, w.net.W, w.net.b, w.boxes[0], 2)
     assert not near_tie(r)
@@ -98,8 +98,8 @@ def test_config1_parity_and_soundness(ctx):
     assert mc_check(g, 0, w.net, w.boxes[0], 1_000_000, np.random.default_rng(1)) == 0
 
 
-def test_config2_parity_and_soundness(ctx):
-    w = wl.config2()
+def test_single_box_4in_parity_and_soundness(ctx):
+    w = wl.single_box_4in()
     g = run_gpu(ctx, w.net, w.boxes)
     r = oracle.propagate(w.net.widths, w.net.W, w.net.b, w.boxes[0], 2)
     assert not near_tie(r)
@@ -107,11 +107,11 @@ def test_config2_parity_and_soundness(ctx):
     assert mc_check(g, 0, w.net, w.boxes[0], 200_000, np.random.default_rng(2)) == 0
 
 
-def test_config3_full_batch_sampled(ctx):
+def test_batch_3in_full_batch_sampled(ctx):
     """The benchmark's launch configuration: all 5120 boxes in one call;
     sampled boxes are checked against the oracle one by one, and every box
     against properties that hold at any size."""
-    w = wl.config3()
+    w = wl.batch_3in()
     g = run_gpu(ctx, w.net, w.boxes)
     B = len(w.boxes)
     assert np.all(np.isfinite(g["lo"])) and np.all(g["lo"] <= g["hi"])
@@ -133,10 +133,10 @@ def test_config3_full_batch_sampled(ctx):
         assert mc_check(g, bi, w.net, box, 9, rng) == 0
 
 
-def test_config3_small_batch_matches_full(ctx):
+def test_batch_3in_small_batch_matches_full(ctx):
     """A ragged batch (37 boxes, several tiles and a tail) gives the same
     numbers as the same boxes inside the full batch (no cross-box state)."""
-    w = wl.config3()
+    w = wl.batch_3in()
     idx = np.r_[0:20, 4096:4113]
     g_small = run_gpu(ctx, w.net, w.boxes[idx])
     g_full = run_gpu(ctx, w.net, w.boxes)
@@ -185,13 +185,13 @@ def test_paper_family_nets(ctx):
 
 # ------------------------------------------------------------ edge cases
 def test_empty_batch(ctx):
-    w = wl.config1()
+    w = wl.single_box_2in()
     g = run_gpu(ctx, w.net, w.boxes[:0])
     assert g["lo"].shape == (0, 1)
 
 
 def test_point_box_gives_network_value(ctx):
-    w = wl.config2()
+    w = wl.single_box_4in()
     x = np.array([0.1, -0.2, 0.3, 0.05], np.float32)
     box = np.stack([x, x], -1)[None]
     g = run_gpu(ctx, w.net, box)
@@ -202,7 +202,7 @@ def test_point_box_gives_network_value(ctx):
 
 
 def test_invalid_box_reported(ctx):
-    w = wl.config1()
+    w = wl.single_box_2in()
     bad = np.array([[[0.5, -0.5], [0.0, 1.0]]], np.float32)
     with pytest.raises(bern.BernError) as ei:
         run_gpu(ctx, w.net, bad)
@@ -214,7 +214,7 @@ def test_invalid_box_reported(ctx):
 
 
 def test_capacity_too_small_reports_need(ctx):
-    w = wl.config1()
+    w = wl.single_box_2in()
     with pytest.raises(bern.BernError) as ei:
         run_gpu(ctx, w.net, w.boxes, cap_terms=4)
     assert ei.value.code == bern.BERN_E_CAPACITY
@@ -236,7 +236,7 @@ def test_all_dead_and_all_active(ctx):
 
 
 def test_host_mode_matches_device_mode(ctx):
-    w = wl.config3(n_random=8, cells=2)
+    w = wl.batch_3in(n_random=8, cells=2)
     g = run_gpu(ctx, w.net, w.boxes)
     h = ctx.propagate_host(w.net.widths, w.net.W, w.net.b, w.boxes, degree=2)
     assert np.array_equal(h["lo"], g["lo"]) and np.array_equal(h["hi"], g["hi"])
@@ -247,7 +247,7 @@ def test_host_mode_matches_device_mode(ctx):
 
 
 def test_graphs_on_off_identical_and_counted(ctx):
-    w = wl.config3(n_random=16, cells=4)
+    w = wl.batch_3in(n_random=16, cells=4)
     before = ctx.kernel_launches()
     ctx.set_graphs(False)
     a = run_gpu(ctx, w.net, w.boxes)
@@ -262,7 +262,7 @@ def test_graphs_on_off_identical_and_counted(ctx):
 
 
 def test_output_keys_are_graded_monomials(ctx):
-    w = wl.config1()
+    w = wl.single_box_2in()
     g = run_gpu(ctx, w.net, w.boxes, keys=True)
     nt = int(g["n_terms"][0, 0, 0])
     ex = bern.monomials(2, 4)[:nt].astype(np.int64)
@@ -306,7 +306,7 @@ def test_forced_variants_identical(ctx, widths, seed):
 def test_autotune_on_off_identical(ctx):
     """Every tunable variant computes the same values: results with the
     autotuner's choices equal those with the built-in defaults, bit for bit."""
-    w = wl.config3(n_random=40, cells=4)
+    w = wl.batch_3in(n_random=40, cells=4)
     ctx.set_autotune(False)
     try:
         a = run_gpu(ctx, w.net, w.boxes)
@@ -324,7 +324,7 @@ def test_stability_screen_matches_full_enclosure(ctx):
     The outputs agree: bit for bit on (nearly) every box, and within the
     parity tolerance where a Bernstein bound within rounding of 0 takes the
     other ReLU case."""
-    w = wl.config3(n_random=64, cells=4)
+    w = wl.batch_3in(n_random=64, cells=4)
     a = run_gpu(ctx, w.net, w.boxes)
     b = run_gpu(ctx, w.net, w.boxes, trace=True)
     same = np.all(a["lo"] == b["lo"], axis=1) & np.all(a["hi"] == b["hi"], axis=1)

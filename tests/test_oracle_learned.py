@@ -11,7 +11,7 @@ from paper_2211_14438_gb300 import workloads as wl
 
 
 def test_callback_with_fixed_orders_reproduces_fixed_plan():
-    w = wl.config1()
+    w = wl.single_box_2in()
     degs = np.random.default_rng(0).integers(1, 5, 40)
     a = oracle.propagate(w.net.widths, w.net.W, w.net.b, w.boxes[0], degs)
     seen = []

@@ -278,10 +278,10 @@ def _mc_points(rng, box, count):
     return t, lo + t * (hi - lo)
 
 
-def test_config1_monte_carlo_soundness():
-    """Problem 1 on config 1: zero violations over 10^6 sampled inputs, and the
+def test_single_box_2in_monte_carlo_soundness():
+    """Problem 1 on the [2,20,20,1] net over [-1,1]^2: zero violations over 10^6 sampled inputs, and the
     enclosure lo <= NN <= hi."""
-    w = wl.config1()
+    w = wl.single_box_2in()
     box = w.boxes[0]
     r = oracle.propagate(w.net.widths, w.net.W, w.net.b, box, 2)
     rng = np.random.default_rng(0)
@@ -297,7 +297,7 @@ def test_config1_monte_carlo_soundness():
 
 def test_exact_rational_agrees_with_fp64():
     """Config 1 in exact rationals vs the FP64 oracle."""
-    w = wl.config1()
+    w = wl.single_box_2in()
     r = oracle.propagate(w.net.widths, w.net.W, w.net.b, w.boxes[0], 2)
     q = exact.propagate(w.net.widths, w.net.W, w.net.b, w.boxes[0], 2)
     assert float(q["lo"][0]) == pytest.approx(r["lo"][0], rel=1e-11, abs=1e-11)
@@ -313,7 +313,7 @@ def test_exact_rational_agrees_with_fp64():
 def test_point_box_reproduces_network():
     """A degenerate box (a point): every polynomial is a constant equal to the
     network's value (stable neurons only; exact affine steps)."""
-    w = wl.config2()
+    w = wl.single_box_4in()
     rng = np.random.default_rng(4)
     for _ in range(3):
         x = rng.uniform(-0.5, 0.5, size=4).astype(np.float32)
@@ -422,7 +422,7 @@ def test_tightness_improves_with_order():
 
 
 def test_propagate_rejects_bad_input():
-    w = wl.config1()
+    w = wl.single_box_2in()
     bad = np.array([[1.0, -1.0], [0, 1]], np.float32)
     with pytest.raises(ValueError):
         oracle.propagate(w.net.widths, w.net.W, w.net.b, bad, 2)

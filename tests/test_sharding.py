@@ -25,7 +25,7 @@ def test_shard_ranges_cover_and_balance():
 
 
 def test_box_cost_prefers_wide_boxes():
-    w = wl.config3()
+    w = wl.batch_3in()
     c = sharding.box_cost(w.boxes)
     assert c.shape == (len(w.boxes),) and np.all(c >= 1.0)
     assert c[4096:].mean() > c[:4096].mean()      # random boxes are wider than grid cells
@@ -45,7 +45,7 @@ def _worker(rank, world, port, q):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        w = wl.config3(n_random=64, cells=4)
+        w = wl.batch_3in(n_random=64, cells=4)
         a, b = sharding.shard_boxes(w.boxes, rank, world)
         # a stand-in per-box result that depends only on the box: its index
         # and its width sum (the real result comes from the GPU kernels)
@@ -71,7 +71,7 @@ def test_gloo_world2_gather_and_max():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    w = wl.config3(n_random=64, cells=4)
+    w = wl.batch_3in(n_random=64, cells=4)
     want_w = (w.boxes[:, :, 1] - w.boxes[:, :, 0]).sum(-1)
     for rank, idx, width, t in res:
         assert idx == list(range(len(w.boxes)))

@@ -44,15 +44,15 @@ def _close(a, b):
                 assert d <= TOL * (1 + np.abs(b["coef"][i, j, s, :nt]).sum())
 
 
-@pytest.mark.parametrize("which", ["config1", "config3_subset"])
+@pytest.mark.parametrize("which", ["single_box_2in", "batch_3in_subset"])
 def test_noalloc_matches_propagate_twice(which):
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
-    if which == "config1":
-        w = wl.config1()
+    if which == "single_box_2in":
+        w = wl.single_box_2in()
         boxes = w.boxes
     else:
-        w = wl.config3()
+        w = wl.batch_3in()
         boxes = np.ascontiguousarray(w.boxes[::40])   # 128 boxes: several workspace chunks
     W, b = _dev(w.net)
     bx = torch.from_numpy(boxes).cuda()
@@ -88,7 +88,7 @@ def test_noalloc_rejects_horner_plans():
     static table area does not hold: rejected before any GPU work."""
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
-    w = wl.config1()
+    w = wl.single_box_2in()
     W = [torch.from_numpy(x).cuda() for x in w.net.W]
     b = [torch.from_numpy(x).cuda() for x in w.net.b]
     bx = torch.from_numpy(w.boxes).cuda()
