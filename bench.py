@@ -17,8 +17,9 @@ step-level C ABI, events around every launch), the roofline of the dominant
 kernel, the end-to-end rate through bern_propagate with host buffers, the
 FP64 oracle on the host cores, and SM clocks sampled during the timed region.
 
---impl reference times the FP64 oracle (the reference for this build) on the
-host cores with the same metric and workload.
+--impl reference times the FP64 oracle (the reference arm: there is no
+installable reference implementation of the method) on the host cores with the
+same metric and workload.
 """
 from __future__ import annotations
 
