@@ -75,12 +75,16 @@ def _load():
     lib.orc_eval_poly.argtypes = [ctypes.c_int, ctypes.c_int, u8, dp, ctypes.c_longlong, dp, dp]
     lib.orc_propagate.restype = ctypes.c_int
     lib.orc_propagate.argtypes = [ctypes.c_int, ip, dp, dp, dp, ip, ctypes.c_int,
-                                  ctypes.c_double, ctypes.c_longlong, dp, dp, ctypes.c_int,
-                                  ip, u8, dp, dp, dp, ip, ip]
+                                  ctypes.c_double, ctypes.c_longlong, ctypes.c_int, dp, dp,
+                                  ctypes.c_int, ip, u8, dp, dp, dp, ip, ip]
     lib.orc_propagate_cb.restype = ctypes.c_int
     lib.orc_propagate_cb.argtypes = [ctypes.c_int, ip, dp, dp, dp, DEGREE_FN, ctypes.c_void_p,
-                                     ctypes.c_int, ctypes.c_double, ctypes.c_longlong, dp, dp,
-                                     ctypes.c_int, ip, u8, dp, dp, dp, ip, ip, ip]
+                                     ctypes.c_int, ctypes.c_double, ctypes.c_longlong,
+                                     ctypes.c_int, dp, dp, ctypes.c_int, ip, u8, dp, dp, dp, ip,
+                                     ip, ip]
+    lib.orc_linearize.restype = ctypes.c_int
+    lib.orc_linearize.argtypes = [ctypes.c_int, ctypes.c_int, u8, dp, ctypes.c_int,
+                                  ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ip, u8, dp]
     _lib = lib
     return lib
 
@@ -228,8 +232,25 @@ def eval_poly(p, n: int, t: np.ndarray) -> np.ndarray:
     return out
 
 
+def linearize(p, n: int, order: int, upper: bool, budget: int = 0,
+              cap_terms: int = 1 << 12) -> Poly:
+    """Lin step (Sec. 5.3, reading R22) on one polynomial: its least-squares
+    multilinear fit on the box plus the Bernstein enclosure (order `order`)
+    of the residual, max for the upper bound, min for the lower."""
+    e, c = as_poly(p, n)
+    ne = np.zeros(1, np.int32)
+    oe = np.zeros(cap_terms * n, np.uint8)
+    oc = np.zeros(cap_terms)
+    rc = _load().orc_linearize(n, len(c), _u8(e), _dp(c), order, budget, int(bool(upper)),
+                               cap_terms, _ip(ne), _u8(oe), _dp(oc))
+    if rc:
+        raise ValueError("oracle linearize failed (%d)" % rc)
+    k = int(ne[0])
+    return oe.reshape(cap_terms, n)[:k].copy(), oc[:k].copy()
+
+
 def propagate(widths: Sequence[int], W, b, box, degrees, cap: int = 16,
-              tau: float = 0.0, budget: int = 0, cap_terms: int = 1 << 16):
+              tau: float = 0.0, budget: int = 0, cap_terms: int = 1 << 16, lin: int = 0):
     """Whole-network bounds for ONE box.
 
     widths: [n, h_1, ..., o]; W, b: per-layer float arrays (float32 values are
@@ -240,7 +261,8 @@ def propagate(widths: Sequence[int], W, b, box, degrees, cap: int = 16,
     nterms is the dense term count M(n, D) of its pre-activation polynomials).
     Returns a dict with 'lo', 'hi' (o,), 'upper'/'lower' (lists of polys),
     and the per-hidden-neuron trace 'tr_lo', 'tr_hi', 'tr_case', 'degree' and
-    the per-layer Bernstein order 'order'.
+    the per-layer Bernstein order 'order'.  lin > 0 linearises the
+    post-activation bounds after every lin-th hidden layer (Sec. 5.3, R22).
     """
     widths = [int(w) for w in widths]
     H = len(widths) - 1
@@ -272,7 +294,7 @@ def propagate(widths: Sequence[int], W, b, box, degrees, cap: int = 16,
 
         fn = DEGREE_FN(_cb)
         rc = _load().orc_propagate_cb(H, _ip(wid), _dp(Wa), _dp(ba), _dp(bx), fn, None, cap, tau,
-                                      budget, _dp(out_lo), _dp(out_hi), cap_terms, _ip(nterms),
+                                      budget, int(lin), _dp(out_lo), _dp(out_hi), cap_terms, _ip(nterms),
                                       _u8(exps), _dp(coef), _dp(tr_lo), _dp(tr_hi),
                                       _ip(tr_case), _ip(tr_order), _ip(tr_deg))
         if err:
@@ -288,7 +310,7 @@ def propagate(widths: Sequence[int], W, b, box, degrees, cap: int = 16,
                 deg = np.ones(1, np.int32)
         tr_deg[:n_hidden] = deg[:n_hidden]
         rc = _load().orc_propagate(H, _ip(wid), _dp(Wa), _dp(ba), _dp(bx), _ip(deg), cap, tau,
-                                   budget, _dp(out_lo), _dp(out_hi), cap_terms, _ip(nterms),
+                                   budget, int(lin), _dp(out_lo), _dp(out_hi), cap_terms, _ip(nterms),
                                    _u8(exps), _dp(coef), _dp(tr_lo), _dp(tr_hi), _ip(tr_case),
                                    _ip(tr_order))
     if rc:

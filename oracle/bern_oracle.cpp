@@ -47,6 +47,16 @@
 //     the largest order l' with (l'+1)^n <= budget for the terms of total
 //     degree <= l' and the interval [min(0,c),max(0,c)] for every other
 //     term.  (R6)
+//   * Lin (Sec. 5.3): every Lin hidden layers the post-activation bounds are
+//     lowered to order [1,...,1], i.e. to multilinear polynomials.  The cited
+//     linearisation algorithm is not given; here A is the least-squares fit of
+//     P on the box (the multilinear polynomial minimising the integral of
+//     (P - A)^2 over [0,1]^n), the residual P - A is enclosed by its Bernstein
+//     coefficients at the layer's order (Def. 2), and the bound becomes A plus
+//     the residual's max (upper) or min (lower).  The shift makes the result
+//     sound for any A; the fit only decides how tight it is.  The next
+//     layer's order is then min(n, order): the total degree of a multilinear
+//     polynomial of total degree <= order.  (R22)
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -281,6 +291,75 @@ int to_arrays(const Poly& p, int n, int cap_terms, int* nterms, uint8_t* exps,
   return 0;
 }
 
+// ------------------------------------------------------------- Lin step
+// The least-squares fit is the solution of its normal equations, written out:
+// over the multilinear monomials t^S (S a set of variables, |S| <= min(n, deg P);
+// the fit of a degree-D polynomial has degree <= D) the Gram matrix is
+// G_ST = integral of t^S t^T = prod_k 1/(s_k + t_k + 1) and the right-hand side
+// m_S = integral of P t^S = sum_K p_K prod_k 1/(k_k + s_k + 1); solved by
+// Gaussian elimination with partial pivoting.
+bool linearize(const Poly& P, int n, int order, long long budget, bool upper, Poly& out) {
+  int D = 0;
+  for (const auto& t : P) D = std::max(D, total_degree(t.first));
+  const int Dl = std::min(n, D);
+  std::vector<Mono> basis;
+  for (int s = 0; s < (1 << n); ++s) {
+    Mono S(n, 0);
+    int c = 0;
+    for (int k = 0; k < n; ++k)
+      if ((s >> k) & 1) {
+        S[k] = 1;
+        ++c;
+      }
+    if (c <= Dl) basis.push_back(S);
+  }
+  const size_t N = basis.size();
+  std::vector<double> G(N * N), rhs(N), a(N);
+  for (size_t i = 0; i < N; ++i) {
+    for (size_t j = 0; j < N; ++j) {
+      double g = 1.0;
+      for (int k = 0; k < n; ++k) g /= (double)(basis[i][k] + basis[j][k] + 1);
+      G[i * N + j] = g;
+    }
+    double m = 0.0;
+    for (const auto& t : P) {
+      double w = 1.0;
+      for (int k = 0; k < n; ++k) w /= (double)(t.first[k] + basis[i][k] + 1);
+      m += t.second * w;
+    }
+    rhs[i] = m;
+  }
+  for (size_t col = 0; col < N; ++col) {
+    size_t piv = col;
+    for (size_t r = col + 1; r < N; ++r)
+      if (std::fabs(G[r * N + col]) > std::fabs(G[piv * N + col])) piv = r;
+    if (G[piv * N + col] == 0.0) return false;
+    if (piv != col) {
+      for (size_t c = 0; c < N; ++c) std::swap(G[piv * N + c], G[col * N + c]);
+      std::swap(rhs[piv], rhs[col]);
+    }
+    for (size_t r = col + 1; r < N; ++r) {
+      const double f = G[r * N + col] / G[col * N + col];
+      for (size_t c = col; c < N; ++c) G[r * N + c] -= f * G[col * N + c];
+      rhs[r] -= f * rhs[col];
+    }
+  }
+  for (size_t i = N; i-- > 0;) {
+    double v = rhs[i];
+    for (size_t j = i + 1; j < N; ++j) v -= G[i * N + j] * a[j];
+    a[i] = v / G[i * N + i];
+  }
+  Poly A;
+  for (size_t i = 0; i < N; ++i) A[basis[i]] = a[i];
+  Poly R = P;
+  for (const auto& t : A) R[t.first] -= t.second;
+  double emin, emax;
+  if (!enclosure(R, n, order, budget, &emin, &emax)) return false;
+  A[Mono(n, 0)] += upper ? emax : emin;
+  out = A;
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -351,6 +430,16 @@ int orc_affine(int n, int h_in, const int* nt_up, const uint8_t* e_up,
   return rc ? rc : rc2;
 }
 
+// Lin step on one polynomial (upper != 0: the upper bound's shift).
+int orc_linearize(int n, int nterms, const uint8_t* exps, const double* coef, int order,
+                  long long budget, int upper, int cap_terms, int* out_n, uint8_t* out_exps,
+                  double* out_coef) {
+  Poly out;
+  if (!linearize(from_arrays(n, nterms, exps, coef), n, order, budget, upper != 0, out))
+    return 1;
+  return to_arrays(out, n, cap_terms, out_n, out_exps, out_coef);
+}
+
 void orc_eval_poly(int n, int nterms, const uint8_t* exps, const double* coef,
                    long long npts, const double* t, double* out) {
   for (long long p = 0; p < npts; ++p) {
@@ -370,7 +459,8 @@ void orc_eval_poly(int n, int nterms, const uint8_t* exps, const double* coef,
 // Whole network, one box.
 //   widths[0..H]; W_all/b_all: the layers' row-major weights and biases back
 //   to back; box: n (lo,hi) pairs; degrees: ReLU order per hidden neuron
-//   (sum of hidden widths entries, layer-major).
+//   (sum of hidden widths entries, layer-major); lin: linearise the
+//   post-activation bounds after every lin-th hidden layer (0: never).
 //   Outputs: out_lo/out_hi (o), out_nterms (o x 2: upper, lower),
 //   out_exps (o x 2 x cap_terms x n), out_coef (o x 2 x cap_terms);
 //   trace arrays per hidden neuron: lo, hi, case (0 dead, 1 pass, 2 relu),
@@ -398,7 +488,7 @@ long long dense_terms(const Poly& p, int n) {
 
 int propagate_core(int H, const int* widths, const double* W_all,
                    const double* b_all, const double* box, const DegreeChoice& choose,
-                   int cap, double tau, long long budget, double* out_lo,
+                   int cap, double tau, long long budget, int lin, double* out_lo,
                    double* out_hi, int cap_terms, int* out_nterms,
                    uint8_t* out_exps, double* out_coef, double* tr_lo,
                    double* tr_hi, int* tr_case, int* tr_order, int* tr_degree) {
@@ -473,9 +563,19 @@ int propagate_core(int H, const int* widths, const double* W_all,
       }
       ++hidden_idx;
     }
+    order = std::min(order * dmax, cap);
+    if (lin > 0 && layer % lin == 0) {
+      for (int m = 0; m < h_out; ++m) {
+        Poly a, c;
+        if (!linearize(nu[m], n, order, budget, true, a)) return 1;
+        if (!linearize(nl[m], n, order, budget, false, c)) return 1;
+        nu[m] = a;
+        nl[m] = c;
+      }
+      order = std::min(n, order);
+    }
     up.swap(nu);
     lo.swap(nl);
-    order = std::min(order * dmax, cap);
   }
   return 0;
 }
@@ -486,14 +586,14 @@ extern "C" {
 
 int orc_propagate(int H, const int* widths, const double* W_all,
                   const double* b_all, const double* box, const int* degrees,
-                  int cap, double tau, long long budget, double* out_lo,
+                  int cap, double tau, long long budget, int lin, double* out_lo,
                   double* out_hi, int cap_terms, int* out_nterms,
                   uint8_t* out_exps, double* out_coef, double* tr_lo,
                   double* tr_hi, int* tr_case, int* tr_order) {
   DegreeChoice fixed = [degrees](int, int, int k, double, double, long long) {
     return degrees[k];
   };
-  return propagate_core(H, widths, W_all, b_all, box, fixed, cap, tau, budget, out_lo, out_hi,
+  return propagate_core(H, widths, W_all, b_all, box, fixed, cap, tau, budget, lin, out_lo, out_hi,
                         cap_terms, out_nterms, out_exps, out_coef, tr_lo, tr_hi, tr_case,
                         tr_order, nullptr);
 }
@@ -505,14 +605,14 @@ typedef int (*orc_degree_fn)(void* user, int layer, int m, double lo, double hi,
                              long long nterms);
 int orc_propagate_cb(int H, const int* widths, const double* W_all,
                      const double* b_all, const double* box, orc_degree_fn fn, void* user,
-                     int cap, double tau, long long budget, double* out_lo,
+                     int cap, double tau, long long budget, int lin, double* out_lo,
                      double* out_hi, int cap_terms, int* out_nterms,
                      uint8_t* out_exps, double* out_coef, double* tr_lo,
                      double* tr_hi, int* tr_case, int* tr_order, int* tr_degree) {
   DegreeChoice cb = [fn, user](int layer, int m, int, double lo, double hi, long long nt) {
     return fn(user, layer, m, lo, hi, nt);
   };
-  return propagate_core(H, widths, W_all, b_all, box, cb, cap, tau, budget, out_lo, out_hi,
+  return propagate_core(H, widths, W_all, b_all, box, cb, cap, tau, budget, lin, out_lo, out_hi,
                         cap_terms, out_nterms, out_exps, out_coef, tr_lo, tr_hi, tr_case,
                         tr_order, tr_degree);
 }
