@@ -302,6 +302,74 @@ def ncu_traffic(kernel_key):
     return rec.get("dram_bytes_per_launch")
 
 
+# ------------------------------------------------------ Lin linearisation
+def lin_entries(ctx, torch, dev, flush, args, w, Wd, bd, boxes_d, plain_ms, plain_width, world,
+                dist):
+    """Throughput and mean output-bound width with the bounds linearised after
+    every lin-th hidden layer (Sec. 5.3), on the benchmark workload and on the
+    paper's deepest ablation shape (Fig. 7: [2,20x5,1], W and b U(-5,5), the
+    net of the paper-shaped sweeps), each next to the plain method.  Timed
+    like the headline step: CUDA events on the stream, L2 flushed before
+    every timed call."""
+    from paper_2211_14438_gb300 import bern
+    from paper_2211_14438_gb300 import workloads as wl
+    from paper_2211_14438_gb300.sharding import max_over_ranks
+    stream = ctx.stream
+
+    def timed(net, Wd_, bd_, bx_, degree, cap, lin):
+        nb, o_ = int(bx_.shape[0]), net.n_out
+        ct = bern.max_output_terms(net.widths, degree, cap, lin)
+        outx = {"lo": torch.empty(nb, o_, device=dev), "hi": torch.empty(nb, o_, device=dev),
+                "n_terms": torch.empty(nb, o_, 2, device=dev, dtype=torch.int32),
+                "coef": torch.empty(nb, o_, 2, ct, device=dev), "keys": None}
+
+        def st():
+            ctx.propagate(net.widths, Wd_, bd_, bx_, degree=degree, cap=cap, lin=lin,
+                          cap_terms=ct, out=outx, sync=False)
+        for _ in range(args.warmup):
+            st()
+        if ctx.sync() != 0:
+            raise RuntimeError("propagate failed (lin %d)" % lin)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for s_, e_ in ev:
+            flush.zero_()
+            s_.record(stream)
+            st()
+            e_.record(stream)
+        torch.cuda.synchronize()
+        if ctx.sync() != 0:
+            raise RuntimeError("propagate failed (lin %d)" % lin)
+        ms = max_over_ranks(float(np.mean([s_.elapsed_time(e_) for s_, e_ in ev])), world, dist,
+                            dev)
+        return {"value": round(world * nb / (ms / 1e3), 1), "unit": "boxes/s",
+                "ms_per_step": round(ms, 4),
+                "mean_output_width": round(float((outx["hi"] - outx["lo"]).mean().item()), 6)}
+
+    nb = int(boxes_d.shape[0])
+    res = {"workload": "the benchmark workload above",
+           "plain": {"value": round(world * nb / (plain_ms / 1e3), 1), "unit": "boxes/s",
+                     "ms_per_step": round(plain_ms, 4),
+                     "mean_output_width": round(plain_width, 6)}}
+    for lin in (1, 2):
+        res["lin%d" % lin] = timed(w.net, Wd, bd, boxes_d, w.degree, w.degree_cap, lin)
+    net = wl.paper_net(2, [20] * 5, seed=522)
+    rng = np.random.default_rng(1022)
+    c = rng.uniform(-1, 1, (4096, 2))
+    sd = rng.uniform(0.05, 0.5, (4096, 2))
+    bx = torch.from_numpy(wl.box_array(np.clip(c - sd / 2, -1, 1),
+                                       np.clip(c + sd / 2, -1, 1))).to(dev)
+    Wp = [torch.from_numpy(x).to(dev) for x in net.W]
+    bp = [torch.from_numpy(x).to(dev) for x in net.b]
+    deep = {"workload": "paper deep shape [2,20,20,20,20,20,1], W and b U(-5,5) seed 522, 4096 "
+                        "random sub-boxes of [-1,1]^2 (sides U(0.05,0.5)), ReLU order 2, cap 64"}
+    for lin in (0, 1, 2):
+        deep["plain" if lin == 0 else "lin%d" % lin] = timed(net, Wp, bp, bx, 2, 64, lin)
+    res["deep_2in"] = deep
+    return res
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args, rank, world, local_rank, dist):
     import torch
@@ -565,6 +633,16 @@ def run_ours(args, rank, world, local_rank, dist):
                           "U": round(bb.upper(), 5), "L": round(bb.lower(), 5),
                           "seconds": round(dt, 3)}
 
+    # ---- Lin linearisation (Sec. 5.3); reported beside the headline, which
+    # it can never cost: an error here is recorded, not raised
+    lin_res = None
+    if not args.no_lin:
+        try:
+            lin_res = lin_entries(ctx, torch, dev, flush, args, w, Wd, bd, boxes_d, ms_step,
+                                  float(np.mean(hi - lo)), world, dist)
+        except Exception as ex:
+            lin_res = {"error": "%s: %s" % (type(ex).__name__, ex)}
+
     cpu = None
     if pool is not None:
         idx = np.linspace(0, B - 1, 2 * cores).astype(int)
@@ -594,7 +672,7 @@ def run_ours(args, rank, world, local_rank, dist):
         "roofline": roof, "kernels": kernels,
         "kernel_pass_ms_per_step": round(total_kernel_ms, 4),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-        "learned": learned, "learned_6in": learned4, "bnb_6in": bnb5,
+        "learned": learned, "learned_6in": learned4, "bnb_6in": bnb5, "lin": lin_res,
         "clocks": clocks,
     }
     return line
@@ -724,6 +802,8 @@ def main():
                     help="skip the branch-and-bound refinement of the [6,64x4,1] root box [-1,1]^6")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip training and timing the learned-degree form")
+    ap.add_argument("--no-lin", action="store_true",
+                    help="skip timing the Lin-linearised forms")
     ap.add_argument("--n-boxes", type=int, default=0,
                     help="use N evenly strided boxes of the workload (small cases for ncu)")
     ap.add_argument("--paper-sweeps", action="store_true",

@@ -130,6 +130,14 @@ typedef struct {
    * method's order, 0 means 2). */
   const bern_mlp* mlp;
   float min_conf;
+  /* Lin (Sec. 5.3): if > 0, after the composition of every lin_every-th
+   * hidden layer each neuron's bounds are replaced by their least-squares
+   * multilinear fit on the box (order [1,...,1]) plus the Bernstein
+   * enclosure of the residual at the layer's order (max for the upper bound,
+   * min for the lower), so the next layer starts from total degree
+   * min(n, D).  0 = never.  Not with BERN_DEG_LEARNED plans
+   * (BERN_E_UNSUPPORTED) nor with bern_propagate_noalloc. */
+  int lin_every;
 } bern_degree_plan;
 
 /* Results, all caller-owned, in the context's pointer mode.
@@ -303,6 +311,22 @@ int bern_enclose(bern_ctx* ctx, int n, int64_t n_boxes, int h, int order,
                  int64_t budget, const float* pre_up, const float* pre_lo,
                  int64_t ld, const int32_t* nterms, float* lo, float* hi);
 
+/* Lin step, Sec. 5.3 (parameter Lin): for every neuron of a post-activation
+ * block, the least-squares multilinear fit A of each bound on [0,1]^n is
+ * written to lin_up / lin_lo (a layer block with stride lin_ld >=
+ * M(n, min(n, order)); term counts lin_nterms = min(nterms, that)), the
+ * residual post - A (rounded up for the upper bound, down for the lower)
+ * OVERWRITES post_up / post_lo, its Bernstein enclosure of order `order`
+ * goes to res_lo (min over the lower residual) and res_hi (max over the
+ * upper one), and A's constant is shifted by it outward: lin_up >= post_up
+ * and lin_lo <= post_lo on the box.  budget as in bern_enclose.  res_lo /
+ * res_hi: [n_boxes x h]. */
+int bern_linearize(bern_ctx* ctx, int n, int64_t n_boxes, int h, int order,
+                   int64_t budget, float* post_up, float* post_lo, int64_t ld,
+                   const int32_t* nterms, float* lin_up, float* lin_lo,
+                   int64_t lin_ld, int32_t* lin_nterms, float* res_lo,
+                   float* res_hi);
+
 /* a3, Sec. 5.1 Step 2 with Def. 1 and Props. 1-2: per item the case
  * (0: hi <= 0, output 0; 1: lo >= 0, identity; 2: ReLU polynomial), and for
  * case 2 the power form a_0..a_d in s = (y-lo)/(hi-lo) of the order-d
@@ -353,8 +377,9 @@ int bern_compose(bern_ctx* ctx, int n, int64_t n_boxes, int h, int degree_cap,
  *
  *   net, boxes, result: device pointers (layouts as for bern_propagate);
  *   stream: a cudaStream_t (NULL = legacy default stream).
- *   plan: BERN_DEG_GLOBAL or BERN_DEG_PER_LAYER (PER_NEURON returns
- *   BERN_E_UNSUPPORTED); NULL means global order 2, cap 16.
+ *   plan: BERN_DEG_GLOBAL or BERN_DEG_PER_LAYER (PER_NEURON, prune_tau > 0
+ *   and lin_every != 0 return BERN_E_UNSUPPORTED); NULL means global order
+ *   2, cap 16.
  * Boxes are processed in chunks that fit the workspace.  A network whose
  * per-box workspace exceeds 32 MiB, or whose tables exceed 4 MiB, is rejected
  * with BERN_E_UNSUPPORTED before any GPU work.

@@ -52,7 +52,7 @@ EXPORTS = [
     "bern_mlp_num_params", "bern_degree_features", "bern_mlp_forward", "bern_mlp_backward",
     "bern_mlp_adam", "bern_propagate_traced", "bern_split_features",
     "bern_set_horner_smem_limit", "bern_set_autotune", "bern_force_variant",
-    "bern_poly_to_x",
+    "bern_poly_to_x", "bern_linearize",
 ]
 
 
@@ -79,7 +79,8 @@ class bern_degree_plan(ctypes.Structure):
                 ("per_neuron", ctypes.POINTER(ctypes.c_uint8)),
                 ("degree_cap", ctypes.c_int), ("prune_tau", ctypes.c_float),
                 ("bern_budget", ctypes.c_int64),
-                ("mlp", ctypes.POINTER(bern_mlp)), ("min_conf", ctypes.c_float)]
+                ("mlp", ctypes.POINTER(bern_mlp)), ("min_conf", ctypes.c_float),
+                ("lin_every", ctypes.c_int)]
 
 
 class bern_trace(ctypes.Structure):
@@ -130,6 +131,7 @@ def load(build_if_missing: bool = True):
         "bern_init_inputs": (I, [V, I, I64, V, V, V, I64, V]),
         "bern_affine": (I, [V, I64, I, I, V, V, V, V, I64, V, V, V, I64, V]),
         "bern_enclose": (I, [V, I, I64, I, I, I64, V, V, I64, V, V, V]),
+        "bern_linearize": (I, [V, I, I64, I, I, I64, V, V, I64, V, V, V, I64, V, V, V]),
         "bern_relu_coeffs": (I, [V, I64, V, V, V, I, V, V, V]),
         "bern_compose": (I, [V, I, I64, I, I, F, V, V, V, V, I, V, V, V, V, I64, V, V, V, I64,
                              V]),
@@ -266,6 +268,13 @@ class Context:
                                      _ptr(pre_lo), ld, _ptr(nterms), _ptr(lo), _ptr(hi)),
                "bern_enclose")
 
+    def linearize(self, n, n_boxes, h, order, budget, post_up, post_lo, ld, nterms, lin_up,
+                  lin_lo, lin_ld, lin_nterms, res_lo, res_hi):
+        _check(self.lib.bern_linearize(self.h, n, n_boxes, h, order, budget, _ptr(post_up),
+                                       _ptr(post_lo), ld, _ptr(nterms), _ptr(lin_up),
+                                       _ptr(lin_lo), lin_ld, _ptr(lin_nterms), _ptr(res_lo),
+                                       _ptr(res_hi)), "bern_linearize")
+
     def relu_coeffs(self, n_items, lo, hi, degrees, global_d, kind, coef, eps):
         _check(self.lib.bern_relu_coeffs(self.h, n_items, _ptr(lo), _ptr(hi), _ptr(degrees),
                                          global_d, _ptr(kind), _ptr(coef), _ptr(eps)),
@@ -313,19 +322,21 @@ class Context:
     # ------------------------------------------------------------- whole path
     def propagate(self, widths: Sequence[int], W, b, boxes, degree=2, cap: int = 16,
                   tau: float = 0.0, budget: int = 0, cap_terms: Optional[int] = None,
-                  out=None, keys: bool = False, sync: bool = True, trace: bool = False):
+                  out=None, keys: bool = False, sync: bool = True, trace: bool = False,
+                  lin: int = 0):
         """bern_propagate on device tensors (W, b: lists of float32 CUDA tensors;
         boxes: float32 CUDA tensor [B, n, 2]).  degree: int (global), list of
         per-hidden-layer ints, or a uint8 array with one order per hidden
-        neuron.  Returns a dict of CUDA tensors."""
+        neuron.  lin > 0 linearises every lin-th hidden layer (Sec. 5.3).
+        Returns a dict of CUDA tensors."""
         torch = self.torch
         widths = [int(x) for x in widths]
         H = len(widths) - 1
         o = widths[-1]
         B = int(boxes.shape[0])
-        plan, keep = make_plan(degree, widths, cap, tau, budget)
+        plan, keep = make_plan(degree, widths, cap, tau, budget, lin)
         if cap_terms is None:
-            cap_terms = max_output_terms(widths, degree, cap)
+            cap_terms = max_output_terms(widths, degree, cap, lin)
         dev = boxes.device
         if out is None:
             out = {
@@ -360,15 +371,15 @@ class Context:
         return out
 
     def propagate_host(self, widths, W, b, boxes, degree=2, cap: int = 16, tau: float = 0.0,
-                       budget: int = 0, cap_terms: Optional[int] = None, out=None):
+                       budget: int = 0, cap_terms: Optional[int] = None, out=None, lin: int = 0):
         """bern_propagate with host buffers (numpy arrays, ideally pinned):
         copies in, runs, copies out and synchronises inside the call."""
         widths = [int(x) for x in widths]
         o = widths[-1]
         B = int(boxes.shape[0])
-        plan, keep = make_plan(degree, widths, cap, tau, budget)
+        plan, keep = make_plan(degree, widths, cap, tau, budget, lin)
         if cap_terms is None:
-            cap_terms = max_output_terms(widths, degree, cap)
+            cap_terms = max_output_terms(widths, degree, cap, lin)
         if out is None:
             out = {"lo": np.empty((B, o), np.float32), "hi": np.empty((B, o), np.float32),
                    "n_terms": np.empty((B, o, 2), np.int32),
@@ -465,7 +476,7 @@ class Learned:
         self.max_per_layer = None if max_per_layer is None else [int(x) for x in max_per_layer]
 
 
-def make_plan(degree, widths, cap, tau, budget):
+def make_plan(degree, widths, cap, tau, budget, lin: int = 0):
     H = len(widths) - 1
     keep = []
     if isinstance(degree, Learned):
@@ -491,6 +502,7 @@ def make_plan(degree, widths, cap, tau, budget):
             a = (ctypes.c_int * len(arr))(*[int(x) for x in arr])
             keep.append(a)
             plan = bern_degree_plan(BERN_DEG_PER_LAYER, 0, a, None, cap, tau, budget)
+    plan.lin_every = int(lin)
     return plan, keep
 
 
@@ -512,10 +524,14 @@ def layer_degrees(widths, degree):
     return [int(x) for x in arr]
 
 
-def max_output_terms(widths, degree, cap) -> int:
+def max_output_terms(widths, degree, cap, lin: int = 0) -> int:
     """Worst-case term count of an output polynomial (the graded prefix of
-    total degree min(prod d_i, cap))."""
+    total degree min(prod d_i, cap); with Lin every lin-th hidden layer
+    lowers the degree to min(n, D))."""
+    n = int(widths[0])
     D = 1
-    for d in layer_degrees(widths, degree):
+    for i, d in enumerate(layer_degrees(widths, degree)):
         D = min(D * d, cap)
-    return num_monomials(int(widths[0]), D)
+        if lin > 0 and (i + 1) % lin == 0:
+            D = min(n, D)
+    return num_monomials(n, D)

@@ -303,10 +303,17 @@ struct LayerPlan {
   // every value it can take
   size_t off_order = 0;
   std::vector<int> orders;
+  // Lin layers (Sec. 5.3): the post-activation bounds are replaced by their
+  // multilinear fits shifted by the residual's enclosure at order_post
+  bool lin = false;
+  int order_post = 0, D_lin = 0;
+  int64_t M_lin = 0;
+  size_t off_lin_up = 0, off_lin_lo = 0, off_lin_nt = 0, off_lin_rlo = 0, off_lin_rhi = 0;
 };
 
 struct Plan {
   int n, o, H, cap;
+  int lin = 0;      // linearise every lin-th hidden layer (0: never)
   float tau;
   int64_t budget;
   std::vector<LayerPlan> L;
@@ -340,6 +347,9 @@ int make_plan(const bern_net* net, const bern_degree_plan* dp, Plan& P) {
   P.tau = dp->prune_tau;
   if (!(P.tau >= 0.0f)) return BERN_E_INVALID;
   P.budget = dp->bern_budget > 0 ? dp->bern_budget : ((int64_t)1 << 20);
+  P.lin = dp->lin_every;
+  if (P.lin < 0) return BERN_E_INVALID;
+  if (P.lin > 0 && dp->kind == BERN_DEG_LEARNED) return BERN_E_UNSUPPORTED;
   P.L.resize(P.H);
   int Dprev = 1, order = 1;
   int hidden_base = 0;
@@ -392,6 +402,15 @@ int make_plan(const bern_net* net, const bern_degree_plan* dp, Plan& P) {
       hidden_base += l.h_out;
       Dprev = l.D_post;
       order = std::min(order * l.d, P.cap);
+      if (P.lin > 0 && (i + 1) % P.lin == 0) {
+        // a multilinear polynomial of total degree <= D has degree <= min(n, D)
+        l.lin = true;
+        l.order_post = order;
+        l.D_lin = std::min(P.n, l.D_post);
+        l.M_lin = monomials_clamped(P.n, l.D_lin);
+        Dprev = l.D_lin;
+        order = std::min(P.n, order);
+      }
     } else {
       l.D_post = l.D_pre;
     }
@@ -438,6 +457,13 @@ int make_plan(const bern_net* net, const bern_degree_plan* dp, Plan& P) {
       l.off_post_lo = take(sizeof(float) * l.h_out * l.M_post);
       l.off_post_nt = take(sizeof(int32_t) * l.h_out);
       l.off_deg = (P.per_neuron || P.learned) ? take(l.h_out) : 0;
+      if (l.lin) {
+        l.off_lin_up = take(sizeof(float) * l.h_out * l.M_lin);
+        l.off_lin_lo = take(sizeof(float) * l.h_out * l.M_lin);
+        l.off_lin_nt = take(sizeof(int32_t) * l.h_out);
+        l.off_lin_rlo = take(sizeof(float) * l.h_out);
+        l.off_lin_rhi = take(sizeof(float) * l.h_out);
+      }
     }
     if (P.learned) l.off_order = take(sizeof(int32_t));
   }
@@ -537,10 +563,24 @@ int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
     e = launch_compose(L, T, CS, B, l.h_out, P.cap, P.tau, kind, coef, eps, deg, l.d, lo, hi,
                        pre_up, pre_lo, l.M_pre, pre_nt, post_up, post_lo, l.M_post, post_nt);
     if (e != cudaSuccess) return map_cuda(e);
-    in_up = post_up;
-    in_lo = post_lo;
-    in_nt = post_nt;
-    in_stride = l.M_post;
+    if (l.lin) {
+      float* lin_up = ch.at<float>(l.off_lin_up);
+      float* lin_lo = ch.at<float>(l.off_lin_lo);
+      int32_t* lin_nt = ch.at<int32_t>(l.off_lin_nt);
+      e = launch_linearize(L, T, B, l.h_out, l.order_post, P.budget, post_up, post_lo, l.M_post,
+                           post_nt, lin_up, lin_lo, l.M_lin, lin_nt, ch.at<float>(l.off_lin_rlo),
+                           ch.at<float>(l.off_lin_rhi));
+      if (e != cudaSuccess) return map_cuda(e);
+      in_up = lin_up;
+      in_lo = lin_lo;
+      in_nt = lin_nt;
+      in_stride = l.M_lin;
+    } else {
+      in_up = post_up;
+      in_lo = post_lo;
+      in_nt = post_nt;
+      in_stride = l.M_post;
+    }
   }
   return BERN_OK;
 }
@@ -572,6 +612,7 @@ std::string graph_key(const Plan& P, const bern_net* net, const float* boxes, in
   add(&P.cap, sizeof P.cap);
   add(&P.tau, sizeof P.tau);
   add(&P.budget, sizeof P.budget);
+  add(&P.lin, sizeof P.lin);
   add(&P.learned, sizeof P.learned);
   if (P.learned) {
     add(&P.mlp, sizeof P.mlp);
@@ -775,6 +816,23 @@ int bern_enclose(bern_ctx* c, int n, int64_t n_boxes, int h, int order, int64_t 
                                  nterms, lo, hi));
 }
 
+int bern_linearize(bern_ctx* c, int n, int64_t n_boxes, int h, int order, int64_t budget,
+                   float* post_up, float* post_lo, int64_t ld, const int32_t* nterms,
+                   float* lin_up, float* lin_lo, int64_t lin_ld, int32_t* lin_nterms,
+                   float* res_lo, float* res_hi) {
+  if (!c || n < 1 || n > kMaxVars || n_boxes < 0 || h < 1 || order < 0 || ld < 1 ||
+      lin_ld < num_monomials(n, std::min(n, order)))
+    return BERN_E_INVALID;
+  cudaSetDevice(c->device);
+  const Tables* T;
+  int rc = ensure_tables(c, n, 0, &T);
+  if (rc) return rc;
+  if (ld > T->mexps) return BERN_E_UNSUPPORTED;
+  return map_cuda(launch_linearize(c->launch(), *T, n_boxes, h, order, budget, post_up, post_lo,
+                                   ld, nterms, lin_up, lin_lo, lin_ld, lin_nterms, res_lo,
+                                   res_hi));
+}
+
 int bern_relu_coeffs(bern_ctx* c, int64_t n_items, const float* lo, const float* hi,
                      const uint8_t* degrees, int global_d, int8_t* kind, float* coef,
                      float* eps) {
@@ -930,6 +988,7 @@ int bern_propagate_traced(bern_ctx* c, const bern_net* net, const float* boxes,
       add(&P.cap, sizeof P.cap);
       add(&P.tau, sizeof P.tau);
       add(&P.budget, sizeof P.budget);
+      add(&P.lin, sizeof P.lin);
       add(&P.learned, sizeof P.learned);
       for (int i = 0; i <= P.H; ++i) add(&net->widths[i], sizeof(int));
       for (const auto& l : P.L) add(&l.d, sizeof l.d);

@@ -228,6 +228,16 @@ cudaError_t launch_enclose_by_order(const Launch& L, const Tables& T, const Comp
                                     const float* pre_up, const float* pre_lo, int64_t ld,
                                     const int32_t* nterms, float* lo, float* hi);
 
+// Lin step (Sec. 5.3) on a post-activation block: the least-squares
+// multilinear fit of every bound goes to lin (graded prefix of
+// M(n, min(n, order)) ranks, stride lin_ld, term counts lin_nt), the rounded
+// residual overwrites post, its enclosure at `order` goes to rlo/rhi, and the
+// fit's constant is shifted by it outward.
+cudaError_t launch_linearize(const Launch& L, const Tables& T, int64_t n_boxes, int h, int order,
+                             int64_t budget, float* post_up, float* post_lo, int64_t ld,
+                             const int32_t* nterms, float* lin_up, float* lin_lo, int64_t lin_ld,
+                             int32_t* lin_nt, float* rlo, float* rhi);
+
 // Largest input degree the row-convolution path handles for n variables.
 int row_path_max_degree(int n);
 cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratch& S,

@@ -201,7 +201,7 @@ extern "C" int bern_propagate_noalloc(const bern_net* net, const float* boxes, i
   if (cap > bern::kMaxTableDegree || !(dp->prune_tau >= 0.0f)) return BERN_E_INVALID;
   // the static tables hold the order-1/2 kernels' tables only: no Horner
   // items (orders >= 3, pruning) on this path
-  if (dp->prune_tau > 0.0f) return BERN_E_UNSUPPORTED;
+  if (dp->prune_tau > 0.0f || dp->lin_every != 0) return BERN_E_UNSUPPORTED;
   const int64_t budget = dp->bern_budget > 0 ? dp->bern_budget : ((int64_t)1 << 20);
   if (n_boxes == 0) return BERN_OK;
   if (!result->lo || !result->hi || !result->n_terms || result->cap_terms < 0)
