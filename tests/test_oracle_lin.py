@@ -135,3 +135,20 @@ def test_lin_beyond_depth_is_a_no_op():
     a = oracle.propagate(net.widths, net.W, net.b, w.boxes[0], 2)
     b = oracle.propagate(net.widths, net.W, net.b, w.boxes[0], 2, lin=5)
     assert a["lo"][0] == b["lo"][0] and a["hi"][0] == b["hi"][0]
+
+
+@pytest.mark.parametrize("widths,lin", [([2, 20, 20, 1], 1), ([2, 20, 20, 1], 2),
+                                        ([3, 8, 8, 8, 1], 2), ([4, 6, 6, 6, 2], 3)])
+def test_output_capacity_rule_covers_the_oracle(widths, lin):
+    """The binding sizes output polynomials by the degree bookkeeping of the
+    plan (with Lin, min(n, D) after every Lin layer); the oracle's outputs
+    must fit that graded prefix."""
+    from paper_2211_14438_gb300 import bern
+    n = widths[0]
+    net = wl.make_net(widths, seed=30 + lin)
+    box = wl.box_array([-1.0] * n, [1.0] * n)
+    r = oracle.propagate(net.widths, net.W, net.b, box, 2, lin=lin)
+    deg = max(int(np.asarray(e).sum(axis=1).max()) for e, _ in r["upper"] + r["lower"])
+    cap_terms = bern.max_output_terms(widths, 2, 16, lin)
+    assert cap_terms >= bern.num_monomials(n, deg)
+    assert bern.max_output_terms(widths, 2, 16, lin) <= bern.max_output_terms(widths, 2, 16)
