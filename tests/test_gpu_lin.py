@@ -92,6 +92,22 @@ def test_lin_paper_deep_net(ctx, lin):
     assert mc_check(g, 0, net, box, 100_000, np.random.default_rng(6)) == 0
 
 
+@pytest.mark.parametrize("widths", [[6, 10, 10, 1], [8, 6, 6, 1]])
+def test_lin_many_inputs(ctx, widths):
+    """Six and eight inputs: 64 and 256 variable sets in the fit (more sets
+    than lanes), and with eight inputs Bernstein grids above the library's
+    limit, lowered by the budget rule on both sides."""
+    n = widths[0]
+    net = wl.make_net(widths, seed=40 + n)
+    box = wl.box_array([-0.5] * n, [0.5] * n)
+    budget = bern.effective_budget(0)
+    g = run_gpu(ctx, net, box[None], lin=1)
+    r = oracle.propagate(net.widths, net.W, net.b, box, 2, lin=1, budget=budget)
+    if not near_tie(r):
+        compare_box(g, 0, r, n, 1)
+    assert mc_check(g, 0, net, box, 50_000, np.random.default_rng(n)) == 0
+
+
 def test_lin_beyond_depth_is_the_plain_method(ctx):
     w = wl.batch_3in(n_random=8, cells=2)
     a = run_gpu(ctx, w.net, w.boxes)
