@@ -13,8 +13,10 @@ Parity status per function: all pinned by ``tests/test_oracle_pins.py``
 (closed forms, Table 1, vertex/basis identities of the Bernstein expansion,
 dense-grid min/max, brute-force products, exact-network special cases and
 Monte-Carlo soundness), ``tests/test_oracle_helpers.py`` (evaluation helpers)
-and ``tests/test_oracle_lin.py`` (the Lin step: hand-worked fits, numerical
-least squares, soundness), except the tightness of whole-network bounds, which
+``tests/test_oracle_lin.py`` (the Lin step: hand-worked fits, numerical
+least squares, soundness) and ``tests/test_oracle_bern_tensor.py`` (the
+paper's dense Bernstein-tensor arithmetic in ``bern_tensor.py``, against the
+definition and against the power basis), except the tightness of whole-network bounds, which
 is "parity unpinned": the paper's volumes come from unseeded networks.
 """
 from __future__ import annotations
