@@ -12,7 +12,11 @@ Steps follow the paper in order: input init (Sec. 5.3), layer step with W+/W-
 Bernstein polynomial (Def. 1, Prop. 1/2), Step 3 composition
 (eqs. post_bounds_1/2).  Polynomials are dicts {exponent tuple: Fraction} in
 t in [0,1]^n.  No truncation (the degree cap is never reached on the tiny
-nets this serves) and no pruning.
+nets this serves) and no pruning.  With lin > 0, the Lin step of Sec. 5.3 in
+the reading of the FP64 oracle (least-squares multilinear fit on the box,
+Bernstein enclosure of the residual at the layer's order, outward shift) runs
+after every lin-th hidden layer; the fit's normal equations are solved
+exactly.
 """
 from __future__ import annotations
 
@@ -61,7 +65,47 @@ def _relu_power(lo, hi, d):
     return a, eps
 
 
-def propagate(widths, W, b, box, degree):
+def _linearize(P, n, order, upper):
+    """Least-squares multilinear fit A of P on [0,1]^n (normal equations over
+    the monomials t^S, S a set of at most min(n, deg P) variables, with the
+    exact moments of t^K on the box), plus the residual's Bernstein max
+    (upper) or min (lower) in the constant."""
+    D = max(sum(k) for k in P)
+    basis = [S for S in product((0, 1), repeat=n) if sum(S) <= min(n, D)]
+    N = len(basis)
+
+    def moment(K):
+        r = Fraction(1)
+        for k in K:
+            r /= k + 1
+        return r
+
+    G = [[moment(tuple(x + y for x, y in zip(S, T))) for T in basis] for S in basis]
+    rhs = [sum((c * moment(tuple(x + y for x, y in zip(K, S))) for K, c in P.items()),
+               Fraction(0)) for S in basis]
+    for col in range(N):                       # exact Gaussian elimination
+        piv = next(r for r in range(col, N) if G[r][col] != 0)
+        G[col], G[piv] = G[piv], G[col]
+        rhs[col], rhs[piv] = rhs[piv], rhs[col]
+        for r in range(col + 1, N):
+            f = G[r][col] / G[col][col]
+            if f:
+                G[r] = [x - f * y for x, y in zip(G[r], G[col])]
+                rhs[r] -= f * rhs[col]
+    a = [Fraction(0)] * N
+    for i in range(N - 1, -1, -1):
+        a[i] = (rhs[i] - sum((G[i][j] * a[j] for j in range(i + 1, N)), Fraction(0))) / G[i][i]
+    A = dict(zip(basis, a))
+    R = dict(P)
+    for k, v in A.items():
+        R[k] = R.get(k, Fraction(0)) - v
+    rmin, rmax = _bern_minmax(R, n, order)
+    zero = tuple([0] * n)
+    A[zero] += rmax if upper else rmin
+    return A
+
+
+def propagate(widths, W, b, box, degree, lin=0):
     n = widths[0]
     H = len(widths) - 1
     zero = tuple([0] * n)
@@ -119,5 +163,9 @@ def propagate(widths, W, b, box, degree):
                 res[1][zero] = res[1].get(zero, Fraction(0)) - eps
                 nu.append(res[0])
                 nl.append(res[1])
-        up, lo = nu, nl
         order = order * degree
+        if lin > 0 and (layer + 1) % lin == 0:
+            nu = [_linearize(P, n, order, True) for P in nu]
+            nl = [_linearize(P, n, order, False) for P in nl]
+            order = min(n, order)
+        up, lo = nu, nl

@@ -152,3 +152,21 @@ def test_output_capacity_rule_covers_the_oracle(widths, lin):
     cap_terms = bern.max_output_terms(widths, 2, 16, lin)
     assert cap_terms >= bern.num_monomials(n, deg)
     assert bern.max_output_terms(widths, 2, 16, lin) <= bern.max_output_terms(widths, 2, 16)
+
+
+@pytest.mark.parametrize("lin", [1, 2])
+def test_exact_rational_lin_agrees_with_fp64(lin):
+    """The [2,20,20,1] net over [-1,1]^2 with Lin, in exact rationals (the fit's
+    normal equations solved exactly) against the FP64 oracle."""
+    from oracle import exact
+    w = wl.single_box_2in()
+    r = oracle.propagate(w.net.widths, w.net.W, w.net.b, w.boxes[0], 2, lin=lin)
+    q = exact.propagate(w.net.widths, w.net.W, w.net.b, w.boxes[0], 2, lin=lin)
+    assert float(q["lo"][0]) == pytest.approx(r["lo"][0], rel=1e-11, abs=1e-11)
+    assert float(q["hi"][0]) == pytest.approx(r["hi"][0], rel=1e-11, abs=1e-11)
+    for name in ("upper", "lower"):
+        d = oracle.to_dict(r[name][0])
+        qe = q[name][0]
+        assert set(d) == set(qe)
+        for k in d:
+            assert d[k] == pytest.approx(float(qe[k]), rel=1e-9, abs=1e-10)
