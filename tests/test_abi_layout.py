@@ -56,3 +56,49 @@ def test_struct_matches_header(c_layout, name):
     assert [f[0] for f in cls._fields_] == fields
     for f in fields:
         assert getattr(cls, f).offset == c_layout[(name, f)], (name, f)
+
+
+def _header_prototypes():
+    import re
+    src = open(os.path.join(ROOT, "include", "bern.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    protos = {}
+    for m in re.finditer(r"([A-Za-z_][\w\s\*]*?)\b(bern_[a-z_]+)\s*\(([^;{]*?)\)\s*;", src):
+        ret, name, params = m.group(1), m.group(2), m.group(3)
+        ps = [p.strip() for p in params.split(",") if p.strip() and p.strip() != "void"]
+        protos[name] = (ret.strip(), ps)
+    return protos
+
+
+def _kind_of_c(decl):
+    if "*" in decl:
+        return "ptr"
+    t = decl.replace("const", "").split()[0]
+    return {"int": "i32", "int64_t": "i64", "float": "f32", "double": "f64"}[t]
+
+
+def _kind_of_ctypes(t):
+    if t in (ctypes.c_int, ctypes.c_int32):
+        return "i32"
+    if t in (ctypes.c_int64, ctypes.c_longlong):
+        return "i64"
+    if t is ctypes.c_float:
+        return "f32"
+    if t is ctypes.c_double:
+        return "f64"
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(t, ctypes._Pointer):
+        return "ptr"
+    raise AssertionError(t)
+
+
+def test_function_signatures_match_header():
+    lib = bern.load()
+    protos = _header_prototypes()
+    assert set(protos) == set(bern.EXPORTS)
+    for name, (ret, params) in protos.items():
+        fn = getattr(lib, name)
+        got = [_kind_of_ctypes(t) for t in fn.argtypes]
+        want = [_kind_of_c(p) for p in params]
+        assert got == want, (name, got, want)
+        assert _kind_of_ctypes(fn.restype) == _kind_of_c(ret + (" *" if "*" in ret else "")), name
