@@ -94,9 +94,10 @@ def _rank_main(rank, world, port, q):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     root = np.array([[-1, 1], [-1, 1], [-1, 1]], np.float32)
-    # rank 0 starts with the half of the root holding the maximum, rank 1 the other half
+    # rank 0 starts with the half of the root holding the maximum, rank 1 the
+    # other half, any further rank with nothing
     halves = bnb.split_boxes(root[None], np.array([0]))
-    mine = halves[1:] if rank == 0 else halves[:1]
+    mine = halves[1:] if rank == 0 else (halves[:1] if rank == 1 else halves[:0])
     bb = bnb.BranchAndBound(interval_bound, root, batch=8, max_leaves=400, boxes=mine)
     before = bb.count()
     for r in range(6):
@@ -109,7 +110,8 @@ def _rank_main(rank, world, port, q):
     dist.destroy_process_group()
 
 
-def test_rebalance_two_gloo_ranks():
+@pytest.mark.parametrize("world", [2, 4])
+def test_rebalance_gloo_ranks(world):
     import multiprocessing as mp
     import socket
     s = socket.socket()
@@ -118,7 +120,7 @@ def test_rebalance_two_gloo_ranks():
     s.close()
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    ps = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    ps = [ctx.Process(target=_rank_main, args=(r, world, port, q)) for r in range(world)]
     for p in ps:
         p.start()
     res = [q.get(timeout=120) for _ in ps]
@@ -127,11 +129,12 @@ def test_rebalance_two_gloo_ranks():
         assert p.exitcode == 0
     res.sort()
     totals = {r[3] for r in res}
-    assert len(totals) == 1 and totals.pop() == res[0][2] + res[1][2]
+    assert len(totals) == 1 and totals.pop() == sum(r[2] for r in res)
     U, L = res[0][4], res[0][5]
     assert L <= 0.0 <= U
-    # after the last rebalance both ranks held work near the top of the queue
+    # after the last rebalance every rank held work near the top of the queue,
+    # including the ranks that started with nothing
     assert all(r[2] > 0 for r in res)
     # no box is duplicated across ranks
-    allb = np.concatenate([res[0][7], res[1][7]], 0).reshape(len(res[0][7]) + len(res[1][7]), -1)
+    allb = np.concatenate([r[7].reshape(len(r[7]), -1) for r in res], 0)
     assert len(np.unique(allb, axis=0)) == len(allb)

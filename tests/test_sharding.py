@@ -58,13 +58,14 @@ def _worker(rank, world, port, q):
         dist.destroy_process_group()
 
 
-def test_gloo_world2_gather_and_max():
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_gather_and_max(world):
     torch = pytest.importorskip("torch")
     import torch.multiprocessing as tmp
     ctx = tmp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
     for p in procs:
         p.start()
     res = [q.get(timeout=120) for _ in procs]
@@ -76,4 +77,4 @@ def test_gloo_world2_gather_and_max():
     for rank, idx, width, t in res:
         assert idx == list(range(len(w.boxes)))
         np.testing.assert_allclose(width, want_w)
-        assert t == 3.0
+        assert t == 1.5 * world
