@@ -13,8 +13,9 @@
 //   c_S = 3^|S| sum_K p_K prod_{k in S} e_k / ((e_k+1)(e_k+2)) prod_{k not in S} 1/(e_k+1)
 // (the integrals of t^K times the basis function), and in the power basis
 //   a_T = 2^|T| sum_{S contains T} (-1)^(|S|-|T|) c_S.
-// c_S is exactly 0 unless every variable of S occurs in some term, so the
-// fit of a degree-D polynomial has degree <= min(n, D).
+// c_S is exactly 0 unless some term contains every variable of S (a factor
+// e_k = 0 in its weight vanishes otherwise), so the fit of a degree-D
+// polynomial has degree <= min(n, D).
 //
 // Soundness does not depend on the fit: A enters the bound exactly as stored
 // (float32).  The residual coefficients are rounded up (upper) or down
