@@ -81,8 +81,9 @@ struct bern_ctx {
   Tuner tuner;
   int autotune = 1;
   std::set<std::string> tuned;     // plan signatures already tuned
-  Launch launch() { return Launch{stream, d_status, &launches, &tuner}; }
-  Launch launch_on(cudaStream_t s) { return Launch{s, d_status, &launches, &tuner}; }
+  int sms = 0;                      // multiprocessors of the device
+  Launch launch() { return Launch{stream, d_status, &launches, &tuner, sms}; }
+  Launch launch_on(cudaStream_t s) { return Launch{s, d_status, &launches, &tuner, sms}; }
 };
 
 namespace {
@@ -280,6 +281,7 @@ int ensure_queues(bern_ctx* c, int64_t items, ComposeScratch* out, size_t horner
   out->hws = nullptr;
   out->hws_floats = 0;
   out->horner_smem_limit = c->horner_smem_limit;
+  out->hws_blocks = kHornerGlobalPerSM * std::max(1, c->sms);
   if (horner_floats) {
     if ((e = c->hbuf.reserve(horner_floats * sizeof(float))) != cudaSuccess) return map_cuda(e);
     out->hws = (float*)c->hbuf.p;
@@ -663,6 +665,7 @@ int bern_create(bern_ctx** out, int device, void* stream) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
   if (e != cudaSuccess) {
     delete c;
     return map_cuda(e);
@@ -865,7 +868,8 @@ int bern_compose(bern_ctx* c, int n, int64_t n_boxes, int h, int degree_cap, flo
     const int Dout = std::min(degree_cap, global_d * Dmax);
     const size_t per_block = horner_smem_floats(*T, Dmax, Dout);
     if (per_block == SIZE_MAX || per_block > ((size_t)64 << 20)) return BERN_E_UNSUPPORTED;
-    horner_floats = horner_global_floats(*T, Dmax, Dout, c->horner_smem_limit);
+    horner_floats = horner_global_floats(*T, Dmax, Dout, c->horner_smem_limit,
+                                         kHornerGlobalPerSM * std::max(1, c->sms));
   }
   ComposeScratch CS;
   if ((rc = ensure_queues(c, std::max<int64_t>(1, n_boxes * h), &CS, horner_floats))) return rc;
@@ -914,8 +918,9 @@ int bern_propagate_traced(bern_ctx* c, const bern_net* net, const float* boxes,
     if ((rc = ensure_prod_tables(c, P.n, l.D_pre, l.d, P.cap))) return rc;
     const size_t per_block = horner_smem_floats(*T, l.D_pre, l.D_post);
     if (per_block == SIZE_MAX || per_block > ((size_t)64 << 20)) return BERN_E_UNSUPPORTED;
-    horner_floats = std::max(horner_floats, horner_global_floats(*T, l.D_pre, l.D_post,
-                                                                 c->horner_smem_limit));
+    horner_floats = std::max(horner_floats,
+                             horner_global_floats(*T, l.D_pre, l.D_post, c->horner_smem_limit,
+                                                  kHornerGlobalPerSM * std::max(1, c->sms)));
   }
 
   const bool host = c->mem_mode == BERN_MEM_HOST;

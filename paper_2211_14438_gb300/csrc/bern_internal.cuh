@@ -146,7 +146,11 @@ struct Launch {
   int* status;                     // device status word
   int64_t* launches;               // host counter
   Tuner* tuner = nullptr;
+  int sms = 0;                     // multiprocessors of the device (0: query it)
 };
+// Multiprocessor count of the launch's device (L.sms, else the current
+// device's attribute); grids of persistent kernels are multiples of it.
+int device_sms(const Launch& L);
 
 // Variant of `kind` to run for `key` (dflt when untuned).
 int tune_variant(const Launch& L, const char* kind, const std::string& key, int dflt);
@@ -215,10 +219,12 @@ struct ComposeScratch {
   int* queue;        // kComposeQueues * qcap item indices
   int64_t qcap;
   float* hws = nullptr;      // Horner buffers in global memory (polynomials too
-  int64_t hws_floats = 0;    // large for shared memory), kHornerGlobalBlocks slices
+  int64_t hws_floats = 0;    // large for shared memory), hws_blocks slices
+  int hws_blocks = 0;        // blocks of the global-workspace Horner launch
   int64_t horner_smem_limit = 200 * 1024;   // bytes of shared memory before hws is used
 };
-constexpr int kHornerGlobalBlocks = 152 * 2;
+// Blocks of the global-workspace Horner launch: two per multiprocessor.
+constexpr int kHornerGlobalPerSM = 2;
 // Enclosure with a Bernstein order per box (box_order[b]); `orders` lists
 // every value box_order may take (at most kOrderQueues).  Items are sorted
 // into one list per order in S, then each order runs on its list.

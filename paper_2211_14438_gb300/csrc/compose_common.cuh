@@ -51,9 +51,10 @@ __device__ __forceinline__ int degree_of(const Tables& T, int m) {
 // <= Dmax and outputs of degree <= Dout (host functions; the sizes come from
 // num_monomials, never from the device tables).
 size_t horner_smem_floats(const Tables& T, int Dmax, int Dout);
-// Global workspace floats (ComposeScratch::hws) the Horner kernel needs, 0
-// when its buffers fit `smem_limit` bytes of shared memory.
-size_t horner_global_floats(const Tables& T, int Dmax, int Dout, int64_t smem_limit);
+// Global workspace floats (ComposeScratch::hws) the Horner kernel needs with
+// `blocks` workspace slices, 0 when its buffers fit `smem_limit` bytes of
+// shared memory.
+size_t horner_global_floats(const Tables& T, int Dmax, int Dout, int64_t smem_limit, int blocks);
 cudaError_t launch_compose_horner(const Launch& L, const Tables& T, const ComposeScratch& S,
                                   const ComposeArgs& A, int Dmax, int Dout);
 

@@ -836,7 +836,7 @@ cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
       const int max_sm = v == 0 ? 4 : (v == 2 ? 6 : 8);
       int per_sm = (int)std::min<size_t>(max_sm, (220 * 1024) / (wsmem + 1024));
       if (per_sm < 1) per_sm = 1;
-      const int64_t blocks = std::min<int64_t>(n_boxes, 152 * per_sm);
+      const int64_t blocks = std::min<int64_t>(n_boxes, device_sms(L) * per_sm);
       kern<<<(unsigned)blocks, kWThreads, wsmem, L.stream>>>(
           n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld, in_nterms, out_up, out_lo, out_ld,
           out_nterms, L.status);
@@ -857,7 +857,7 @@ cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
           k_affine_short, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem);
       if (e != cudaSuccess) return e;
       const int per_sm = ssmem <= 54 * 1024 ? 4 : (ssmem <= 72 * 1024 ? 3 : (ssmem <= 110 * 1024 ? 2 : 1));
-      const int64_t blocks = std::min<int64_t>((n_boxes + 3) / 4, 152 * per_sm);
+      const int64_t blocks = std::min<int64_t>((n_boxes + 3) / 4, device_sms(L) * per_sm);
       k_affine_short<<<(unsigned)blocks, kWThreads, ssmem, L.stream>>>(
           n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld, in_nterms, out_up, out_lo, out_ld,
           out_nterms, L.status);

@@ -539,16 +539,16 @@ cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratc
     if (e != cudaSuccess) return e;
   }
   const int64_t tasks = n_items / 32 + row_dmax + 1;
-  const int blocks = (int)std::min<int64_t>(tasks, 152 * kRowBlocks);
+  const int blocks = (int)std::min<int64_t>(tasks, device_sms(L) * kRowBlocks);
   k_compose_rows<true><<<blocks, 32 * kRowWarps, smem, L.stream>>>(T, A, S, row_dmax, sstride,
                                                                    L.status);
   k_compose_rows<false><<<blocks, 32 * kRowWarps, smem, L.stream>>>(T, A, S, row_dmax, sstride,
                                                                     L.status);
   *L.launches += 2;
-  k_compose_copy<<<(unsigned)std::min<int64_t>((n_items + 31) / 32, 152 * 16), 256, 0,
+  k_compose_copy<<<(unsigned)std::min<int64_t>((n_items + 31) / 32, device_sms(L) * 16), 256, 0,
                    L.stream>>>(A, S);
   ++*L.launches;
-  k_compose_linear<<<(unsigned)std::min<int64_t>((n_items + 7) / 8, 152 * 16), 256, 0,
+  k_compose_linear<<<(unsigned)std::min<int64_t>((n_items + 7) / 8, device_sms(L) * 16), 256, 0,
                      L.stream>>>(A, S, L.status);
   ++*L.launches;
   // pair-list kernel for order-2 items beyond the row path
@@ -560,7 +560,7 @@ cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratc
                                (int)psmem);
       if (e != cudaSuccess) return e;
     }
-    k_compose_pairs<<<(unsigned)std::min<int64_t>(n_items, 152 * 8), 256, psmem, L.stream>>>(
+    k_compose_pairs<<<(unsigned)std::min<int64_t>(n_items, device_sms(L) * 8), 256, psmem, L.stream>>>(
         T, A, S, L.status);
     ++*L.launches;
   }

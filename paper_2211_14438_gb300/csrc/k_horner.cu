@@ -218,10 +218,10 @@ size_t horner_smem_floats(const Tables& T, int Dmax, int Dout) {
   return (size_t)ms + 4 * (size_t)mq;
 }
 
-size_t horner_global_floats(const Tables& T, int Dmax, int Dout, int64_t smem_limit) {
+size_t horner_global_floats(const Tables& T, int Dmax, int Dout, int64_t smem_limit, int blocks) {
   const size_t f = horner_smem_floats(T, Dmax, Dout);
   if (f == SIZE_MAX || (int64_t)(f * sizeof(float)) <= smem_limit) return 0;
-  return f * kHornerGlobalBlocks;
+  return f * (size_t)blocks;
 }
 
 cudaError_t launch_compose_horner(const Launch& L, const Tables& T, const ComposeScratch& S,
@@ -230,9 +230,9 @@ cudaError_t launch_compose_horner(const Launch& L, const Tables& T, const Compos
   if (floats == SIZE_MAX) return cudaErrorInvalidValue;
   const int ms_cap = (int)num_monomials(T.n, Dmax), mq_cap = (int)num_monomials(T.n, Dout);
   if ((int64_t)(floats * sizeof(float)) > std::min<int64_t>(S.horner_smem_limit, 200 * 1024)) {
-    if (!S.hws || S.hws_floats < (int64_t)(floats * kHornerGlobalBlocks))
+    if (!S.hws || S.hws_blocks < 1 || S.hws_floats < (int64_t)(floats * S.hws_blocks))
       return cudaErrorInvalidValue;
-    k_compose_horner<<<kHornerGlobalBlocks, kHornerThreads, 0, L.stream>>>(
+    k_compose_horner<<<S.hws_blocks, kHornerThreads, 0, L.stream>>>(
         T, A, S, ms_cap, mq_cap, S.hws, (int64_t)floats, L.status);
     ++*L.launches;
     return cudaGetLastError();
@@ -244,7 +244,7 @@ cudaError_t launch_compose_horner(const Launch& L, const Tables& T, const Compos
     if (e != cudaSuccess) return e;
   }
   const int per_sm = std::max(1, std::min(8, (int)((228 * 1024) / (smem + 1024))));
-  k_compose_horner<<<152 * per_sm, kHornerThreads, smem, L.stream>>>(T, A, S, ms_cap, mq_cap,
+  k_compose_horner<<<device_sms(L) * per_sm, kHornerThreads, smem, L.stream>>>(T, A, S, ms_cap, mq_cap,
                                                                       nullptr, 0, L.status);
   ++*L.launches;
   return cudaGetLastError();

@@ -105,7 +105,7 @@ cudaError_t launch_trace(const Launch& L, int64_t n_boxes, int h, int64_t n_hidd
                          const uint8_t* deg, int global_d, const bern_trace& tr) {
   const int64_t n = n_boxes * h;
   if (n == 0) return cudaSuccess;
-  const int64_t g = std::min<int64_t>((n + 255) / 256, 152 * 8);
+  const int64_t g = std::min<int64_t>((n + 255) / 256, device_sms(L) * 8);
   k_trace<<<(unsigned)g, 256, 0, L.stream>>>(n_boxes, h, n_hidden, off, lo, hi, nt, deg,
                                               global_d, tr);
   ++*L.launches;
@@ -173,7 +173,7 @@ cudaError_t launch_split_features(const Launch& L, const Tables& T, int64_t n_bo
                                   const float* boxes, const float* root, const bern_result& res,
                                   float* x) {
   if (n_boxes == 0) return cudaSuccess;
-  const unsigned g = (unsigned)std::min<int64_t>(n_boxes, 152 * 16);
+  const unsigned g = (unsigned)std::min<int64_t>(n_boxes, device_sms(L) * 16);
   k_split_features<<<g, 128, 0, L.stream>>>(T, n_boxes, o, j, boxes, root, res, x, L.status);
   ++*L.launches;
   return cudaGetLastError();

@@ -308,7 +308,7 @@ static unsigned grid_for(int64_t n, int threads, int cap) {
 cudaError_t launch_degree_features(const Launch& L, int64_t n_items, const float* lo,
                                    const float* hi, const int32_t* nterms, int layer, float* x) {
   if (n_items == 0) return cudaSuccess;
-  k_degree_features<<<grid_for(n_items, 128, 152 * 32), 128, 0, L.stream>>>(n_items, lo, hi,
+  k_degree_features<<<grid_for(n_items, 128, device_sms(L) * 32), 128, 0, L.stream>>>(n_items, lo, hi,
                                                                            nterms, layer, x);
   ++*L.launches;
   return cudaGetLastError();
@@ -322,7 +322,7 @@ cudaError_t launch_learned_degrees(const Launch& L, const MlpView& M, int64_t n_
                                    float* coef, float* eps) {
   if (n_boxes == 0) return cudaSuccess;
   if (M.F != kDegFeatures || M.C != kDegClasses) return cudaErrorInvalidValue;
-  k_learned_degrees<<<grid_for(n_boxes, 1, 152 * 16), 128, 0, L.stream>>>(
+  k_learned_degrees<<<grid_for(n_boxes, 1, device_sms(L) * 16), 128, 0, L.stream>>>(
       M, n_boxes, h, layer, lo, hi, pre_nterms, min_conf, fallback_d, max_d, cap, order_in,
       order_out,
       degrees, kind, coef, eps, L.status);
@@ -332,7 +332,7 @@ cudaError_t launch_learned_degrees(const Launch& L, const MlpView& M, int64_t n_
 
 cudaError_t launch_fill_i32(const Launch& L, int32_t* p, int64_t n, int32_t v) {
   if (n == 0) return cudaSuccess;
-  k_fill_i32<<<grid_for(n, 256, 152 * 8), 256, 0, L.stream>>>(p, n, v);
+  k_fill_i32<<<grid_for(n, 256, device_sms(L) * 8), 256, 0, L.stream>>>(p, n, v);
   ++*L.launches;
   return cudaGetLastError();
 }
@@ -340,7 +340,7 @@ cudaError_t launch_fill_i32(const Launch& L, int32_t* p, int64_t n, int32_t v) {
 cudaError_t launch_mlp_forward(const Launch& L, const MlpView& M, int64_t n, const float* x,
                                float* logits) {
   if (n == 0) return cudaSuccess;
-  k_mlp_forward<<<grid_for(n, 128, 152 * 16), 128, 0, L.stream>>>(M, n, x, logits);
+  k_mlp_forward<<<grid_for(n, 128, device_sms(L) * 16), 128, 0, L.stream>>>(M, n, x, logits);
   ++*L.launches;
   return cudaGetLastError();
 }
@@ -351,7 +351,7 @@ cudaError_t launch_mlp_backward(const Launch& L, const MlpView& M, int64_t n, co
   if (n <= 0) return cudaErrorInvalidValue;
   const int64_t P = mlp_num_params(M.F, M.C);
   BackScratch B = carve(scratch, n, M.C, P);
-  k_mlp_back_samples<<<grid_for(n, 128, 152 * 16), 128, 0, L.stream>>>(M, n, x, labels, w, B,
+  k_mlp_back_samples<<<grid_for(n, 128, device_sms(L) * 16), 128, 0, L.stream>>>(M, n, x, labels, w, B,
                                                                        L.status);
   const int chunks = chunks_of(n);
   dim3 g2((unsigned)((P + 1 + 127) / 128), (unsigned)chunks);

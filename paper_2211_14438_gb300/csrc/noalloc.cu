@@ -41,6 +41,7 @@ struct DeviceSlot {
   unsigned char* scratch = nullptr;   // device address of g_scratch on this device
   unsigned char* tables = nullptr;
   int* status = nullptr;
+  int sms = 0;                        // multiprocessors of the device
   int table_n = -1, table_dmax = -1;  // which tables g_tables currently holds
   bern::Tables view{};
   int64_t launches = 0;
@@ -64,6 +65,8 @@ int setup_device(int dev, DeviceSlot** out) {
     s.tables = (unsigned char*)p;
     if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return BERN_E_CUDA;
     s.status = (int*)p;
+    if (cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return BERN_E_CUDA;
     s.ready = true;
   }
   *out = &s;
@@ -172,6 +175,54 @@ int upload_tables(DeviceSlot& s, int n, int dmax, int deg_exps, cudaStream_t str
   return BERN_OK;
 }
 
+// Bytes of the table image upload_tables would build, from the monomial
+// counts alone (every table's length is fixed by n and the degrees), so that
+// a plan whose tables cannot fit is rejected before any of them is built.
+// Returns SIZE_MAX when a count overflows.
+size_t table_image_bytes(int n, int dmax, int deg_exps) {
+  size_t total = 0;
+  bool bad = false;
+  auto add = [&](double bytes) {
+    if (!(bytes >= 0.0) || bytes > 1e15) {
+      bad = true;
+      return;
+    }
+    total = align256(total) + (size_t)bytes;
+  };
+  auto M = [&](int nn, int D) -> double {
+    const int64_t m = bern::num_monomials(nn, D);
+    if (m < 0) bad = true;
+    return (double)m;
+  };
+  add(4.0 * (bern::kMaxTableDegree + 1));                 // M(n, D) counts
+  add(M(n, deg_exps) * n);                                // graded exponents
+  add(M(n, deg_exps) + 1);                                // degree of a prefix length
+  const int rmax = bern::max_enclose_order(n);
+  for (int l = 0; l <= rmax; ++l) {
+    double lines = 1.0;
+    for (int k = 0; k < n - 1; ++k) lines *= (l + 1);
+    add(8.0 * M(n, l));                                   // reciprocal brackets
+    add(4.0 * M(n, l));                                   // grid index per rank
+    add(8.0 * n * lines);                                 // line bases and digit sums
+  }
+  const int row_dmax = std::min(bern::kMaxRowDegree, bern::row_path_max_degree(n));
+  for (int D = 0; D <= row_dmax; ++D) {
+    const double np_out = n == 1 ? 1.0 : M(n - 1, 2 * D);
+    const double np_in = n == 1 ? 1.0 : M(n - 1, D);
+    add(4.0 * M(n, D));                                   // row-layout positions
+    add(16.0 * np_out);                                   // row headers
+    add(4.0 * np_out);                                    // input-row offsets
+    add(16.0 * np_in * (np_in + 1) / 2);                  // row pairs
+    add(4.0 * M(n, 2 * D));                               // output ranks
+  }
+  for (int D = 0; D <= dmax; ++D) {
+    const double m = M(n, D);
+    add(4.0 * (M(n, 2 * D) + 1));                         // pair pointers
+    add(4.0 * m * (m + 1) / 2);                           // square pairs
+  }
+  return bad ? SIZE_MAX : total;
+}
+
 struct NaLayer {
   int h_in, h_out, d, D_pre, D_post, order;
   int64_t M_pre, M_post;
@@ -262,6 +313,8 @@ extern "C" int bern_propagate_noalloc(const bern_net* net, const float* boxes, i
   const size_t per_box = off;
   const size_t counters = 256;   // composition queue counters, ahead of the per-box regions
   if (per_box + counters > kNoAllocScratchBytes) return BERN_E_UNSUPPORTED;   // one box must fit
+  // the tables' size follows from the plan: reject before building any of them
+  if (table_image_bytes(n, dsq, dexp) > kNoAllocTableBytes) return BERN_E_UNSUPPORTED;
   const int64_t chunk =
       std::min<int64_t>(n_boxes, (int64_t)((kNoAllocScratchBytes - counters) / per_box));
 
@@ -276,7 +329,7 @@ extern "C" int bern_propagate_noalloc(const bern_net* net, const float* boxes, i
   if (rc) return rc;
   // the status word keeps the previous call's value: clear it first
   if (cudaMemsetAsync(s->status, 0, sizeof(int), stream) != cudaSuccess) return BERN_E_CUDA;
-  bern::Launch La{stream, s->status, &s->launches};
+  bern::Launch La{stream, s->status, &s->launches, nullptr, s->sms};
   const bern::Tables& T = s->view;
 
   for (int64_t b0 = 0; b0 < n_boxes; b0 += chunk) {
@@ -327,11 +380,18 @@ extern "C" int bern_propagate_noalloc(const bern_net* net, const float* boxes, i
       in_nt = qn;
       in_stride = l.M_post;
     }
-    if (e != cudaSuccess) return BERN_E_CUDA;
+    if (e != cudaSuccess) {
+      // launches already queued may still use the shared arrays: let them
+      // finish before the lock is released
+      cudaStreamSynchronize(stream);
+      return BERN_E_CUDA;
+    }
   }
   int st = 0;
-  if (cudaMemcpyAsync(&st, s->status, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+  if (cudaMemcpyAsync(&st, s->status, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess) {
+    cudaStreamSynchronize(stream);
     return BERN_E_CUDA;
+  }
   if (cudaStreamSynchronize(stream) != cudaSuccess) return BERN_E_CUDA;
   if (st & bern::kStatusInvalid) return BERN_E_INVALID;
   if (st & bern::kStatusUnsupported) return BERN_E_UNSUPPORTED;

@@ -329,6 +329,15 @@ void build_enclose_tables(int n, int l, std::vector<int32_t>& gidx, std::vector<
 
 namespace bern {
 
+int device_sms(const Launch& L) {
+  if (L.sms > 0) return L.sms;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    return 1;
+  return sms;
+}
+
 int tune_variant(const Launch& L, const char* kind, const std::string& key, int dflt) {
   if (!L.tuner) return dflt;
   if (!L.tuner->probe_kind.empty())
