@@ -210,6 +210,17 @@ int bern_sync(bern_ctx* ctx);
  * every kernel node of the graph). */
 int64_t bern_kernel_launches(const bern_ctx* ctx);
 
+/* Measured FP32 fused multiply-add throughput of `device` in TFLOP/s (two
+ * flops per FMA), the denominator of the kernels' arithmetic rooflines.  The
+ * paper has no counterpart: it is the measured peak of the CUDA-core FMA
+ * pipe that the bound kernels use.  Every resident thread runs eight
+ * independent FMA chains; directed != 0 measures round-up FMAs (as the bound
+ * kernels issue), 0 round-to-nearest.  The fastest of `reps` launches (after
+ * one warm-up) on `stream` (a cudaStream_t, NULL = legacy default stream);
+ * synchronises the stream.  Returns BERN_OK, BERN_E_INVALID (reps < 1 or
+ * tflops NULL) or BERN_E_CUDA. */
+int bern_fp32_fma_rate(int device, void* stream, int directed, int reps, double* tflops);
+
 /* ------------------------------------------------------------ tables */
 
 /* M(n, D) = C(n+D, n), the number of monomials of total degree <= D in n

@@ -133,7 +133,9 @@ def test_affine_step(ctx, n, D, h_in, h_out, B):
 # ---------------------------------------------------------------- a2
 @pytest.mark.parametrize("n,D,order,budget", [
     (1, 6, 6, 0), (2, 4, 4, 0), (2, 4, 7, 0), (3, 8, 8, 0), (3, 8, 16, 0), (3, 6, 4, 0),
-    (4, 4, 4, 0), (4, 8, 8, 0), (3, 8, 8, 100), (5, 2, 2, 0), (2, 1, 1, 0)])
+    (4, 4, 4, 0), (4, 8, 8, 0), (3, 8, 8, 100), (5, 2, 2, 0), (2, 1, 1, 0),
+    # six inputs at order 8 (the branch-and-bound network's fourth hidden layer)
+    (6, 8, 8, 0)])
 def test_enclose_step(ctx, n, D, order, budget):
     rng = np.random.default_rng(7 * n + D + order)
     M = bern.num_monomials(n, D)
