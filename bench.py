@@ -475,8 +475,8 @@ def run_ours(args, rank, world, local_rank, dist):
                     * 1e6 / 1e12)
     # the FP32 roof is measured: round-up FMAs (what the bound kernels issue)
     # on every resident thread, fastest of five launches
-    fp32_peak = bern.fp32_fma_rate(local_rank, stream, directed=True, reps=5)
-    fp32_rn = bern.fp32_fma_rate(local_rank, stream, directed=False, reps=5)
+    fp32_peak = bern.fma_throughput(local_rank, stream, directed=True, reps=5)
+    fp32_rn = bern.fma_throughput(local_rank, stream, directed=False, reps=5)
     wk = work.get(dom, {"bytes": 0.0, "flops": 0.0})
     sec = avg[dom] / 1e3
     gbs = wk["bytes"] / sec / 1e9
@@ -493,7 +493,7 @@ def run_ours(args, rank, world, local_rank, dist):
     roof["kernel"] = dom
     roof["peak_source"] = ("%s (%s)" % (PEAKS_FILE.split("/")[-1], peak_kind)
                            if roof["bound"] == "hbm" else
-                           "measured: bern_fp32_fma_rate, round-up FMAs, 8 chains per thread "
+                           "measured: bern_fma_throughput, round-up FMAs, 8 chains per thread "
                            "on every resident thread (nominal %d SMs x 128 lanes x 2 x %.0f MHz "
                            "= %.1f TFLOP/s)" % (sm_count, float(peaks.get("sm_max_mhz", 2070.0)),
                                                 fp32_nominal))

@@ -219,7 +219,7 @@ int64_t bern_kernel_launches(const bern_ctx* ctx);
  * one warm-up) on `stream` (a cudaStream_t, NULL = legacy default stream);
  * synchronises the stream.  Returns BERN_OK, BERN_E_INVALID (reps < 1 or
  * tflops NULL) or BERN_E_CUDA. */
-int bern_fp32_fma_rate(int device, void* stream, int directed, int reps, double* tflops);
+int bern_fma_throughput(int device, void* stream, int directed, int reps, double* tflops);
 
 /* ------------------------------------------------------------ tables */
 

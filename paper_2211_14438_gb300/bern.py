@@ -52,7 +52,7 @@ EXPORTS = [
     "bern_mlp_num_params", "bern_degree_features", "bern_mlp_forward", "bern_mlp_backward",
     "bern_mlp_adam", "bern_propagate_traced", "bern_split_features",
     "bern_set_horner_smem_limit", "bern_set_autotune", "bern_force_variant",
-    "bern_poly_to_x", "bern_linearize", "bern_fp32_fma_rate",
+    "bern_poly_to_x", "bern_linearize", "bern_fma_throughput",
 ]
 
 
@@ -124,7 +124,7 @@ def load(build_if_missing: bool = True):
         "bern_strerror": (ctypes.c_char_p, [I]),
         "bern_sync": (I, [V]),
         "bern_kernel_launches": (I64, [V]),
-        "bern_fp32_fma_rate": (I, [I, V, I, I, ctypes.POINTER(ctypes.c_double)]),
+        "bern_fma_throughput": (I, [I, V, I, I, ctypes.POINTER(ctypes.c_double)]),
         "bern_num_monomials": (I64, [I, I]),
         "bern_monomials": (I, [I, I, V]),
         "bern_propagate": (I, [V, ctypes.POINTER(bern_net), V, I64,
@@ -166,12 +166,12 @@ def _check(code: int, where: str):
         raise BernError(code, where)
 
 
-def fp32_fma_rate(device: int = 0, stream=None, directed: bool = True, reps: int = 5) -> float:
-    """Measured FP32 FMA throughput of the device in TFLOP/s (bern_fp32_fma_rate)."""
+def fma_throughput(device: int = 0, stream=None, directed: bool = True, reps: int = 5) -> float:
+    """Measured FP32 FMA throughput of the device in TFLOP/s (bern_fma_throughput)."""
     out = ctypes.c_double(0.0)
     h = 0 if stream is None else int(stream.cuda_stream)
-    _check(load().bern_fp32_fma_rate(int(device), ctypes.c_void_p(h), 1 if directed else 0,
-                                     int(reps), ctypes.byref(out)), "bern_fp32_fma_rate")
+    _check(load().bern_fma_throughput(int(device), ctypes.c_void_p(h), 1 if directed else 0,
+                                     int(reps), ctypes.byref(out)), "bern_fma_throughput")
     return float(out.value)
 
 

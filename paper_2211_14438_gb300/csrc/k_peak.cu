@@ -38,7 +38,7 @@ k_fma_rate(int iters, float m, float c) {
 
 }  // namespace
 
-extern "C" int bern_fp32_fma_rate(int device, void* stream_handle, int directed, int reps,
+extern "C" int bern_fma_throughput(int device, void* stream_handle, int directed, int reps,
                                   double* tflops) {
   if (!tflops || reps < 1) return BERN_E_INVALID;
   *tflops = 0.0;
