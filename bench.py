@@ -158,14 +158,21 @@ class ClockSampler:
 
 # ----------------------------------------------------- per-kernel timing pass
 class KernelPass:
-    """Drives the same kernels as bern_propagate through the step-level C ABI
-    on torch-allocated buffers, with CUDA events around every launch on the
-    launching stream; keeps the intermediates for algorithmic-work counts."""
+    """Drives the kernels bern_propagate runs for this workload through the
+    step-level C ABI on torch-allocated buffers, with CUDA events around every
+    launch on the launching stream: init, the first layer's affine step, one
+    fused launch per hidden layer (bern_layer: enclosure, ReLU coefficients,
+    composition and the next layer's affine step) and the output enclosure.
+    A separate pass through the per-step kernels (bern_enclose,
+    bern_relu_coeffs, bern_compose, bern_affine) supplies the ReLU cases and
+    term counts for the algorithmic-work counts; with fused=False that pass is
+    the one timed (the per-step path)."""
 
-    def __init__(self, ctx, torch, w, Wd, bd, boxes_d):
+    def __init__(self, ctx, torch, w, Wd, bd, boxes_d, fused=True):
         from paper_2211_14438_gb300 import bern
         self.bern, self.torch, self.ctx = bern, torch, ctx
         self.w, self.Wd, self.bd, self.boxes = w, Wd, bd, boxes_d
+        self.fused = fused
         widths = w.net.widths
         self.n, self.B, self.H = widths[0], len(w.boxes), len(widths) - 1
         dev = boxes_d.device
@@ -210,6 +217,34 @@ class KernelPass:
         self.pending.append((name, s, e))
 
     def step(self):
+        if self.fused:
+            self.step_fused()
+        else:
+            self.step_per_kernel()
+
+    def step_fused(self):
+        ctx, w = self.ctx, self.w
+        n, B = self.n, self.B
+        self.pending = []
+        self._timed("init", lambda: ctx.init_inputs(n, self.boxes, self.z[0], self.z[1], n + 1,
+                                                    self.znt))
+        L0 = self.layers[0]
+        self._timed("affine_L1", lambda: ctx.affine(
+            B, L0["h"], L0["h_in"], self.Wd[0], self.bd[0], self.z[0], self.z[1], n + 1,
+            self.znt, L0["pre"][0], L0["pre"][1], L0["Mpre"], L0["pre_nt"]))
+        for i, L in enumerate(self.layers):
+            if not L["hidden"]:
+                self._timed("enclose_L%d" % (i + 1), lambda: ctx.enclose(
+                    n, B, L["h"], L["order"], 0, L["pre"][0], L["pre"][1], L["Mpre"],
+                    L["pre_nt"], L["lo"], L["hi"]))
+                break
+            N = self.layers[i + 1]
+            self._timed("layer_L%d" % (i + 1), lambda: ctx.layer(
+                n, B, L["h"], L["order"], 0, w.degree, w.degree_cap, L["pre"][0], L["pre"][1],
+                L["Mpre"], L["pre_nt"], N["h"], self.Wd[i + 1], self.bd[i + 1], N["pre"][0],
+                N["pre"][1], N["Mpre"], N["pre_nt"]))
+
+    def step_per_kernel(self):
         ctx, w = self.ctx, self.w
         n, B = self.n, self.B
         self.pending = []
@@ -240,9 +275,18 @@ class KernelPass:
 
     def work(self):
         """Algorithmic bytes and flops per launch of every kernel, from the
-        intermediates of the last step (actual term counts and ReLU cases)."""
+        intermediates of a per-step pass (actual term counts and ReLU cases).
+        Bytes: every polynomial coefficient a launch must read or write once
+        (both bounds, float32).  Flops: two per fused multiply-add of the
+        method's arithmetic (the sign-split layer step: one FMA per product
+        and bound; the enclosure's line transforms; the square's pair
+        products and the ReLU polynomial's terms)."""
         bern = self.bern
         n, B = self.n, self.B
+        saved = self.pending if hasattr(self, "pending") else []
+        self.step_per_kernel()                       # fills the intermediates
+        self.torch.cuda.synchronize()
+        self.pending = saved
         out = {}
         in_nt = self.znt.cpu().numpy().reshape(B, n).astype(np.int64)
         for i, L in enumerate(self.layers):
@@ -251,12 +295,13 @@ class KernelPass:
             Mb = pre_nt[:, 0]
             rd = 2 * 4 * in_nt.sum()
             wr = 2 * 4 * h * Mb.sum()
-            out["affine_L%d" % (i + 1)] = {"bytes": float(rd + wr),
-                                           "flops": float(4 * h * in_nt.sum())}
+            affine = {"bytes": float(rd + wr), "flops": float(4 * h * in_nt.sum())}
+            out["affine_L%d" % (i + 1)] = affine
             lb = L["order"]
             g_lines = n * (lb + 1) ** (n - 1) * lb * (lb + 1) // 2
-            out["enclose_L%d" % (i + 1)] = {"bytes": float(2 * 4 * pre_nt.sum() + 8 * B * h),
-                                            "flops": float(2 * B * h * g_lines)}
+            enc = {"bytes": float(2 * 4 * pre_nt.sum() + 8 * B * h),
+                   "flops": float(2 * B * h * g_lines)}
+            out["enclose_L%d" % (i + 1)] = enc
             if not L["hidden"]:
                 break
             kind = L["kind"].cpu().numpy().reshape(B, h)
@@ -267,11 +312,21 @@ class KernelPass:
             wr = 2 * 4 * (post_nt[act].sum() + post_nt[unst].sum())
             Mp = pre_nt[unst]
             pairs = (Mp * (Mp + 1) // 2).sum()
-            out["compose_L%d" % (i + 1)] = {"bytes": float(rd + wr),
-                                            "flops": float(2 * 2 * pairs + 2 * 2 * post_nt[unst].sum()),
+            comp_flops = float(2 * 2 * pairs + 2 * 2 * post_nt[unst].sum())
+            out["compose_L%d" % (i + 1)] = {"bytes": float(rd + wr), "flops": comp_flops,
                                             "unstable": int(unst.sum()), "active": int(act.sum()),
                                             "items": int(B * h)}
             out["relu_L%d" % (i + 1)] = {"bytes": float(8 * B * h + 41 * unst.sum()), "flops": 0.0}
+            # the fused launch: reads this layer's block, writes the next one; its
+            # flops are the enclosures of the unstable items, their compositions
+            # and the next layer's step over the live (active or unstable) items
+            hn = self.layers[i + 1]["h"]
+            Mn = post_nt.max(axis=1).clip(min=1)
+            live_nt = (post_nt * (act | unst)).sum()
+            out["layer_L%d" % (i + 1)] = {
+                "bytes": float(2 * 4 * pre_nt.sum() + 2 * 4 * hn * Mn.sum()),
+                "flops": float(2 * 2 * unst.sum() * g_lines) + comp_flops + float(4 * hn * live_nt),
+                "unstable": int(unst.sum()), "active": int(act.sum()), "items": int(B * h)}
             in_nt = post_nt
         out["init"] = {"bytes": float(B * n * 8 + 2 * B * n * (n + 1) * 4), "flops": 0.0}
         return out
@@ -283,7 +338,7 @@ def source_sha(path):
 
 
 KERNEL_SOURCES = {"affine": "k_affine.cu", "enclose": "k_enclose.cu", "compose": "k_compose.cu",
-                  "relu": "k_enclose.cu", "init": "k_io.cu"}
+                  "relu": "k_enclose.cu", "init": "k_io.cu", "layer": "k_layer.cu"}
 
 
 def ncu_traffic(kernel_key):
@@ -408,6 +463,9 @@ def run_ours(args, rank, world, local_rank, dist):
         ctx.propagate(w.net.widths, Wd, bd, boxes_d, degree=w.degree, cap=w.degree_cap,
                       cap_terms=cap_terms, out=out, sync=False)
 
+    if args.no_fused:
+        ctx.set_fused(False)
+    from paper_2211_14438_gb300.sharding import max_over_ranks
     sampler = ClockSampler(local_rank)
     sampler.start()
     for _ in range(args.warmup):
@@ -438,12 +496,38 @@ def run_ours(args, rank, world, local_rank, dist):
         raise RuntimeError("propagate failed: %s" % bern.strerror(rc))
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms_local = float(np.sum(ms)) / args.steps
-    from paper_2211_14438_gb300.sharding import max_over_ranks
     ms_step = max_over_ranks(ms_local, world, dist, dev)
     value = world * B / (ms_step / 1e3)
 
     lo = out["lo"].cpu().numpy()[:, 0].astype(np.float64)
     hi = out["hi"].cpu().numpy()[:, 0].astype(np.float64)
+
+    # ---- the same step through the per-step kernels (no fused layer launches),
+    # timed the same way: what the fused kernels gain
+    per_step = None
+    if not args.no_fused:
+        ctx.set_fused(False)
+        try:
+            for _ in range(args.warmup):
+                step()
+            torch.cuda.synchronize()
+            for k in range(args.steps):
+                flush.zero_()
+                starts[k].record(stream)
+                step()
+                ends[k].record(stream)
+            torch.cuda.synchronize()
+            if ctx.sync() != 0:
+                raise RuntimeError("per-step path failed")
+            ms_ps = max_over_ranks(float(np.mean([s_.elapsed_time(e_) for s_, e_ in
+                                                  zip(starts, ends)])), world, dist, dev)
+            w_ps = float((out["hi"] - out["lo"]).float().mean().item())
+            per_step = {"ms_per_step": round(ms_ps, 4), "value": round(world * B / (ms_ps / 1e3), 1),
+                        "unit": "boxes/s", "mean_output_width": round(w_ps, 6),
+                        "note": "bern_propagate with bern_set_fused(0): every layer through the "
+                                "per-step kernels"}
+        finally:
+            ctx.set_fused(True)
     nt = out["n_terms"].cpu().numpy()[:, 0, 0]
     coef = out["coef"].cpu().numpy()[:, 0].astype(np.float64)
     ex = bern.monomials(w.net.n_in, w.degree_cap).astype(np.float64)
@@ -452,7 +536,7 @@ def run_ours(args, rank, world, local_rank, dist):
                     for i in range(B)])
 
     # ---- per-kernel pass (same kernels through the step ABI)
-    kp = KernelPass(ctx, torch, w, Wd, bd, boxes_d)
+    kp = KernelPass(ctx, torch, w, Wd, bd, boxes_d, fused=not args.no_fused)
     for _ in range(max(1, args.warmup)):
         kp.step()
     kp.collect()
@@ -690,8 +774,8 @@ def run_ours(args, rank, world, local_rank, dist):
                    "mean_vol_relative": round(float(np.mean(vol)), 6),
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "box-sharded dp%d (each rank its own batch)" % world,
-                   "graphs": True},
-        "roofline": roof, "kernels": kernels,
+                   "graphs": True, "fused_layers": not args.no_fused},
+        "roofline": roof, "kernels": kernels, "per_step_kernels_path": per_step,
         "kernel_pass_ms_per_step": round(total_kernel_ms, 4),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "learned": learned, "learned_6in": learned4, "bnb_6in": bnb5, "lin": lin_res,
@@ -826,6 +910,8 @@ def main():
                     help="skip training and timing the learned-degree form")
     ap.add_argument("--no-lin", action="store_true",
                     help="skip timing the Lin-linearised forms")
+    ap.add_argument("--no-fused", action="store_true",
+                    help="run every layer through the per-step kernels (no fused layer launches)")
     ap.add_argument("--n-boxes", type=int, default=0,
                     help="use N evenly strided boxes of the workload (small cases for ncu)")
     ap.add_argument("--paper-sweeps", action="store_true",

@@ -375,6 +375,43 @@ int bern_compose(bern_ctx* ctx, int n, int64_t n_boxes, int h, int degree_cap,
                  const int32_t* pre_nterms, float* post_up, float* post_lo,
                  int64_t post_ld, int32_t* post_nterms);
 
+/* a2 + a3 + a4 of one hidden layer and a1 of the next, fused: from the
+ * hidden layer's pre-activation block to the next layer's pre-activation
+ * block in one launch (Sec. 5.1 Steps 1-3 per neuron, then the layer step of
+ * Sec. 5.2 with the next layer's weights), for ReLU orders 1 and 2.  Per box:
+ * the stability screen (the coefficient-sign interval of every polynomial,
+ * as bern_propagate applies before the enclosure), the Bernstein enclosure of
+ * the undecided neurons at `order` under `budget` (0 = 2^20), the ReLU case
+ * and coefficients, the composition and the next layer's midpoint-radius
+ * affine step, with the rounding of bern_enclose / bern_relu_coeffs /
+ * bern_compose / bern_affine; the post-activation polynomials stay in shared
+ * memory.
+ *   pre_up, pre_lo, pre_nterms: the hidden layer's block (h neurons,
+ *     leading dimension pre_ld, layout of bern_affine's output);
+ *   W_next [h_next x h] row-major, b_next [h_next]: the next layer;
+ *   next_up, next_lo [n_boxes x next_ld x h_next], next_nterms
+ *     [n_boxes x h_next]: the next layer's pre-activation block, every
+ *     neuron's term count the box's largest post-activation count (as
+ *     bern_affine sets it); next_ld must hold the output degree
+ *     min(global_d * D, degree_cap) (BERN_E_CAPACITY at bern_sync otherwise).
+ * Device pointers; asynchronous on the context's stream.  Shapes the fused
+ * kernel does not cover (global_d > 2, h > 256, an input degree beyond the
+ * row tables, an effective enclosure order above 8, or shared memory) return
+ * BERN_E_UNSUPPORTED before any launch; bern_propagate then uses the
+ * per-step kernels for that layer. */
+int bern_layer(bern_ctx* ctx, int n, int64_t n_boxes, int h, int order, int64_t budget,
+               int global_d, int degree_cap, const float* pre_up, const float* pre_lo,
+               int64_t pre_ld, const int32_t* pre_nterms, int h_next, const float* W_next,
+               const float* b_next, float* next_up, float* next_lo, int64_t next_ld,
+               int32_t* next_nterms);
+
+/* Use the fused layer kernel (bern_layer) inside bern_propagate wherever a
+ * plan allows it (default 1): plain plans (BERN_DEG_GLOBAL or PER_LAYER) with
+ * prune_tau = 0 and lin_every = 0, untraced, layer by layer where the shape
+ * qualifies.  enable = 0 runs the per-step kernels for every layer.  Both
+ * give the same bounds up to the rounding of sums taken in another order. */
+int bern_set_fused(bern_ctx* ctx, int enable);
+
 /* -------------------------------------------- allocation-free variant
  * The paper has no counterpart to this entry point.  It serves callers that
  * may not allocate device memory: a host framework that owns every GPU

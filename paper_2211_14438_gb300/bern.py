@@ -52,7 +52,7 @@ EXPORTS = [
     "bern_mlp_num_params", "bern_degree_features", "bern_mlp_forward", "bern_mlp_backward",
     "bern_mlp_adam", "bern_propagate_traced", "bern_split_features",
     "bern_set_horner_smem_limit", "bern_set_autotune", "bern_force_variant",
-    "bern_poly_to_x", "bern_linearize", "bern_fma_throughput",
+    "bern_poly_to_x", "bern_linearize", "bern_fma_throughput", "bern_layer", "bern_set_fused",
 ]
 
 
@@ -136,6 +136,8 @@ def load(build_if_missing: bool = True):
         "bern_relu_coeffs": (I, [V, I64, V, V, V, I, V, V, V]),
         "bern_compose": (I, [V, I, I64, I, I, F, V, V, V, V, I, V, V, V, V, I64, V, V, V, I64,
                              V]),
+        "bern_layer": (I, [V, I, I64, I, I, I64, I, I, V, V, I64, V, I, V, V, V, V, I64, V]),
+        "bern_set_fused": (I, [V, I]),
         "bern_propagate_noalloc": (I, [ctypes.POINTER(bern_net), V, I64,
                                        ctypes.POINTER(bern_degree_plan),
                                        ctypes.POINTER(bern_result), V]),
@@ -240,6 +242,17 @@ class Context:
         ("affine" or "enclose") for later launches (tests and tuning)."""
         _check(self.lib.bern_force_variant(self.h, kind.encode(), int(variant)),
                "bern_force_variant")
+
+    def set_fused(self, on: bool):
+        _check(self.lib.bern_set_fused(self.h, 1 if on else 0), "bern_set_fused")
+
+    def layer(self, n, n_boxes, h, order, budget, global_d, cap, pre_up, pre_lo, pre_ld,
+              pre_nterms, h_next, W_next, b_next, next_up, next_lo, next_ld, next_nterms):
+        """bern_layer: one fused hidden layer (a2-a4) plus the next layer's a1."""
+        _check(self.lib.bern_layer(self.h, n, n_boxes, h, order, budget, global_d, cap,
+                                   _ptr(pre_up), _ptr(pre_lo), pre_ld, _ptr(pre_nterms), h_next,
+                                   _ptr(W_next), _ptr(b_next), _ptr(next_up), _ptr(next_lo),
+                                   next_ld, _ptr(next_nterms)), "bern_layer")
 
     def set_horner_smem_limit(self, nbytes: int):
         _check(self.lib.bern_set_horner_smem_limit(self.h, int(nbytes)),

@@ -58,6 +58,10 @@ struct GraphEntry {
   int64_t kernels = 0;
 };
 
+// box counters of the fused layer launches (one per launch of a chunk, reused
+// modulo this count: launches on one stream run in order)
+constexpr int kLayerCounters = 64;
+
 int64_t monomials_clamped(int n, int D) {
   int64_t m = num_monomials(n, D);
   return m < 0 ? -1 : m;
@@ -77,11 +81,14 @@ struct bern_ctx {
   int64_t launches = 0;
   std::map<int, TableSet> tables;
   DevBuf ws, stage_in, stage_out, qbuf, mlp_ws, hbuf;
+  DevBuf ctr;                       // box counters of the fused layer kernels
+  int fused = 1;                    // fused layer kernels where a plan allows them
   std::vector<GraphEntry> graphs;
   Tuner tuner;
   int autotune = 1;
   std::set<std::string> tuned;     // plan signatures already tuned
   int sms = 0;                      // multiprocessors of the device
+  int* counters() { return (int*)ctr.p; }
   Launch launch() { return Launch{stream, d_status, &launches, &tuner, sms}; }
   Launch launch_on(cudaStream_t s) { return Launch{s, d_status, &launches, &tuner, sms}; }
 };
@@ -305,6 +312,9 @@ struct LayerPlan {
   // every value it can take
   size_t off_order = 0;
   std::vector<int> orders;
+  // fused hidden layer: one kernel from this layer's pre-activation block to
+  // the next layer's (no post-activation block, lo/hi or coefficients in HBM)
+  bool fused = false;
   // Lin layers (Sec. 5.3): the post-activation bounds are replaced by their
   // multilinear fits shifted by the residual's enclosure at order_post
   bool lin = false;
@@ -332,7 +342,7 @@ struct Plan {
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-int make_plan(const bern_net* net, const bern_degree_plan* dp, Plan& P) {
+int make_plan(const bern_net* net, const bern_degree_plan* dp, Plan& P, bool allow_fused) {
   if (!net || !net->widths || net->n_layers < 1) return BERN_E_INVALID;
   P.H = net->n_layers;
   P.n = net->widths[0];
@@ -434,6 +444,13 @@ int make_plan(const bern_net* net, const bern_degree_plan* dp, Plan& P) {
       if ((int)l.orders.size() > kOrderQueues) return BERN_E_UNSUPPORTED;
     }
   }
+  // fused layers: plain plans (one order per layer), no pruning, no Lin
+  if (allow_fused && !P.learned && !P.per_neuron && P.lin == 0 && P.tau == 0.0f)
+    for (int i = 0; i + 1 < P.H; ++i) {
+      LayerPlan& l = P.L[i];
+      l.fused = layer_fused_shape(P.n, l.h_out, P.L[i + 1].h_out, l.d, l.D_pre, l.order,
+                                  P.budget, P.cap, nullptr);
+    }
   // per-box workspace layout
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -449,6 +466,7 @@ int make_plan(const bern_net* net, const bern_degree_plan* dp, Plan& P) {
     l.off_pre_up = take(sizeof(float) * l.h_out * l.M_pre);
     l.off_pre_lo = take(sizeof(float) * l.h_out * l.M_pre);
     l.off_pre_nt = take(sizeof(int32_t) * l.h_out);
+    if (l.fused) continue;   // everything past the pre-activation block stays on chip
     l.off_lo = take(sizeof(float) * l.h_out);
     l.off_hi = take(sizeof(float) * l.h_out);
     if (l.hidden) {
@@ -506,14 +524,31 @@ int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
     e = launch_fill_i32(L, ch.at<int32_t>(P.L[0].off_order), B, 1);
     if (e != cudaSuccess) return map_cuda(e);
   }
+  bool pre_ready = false;   // this layer's block was written by a fused kernel
+  int fused_idx = 0;
   for (int i = 0; i < P.H; ++i) {
     const LayerPlan& l = P.L[i];
     float* pre_up = ch.at<float>(l.off_pre_up);
     float* pre_lo = ch.at<float>(l.off_pre_lo);
     int32_t* pre_nt = ch.at<int32_t>(l.off_pre_nt);
-    e = launch_affine(L, B, l.h_out, l.h_in, net->W[i], net->b[i], in_up, in_lo, in_stride,
-                      in_nt, pre_up, pre_lo, l.M_pre, pre_nt);
-    if (e != cudaSuccess) return map_cuda(e);
+    if (!pre_ready) {
+      e = launch_affine(L, B, l.h_out, l.h_in, net->W[i], net->b[i], in_up, in_lo, in_stride,
+                        in_nt, pre_up, pre_lo, l.M_pre, pre_nt);
+      if (e != cudaSuccess) return map_cuda(e);
+    }
+    pre_ready = false;
+    if (l.fused) {
+      const LayerPlan& nl = P.L[i + 1];
+      e = launch_layer(L, T, B, l.h_out, l.d, l.order, P.budget, P.cap, pre_up, pre_lo, l.M_pre,
+                       pre_nt, nl.h_out, net->W[i + 1], net->b[i + 1],
+                       ch.at<float>(nl.off_pre_up), ch.at<float>(nl.off_pre_lo), nl.M_pre,
+                       ch.at<int32_t>(nl.off_pre_nt),
+                       c->counters() + (fused_idx++ % kLayerCounters));
+      if (e != cudaSuccess) return map_cuda(e);
+      pre_ready = true;
+      hidden_off += l.h_out;
+      continue;
+    }
     if (!l.hidden) {
       if (P.learned)
         e = launch_enclose_by_order(L, T, CS, B, l.h_out, ch.at<int32_t>(l.off_order), l.orders,
@@ -666,6 +701,7 @@ int bern_create(bern_ctx** out, int device, void* stream) {
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = c->ctr.reserve(kLayerCounters * sizeof(int));
   if (e != cudaSuccess) {
     delete c;
     return map_cuda(e);
@@ -743,6 +779,39 @@ int bern_set_graphs(bern_ctx* c, int enable) {
   if (!c) return BERN_E_INVALID;
   c->use_graphs = enable ? 1 : 0;
   return BERN_OK;
+}
+
+int bern_set_fused(bern_ctx* c, int enable) {
+  if (!c) return BERN_E_INVALID;
+  c->fused = enable ? 1 : 0;
+  return BERN_OK;
+}
+
+int bern_layer(bern_ctx* c, int n, int64_t n_boxes, int h, int order, int64_t budget,
+               int global_d, int degree_cap, const float* pre_up, const float* pre_lo,
+               int64_t pre_ld, const int32_t* pre_nterms, int h_next, const float* W_next,
+               const float* b_next, float* next_up, float* next_lo, int64_t next_ld,
+               int32_t* next_nterms) {
+  if (!c || n < 1 || n > kMaxVars || n_boxes < 0 || h < 1 || h_next < 1 || pre_ld < 1 ||
+      next_ld < 1 || order < 0 || degree_cap < 1 || degree_cap > kMaxTableDegree ||
+      global_d < 1 || global_d > kMaxOrder)
+    return BERN_E_INVALID;
+  if (n_boxes == 0) return BERN_OK;
+  if (!pre_up || !pre_lo || !pre_nterms || !W_next || !b_next || !next_up || !next_lo ||
+      !next_nterms || n_boxes > INT32_MAX)
+    return BERN_E_INVALID;
+  cudaSetDevice(c->device);
+  int D_pre = 0;
+  while (D_pre < kMaxTableDegree && num_monomials(n, D_pre + 1) <= pre_ld) ++D_pre;
+  if (budget <= 0) budget = (int64_t)1 << 20;
+  if (!layer_fused_shape(n, h, h_next, global_d, D_pre, order, budget, degree_cap, nullptr))
+    return BERN_E_UNSUPPORTED;
+  const Tables* T;
+  int rc = ensure_tables(c, n, 0, &T);
+  if (rc) return rc;
+  return map_cuda(launch_layer(c->launch(), *T, n_boxes, h, global_d, order, budget, degree_cap,
+                               pre_up, pre_lo, pre_ld, pre_nterms, h_next, W_next, b_next,
+                               next_up, next_lo, next_ld, next_nterms, c->counters()));
 }
 
 int bern_sync(bern_ctx* c) {
@@ -889,7 +958,7 @@ int bern_propagate_traced(bern_ctx* c, const bern_net* net, const float* boxes,
   if (!c || !net || !result || n_boxes < 0 || (!boxes && n_boxes > 0)) return BERN_E_INVALID;
   if (trace && c->mem_mode == BERN_MEM_HOST) return BERN_E_INVALID;
   Plan P;
-  int rc = make_plan(net, plan, P);
+  int rc = make_plan(net, plan, P, c->fused && !trace);
   if (rc) return rc;
   if (n_boxes == 0) return BERN_OK;
   if (!result->lo || !result->hi || !result->n_terms || result->cap_terms < 0)

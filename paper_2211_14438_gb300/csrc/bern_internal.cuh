@@ -244,6 +244,29 @@ cudaError_t launch_linearize(const Launch& L, const Tables& T, int64_t n_boxes, 
                              const int32_t* nterms, float* lin_up, float* lin_lo, int64_t lin_ld,
                              int32_t* lin_nt, float* rlo, float* rhi);
 
+// Fused hidden layer (k_layer.cu): stability screen, Bernstein enclosure,
+// ReLU coefficients and composition (orders 1-2) of one hidden layer and the
+// affine step of the next layer in one launch per layer, from the layer's
+// pre-activation block to the next layer's.  layer_fused_shape tells whether
+// a layer qualifies (order 1 or 2, input degree within the row tables,
+// effective enclosure order <= kLayerMaxOrder, shared memory) and its layout.
+constexpr int kLayerMaxOrder = 8;
+constexpr int kLayerSmemMax = 227 * 1024 - 256;
+struct LayerShape {
+  int lb = 0;            // effective Bernstein order of the enclosure
+  int ss = 0, hnp = 0, offW = 0, offU = 0, uni = 0, offN = 0, rem_on = 0;
+  size_t smem = 0;       // dynamic shared memory per block
+};
+bool layer_fused_shape(int n, int h, int hn, int d, int D_pre, int order, int64_t budget, int cap,
+                       LayerShape* out);
+// counter: one device int, zeroed by the launcher (boxes taken by blocks).
+cudaError_t launch_layer(const Launch& L, const Tables& T, int64_t n_boxes, int h, int d,
+                         int order, int64_t budget, int cap, const float* pre_up,
+                         const float* pre_lo, int64_t pre_ld, const int32_t* pre_nt, int hn,
+                         const float* Wn, const float* bn, float* nx_up, float* nx_lo,
+                         int64_t nx_ld, int32_t* nx_nt, int* counter);
+int effective_order(int n, int order, int64_t budget, int* grid_out);
+
 // Largest input degree the row-convolution path handles for n variables.
 int row_path_max_degree(int n);
 cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratch& S,

@@ -149,15 +149,17 @@ __device__ __forceinline__ void line_transform(const float (&x)[LB + 1], float (
 
 // Scatter the scaled coefficients of the first m_eff graded ranks (degree
 // <= Deff) into the grid at their precomputed grid indices; return the
-// directed sum of the one-sided ranges of all other terms.
-template <bool UP>
+// directed sum of the one-sided ranges of all other terms.  Coefficient r is
+// P[r * ps], or P[pos[r]] when PERM (a polynomial held in another order, e.g.
+// the row layout of the fused layer kernel).
+template <bool UP, bool PERM = false>
 __device__ float scatter_terms(const float* __restrict__ P, int ps, int nt,
                                const int32_t* __restrict__ gidx, const float2* __restrict__ rs,
-                               int m_eff, float* grid) {
+                               int m_eff, float* grid, const int32_t* __restrict__ pos = nullptr) {
   const int lane = threadIdx.x & 31;
   float rem = 0.0f;
   for (int r = lane; r < nt; r += 32) {
-    const float a = P[(int64_t)r * ps];
+    const float a = PERM ? P[__ldg(pos + r)] : P[(int64_t)r * ps];
     if (r < m_eff) {
       const float2 sc = rs[r];
       // a / C bracketed: choose the end that rounds the product the right way
@@ -185,14 +187,15 @@ __device__ __forceinline__ int prefix_degree(const Tables& T, int nt) {
   return nt <= T.mexps ? (int)T.deg_of[nt] : kMaxTableDegree;
 }
 
-template <int LB, bool UP>
+template <int LB, bool UP, bool PERM = false>
 __device__ float enclose_warp(const float* __restrict__ P, int ps, int nt, int n,
-                              const Tables& T, const float2* __restrict__ rs, float* grid) {
+                              const Tables& T, const float2* __restrict__ rs, float* grid,
+                              const int32_t* __restrict__ pos = nullptr) {
   const int lane = threadIdx.x & 31;
   constexpr int R = LB + 1;
   const int Dnt = prefix_degree(T, nt);
   const int Deff = Dnt < LB ? Dnt : LB;
-  float rem = scatter_terms<UP>(P, ps, nt, T.gidx[LB], rs, T.mcount[Deff], grid);
+  float rem = scatter_terms<UP, PERM>(P, ps, nt, T.gidx[LB], rs, T.mcount[Deff], grid, pos);
   __syncwarp();
   float best = UP ? -CUDART_INF_F : CUDART_INF_F;
   const int nlines = ipow(R, n - 1);

@@ -25,6 +25,7 @@
 #include <algorithm>
 
 #include "compose_common.cuh"
+#include "row_conv.cuh"
 
 namespace bern {
 
@@ -107,61 +108,6 @@ k_compose_queue(Tables T, ComposeArgs A, int64_t n_items, int row_dmax, ComposeS
 // ------------------------------------------------------------ row convolution
 constexpr int kRowWarps = 4;    // warps sharing one 32-item group
 constexpr int kRowBlocks = 8;   // resident blocks per SM (registers and shared memory)
-
-// One accumulator per output slot holds the square directly: an off-diagonal
-// row pair (p < q) counts twice in the square, so it multiplies 2*x[a]
-// (exact) by y[b]; the diagonal pair (p == q) is the row's own square,
-// sum_a x[a]^2 t^(2a) + sum_(a<b) 2 x[a] x[b] t^(a+b), taken as a triangle.
-// Every product is accumulated with a directed FMA.
-template <int L1, int L2, bool UP>
-__device__ __forceinline__ void conv_rows(const float* __restrict__ s, int offp, int offq,
-                                          float (&acc)[2 * kRowLen - 1]) {
-  float x[L1], y[L2];
-#pragma unroll
-  for (int a = 0; a < L1; ++a) {
-    const float v = s[offp + a];
-    x[a] = v + v;
-  }
-#pragma unroll
-  for (int b = 0; b < L2; ++b) y[b] = s[offq + b];
-#pragma unroll
-  for (int a = 0; a < L1; ++a)
-#pragma unroll
-    for (int b = 0; b < L2; ++b) acc[a + b] = dfma<UP>(x[a], y[b], acc[a + b]);
-}
-
-template <int L, bool UP>
-__device__ __forceinline__ void conv_diag(const float* __restrict__ s, int off,
-                                          float (&acc)[2 * kRowLen - 1]) {
-  float x[L], x2[L];
-#pragma unroll
-  for (int a = 0; a < L; ++a) {
-    x[a] = s[off + a];
-    x2[a] = x[a] + x[a];
-  }
-#pragma unroll
-  for (int a = 0; a < L; ++a) {
-    acc[2 * a] = dfma<UP>(x[a], x[a], acc[2 * a]);
-#pragma unroll
-    for (int b = a + 1; b < L; ++b) acc[a + b] = dfma<UP>(x2[a], x[b], acc[a + b]);
-  }
-}
-
-#define BERN_CC(L1, L2) \
-  case row_pair_case(L1, L2): conv_rows<L1, L2, UP>(s, pr.x, pr.y, acc); break;
-#define BERN_CONV_ALL_CASES                                                                     \
-  BERN_CC(1, 1) BERN_CC(1, 2) BERN_CC(1, 3) BERN_CC(1, 4) BERN_CC(1, 5) BERN_CC(1, 6)          \
-  BERN_CC(1, 7) BERN_CC(1, 8) BERN_CC(1, 9) BERN_CC(2, 2) BERN_CC(2, 3) BERN_CC(2, 4)          \
-  BERN_CC(2, 5) BERN_CC(2, 6) BERN_CC(2, 7) BERN_CC(2, 8) BERN_CC(2, 9) BERN_CC(3, 3)          \
-  BERN_CC(3, 4) BERN_CC(3, 5) BERN_CC(3, 6) BERN_CC(3, 7) BERN_CC(3, 8) BERN_CC(3, 9)          \
-  BERN_CC(4, 4) BERN_CC(4, 5) BERN_CC(4, 6) BERN_CC(4, 7) BERN_CC(4, 8) BERN_CC(4, 9)          \
-  BERN_CC(5, 5) BERN_CC(5, 6) BERN_CC(5, 7) BERN_CC(5, 8) BERN_CC(5, 9) BERN_CC(6, 6)          \
-  BERN_CC(6, 7) BERN_CC(6, 8) BERN_CC(6, 9) BERN_CC(7, 7) BERN_CC(7, 8) BERN_CC(7, 9)          \
-  BERN_CC(8, 8) BERN_CC(8, 9) BERN_CC(9, 9)
-#define BERN_CD(L) \
-  case L: conv_diag<L, UP>(s, pr.x, acc); break;
-#define BERN_DIAG_CASES \
-  BERN_CD(1) BERN_CD(2) BERN_CD(3) BERN_CD(4) BERN_CD(5) BERN_CD(6) BERN_CD(7) BERN_CD(8) BERN_CD(9)
 
 // Load one bound of the 32 items of a lane group into row layout:
 // s = (pre - lo*[K=0]) / (hi - lo) in round-to-nearest; returns this warp's
