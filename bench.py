@@ -3,14 +3,19 @@
 Workload: the batched plain method, ReLU MLP [3, 64, 64, 64, 64, 1] (seed 2),
 5120 boxes (the 16^3 grid of [-1,1]^3 plus 1024 random boxes with sides
 U(0.01,0.5)), Bernstein ReLU order 2, total-degree cap 16.  A step is one
-bern_propagate over all 5120 boxes (init, 5 affine steps, 5 enclosures, 4
-ReLU-coefficient and composition steps, output copy-out), replayed as one CUDA
-graph.  L2 is flushed (256 MB write) before every timed step, outside the
-timed interval; each step is timed with CUDA events on the launching stream.
+bern_propagate over all 5120 boxes (init, the first layer's affine step, one
+fused launch per hidden layer, the output enclosure and copy-out), replayed as
+one CUDA graph.  L2 is flushed (256 MB write) before every timed step, outside
+the timed interval; each step is timed with CUDA events on the launching
+stream.
 
-Multi-GPU (torchrun): every rank propagates its own full batch (weak
-scaling); there is no collective on the data path, only a barrier and a max
-over ranks of the timed region.
+Multi-GPU (torchrun, weak scaling): N replicas of the 5120-box batch (the
+same grid cells, fresh random boxes per replica) are split into N contiguous
+slices of equal estimated cost (interval arithmetic counts each box's
+straddling neurons, weighted by the term pairs of their squares); every rank
+bounds its slice, and the per-box bounds and term counts come back to every
+rank by one NCCL all_gather per tensor inside the timed step.  Barrier and
+max over ranks of the timed region.
 
 Also reported: per-kernel durations (a second K-step pass through the
 step-level C ABI, events around every launch), the roofline of the dominant
@@ -446,6 +451,24 @@ def run_ours(args, rank, world, local_rank, dist):
         # an evenly strided subset keeps the mix of grid cells and random boxes
         pick = np.linspace(0, len(w.boxes) - 1, args.n_boxes).astype(int)
         w.boxes = np.ascontiguousarray(w.boxes[pick])
+    B_total = len(w.boxes)
+    counts = [B_total]
+    if world > 1:
+        # weak scaling: world replicas of the batch (5120 boxes each), split
+        # into cost-balanced contiguous slices, one per rank; the per-box
+        # results come back to every rank by one all_gather per tensor
+        from paper_2211_14438_gb300 import sharding
+        wg = wl.batch_3in_replicas(world)
+        if args.n_boxes:
+            pick = np.linspace(0, len(wg.boxes) - 1, args.n_boxes * world).astype(int)
+            wg.boxes = np.ascontiguousarray(wg.boxes[pick])
+        costs = sharding.interval_cost(wg.net.widths, wg.net.W, wg.net.b, wg.boxes, wg.degree,
+                                       wg.degree_cap)
+        ranges = sharding.shard_ranges(costs, world)
+        a0, z0 = ranges[rank]
+        counts = [r1 - r0 for r0, r1 in ranges]
+        w.boxes = np.ascontiguousarray(wg.boxes[a0:z0])
+        B_total = len(wg.boxes)
     B = len(w.boxes)
     ctx = bern.Context(local_rank, stream=torch.cuda.current_stream(dev))
     stream = ctx.stream
@@ -462,6 +485,9 @@ def run_ours(args, rank, world, local_rank, dist):
     def step():
         ctx.propagate(w.net.widths, Wd, bd, boxes_d, degree=w.degree, cap=w.degree_cap,
                       cap_terms=cap_terms, out=out, sync=False)
+        if world > 1:
+            sharding.gather_tensors({"lo": out["lo"], "hi": out["hi"],
+                                     "n_terms": out["n_terms"]}, B, counts, dist)
 
     if args.no_fused:
         ctx.set_fused(False)
@@ -497,7 +523,7 @@ def run_ours(args, rank, world, local_rank, dist):
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms_local = float(np.sum(ms)) / args.steps
     ms_step = max_over_ranks(ms_local, world, dist, dev)
-    value = world * B / (ms_step / 1e3)
+    value = B_total / (ms_step / 1e3)
 
     lo = out["lo"].cpu().numpy()[:, 0].astype(np.float64)
     hi = out["hi"].cpu().numpy()[:, 0].astype(np.float64)
@@ -522,7 +548,7 @@ def run_ours(args, rank, world, local_rank, dist):
             ms_ps = max_over_ranks(float(np.mean([s_.elapsed_time(e_) for s_, e_ in
                                                   zip(starts, ends)])), world, dist, dev)
             w_ps = float((out["hi"] - out["lo"]).float().mean().item())
-            per_step = {"ms_per_step": round(ms_ps, 4), "value": round(world * B / (ms_ps / 1e3), 1),
+            per_step = {"ms_per_step": round(ms_ps, 4), "value": round(B_total / (ms_ps / 1e3), 1),
                         "unit": "boxes/s", "mean_output_width": round(w_ps, 6),
                         "note": "bern_propagate with bern_set_fused(0): every layer through the "
                                 "per-step kernels"}
@@ -621,14 +647,16 @@ def run_ours(args, rank, world, local_rank, dist):
         wall = max_over_ranks(wall, world, dist, dev)
         h2d = boxes_h.nbytes + sum(x.nbytes for x in W_h) + sum(x.nbytes for x in b_h)
         d2h = sum(v.nbytes for v in out_h.values())
-        e2e = {"value": round(world * B / wall, 1), "unit": "boxes/s",
+        e2e = {"value": round(B_total / wall, 1), "unit": "boxes/s",
+               "note": ("each rank its own slice through host buffers, no gather"
+                        if world > 1 else "host buffers in, host buffers out"),
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": round(wall * 1e3, 3)}
 
     # ---- the learned form: degree MLP trained on the GPU, then timed like the plain form
     learned = None
     learned4 = None
-    if not args.no_learned:
+    if not args.no_learned and world == 1:
         from paper_2211_14438_gb300 import learned as lm
 
         def timed(net, Wd_, bd_, bx_, degree, ct, o_, tau=0.0):
@@ -738,7 +766,7 @@ def run_ours(args, rank, world, local_rank, dist):
     # ---- Lin linearisation (Sec. 5.3); reported beside the headline, which
     # it can never cost: an error here is recorded, not raised
     lin_res = None
-    if not args.no_lin:
+    if not args.no_lin and world == 1:
         try:
             lin_res = lin_entries(ctx, torch, dev, flush, args, w, Wd, bd, boxes_d, ms_step,
                                   float(np.mean(hi - lo)), world, dist)
@@ -773,7 +801,11 @@ def run_ours(args, rank, world, local_rank, dist):
                    "mean_output_width": round(float(np.mean(hi - lo)), 6),
                    "mean_vol_relative": round(float(np.mean(vol)), 6),
                    "l2": "flushed (256 MB write) before every timed step",
-                   "parallelism": "box-sharded dp%d (each rank its own batch)" % world,
+                   "parallelism": ("box-sharded dp%d: %d replicas of the batch split into "
+                                   "cost-balanced slices (interval-arithmetic term-pair cost), "
+                                   "results all_gathered (lo, hi, n_terms) every step"
+                                   % (world, world)) if world > 1 else "single GPU",
+                   "boxes_total": B_total,
                    "graphs": True, "fused_layers": not args.no_fused},
         "roofline": roof, "kernels": kernels, "per_step_kernels_path": per_step,
         "kernel_pass_ms_per_step": round(total_kernel_ms, 4),

@@ -140,6 +140,21 @@ def batch_3in(n_random: int = 1024, cells: int = 16) -> Workload:
                     np.concatenate([g, r], 0), degree=2)
 
 
+def batch_3in_replicas(world: int) -> Workload:
+    """The batched workload for `world` ranks at fixed work per rank (weak
+    scaling): replica 0 is batch_3in's 5120 boxes; replica r >= 1 is the same
+    16^3 grid plus 1024 random boxes drawn like batch_3in's from the generator
+    seeded 2000 + r.  The network is batch_3in's."""
+    w = batch_3in()
+    parts = [w.boxes]
+    for r in range(1, int(world)):
+        rng = np.random.default_rng(2000 + r)
+        parts.append(np.concatenate([grid_boxes(3, 16), random_boxes(rng, 1024, 3, 0.01, 0.5)],
+                                    0))
+    return Workload("mlp3-64x4-1_boxes%d_d2" % sum(len(x) for x in parts), w.net,
+                    np.ascontiguousarray(np.concatenate(parts, 0)), degree=2)
+
+
 def batch_3in_training_boxes(count: int = 800, seed: int = 1002) -> np.ndarray:
     """Training boxes for the learned component on the [3,64x4,1] network, drawn
     like the benchmark's boxes (4/5 grid-cell sized, 1/5 random sized) but from
