@@ -444,12 +444,13 @@ int make_plan(const bern_net* net, const bern_degree_plan* dp, Plan& P, bool all
       if ((int)l.orders.size() > kOrderQueues) return BERN_E_UNSUPPORTED;
     }
   }
-  // fused layers: plain plans (one order per layer), no pruning, no Lin
-  if (allow_fused && !P.learned && !P.per_neuron && P.lin == 0 && P.tau == 0.0f)
+  // fused layers: plain plans (one order per layer), no pruning; a Lin layer
+  // needs its post-activation block, so it runs the per-step kernels
+  if (allow_fused && !P.learned && !P.per_neuron && P.tau == 0.0f)
     for (int i = 0; i + 1 < P.H; ++i) {
       LayerPlan& l = P.L[i];
-      l.fused = layer_fused_shape(P.n, l.h_out, P.L[i + 1].h_out, l.d, l.D_pre, l.order,
-                                  P.budget, P.cap, nullptr);
+      l.fused = !l.lin && layer_fused_shape(P.n, l.h_out, P.L[i + 1].h_out, l.d, l.D_pre,
+                                            l.order, P.budget, P.cap, nullptr);
     }
   // per-box workspace layout
   size_t off = 0;

@@ -67,13 +67,25 @@ def test_learned_plan_matches_oracle(ctx, widths, seed, tseed):
     assert checked >= 2
 
 
+def run_per_step(ctx, *a, **kw):
+    """The plain plan through the per-step kernels (learned plans always run
+    them; the fused layer kernels order the output layer's sums differently)."""
+    ctx.set_fused(False)
+    try:
+        return run_gpu(ctx, *a, **kw)
+    finally:
+        ctx.set_fused(True)
+
+
 @pytest.mark.parametrize("cls", [0, 1, 2, 3])
 def test_sure_proposal_equals_global_plan(ctx, cls):
-    """An MLP that always proposes order cls+1 gives exactly the global plan."""
+    """An MLP that always proposes order cls+1 gives exactly the global plan
+    (both through the per-step kernels, which learned plans always use: the
+    fused layer kernels order the output layer's sums differently)."""
     w = wl.batch_3in(n_random=8, cells=2)
     m = bern.Mlp(torch, F, C, const_theta(cls))
     a = run_gpu(ctx, w.net, w.boxes, degree=bern.Learned(m), cap=16)
-    b = run_gpu(ctx, w.net, w.boxes, degree=cls + 1, cap=16)
+    b = run_per_step(ctx, w.net, w.boxes, degree=cls + 1, cap=16)
     for k in ("lo", "hi", "n_terms"):
         assert np.array_equal(a[k], b[k]), k
     for bi in range(len(w.boxes)):
@@ -85,7 +97,7 @@ def test_low_confidence_falls_back_to_plain(ctx):
     w = wl.batch_3in(n_random=8, cells=2)
     m = bern.Mlp(torch, F, C, random_theta(5))
     a = run_gpu(ctx, w.net, w.boxes, degree=bern.Learned(m, min_conf=1.01, fallback=2))
-    b = run_gpu(ctx, w.net, w.boxes, degree=2)
+    b = run_per_step(ctx, w.net, w.boxes, degree=2)
     for k in ("lo", "hi", "n_terms"):
         assert np.array_equal(a[k], b[k]), k
 
@@ -136,10 +148,10 @@ def test_per_layer_caps_clamp_proposals(ctx):
     w = wl.batch_3in(n_random=8, cells=2)
     m = bern.Mlp(torch, F, C, const_theta(3))
     a = run_gpu(ctx, w.net, w.boxes, degree=bern.Learned(m, max_per_layer=[2, 2, 2, 2]))
-    b = run_gpu(ctx, w.net, w.boxes, degree=2)
+    b = run_per_step(ctx, w.net, w.boxes, degree=2)
     for k in ("lo", "hi", "n_terms"):
         assert np.array_equal(a[k], b[k]), k
     a = run_gpu(ctx, w.net, w.boxes, degree=bern.Learned(m, max_per_layer=[4, 1, 1, 1]))
-    b = run_gpu(ctx, w.net, w.boxes, degree=[4, 1, 1, 1])
+    b = run_per_step(ctx, w.net, w.boxes, degree=[4, 1, 1, 1])
     for k in ("lo", "hi", "n_terms"):
         assert np.array_equal(a[k], b[k]), k
