@@ -489,8 +489,7 @@ def run_ours(args, rank, world, local_rank, dist):
             sharding.gather_tensors({"lo": out["lo"], "hi": out["hi"],
                                      "n_terms": out["n_terms"]}, B, counts, dist)
 
-    if args.no_fused:
-        ctx.set_fused(False)
+    ctx.set_fused(bool(args.fused))
     from paper_2211_14438_gb300.sharding import max_over_ranks
     sampler = ClockSampler(local_rank)
     sampler.start()
@@ -528,11 +527,11 @@ def run_ours(args, rank, world, local_rank, dist):
     lo = out["lo"].cpu().numpy()[:, 0].astype(np.float64)
     hi = out["hi"].cpu().numpy()[:, 0].astype(np.float64)
 
-    # ---- the same step through the per-step kernels (no fused layer launches),
-    # timed the same way: what the fused kernels gain
-    per_step = None
-    if not args.no_fused:
-        ctx.set_fused(False)
+    # ---- the same step through the other path (fused layer launches when the
+    # headline runs the per-step kernels, and the reverse), timed the same way
+    alt = None
+    if not args.no_alt_path:
+        ctx.set_fused(not args.fused)
         try:
             for _ in range(args.warmup):
                 step()
@@ -544,16 +543,16 @@ def run_ours(args, rank, world, local_rank, dist):
                 ends[k].record(stream)
             torch.cuda.synchronize()
             if ctx.sync() != 0:
-                raise RuntimeError("per-step path failed")
-            ms_ps = max_over_ranks(float(np.mean([s_.elapsed_time(e_) for s_, e_ in
-                                                  zip(starts, ends)])), world, dist, dev)
-            w_ps = float((out["hi"] - out["lo"]).float().mean().item())
-            per_step = {"ms_per_step": round(ms_ps, 4), "value": round(B_total / (ms_ps / 1e3), 1),
-                        "unit": "boxes/s", "mean_output_width": round(w_ps, 6),
-                        "note": "bern_propagate with bern_set_fused(0): every layer through the "
-                                "per-step kernels"}
+                raise RuntimeError("alternate path failed")
+            ms_alt = max_over_ranks(float(np.mean([s_.elapsed_time(e_) for s_, e_ in
+                                                   zip(starts, ends)])), world, dist, dev)
+            w_alt = float((out["hi"] - out["lo"]).float().mean().item())
+            alt = {"fused_layers": not args.fused, "ms_per_step": round(ms_alt, 4),
+                   "value": round(B_total / (ms_alt / 1e3), 1), "unit": "boxes/s",
+                   "mean_output_width": round(w_alt, 6),
+                   "note": "bern_propagate with bern_set_fused(%d)" % (0 if args.fused else 1)}
         finally:
-            ctx.set_fused(True)
+            ctx.set_fused(bool(args.fused))
     nt = out["n_terms"].cpu().numpy()[:, 0, 0]
     coef = out["coef"].cpu().numpy()[:, 0].astype(np.float64)
     ex = bern.monomials(w.net.n_in, w.degree_cap).astype(np.float64)
@@ -562,7 +561,7 @@ def run_ours(args, rank, world, local_rank, dist):
                     for i in range(B)])
 
     # ---- per-kernel pass (same kernels through the step ABI)
-    kp = KernelPass(ctx, torch, w, Wd, bd, boxes_d, fused=not args.no_fused)
+    kp = KernelPass(ctx, torch, w, Wd, bd, boxes_d, fused=bool(args.fused))
     for _ in range(max(1, args.warmup)):
         kp.step()
     kp.collect()
@@ -576,6 +575,27 @@ def run_ours(args, rank, world, local_rank, dist):
         raise RuntimeError("kernel pass failed: %s" % bern.strerror(rc))
     work = kp.work()
     avg = {k: float(np.mean(v)) for k, v in kp.times.items()}
+    fused_kernels = None
+    if not args.fused and not args.no_alt_path:
+        kf = KernelPass(ctx, torch, w, Wd, bd, boxes_d, fused=True)
+        for _ in range(max(1, args.warmup)):
+            kf.step()
+        kf.collect()
+        kf.times = {}
+        for _ in range(args.steps):
+            flush.zero_()
+            kf.step()
+            kf.collect()
+        if ctx.sync() != 0:
+            raise RuntimeError("fused kernel pass failed")
+        fwork = kf.work()
+        fused_kernels = {}
+        for k_, v_ in sorted(kf.times.items(), key=lambda kv: -float(np.mean(kv[1]))):
+            ms_ = float(np.mean(v_))
+            wk_ = fwork.get(k_, {"bytes": 0.0, "flops": 0.0})
+            fused_kernels[k_] = {"ms": round(ms_, 4),
+                                 "GBps": round(wk_["bytes"] / (ms_ / 1e3) / 1e9, 1),
+                                 "TFLOPs": round(wk_["flops"] / (ms_ / 1e3) / 1e12, 3)}
     total_kernel_ms = sum(avg.values())
     dom = max(avg, key=lambda k: avg[k])
     peaks, peak_kind = load_peaks()
@@ -806,8 +826,9 @@ def run_ours(args, rank, world, local_rank, dist):
                                    "results all_gathered (lo, hi, n_terms) every step"
                                    % (world, world)) if world > 1 else "single GPU",
                    "boxes_total": B_total,
-                   "graphs": True, "fused_layers": not args.no_fused},
-        "roofline": roof, "kernels": kernels, "per_step_kernels_path": per_step,
+                   "graphs": True, "fused_layers": bool(args.fused)},
+        "roofline": roof, "kernels": kernels, "alternate_path": alt,
+        "fused_layer_kernels": fused_kernels,
         "kernel_pass_ms_per_step": round(total_kernel_ms, 4),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "learned": learned, "learned_6in": learned4, "bnb_6in": bnb5, "lin": lin_res,
@@ -942,8 +963,10 @@ def main():
                     help="skip training and timing the learned-degree form")
     ap.add_argument("--no-lin", action="store_true",
                     help="skip timing the Lin-linearised forms")
-    ap.add_argument("--no-fused", action="store_true",
-                    help="run every layer through the per-step kernels (no fused layer launches)")
+    ap.add_argument("--fused", action="store_true",
+                    help="headline through the fused layer kernels (bern_set_fused(1))")
+    ap.add_argument("--no-alt-path", action="store_true",
+                    help="skip timing the other path (fused / per-step) beside the headline")
     ap.add_argument("--n-boxes", type=int, default=0,
                     help="use N evenly strided boxes of the workload (small cases for ncu)")
     ap.add_argument("--paper-sweeps", action="store_true",

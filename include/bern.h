@@ -406,7 +406,7 @@ int bern_layer(bern_ctx* ctx, int n, int64_t n_boxes, int h, int order, int64_t 
                int32_t* next_nterms);
 
 /* Use the fused layer kernel (bern_layer) inside bern_propagate wherever a
- * plan allows it (default 1): plain plans (BERN_DEG_GLOBAL or PER_LAYER) with
+ * plan allows it (default 0): plain plans (BERN_DEG_GLOBAL or PER_LAYER) with
  * prune_tau = 0, untraced, layer by layer where the shape qualifies and the
  * layer is not linearised (lin_every).  enable = 0 runs the per-step kernels for every layer.  Both
  * give the same bounds up to the rounding of sums taken in another order. */

@@ -82,7 +82,7 @@ struct bern_ctx {
   std::map<int, TableSet> tables;
   DevBuf ws, stage_in, stage_out, qbuf, mlp_ws, hbuf;
   DevBuf ctr;                       // box counters of the fused layer kernels
-  int fused = 1;                    // fused layer kernels where a plan allows them
+  int fused = 0;                    // fused layer kernels where a plan allows them
   std::vector<GraphEntry> graphs;
   Tuner tuner;
   int autotune = 1;

@@ -68,13 +68,11 @@ def test_learned_plan_matches_oracle(ctx, widths, seed, tseed):
 
 
 def run_per_step(ctx, *a, **kw):
-    """The plain plan through the per-step kernels (learned plans always run
-    them; the fused layer kernels order the output layer's sums differently)."""
+    """The plain plan through the per-step kernels (the default; learned plans
+    always run them, while the fused layer kernels order the output layer's
+    sums differently)."""
     ctx.set_fused(False)
-    try:
-        return run_gpu(ctx, *a, **kw)
-    finally:
-        ctx.set_fused(True)
+    return run_gpu(ctx, *a, **kw)
 
 
 @pytest.mark.parametrize("cls", [0, 1, 2, 3])

@@ -325,8 +325,19 @@ def test_stability_screen_matches_full_enclosure(ctx):
     parity tolerance where a Bernstein bound within rounding of 0 takes the
     other ReLU case."""
     w = wl.batch_3in(n_random=64, cells=4)
+    ctx.set_fused(False)          # the per-step kernels (the default), as traced runs use
     a = run_gpu(ctx, w.net, w.boxes)
     b = run_gpu(ctx, w.net, w.boxes, trace=True)
+    # the fused layer kernels screen the same way; their output layer's sums
+    # run in another order
+    ctx.set_fused(True)
+    try:
+        f = run_gpu(ctx, w.net, w.boxes)
+    finally:
+        ctx.set_fused(False)
+    assert np.array_equal(f["n_terms"], a["n_terms"])
+    assert np.all(np.abs(f["lo"] - a["lo"]) <= 1e-5 * (1 + np.abs(a["lo"])))
+    assert np.all(np.abs(f["hi"] - a["hi"]) <= 1e-5 * (1 + np.abs(a["hi"])))
     same = np.all(a["lo"] == b["lo"], axis=1) & np.all(a["hi"] == b["hi"], axis=1)
     assert same.mean() >= 0.95
     assert np.all(np.abs(a["lo"] - b["lo"]) <= TOL * (1 + np.abs(b["lo"])))
