@@ -60,7 +60,11 @@ extern "C" {
 #define BERN_MAX_VARS   8
 #define BERN_MAX_ORDER  16    /* largest ReLU Bernstein order d */
 #define BERN_MAX_GRID   24576 /* largest Bernstein grid one enclosure stages in shared memory;
-                                 bern_budget is clamped to it */
+                                 larger grids (up to BERN_MAX_BIG_GRID, orders <= 16) run
+                                 in a global-memory workspace of the context */
+#define BERN_MAX_BIG_GRID 4194304 /* largest Bernstein grid of any enclosure;
+                                 bern_budget is clamped to it (to BERN_MAX_GRID in
+                                 bern_propagate_noalloc, which has no workspace) */
 #define BERN_MAX_ENCLOSE_ORDER 24 /* Bernstein orders above this are lowered to it */
 
 /* the learned component's MLP */
@@ -93,7 +97,9 @@ typedef struct {
  *   bern_budget: largest Bernstein grid (l+1)^n one enclosure may use; above
  *                it the enclosure uses a lower order for the low-degree terms
  *                and coefficient intervals for the rest (0 means 2^20; values
- *                above BERN_MAX_GRID act as BERN_MAX_GRID).
+ *                above BERN_MAX_BIG_GRID act as BERN_MAX_BIG_GRID).  Grids
+ *                above BERN_MAX_GRID run in a global-memory workspace (up to
+ *                1 GiB per context; orders up to 16).
  * per_layer / per_neuron are host arrays. */
 /* The learned component (not part of the paper's method): a two-layer MLP
  * with BF16 weights and activations and FP32 accumulation,

@@ -34,15 +34,18 @@ BERN_DEGREE_FEATURES = 8
 BERN_DEGREE_CLASSES = 4
 BERN_MAX_ORDER = 16
 BERN_MAX_GRID = 24576
+BERN_MAX_BIG_GRID = 4194304
 BERN_MAX_ENCLOSE_ORDER = 24
 COEF_STRIDE = BERN_MAX_ORDER + 1
 
 
-def effective_budget(budget: int = 0) -> int:
-    """The Bernstein-grid budget the library applies (0 means 2^20, clamped
-    to BERN_MAX_GRID)."""
+def effective_budget(budget: int = 0, noalloc: bool = False) -> int:
+    """The Bernstein-grid budget the library applies: 0 means 2^20; clamped
+    to BERN_MAX_BIG_GRID (grids above BERN_MAX_GRID run in the context's
+    global-memory workspace, at orders up to 16), or to BERN_MAX_GRID for
+    bern_propagate_noalloc, which has no workspace."""
     b = budget if budget > 0 else 1 << 20
-    return min(b, BERN_MAX_GRID)
+    return min(b, BERN_MAX_GRID if noalloc else BERN_MAX_BIG_GRID)
 
 EXPORTS = [
     "bern_create", "bern_destroy", "bern_set_pointer_mode", "bern_set_graphs",

@@ -15,9 +15,6 @@
 #include "compose_common.cuh"
 #include "mlp.cuh"
 
-namespace bern {
-int effective_order(int n, int order, int64_t budget, int* grid_out);
-}
 
 using namespace bern;
 
@@ -82,6 +79,7 @@ struct bern_ctx {
   std::map<int, TableSet> tables;
   DevBuf ws, stage_in, stage_out, qbuf, mlp_ws, hbuf;
   DevBuf ctr;                       // box counters of the fused layer kernels
+  DevBuf ebuf;                      // grids of enclosures above shared memory
   int fused = 0;                    // fused layer kernels where a plan allows them
   std::vector<GraphEntry> graphs;
   Tuner tuner;
@@ -89,9 +87,26 @@ struct bern_ctx {
   std::set<std::string> tuned;     // plan signatures already tuned
   int sms = 0;                      // multiprocessors of the device
   int* counters() { return (int*)ctr.p; }
-  Launch launch() { return Launch{stream, d_status, &launches, &tuner, sms}; }
-  Launch launch_on(cudaStream_t s) { return Launch{s, d_status, &launches, &tuner, sms}; }
+  Launch launch() { return launch_on(stream); }
+  Launch launch_on(cudaStream_t s) {
+    return Launch{s, d_status, &launches, &tuner, sms, (float*)ebuf.p,
+                  (int64_t)(ebuf.bytes / sizeof(float))};
+  }
+  // reserve the enclosure workspace for grids of (n, order, budget); graphs
+  // captured with an older buffer are dropped when it moves
+  cudaError_t reserve_enclose(int n, int order, int64_t budget);
 };
+
+cudaError_t bern_ctx::reserve_enclose(int n, int order, int64_t budget) {
+  const size_t floats = enclose_big_floats(n, order, budget, std::max(1, sms));
+  if (floats * sizeof(float) <= ebuf.bytes) return cudaSuccess;
+  for (auto& g : graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  graphs.clear();
+  cudaStreamSynchronize(stream);
+  if (gstream) cudaStreamSynchronize(gstream);
+  return ebuf.reserve(floats * sizeof(float));
+}
 
 namespace {
 
@@ -159,7 +174,10 @@ int ensure_tables(bern_ctx* c, int n, int dmax, const Tables** out) {
     ts.view.deg_of = (const uint8_t*)b.p;
     ts.bufs.push_back(b);
   }
-  ts.view.rscale_max = max_enclose_order(n);
+  // reciprocal brackets and grid indices up to the largest order of any
+  // enclosure; line tables only for the shared-memory kernels' orders
+  ts.view.rscale_max = max_enclose_order_big(n);
+  const int lines_max = max_enclose_order(n);
   for (int l = 0; l <= ts.view.rscale_max; ++l) {
     std::vector<float> rs;
     build_rscale(n, l, rs);
@@ -169,15 +187,16 @@ int ensure_tables(bern_ctx* c, int n, int dmax, const Tables** out) {
     ts.view.rscale[l] = (const float2*)b.p;
     ts.bufs.push_back(b);
     std::vector<int32_t> gi, li;
-    build_enclose_tables(n, l, gi, li);
+    build_enclose_tables(n, l, gi, li, l <= lines_max);
     DevBuf bg, bl;
     if ((e = bg.reserve(gi.size() * sizeof(int32_t))) != cudaSuccess) return map_cuda(e);
-    if ((e = bl.reserve(li.size() * sizeof(int32_t))) != cudaSuccess) {
+    if (!li.empty() && (e = bl.reserve(li.size() * sizeof(int32_t))) != cudaSuccess) {
       bg.release();
       return map_cuda(e);
     }
     cudaMemcpy(bg.p, gi.data(), gi.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-    cudaMemcpy(bl.p, li.data(), li.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (!li.empty())
+      cudaMemcpy(bl.p, li.data(), li.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     ts.view.gidx[l] = (const int32_t*)bg.p;
     ts.view.lines[l] = (const int2*)bl.p;
     ts.bufs.push_back(bg);
@@ -734,6 +753,8 @@ int bern_destroy(bern_ctx* c) {
   c->stage_out.release();
   c->mlp_ws.release();
   c->hbuf.release();
+  c->ctr.release();
+  c->ebuf.release();
   if (c->d_status) cudaFree(c->d_status);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -885,6 +906,8 @@ int bern_enclose(bern_ctx* c, int n, int64_t n_boxes, int h, int order, int64_t 
   int rc = ensure_tables(c, n, 0, &T);
   if (rc) return rc;
   if (ld > T->mexps) return BERN_E_UNSUPPORTED;
+  cudaError_t e = c->reserve_enclose(n, order, budget);
+  if (e != cudaSuccess) return map_cuda(e);
   return map_cuda(launch_enclose(c->launch(), *T, n_boxes, h, order, budget, pre_up, pre_lo, ld,
                                  nterms, lo, hi));
 }
@@ -901,6 +924,8 @@ int bern_linearize(bern_ctx* c, int n, int64_t n_boxes, int h, int order, int64_
   int rc = ensure_tables(c, n, 0, &T);
   if (rc) return rc;
   if (ld > T->mexps) return BERN_E_UNSUPPORTED;
+  cudaError_t e = c->reserve_enclose(n, order, budget);
+  if (e != cudaSuccess) return map_cuda(e);
   return map_cuda(launch_linearize(c->launch(), *T, n_boxes, h, order, budget, post_up, post_lo,
                                    ld, nterms, lin_up, lin_lo, lin_ld, lin_nterms, res_lo,
                                    res_hi));
@@ -982,6 +1007,14 @@ int bern_propagate_traced(bern_ctx* c, const bern_net* net, const float* boxes,
   if (rc) return rc;
   for (const auto& l : P.L)
     if (l.M_pre > T->mexps || l.M_post > T->mexps) return BERN_E_UNSUPPORTED;
+  // workspace of the enclosures whose grids exceed shared memory
+  for (const auto& l : P.L) {
+    cudaError_t e0 = c->reserve_enclose(P.n, l.order, P.budget);
+    for (int o : l.orders)
+      if (e0 == cudaSuccess) e0 = c->reserve_enclose(P.n, o, P.budget);
+    if (e0 == cudaSuccess && l.lin) e0 = c->reserve_enclose(P.n, l.order_post, P.budget);
+    if (e0 != cudaSuccess) return map_cuda(e0);
+  }
   size_t horner_floats = 0;
   for (const auto& l : P.L) {
     if (!l.hidden || (l.d < 3 && P.tau == 0.0f)) continue;

@@ -119,13 +119,17 @@ struct Tables {
 
 // Largest Bernstein order whose grid fits the shared-memory limit for n vars.
 int max_enclose_order(int n);
+// Largest Bernstein order the global-memory enclosure handles for n vars
+// (grid <= BERN_MAX_BIG_GRID cells, order <= 16, or the shared-memory limit).
+int max_enclose_order_big(int n);
 // deg_of[c] for c = 0..M(n,De): the smallest D with M(n,D) >= c.
 void build_degree_of(int n, int De, std::vector<uint8_t>& out);
 // Host image of the reciprocal brackets for order l: 2*M(n,l) floats.
 void build_rscale(int n, int l, std::vector<float>& out);
 // Enclosure index tables for order l (grid indices of the graded ranks, and
 // the lines' base offsets and prefix digit sums; two int32 per line).
-void build_enclose_tables(int n, int l, std::vector<int32_t>& gidx, std::vector<int32_t>& lines);
+void build_enclose_tables(int n, int l, std::vector<int32_t>& gidx, std::vector<int32_t>& lines,
+                          bool with_lines = true);
 
 // ------------------------------------------------------------ launchers
 // Autotuning.  Launchers that have several valid variants for a shape ask
@@ -147,6 +151,10 @@ struct Launch {
   int64_t* launches;               // host counter
   Tuner* tuner = nullptr;
   int sms = 0;                     // multiprocessors of the device (0: query it)
+  // workspace of the global-memory enclosure (grids above shared memory);
+  // null: enclosures are limited to shared-memory grids (BERN_MAX_GRID)
+  float* ews = nullptr;
+  int64_t ews_floats = 0;
 };
 // Multiprocessor count of the launch's device (L.sms, else the current
 // device's attribute); grids of persistent kernels are multiples of it.
@@ -265,7 +273,20 @@ cudaError_t launch_layer(const Launch& L, const Tables& T, int64_t n_boxes, int 
                          const float* pre_lo, int64_t pre_ld, const int32_t* pre_nt, int hn,
                          const float* Wn, const float* bn, float* nx_up, float* nx_lo,
                          int64_t nx_ld, int32_t* nx_nt, int* counter);
-int effective_order(int n, int order, int64_t budget, int* grid_out);
+// Effective Bernstein order of an enclosure: the requested order, lowered
+// until its grid fits the budget and the grid limit (BERN_MAX_GRID without
+// the global-memory path, BERN_MAX_BIG_GRID and order <= 16 with it).
+int effective_order(int n, int order, int64_t budget, int* grid_out, bool big = false);
+// Global-memory enclosure (k_enclose_big.cu) for grids above BERN_MAX_GRID:
+// workspace floats it needs for (n, order, budget) (0 if the grid fits
+// shared memory), and its launcher over an item list (list == null: items
+// 0..n_items-1); lo/hi only (the ReLU step runs separately).
+constexpr int64_t kEncloseBigBytes = (int64_t)1 << 30;
+size_t enclose_big_floats(int n, int order, int64_t budget, int sms);
+cudaError_t launch_enclose_big(const Launch& L, const Tables& T, int lb, int G, int64_t n_items,
+                               int h, const float* pre_up, const float* pre_lo, int64_t ld,
+                               const int32_t* nterms, float* lo, float* hi, const int* list,
+                               const int* count);
 
 // Largest input degree the row-convolution path handles for n variables.
 int row_path_max_degree(int n);

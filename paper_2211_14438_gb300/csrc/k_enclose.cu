@@ -76,22 +76,39 @@ static cudaError_t launch_generic(const Launch& L, const Tables& T, int lb, int 
 }
 
 // Effective Bernstein order: the requested order, lowered until the grid
-// fits both the caller's budget and the shared-memory grid limit (and the
-// exact-binomial limit).  Terms above it are enclosed by coefficient
+// fits both the caller's budget and the grid limit (shared memory, or with
+// the global-memory path BERN_MAX_BIG_GRID at orders <= 16), and the
+// exact-binomial limit.  Terms above it are enclosed by coefficient
 // intervals (budget rule).
-int effective_order(int n, int order, int64_t budget, int* grid_out) {
+int effective_order(int n, int order, int64_t budget, int* grid_out, bool big) {
   if (budget <= 0) budget = (int64_t)1 << 20;
-  int64_t lim = budget < kEncloseGridMax ? budget : kEncloseGridMax;
+  const int64_t gmax = big ? (int64_t)BERN_MAX_BIG_GRID : (int64_t)kEncloseGridMax;
+  const int64_t lim = budget < gmax ? budget : gmax;
   int lb = order < kMaxEncloseOrder ? order : kMaxEncloseOrder;
   for (; lb > 0; --lb) {
     int64_t g = 1;
     for (int k = 0; k < n && g <= lim; ++k) g *= (lb + 1);
-    if (g <= lim) break;
+    if (g <= lim && (g <= kEncloseGridMax || lb <= 16)) break;
   }
   int64_t g = 1;
   for (int k = 0; k < n; ++k) g *= (lb + 1);
   *grid_out = (int)g;
   return lb;
+}
+
+// ReLU cases and coefficients of the items of a list (the enclosure of grids
+// above shared memory computes lo/hi only).
+__global__ void k_relu_coeffs_list(const int* __restrict__ list, const int* __restrict__ count,
+                                   int64_t n_items, const float* __restrict__ lo,
+                                   const float* __restrict__ hi, const uint8_t* __restrict__ degrees,
+                                   int global_d, int8_t* __restrict__ kind, float* __restrict__ coef,
+                                   float* __restrict__ eps, int* status) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = list ? (int64_t)*count : n_items;
+  if (i >= n) return;
+  const int64_t it = list ? (int64_t)list[i] : i;
+  const int d = degrees ? (int)degrees[it] : global_d;
+  kind[it] = (int8_t)relu_item(lo[it], hi[it], d, coef + it * kCoefStride, eps + it, status);
 }
 
 static cudaError_t launch_enclose_impl(const Launch& L, const Tables& T, int64_t n_boxes, int h,
@@ -101,8 +118,19 @@ static cudaError_t launch_enclose_impl(const Launch& L, const Tables& T, int64_t
   const int64_t n_items = n_boxes * h;   // with a list: its largest possible length
   if (n_items == 0) return cudaSuccess;
   int G;
-  const int lb = effective_order(T.n, order, budget, &G);
+  const int lb = effective_order(T.n, order, budget, &G, L.ews != nullptr);
   if (lb > T.rscale_max || T.rscale[lb] == nullptr) return cudaErrorInvalidValue;
+  if (G > kEncloseGridMax) {
+    // global-memory grids: lo/hi, then the ReLU step on the same items
+    cudaError_t e = launch_enclose_big(L, T, lb, G, n_items, h, pre_up, pre_lo, ld, nterms, lo,
+                                       hi, ro.list, ro.count);
+    if (e != cudaSuccess || ro.kind == nullptr) return e;
+    k_relu_coeffs_list<<<(unsigned)((n_items + 127) / 128), 128, 0, L.stream>>>(
+        ro.list, ro.count, n_items, lo, hi, ro.degrees, ro.global_d, ro.kind, ro.coef, ro.eps,
+        L.status);
+    ++*L.launches;
+    return cudaGetLastError();
+  }
   if (G <= kSmallGrid && lb <= 7) {
 #define BERN_SMALL_CASE(X) \
   case X: return launch_small<X>(L, T, G, n_items, h, pre_up, pre_lo, ld, nterms, lo, hi, ro);

@@ -653,8 +653,10 @@ bool layer_fused_shape(int n, int h, int hn, int d, int D_pre, int order, int64_
   if (D_pre < 0 || D_pre > std::min(kMaxRowDegree, row_path_max_degree(n))) return false;
   if (cap < 1 || cap > kMaxTableDegree) return false;
   int G = 0;
-  const int lb = effective_order(n, order, budget, &G);
-  if (lb > kLayerMaxOrder || lb > max_enclose_order(n)) return false;
+  // the order bern_propagate's enclosure uses (with its global-memory path):
+  // grids beyond shared memory are not fused
+  const int lb = effective_order(n, order, budget, &G, true);
+  if (G > kEncloseGridMax || lb > kLayerMaxOrder || lb > max_enclose_order(n)) return false;
   const int64_t m_pre = num_monomials(n, D_pre);
   if (m_pre < 1) return false;
   LayerShape S;

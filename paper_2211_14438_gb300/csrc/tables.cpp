@@ -254,6 +254,16 @@ int max_enclose_order(int n) {
   return l;
 }
 
+int max_enclose_order_big(int n) {
+  int l = kMaxEncloseOrder;
+  for (; l > 0; --l) {
+    int64_t g = 1;
+    for (int k = 0; k < n && g <= BERN_MAX_BIG_GRID; ++k) g *= (l + 1);
+    if (g <= BERN_MAX_GRID || (g <= BERN_MAX_BIG_GRID && l <= 16)) break;
+  }
+  return std::max(l, max_enclose_order(n));
+}
+
 void build_rscale(int n, int l, std::vector<float>& out) {
   std::vector<uint8_t> ex;
   graded_monomials(n, l, ex);
@@ -289,7 +299,8 @@ namespace bern {
 // holds, for each variable k and each line Ln along k (Ln enumerates the
 // digits of the other variables, the highest variable first), the pair
 // (base offset, digit sum of the variables before k).
-void build_enclose_tables(int n, int l, std::vector<int32_t>& gidx, std::vector<int32_t>& lines) {
+void build_enclose_tables(int n, int l, std::vector<int32_t>& gidx, std::vector<int32_t>& lines,
+                          bool with_lines) {
   const int R = l + 1;
   std::vector<int64_t> pw(n);
   int64_t p = 1;
@@ -306,6 +317,8 @@ void build_enclose_tables(int n, int l, std::vector<int32_t>& gidx, std::vector<
     for (int k = 0; k < n; ++k) ix += ex[(size_t)r * n + k] * pw[k];
     gidx[(size_t)r] = (int32_t)ix;
   }
+  lines.clear();
+  if (!with_lines) return;
   int64_t nlines = 1;
   for (int k = 0; k < n - 1; ++k) nlines *= R;
   lines.assign((size_t)(2 * n * nlines), 0);

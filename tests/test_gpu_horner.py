@@ -47,7 +47,7 @@ def check_all(ctx, net, boxes, degree, cap=16, tau=0.0, mc=20_000, seed=0):
     checked = 0
     for bi in range(len(boxes)):
         r = oracle.propagate(widths, net.W, net.b, boxes[bi], degs, cap=cap, tau=tau,
-                             budget=bern.effective_budget())
+                             budget=1 << 20)
         if not near_tie(r):
             compare_box(g, bi, r, widths[0], widths[-1])
             checked += 1

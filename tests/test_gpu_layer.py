@@ -165,7 +165,7 @@ def test_layer_against_oracle(ctx, n, D, h, hn, d, cap, B, ragged):
     nu, nl, nnt, Mn = run_layer(ctx, n, up, lo, nt, order, d, cap, W, bias)
     gu = from_layer_block(nu, B, Mn, hn)
     gl = from_layer_block(nl, B, Mn, hn)
-    want = oracle_layer(n, up, lo, nt, order, d, cap, W, bias, bern.effective_budget(0))
+    want = oracle_layer(n, up, lo, nt, order, d, cap, W, bias, 1 << 20)
     for b in range(B):
         rows, post_u, post_l = want[b]
         k = int(nnt[b, 0])

@@ -100,7 +100,7 @@ def test_lin_many_inputs(ctx, widths):
     n = widths[0]
     net = wl.make_net(widths, seed=40 + n)
     box = wl.box_array([-0.5] * n, [0.5] * n)
-    budget = bern.effective_budget(0)
+    budget = 1 << 20              # the plans' default budget
     g = run_gpu(ctx, net, box[None], lin=1)
     r = oracle.propagate(net.widths, net.W, net.b, box, 2, lin=1, budget=budget)
     if not near_tie(r):
