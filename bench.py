@@ -765,14 +765,31 @@ def run_ours(args, rank, world, local_rank, dist):
         info5 = lm.fit(ctx, w5.net.widths, w5.net.W, w5.net.b, tr5, cap=16)
         train5 = time.time() - t0
         bnb5 = {"workload": "branch-and-bound network [6,64x4,1] seed 4, root [-1,1]^6, best-first "
-                            "refinement of output 0 in rounds of 1024 splits (widest side) "
-                            "until 4096 leaves; boxes/s counts every bounded child, wall "
-                            "clock with host work",
+                            "refinement of output 0 in rounds of 1024 splits until %d "
+                            "leaves: plain order 2 and the learned degrees with the widest "
+                            "side split, and the learned degrees with the learned split head; "
+                            "boxes/s counts every bounded child, wall clock with host work"
+                            % args.bnb_leaves,
                 "learned_caps": info5["max_per_layer"], "train_seconds": round(train5, 2)}
-        for name, deg in (("plain", 2), ("learned", info5["plan"])):
+        # the split head: trained on the leaves of a widest-side and a random-side
+        # search, labelled by the plain method (the dimension whose halving
+        # gives the smallest larger child upper bound)
+        t0 = time.time()
+        fn_plain = bnb.gpu_bound_fn(ctx, w5.net.widths, w5.net.W, w5.net.b, root5, 2, 16, 0.0)
+        sb, sf = bnb.split_training_boxes(fn_plain, root5, rounds=10, batch=64)
+        slab = bnb.split_labels(fn_plain, sb)
+        head, head_loss = bnb.train_split_head(ctx, sf, slab, 6)
+        split_fn = bnb.mlp_split_fn(ctx, head, root5)
+        bnb5["split_head"] = {"train_boxes": int(len(sb)), "train_seconds": round(time.time() - t0, 2),
+                              "loss": round(head_loss, 4),
+                              "label_histogram": np.bincount(slab, minlength=6).tolist()}
+        arms = (("plain", 2, None), ("learned", info5["plan"], None),
+                ("learned_split", info5["plan"], split_fn))
+        for name, deg, sfn in arms:
             fn = bnb.gpu_bound_fn(ctx, w5.net.widths, w5.net.W, w5.net.b, root5, deg, 16, 0.0)
             fn(root5[None])                                   # warm-up (tuning, graphs)
-            bb = bnb.BranchAndBound(fn, root5, batch=1024, max_leaves=4096)
+            bb = bnb.BranchAndBound(fn, root5, split_fn=sfn, batch=1024,
+                                    max_leaves=args.bnb_leaves)
             torch.cuda.synchronize()
             t0 = time.time()
             bb.run(64)
@@ -957,6 +974,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--bnb-leaves", type=int, default=4096,
+                    help="leaf budget of the branch-and-bound refinement (65536: the stated size)")
     ap.add_argument("--no-bnb", action="store_true",
                     help="skip the branch-and-bound refinement of the [6,64x4,1] root box [-1,1]^6")
     ap.add_argument("--no-learned", action="store_true",

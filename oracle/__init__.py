@@ -62,6 +62,9 @@ def _load():
     lib.orc_relu_coeffs.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp]
     lib.orc_bernstein_coeffs.restype = ctypes.c_int
     lib.orc_bernstein_coeffs.argtypes = [ctypes.c_int, ctypes.c_int, u8, dp, ctypes.c_int, dp]
+    lib.orc_bernstein_coeffs_factored.restype = ctypes.c_int
+    lib.orc_bernstein_coeffs_factored.argtypes = [ctypes.c_int, ctypes.c_int, u8, dp,
+                                                  ctypes.c_int, dp]
     lib.orc_enclosure.restype = ctypes.c_int
     lib.orc_enclosure.argtypes = [ctypes.c_int, ctypes.c_int, u8, dp, ctypes.c_int,
                                   ctypes.c_longlong, dp, dp]
@@ -152,10 +155,23 @@ def relu_coeffs(lo: float, hi: float, d: int):
 
 
 def bernstein_coeffs(p, n: int, l: int) -> np.ndarray:
-    """Bernstein coefficients on [0,1]^n, order l per variable, shape (l+1,)*n."""
+    """Bernstein coefficients on [0,1]^n, order l per variable, shape (l+1,)*n
+    (Def. 2 term by term)."""
     e, c = as_poly(p, n)
     out = np.zeros((l + 1) ** n)
     rc = _load().orc_bernstein_coeffs(n, len(c), _u8(e), _dp(c), l, _dp(out))
+    if rc:
+        raise ValueError("polynomial exponent exceeds Bernstein order")
+    return out.reshape((l + 1,) * n)
+
+
+def bernstein_coeffs_factored(p, n: int, l: int) -> np.ndarray:
+    """The same coefficients by the weight's factorisation over the variables
+    (one triangular transform per variable), which the enclosure uses on large
+    grids."""
+    e, c = as_poly(p, n)
+    out = np.zeros((l + 1) ** n)
+    rc = _load().orc_bernstein_coeffs_factored(n, len(c), _u8(e), _dp(c), l, _dp(out))
     if rc:
         raise ValueError("polynomial exponent exceeds Bernstein order")
     return out.reshape((l + 1,) * n)

@@ -134,6 +134,46 @@ bool bernstein_coeffs(const Poly& p, int n, int l, std::vector<double>& out) {
   return true;
 }
 
+// The same coefficients with the weight's factorisation over the variables:
+// prod_k C(i_k, j_k) / C(l, j_k) = prod_k C(i_k, j_k) * (1 / prod_k C(l, j_k)),
+// so b = T_1 (x) ... (x) T_n applied to c_J = a_J / prod_k C(l, j_k), where T
+// is the lower-triangular matrix C(i, j), j <= i <= l.  Applied one variable
+// at a time (line by line), that is n (l+1)^n (l+2)/2 multiply-adds instead of
+// (l+1)^n times the number of terms; used for large grids.
+bool bernstein_coeffs_factored(const Poly& p, int n, int l, std::vector<double>& out) {
+  const size_t R = (size_t)(l + 1);
+  size_t grid = 1;
+  for (int k = 0; k < n; ++k) grid *= R;
+  out.assign(grid, 0.0);
+  for (const auto& term : p) {
+    size_t idx = 0;
+    double scale = 1.0;
+    for (int k = 0; k < n; ++k) {
+      if (term.first[k] > l) return false;
+      idx = idx * R + (size_t)term.first[k];
+      scale *= binom(l, term.first[k]);
+    }
+    out[idx] += term.second / scale;
+  }
+  std::vector<double> x(R), y(R);
+  for (int k = 0; k < n; ++k) {
+    size_t stride = 1;
+    for (int m = k + 1; m < n; ++m) stride *= R;
+    // every line along variable k: cells whose digit k runs over 0..l
+    for (size_t g = 0; g < grid; ++g) {
+      if ((g / stride) % R != 0) continue;      // g is the line's first cell
+      for (size_t i = 0; i < R; ++i) x[i] = out[g + i * stride];
+      for (size_t i = 0; i < R; ++i) {
+        double acc = 0.0;
+        for (size_t j = 0; j <= i; ++j) acc += binom((int)i, (int)j) * x[j];
+        y[i] = acc;
+      }
+      for (size_t i = 0; i < R; ++i) out[g + i * stride] = y[i];
+    }
+  }
+  return true;
+}
+
 size_t grid_size(int n, int l) {
   size_t g = 1;
   for (int k = 0; k < n; ++k) {
@@ -161,7 +201,12 @@ bool enclosure(const Poly& p, int n, int l, long long budget, double* emin,
   }
   if (head.empty()) head = poly_const(n, 0.0);
   std::vector<double> b;
-  if (!bernstein_coeffs(head, n, lb, b)) return false;
+  // the definition term by term while it is cheap, the factored form above
+  if ((double)grid_size(n, lb) * (double)head.size() <= 4.0e6) {
+    if (!bernstein_coeffs(head, n, lb, b)) return false;
+  } else {
+    if (!bernstein_coeffs_factored(head, n, lb, b)) return false;
+  }
   double mn = b[0], mx = b[0];
   for (double v : b) {
     mn = std::min(mn, v);
@@ -380,6 +425,14 @@ int orc_bernstein_coeffs(int n, int nterms, const uint8_t* exps,
                          const double* coef, int l, double* out) {
   std::vector<double> b;
   if (!bernstein_coeffs(from_arrays(n, nterms, exps, coef), n, l, b)) return 1;
+  std::memcpy(out, b.data(), b.size() * sizeof(double));
+  return 0;
+}
+
+int orc_bernstein_coeffs_factored(int n, int nterms, const uint8_t* exps,
+                                  const double* coef, int l, double* out) {
+  std::vector<double> b;
+  if (!bernstein_coeffs_factored(from_arrays(n, nterms, exps, coef), n, l, b)) return 1;
   std::memcpy(out, b.data(), b.size() * sizeof(double));
   return 0;
 }

@@ -145,6 +145,41 @@ def test_bernstein_vertex_property(n, deg, l):
         assert b[I] == pytest.approx(v, abs=1e-12 * (1 + abs(v)))
 
 
+@pytest.mark.parametrize("n,deg,l", [(1, 5, 7), (2, 4, 4), (2, 3, 6), (3, 3, 3), (3, 2, 5),
+                                     (4, 2, 2), (5, 1, 2)])
+def test_bernstein_factored_equals_definition(n, deg, l):
+    """The factored transform (one triangular binomial transform per
+    variable, used by the enclosure on large grids) gives Def. 2's
+    coefficients computed term by term, and it satisfies the expansion
+    identity and the vertex property itself."""
+    rng = np.random.default_rng(500 + 10 * n + deg + l)
+    p = random_poly(rng, n, deg)
+    a = oracle.bernstein_coeffs(p, n, l)
+    b = oracle.bernstein_coeffs_factored(p, n, l)
+    sc = 1 + np.abs(p[1]).sum()
+    assert np.max(np.abs(a - b)) <= 1e-12 * sc
+    t = rng.random(n)
+    s = sum(b[I] * ber_basis(I, l, t) for I in itertools.product(range(l + 1), repeat=n))
+    assert s == pytest.approx(oracle.eval_poly(p, n, t[None])[0], abs=1e-11 * sc)
+    for corner in itertools.product([0, 1], repeat=n):
+        v = oracle.eval_poly(p, n, np.array([corner], float))[0]
+        assert b[tuple(c * l for c in corner)] == pytest.approx(v, abs=1e-12 * (1 + abs(v)))
+
+
+def test_enclosure_large_grid_uses_the_same_coefficients():
+    """A six-variable degree-4 polynomial at order 5 (6^6 = 46,656 cells x 210
+    terms, past the term-by-term threshold): the enclosure is the min/max of
+    the factored coefficients, and it contains the polynomial on a grid."""
+    rng = np.random.default_rng(77)
+    p = random_poly(rng, 6, 4)
+    mn, mx = oracle.enclosure(p, 6, 5)
+    b = oracle.bernstein_coeffs_factored(p, 6, 5)
+    assert mn == pytest.approx(b.min(), abs=1e-12) and mx == pytest.approx(b.max(), abs=1e-12)
+    pts = rng.random((2000, 6))
+    v = oracle.eval_poly(p, 6, pts)
+    assert mn <= v.min() + 1e-12 and mx >= v.max() - 1e-12
+
+
 @pytest.mark.parametrize("n,deg,grid", [(1, 6, 2001), (2, 4, 201), (2, 8, 201), (3, 4, 41)])
 def test_enclosure_contains_dense_grid(n, deg, grid):
     """Def. 2: min b <= p(t) <= max b for every t; checked against a dense
