@@ -682,6 +682,7 @@ std::string graph_key(const Plan& P, const bern_net* net, const float* boxes, in
     add(&net->W[i], sizeof(void*));
     add(&net->b[i], sizeof(void*));
     add(&P.L[i].d, sizeof(int));
+    add(&P.L[i].fused, sizeof(bool));   // fused and per-step launch sequences differ
   }
   add(P.neuron_deg.data(), P.neuron_deg.size());
   add(&r, sizeof r);
@@ -1099,7 +1100,10 @@ int bern_propagate_traced(bern_ctx* c, const bern_net* net, const float* boxes,
       add(&P.lin, sizeof P.lin);
       add(&P.learned, sizeof P.learned);
       for (int i = 0; i <= P.H; ++i) add(&net->widths[i], sizeof(int));
-      for (const auto& l : P.L) add(&l.d, sizeof l.d);
+      for (const auto& l : P.L) {
+        add(&l.d, sizeof l.d);
+        add(&l.fused, sizeof l.fused);
+      }
     }
     if (!c->tuned.count(sig)) {
       const int64_t B = std::min(chunk, n_boxes);
