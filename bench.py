@@ -974,7 +974,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--bnb-leaves", type=int, default=4096,
+    ap.add_argument("--bnb-leaves", type=int, default=65536,
                     help="leaf budget of the branch-and-bound refinement (65536: the stated size)")
     ap.add_argument("--no-bnb", action="store_true",
                     help="skip the branch-and-bound refinement of the [6,64x4,1] root box [-1,1]^6")
