@@ -432,6 +432,75 @@ def lin_entries(ctx, torch, dev, flush, args, w, Wd, bd, boxes_d, plain_ms, plai
     return res
 
 
+# ------------------------------------------- Bernstein-tensor arithmetic (Sec. 4)
+def bernstein_basis_entry(ctx, torch, dev, flush, args):
+    """The composition's squares in the paper's representation against the power
+    basis, on the layer-4 size of the benchmark net (three variables, degree
+    8): P = 4096 items of the power-basis composition at order 2 (both bounds:
+    two squares of 165-term polynomials per item, the library's row kernels,
+    plus the queue, the linear term and the epilogue), against 2P Prod_Bern
+    squares of order-8 Bernstein tensors (9^3 = 729 coefficients, 729^2 term
+    products each, bern_bernstein_square).  Random seeded coefficients; CUDA
+    events, L2 flushed before every timed call."""
+    from paper_2211_14438_gb300 import bern
+    n, D, P, h = 3, 8, 4096, 64
+    B = P // h
+    M, Mo = bern.num_monomials(n, D), bern.num_monomials(n, 2 * D)
+    rng = np.random.default_rng(4242)
+    deg = np.array([sum(r) for r in bern.monomials(n, D)], np.float64)
+    base = (rng.normal(0, 0.3, (P, M)) * 0.6 ** deg).astype(np.float32)
+    gap = np.abs(rng.normal(0, 0.01, (P, M)) * 0.6 ** deg).astype(np.float32)
+    up, lo_p = base + gap, base - gap
+    mag = np.abs(up).sum(1) + np.abs(lo_p).sum(1)
+    lo = (-mag - 1.0).astype(np.float32)                 # every item unstable
+    hi = (mag + 1.0).astype(np.float32)
+    blk = lambda a: torch.from_numpy(np.ascontiguousarray(a.reshape(B, h, M).transpose(0, 2, 1))).to(dev)
+    pu, pl = blk(up), blk(lo_p)
+    nt = torch.full((P,), M, dtype=torch.int32, device=dev)
+    glo, ghi = torch.from_numpy(lo).to(dev), torch.from_numpy(hi).to(dev)
+    kind = torch.zeros(P, dtype=torch.int8, device=dev)
+    coef = torch.zeros(P * bern.COEF_STRIDE, device=dev)
+    eps = torch.zeros(P, device=dev)
+    ctx.relu_coeffs(P, glo, ghi, None, 2, kind, coef, eps)
+    qu = torch.empty(B * Mo * h, device=dev)
+    ql = torch.empty_like(qu)
+    qnt = torch.empty(P, dtype=torch.int32, device=dev)
+    tens = torch.from_numpy(rng.normal(0, 1, (2 * P, (D + 1) ** n)).astype(np.float32)).to(dev)
+    chi = torch.empty(2 * P, (2 * D + 1) ** n, device=dev)
+    clo = torch.empty_like(chi)
+    stream = ctx.stream
+
+    def timed(fn, reps=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        if ctx.sync() != 0:
+            raise RuntimeError("bernstein-basis comparison failed")
+        return float(np.median(ms))
+
+    ms_pow = timed(lambda: ctx.compose(n, B, h, 16, 0.0, kind, coef, eps, None, 2, glo, ghi, pu,
+                                       pl, M, nt, qu, ql, Mo, qnt))
+    ms_bern = timed(lambda: ctx.bernstein_square(n, D, tens, chi, clo))
+    return {"workload": "4096 items of three variables at degree 8 (the benchmark net's layer-4 "
+                        "size), both bounds: 8192 squares in each representation",
+            "power_basis_composition_ms": round(ms_pow, 4),
+            "bernstein_prod_bern_squares_ms": round(ms_bern, 4),
+            "bernstein_over_power_time": round(ms_bern / ms_pow, 2),
+            "term_products_per_square": {"power_basis": M * (M + 1) // 2,
+                                         "bernstein_tensor": ((D + 1) ** n) ** 2},
+            "coefficients": {"power_basis_in_out": [M, Mo],
+                             "bernstein_in_out": [(D + 1) ** n, (2 * D + 1) ** n]}}
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args, rank, world, local_rank, dist):
     import torch
@@ -800,6 +869,14 @@ def run_ours(args, rank, world, local_rank, dist):
                           "U": round(bb.upper(), 5), "L": round(bb.lower(), 5),
                           "seconds": round(dt, 3)}
 
+    # ---- the paper's Bernstein-tensor squares against the power basis (context)
+    bern_basis = None
+    if world == 1 and not args.no_bernstein_basis:
+        try:
+            bern_basis = bernstein_basis_entry(ctx, torch, dev, flush, args)
+        except Exception as ex:
+            bern_basis = {"error": "%s: %s" % (type(ex).__name__, ex)}
+
     # ---- Lin linearisation (Sec. 5.3); reported beside the headline, which
     # it can never cost: an error here is recorded, not raised
     lin_res = None
@@ -849,6 +926,7 @@ def run_ours(args, rank, world, local_rank, dist):
         "kernel_pass_ms_per_step": round(total_kernel_ms, 4),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "learned": learned, "learned_6in": learned4, "bnb_6in": bnb5, "lin": lin_res,
+        "bernstein_basis": bern_basis,
         "clocks": clocks,
     }
     return line
@@ -982,6 +1060,8 @@ def main():
                     help="skip training and timing the learned-degree form")
     ap.add_argument("--no-lin", action="store_true",
                     help="skip timing the Lin-linearised forms")
+    ap.add_argument("--no-bernstein-basis", action="store_true",
+                    help="skip the Bernstein-tensor (Prod_Bern) comparison")
     ap.add_argument("--fused", action="store_true",
                     help="headline through the fused layer kernels (bern_set_fused(1))")
     ap.add_argument("--no-alt-path", action="store_true",

@@ -411,6 +411,23 @@ int bern_layer(bern_ctx* ctx, int n, int64_t n_boxes, int h, int order, int64_t 
                const float* b_next, float* next_up, float* next_lo, int64_t next_ld,
                int32_t* next_nterms);
 
+/* The paper's own representation, for comparison with the power basis: the
+ * square of polynomials held as dense Bernstein tensors of order l in every
+ * variable (Sec. 4.1), by Prod_Bern (Sec. 4.2: scale by the binomial
+ * tensors, multiply as power series, unscale):
+ *   c_K = [sum_{I+J=K} (a_I C_l(I)) (a_J C_l(J))] / C_2l(K),
+ *   C_l(I) = prod_k C(l, i_k).
+ *   a    : [n_polys x (l+1)^n] tensors, index sum_k i_k (l+1)^(n-1-k)
+ *          (t_1 the slowest), device pointer;
+ *   c_hi, c_lo : [n_polys x (2l+1)^n], the same indexing at order 2l: an
+ *          interval containing every exact coefficient of the square
+ *          (round-to-nearest sums widened by their a-posteriori error bound).
+ * n <= 4 and l <= 8 with (max_k C(l,k))^n < 2^24 (BERN_E_UNSUPPORTED
+ * otherwise).  Asynchronous on the context's stream; a non-finite
+ * coefficient is reported by bern_sync. */
+int bern_bernstein_square(bern_ctx* ctx, int n, int l, int64_t n_polys, const float* a,
+                          float* c_hi, float* c_lo);
+
 /* Use the fused layer kernel (bern_layer) inside bern_propagate wherever a
  * plan allows it (default 0): plain plans (BERN_DEG_GLOBAL or PER_LAYER) with
  * prune_tau = 0, untraced, layer by layer where the shape qualifies and the

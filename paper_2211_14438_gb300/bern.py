@@ -56,6 +56,7 @@ EXPORTS = [
     "bern_mlp_adam", "bern_propagate_traced", "bern_split_features",
     "bern_set_horner_smem_limit", "bern_set_autotune", "bern_force_variant",
     "bern_poly_to_x", "bern_linearize", "bern_fma_throughput", "bern_layer", "bern_set_fused",
+    "bern_bernstein_square",
 ]
 
 
@@ -141,6 +142,7 @@ def load(build_if_missing: bool = True):
                              V]),
         "bern_layer": (I, [V, I, I64, I, I, I64, I, I, V, V, I64, V, I, V, V, V, V, I64, V]),
         "bern_set_fused": (I, [V, I]),
+        "bern_bernstein_square": (I, [V, I, I, I64, V, V, V]),
         "bern_propagate_noalloc": (I, [ctypes.POINTER(bern_net), V, I64,
                                        ctypes.POINTER(bern_degree_plan),
                                        ctypes.POINTER(bern_result), V]),
@@ -245,6 +247,12 @@ class Context:
         ("affine" or "enclose") for later launches (tests and tuning)."""
         _check(self.lib.bern_force_variant(self.h, kind.encode(), int(variant)),
                "bern_force_variant")
+
+    def bernstein_square(self, n, l, a, c_hi, c_lo):
+        """bern_bernstein_square: Prod_Bern squares of dense Bernstein tensors
+        a [P, (l+1)^n] into coefficient intervals [c_lo, c_hi] [P, (2l+1)^n]."""
+        _check(self.lib.bern_bernstein_square(self.h, n, l, int(a.shape[0]), _ptr(a), _ptr(c_hi),
+                                              _ptr(c_lo)), "bern_bernstein_square")
 
     def set_fused(self, on: bool):
         _check(self.lib.bern_set_fused(self.h, 1 if on else 0), "bern_set_fused")

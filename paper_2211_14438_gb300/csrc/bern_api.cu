@@ -804,6 +804,14 @@ int bern_set_graphs(bern_ctx* c, int enable) {
   return BERN_OK;
 }
 
+int bern_bernstein_square(bern_ctx* c, int n, int l, int64_t n_polys, const float* a,
+                          float* c_hi, float* c_lo) {
+  if (!c || n_polys < 0 || (n_polys > 0 && (!a || !c_hi || !c_lo))) return BERN_E_INVALID;
+  if (!bernstein_square_ok(n, l)) return BERN_E_UNSUPPORTED;
+  cudaSetDevice(c->device);
+  return map_cuda(launch_bernstein_square(c->launch(), n, l, n_polys, a, c_hi, c_lo));
+}
+
 int bern_set_fused(bern_ctx* c, int enable) {
   if (!c) return BERN_E_INVALID;
   c->fused = enable ? 1 : 0;

@@ -288,6 +288,13 @@ cudaError_t launch_enclose_big(const Launch& L, const Tables& T, int lb, int G, 
                                const int32_t* nterms, float* lo, float* hi, const int* list,
                                const int* count);
 
+// The square of dense Bernstein tensors by Prod_Bern (k_bern_tensor.cu):
+// a [n_polys][(l+1)^n] -> coefficient intervals [c_lo, c_hi] of the square at
+// order 2l, [n_polys][(2l+1)^n].  n <= 4, l <= 8, (max_k C(l,k))^n < 2^24.
+bool bernstein_square_ok(int n, int l);
+cudaError_t launch_bernstein_square(const Launch& L, int n, int l, int64_t n_polys,
+                                    const float* a, float* c_hi, float* c_lo);
+
 // Largest input degree the row-convolution path handles for n variables.
 int row_path_max_degree(int n);
 cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratch& S,
