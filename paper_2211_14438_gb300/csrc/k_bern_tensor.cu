@@ -8,8 +8,9 @@
 // the Bernstein tensor of the square at order 2l (scale by the binomial
 // tensors, multiply as power series, i.e. the full n-dimensional convolution,
 // unscale).  One block per polynomial: the scaled tensor in shared memory,
-// the threads over the output cells K, each summing over the box of I with
-// max(0, k_j - l) <= i_j <= min(k_j, l).  The sums run in round-to-nearest
+// a thread per output row along the last variable, which adds the 1-D
+// convolutions of every pair of input rows whose prefixes sum to its own
+// (register-blocked, compile-time row length).  The sums run in round-to-nearest
 // beside the sum of the terms' magnitudes; an a-posteriori bound of every
 // rounding on the way (the scaling products, the term products, the m-term
 // sum, the binomial and the division) widens each coefficient to an
@@ -24,59 +25,84 @@ namespace bern {
 
 namespace {
 
-constexpr int kBtThreads = 256;
+constexpr int kBtMaxThreads = 512;
 constexpr int kBtMaxVars = 4;
 constexpr int kBtMaxOrder = 8;
 
 __device__ __forceinline__ float binom_l(int l, int k) { return binomf(l, k); }
 
-__global__ void __launch_bounds__(kBtThreads)
-k_bern_square(int n, int l, int64_t n_polys, const float* __restrict__ a, float* __restrict__ c_hi,
+// One thread per output row (the 2L+1 cells that differ only in the last
+// variable): for every pair of input rows whose prefixes add up to the output
+// row's prefix, the 1-D convolution of the two rows (compile-time length
+// L+1) into the row's accumulators, beside the same convolution of the
+// magnitudes.  The tensor of the polynomial is scaled once per block.
+template <int L>
+__global__ void __launch_bounds__(kBtMaxThreads)
+k_bern_square(int n, int64_t n_polys, const float* __restrict__ a, float* __restrict__ c_hi,
               float* __restrict__ c_lo, int* status) {
-  extern __shared__ float su[];                 // (l+1)^n scaled coefficients
-  const int R = l + 1, Ro = 2 * l + 1;
-  int G = 1, Go = 1;
+  extern __shared__ float su[];                 // (L+1)^n scaled coefficients
+  constexpr int R = L + 1, Ro = 2 * L + 1;
+  int G = 1, Go = 1, rows_out = 1;
   for (int k = 0; k < n; ++k) {
     G *= R;
     Go *= Ro;
   }
+  rows_out = Go / Ro;
+  // the largest number of products one output cell sums (a bound for the
+  // a-posteriori error): (L+1)^n
+  const float ku = (float)(G + 2 * n + 6) * kU;
+  const float gamma = __fdiv_ru(ku, __fsub_rd(1.0f, ku));
   for (int64_t p = blockIdx.x; p < n_polys; p += gridDim.x) {
     const float* ap = a + p * G;
-    for (int g = threadIdx.x; g < G; g += kBtThreads) {
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
       int rest = g;
       float w = 1.0f;
       for (int k = n - 1; k >= 0; --k) {
-        w *= binom_l(l, rest % R);              // C(l, i) <= C(8,4) = 70: the product of
-        rest /= R;                              // up to four is < 2^24, exact in float
+        w *= binom_l(L, rest % R);              // exact: (max_k C(L,k))^n < 2^24
+        rest /= R;
       }
       su[g] = __fmul_rn(ap[g], w);
     }
     __syncthreads();
-    for (int K = threadIdx.x; K < Go; K += kBtThreads) {
+    for (int orow = threadIdx.x; orow < rows_out; orow += blockDim.x) {
       int kd[kBtMaxVars], lo[kBtMaxVars], hi[kBtMaxVars], id[kBtMaxVars];
-      int rest = K;
-      float ck = 1.0f;
-      for (int k = n - 1; k >= 0; --k) {
+      int rest = orow;
+      float ck_row = 1.0f;
+      const int np = n - 1;                     // prefix digits (variables 1..n-1)
+      for (int k = np - 1; k >= 0; --k) {
         kd[k] = rest % Ro;
         rest /= Ro;
-        lo[k] = max(0, kd[k] - l);
-        hi[k] = min(kd[k], l);
+        lo[k] = max(0, kd[k] - L);
+        hi[k] = min(kd[k], L);
         id[k] = lo[k];
-        ck *= binom_l(2 * l, kd[k]);            // rounded: C(16,8)^n exceeds 2^24
+        ck_row *= binom_l(2 * L, kd[k]);        // rounded: C(2L, .)^n can exceed 2^24
       }
-      float s = 0.0f, m = 0.0f;
-      int terms = 0;
+      float acc[Ro], mag[Ro];
+#pragma unroll
+      for (int c = 0; c < Ro; ++c) {
+        acc[c] = 0.0f;
+        mag[c] = 0.0f;
+      }
       for (;;) {
-        int gi = 0, gj = 0;
-        for (int k = 0; k < n; ++k) {
-          gi = gi * R + id[k];
-          gj = gj * R + (kd[k] - id[k]);
+        int ri = 0, rj = 0;
+        for (int k = 0; k < np; ++k) {
+          ri = ri * R + id[k];
+          rj = rj * R + (kd[k] - id[k]);
         }
-        const float x = su[gi], y = su[gj];
-        s = __fmaf_rn(x, y, s);
-        m = __fmaf_rn(fabsf(x), fabsf(y), m);
-        ++terms;
-        int k = n - 1;                          // odometer over the box of I
+        float x[R], y[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+          x[t] = su[ri * R + t];
+          y[t] = su[rj * R + t];
+        }
+#pragma unroll
+        for (int u = 0; u < R; ++u)
+#pragma unroll
+          for (int v = 0; v < R; ++v) {
+            acc[u + v] = __fmaf_rn(x[u], y[v], acc[u + v]);
+            mag[u + v] = __fmaf_rn(fabsf(x[u]), fabsf(y[v]), mag[u + v]);
+          }
+        int k = np - 1;                         // odometer over the prefix box
         while (k >= 0 && id[k] == hi[k]) {
           id[k] = lo[k];
           --k;
@@ -84,27 +110,49 @@ k_bern_square(int n, int l, int64_t n_polys, const float* __restrict__ a, float*
         if (k < 0) break;
         ++id[k];
       }
-      // |s - exact numerator| <= gamma_(terms+4) * sum |terms| (the two scaled
-      // factors, the product and the terms-1 additions), and the computed m
-      // underestimates that sum by at most the same factor; the binomial
-      // product ck carries n roundings.  gamma_k = k u / (1 - k u), with k
-      // taken as terms + 2n + 6 to cover all of them.
-      const float ku = (float)(terms + 2 * n + 6) * kU;
-      const float gamma = __fdiv_ru(ku, __fsub_rd(1.0f, ku));
-      const float err = __fmul_ru(gamma, __fmul_ru(m, __fadd_ru(1.0f, gamma)));
-      const float c_min = __fmul_rd(ck, __fsub_rd(1.0f, gamma));   // <= the exact C_2l(K)
-      const float c_max = __fmul_ru(ck, __fadd_ru(1.0f, gamma));   // >= it
-      const float nh = __fadd_ru(s, err), nl = __fsub_rd(s, err);
-      // dividing by the smaller divisor moves a positive numerator up and a
-      // negative one down
-      const float hi2 = nh >= 0.0f ? __fdiv_ru(nh, c_min) : __fdiv_ru(nh, c_max);
-      const float lo2 = nl <= 0.0f ? __fdiv_rd(nl, c_min) : __fdiv_rd(nl, c_max);
-      c_hi[p * Go + K] = hi2;
-      c_lo[p * Go + K] = lo2;
-      if (!isfinite(hi2) || !isfinite(lo2)) atomicOr(status, kStatusNonFinite);
+      // |acc - exact numerator| <= gamma_(terms+4) sum |terms| and the computed
+      // mag falls short of that sum by at most the same factor; the binomials
+      // carry n roundings; gamma uses (L+1)^n + 2n + 6 >= all of them
+#pragma unroll
+      for (int c = 0; c < Ro; ++c) {
+        const float ck = ck_row * binom_l(2 * L, c);
+        const float err = __fmul_ru(gamma, __fmul_ru(mag[c], __fadd_ru(1.0f, gamma)));
+        const float c_min = __fmul_rd(ck, __fsub_rd(1.0f, gamma));   // <= the exact C_2L(K)
+        const float c_max = __fmul_ru(ck, __fadd_ru(1.0f, gamma));   // >= it
+        const float nh = __fadd_ru(acc[c], err), nl = __fsub_rd(acc[c], err);
+        // a smaller divisor moves a positive numerator up, a negative one down
+        const float hv = nh >= 0.0f ? __fdiv_ru(nh, c_min) : __fdiv_ru(nh, c_max);
+        const float lv = nl <= 0.0f ? __fdiv_rd(nl, c_min) : __fdiv_rd(nl, c_max);
+        const int64_t K = p * Go + (int64_t)orow * Ro + c;
+        c_hi[K] = hv;
+        c_lo[K] = lv;
+        if (!isfinite(hv) || !isfinite(lv)) atomicOr(status, kStatusNonFinite);
+      }
     }
     __syncthreads();
   }
+}
+
+template <int L>
+cudaError_t launch_l(const Launch& L_, int n, int64_t n_polys, const float* a, float* c_hi,
+                     float* c_lo) {
+  int G = 1;
+  for (int k = 0; k < n; ++k) G *= L + 1;
+  const size_t smem = (size_t)G * sizeof(float);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_bern_square<L>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  // a thread per output row: (2L+1)^(n-1) rows, rounded up to whole warps
+  int rows = 1;
+  for (int k = 0; k < n - 1; ++k) rows *= 2 * L + 1;
+  const int threads = std::min(kBtMaxThreads, std::max(32, (rows + 31) & ~31));
+  const int64_t blocks = std::min<int64_t>(n_polys, (int64_t)device_sms(L_) * 16);
+  k_bern_square<L><<<(unsigned)blocks, threads, smem, L_.stream>>>(n, n_polys, a, c_hi, c_lo,
+                                                                   L_.status);
+  ++*L_.launches;
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -125,19 +173,18 @@ cudaError_t launch_bernstein_square(const Launch& L, int n, int l, int64_t n_pol
                                     const float* a, float* c_hi, float* c_lo) {
   if (n_polys == 0) return cudaSuccess;
   if (!bernstein_square_ok(n, l) || n_polys < 0) return cudaErrorInvalidValue;
-  int G = 1;
-  for (int k = 0; k < n; ++k) G *= l + 1;
-  const size_t smem = (size_t)G * sizeof(float);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_bern_square, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
+  switch (l) {
+    case 0: return launch_l<0>(L, n, n_polys, a, c_hi, c_lo);
+    case 1: return launch_l<1>(L, n, n_polys, a, c_hi, c_lo);
+    case 2: return launch_l<2>(L, n, n_polys, a, c_hi, c_lo);
+    case 3: return launch_l<3>(L, n, n_polys, a, c_hi, c_lo);
+    case 4: return launch_l<4>(L, n, n_polys, a, c_hi, c_lo);
+    case 5: return launch_l<5>(L, n, n_polys, a, c_hi, c_lo);
+    case 6: return launch_l<6>(L, n, n_polys, a, c_hi, c_lo);
+    case 7: return launch_l<7>(L, n, n_polys, a, c_hi, c_lo);
+    case 8: return launch_l<8>(L, n, n_polys, a, c_hi, c_lo);
+    default: return cudaErrorInvalidValue;
   }
-  const int64_t blocks = std::min<int64_t>(n_polys, (int64_t)device_sms(L) * 8);
-  k_bern_square<<<(unsigned)blocks, kBtThreads, smem, L.stream>>>(n, l, n_polys, a, c_hi, c_lo,
-                                                                   L.status);
-  ++*L.launches;
-  return cudaGetLastError();
 }
 
 }  // namespace bern

@@ -1,8 +1,13 @@
 """The paper's dense Bernstein-tensor product on the GPU (bern_bernstein_square,
 Prod_Bern of Sec. 4.2) against the FP64 tensor arithmetic of
 oracle/bern_tensor.py: every exact coefficient of the square lies in the GPU
-interval [c_lo, c_hi], whose width stays within 1e-4 (1 + the coefficient of
-the square of |a|), an upper bound of the terms' magnitudes."""
+interval [c_lo, c_hi].  The interval is the round-to-nearest sum widened by
+its a-posteriori bound, gamma_m times the sum of the terms' magnitudes (the
+coefficient of the square of |a|), with gamma_m = m u / (1 - m u), u = 2^-24
+and m = (l+1)^n + 2n + 6 (every product a cell can sum, plus the scaling,
+binomial and division roundings); the bound enters twice on each side (the
+numerator and the binomial bracket), so the width is at most 4.5 gamma_m
+(1 + magnitude)."""
 import numpy as np
 import pytest
 
@@ -43,7 +48,9 @@ def test_bernstein_square_contains_exact(ctx, n, l, P):
         tol64 = 1e-12 * (1 + mag)                # the float64 reference's own rounding
         assert np.all(lo[p] <= exact + tol64), p
         assert np.all(hi[p] >= exact - tol64), p
-        assert np.all(hi[p] - lo[p] <= 1e-4 * (1 + mag)), p
+        m = (l + 1) ** n + 2 * n + 6
+        gamma = m * 2.0 ** -24 / (1 - m * 2.0 ** -24)
+        assert np.all(hi[p] - lo[p] <= 4.5 * gamma * (1 + mag)), p
 
 
 def test_bernstein_square_declines_large_weights(ctx):
