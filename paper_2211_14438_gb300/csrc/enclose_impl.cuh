@@ -187,14 +187,16 @@ __device__ __forceinline__ int prefix_degree(const Tables& T, int nt) {
   return nt <= T.mexps ? (int)T.deg_of[nt] : kMaxTableDegree;
 }
 
-// The transforms and reductions of one warp's grid, once its cells hold the
-// scaled coefficients (simplex of digit sums <= Deff) and every lane its
-// share `rem` of the one-sided ranges of the terms above the order.
-template <int LB, bool UP>
-__device__ float enclose_warp_transform(int Deff, float rem, int n, const Tables& T,
-                                        float* grid) {
+template <int LB, bool UP, bool PERM = false>
+__device__ float enclose_warp(const float* __restrict__ P, int ps, int nt, int n,
+                              const Tables& T, const float2* __restrict__ rs, float* grid,
+                              const int32_t* __restrict__ pos = nullptr) {
   const int lane = threadIdx.x & 31;
   constexpr int R = LB + 1;
+  const int Dnt = prefix_degree(T, nt);
+  const int Deff = Dnt < LB ? Dnt : LB;
+  float rem = scatter_terms<UP, PERM>(P, ps, nt, T.gidx[LB], rs, T.mcount[Deff], grid, pos);
+  __syncwarp();
   float best = UP ? -CUDART_INF_F : CUDART_INF_F;
   const int nlines = ipow(R, n - 1);
   const int2* __restrict__ lines = T.lines[LB];
@@ -234,17 +236,6 @@ __device__ float enclose_warp_transform(int Deff, float rem, int n, const Tables
   return dadd<UP>(best, rem);
 }
 
-template <int LB, bool UP, bool PERM = false>
-__device__ float enclose_warp(const float* __restrict__ P, int ps, int nt, int n,
-                              const Tables& T, const float2* __restrict__ rs, float* grid,
-                              const int32_t* __restrict__ pos = nullptr) {
-  const int Dnt = prefix_degree(T, nt);
-  const int Deff = Dnt < LB ? Dnt : LB;
-  const float rem = scatter_terms<UP, PERM>(P, ps, nt, T.gidx[LB], rs, T.mcount[Deff], grid, pos);
-  __syncwarp();
-  return enclose_warp_transform<LB, UP>(Deff, rem, n, T, grid);
-}
-
 // Options of one enclosure launch: the fused a3 outputs (kind == nullptr:
 // enclosure only) and an optional item list (list != nullptr: the launch
 // covers items list[0 .. *count), a device-side count; otherwise items
@@ -264,85 +255,34 @@ __device__ __forceinline__ int64_t map_item(const EncloseOpts& o, int64_t idx, i
   return idx < n_items ? idx : -1;
 }
 
-// Orders up to 5 fit 32 registers without spills: four 512-thread blocks per
+// Orders up to 6 fit 32 registers without spills: four 512-thread blocks per
 // SM (64 warps); higher orders keep three.
 template <int LB>
-__global__ void __launch_bounds__(512, (LB <= 5 ? 4 : 3))
+__global__ void __launch_bounds__(512, (LB <= 6 ? 4 : 3))
 k_enclose(Tables T, int G, const float2* __restrict__ rs, int64_t n_items, int h,
           const float* __restrict__ pre_up, const float* __restrict__ pre_lo, int64_t ld,
           const int32_t* __restrict__ nterms, float* __restrict__ lo, float* __restrict__ hi,
           EncloseOpts ro, int* status) {
   extern __shared__ float smem[];
   __shared__ float s_lohi[8][2];
-  __shared__ int64_t s_base[8];
-  __shared__ int s_nt[8], s_deff[8], s_meff[8];
-  __shared__ float s_rem[16][33];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int per_block = blockDim.x >> 6;               // items per block
-  const int npoly = 2 * per_block;                     // warp 2i: lower of item i, 2i+1: upper
-  if (threadIdx.x < per_block) {
-    const int i = threadIdx.x;
-    const int64_t item = map_item(ro, (int64_t)blockIdx.x * per_block + i, n_items);
-    int nt = -1;
-    int64_t base = 0;
-    if (item >= 0) {
-      nt = nterms[item];
-      if (nt < 0 || nt > ld || nt > T.mexps) {
-        atomicOr(status, kStatusInvalid);
-        nt = 0;
-      }
-      const int64_t b = item / h;
-      base = (b * ld) * h + (item - b * h);
-    }
-    const int Dnt = nt >= 0 ? prefix_degree(T, nt) : 0;
-    const int Deff = Dnt < LB ? Dnt : LB;
-    s_nt[i] = nt;
-    s_base[i] = base;
-    s_deff[i] = Deff;
-    s_meff[i] = T.mcount[Deff];
-  }
-  __syncthreads();
-  // Scatter, the whole block at once: thread t takes polynomial q = t % npoly
-  // (q = bound * per_block + item slot, so neighbouring threads read
-  // neighbouring neurons of a row) and the coefficients r = t / npoly + 32 k,
-  // exactly the coefficients lane t / npoly of that polynomial's warp would
-  // take; its share of the remainder goes to that lane.
-  {
-    const int q = threadIdx.x % npoly, slot = q % per_block, up = q / per_block;
-    const int lane_eq = threadIdx.x / npoly;           // 0..31
-    const int nt = s_nt[slot];
-    float rem = 0.0f;
-    if (nt >= 0) {
-      const float* P = (up ? pre_up : pre_lo) + s_base[slot];
-      float* grid = smem + (2 * slot + up) * G;
-      const int m_eff = s_meff[slot];
-      const int32_t* __restrict__ gidx = T.gidx[LB];
-      for (int r = lane_eq; r < nt; r += 32) {
-        const float a = P[(int64_t)r * h];
-        if (r < m_eff) {
-          const float2 sc = rs[r];
-          grid[__ldg(gidx + r)] = up ? __fmul_ru(a, a >= 0.0f ? sc.y : sc.x)
-                                     : __fmul_rd(a, a >= 0.0f ? sc.x : sc.y);
-        } else {
-          rem = up ? __fadd_ru(rem, fmaxf(a, 0.0f)) : __fadd_rd(rem, fminf(a, 0.0f));
-        }
-      }
-      for (int r = nt + lane_eq; r < m_eff; r += 32) grid[__ldg(gidx + r)] = 0.0f;
-    }
-    s_rem[2 * slot + up][lane_eq] = rem;
-  }
-  __syncthreads();
-  const int slot = warp >> 1;
+  const int64_t item = map_item(ro, (int64_t)blockIdx.x * per_block + (warp >> 1), n_items);
   const bool up = warp & 1;
-  const int64_t item = map_item(ro, (int64_t)blockIdx.x * per_block + slot, n_items);
   if (item >= 0) {
+    int nt = nterms[item];
+    if (nt < 0 || nt > ld || nt > T.mexps) {
+      if (lane == 0) atomicOr(status, kStatusInvalid);
+      nt = 0;
+    }
+    const int64_t b = item / h;
+    const int64_t base = (b * ld) * h + (item - b * h);
     float* grid = smem + warp * G;
-    const float rem = s_rem[warp][lane];
-    const float v = up ? enclose_warp_transform<LB, true>(s_deff[slot], rem, T.n, T, grid)
-                       : enclose_warp_transform<LB, false>(s_deff[slot], rem, T.n, T, grid);
+    const float v = up ? enclose_warp<LB, true>(pre_up + base, h, nt, T.n, T, rs, grid)
+                       : enclose_warp<LB, false>(pre_lo + base, h, nt, T.n, T, rs, grid);
     if (lane == 0) {
       (up ? hi : lo)[item] = v;
-      s_lohi[slot][up ? 1 : 0] = v;
+      s_lohi[warp >> 1][up ? 1 : 0] = v;
       if (!isfinite(v)) atomicOr(status, kStatusNonFinite);
     }
   }
