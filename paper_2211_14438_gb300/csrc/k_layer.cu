@@ -168,8 +168,10 @@ __device__ __forceinline__ void tile_to_midrad(float* tU, float* tL, int E, int 
   }
 }
 
+// Up to order 4 the layer blocks are small enough for four blocks per SM (64
+// registers); above, the block of a box takes half an SM's shared memory.
 template <int LB>
-__global__ void __launch_bounds__(kLThreads, 2)
+__global__ void __launch_bounds__(kLThreads, LB <= 4 ? 4 : 2)
 k_layer(Tables T, LayerArgs A, const float2* __restrict__ rs, int* status) {
   extern __shared__ __align__(16) float smem[];
   __shared__ int sh_box, sh_M, sh_Mnext, sh_tile_end, sh_row_end;
