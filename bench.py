@@ -3,11 +3,14 @@
 Workload: the batched plain method, ReLU MLP [3, 64, 64, 64, 64, 1] (seed 2),
 5120 boxes (the 16^3 grid of [-1,1]^3 plus 1024 random boxes with sides
 U(0.01,0.5)), Bernstein ReLU order 2, total-degree cap 16.  A step is one
-bern_propagate over all 5120 boxes (init, the first layer's affine step, one
-fused launch per hidden layer, the output enclosure and copy-out), replayed as
-one CUDA graph.  L2 is flushed (256 MB write) before every timed step, outside
-the timed interval; each step is timed with CUDA events on the launching
-stream.
+bern_propagate over all 5120 boxes (init, the first layer's affine step, then
+per hidden layer the enclosure of the pre-activations, the ReLU coefficients,
+the composition of the unstable neurons and the next affine step, and the
+output enclosure with copy-out), replayed as one CUDA graph.  The fused
+per-layer kernel (one launch per hidden layer) is timed beside it as an
+alternate path (--fused makes it the headline).  L2 is flushed (256 MB
+write) before every timed step, outside the timed interval; each step is
+timed with CUDA events on the launching stream.
 
 Multi-GPU (torchrun, weak scaling): N replicas of the 5120-box batch (the
 same grid cells, fresh random boxes per replica) are split into N contiguous
@@ -165,13 +168,14 @@ class ClockSampler:
 class KernelPass:
     """Drives the kernels bern_propagate runs for this workload through the
     step-level C ABI on torch-allocated buffers, with CUDA events around every
-    launch on the launching stream: init, the first layer's affine step, one
-    fused launch per hidden layer (bern_layer: enclosure, ReLU coefficients,
-    composition and the next layer's affine step) and the output enclosure.
-    A separate pass through the per-step kernels (bern_enclose,
-    bern_relu_coeffs, bern_compose, bern_affine) supplies the ReLU cases and
-    term counts for the algorithmic-work counts; with fused=False that pass is
-    the one timed (the per-step path)."""
+    launch on the launching stream.  With fused=False (the default path): init,
+    the first layer's affine step, per hidden layer the per-step kernels
+    (bern_enclose, bern_relu_coeffs, bern_compose, bern_affine) and the output
+    enclosure; that pass also supplies the ReLU cases and term counts for the
+    algorithmic-work counts.  With fused=True the hidden layers run as one
+    bern_layer launch each (enclosure, ReLU coefficients, composition and the
+    next layer's affine step), timed after the per-step pass that supplies the
+    counts."""
 
     def __init__(self, ctx, torch, w, Wd, bd, boxes_d, fused=True):
         from paper_2211_14438_gb300 import bern

@@ -969,10 +969,9 @@ int bern_compose(bern_ctx* c, int n, int64_t n_boxes, int h, int degree_cap, flo
   size_t horner_floats = 0;
   if (global_d >= 3 || prune_tau > 0.0f) {
     if ((rc = ensure_prod_tables(c, n, Dmax, global_d, degree_cap))) return rc;
-    const int Dout = std::min(degree_cap, global_d * Dmax);
-    const size_t per_block = horner_smem_floats(*T, Dmax, Dout);
+    const size_t per_block = horner_smem_floats(*T, Dmax, degree_cap, global_d);
     if (per_block == SIZE_MAX || per_block > ((size_t)64 << 20)) return BERN_E_UNSUPPORTED;
-    horner_floats = horner_global_floats(*T, Dmax, Dout, c->horner_smem_limit,
+    horner_floats = horner_global_floats(*T, Dmax, degree_cap, global_d, c->horner_smem_limit,
                                          kHornerGlobalPerSM * std::max(1, c->sms));
   }
   ComposeScratch CS;
@@ -1028,10 +1027,10 @@ int bern_propagate_traced(bern_ctx* c, const bern_net* net, const float* boxes,
   for (const auto& l : P.L) {
     if (!l.hidden || (l.d < 3 && P.tau == 0.0f)) continue;
     if ((rc = ensure_prod_tables(c, P.n, l.D_pre, l.d, P.cap))) return rc;
-    const size_t per_block = horner_smem_floats(*T, l.D_pre, l.D_post);
+    const size_t per_block = horner_smem_floats(*T, l.D_pre, P.cap, l.d);
     if (per_block == SIZE_MAX || per_block > ((size_t)64 << 20)) return BERN_E_UNSUPPORTED;
     horner_floats = std::max(horner_floats,
-                             horner_global_floats(*T, l.D_pre, l.D_post, c->horner_smem_limit,
+                             horner_global_floats(*T, l.D_pre, P.cap, l.d, c->horner_smem_limit,
                                                   kHornerGlobalPerSM * std::max(1, c->sms)));
   }
 

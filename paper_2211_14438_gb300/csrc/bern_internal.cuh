@@ -218,7 +218,7 @@ cudaError_t launch_pack(const Launch& L, const Tables& T, int64_t n_boxes, int o
 
 // Work queues of the composition step: kComposeQueues lists of item
 // indices, each of capacity qcap, and their counters.
-constexpr int kComposeQueues = kMaxRowDegree + 5;
+constexpr int kComposeQueues = kMaxRowDegree + 6;
 // Lists for the per-box Bernstein orders of learned plans (one per order value).
 constexpr int kOrderQueues = 32;
 constexpr int kQueueLists = kComposeQueues > kOrderQueues ? kComposeQueues : kOrderQueues;

@@ -10,8 +10,15 @@ constexpr float kU = 0x1p-24f;   // unit roundoff of float32
 constexpr int kQIdent = kMaxRowDegree + 1;   // identity copies
 constexpr int kQLinear = kMaxRowDegree + 2;  // order-1 items
 constexpr int kQPairs = kMaxRowDegree + 3;   // order-2 items outside the row path
-constexpr int kQHorner = kMaxRowDegree + 4;  // Horner items (order >= 3, or pruning)
-static_assert(kQHorner + 1 == kComposeQueues, "queue ids");
+constexpr int kQHorner = kMaxRowDegree + 4;  // Horner items in float32 (order >= 3, or pruning)
+constexpr int kQHorner64 = kMaxRowDegree + 5;  // Horner items in float64 (order >= kHornerF64Order)
+static_assert(kQHorner64 + 1 == kComposeQueues, "queue ids");
+// From this ReLU order on the composition runs in float64: the power-form
+// coefficients of the order-d ReLU polynomial grow like C(d, d/2) 2^(d/2)
+// (hi - lo) / d while the composed result stays of the order of hi - lo, so
+// float32 rounding of the intermediate coefficients (u times their size)
+// swamps the result's own accuracy at about this order.
+constexpr int kHornerF64Order = 6;
 
 struct ComposeArgs {
   int cap;
@@ -47,15 +54,20 @@ __device__ __forceinline__ int degree_of(const Tables& T, int m) {
   return D;
 }
 
-// The Horner kernel (k_horner.cu) over queue kQHorner, for inputs of degree
-// <= Dmax and outputs of degree <= Dout (host functions; the sizes come from
-// num_monomials, never from the device tables).
-size_t horner_smem_floats(const Tables& T, int Dmax, int Dout);
-// Global workspace floats (ComposeScratch::hws) the Horner kernel needs with
-// `blocks` workspace slices, 0 when its buffers fit `smem_limit` bytes of
-// shared memory.
-size_t horner_global_floats(const Tables& T, int Dmax, int Dout, int64_t smem_limit, int blocks);
+// The Horner kernels (k_horner.cu) over queues kQHorner (float32) and
+// kQHorner64 (float64), for inputs of degree <= Dmax, ReLU orders <= d and
+// total-degree cap `cap` (host functions; the sizes come from
+// num_monomials, never from the device tables).  Buffer floats per block
+// (the larger of the two variants; float64 elements count as two floats).
+size_t horner_smem_floats(const Tables& T, int Dmax, int cap, int d);
+// Global workspace floats (ComposeScratch::hws) the Horner kernels need with
+// `blocks` workspace slices, 0 when their buffers fit `smem_limit` bytes of
+// shared memory (at most 200 KB).
+size_t horner_global_floats(const Tables& T, int Dmax, int cap, int d, int64_t smem_limit,
+                            int blocks);
+// Launches the float32 kernel when its queue can be non-empty and the
+// float64 one when A.global_d >= kHornerF64Order.
 cudaError_t launch_compose_horner(const Launch& L, const Tables& T, const ComposeScratch& S,
-                                  const ComposeArgs& A, int Dmax, int Dout);
+                                  const ComposeArgs& A, int Dmax);
 
 }  // namespace bern

@@ -37,6 +37,7 @@
 #include <string>
 
 #include "device_util.cuh"
+#include "relu_form.cuh"
 
 namespace bern {
 
@@ -48,79 +49,6 @@ constexpr float cbin(int i, int j) {
   return r;
 }
 
-// ------------------------------------------------------------------ a3
-// C(d,k) for d <= 16, exact in float64
-static __constant__ const double c_dbin[17][17] = {
-    {1},
-    {1, 1},
-    {1, 2, 1},
-    {1, 3, 3, 1},
-    {1, 4, 6, 4, 1},
-    {1, 5, 10, 10, 5, 1},
-    {1, 6, 15, 20, 15, 6, 1},
-    {1, 7, 21, 35, 35, 21, 7, 1},
-    {1, 8, 28, 56, 70, 56, 28, 8, 1},
-    {1, 9, 36, 84, 126, 126, 84, 36, 9, 1},
-    {1, 10, 45, 120, 210, 252, 210, 120, 45, 10, 1},
-    {1, 11, 55, 165, 330, 462, 462, 330, 165, 55, 11, 1},
-    {1, 12, 66, 220, 495, 792, 924, 792, 495, 220, 66, 12, 1},
-    {1, 13, 78, 286, 715, 1287, 1716, 1716, 1287, 715, 286, 78, 13, 1},
-    {1, 14, 91, 364, 1001, 2002, 3003, 3432, 3003, 2002, 1001, 364, 91, 14, 1},
-    {1, 15, 105, 455, 1365, 3003, 5005, 6435, 6435, 5005, 3003, 1365, 455, 105, 15, 1},
-    {1, 16, 120, 560, 1820, 4368, 8008, 11440, 12870, 11440, 8008, 4368, 1820, 560, 120, 16, 1}};
-
-static __device__ __forceinline__ double dbin(int d, int k) { return c_dbin[d][k]; }
-
-// Order-d Bernstein polynomial of ReLU on [lo,hi], power form in s, every
-// coefficient rounded up (>= the exact one); eps >= B(0) + sum_j (a~_j - a_j).
-static __device__ void relu_power_form(float lo, float hi, int d, float* a_out, float* eps_out) {
-  const double L = lo, H = hi, w = H - L;
-  const double inv_d = 1.0 / (double)d;
-  double b[kMaxOrder + 1];
-  for (int k = 0; k <= d; ++k) {
-    double node = L + w * ((double)k * inv_d);   // Def. 1 grid point
-    b[k] = node > 0.0 ? node : 0.0;
-  }
-  double excess = 0.0;
-  for (int j = 0; j <= d; ++j) {
-    double s = 0.0, mag = 0.0;
-    for (int k = 0; k <= j; ++k) {
-      // coefficient of s^j in C(d,k) s^k (1-s)^(d-k)
-      double t = b[k] * (dbin(d, k) * dbin(d - k, j - k));
-      s += ((j - k) & 1) ? -t : t;
-      mag += t;
-    }
-    const double margin = mag * 0x1p-40;
-    const float aj = __double2float_ru(s + margin);
-    a_out[j] = aj;
-    excess += ((double)aj - s) + margin;
-  }
-  const double s0 = -L / w;
-  double e = 0.0;
-  for (int k = 0; k <= d; ++k) {
-    double t = b[k] * dbin(d, k);
-    for (int i = 0; i < k; ++i) t *= s0;
-    for (int i = 0; i < d - k; ++i) t *= (1.0 - s0);
-    e += t;
-  }
-  *eps_out = __double2float_ru((e + excess) * (1.0 + 0x1p-40) + w * 0x1p-40);
-}
-
-// Case of one item and, for case 2, its coefficients.  Returns the case.
-static __device__ int relu_item(float l, float h, int d, float* a, float* eps, int* status) {
-  if (!(isfinite(l) && isfinite(h))) {
-    atomicOr(status, kStatusNonFinite);
-    return 0;
-  }
-  if (h <= 0.0f) return 0;        // ReLU is 0 on [lo,hi]
-  if (l >= 0.0f) return 1;        // ReLU is the identity on [lo,hi]
-  if (d < 1 || d > kMaxOrder) {
-    atomicOr(status, kStatusInvalid);
-    return 0;
-  }
-  relu_power_form(l, h, d, a, eps);
-  return 2;
-}
 
 // ------------------------------------------------------------------ a2
 // In place, from the top: y_i needs x_0 .. x_i only, so x_i can take y_i

@@ -66,7 +66,7 @@ k_compose_queue(Tables T, ComposeArgs A, int64_t n_items, int row_dmax, ComposeS
         if (Mout > A.post_ld) {
           atomicOr(status, kStatusCapacity);
         } else if (A.tau > 0.0f || d >= 3) {
-          q = kQHorner;
+          q = d >= kHornerF64Order ? kQHorner64 : kQHorner;
           nt = A.tau > 0.0f ? 0 : Mout;   // with pruning the Horner kernel sets it
         } else if (d == 1) {
           q = kQLinear;
@@ -510,10 +510,9 @@ cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratc
         T, A, S, L.status);
     ++*L.launches;
   }
-  // Horner kernel for orders >= 3, and for every order when pruning
+  // Horner kernels for orders >= 3, and for every order when pruning
   if (tau > 0.0f || global_d >= 3) {
-    const int Dout = std::min(cap, std::max(1, global_d) * Dmax);
-    e = launch_compose_horner(L, T, S, A, Dmax, Dout);
+    e = launch_compose_horner(L, T, S, A, Dmax);
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
