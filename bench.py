@@ -438,14 +438,17 @@ def lin_entries(ctx, torch, dev, flush, args, w, Wd, bd, boxes_d, plain_ms, plai
 
 # ------------------------------------------- Bernstein-tensor arithmetic (Sec. 4)
 def bernstein_basis_entry(ctx, torch, dev, flush, args):
-    """The composition's squares in the paper's representation against the power
-    basis, on the layer-4 size of the benchmark net (three variables, degree
-    8): P = 4096 items of the power-basis composition at order 2 (both bounds:
+    """One layer step in the paper's representation against the power basis,
+    on the layer-4 size of the benchmark net (three variables, degree 8):
+    P = 4096 items of the power-basis composition at order 2 (both bounds:
     two squares of 165-term polynomials per item, the library's row kernels,
     plus the queue, the linear term and the epilogue), against 2P Prod_Bern
     squares of order-8 Bernstein tensors (9^3 = 729 coefficients, 729^2 term
-    products each, bern_bernstein_square).  Random seeded coefficients; CUDA
-    events, L2 flushed before every timed call."""
+    products each, bern_bernstein_square); the degree elevation of 2P order-8
+    tensors to order 16 (bern_bernstein_elevate); and the layer sums
+    (bern_affine on 165- and 969-coefficient blocks against
+    bern_bernstein_affine on 729- and 4913-coefficient tensors).  Random
+    seeded coefficients; CUDA events, L2 flushed before every timed call."""
     from paper_2211_14438_gb300 import bern
     n, D, P, h = 3, 8, 4096, 64
     B = P // h
@@ -494,15 +497,55 @@ def bernstein_basis_entry(ctx, torch, dev, flush, args):
     ms_pow = timed(lambda: ctx.compose(n, B, h, 16, 0.0, kind, coef, eps, None, 2, glo, ghi, pu,
                                        pl, M, nt, qu, ql, Mo, qnt))
     ms_bern = timed(lambda: ctx.bernstein_square(n, D, tens, chi, clo))
+    # Sum_Bern: degree elevation (order 8 -> 16, what an identity neuron's
+    # tensor needs before the next sum) and the layer sums: 64 -> 64 neurons on
+    # the layer-4 pre-activation size and 64 -> 1 on the output layer's input,
+    # against the affine step on the power-basis blocks of the same items
+    ms_elev = timed(lambda: ctx.bernstein_elevate(n, D, D, tens, tens, chi, clo))
+    W4 = torch.from_numpy((rng.normal(size=(h, h)) / np.sqrt(h)).astype(np.float32)).to(dev)
+    b4 = torch.from_numpy(rng.uniform(-0.1, 0.1, h).astype(np.float32)).to(dev)
+    W5 = torch.from_numpy((rng.normal(size=(1, h)) / np.sqrt(h)).astype(np.float32)).to(dev)
+    b5 = torch.from_numpy(rng.uniform(-0.1, 0.1, 1).astype(np.float32)).to(dev)
+    G8, G16 = (D + 1) ** n, (2 * D + 1) ** n
+    a4u, a4l = torch.empty(B * M * h, device=dev), torch.empty(B * M * h, device=dev)
+    a4nt = torch.empty(P, dtype=torch.int32, device=dev)
+    a5u, a5l = torch.empty(B * Mo, device=dev), torch.empty(B * Mo, device=dev)
+    a5nt = torch.empty(B, dtype=torch.int32, device=dev)
+    ms_pow_a4 = timed(lambda: ctx.affine(B, h, h, W4, b4, pu, pl, M, nt, a4u, a4l, M, a4nt))
+    ms_pow_a5 = timed(lambda: ctx.affine(B, 1, h, W5, b5, qu, ql, Mo, qnt, a5u, a5l, Mo, a5nt))
+    del a4u, a4l, a5u, a5l
+    t8 = torch.from_numpy(rng.normal(0, 1, (B, G8, h)).astype(np.float32)).to(dev)
+    o8u, o8l = torch.empty(B * G8 * h, device=dev), torch.empty(B * G8 * h, device=dev)
+    ms_bern_a4 = timed(lambda: ctx.bernstein_affine(B, h, h, W4, b4, G8, t8, t8, o8u, o8l))
+    del t8, o8u, o8l
+    t16 = torch.from_numpy(rng.normal(0, 1, (B, G16, h)).astype(np.float32)).to(dev)
+    o16u, o16l = torch.empty(B * G16, device=dev), torch.empty(B * G16, device=dev)
+    ms_bern_a5 = timed(lambda: ctx.bernstein_affine(B, 1, h, W5, b5, G16, t16, t16, o16u, o16l))
+    del t16
+    layer_pow = ms_pow_a4 + ms_pow + ms_pow_a5
+    layer_bern = ms_bern_a4 + ms_bern + ms_elev + ms_bern_a5
     return {"workload": "4096 items of three variables at degree 8 (the benchmark net's layer-4 "
-                        "size), both bounds: 8192 squares in each representation",
+                        "size, 64 boxes of 64 neurons), both bounds: 8192 squares in each "
+                        "representation, 8192 elevations of order-8 tensors to order 16, and "
+                        "the layer sums 64 -> 64 (pre-activation size) and 64 -> 1 (the output "
+                        "layer's input)",
             "power_basis_composition_ms": round(ms_pow, 4),
             "bernstein_prod_bern_squares_ms": round(ms_bern, 4),
             "bernstein_over_power_time": round(ms_bern / ms_pow, 2),
+            "bernstein_elevate_ms": round(ms_elev, 4),
+            "affine_64_64_ms": {"power_basis": round(ms_pow_a4, 4),
+                                "bernstein": round(ms_bern_a4, 4)},
+            "affine_64_1_ms": {"power_basis": round(ms_pow_a5, 4),
+                               "bernstein": round(ms_bern_a5, 4)},
+            "layer_step_ms": {"power_basis": round(layer_pow, 4),
+                              "bernstein": round(layer_bern, 4),
+                              "bernstein_over_power": round(layer_bern / layer_pow, 2),
+                              "note": "sum + square + output sum; the Bernstein step adds the "
+                                      "elevation its identity neurons need (timed for all items)"},
             "term_products_per_square": {"power_basis": M * (M + 1) // 2,
                                          "bernstein_tensor": ((D + 1) ** n) ** 2},
             "coefficients": {"power_basis_in_out": [M, Mo],
-                             "bernstein_in_out": [(D + 1) ** n, (2 * D + 1) ** n]}}
+                             "bernstein_in_out": [G8, G16]}}
 
 
 # ---------------------------------------------------------------- our arm

@@ -428,6 +428,39 @@ int bern_layer(bern_ctx* ctx, int n, int64_t n_boxes, int h, int order, int64_t 
 int bern_bernstein_square(bern_ctx* ctx, int n, int l, int64_t n_polys, const float* a,
                           float* c_hi, float* c_lo);
 
+/* Degree elevation of dense Bernstein tensors (Sec. 4.3, the step Sum_Bern
+ * takes before adding tensors of different orders): an order-l tensor in n
+ * variables becomes the order-(l + r) tensor of the same polynomial,
+ *   c'_k = sum_j c_j C(l, j) C(r, k - j) / C(l + r, k)   in every variable.
+ *   a_hi, a_lo: device, n_polys x (l+1)^n floats each, contiguous per
+ *          polynomial, row-major with the last variable fastest: an interval
+ *          tensor (a_lo <= a_hi; pass one array twice for a point tensor);
+ *   c_hi, c_lo: device, n_polys x (l+r+1)^n floats: every exact elevated
+ *          coefficient of any tensor in [a_lo, a_hi] lies in [c_lo, c_hi]
+ *          (the weights are positive, so the passes round up the upper and
+ *          down the lower tensor).
+ * l + r <= 24 (exact float binomials) and 4 (l+r+1)^n floats within 200 KB of
+ * shared memory (BERN_E_UNSUPPORTED otherwise).  Asynchronous on the context's
+ * stream; a non-finite coefficient is reported by bern_sync. */
+int bern_bernstein_elevate(bern_ctx* ctx, int n, int l, int r, int64_t n_polys,
+                           const float* a_hi, const float* a_lo, float* c_hi, float* c_lo);
+
+/* The layer step of Sec. 5.2 (the sum over a layer's neurons) on dense
+ * Bernstein tensors, the Sum_Bern of Sec. 4.3 with weights: for every box and
+ * output neuron m,
+ *   out_hi_m = b_m + sum_j W+_mj in_hi_j + W-_mj in_lo_j   (out_lo symmetric)
+ * coefficient by coefficient, the bias added to every coefficient (the
+ * Bernstein basis sums to one).  The tensors share one order and coefficient
+ * count n_coef, in the layer-block layout of bern_affine (coefficient g of
+ * neuron j of box b at (b * n_coef + g) * h + j).  Every output coefficient
+ * bounds the exact one from the correct side (the affine step's directed
+ * arithmetic; the Bernstein basis is >= 0 on the box, so the tensors bound
+ * the polynomials).  W: h_out x h_in row-major, b: h_out, device.  Holds
+ * n_boxes * (h_in + h_out) ints of context scratch.  Asynchronous. */
+int bern_bernstein_affine(bern_ctx* ctx, int64_t n_boxes, int h_out, int h_in, const float* W,
+                          const float* b, int64_t n_coef, const float* in_hi, const float* in_lo,
+                          float* out_hi, float* out_lo);
+
 /* Use the fused layer kernel (bern_layer) inside bern_propagate wherever a
  * plan allows it (default 0): plain plans (BERN_DEG_GLOBAL or PER_LAYER) with
  * prune_tau = 0, untraced, layer by layer where the shape qualifies and the

@@ -57,6 +57,8 @@ EXPORTS = [
     "bern_set_horner_smem_limit", "bern_set_autotune", "bern_force_variant",
     "bern_poly_to_x", "bern_linearize", "bern_fma_throughput", "bern_layer", "bern_set_fused",
     "bern_bernstein_square",
+    "bern_bernstein_elevate",
+    "bern_bernstein_affine",
 ]
 
 
@@ -143,6 +145,8 @@ def load(build_if_missing: bool = True):
         "bern_layer": (I, [V, I, I64, I, I, I64, I, I, V, V, I64, V, I, V, V, V, V, I64, V]),
         "bern_set_fused": (I, [V, I]),
         "bern_bernstein_square": (I, [V, I, I, I64, V, V, V]),
+        "bern_bernstein_elevate": (I, [V, I, I, I, I64, V, V, V, V]),
+        "bern_bernstein_affine": (I, [V, I64, I, I, V, V, I64, V, V, V, V]),
         "bern_propagate_noalloc": (I, [ctypes.POINTER(bern_net), V, I64,
                                        ctypes.POINTER(bern_degree_plan),
                                        ctypes.POINTER(bern_result), V]),
@@ -253,6 +257,20 @@ class Context:
         a [P, (l+1)^n] into coefficient intervals [c_lo, c_hi] [P, (2l+1)^n]."""
         _check(self.lib.bern_bernstein_square(self.h, n, l, int(a.shape[0]), _ptr(a), _ptr(c_hi),
                                               _ptr(c_lo)), "bern_bernstein_square")
+
+    def bernstein_elevate(self, n, l, r, a_hi, a_lo, c_hi, c_lo):
+        """bern_bernstein_elevate: interval tensors [a_lo, a_hi] [P, (l+1)^n]
+        elevated to order l + r: [c_lo, c_hi] [P, (l+r+1)^n]."""
+        _check(self.lib.bern_bernstein_elevate(self.h, n, l, r, int(a_hi.shape[0]), _ptr(a_hi),
+                                               _ptr(a_lo), _ptr(c_hi), _ptr(c_lo)),
+               "bern_bernstein_elevate")
+
+    def bernstein_affine(self, n_boxes, h_out, h_in, W, b, n_coef, in_hi, in_lo, out_hi, out_lo):
+        """bern_bernstein_affine: the layer sum on dense Bernstein tensors in
+        the layer-block layout [B, n_coef, h] (bias on every coefficient)."""
+        _check(self.lib.bern_bernstein_affine(self.h, int(n_boxes), h_out, h_in, _ptr(W), _ptr(b),
+                                              int(n_coef), _ptr(in_hi), _ptr(in_lo), _ptr(out_hi),
+                                              _ptr(out_lo)), "bern_bernstein_affine")
 
     def set_fused(self, on: bool):
         _check(self.lib.bern_set_fused(self.h, 1 if on else 0), "bern_set_fused")

@@ -80,6 +80,7 @@ struct bern_ctx {
   DevBuf ws, stage_in, stage_out, qbuf, mlp_ws, hbuf;
   DevBuf ctr;                       // box counters of the fused layer kernels
   DevBuf ebuf;                      // grids of enclosures above shared memory
+  DevBuf btnt;                      // term counts of the Bernstein-basis layer sum
   int fused = 0;                    // fused layer kernels where a plan allows them
   std::vector<GraphEntry> graphs;
   Tuner tuner;
@@ -756,6 +757,7 @@ int bern_destroy(bern_ctx* c) {
   c->hbuf.release();
   c->ctr.release();
   c->ebuf.release();
+  c->btnt.release();
   if (c->d_status) cudaFree(c->d_status);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -810,6 +812,31 @@ int bern_bernstein_square(bern_ctx* c, int n, int l, int64_t n_polys, const floa
   if (!bernstein_square_ok(n, l)) return BERN_E_UNSUPPORTED;
   cudaSetDevice(c->device);
   return map_cuda(launch_bernstein_square(c->launch(), n, l, n_polys, a, c_hi, c_lo));
+}
+
+int bern_bernstein_elevate(bern_ctx* c, int n, int l, int r, int64_t n_polys,
+                           const float* a_hi, const float* a_lo, float* c_hi, float* c_lo) {
+  if (!c || n < 1 || n > kMaxVars || l < 0 || r < 0 || n_polys < 0 ||
+      (n_polys > 0 && (!a_hi || !a_lo || !c_hi || !c_lo)))
+    return BERN_E_INVALID;
+  if (bernstein_elevate_smem(n, l, r) > 200 * 1024) return BERN_E_UNSUPPORTED;
+  cudaSetDevice(c->device);
+  return map_cuda(launch_bernstein_elevate(c->launch(), n, l, r, n_polys, a_hi, a_lo, c_hi, c_lo));
+}
+
+int bern_bernstein_affine(bern_ctx* c, int64_t n_boxes, int h_out, int h_in, const float* W,
+                          const float* b, int64_t n_coef, const float* in_hi, const float* in_lo,
+                          float* out_hi, float* out_lo) {
+  if (!c || n_boxes < 0 || h_out < 1 || h_in < 1 || n_coef < 1 || n_coef > INT32_MAX)
+    return BERN_E_INVALID;
+  if (n_boxes == 0) return BERN_OK;
+  if (!W || !b || !in_hi || !in_lo || !out_hi || !out_lo) return BERN_E_INVALID;
+  if ((n_coef + 15) / 16 > 65535 || n_boxes > INT32_MAX) return BERN_E_UNSUPPORTED;
+  cudaSetDevice(c->device);
+  cudaError_t e = c->btnt.reserve((size_t)n_boxes * (h_in + h_out) * sizeof(int32_t));
+  if (e != cudaSuccess) return map_cuda(e);
+  return map_cuda(launch_bernstein_affine(c->launch(), n_boxes, h_out, h_in, W, b, (int)n_coef,
+                                          in_hi, in_lo, out_hi, out_lo, (int32_t*)c->btnt.p));
 }
 
 int bern_set_fused(bern_ctx* c, int enable) {

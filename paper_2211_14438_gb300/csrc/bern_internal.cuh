@@ -294,6 +294,18 @@ cudaError_t launch_enclose_big(const Launch& L, const Tables& T, int lb, int G, 
 bool bernstein_square_ok(int n, int l);
 cudaError_t launch_bernstein_square(const Launch& L, int n, int l, int64_t n_polys,
                                     const float* a, float* c_hi, float* c_lo);
+// Degree elevation of dense Bernstein tensors (order l -> l + r in every
+// variable): shared-memory bytes per block, SIZE_MAX when out of range.
+size_t bernstein_elevate_smem(int n, int l, int r);
+cudaError_t launch_bernstein_elevate(const Launch& L, int n, int l, int r, int64_t n_polys,
+                                     const float* a_hi, const float* a_lo, float* c_hi,
+                                     float* c_lo);
+// The layer sum in the Bernstein basis on dense tensors of G coefficients in
+// the layer-block layout; nt_scratch holds n_boxes * (h_in + h_out) ints.
+cudaError_t launch_bernstein_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
+                                    const float* W, const float* b, int G, const float* in_hi,
+                                    const float* in_lo, float* out_hi, float* out_lo,
+                                    int32_t* nt_scratch);
 
 // Largest input degree the row-convolution path handles for n variables.
 int row_path_max_degree(int n);

@@ -15,6 +15,20 @@
 // rounding on the way (the scaling products, the term products, the m-term
 // sum, the binomial and the division) widens each coefficient to an
 // interval [c_lo, c_hi] that contains the exact one.
+//
+// Sum_Bern (Sec. 4.3) needs both operands at one order: degree elevation of
+// a tensor from order l to l + r in every variable,
+//
+//   c'_k = sum_j c_j C(l, j) C(r, k - j) / C(l + r, k)     (per variable),
+//
+// one pass per variable with positive weights (exact float integers for
+// l + r <= 24; the division by a bracket of the reciprocal), so round-up
+// passes of an upper tensor and round-down passes of a lower one bound the
+// exact elevation from the correct side; and the
+// sum over a layer's neurons, b_m + sum_j W_mj c_j, which in the Bernstein
+// basis adds the bias to every coefficient (the basis sums to one): the
+// affine step's kernels on the tensors' coefficients, then the bias on the
+// coefficients past the first.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -185,6 +199,159 @@ cudaError_t launch_bernstein_square(const Launch& L, int n, int l, int64_t n_pol
     case 8: return launch_l<8>(L, n, n_polys, a, c_hi, c_lo);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// ------------------------------------------------------------ elevation
+namespace {
+
+constexpr int kElThreads = 256;
+
+// One block per polynomial: the tensor in shared memory (upper and lower, two
+// buffers each), one pass per variable, a thread per line of a pass.
+__global__ void __launch_bounds__(kElThreads)
+k_bern_elevate(int n, int l, int r, int64_t n_polys, const float* __restrict__ a_hi,
+               const float* __restrict__ a_lo, float* __restrict__ c_hi,
+               float* __restrict__ c_lo, int go_max, int* status) {
+  extern __shared__ float se[];
+  __shared__ float2 s_rcp[kMaxEncloseOrder + 1];   // [RD, RU] of 1 / C(l + r, k)
+  float* bh[2] = {se, se + go_max};
+  float* bl[2] = {se + 2 * go_max, se + 3 * go_max};
+  const int Ri = l + 1, Ro = l + r + 1;
+  for (int k = threadIdx.x; k < Ro; k += kElThreads)
+    s_rcp[k] = make_float2(__frcp_rd(binomf(l + r, k)), __frcp_ru(binomf(l + r, k)));
+  int Gi = 1, Go = 1;
+  for (int k = 0; k < n; ++k) {
+    Gi *= Ri;
+    Go *= Ro;
+  }
+  for (int64_t p = blockIdx.x; p < n_polys; p += gridDim.x) {
+    __syncthreads();   // (the first time: s_rcp)
+    for (int g = threadIdx.x; g < Gi; g += kElThreads) {
+      bh[0][g] = a_hi[p * Gi + g];
+      bl[0][g] = a_lo[p * Gi + g];
+    }
+    __syncthreads();
+    int cur = 0;
+    // before pass k: variables < k at order l + r, the others at order l
+    for (int k = 0; k < n; ++k) {
+      int stride = 1;   // of variable k (the last variable is the fastest)
+      for (int q = k + 1; q < n; ++q) stride *= Ri;
+      int gk = stride * Ro;
+      for (int q = 0; q < k; ++q) gk *= Ro;
+      const float* ih = bh[cur];
+      const float* il = bl[cur];
+      float* oh = bh[cur ^ 1];
+      float* ol = bl[cur ^ 1];
+      // a thread per line (the cells that differ only in variable k)
+      const int nl = gk / Ro;
+      for (int line = threadIdx.x; line < nl; line += kElThreads) {
+        const int inner = line % stride, outer = line / stride;
+        const float* xh = ih + outer * (Ri * stride) + inner;
+        const float* xl = il + outer * (Ri * stride) + inner;
+        float* yh = oh + outer * (Ro * stride) + inner;
+        float* yl = ol + outer * (Ro * stride) + inner;
+        for (int kk = 0; kk < Ro; ++kk) {
+          float hu = 0.0f, hl = 0.0f;
+          const int j0 = max(0, kk - r), j1 = min(l, kk);
+          for (int j = j0; j <= j1; ++j) {
+            const float wl = binomf(l, j), wr = binomf(r, kk - j);
+            hu = __fmaf_ru(__fmul_ru(xh[j * stride], wl), wr, hu);
+            hl = __fmaf_rd(__fmul_rd(xl[j * stride], wl), wr, hl);
+          }
+          // x / C with a bracket [q_lo, q_hi] of 1/C: the end that moves x * q
+          // up (down) is picked by the sign of x
+          const float2 q = s_rcp[kk];
+          yh[kk * stride] = __fmul_ru(hu, hu >= 0.0f ? q.y : q.x);
+          yl[kk * stride] = __fmul_rd(hl, hl >= 0.0f ? q.x : q.y);
+        }
+      }
+      __syncthreads();
+      cur ^= 1;
+    }
+    for (int g = threadIdx.x; g < Go; g += kElThreads) {
+      const float vh = bh[cur][g], vl = bl[cur][g];
+      c_hi[p * Go + g] = vh;
+      c_lo[p * Go + g] = vl;
+      if (!isfinite(vh) || !isfinite(vl)) atomicOr(status, kStatusNonFinite);
+    }
+    __syncthreads();   // the buffers are reused by the next polynomial
+  }
+}
+
+__global__ void k_fill_i32(int32_t* __restrict__ x, int64_t count, int32_t v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+// The bias on coefficients 1 .. G-1 of every output neuron (coefficient 0
+// got it in the affine step), upward for the upper and downward for the lower
+// tensor.
+__global__ void k_bias_rows(int64_t n_boxes, int h, int G, const float* __restrict__ bias,
+                            float* __restrict__ out_hi, float* __restrict__ out_lo) {
+  const int64_t total = n_boxes * (int64_t)(G - 1) * h;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int m = (int)(i % h);
+    const int64_t rest = i / h;
+    const int64_t g = 1 + rest % (G - 1), b = rest / (G - 1);
+    const int64_t o = (b * G + g) * h + m;
+    out_hi[o] = __fadd_ru(out_hi[o], bias[m]);
+    out_lo[o] = __fadd_rd(out_lo[o], bias[m]);
+  }
+}
+
+}  // namespace
+
+size_t bernstein_elevate_smem(int n, int l, int r) {
+  if (n < 1 || n > kMaxVars || l < 0 || r < 0 || l + r > kMaxEncloseOrder) return SIZE_MAX;
+  int64_t go = 1;
+  for (int k = 0; k < n; ++k) {
+    go *= l + r + 1;
+    if (go > (1 << 20)) return SIZE_MAX;
+  }
+  return (size_t)4 * go * sizeof(float);
+}
+
+cudaError_t launch_bernstein_elevate(const Launch& L, int n, int l, int r, int64_t n_polys,
+                                     const float* a_hi, const float* a_lo, float* c_hi,
+                                     float* c_lo) {
+  if (n_polys == 0) return cudaSuccess;
+  const size_t smem = bernstein_elevate_smem(n, l, r);
+  if (n_polys < 0 || smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_bern_elevate,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int go = (int)(smem / (4 * sizeof(float)));
+  const int per_sm = std::max(1, std::min(8, (int)((228 * 1024) / (smem + 1024))));
+  const int64_t blocks = std::min<int64_t>(n_polys, (int64_t)device_sms(L) * per_sm);
+  k_bern_elevate<<<(unsigned)blocks, kElThreads, smem, L.stream>>>(n, l, r, n_polys, a_hi, a_lo,
+                                                                   c_hi, c_lo, go, L.status);
+  ++*L.launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bernstein_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
+                                    const float* W, const float* b, int G, const float* in_hi,
+                                    const float* in_lo, float* out_hi, float* out_lo,
+                                    int32_t* nt_scratch) {
+  if (n_boxes == 0) return cudaSuccess;
+  if (n_boxes < 0 || G < 1 || !nt_scratch) return cudaErrorInvalidValue;
+  const int64_t nin = n_boxes * h_in, nout = n_boxes * h_out;
+  const unsigned fb = (unsigned)std::min<int64_t>((nin + 255) / 256, device_sms(L) * 8);
+  k_fill_i32<<<fb, 256, 0, L.stream>>>(nt_scratch, nin, G);
+  ++*L.launches;
+  cudaError_t e = launch_affine(L, n_boxes, h_out, h_in, W, b, in_hi, in_lo, G, nt_scratch,
+                                out_hi, out_lo, G, nt_scratch + nin);
+  if (e != cudaSuccess || G == 1) return e;
+  const int64_t total = n_boxes * (int64_t)(G - 1) * h_out;
+  const unsigned bb = (unsigned)std::min<int64_t>((total + 255) / 256, device_sms(L) * 8);
+  k_bias_rows<<<bb, 256, 0, L.stream>>>(n_boxes, h_out, G, b, out_hi, out_lo);
+  ++*L.launches;
+  (void)nout;
+  return cudaGetLastError();
 }
 
 }  // namespace bern
