@@ -82,3 +82,10 @@ def random_dense(rng, n, D, scale=1.0, zero_frac=0.0):
 
 def l1(v):
     return float(np.abs(np.asarray(v, np.float64)).sum())
+
+
+def oracle_propagate_job(args):
+    """One box through the oracle, as a process-pool job (the pool is started
+    with 'spawn': a process forked after the GPU is in use can hang)."""
+    widths, W, b, box, degree, kw = args
+    return oracle.propagate(widths, W, b, box, degree, **kw)
