@@ -11,7 +11,10 @@
 // returned eps is >= B(s0) (s0 the s of y = 0) plus the sum of every upward
 // coefficient excess, so the polynomial minus eps stays below ReLU.  Two
 // precisions: float32 coefficients for the float32 composition kernels, and
-// float64 ones for the float64 Horner kernel of high orders.
+// float64 ones for the float64 Horner kernel of high orders.  The float32
+// path of orders 1 and 2 (the common case) uses their closed forms in float32
+// instead (relu_power_form_low): the GPU's float64 units run at a small
+// fraction of its float32 rate.
 #pragma once
 
 #include <type_traits>
@@ -92,6 +95,37 @@ static __device__ __forceinline__ void relu_power_form(float lo, float hi, int d
   relu_power_form_t<float>(lo, hi, d, a_out, eps_out);
 }
 
+// Orders 1 and 2 in closed form, float32 with directed rounding (lo < 0 < hi,
+// w = hi - lo, s0 = -lo / w).  Order 1: B(s) = hi s (the chord), B(s0) =
+// -lo hi / w.  Order 2: the middle sample is max((lo + hi)/2, 0); when lo + hi
+// > 0, B(s) = (lo + hi) s - lo s^2 and B(s0) = -lo hi^2 / w^2, otherwise
+// B(s) = hi s^2 and B(s0) = hi lo^2 / w^2 (the sign of the float sum lo + hi
+// is that of the exact one).  Every coefficient is exact but lo + hi, which
+// is rounded up; its excess and the shift are bounded with upward roundings of
+// positive quantities (w rounded down where it divides).
+static __device__ void relu_power_form_low(float lo, float hi, int d, float* a_out,
+                                           float* eps_out) {
+  const float wd = __fsub_rd(hi, lo);
+  float a1, a2 = 0.0f, excess = 0.0f, e;
+  if (d == 1) {
+    a1 = hi;
+    e = __fdiv_ru(__fmul_ru(-lo, hi), wd);
+  } else if (__fadd_rn(lo, hi) > 0.0f) {
+    a1 = __fadd_ru(lo, hi);
+    a2 = -lo;
+    excess = __fsub_ru(a1, __fadd_rd(lo, hi));   // >= a1 - (lo + hi)
+    e = __fdiv_ru(__fmul_ru(-lo, __fmul_ru(hi, hi)), __fmul_rd(wd, wd));
+  } else {
+    a1 = 0.0f;
+    a2 = hi;
+    e = __fdiv_ru(__fmul_ru(hi, __fmul_ru(lo, lo)), __fmul_rd(wd, wd));
+  }
+  a_out[0] = 0.0f;
+  a_out[1] = a1;
+  if (d == 2) a_out[2] = a2;
+  *eps_out = __fadd_ru(e, excess);
+}
+
 // Case of one item and, for case 2, its coefficients.  Returns the case.
 static __device__ int relu_item(float l, float h, int d, float* a, float* eps, int* status) {
   if (!(isfinite(l) && isfinite(h))) {
@@ -104,7 +138,10 @@ static __device__ int relu_item(float l, float h, int d, float* a, float* eps, i
     atomicOr(status, kStatusInvalid);
     return 0;
   }
-  relu_power_form(l, h, d, a, eps);
+  if (d <= 2)
+    relu_power_form_low(l, h, d, a, eps);
+  else
+    relu_power_form(l, h, d, a, eps);
   return 2;
 }
 
