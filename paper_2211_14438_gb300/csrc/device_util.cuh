@@ -81,10 +81,5 @@ __constant__ const BinomTable c_binom = make_binom_table();
 
 __device__ __forceinline__ float binomf(int l, int k) { return c_binom.v[l][k]; }
 
-__device__ __forceinline__ double binomd(int l, int k) {
-  double r = 1.0;
-  for (int i = 1; i <= k; ++i) r = r * (double)(l - k + i) / (double)i;
-  return r;
-}
 
 }  // namespace bern
