@@ -286,7 +286,22 @@ k_compose_copy(ComposeArgs A, ComposeScratch S) {
     const float* sl = A.pre_lo + A.base(item, A.pre_ld);
     float* du = A.post_up + A.base(item, A.post_ld);
     float* dl = A.post_lo + A.base(item, A.post_ld);
-    for (int r = warp; r < nt; r += nw) {
+    // four rows of each bound in flight per round
+    int r = warp;
+    for (; r + 3 * nw < nt; r += 4 * nw) {
+      float vu[4], vl[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        vu[q] = su[(r + q * nw) * h];
+        vl[q] = sl[(r + q * nw) * h];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        du[(r + q * nw) * h] = vu[q];
+        dl[(r + q * nw) * h] = vl[q];
+      }
+    }
+    for (; r < nt; r += nw) {
       du[r * h] = su[r * h];
       dl[r * h] = sl[r * h];
     }

@@ -200,7 +200,23 @@ k_stable_screen(int64_t n_items, int h, const float* __restrict__ pre_up,
       if (nt > 0) {
         l = pre_lo[base];
         u = pre_up[base];
-        for (int r = 1; r < nt; ++r) {
+        // eight coefficients of each bound in flight per round; the sums
+        // keep the sequential order
+        int r = 1;
+        for (; r + 8 <= nt; r += 8) {
+          float xl[8], xu[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            xl[q] = pre_lo[base + (int64_t)(r + q) * h];
+            xu[q] = pre_up[base + (int64_t)(r + q) * h];
+          }
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            l = __fadd_rd(l, fminf(xl[q], 0.0f));
+            u = __fadd_ru(u, fmaxf(xu[q], 0.0f));
+          }
+        }
+        for (; r < nt; ++r) {
           l = __fadd_rd(l, fminf(pre_lo[base + (int64_t)r * h], 0.0f));
           u = __fadd_ru(u, fmaxf(pre_up[base + (int64_t)r * h], 0.0f));
         }
