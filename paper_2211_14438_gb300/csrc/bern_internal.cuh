@@ -287,6 +287,13 @@ cudaError_t launch_enclose_big(const Launch& L, const Tables& T, int lb, int G, 
                                int h, const float* pre_up, const float* pre_lo, int64_t ld,
                                const int32_t* nterms, float* lo, float* hi, const int* list,
                                const int* count);
+// Grids of at least kEncloseBlkGrid cells that fit shared memory: one block
+// per polynomial (lo/hi only; the ReLU step runs on the items afterwards).
+constexpr int kEncloseBlkGrid = 2048;
+cudaError_t launch_enclose_blk(const Launch& L, const Tables& T, int lb, int G, int64_t n_items,
+                               int h, const float* pre_up, const float* pre_lo, int64_t ld,
+                               const int32_t* nterms, float* lo, float* hi, const int* list,
+                               const int* count);
 
 // The square of dense Bernstein tensors by Prod_Bern (k_bern_tensor.cu):
 // a [n_polys][(l+1)^n] -> coefficient intervals [c_lo, c_hi] of the square at

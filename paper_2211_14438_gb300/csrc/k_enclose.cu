@@ -2,6 +2,8 @@
 // effective Bernstein order.  The per-order kernels are instantiated here
 // (orders 0-8) and in k_enclose_hi.cu (9-16); orders above 16 use the
 // runtime-order kernel below.
+#include <string>
+
 #include "enclose_impl.cuh"
 
 namespace bern {
@@ -120,16 +122,37 @@ static cudaError_t launch_enclose_impl(const Launch& L, const Tables& T, int64_t
   int G;
   const int lb = effective_order(T.n, order, budget, &G, L.ews != nullptr);
   if (lb > T.rscale_max || T.rscale[lb] == nullptr) return cudaErrorInvalidValue;
-  if (G > kEncloseGridMax) {
-    // global-memory grids: lo/hi, then the ReLU step on the same items
-    cudaError_t e = launch_enclose_big(L, T, lb, G, n_items, h, pre_up, pre_lo, ld, nterms, lo,
-                                       hi, ro.list, ro.count);
-    if (e != cudaSuccess || ro.kind == nullptr) return e;
-    k_relu_coeffs_list<<<(unsigned)((n_items + 127) / 128), 128, 0, L.stream>>>(
-        ro.list, ro.count, n_items, lo, hi, ro.degrees, ro.global_d, ro.kind, ro.coef, ro.eps,
-        L.status);
-    ++*L.launches;
-    return cudaGetLastError();
+  // Shared-memory grids of at least 1024 cells: a block per polynomial
+  // (variant 3 of the enclosure tuner, the default from kEncloseBlkGrid
+  // cells) or a warp per polynomial (variants 0-2, items per block)
+  const bool blk_ok = G >= 1024 && G <= kEncloseGridMax && lb >= 3 && lb <= 16;
+  bool blk = false;
+  TuneTimer tt;
+  std::string key;
+  if (blk_ok) {
+    key = "enclose/" + std::to_string(lb) + "/" + std::to_string(T.n) + "/" +
+          std::to_string(n_items);
+    blk = tune_variant(L, "enclose", key, G >= kEncloseBlkGrid ? 3 : 0) == 3;
+  }
+  if (G > kEncloseGridMax || blk) {
+    // global-memory grids, or a block per polynomial: lo/hi, then the ReLU
+    // step on the same items
+    if (blk) tune_begin(L, "enclose", tt);
+    cudaError_t e =
+        G > kEncloseGridMax
+            ? launch_enclose_big(L, T, lb, G, n_items, h, pre_up, pre_lo, ld, nterms, lo, hi,
+                                 ro.list, ro.count)
+            : launch_enclose_blk(L, T, lb, G, n_items, h, pre_up, pre_lo, ld, nterms, lo, hi,
+                                 ro.list, ro.count);
+    if (e == cudaSuccess && ro.kind != nullptr) {
+      k_relu_coeffs_list<<<(unsigned)((n_items + 127) / 128), 128, 0, L.stream>>>(
+          ro.list, ro.count, n_items, lo, hi, ro.degrees, ro.global_d, ro.kind, ro.coef, ro.eps,
+          L.status);
+      ++*L.launches;
+      e = cudaGetLastError();
+    }
+    if (blk) tune_end(L, "enclose", key, tt);
+    return e;
   }
   if (G <= kSmallGrid && lb <= 7) {
 #define BERN_SMALL_CASE(X) \

@@ -23,7 +23,7 @@ namespace {
 
 constexpr int kBigThreads = 512;
 
-template <int LB, bool UP>
+template <int LB, bool UP, int NT>
 __device__ float enclose_block_big(const float* __restrict__ P, int ps, int nt, int n,
                                    const Tables& T, const float2* __restrict__ rs, float* grid,
                                    float* red) {
@@ -35,7 +35,7 @@ __device__ float enclose_block_big(const float* __restrict__ P, int ps, int nt, 
   const int32_t* __restrict__ gidx = T.gidx[LB];
   // scatter (block-strided; the remainder of terms above the order)
   float rem = 0.0f;
-  for (int r = tid; r < nt; r += kBigThreads) {
+  for (int r = tid; r < nt; r += NT) {
     const float a = P[(int64_t)r * ps];
     if (r < m_eff) {
       const float2 sc = rs[r];
@@ -45,7 +45,7 @@ __device__ float enclose_block_big(const float* __restrict__ P, int ps, int nt, 
       rem = UP ? __fadd_ru(rem, fmaxf(a, 0.0f)) : __fadd_rd(rem, fminf(a, 0.0f));
     }
   }
-  for (int r = nt + tid; r < m_eff; r += kBigThreads) grid[__ldg(gidx + r)] = 0.0f;
+  for (int r = nt + tid; r < m_eff; r += NT) grid[__ldg(gidx + r)] = 0.0f;
   __syncthreads();
   float best = UP ? -CUDART_INF_F : CUDART_INF_F;
   int nlines = 1;
@@ -53,7 +53,7 @@ __device__ float enclose_block_big(const float* __restrict__ P, int ps, int nt, 
   for (int k = n - 1; k >= 0; --k) {
     int sk = 1;
     for (int j = k + 1; j < n; ++j) sk *= R;
-    for (int Ln = tid; Ln < nlines; Ln += kBigThreads) {
+    for (int Ln = tid; Ln < nlines; Ln += NT) {
       // digits of the other variables, the highest variable first
       int rest = Ln, base = 0, psum = 0, pw = 1;
       for (int mm = n - 1; mm >= 0; --mm) {
@@ -100,7 +100,7 @@ __device__ float enclose_block_big(const float* __restrict__ P, int ps, int nt, 
   __syncthreads();
   float v = 0.0f;
   if (wid == 0) {
-    constexpr int kW = kBigThreads / 32;
+    constexpr int kW = NT / 32;
     float b2 = lane < kW ? red[lane] : (UP ? -CUDART_INF_F : CUDART_INF_F);
     float r2 = lane < kW ? red[32 + lane] : 0.0f;
     b2 = UP ? warp_max(b2) : warp_min(b2);
@@ -133,13 +133,71 @@ k_enclose_big(Tables T, int G, const float2* __restrict__ rs, int64_t n_items, i
     }
     const int64_t b = item / h;
     const int64_t base = (b * ld) * h + (item - b * h);
-    const float v = up ? enclose_block_big<LB, true>(pre_up + base, h, nt, T.n, T, rs, grid, red)
-                       : enclose_block_big<LB, false>(pre_lo + base, h, nt, T.n, T, rs, grid, red);
+    const float v =
+        up ? enclose_block_big<LB, true, kBigThreads>(pre_up + base, h, nt, T.n, T, rs, grid, red)
+           : enclose_block_big<LB, false, kBigThreads>(pre_lo + base, h, nt, T.n, T, rs, grid, red);
     if (threadIdx.x == 0) {
       (up ? hi : lo)[item] = v;
       if (!isfinite(v)) atomicOr(status, kStatusNonFinite);
     }
   }
+}
+
+// The same block-level transforms on grids in shared memory, for grids that
+// fit it but leave a warp-per-polynomial launch few warps per SM (e.g. 17^3
+// = 4913 cells, 19.6 KB, at order 16 in three variables): one block of
+// kBlkThreads per polynomial, as many blocks per SM as the grids allow.
+constexpr int kBlkThreads = 128;
+
+template <int LB>
+__global__ void __launch_bounds__(kBlkThreads)
+k_enclose_blk(Tables T, const float2* __restrict__ rs, int64_t n_items, int h,
+              const float* __restrict__ pre_up, const float* __restrict__ pre_lo, int64_t ld,
+              const int32_t* __restrict__ nterms, float* __restrict__ lo, float* __restrict__ hi,
+              const int* list, const int* count, int* status) {
+  extern __shared__ float sgrid[];
+  __shared__ float red[64];
+  const int64_t n_list = list ? (int64_t)*count : n_items;
+  for (int64_t p = blockIdx.x; p < 2 * n_list; p += gridDim.x) {
+    const int64_t idx = p >> 1;
+    const bool up = p & 1;
+    const int64_t item = list ? (int64_t)list[idx] : idx;
+    int nt = nterms[item];
+    if (nt < 0 || nt > ld || nt > T.mexps) {
+      if (threadIdx.x == 0) atomicOr(status, kStatusInvalid);
+      nt = 0;
+    }
+    const int64_t b = item / h;
+    const int64_t base = (b * ld) * h + (item - b * h);
+    const float v =
+        up ? enclose_block_big<LB, true, kBlkThreads>(pre_up + base, h, nt, T.n, T, rs, sgrid, red)
+           : enclose_block_big<LB, false, kBlkThreads>(pre_lo + base, h, nt, T.n, T, rs, sgrid,
+                                                       red);
+    if (threadIdx.x == 0) {
+      (up ? hi : lo)[item] = v;
+      if (!isfinite(v)) atomicOr(status, kStatusNonFinite);
+    }
+  }
+}
+
+template <int LB>
+cudaError_t launch_blk_lb(const Launch& L, const Tables& T, int G, int64_t n_items, int h,
+                          const float* pre_up, const float* pre_lo, int64_t ld,
+                          const int32_t* nterms, float* lo, float* hi, const int* list,
+                          const int* count) {
+  const size_t smem = (size_t)G * sizeof(float);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_enclose_blk<LB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int per_sm = std::max(1, std::min(16, (int)((220 * 1024) / (smem + 1024))));
+  const int64_t blocks = std::min<int64_t>((int64_t)device_sms(L) * per_sm, 2 * n_items);
+  k_enclose_blk<LB><<<(unsigned)blocks, kBlkThreads, smem, L.stream>>>(
+      T, T.rscale[LB], n_items, h, pre_up, pre_lo, ld, nterms, lo, hi, list, count, L.status);
+  ++*L.launches;
+  return cudaGetLastError();
 }
 
 template <int LB>
@@ -159,6 +217,22 @@ cudaError_t launch_big_lb(const Launch& L, const Tables& T, int G, int64_t n_ite
 }
 
 }  // namespace
+
+cudaError_t launch_enclose_blk(const Launch& L, const Tables& T, int lb, int G, int64_t n_items,
+                               int h, const float* pre_up, const float* pre_lo, int64_t ld,
+                               const int32_t* nterms, float* lo, float* hi, const int* list,
+                               const int* count) {
+  if (lb > T.rscale_max || !T.rscale[lb] || !T.gidx[lb]) return cudaErrorInvalidValue;
+#define BERN_BLK_CASE(X) \
+  case X: return launch_blk_lb<X>(L, T, G, n_items, h, pre_up, pre_lo, ld, nterms, lo, hi, list, count);
+  switch (lb) {
+    BERN_BLK_CASE(3) BERN_BLK_CASE(4) BERN_BLK_CASE(5) BERN_BLK_CASE(6) BERN_BLK_CASE(7)
+    BERN_BLK_CASE(8) BERN_BLK_CASE(9) BERN_BLK_CASE(10) BERN_BLK_CASE(11) BERN_BLK_CASE(12)
+    BERN_BLK_CASE(13) BERN_BLK_CASE(14) BERN_BLK_CASE(15) BERN_BLK_CASE(16)
+    default: return cudaErrorInvalidValue;
+  }
+#undef BERN_BLK_CASE
+}
 
 size_t enclose_big_floats(int n, int order, int64_t budget, int sms) {
   int G = 0;
