@@ -196,9 +196,12 @@ class KernelPass:
             h = widths[i + 1]
             hidden = i < self.H - 1
             Mpre = bern.num_monomials(n, D)
+            # hidden layers compose in place, as bern_propagate does: the
+            # pre-activation block has the post-activation block's row stride
+            ld = bern.num_monomials(n, min(D * w.degree, w.degree_cap)) if hidden else Mpre
             L = {"h_in": widths[i], "h": h, "hidden": hidden, "D": D, "order": order,
-                 "Mpre": Mpre,
-                 "pre": [torch.empty(B * h * Mpre, device=dev, dtype=f32) for _ in range(2)],
+                 "Mpre": Mpre, "ld": ld,
+                 "pre": [torch.empty(B * h * ld, device=dev, dtype=f32) for _ in range(2)],
                  "pre_nt": torch.empty(B * h, device=dev, dtype=i32),
                  "lo": torch.empty(B * h, device=dev, dtype=f32),
                  "hi": torch.empty(B * h, device=dev, dtype=f32)}
@@ -209,8 +212,7 @@ class KernelPass:
                           "kind": torch.empty(B * h, device=dev, dtype=torch.int8),
                           "coef": torch.empty(B * h * bern.COEF_STRIDE, device=dev, dtype=f32),
                           "eps": torch.empty(B * h, device=dev, dtype=f32),
-                          "post": [torch.empty(B * h * Mpost, device=dev, dtype=f32)
-                                   for _ in range(2)],
+                          "post": L["pre"],
                           "post_nt": torch.empty(B * h, device=dev, dtype=i32)})
                 D, order = Dp, min(order * w.degree, w.degree_cap)
             self.layers.append(L)
@@ -232,6 +234,8 @@ class KernelPass:
             self.step_per_kernel()
 
     def step_fused(self):
+        # the fused layer kernels keep separate blocks: pre-activation rows at
+        # the layer's own stride (the buffers are large enough)
         ctx, w = self.ctx, self.w
         n, B = self.n, self.B
         self.pending = []
@@ -263,9 +267,9 @@ class KernelPass:
         for i, L in enumerate(self.layers):
             self._timed("affine_L%d" % (i + 1), lambda: ctx.affine(
                 B, L["h"], L["h_in"], self.Wd[i], self.bd[i], in_u, in_l, in_stride, in_nt,
-                L["pre"][0], L["pre"][1], L["Mpre"], L["pre_nt"]))
+                L["pre"][0], L["pre"][1], L["ld"], L["pre_nt"]))
             self._timed("enclose_L%d" % (i + 1), lambda: ctx.enclose(
-                n, B, L["h"], L["order"], 0, L["pre"][0], L["pre"][1], L["Mpre"], L["pre_nt"],
+                n, B, L["h"], L["order"], 0, L["pre"][0], L["pre"][1], L["ld"], L["pre_nt"],
                 L["lo"], L["hi"]))
             if not L["hidden"]:
                 break
@@ -273,9 +277,9 @@ class KernelPass:
                 B * L["h"], L["lo"], L["hi"], None, w.degree, L["kind"], L["coef"], L["eps"]))
             self._timed("compose_L%d" % (i + 1), lambda: ctx.compose(
                 n, B, L["h"], w.degree_cap, 0.0, L["kind"], L["coef"], L["eps"], None, w.degree,
-                L["lo"], L["hi"], L["pre"][0], L["pre"][1], L["Mpre"], L["pre_nt"],
-                L["post"][0], L["post"][1], L["Mpost"], L["post_nt"]))
-            in_u, in_l, in_nt, in_stride = L["post"][0], L["post"][1], L["post_nt"], L["Mpost"]
+                L["lo"], L["hi"], L["pre"][0], L["pre"][1], L["ld"], L["pre_nt"],
+                L["post"][0], L["post"][1], L["ld"], L["post_nt"]))
+            in_u, in_l, in_nt, in_stride = L["post"][0], L["post"][1], L["post_nt"], L["ld"]
 
     def collect(self):
         self.torch.cuda.synchronize()

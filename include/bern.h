@@ -374,7 +374,12 @@ int bern_relu_coeffs(bern_ctx* ctx, int64_t n_items, const float* lo,
  * Orders 1 and 2 use closed forms (c = a0 + a1 s, a0 + a1 s + a2 s^2); orders
  * >= 3, and every order when prune_tau > 0, use Horner's rule with interval
  * coefficients.  Shapes whose Horner buffers exceed shared memory return
- * BERN_E_UNSUPPORTED. */
+ * BERN_E_UNSUPPORTED.
+ * In place: post_up == pre_up, post_lo == pre_lo and post_ld == pre_ld
+ * (which must then hold the outputs) compose the block where it stands; every
+ * kernel reads an item's inputs before writing its outputs, and identity
+ * items keep their coefficients without a copy (bern_propagate composes its
+ * hidden layers this way).  Other overlaps of pre and post are not allowed. */
 int bern_compose(bern_ctx* ctx, int n, int64_t n_boxes, int h, int degree_cap,
                  float prune_tau, const int8_t* kind, const float* coef,
                  const float* eps, const uint8_t* degrees, int global_d,

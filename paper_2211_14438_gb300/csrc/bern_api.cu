@@ -323,6 +323,10 @@ struct LayerPlan {
   int d;            // max ReLU order of this layer's neurons (hidden only)
   int D_pre, D_post;
   int64_t M_pre, M_post;
+  // row stride of the pre-activation block: M_post for the per-step hidden
+  // layers, whose composition writes the post-activation block in place
+  // (it is the same block), M_pre otherwise
+  int64_t ld_pre = 0;
   int order;        // Bernstein order of this layer's enclosure
   bool hidden;
   // per-box offsets (in bytes) into the workspace
@@ -484,8 +488,10 @@ int make_plan(const bern_net* net, const bern_degree_plan* dp, Plan& P, bool all
   P.off_z_lo = take(sizeof(float) * n * (n + 1));
   P.off_z_nt = take(sizeof(int32_t) * n);
   for (auto& l : P.L) {
-    l.off_pre_up = take(sizeof(float) * l.h_out * l.M_pre);
-    l.off_pre_lo = take(sizeof(float) * l.h_out * l.M_pre);
+    const bool in_place = l.hidden && !l.fused;
+    l.ld_pre = in_place ? std::max(l.M_pre, l.M_post) : l.M_pre;
+    l.off_pre_up = take(sizeof(float) * l.h_out * l.ld_pre);
+    l.off_pre_lo = take(sizeof(float) * l.h_out * l.ld_pre);
     l.off_pre_nt = take(sizeof(int32_t) * l.h_out);
     if (l.fused) continue;   // everything past the pre-activation block stays on chip
     l.off_lo = take(sizeof(float) * l.h_out);
@@ -494,8 +500,8 @@ int make_plan(const bern_net* net, const bern_degree_plan* dp, Plan& P, bool all
       l.off_kind = take(l.h_out);
       l.off_coef = take(sizeof(float) * l.h_out * kCoefStride);
       l.off_eps = take(sizeof(float) * l.h_out);
-      l.off_post_up = take(sizeof(float) * l.h_out * l.M_post);
-      l.off_post_lo = take(sizeof(float) * l.h_out * l.M_post);
+      l.off_post_up = l.off_pre_up;   // composed in place
+      l.off_post_lo = l.off_pre_lo;
       l.off_post_nt = take(sizeof(int32_t) * l.h_out);
       l.off_deg = (P.per_neuron || P.learned) ? take(l.h_out) : 0;
       if (l.lin) {
@@ -552,17 +558,18 @@ int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
     float* pre_up = ch.at<float>(l.off_pre_up);
     float* pre_lo = ch.at<float>(l.off_pre_lo);
     int32_t* pre_nt = ch.at<int32_t>(l.off_pre_nt);
+    const int64_t ldp = l.ld_pre;
     if (!pre_ready) {
       e = launch_affine(L, B, l.h_out, l.h_in, net->W[i], net->b[i], in_up, in_lo, in_stride,
-                        in_nt, pre_up, pre_lo, l.M_pre, pre_nt);
+                        in_nt, pre_up, pre_lo, ldp, pre_nt);
       if (e != cudaSuccess) return map_cuda(e);
     }
     pre_ready = false;
     if (l.fused) {
       const LayerPlan& nl = P.L[i + 1];
-      e = launch_layer(L, T, B, l.h_out, l.d, l.order, P.budget, P.cap, pre_up, pre_lo, l.M_pre,
+      e = launch_layer(L, T, B, l.h_out, l.d, l.order, P.budget, P.cap, pre_up, pre_lo, ldp,
                        pre_nt, nl.h_out, net->W[i + 1], net->b[i + 1],
-                       ch.at<float>(nl.off_pre_up), ch.at<float>(nl.off_pre_lo), nl.M_pre,
+                       ch.at<float>(nl.off_pre_up), ch.at<float>(nl.off_pre_lo), nl.ld_pre,
                        ch.at<int32_t>(nl.off_pre_nt),
                        c->counters() + (fused_idx++ % kLayerCounters));
       if (e != cudaSuccess) return map_cuda(e);
@@ -573,12 +580,12 @@ int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
     if (!l.hidden) {
       if (P.learned)
         e = launch_enclose_by_order(L, T, CS, B, l.h_out, ch.at<int32_t>(l.off_order), l.orders,
-                                    P.budget, pre_up, pre_lo, l.M_pre, pre_nt, out_lo, out_hi);
+                                    P.budget, pre_up, pre_lo, ldp, pre_nt, out_lo, out_hi);
       else
-        e = launch_enclose(L, T, B, l.h_out, l.order, P.budget, pre_up, pre_lo, l.M_pre, pre_nt,
+        e = launch_enclose(L, T, B, l.h_out, l.order, P.budget, pre_up, pre_lo, ldp, pre_nt,
                            out_lo, out_hi);
       if (e != cudaSuccess) return map_cuda(e);
-      e = launch_pack(L, T, B, P.o, pre_up, pre_lo, l.M_pre, pre_nt, res);
+      e = launch_pack(L, T, B, P.o, pre_up, pre_lo, ldp, pre_nt, res);
       if (e != cudaSuccess) return map_cuda(e);
       break;
     }
@@ -593,7 +600,7 @@ int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
       // enclosure at each box's order, then the MLP's orders and the a3 step
       int32_t* ord = ch.at<int32_t>(l.off_order);
       e = launch_enclose_by_order(L, T, CS, B, l.h_out, ord, l.orders, P.budget, pre_up, pre_lo,
-                                  l.M_pre, pre_nt, lo, hi);
+                                  ldp, pre_nt, lo, hi);
       if (e != cudaSuccess) return map_cuda(e);
       e = launch_learned_degrees(L, mv, B, l.h_out, i + 1, lo, hi, pre_nt, P.min_conf,
                                  P.fallback_d, l.d, P.cap, ord,
@@ -604,9 +611,9 @@ int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
       // (their lo/hi are read by nothing downstream; a trace reports the
       // Bernstein bounds of every item, so traced runs enclose all of them)
       e = launch_enclose_relu_screened(L, T, CS, B, l.h_out, l.order, P.budget, pre_up, pre_lo,
-                                       l.M_pre, pre_nt, lo, hi, deg, l.d, kind, coef, eps);
+                                       ldp, pre_nt, lo, hi, deg, l.d, kind, coef, eps);
     } else {
-      e = launch_enclose_relu(L, T, B, l.h_out, l.order, P.budget, pre_up, pre_lo, l.M_pre,
+      e = launch_enclose_relu(L, T, B, l.h_out, l.order, P.budget, pre_up, pre_lo, ldp,
                               pre_nt, lo, hi, deg, l.d, kind, coef, eps);
     }
     if (e != cudaSuccess) return map_cuda(e);
@@ -618,14 +625,15 @@ int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
     float* post_up = ch.at<float>(l.off_post_up);
     float* post_lo = ch.at<float>(l.off_post_lo);
     int32_t* post_nt = ch.at<int32_t>(l.off_post_nt);
+    // in place: the post-activation block is the pre-activation block
     e = launch_compose(L, T, CS, B, l.h_out, P.cap, P.tau, kind, coef, eps, deg, l.d, lo, hi,
-                       pre_up, pre_lo, l.M_pre, pre_nt, post_up, post_lo, l.M_post, post_nt);
+                       pre_up, pre_lo, ldp, pre_nt, post_up, post_lo, ldp, post_nt, l.M_pre);
     if (e != cudaSuccess) return map_cuda(e);
     if (l.lin) {
       float* lin_up = ch.at<float>(l.off_lin_up);
       float* lin_lo = ch.at<float>(l.off_lin_lo);
       int32_t* lin_nt = ch.at<int32_t>(l.off_lin_nt);
-      e = launch_linearize(L, T, B, l.h_out, l.order_post, P.budget, post_up, post_lo, l.M_post,
+      e = launch_linearize(L, T, B, l.h_out, l.order_post, P.budget, post_up, post_lo, ldp,
                            post_nt, lin_up, lin_lo, l.M_lin, lin_nt, ch.at<float>(l.off_lin_rlo),
                            ch.at<float>(l.off_lin_rhi));
       if (e != cudaSuccess) return map_cuda(e);
@@ -637,7 +645,7 @@ int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
       in_up = post_up;
       in_lo = post_lo;
       in_nt = post_nt;
-      in_stride = l.M_post;
+      in_stride = ldp;
     }
   }
   return BERN_OK;

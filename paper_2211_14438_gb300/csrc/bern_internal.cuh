@@ -316,12 +316,18 @@ cudaError_t launch_bernstein_affine(const Launch& L, int64_t n_boxes, int h_out,
 
 // Largest input degree the row-convolution path handles for n variables.
 int row_path_max_degree(int n);
+// The composition step (a4) over a layer block.  pre_ld / post_ld are the
+// blocks' row strides; pre_cap (0: pre_ld) the largest term count an input
+// can have, which sizes the kernels.  The post block may be the pre block
+// itself (post_up == pre_up, post_lo == pre_lo, post_ld == pre_ld): every
+// kernel reads an item's inputs before it writes the item's outputs, and the
+// identity items then need no copy.
 cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratch& S,
                            int64_t n_boxes, int h, int cap, float tau, const int8_t* kind,
                            const float* coef, const float* eps, const uint8_t* degrees,
                            int global_d, const float* lo, const float* hi, const float* pre_up,
                            const float* pre_lo, int64_t pre_ld, const int32_t* pre_nterms,
                            float* post_up, float* post_lo, int64_t post_ld,
-                           int32_t* post_nterms);
+                           int32_t* post_nterms, int64_t pre_cap = 0);
 
 }  // namespace bern

@@ -39,6 +39,7 @@ struct ComposeArgs {
   float* post_lo;
   int64_t post_ld;
   int32_t* post_nterms;
+  int64_t pre_cap;           // largest input term count (<= pre_ld)
   // offset of coefficient 0 of an item in a block with leading dimension ld;
   // coefficient r is at offset + r*h
   __device__ __forceinline__ int64_t base(int64_t item, int64_t ld) const {

@@ -47,7 +47,7 @@ k_compose_queue(Tables T, ComposeArgs A, int64_t n_items, int row_dmax, ComposeS
     const int k = A.kind[item];
     const int Mpre = A.pre_nterms[item];
     int nt = 0;
-    if (Mpre < 0 || Mpre > A.pre_ld) {
+    if (Mpre < 0 || Mpre > A.pre_cap) {
       atomicOr(status, kStatusInvalid);
     } else if (k == 1) {
       if (Mpre > A.post_ld) {
@@ -59,7 +59,7 @@ k_compose_queue(Tables T, ComposeArgs A, int64_t n_items, int row_dmax, ComposeS
     } else if (k == 2) {
       const int d = A.degrees ? (int)A.degrees[item] : A.global_d;
       const int D = degree_of(T, Mpre);
-      if (T.mcount[D] > A.pre_ld || d < 1 || d > kMaxOrder || (A.degrees && d > A.global_d)) {
+      if (T.mcount[D] > A.pre_cap || d < 1 || d > kMaxOrder || (A.degrees && d > A.global_d)) {
         atomicOr(status, kStatusInvalid);
       } else {
         const int Mout = T.mcount[min(d * D, A.cap)];
@@ -388,7 +388,7 @@ k_compose_pairs(Tables T, ComposeArgs A, ComposeScratch S, int* status) {
     const float L = A.lo[item], H = A.hi[item];
     const float inv = 1.0f / (H - L);
     float* su = smem;
-    float* sl = smem + A.pre_ld;
+    float* sl = smem + A.pre_cap;
     float au = 0.0f, al = 0.0f;
     for (int r = threadIdx.x; r < Mp; r += blockDim.x) {
       float vu = r < Mpre ? Pu[(int64_t)r * h] : 0.0f, vl = r < Mpre ? Pl[(int64_t)r * h] : 0.0f;
@@ -469,16 +469,20 @@ cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratc
                            int global_d, const float* lo, const float* hi, const float* pre_up,
                            const float* pre_lo, int64_t pre_ld, const int32_t* pre_nterms,
                            float* post_up, float* post_lo, int64_t post_ld,
-                           int32_t* post_nterms) {
+                           int32_t* post_nterms, int64_t pre_cap) {
   const int64_t n_items = n_boxes * h;
   if (n_items == 0) return cudaSuccess;
-  if (!(tau >= 0.0f) || n_items > S.qcap || n_items > INT32_MAX) return cudaErrorInvalidValue;
+  if (pre_cap <= 0) pre_cap = pre_ld;
+  if (!(tau >= 0.0f) || n_items > S.qcap || n_items > INT32_MAX || pre_cap > pre_ld)
+    return cudaErrorInvalidValue;
+  const bool in_place = post_up == pre_up && post_lo == pre_lo;
+  if (in_place && post_ld != pre_ld) return cudaErrorInvalidValue;
   ComposeArgs A{cap, tau, h, kind, coef, eps, degrees, global_d, lo, hi, pre_up, pre_lo, pre_ld,
-                pre_nterms, post_up, post_lo, post_ld, post_nterms};
+                pre_nterms, post_up, post_lo, post_ld, post_nterms, pre_cap};
   // the largest input degree any item of this call can have
   int Dmax = 0;
   while (Dmax < kMaxTableDegree && num_monomials(T.n, Dmax + 1) >= 0 &&
-         num_monomials(T.n, Dmax + 1) <= pre_ld)
+         num_monomials(T.n, Dmax + 1) <= pre_cap)
     ++Dmax;
   const int row_dmax = std::min(std::min(T.row_dmax, row_path_max_degree(T.n)), Dmax);
   cudaError_t e = cudaMemsetAsync(S.qcount, 0, kComposeQueues * sizeof(int), L.stream);
@@ -506,15 +510,17 @@ cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratc
   k_compose_rows<false><<<blocks, 32 * kRowWarps, smem, L.stream>>>(T, A, S, row_dmax, sstride,
                                                                     L.status);
   *L.launches += 2;
-  k_compose_copy<<<(unsigned)std::min<int64_t>((n_items + 31) / 32, device_sms(L) * 16), 256, 0,
-                   L.stream>>>(A, S);
-  ++*L.launches;
+  if (!in_place) {   // in place, an identity item's outputs are its inputs
+    k_compose_copy<<<(unsigned)std::min<int64_t>((n_items + 31) / 32, device_sms(L) * 16), 256, 0,
+                     L.stream>>>(A, S);
+    ++*L.launches;
+  }
   k_compose_linear<<<(unsigned)std::min<int64_t>((n_items + 7) / 8, device_sms(L) * 16), 256, 0,
                      L.stream>>>(A, S, L.status);
   ++*L.launches;
   // pair-list kernel for order-2 items beyond the row path
   if (Dmax > row_dmax) {
-    const size_t psmem = 2 * (size_t)pre_ld * sizeof(float);
+    const size_t psmem = 2 * (size_t)pre_cap * sizeof(float);
     if (psmem > 200 * 1024) return cudaErrorInvalidValue;
     if (psmem > 48 * 1024) {
       e = cudaFuncSetAttribute(k_compose_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize,

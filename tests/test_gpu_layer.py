@@ -290,3 +290,30 @@ def test_propagate_fused_matches_step_path(ctx):
             k = int(nt[i, 0, s])
             assert np.abs(cf[i, 0, s, :k] - cs[i, 0, s, :k]).sum() <= \
                 1e-5 * (1 + np.abs(cs[i, 0, s, :k]).sum())
+
+
+def test_propagate_fused_then_in_place_layer(ctx):
+    """A six-input net whose last hidden layer is too large for the fused
+    kernel (input degree 8 beyond the row path): the fused kernels of the
+    first layers write that layer's pre-activation block at its in-place row
+    stride (the stride of its post-activation block), and the per-step
+    kernels compose it in place.  The same results as the per-step path."""
+    net = wl.make_net([6, 12, 12, 12, 12, 1], 71)
+    rng = np.random.default_rng(71)
+    c = rng.uniform(-0.8, 0.8, (16, 6))
+    s = rng.uniform(0.05, 0.3, (16, 6))
+    boxes = dev(wl.box_array(c - s / 2, c + s / 2))
+    W = [dev(x) for x in net.W]
+    b = [dev(x) for x in net.b]
+    ct = bern.max_output_terms(net.widths, 2, 16)
+    ctx.set_fused(True)
+    try:
+        fa = ctx.propagate(net.widths, W, b, boxes, degree=2, cap=16, cap_terms=ct)
+    finally:
+        ctx.set_fused(False)
+    st = ctx.propagate(net.widths, W, b, boxes, degree=2, cap=16, cap_terms=ct)
+    assert np.array_equal(fa["n_terms"].cpu().numpy(), st["n_terms"].cpu().numpy())
+    for k in ("lo", "hi"):
+        x, y = fa[k].cpu().numpy().astype(np.float64), st[k].cpu().numpy().astype(np.float64)
+        assert np.all(np.isfinite(x))
+        assert np.all(np.abs(x - y) <= 1e-5 * (1 + np.abs(y)))
