@@ -490,6 +490,9 @@ cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratc
   k_compose_queue<<<(unsigned)((n_items + 1023) / 1024), 1024, 0, L.stream>>>(
       T, A, n_items, row_dmax, S, L.status);
   ++*L.launches;
+  // order-2 items exist only with order 2 somewhere in the plan (with pruning
+  // they go to the Horner kernel)
+  const bool order2 = tau == 0.0f && (degrees != nullptr || global_d == 2);
   // row-convolution kernels (one per bound): persistent blocks of 2 warps
   // per 32 items; the per-lane stride is odd so that lanes reading the same
   // offset hit distinct banks
@@ -505,21 +508,27 @@ cudaError_t launch_compose(const Launch& L, const Tables& T, const ComposeScratc
   }
   const int64_t tasks = n_items / 32 + row_dmax + 1;
   const int blocks = (int)std::min<int64_t>(tasks, device_sms(L) * kRowBlocks);
-  k_compose_rows<true><<<blocks, 32 * kRowWarps, smem, L.stream>>>(T, A, S, row_dmax, sstride,
-                                                                   L.status);
-  k_compose_rows<false><<<blocks, 32 * kRowWarps, smem, L.stream>>>(T, A, S, row_dmax, sstride,
-                                                                    L.status);
-  *L.launches += 2;
+  if (order2) {
+    k_compose_rows<true><<<blocks, 32 * kRowWarps, smem, L.stream>>>(T, A, S, row_dmax, sstride,
+                                                                     L.status);
+    k_compose_rows<false><<<blocks, 32 * kRowWarps, smem, L.stream>>>(T, A, S, row_dmax,
+                                                                      sstride, L.status);
+    *L.launches += 2;
+  }
   if (!in_place) {   // in place, an identity item's outputs are its inputs
     k_compose_copy<<<(unsigned)std::min<int64_t>((n_items + 31) / 32, device_sms(L) * 16), 256, 0,
                      L.stream>>>(A, S);
     ++*L.launches;
   }
-  k_compose_linear<<<(unsigned)std::min<int64_t>((n_items + 7) / 8, device_sms(L) * 16), 256, 0,
-                     L.stream>>>(A, S, L.status);
-  ++*L.launches;
+  // order-1 items exist only with order 1 somewhere in the plan (with pruning
+  // they go to the Horner kernel)
+  if (tau == 0.0f && (degrees != nullptr || global_d == 1)) {
+    k_compose_linear<<<(unsigned)std::min<int64_t>((n_items + 7) / 8, device_sms(L) * 16), 256,
+                       0, L.stream>>>(A, S, L.status);
+    ++*L.launches;
+  }
   // pair-list kernel for order-2 items beyond the row path
-  if (Dmax > row_dmax) {
+  if (order2 && Dmax > row_dmax) {
     const size_t psmem = 2 * (size_t)pre_cap * sizeof(float);
     if (psmem > 200 * 1024) return cudaErrorInvalidValue;
     if (psmem > 48 * 1024) {
