@@ -260,6 +260,102 @@ k_stable_screen(int64_t n_items, int h, const float* __restrict__ pre_up,
   if (need) list[at + __popc(m & ((1u << lane) - 1u))] = (int)it;
 }
 
+// The same screen with four neighbouring neurons per thread (h a multiple of
+// 4, 16-byte aligned blocks): one float4 load per coefficient row and bound
+// serves four items, each summed in the same order as above.
+__global__ void __launch_bounds__(256)
+k_stable_screen4(int64_t n_items, int h, const float4* __restrict__ pre_up4,
+                 const float4* __restrict__ pre_lo4, int64_t ld,
+                 const int32_t* __restrict__ nterms, float* __restrict__ lo,
+                 float* __restrict__ hi, int8_t* __restrict__ kind, int* __restrict__ list,
+                 int* __restrict__ count) {
+  const int lane = threadIdx.x & 31;
+  const int64_t it0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  bool need[4] = {false, false, false, false};
+  if (it0 < n_items) {
+    int nt[4], ntmax = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      nt[i] = nterms[it0 + i];
+      if (nt[i] < 0 || nt[i] > ld) {
+        need[i] = true;                             // the enclosure reports it
+        nt[i] = 0;
+      }
+      ntmax = max(ntmax, nt[i]);
+    }
+    const int64_t b = it0 / h;
+    const int64_t hq = h >> 2;                      // float4s per coefficient row
+    const int64_t base = ((b * ld) * h + (it0 - b * h)) >> 2;
+    float l[4] = {0.0f, 0.0f, 0.0f, 0.0f}, u[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (ntmax > 0) {
+      const float4 a = pre_lo4[base], c = pre_up4[base];
+      const float al[4] = {a.x, a.y, a.z, a.w}, cu[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        l[i] = nt[i] > 0 ? al[i] : 0.0f;
+        u[i] = nt[i] > 0 ? cu[i] : 0.0f;
+      }
+    }
+    int r = 1;
+    for (; r + 4 <= ntmax; r += 4) {
+      float4 xl[4], xu[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        xl[q] = pre_lo4[base + (r + q) * hq];
+        xu[q] = pre_up4[base + (r + q) * hq];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float vl[4] = {xl[q].x, xl[q].y, xl[q].z, xl[q].w};
+        const float vu[4] = {xu[q].x, xu[q].y, xu[q].z, xu[q].w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (r + q < nt[i]) {
+            l[i] = __fadd_rd(l[i], fminf(vl[i], 0.0f));
+            u[i] = __fadd_ru(u[i], fmaxf(vu[i], 0.0f));
+          }
+      }
+    }
+    for (; r < ntmax; ++r) {
+      const float4 x = pre_lo4[base + r * hq], y = pre_up4[base + r * hq];
+      const float vl[4] = {x.x, x.y, x.z, x.w}, vu[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (r < nt[i]) {
+          l[i] = __fadd_rd(l[i], fminf(vl[i], 0.0f));
+          u[i] = __fadd_ru(u[i], fmaxf(vu[i], 0.0f));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (need[i]) continue;
+      if (!(isfinite(l[i]) && isfinite(u[i])) || (u[i] > 0.0f && l[i] < 0.0f)) {
+        need[i] = true;
+      } else {
+        kind[it0 + i] = u[i] <= 0.0f ? 0 : 1;
+        lo[it0 + i] = l[i];
+        hi[it0 + i] = u[i];
+      }
+    }
+  }
+  // append this thread's undecided items: a warp scan of the counts, one
+  // atomic per warp
+  const int cnt = (int)need[0] + (int)need[1] + (int)need[2] + (int)need[3];
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  int at = 0;
+  if (lane == 31 && total) at = atomicAdd(count, total);
+  at = __shfl_sync(0xffffffffu, at, 31) + incl - cnt;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (need[i]) list[at++] = (int)(it0 + i);
+}
+
 cudaError_t launch_enclose_relu_screened(const Launch& L, const Tables& T,
                                          const ComposeScratch& S, int64_t n_boxes, int h,
                                          int order, int64_t budget, const float* pre_up,
@@ -272,8 +368,16 @@ cudaError_t launch_enclose_relu_screened(const Launch& L, const Tables& T,
   if (n_items > S.qcap || n_items > 0x7fffffff) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(S.qcount, 0, sizeof(int), L.stream);
   if (e != cudaSuccess) return e;
-  k_stable_screen<<<(unsigned)((n_items + 255) / 256), 256, 0, L.stream>>>(
-      n_items, h, pre_up, pre_lo, ld, nterms, lo, hi, kind, S.queue, S.qcount);
+  const bool quads = (h & 3) == 0 &&
+                     ((reinterpret_cast<uintptr_t>(pre_up) | reinterpret_cast<uintptr_t>(pre_lo)) &
+                      15) == 0;
+  if (quads)
+    k_stable_screen4<<<(unsigned)((n_items / 4 + 255) / 256), 256, 0, L.stream>>>(
+        n_items, h, reinterpret_cast<const float4*>(pre_up),
+        reinterpret_cast<const float4*>(pre_lo), ld, nterms, lo, hi, kind, S.queue, S.qcount);
+  else
+    k_stable_screen<<<(unsigned)((n_items + 255) / 256), 256, 0, L.stream>>>(
+        n_items, h, pre_up, pre_lo, ld, nterms, lo, hi, kind, S.queue, S.qcount);
   ++*L.launches;
   EncloseOpts o{kind, coef, eps, degrees, global_d};
   o.list = S.queue;
