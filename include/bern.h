@@ -189,9 +189,10 @@ int bern_set_autotune(bern_ctx* ctx, int enable);
  * 8x4 thread tiles, 64x32 block tiles, persistent register-blocked 8x2 and
  * 8x1 thread tiles; 0, 2 and 3 fall back to 1 where the layer's weights do
  * not fit shared memory) or "enclose"
- * (variants 0-2: 8, 4 or 2 items per block with a warp per polynomial; 3: a
- * block per polynomial for shared-memory grids of 1024 cells or more at
- * orders 3-16, else as 2).  variant = -1 clears the force.
+ * (variants 0-2: 8, 4 or 2 items per block with a warp per polynomial; 3, 4:
+ * a block of 128 or 320 threads per polynomial for shared-memory grids of
+ * 1024 cells or more at orders 3-16, else as 2).  variant = -1 clears the
+ * force.
  * Drops captured graphs.  Returns BERN_E_INVALID for an unknown kind or a
  * variant out of range. */
 int bern_force_variant(bern_ctx* ctx, const char* kind, int variant);

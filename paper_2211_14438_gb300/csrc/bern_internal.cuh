@@ -293,7 +293,7 @@ constexpr int kEncloseBlkGrid = 2048;
 cudaError_t launch_enclose_blk(const Launch& L, const Tables& T, int lb, int G, int64_t n_items,
                                int h, const float* pre_up, const float* pre_lo, int64_t ld,
                                const int32_t* nterms, float* lo, float* hi, const int* list,
-                               const int* count);
+                               const int* count, bool wide);
 
 // The square of dense Bernstein tensors by Prod_Bern (k_bern_tensor.cu):
 // a [n_polys][(l+1)^n] -> coefficient intervals [c_lo, c_hi] of the square at

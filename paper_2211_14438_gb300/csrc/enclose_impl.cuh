@@ -231,9 +231,9 @@ cudaError_t launch_lb(const Launch& L, const Tables& T, int G, int64_t n_items, 
                       const float* pre_up, const float* pre_lo, int64_t ld,
                       const int32_t* nterms, float* lo, float* hi, EncloseOpts ro) {
   // items per block: as many as fit 192 KB of grids, at most 8 (16 warps);
-  // autotuned among 8, 4 and 2 (variants 0, 1, 2; variant 3, a block per
-  // polynomial, is taken before this launcher where it applies, and runs as
-  // variant 2 where it does not)
+  // autotuned among 8, 4 and 2 (variants 0, 1, 2; variants 3 and 4, a block
+  // per polynomial, are taken before this launcher where they apply, and run
+  // as variant 2 where they do not)
   int items = (int)std::min<int64_t>(8, (192 * 1024) / (2 * (int64_t)G * 4));
   const std::string key = "enclose/" + std::to_string(LB) + "/" + std::to_string(T.n) + "/" +
                           std::to_string(n_items);

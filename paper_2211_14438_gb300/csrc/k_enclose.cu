@@ -123,16 +123,19 @@ static cudaError_t launch_enclose_impl(const Launch& L, const Tables& T, int64_t
   const int lb = effective_order(T.n, order, budget, &G, L.ews != nullptr);
   if (lb > T.rscale_max || T.rscale[lb] == nullptr) return cudaErrorInvalidValue;
   // Shared-memory grids of at least 1024 cells: a block per polynomial
-  // (variant 3 of the enclosure tuner, the default from kEncloseBlkGrid
-  // cells) or a warp per polynomial (variants 0-2, items per block)
+  // (variants 3 and 4 of the enclosure tuner: 128 or 320 threads; 3 is the
+  // default from kEncloseBlkGrid cells) or a warp per polynomial (variants
+  // 0-2, items per block)
   const bool blk_ok = G >= 1024 && G <= kEncloseGridMax && lb >= 3 && lb <= 16;
-  bool blk = false;
+  bool blk = false, blk_wide = false;
   TuneTimer tt;
   std::string key;
   if (blk_ok) {
     key = "enclose/" + std::to_string(lb) + "/" + std::to_string(T.n) + "/" +
           std::to_string(n_items);
-    blk = tune_variant(L, "enclose", key, G >= kEncloseBlkGrid ? 3 : 0) == 3;
+    const int v = tune_variant(L, "enclose", key, G >= kEncloseBlkGrid ? 3 : 0);
+    blk = v >= 3;
+    blk_wide = v == 4;
   }
   if (G > kEncloseGridMax || blk) {
     // global-memory grids, or a block per polynomial: lo/hi, then the ReLU
@@ -143,7 +146,7 @@ static cudaError_t launch_enclose_impl(const Launch& L, const Tables& T, int64_t
             ? launch_enclose_big(L, T, lb, G, n_items, h, pre_up, pre_lo, ld, nterms, lo, hi,
                                  ro.list, ro.count)
             : launch_enclose_blk(L, T, lb, G, n_items, h, pre_up, pre_lo, ld, nterms, lo, hi,
-                                 ro.list, ro.count);
+                                 ro.list, ro.count, blk_wide);
     if (e == cudaSuccess && ro.kind != nullptr) {
       k_relu_coeffs_list<<<(unsigned)((n_items + 127) / 128), 128, 0, L.stream>>>(
           ro.list, ro.count, n_items, lo, hi, ro.degrees, ro.global_d, ro.kind, ro.coef, ro.eps,

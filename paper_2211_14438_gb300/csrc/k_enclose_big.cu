@@ -146,11 +146,10 @@ k_enclose_big(Tables T, int G, const float2* __restrict__ rs, int64_t n_items, i
 // The same block-level transforms on grids in shared memory, for grids that
 // fit it but leave a warp-per-polynomial launch few warps per SM (e.g. 17^3
 // = 4913 cells, 19.6 KB, at order 16 in three variables): one block of
-// kBlkThreads per polynomial, as many blocks per SM as the grids allow.
-constexpr int kBlkThreads = 128;
-
-template <int LB>
-__global__ void __launch_bounds__(kBlkThreads)
+// 128 or 320 threads per polynomial, as many blocks per SM as the grids and
+// threads allow.
+template <int LB, int NT>
+__global__ void __launch_bounds__(NT)
 k_enclose_blk(Tables T, const float2* __restrict__ rs, int64_t n_items, int h,
               const float* __restrict__ pre_up, const float* __restrict__ pre_lo, int64_t ld,
               const int32_t* __restrict__ nterms, float* __restrict__ lo, float* __restrict__ hi,
@@ -170,9 +169,8 @@ k_enclose_blk(Tables T, const float2* __restrict__ rs, int64_t n_items, int h,
     const int64_t b = item / h;
     const int64_t base = (b * ld) * h + (item - b * h);
     const float v =
-        up ? enclose_block_big<LB, true, kBlkThreads>(pre_up + base, h, nt, T.n, T, rs, sgrid, red)
-           : enclose_block_big<LB, false, kBlkThreads>(pre_lo + base, h, nt, T.n, T, rs, sgrid,
-                                                       red);
+        up ? enclose_block_big<LB, true, NT>(pre_up + base, h, nt, T.n, T, rs, sgrid, red)
+           : enclose_block_big<LB, false, NT>(pre_lo + base, h, nt, T.n, T, rs, sgrid, red);
     if (threadIdx.x == 0) {
       (up ? hi : lo)[item] = v;
       if (!isfinite(v)) atomicOr(status, kStatusNonFinite);
@@ -180,24 +178,38 @@ k_enclose_blk(Tables T, const float2* __restrict__ rs, int64_t n_items, int h,
   }
 }
 
-template <int LB>
-cudaError_t launch_blk_lb(const Launch& L, const Tables& T, int G, int64_t n_items, int h,
+template <int LB, int NT>
+cudaError_t launch_blk_nt(const Launch& L, const Tables& T, int G, int64_t n_items, int h,
                           const float* pre_up, const float* pre_lo, int64_t ld,
                           const int32_t* nterms, float* lo, float* hi, const int* list,
                           const int* count) {
   const size_t smem = (size_t)G * sizeof(float);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_enclose_blk<LB>,
+    cudaError_t e = cudaFuncSetAttribute(k_enclose_blk<LB, NT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  const int per_sm = std::max(1, std::min(16, (int)((220 * 1024) / (smem + 1024))));
+  const int by_smem = (int)((220 * 1024) / (smem + 1024)), by_threads = 2048 / NT;
+  const int per_sm = std::max(1, std::min(16, std::min(by_smem, by_threads)));
   const int64_t blocks = std::min<int64_t>((int64_t)device_sms(L) * per_sm, 2 * n_items);
-  k_enclose_blk<LB><<<(unsigned)blocks, kBlkThreads, smem, L.stream>>>(
+  k_enclose_blk<LB, NT><<<(unsigned)blocks, NT, smem, L.stream>>>(
       T, T.rscale[LB], n_items, h, pre_up, pre_lo, ld, nterms, lo, hi, list, count, L.status);
   ++*L.launches;
   return cudaGetLastError();
+}
+
+// 128 threads a polynomial, or 320 (a pass over the 289 lines of a 17^3 grid
+// in one round)
+template <int LB>
+cudaError_t launch_blk_lb(const Launch& L, const Tables& T, int G, int64_t n_items, int h,
+                          const float* pre_up, const float* pre_lo, int64_t ld,
+                          const int32_t* nterms, float* lo, float* hi, const int* list,
+                          const int* count, bool wide) {
+  return wide ? launch_blk_nt<LB, 320>(L, T, G, n_items, h, pre_up, pre_lo, ld, nterms, lo, hi,
+                                       list, count)
+              : launch_blk_nt<LB, 128>(L, T, G, n_items, h, pre_up, pre_lo, ld, nterms, lo, hi,
+                                       list, count);
 }
 
 template <int LB>
@@ -221,10 +233,11 @@ cudaError_t launch_big_lb(const Launch& L, const Tables& T, int G, int64_t n_ite
 cudaError_t launch_enclose_blk(const Launch& L, const Tables& T, int lb, int G, int64_t n_items,
                                int h, const float* pre_up, const float* pre_lo, int64_t ld,
                                const int32_t* nterms, float* lo, float* hi, const int* list,
-                               const int* count) {
+                               const int* count, bool wide) {
   if (lb > T.rscale_max || !T.rscale[lb] || !T.gidx[lb]) return cudaErrorInvalidValue;
 #define BERN_BLK_CASE(X) \
-  case X: return launch_blk_lb<X>(L, T, G, n_items, h, pre_up, pre_lo, ld, nterms, lo, hi, list, count);
+  case X: return launch_blk_lb<X>(L, T, G, n_items, h, pre_up, pre_lo, ld, nterms, lo, hi, list, \
+                                  count, wide);
   switch (lb) {
     BERN_BLK_CASE(3) BERN_BLK_CASE(4) BERN_BLK_CASE(5) BERN_BLK_CASE(6) BERN_BLK_CASE(7)
     BERN_BLK_CASE(8) BERN_BLK_CASE(9) BERN_BLK_CASE(10) BERN_BLK_CASE(11) BERN_BLK_CASE(12)
