@@ -559,9 +559,21 @@ int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
     float* pre_lo = ch.at<float>(l.off_pre_lo);
     int32_t* pre_nt = ch.at<int32_t>(l.off_pre_nt);
     const int64_t ldp = l.ld_pre;
+    // the stability screen of a plain untraced hidden layer (R21) rides on
+    // the affine step where its kernel supports it
+    const bool screen_here = l.hidden && !l.fused && !P.learned && !trace && !pre_ready;
+    bool screened = false;
     if (!pre_ready) {
+      ScreenOut so;
+      if (screen_here) {
+        so = ScreenOut{ch.at<float>(l.off_lo), ch.at<float>(l.off_hi), ch.at<int8_t>(l.off_kind),
+                       CS.queue, CS.qcount};
+        e = cudaMemsetAsync(CS.qcount, 0, sizeof(int), s);
+        if (e != cudaSuccess) return map_cuda(e);
+      }
       e = launch_affine(L, B, l.h_out, l.h_in, net->W[i], net->b[i], in_up, in_lo, in_stride,
-                        in_nt, pre_up, pre_lo, ldp, pre_nt);
+                        in_nt, pre_up, pre_lo, ldp, pre_nt, screen_here ? &so : nullptr,
+                        &screened);
       if (e != cudaSuccess) return map_cuda(e);
     }
     pre_ready = false;
@@ -610,8 +622,12 @@ int run_chunk(bern_ctx* c, cudaStream_t s, const Plan& P, const Tables& T,
       // stable items decided by their coefficient signs skip the enclosure
       // (their lo/hi are read by nothing downstream; a trace reports the
       // Bernstein bounds of every item, so traced runs enclose all of them)
-      e = launch_enclose_relu_screened(L, T, CS, B, l.h_out, l.order, P.budget, pre_up, pre_lo,
-                                       ldp, pre_nt, lo, hi, deg, l.d, kind, coef, eps);
+      e = screened
+              ? launch_enclose_relu_listed(L, T, CS, B, l.h_out, l.order, P.budget, pre_up, pre_lo,
+                                           ldp, pre_nt, lo, hi, deg, l.d, kind, coef, eps)
+              : launch_enclose_relu_screened(L, T, CS, B, l.h_out, l.order, P.budget, pre_up,
+                                             pre_lo, ldp, pre_nt, lo, hi, deg, l.d, kind, coef,
+                                             eps);
     } else {
       e = launch_enclose_relu(L, T, B, l.h_out, l.order, P.budget, pre_up, pre_lo, ldp,
                               pre_nt, lo, hi, deg, l.d, kind, coef, eps);

@@ -179,11 +179,25 @@ size_t poly_to_x_smem(int n, int D);
 cudaError_t launch_poly_to_x(const Launch& L, const Tables& T, int n, int64_t n_boxes, int o,
                              const float* boxes, const int32_t* nterms, const float* coef_t,
                              int64_t cap, float* coef_x, int D);
+// Outputs of the stability screen (R21) when the affine step computes it
+// from the coefficients it writes: per item the case and the interval of the
+// decided items, and the list of the undecided ones (count zeroed by the
+// caller).
+struct ScreenOut {
+  float* lo = nullptr;
+  float* hi = nullptr;
+  int8_t* kind = nullptr;
+  int* list = nullptr;
+  int* count = nullptr;
+};
+// The affine step (a1).  With `screen`, kernels that can also screen the
+// output items do, and *screened says whether this launch did.
 cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
                           const float* W, const float* b, const float* in_up,
                           const float* in_lo, int64_t in_ld, const int32_t* in_nterms,
                           float* out_up, float* out_lo, int64_t out_ld,
-                          int32_t* out_nterms);
+                          int32_t* out_nterms, const ScreenOut* screen = nullptr,
+                          bool* screened = nullptr);
 cudaError_t launch_enclose(const Launch& L, const Tables& T, int64_t n_boxes, int h, int order,
                            int64_t budget, const float* pre_up, const float* pre_lo, int64_t ld,
                            const int32_t* nterms, float* lo, float* hi);
@@ -197,6 +211,15 @@ struct ComposeScratch;
 // shows stable get their case (and that interval as lo/hi) without the
 // enclosure; the rest go through it as an item list in S's first queue.
 cudaError_t launch_enclose_relu_screened(const Launch& L, const Tables& T,
+                                         const ComposeScratch& S, int64_t n_boxes, int h,
+                                         int order, int64_t budget, const float* pre_up,
+                                         const float* pre_lo, int64_t ld,
+                                         const int32_t* nterms, float* lo, float* hi,
+                                         const uint8_t* degrees, int global_d, int8_t* kind,
+                                         float* coef, float* eps);
+// The same when the items were screened already (by the affine step): the
+// enclosure and ReLU step over the list in the scratch queue.
+cudaError_t launch_enclose_relu_listed(const Launch& L, const Tables& T,
                                          const ComposeScratch& S, int64_t n_boxes, int h,
                                          int order, int64_t budget, const float* pre_up,
                                          const float* pre_lo, int64_t ld,

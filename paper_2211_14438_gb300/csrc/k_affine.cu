@@ -164,24 +164,34 @@ k_affine(int h_out, int h_in, const float* __restrict__ W, const float* __restri
 // load; 4 pairs are read as float2 per input j, and |w| is taken in the
 // radius FMA itself.  The staging issues kWBatch loads of each bound per
 // thread before converting any.  A warp covers 16 rows of the tile and skips
-// the tile when all of them are at or past the box's term count.
+// the tile when all of them are at or past the box's term count.  With a
+// ScreenOut it also screens the box's output items (R21): every thread sums
+// max(0, upper) and min(0, lower) of its output coefficients past the first
+// (rounding up, resp. down), the four lanes of a warp that share neurons
+// combine theirs, each warp adds its sum into its own shared row, and after
+// the box the rows are added to the constant coefficient in warp order.
 constexpr int kWThreads = 128;
 constexpr int kWBatch = 8;
 
-template <int TR, int MINB>
+template <int TR, int MINB, bool SCREEN>
 __global__ void __launch_bounds__(kWThreads, MINB)
 k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
               const float* __restrict__ bias, const float* __restrict__ in_up,
               const float* __restrict__ in_lo, int64_t in_ld,
               const int32_t* __restrict__ in_nterms, float* __restrict__ out_up,
               float* __restrict__ out_lo, int64_t out_ld, int32_t* __restrict__ out_nterms,
-              int* status) {
+              ScreenOut so, int* status) {
   constexpr int ROWS = 16 * TR;                      // rows per tile
   extern __shared__ float4 smem4[];
   const int hp = (h_out + 63) & ~63;                 // neurons padded to 64
   float* sW = reinterpret_cast<float*>(smem4);       // [h_in][hp]
   float2* sCR = reinterpret_cast<float2*>(sW + (size_t)h_in * hp);   // [ROWS][h_in + 1]
   int* sN = reinterpret_cast<int*>(sCR + (size_t)ROWS * (h_in + 1));   // [h_in]
+  // screen partials: per warp and neuron the directed sums of max(0, upper)
+  // and min(0, lower) over the warp's rows past the first, and row 0 itself
+  float* sScr = reinterpret_cast<float*>(sN + h_in);   // [4][2][hp]
+  float* sC0 = sScr + 8 * hp;                          // [2][hp]
+  constexpr bool screen = SCREEN;
   __shared__ int sMax;
   const int tid = threadIdx.x, warp = tid >> 5;
   for (int idx = tid; idx < h_in * hp; idx += kWThreads) {
@@ -216,6 +226,8 @@ k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
       continue;
     }
     for (int m = tid; m < h_out; m += kWThreads) out_nterms[b * h_out + m] = M;
+    if (screen)
+      for (int x = tid; x < 8 * hp; x += kWThreads) sScr[x] = 0.0f;
     const float* gU = in_up + (b * in_ld) * h_in;
     const float* gL = in_lo + (b * in_ld) * h_in;
     for (int r0 = 0; r0 < M; r0 += ROWS) {
@@ -287,33 +299,95 @@ k_affine_wide(int64_t n_boxes, int h_out, int h_in, const float* __restrict__ W,
 #pragma unroll
         for (int k = 0; k < TR; ++k) {
           const int r = r0 + tr * TR + k;
-          if (r >= M) continue;
+          const bool valid = r < M;
           float vu[8], vl[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             vu[i] = __fadd_ru(uc[k][i], rad[k][i]);
             vl[i] = __fsub_rd(lc[k][i], rad[k][i]);
           }
-          const int64_t o = (b * out_ld + r) * h_out + m0;
+          if (valid) {
+            const int64_t o = (b * out_ld + r) * h_out + m0;
 #pragma unroll
-          for (int half = 0; half < 2; ++half) {
-            const int mb = m0 + 32 * half + 4 * tm;
-            const int64_t oh = o + 32 * half + 4 * tm;
-            const float* pu = vu + 4 * half;
-            const float* pl = vl + 4 * half;
-            if (vec_out && mb + 4 <= h_out) {
-              *reinterpret_cast<float4*>(out_up + oh) = make_float4(pu[0], pu[1], pu[2], pu[3]);
-              *reinterpret_cast<float4*>(out_lo + oh) = make_float4(pl[0], pl[1], pl[2], pl[3]);
-            } else {
+            for (int half = 0; half < 2; ++half) {
+              const int mb = m0 + 32 * half + 4 * tm;
+              const int64_t oh = o + 32 * half + 4 * tm;
+              const float* pu = vu + 4 * half;
+              const float* pl = vl + 4 * half;
+              if (vec_out && mb + 4 <= h_out) {
+                *reinterpret_cast<float4*>(out_up + oh) = make_float4(pu[0], pu[1], pu[2], pu[3]);
+                *reinterpret_cast<float4*>(out_lo + oh) = make_float4(pl[0], pl[1], pl[2], pl[3]);
+              } else {
 #pragma unroll
-              for (int i = 0; i < 4; ++i)
-                if (mb + i < h_out) {
-                  out_up[oh + i] = pu[i];
-                  out_lo[oh + i] = pl[i];
-                }
+                for (int i = 0; i < 4; ++i)
+                  if (mb + i < h_out) {
+                    out_up[oh + i] = pu[i];
+                    out_lo[oh + i] = pl[i];
+                  }
+              }
+            }
+          }
+          if (screen) {   // warp-uniform (every lane runs every k)
+            if (valid && r == 0) {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const int m = m0 + (i < 4 ? 4 * tm + i : 28 + 4 * tm + i);
+                sC0[m] = vu[i];
+                sC0[hp + m] = vl[i];
+              }
+            }
+            // this row's one-sided parts, combined over the four lanes of the
+            // warp that share neurons (lane, lane ^ 8, ^ 16, ^ 24), then added
+            // into the warp's own shared row
+            const bool part = valid && r > 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              float cu = part ? fmaxf(vu[i], 0.0f) : 0.0f;
+              float cl = part ? fminf(vl[i], 0.0f) : 0.0f;
+              cu = __fadd_ru(cu, __shfl_xor_sync(0xffffffffu, cu, 8));
+              cl = __fadd_rd(cl, __shfl_xor_sync(0xffffffffu, cl, 8));
+              cu = __fadd_ru(cu, __shfl_xor_sync(0xffffffffu, cu, 16));
+              cl = __fadd_rd(cl, __shfl_xor_sync(0xffffffffu, cl, 16));
+              if ((tid & 31) < 8) {
+                const int m = m0 + (i < 4 ? 4 * tm + i : 28 + 4 * tm + i);
+                float* ps = sScr + (warp * 2) * hp + m;
+                ps[0] = __fadd_ru(ps[0], cu);
+                ps[hp] = __fadd_rd(ps[hp], cl);
+              }
             }
           }
         }
+      }
+    }
+    if (screen) {
+      // the box's items: row 0 plus the warps' partials in warp order; the
+      // stable ones get their case and interval, the others join the list
+      __syncthreads();
+      const int lane = tid & 31;
+      for (int m0 = 0; m0 < h_out; m0 += kWThreads) {
+        const int m = m0 + tid;
+        bool need = false;
+        if (m < h_out) {
+          float u = sC0[m], l = sC0[hp + m];
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            u = __fadd_ru(u, sScr[(w * 2) * hp + m]);
+            l = __fadd_rd(l, sScr[(w * 2 + 1) * hp + m]);
+          }
+          const int64_t it = b * h_out + m;
+          if (!(isfinite(l) && isfinite(u)) || (u > 0.0f && l < 0.0f)) {
+            need = true;
+          } else {
+            so.kind[it] = u <= 0.0f ? 0 : 1;
+            so.lo[it] = l;
+            so.hi[it] = u;
+          }
+        }
+        const unsigned msk = __ballot_sync(0xffffffffu, need);
+        int at = 0;
+        if (lane == 0 && msk) at = atomicAdd(so.count, __popc(msk));
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (need) so.list[at + __popc(msk & ((1u << lane) - 1u))] = (int)(b * h_out + m);
       }
     }
   }
@@ -480,7 +554,7 @@ static size_t short_smem(int h_out, int h_in) {
 static size_t wide_smem(int h_out, int h_in, int rows) {
   const size_t hp = (size_t)((h_out + 63) & ~63);
   return hp * h_in * sizeof(float) + (size_t)rows * (h_in + 1) * sizeof(float2) +
-         (size_t)h_in * sizeof(int);
+         (size_t)h_in * sizeof(int) + 10 * hp * sizeof(float);   // + the screen partials
 }
 
 // Narrow output layers (h_out <= 4, e.g. a network's output): one thread per
@@ -810,7 +884,8 @@ cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
                           const float* W, const float* b, const float* in_up,
                           const float* in_lo, int64_t in_ld, const int32_t* in_nterms,
                           float* out_up, float* out_lo, int64_t out_ld,
-                          int32_t* out_nterms) {
+                          int32_t* out_nterms, const ScreenOut* screen, bool* screened) {
+  if (screened) *screened = false;
   if (n_boxes == 0) return cudaSuccess;
   if (n_boxes > 0x7fffffff || (std::min(in_ld, out_ld) + 15) / 16 > 65535)
     return cudaErrorInvalidValue;
@@ -830,7 +905,11 @@ cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
     if (v == 0 || v == 2 || v == 3) {
       const int rows = v == 0 ? 64 : (v == 2 ? 32 : 16);
       const size_t wsmem = wide_smem(h_out, h_in, rows);
-      auto kern = v == 0 ? k_affine_wide<4, 4> : (v == 2 ? k_affine_wide<2, 6> : k_affine_wide<1, 8>);
+      auto kern = screen ? (v == 0 ? k_affine_wide<4, 4, true>
+                                   : (v == 2 ? k_affine_wide<2, 6, true> : k_affine_wide<1, 8, true>))
+                         : (v == 0 ? k_affine_wide<4, 4, false>
+                                   : (v == 2 ? k_affine_wide<2, 6, false>
+                                             : k_affine_wide<1, 8, false>));
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
       if (e != cudaSuccess) return e;
       const int max_sm = v == 0 ? 4 : (v == 2 ? 6 : 8);
@@ -839,9 +918,10 @@ cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
       const int64_t blocks = std::min<int64_t>(n_boxes, device_sms(L) * per_sm);
       kern<<<(unsigned)blocks, kWThreads, wsmem, L.stream>>>(
           n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld, in_nterms, out_up, out_lo, out_ld,
-          out_nterms, L.status);
+          out_nterms, screen ? *screen : ScreenOut{}, L.status);
       ++*L.launches;
       e = cudaGetLastError();
+      if (screen && screened) *screened = true;
     } else {
       e = launch_cfg<64, 32, 4, 2, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
                                        in_nterms, out_up, out_lo, out_ld, out_nterms);

@@ -389,6 +389,23 @@ cudaError_t launch_enclose_relu_screened(const Launch& L, const Tables& T,
                              hi, o);
 }
 
+cudaError_t launch_enclose_relu_listed(const Launch& L, const Tables& T,
+                                       const ComposeScratch& S, int64_t n_boxes, int h,
+                                       int order, int64_t budget, const float* pre_up,
+                                       const float* pre_lo, int64_t ld,
+                                       const int32_t* nterms, float* lo, float* hi,
+                                       const uint8_t* degrees, int global_d, int8_t* kind,
+                                       float* coef, float* eps) {
+  const int64_t n_items = n_boxes * h;
+  if (n_items == 0) return cudaSuccess;
+  if (n_items > S.qcap || n_items > 0x7fffffff) return cudaErrorInvalidValue;
+  EncloseOpts o{kind, coef, eps, degrees, global_d};
+  o.list = S.queue;
+  o.count = S.qcount;
+  return launch_enclose_impl(L, T, n_boxes, h, order, budget, pre_up, pre_lo, ld, nterms, lo,
+                             hi, o);
+}
+
 // ------------------------------------------------------------------ per-box orders
 struct OrderKeys {
   int8_t key[kMaxTableDegree + 1];   // order value -> list index, -1 if absent
