@@ -191,7 +191,7 @@ int bern_set_autotune(bern_ctx* ctx, int enable);
  * not fit shared memory) or "enclose"
  * (variants 0-2: 8, 4 or 2 items per block with a warp per polynomial; 3, 4:
  * a block of 128 or 320 threads per polynomial for shared-memory grids of
- * 1024 cells or more at orders 3-16, else as 2).  variant = -1 clears the
+ * 256 cells or more at orders 3-16, else as 2).  variant = -1 clears the
  * force.
  * Drops captured graphs.  Returns BERN_E_INVALID for an unknown kind or a
  * variant out of range. */

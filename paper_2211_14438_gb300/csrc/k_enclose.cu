@@ -122,11 +122,11 @@ static cudaError_t launch_enclose_impl(const Launch& L, const Tables& T, int64_t
   int G;
   const int lb = effective_order(T.n, order, budget, &G, L.ews != nullptr);
   if (lb > T.rscale_max || T.rscale[lb] == nullptr) return cudaErrorInvalidValue;
-  // Shared-memory grids of at least 1024 cells: a block per polynomial
+  // Shared-memory grids of at least 256 cells: a block per polynomial
   // (variants 3 and 4 of the enclosure tuner: 128 or 320 threads; 3 is the
   // default from kEncloseBlkGrid cells) or a warp per polynomial (variants
   // 0-2, items per block)
-  const bool blk_ok = G >= 1024 && G <= kEncloseGridMax && lb >= 3 && lb <= 16;
+  const bool blk_ok = G >= 256 && G <= kEncloseGridMax && lb >= 3 && lb <= 16;
   bool blk = false, blk_wide = false;
   TuneTimer tt;
   std::string key;
