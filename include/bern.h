@@ -380,7 +380,8 @@ int bern_relu_coeffs(bern_ctx* ctx, int64_t n_items, const float* lo,
  * (which must then hold the outputs) compose the block where it stands; every
  * kernel reads an item's inputs before writing its outputs, and identity
  * items keep their coefficients without a copy (bern_propagate composes its
- * hidden layers this way).  Other overlaps of pre and post are not allowed. */
+ * hidden layers this way); the kernels are then sized for inputs of up to
+ * pre_ld terms.  Other overlaps of pre and post are not allowed. */
 int bern_compose(bern_ctx* ctx, int n, int64_t n_boxes, int h, int degree_cap,
                  float prune_tau, const int8_t* kind, const float* coef,
                  const float* eps, const uint8_t* degrees, int global_d,

@@ -308,3 +308,66 @@ def test_compose_stable_cases(ctx):
     qu = qu.cpu().numpy().reshape(Mout, 3).T
     ql = ql.cpu().numpy().reshape(Mout, 3).T
     assert np.array_equal(qu[1, :M], pu[1]) and np.array_equal(ql[1, :M], pl[1])
+
+
+@pytest.mark.parametrize("n,D,d,cap,tau", [(3, 4, 2, 16, 0.0), (3, 8, 2, 16, 0.0),
+                                           (2, 4, 3, 16, 0.0), (3, 4, 2, 16, 1e-3),
+                                           (4, 4, 2, 8, 0.0), (2, 4, 1, 16, 0.0)])
+def test_compose_in_place_matches_separate_blocks(ctx, n, D, d, cap, tau):
+    """bern_compose in place (post block = pre block, the post stride) gives
+    the bits of the separate-block call, including identity items (whose
+    coefficients stay where they are) and zero items, on the row, Horner and
+    linear paths.  (In place the step entry point sizes its kernels by the
+    stride, so shapes whose pair-list inputs would not fit shared memory at
+    that stride are declined; bern_propagate passes the true capacity.)"""
+    rng = np.random.default_rng(2000 + 100 * n + 10 * D + d)
+    M = bern.num_monomials(n, D)
+    Mout = bern.num_monomials(n, min(max(d, 1) * D, cap))
+    h, B = 8, 3
+    items = h * B
+    base = rng.normal(0, 0.3, (items, M)).astype(np.float32)
+    gap = np.abs(rng.normal(0, 0.01, (items, M))).astype(np.float32)
+    pu, pl = base + gap, base - gap
+    mag = np.abs(pu).sum(1) + np.abs(pl).sum(1)
+    lo = (-mag - 0.1).astype(np.float32)
+    hi = (mag + 0.2).astype(np.float32)
+    # a dead and an identity item in every box
+    for b in range(B):
+        hi[b * h + 1] = -0.5
+        lo[b * h + 1] = -1.0
+        lo[b * h + 2] = 0.5
+        hi[b * h + 2] = 1.5
+    glo, ghi = dev(lo), dev(hi)
+    kind = torch.zeros(items, dtype=torch.int8, device="cuda")
+    coef = torch.zeros(items * bern.COEF_STRIDE, device="cuda")
+    eps = torch.zeros(items, device="cuda")
+    ctx.relu_coeffs(items, glo, ghi, None, d, kind, coef, eps)
+    nt = dev(np.full(items, M, np.int32))
+
+    def block(a, ld):
+        out = np.zeros((B, ld, h), np.float32)
+        out[:, :M, :] = a.reshape(B, h, M).transpose(0, 2, 1)
+        return dev(out.reshape(-1))
+
+    su, sl = block(pu, M), block(pl, M)
+    qu = torch.full((B * Mout * h,), np.nan, device="cuda")
+    ql = torch.full_like(qu, np.nan)
+    qn = torch.zeros(items, dtype=torch.int32, device="cuda")
+    ctx.compose(n, B, h, cap, tau, kind, coef, eps, None, d, glo, ghi, su, sl, M, nt, qu, ql, Mout,
+                qn)
+    iu, il = block(pu, Mout), block(pl, Mout)
+    qn2 = torch.zeros(items, dtype=torch.int32, device="cuda")
+    ctx.compose(n, B, h, cap, tau, kind, coef, eps, None, d, glo, ghi, iu, il, Mout, nt, iu, il,
+                Mout, qn2)
+    assert ctx.sync() == 0
+    qn, qn2 = qn.cpu().numpy(), qn2.cpu().numpy()
+    assert np.array_equal(qn, qn2)
+    a_u = qu.cpu().numpy().reshape(B, Mout, h)
+    a_l = ql.cpu().numpy().reshape(B, Mout, h)
+    b_u = iu.cpu().numpy().reshape(B, Mout, h)
+    b_l = il.cpu().numpy().reshape(B, Mout, h)
+    for b in range(B):
+        for m in range(h):
+            k = int(qn[b * h + m])
+            assert np.array_equal(a_u[b, :k, m], b_u[b, :k, m]), (b, m)
+            assert np.array_equal(a_l[b, :k, m], b_l[b, :k, m]), (b, m)
