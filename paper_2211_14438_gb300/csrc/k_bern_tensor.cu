@@ -339,7 +339,7 @@ cudaError_t launch_bernstein_affine(const Launch& L, int64_t n_boxes, int h_out,
                                     int32_t* nt_scratch) {
   if (n_boxes == 0) return cudaSuccess;
   if (n_boxes < 0 || G < 1 || !nt_scratch) return cudaErrorInvalidValue;
-  const int64_t nin = n_boxes * h_in, nout = n_boxes * h_out;
+  const int64_t nin = n_boxes * h_in;   // input counts first, output counts after them
   const unsigned fb = (unsigned)std::min<int64_t>((nin + 255) / 256, device_sms(L) * 8);
   k_fill_i32<<<fb, 256, 0, L.stream>>>(nt_scratch, nin, G);
   ++*L.launches;
@@ -350,7 +350,6 @@ cudaError_t launch_bernstein_affine(const Launch& L, int64_t n_boxes, int h_out,
   const unsigned bb = (unsigned)std::min<int64_t>((total + 255) / 256, device_sms(L) * 8);
   k_bias_rows<<<bb, 256, 0, L.stream>>>(n_boxes, h_out, G, b, out_hi, out_lo);
   ++*L.launches;
-  (void)nout;
   return cudaGetLastError();
 }
 
