@@ -381,7 +381,8 @@ int bern_relu_coeffs(bern_ctx* ctx, int64_t n_items, const float* lo,
  * kernel reads an item's inputs before writing its outputs, and identity
  * items keep their coefficients without a copy (bern_propagate composes its
  * hidden layers this way); the kernels are then sized for inputs of up to
- * pre_ld terms.  Other overlaps of pre and post are not allowed. */
+ * pre_ld terms.  Other overlaps of pre and post are not allowed (a post
+ * pointer equal to a pre pointer otherwise returns BERN_E_INVALID). */
 int bern_compose(bern_ctx* ctx, int n, int64_t n_boxes, int h, int degree_cap,
                  float prune_tau, const int8_t* kind, const float* coef,
                  const float* eps, const uint8_t* degrees, int global_d,

@@ -1011,6 +1011,11 @@ int bern_compose(bern_ctx* c, int n, int64_t n_boxes, int h, int degree_cap, flo
       degree_cap < 1 || degree_cap > kMaxTableDegree || !(prune_tau >= 0.0f) ||
       global_d < 1 || global_d > kMaxOrder)
     return BERN_E_INVALID;
+  // in place is both bounds at one stride; any other aliasing is an error
+  const bool aliased = (const float*)post_up == pre_up || (const float*)post_lo == pre_lo;
+  if (aliased && !((const float*)post_up == pre_up && (const float*)post_lo == pre_lo &&
+                   post_ld == pre_ld))
+    return BERN_E_INVALID;
   cudaSetDevice(c->device);
   int Dmax = 0;
   while (Dmax < kMaxTableDegree && num_monomials(n, Dmax + 1) <= pre_ld) ++Dmax;

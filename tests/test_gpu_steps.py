@@ -371,3 +371,24 @@ def test_compose_in_place_matches_separate_blocks(ctx, n, D, d, cap, tau):
             k = int(qn[b * h + m])
             assert np.array_equal(a_u[b, :k, m], b_u[b, :k, m]), (b, m)
             assert np.array_equal(a_l[b, :k, m], b_l[b, :k, m]), (b, m)
+
+
+def test_compose_partial_alias_rejected(ctx):
+    """Aliasing only one bound, or in place at two strides, is BERN_E_INVALID."""
+    n, D = 2, 2
+    M = bern.num_monomials(n, D)
+    Mo = bern.num_monomials(n, 4)
+    z = torch.zeros(4 * Mo, device="cuda")
+    z2 = torch.zeros(4 * Mo, device="cuda")
+    kind = torch.zeros(4, dtype=torch.int8, device="cuda")
+    coef = torch.zeros(4 * bern.COEF_STRIDE, device="cuda")
+    f = torch.zeros(4, device="cuda")
+    nt = torch.full((4,), M, dtype=torch.int32, device="cuda")
+    qn = torch.zeros(4, dtype=torch.int32, device="cuda")
+    for pu, pl, qu, ql, pld, qld in ((z, z2, z, torch.zeros_like(z), Mo, Mo),
+                                     (z, z2, z, z2, M, Mo)):
+        with pytest.raises(bern.BernError) as ei:
+            ctx.compose(n, 1, 4, 16, 0.0, kind, coef, f, None, 2, f, f, pu, pl, pld, nt, qu, ql,
+                        qld, qn)
+        assert ei.value.code == bern.BERN_E_INVALID
+
