@@ -185,10 +185,11 @@ int bern_set_autotune(bern_ctx* ctx, int enable);
 
 /* Force one variant of a tunable kernel family for every later launch on
  * this context (a setting for tests and tuning; the paper has no
- * counterpart).  kind: "affine" (variants 0-3: persistent register-blocked
- * 8x4 thread tiles, 64x32 block tiles, persistent register-blocked 8x2 and
- * 8x1 thread tiles; 0, 2 and 3 fall back to 1 where the layer's weights do
- * not fit shared memory) or "enclose"
+ * counterpart).  kind: "affine" (variants 0-4: persistent register-blocked
+ * 8x4 thread tiles, block tiles, persistent register-blocked 8x2 and 8x1
+ * thread tiles, a warp per box for polynomials of at most 16 terms; 0, 2 and
+ * 3 fall back to 1 where the layer's weights do not fit shared memory, 4 to
+ * 2 for longer polynomials) or "enclose"
  * (variants 0-2: 8, 4 or 2 items per block with a warp per polynomial; 3, 4:
  * a block of 128 or 320 threads per polynomial for shared-memory grids of
  * 256 cells or more at orders 3-16, else as 2).  variant = -1 clears the

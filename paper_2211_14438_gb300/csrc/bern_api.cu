@@ -805,7 +805,7 @@ int bern_set_autotune(bern_ctx* c, int enable) {
 int bern_force_variant(bern_ctx* c, const char* kind, int variant) {
   if (!c || !kind) return BERN_E_INVALID;
   const std::string k(kind);
-  const int nvar = k == "affine" ? 4 : (k == "enclose" ? 5 : 0);
+  const int nvar = k == "affine" ? 5 : (k == "enclose" ? 5 : 0);
   if (nvar == 0 || variant < -1 || variant >= nvar) return BERN_E_INVALID;
   cudaStreamSynchronize(c->stream);
   for (auto& g : c->graphs)
@@ -1173,7 +1173,7 @@ int bern_propagate_traced(bern_ctx* c, const bern_net* net, const float* boxes,
       Chunk ch{(char*)c->ws.p, B};
       if ((rc = fill_degrees(c, P, ch, B))) return rc;
       const char* kinds[] = {"affine", "enclose"};
-      const int nvar[] = {4, 5};
+      const int nvar[] = {5, 5};
       for (int k = 0; k < 2; ++k) {
         for (int v = 0; v < nvar[k]; ++v) {
           c->tuner.probe_kind = kinds[k];

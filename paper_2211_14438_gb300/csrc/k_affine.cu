@@ -890,15 +890,19 @@ cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
   if (n_boxes > 0x7fffffff || (std::min(in_ld, out_ld) + 15) / 16 > 65535)
     return cudaErrorInvalidValue;
   const bool few_rows = std::min(in_ld, out_ld) <= 16;     // short polynomials: short tiles
-  if (h_out >= 32 && !few_rows) {
+  if (h_out >= 32) {
     // wide layers: autotuned among the persistent register-blocked kernel with
-    // 4-row (0), 2-row (2, the default) or 1-row (3) thread tiles, when its
-    // weights fit shared memory, and 64 x 32 block tiles (1)
+    // 4-row (0), 2-row (2, the default for longer polynomials) or 1-row (3)
+    // thread tiles, when its weights fit shared memory, block tiles (1), and
+    // for short polynomials a warp per box (4, their default)
     const std::string key = "affine/" + std::to_string(h_out) + "/" + std::to_string(h_in) +
                             "/" + std::to_string(in_ld) + "/" + std::to_string(n_boxes);
     const bool wide_ok = wide_smem(h_out, h_in, 64) <= 200 * 1024;
-    int v = tune_variant(L, "affine", key, wide_ok ? 2 : 1);
-    if (v != 1 && !wide_ok) v = 1;
+    const size_t ssmem = short_smem(h_out, h_in);
+    const bool short_ok = few_rows && ssmem <= 200 * 1024;
+    int v = tune_variant(L, "affine", key, short_ok ? 4 : (wide_ok ? 2 : 1));
+    if (v == 4 && !short_ok) v = wide_ok ? 2 : 1;
+    if (v != 1 && v != 4 && !wide_ok) v = short_ok ? 4 : 1;
     TuneTimer tt;
     tune_begin(L, "affine", tt);
     cudaError_t e;
@@ -922,19 +926,9 @@ cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
       ++*L.launches;
       e = cudaGetLastError();
       if (screen && screened) *screened = true;
-    } else {
-      e = launch_cfg<64, 32, 4, 2, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
-                                       in_nterms, out_up, out_lo, out_ld, out_nterms);
-    }
-    tune_end(L, "affine", key, tt);
-    return e;
-  }
-  if (h_out >= 32 && few_rows) {
-    // short polynomials: a warp per box where the weights fit shared memory
-    const size_t ssmem = short_smem(h_out, h_in);
-    if (ssmem <= 200 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(
-          k_affine_short, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem);
+    } else if (v == 4) {
+      e = cudaFuncSetAttribute(k_affine_short, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)ssmem);
       if (e != cudaSuccess) return e;
       const int per_sm = ssmem <= 54 * 1024 ? 4 : (ssmem <= 72 * 1024 ? 3 : (ssmem <= 110 * 1024 ? 2 : 1));
       const int64_t blocks = std::min<int64_t>((n_boxes + 3) / 4, device_sms(L) * per_sm);
@@ -942,10 +936,16 @@ cudaError_t launch_affine(const Launch& L, int64_t n_boxes, int h_out, int h_in,
           n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld, in_nterms, out_up, out_lo, out_ld,
           out_nterms, L.status);
       ++*L.launches;
-      return cudaGetLastError();
+      e = cudaGetLastError();
+    } else if (few_rows) {
+      e = launch_cfg<64, 16, 4, 1, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
+                                       in_nterms, out_up, out_lo, out_ld, out_nterms);
+    } else {
+      e = launch_cfg<64, 32, 4, 2, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
+                                       in_nterms, out_up, out_lo, out_ld, out_nterms);
     }
-    return launch_cfg<64, 16, 4, 1, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,
-                                        in_nterms, out_up, out_lo, out_ld, out_nterms);
+    tune_end(L, "affine", key, tt);
+    return e;
   }
   if (h_out > 8 && few_rows)
     return launch_cfg<16, 16, 2, 1, 32>(L, n_boxes, h_out, h_in, W, b, in_up, in_lo, in_ld,

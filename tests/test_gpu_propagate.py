@@ -297,7 +297,7 @@ def test_forced_variants_identical(ctx, widths, seed):
     boxes = wl.box_array(c - s / 2, c + s / 2)
     ref = None
     try:
-        for kind, nv in (("affine", 4), ("enclose", 5)):
+        for kind, nv in (("affine", 5), ("enclose", 5)):
             for v in range(nv):
                 ctx.force_variant(kind, v)
                 g = run_gpu(ctx, net, boxes)
