@@ -3,10 +3,11 @@
 Workload: the batched plain method, ReLU MLP [3, 64, 64, 64, 64, 1] (seed 2),
 5120 boxes (the 16^3 grid of [-1,1]^3 plus 1024 random boxes with sides
 U(0.01,0.5)), Bernstein ReLU order 2, total-degree cap 16.  A step is one
-bern_propagate over all 5120 boxes (init, the first layer's affine step, then
-per hidden layer the enclosure of the pre-activations, the ReLU coefficients,
-the composition of the unstable neurons and the next affine step, and the
-output enclosure with copy-out), replayed as one CUDA graph.  The fused
+bern_propagate over all 5120 boxes (init, then per hidden layer the affine step
+with the stability screen, the enclosure of the undecided pre-activations with
+their ReLU coefficients, and the in-place composition of the unstable neurons;
+the output layer's affine step, its enclosure and copy-out), replayed as one
+CUDA graph.  The fused
 per-layer kernel (one launch per hidden layer) is timed beside it as an
 alternate path (--fused makes it the headline).  L2 is flushed (256 MB
 write) before every timed step, outside the timed interval; each step is
