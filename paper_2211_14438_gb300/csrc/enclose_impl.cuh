@@ -110,12 +110,28 @@ __device__ __forceinline__ int ipow(int R, int e) {
   return p;
 }
 
+// Lines of pass k whose prefix digit sum is <= D: C(D + k, k) prefixes times
+// R^(n-1-k) suffixes, for D <= R-1.  From four variables on the line tables
+// put those of D = R-1 first in each pass, so a loop over that many lines
+// (skipping prefix sums above the polynomial's degree) covers every line the
+// polynomial needs; below, the loops cover all lines.
+__device__ __forceinline__ int simplex_lines(int D, int k, int suffixes) {
+  if (D + k > kMaxEncloseOrder) {   // beyond the exact binomial table
+    int c = 1;
+    for (int i = 1; i <= k; ++i) c = c * (D + i) / i;
+    return c * suffixes;
+  }
+  return (int)binomf(D + k, k) * suffixes;   // C(D + k, k), exact in float
+}
+
 // Total degree of a graded prefix of nt terms (the smallest D with M(n,D) >= nt).
 __device__ __forceinline__ int prefix_degree(const Tables& T, int nt) {
   return nt <= T.mexps ? (int)T.deg_of[nt] : kMaxTableDegree;
 }
 
-template <int LB, bool UP, bool PERM = false>
+// SIMP: loop over the in-simplex prefix of each pass (tables of four or more
+// variables, see simplex_lines); otherwise over all lines.
+template <int LB, bool UP, bool PERM = false, bool SIMP = false>
 __device__ float enclose_warp(const float* __restrict__ P, int ps, int nt, int n,
                               const Tables& T, const float2* __restrict__ rs, float* grid,
                               const int32_t* __restrict__ pos = nullptr) {
@@ -132,7 +148,8 @@ __device__ float enclose_warp(const float* __restrict__ P, int ps, int nt, int n
     // lines along variable k: prefix digits (variables < k) untransformed,
     // suffix digits (variables > k) transformed
     const int sk = ipow(R, n - 1 - k);
-    for (int Ln = lane; Ln < nlines; Ln += 32) {
+    const int nl = SIMP ? simplex_lines(LB, k, sk) : nlines;
+    for (int Ln = lane; Ln < nl; Ln += 32) {
       const int2 ln = __ldg(lines + (int64_t)k * nlines + Ln);
       const int base = ln.x, psum = ln.y;
       if (psum > Deff) continue;
@@ -185,7 +202,7 @@ __device__ __forceinline__ int64_t map_item(const EncloseOpts& o, int64_t idx, i
 
 // Orders up to 6 fit 32 registers without spills: four 512-thread blocks per
 // SM (64 warps); higher orders keep three.
-template <int LB>
+template <int LB, bool SIMP>
 __global__ void __launch_bounds__(512, (LB <= 6 ? 4 : 3))
 k_enclose(Tables T, int G, const float2* __restrict__ rs, int64_t n_items, int h,
           const float* __restrict__ pre_up, const float* __restrict__ pre_lo, int64_t ld,
@@ -206,8 +223,8 @@ k_enclose(Tables T, int G, const float2* __restrict__ rs, int64_t n_items, int h
     const int64_t b = item / h;
     const int64_t base = (b * ld) * h + (item - b * h);
     float* grid = smem + warp * G;
-    const float v = up ? enclose_warp<LB, true>(pre_up + base, h, nt, T.n, T, rs, grid)
-                       : enclose_warp<LB, false>(pre_lo + base, h, nt, T.n, T, rs, grid);
+    const float v = up ? enclose_warp<LB, true, false, SIMP>(pre_up + base, h, nt, T.n, T, rs, grid)
+                       : enclose_warp<LB, false, false, SIMP>(pre_lo + base, h, nt, T.n, T, rs, grid);
     if (lane == 0) {
       (up ? hi : lo)[item] = v;
       s_lohi[warp >> 1][up ? 1 : 0] = v;
@@ -243,15 +260,19 @@ cudaError_t launch_lb(const Launch& L, const Tables& T, int G, int64_t n_items, 
   TuneTimer tt;
   tune_begin(L, "enclose", tt);
   const size_t smem = (size_t)2 * items * G * sizeof(float);
+  // the in-simplex prefix loop for four or more variables (their grids of
+  // l >= 12, 13^4 cells and more, exceed kEncloseGridMax and run elsewhere)
+  auto kern = k_enclose<LB, false>;
+  if constexpr (LB <= 11)
+    if (T.n >= 4) kern = k_enclose<LB, true>;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_enclose<LB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
   }
   const unsigned blocks = (unsigned)((n_items + items - 1) / items);
-  k_enclose<LB><<<blocks, 64 * items, smem, L.stream>>>(T, G, T.rscale[LB], n_items, h, pre_up,
-                                                        pre_lo, ld, nterms, lo, hi, ro,
-                                                        L.status);
+  kern<<<blocks, 64 * items, smem, L.stream>>>(T, G, T.rscale[LB], n_items, h, pre_up, pre_lo,
+                                               ld, nterms, lo, hi, ro, L.status);
   ++*L.launches;
   const cudaError_t e = cudaGetLastError();
   tune_end(L, "enclose", key, tt);
@@ -287,7 +308,8 @@ __device__ float enclose_lane(const float* __restrict__ P, int ps, int nt, int n
   const int nlines = ipow(R, n - 1);
   for (int k = n - 1; k >= 0; --k) {
     const int sk = ipow(R, n - 1 - k);
-    for (int Ln = 0; Ln < nlines; ++Ln) {
+    const int nl = n >= 4 ? simplex_lines(LB, k, sk) : nlines;
+    for (int Ln = 0; Ln < nl; ++Ln) {
       const int2 ln = __ldg(lines + (int64_t)k * nlines + Ln);
       const int base = ln.x, psum = ln.y;
       if (psum > Deff) continue;
@@ -385,7 +407,8 @@ __device__ float enclose_warp_generic(const float* __restrict__ P, int ps, int n
   const int2* __restrict__ lines = T.lines[lb];
   for (int k = n - 1; k >= 0; --k) {
     const int sk = ipow(R, n - 1 - k);
-    for (int Ln = lane; Ln < nlines; Ln += 32) {
+    const int nl = n >= 4 ? simplex_lines(lb, k, sk) : nlines;
+    for (int Ln = lane; Ln < nl; Ln += 32) {
       const int2 ln = __ldg(lines + (int64_t)k * nlines + Ln);
       const int base = ln.x, psum = ln.y;
       if (psum > Deff) continue;

@@ -336,6 +336,23 @@ void build_enclose_tables(int n, int l, std::vector<int32_t>& gidx, std::vector<
       lines[(size_t)(2 * (k * nlines + Ln))] = (int32_t)base;
       lines[(size_t)(2 * (k * nlines + Ln)) + 1] = psum;
     }
+  // within a pass the lines are independent: from four variables on (where
+  // the simplex is a small part of the grid) the lines whose prefix digit
+  // sum is <= l (all a polynomial of degree <= l can need) come first, the
+  // first C(l + k, k) * (l+1)^(n-1-k) of pass k, each group in its natural
+  // order (neighbouring lanes keep neighbouring grid offsets)
+  if (n < 4) return;
+  std::vector<std::pair<int32_t, int32_t>> tmp((size_t)nlines);
+  for (int k = 0; k < n; ++k) {
+    int32_t* pl = &lines[(size_t)(2 * k * nlines)];
+    for (int64_t Ln = 0; Ln < nlines; ++Ln) tmp[(size_t)Ln] = {pl[2 * Ln + 1], pl[2 * Ln]};
+    std::stable_partition(tmp.begin(), tmp.end(),
+                          [l](const std::pair<int32_t, int32_t>& a) { return a.first <= l; });
+    for (int64_t Ln = 0; Ln < nlines; ++Ln) {
+      pl[2 * Ln] = tmp[(size_t)Ln].second;
+      pl[2 * Ln + 1] = tmp[(size_t)Ln].first;
+    }
+  }
 }
 
 }  // namespace bern
