@@ -109,6 +109,7 @@ __device__ __forceinline__ int ipow(int R, int e) {
   for (int i = 0; i < e; ++i) p *= R;
   return p;
 }
+constexpr int cipow(int R, int e) { return e == 0 ? 1 : R * cipow(R, e - 1); }
 
 // Lines of pass k whose prefix digit sum is <= D: C(D + k, k) prefixes times
 // R^(n-1-k) suffixes, for D <= R-1.  From four variables on the line tables
@@ -129,52 +130,74 @@ __device__ __forceinline__ int prefix_degree(const Tables& T, int nt) {
   return nt <= T.mexps ? (int)T.deg_of[nt] : kMaxTableDegree;
 }
 
+// One pass of the warp enclosure: the lines along variable k (prefix digits,
+// variables < k, untransformed; suffix digits, variables > k, transformed),
+// sk the stride of variable k, nl the lines looped over, nlines the lines of
+// a pass in the table.  The last pass (k == 0) takes the extreme into best.
+template <int LB, bool UP>
+__device__ __forceinline__ void enclose_pass(int k, int sk, int nl, int nlines,
+                                             const int2* __restrict__ lines, int Deff,
+                                             float* grid, float& best) {
+  constexpr int R = LB + 1;
+  const int lane = threadIdx.x & 31;
+  for (int Ln = lane; Ln < nl; Ln += 32) {
+    const int2 ln = __ldg(lines + (int64_t)k * nlines + Ln);
+    const int base = ln.x, psum = ln.y;
+    if (psum > Deff) continue;
+    const int p = Deff - psum;
+    float x[R], y[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) x[j] = j <= p ? grid[base + j * sk] : 0.0f;
+    // in place up to order 8 (fewer live registers); above, the separate
+    // output array schedules better (measured)
+    if constexpr (LB <= 8) {
+      line_transform_inplace<LB, UP>(x);
+#pragma unroll
+      for (int i = 0; i < R; ++i) y[i] = x[i];
+    } else {
+      line_transform<LB, UP>(x, y);
+    }
+    if (k > 0) {
+#pragma unroll
+      for (int i = 0; i < R; ++i) grid[base + i * sk] = y[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < R; ++i) best = UP ? fmaxf(best, y[i]) : fminf(best, y[i]);
+    }
+  }
+}
+
 // SIMP: loop over the in-simplex prefix of each pass (tables of four or more
-// variables, see simplex_lines); otherwise over all lines.
-template <int LB, bool UP, bool PERM = false, bool SIMP = false>
+// variables, see simplex_lines); otherwise over all lines.  NV > 0: the
+// variable count is NV at compile time (n == NV), so the passes unroll and
+// the line strides become immediate offsets.
+template <int LB, bool UP, bool PERM = false, bool SIMP = false, int NV = 0>
 __device__ float enclose_warp(const float* __restrict__ P, int ps, int nt, int n,
                               const Tables& T, const float2* __restrict__ rs, float* grid,
                               const int32_t* __restrict__ pos = nullptr) {
-  const int lane = threadIdx.x & 31;
   constexpr int R = LB + 1;
   const int Dnt = prefix_degree(T, nt);
   const int Deff = Dnt < LB ? Dnt : LB;
   float rem = scatter_terms<UP, PERM>(P, ps, nt, T.gidx[LB], rs, T.mcount[Deff], grid, pos);
   __syncwarp();
   float best = UP ? -CUDART_INF_F : CUDART_INF_F;
-  const int nlines = ipow(R, n - 1);
   const int2* __restrict__ lines = T.lines[LB];
-  for (int k = n - 1; k >= 0; --k) {
-    // lines along variable k: prefix digits (variables < k) untransformed,
-    // suffix digits (variables > k) transformed
-    const int sk = ipow(R, n - 1 - k);
-    const int nl = SIMP ? simplex_lines(LB, k, sk) : nlines;
-    for (int Ln = lane; Ln < nl; Ln += 32) {
-      const int2 ln = __ldg(lines + (int64_t)k * nlines + Ln);
-      const int base = ln.x, psum = ln.y;
-      if (psum > Deff) continue;
-      const int p = Deff - psum;
-      float x[R], y[R];
+  if constexpr (NV > 0) {
+    constexpr int nlines = cipow(R, NV - 1);
 #pragma unroll
-      for (int j = 0; j < R; ++j) x[j] = j <= p ? grid[base + j * sk] : 0.0f;
-      // in place up to order 8 (fewer live registers); above, the separate
-      // output array schedules better (measured)
-      if constexpr (LB <= 8) {
-        line_transform_inplace<LB, UP>(x);
-#pragma unroll
-        for (int i = 0; i < R; ++i) y[i] = x[i];
-      } else {
-        line_transform<LB, UP>(x, y);
-      }
-      if (k > 0) {
-#pragma unroll
-        for (int i = 0; i < R; ++i) grid[base + i * sk] = y[i];
-      } else {
-#pragma unroll
-        for (int i = 0; i < R; ++i) best = UP ? fmaxf(best, y[i]) : fminf(best, y[i]);
-      }
+    for (int k = NV - 1; k >= 0; --k) {
+      const int sk = cipow(R, NV - 1 - k);
+      enclose_pass<LB, UP>(k, sk, nlines, nlines, lines, Deff, grid, best);
+      __syncwarp();
     }
-    __syncwarp();
+  } else {
+    const int nlines = ipow(R, n - 1);
+    for (int k = n - 1; k >= 0; --k) {
+      const int sk = ipow(R, n - 1 - k);
+      const int nl = SIMP ? simplex_lines(LB, k, sk) : nlines;
+      enclose_pass<LB, UP>(k, sk, nl, nlines, lines, Deff, grid, best);
+      __syncwarp();
+    }
   }
   best = UP ? warp_max(best) : warp_min(best);
   rem = warp_dsum<UP>(rem);
@@ -202,7 +225,8 @@ __device__ __forceinline__ int64_t map_item(const EncloseOpts& o, int64_t idx, i
 
 // Orders up to 6 fit 32 registers without spills: four 512-thread blocks per
 // SM (64 warps); higher orders keep three.
-template <int LB, bool SIMP>
+// SIMP as in enclose_warp; NV > 0: compiled for NV variables
+template <int LB, bool SIMP, int NV>
 __global__ void __launch_bounds__(512, (LB <= 6 ? 4 : 3))
 k_enclose(Tables T, int G, const float2* __restrict__ rs, int64_t n_items, int h,
           const float* __restrict__ pre_up, const float* __restrict__ pre_lo, int64_t ld,
@@ -223,8 +247,9 @@ k_enclose(Tables T, int G, const float2* __restrict__ rs, int64_t n_items, int h
     const int64_t b = item / h;
     const int64_t base = (b * ld) * h + (item - b * h);
     float* grid = smem + warp * G;
-    const float v = up ? enclose_warp<LB, true, false, SIMP>(pre_up + base, h, nt, T.n, T, rs, grid)
-                       : enclose_warp<LB, false, false, SIMP>(pre_lo + base, h, nt, T.n, T, rs, grid);
+    const float v =
+        up ? enclose_warp<LB, true, false, SIMP, NV>(pre_up + base, h, nt, T.n, T, rs, grid)
+           : enclose_warp<LB, false, false, SIMP, NV>(pre_lo + base, h, nt, T.n, T, rs, grid);
     if (lane == 0) {
       (up ? hi : lo)[item] = v;
       s_lohi[warp >> 1][up ? 1 : 0] = v;
@@ -262,9 +287,11 @@ cudaError_t launch_lb(const Launch& L, const Tables& T, int G, int64_t n_items, 
   const size_t smem = (size_t)2 * items * G * sizeof(float);
   // the in-simplex prefix loop for four or more variables (their grids of
   // l >= 12, 13^4 cells and more, exceed kEncloseGridMax and run elsewhere)
-  auto kern = k_enclose<LB, false>;
+  auto kern = k_enclose<LB, false, 0>;
+  if constexpr (LB >= 4)   // three-variable grids of l <= 3 take the small-grid kernel
+    if (T.n == 3) kern = k_enclose<LB, false, 3>;
   if constexpr (LB <= 11)
-    if (T.n >= 4) kern = k_enclose<LB, true>;
+    if (T.n >= 4) kern = k_enclose<LB, true, 0>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
