@@ -134,15 +134,26 @@ __device__ __forceinline__ int prefix_degree(const Tables& T, int nt) {
 // variables < k, untransformed; suffix digits, variables > k, transformed),
 // sk the stride of variable k, nl the lines looped over, nlines the lines of
 // a pass in the table.  The last pass (k == 0) takes the extreme into best.
-template <int LB, bool UP>
+// NV == 3: the line's base and prefix sum follow from Ln (the line tables'
+// order: the low digit of Ln is the highest variable other than k) instead of
+// a table load.
+template <int LB, bool UP, int NV = 0>
 __device__ __forceinline__ void enclose_pass(int k, int sk, int nl, int nlines,
                                              const int2* __restrict__ lines, int Deff,
                                              float* grid, float& best) {
   constexpr int R = LB + 1;
   const int lane = threadIdx.x & 31;
   for (int Ln = lane; Ln < nl; Ln += 32) {
-    const int2 ln = __ldg(lines + (int64_t)k * nlines + Ln);
-    const int base = ln.x, psum = ln.y;
+    int base, psum;
+    if constexpr (NV == 3) {
+      const int q = Ln / R, r = Ln - q * R;
+      base = k == 2 ? Ln * R : k == 1 ? q * (R * R) + r : Ln;
+      psum = k == 2 ? q + r : k == 1 ? q : 0;
+    } else {
+      const int2 ln = __ldg(lines + (int64_t)k * nlines + Ln);
+      base = ln.x;
+      psum = ln.y;
+    }
     if (psum > Deff) continue;
     const int p = Deff - psum;
     float x[R], y[R];
@@ -175,6 +186,7 @@ template <int LB, bool UP, bool PERM = false, bool SIMP = false, int NV = 0>
 __device__ float enclose_warp(const float* __restrict__ P, int ps, int nt, int n,
                               const Tables& T, const float2* __restrict__ rs, float* grid,
                               const int32_t* __restrict__ pos = nullptr) {
+  static_assert(NV == 0 || NV == 3, "compiled variable counts");
   constexpr int R = LB + 1;
   const int Dnt = prefix_degree(T, nt);
   const int Deff = Dnt < LB ? Dnt : LB;
@@ -187,7 +199,7 @@ __device__ float enclose_warp(const float* __restrict__ P, int ps, int nt, int n
 #pragma unroll
     for (int k = NV - 1; k >= 0; --k) {
       const int sk = cipow(R, NV - 1 - k);
-      enclose_pass<LB, UP>(k, sk, nlines, nlines, lines, Deff, grid, best);
+      enclose_pass<LB, UP, NV>(k, sk, nlines, nlines, lines, Deff, grid, best);
       __syncwarp();
     }
   } else {
