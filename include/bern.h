@@ -240,6 +240,24 @@ int64_t bern_num_monomials(int n, int D);
 /* Host array exps[M(n,D) x n] of the graded order described above. */
 int bern_monomials(int n, int D, uint8_t* exps);
 
+/* The enclosure's line table for order l (Sec. 5.1 Step 1 with Def. 2: the
+ * Bernstein coefficients on the grid {0..l}^n follow from one triangular
+ * transform per variable along every grid line of that variable), as the
+ * shared-memory enclosure kernels use it.  Cell (d_0 .. d_{n-1}) has grid
+ * index sum_k d_k (l+1)^(n-1-k).  For each variable k, (l+1)^(n-1) lines of
+ * two int32 each: the grid index of the line's first cell (d_k = 0) and the
+ * digit sum of the variables before k; pass k starts at out[2 k (l+1)^(n-1)].
+ * Within a pass the lines are in the order of the other variables' digits
+ * read as one number whose lowest digit is the highest variable; from n = 4
+ * on, the C(l+k, k) (l+1)^(n-1-k) lines of prefix sum <= l come first and
+ * the rest after them, each part in that order.  (The three-variable kernels
+ * compute these entries from the line index instead of loading them.)
+ *   out: host array of at least cap int32 (2 n (l+1)^(n-1) are written).
+ * Host only; no GPU needed.  Returns BERN_OK; BERN_E_INVALID (out NULL, n
+ * outside [1, 8], l < 0, or cap too small); BERN_E_UNSUPPORTED for grids
+ * above 2^22 cells. */
+int bern_enclose_lines(int n, int l, int32_t* out, int64_t cap);
+
 /* ------------------------------------------------------------ hot path */
 
 /* Whole path, Sec. 5.3: input init, then per layer the affine step

@@ -59,6 +59,7 @@ EXPORTS = [
     "bern_bernstein_square",
     "bern_bernstein_elevate",
     "bern_bernstein_affine",
+    "bern_enclose_lines",
 ]
 
 
@@ -133,6 +134,7 @@ def load(build_if_missing: bool = True):
         "bern_fma_throughput": (I, [I, V, I, I, ctypes.POINTER(ctypes.c_double)]),
         "bern_num_monomials": (I64, [I, I]),
         "bern_monomials": (I, [I, I, V]),
+        "bern_enclose_lines": (I, [I, I, V, I64]),
         "bern_propagate": (I, [V, ctypes.POINTER(bern_net), V, I64,
                                ctypes.POINTER(bern_degree_plan), ctypes.POINTER(bern_result)]),
         "bern_init_inputs": (I, [V, I, I64, V, V, V, I64, V]),
@@ -195,6 +197,16 @@ def monomials(n: int, D: int) -> np.ndarray:
     m = num_monomials(n, D)
     out = np.zeros((m, n), np.uint8)
     _check(load().bern_monomials(n, D, out.ctypes.data), "bern_monomials")
+    return out
+
+
+def enclose_lines(n: int, l: int) -> np.ndarray:
+    """The enclosure's line table for order l (bern_enclose_lines): array
+    [n, (l+1)^(n-1), 2] of (grid index of the line's first cell, digit sum of
+    the variables before the line's variable)."""
+    nl = (l + 1) ** (n - 1)
+    out = np.zeros((n, nl, 2), np.int32)
+    _check(load().bern_enclose_lines(n, l, out.ctypes.data, out.size), "bern_enclose_lines")
     return out
 
 

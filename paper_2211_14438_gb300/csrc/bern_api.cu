@@ -920,6 +920,22 @@ int bern_monomials(int n, int D, uint8_t* exps) {
   return BERN_OK;
 }
 
+int bern_enclose_lines(int n, int l, int32_t* out, int64_t cap) {
+  if (!out || n < 1 || n > kMaxVars || l < 0) return BERN_E_INVALID;
+  int64_t cells = 1;
+  for (int k = 0; k < n; ++k) {
+    cells *= (int64_t)l + 1;
+    if (cells > ((int64_t)1 << 22)) return BERN_E_UNSUPPORTED;
+  }
+  const int64_t need = 2 * (int64_t)n * (cells / (l + 1));
+  if (cap < need) return BERN_E_INVALID;
+  std::vector<int32_t> gi, li;
+  build_enclose_tables(n, l, gi, li, true);
+  if ((int64_t)li.size() != need) return BERN_E_INVALID;
+  std::memcpy(out, li.data(), li.size() * sizeof(int32_t));
+  return BERN_OK;
+}
+
 int bern_init_inputs(bern_ctx* c, int n, int64_t n_boxes, const float* boxes, float* z_up,
                      float* z_lo, int64_t ld, int32_t* nterms) {
   if (!c || n < 1 || n > kMaxVars || n_boxes < 0 || ld < n + 1) return BERN_E_INVALID;

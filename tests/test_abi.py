@@ -61,3 +61,86 @@ def test_graded_order(n, D):
         assert bern.num_monomials(n, g) == int((deg <= g).sum())
     # degree-1 block is t_1, ..., t_n in order
     assert [tuple(r) for r in ex[1:n + 1]] == [tuple(np.eye(n, dtype=int)[i]) for i in range(n)]
+
+
+# ------------------------------------------------------------ enclosure line tables
+def _digits(idx, n, R):
+    """Digits (d_0 .. d_{n-1}) of a grid index, variable 0 the slowest."""
+    d = []
+    for _ in range(n):
+        d.append(idx % R)
+        idx //= R
+    return d[::-1]
+
+
+def _natural_index(d, k, R):
+    """A line's place in the natural order: the digits of the variables other
+    than k read as one number whose lowest digit is the highest variable."""
+    idx, w = 0, 1
+    for mm in range(len(d) - 1, -1, -1):
+        if mm == k:
+            continue
+        idx += d[mm] * w
+        w *= R
+    return idx
+
+
+@pytest.mark.parametrize("n,l", [(1, 5), (2, 4), (3, 0), (3, 4), (3, 8), (3, 16), (4, 3),
+                                 (4, 6), (5, 3), (6, 2), (6, 4), (8, 2)])
+def test_enclose_lines_cover_every_line_once(n, l):
+    # Def. 2's per-variable transform runs along every line of the grid once:
+    # pass k holds each cell with d_k = 0 once, with the digit sum of the
+    # variables before k
+    R = l + 1
+    t = bern.enclose_lines(n, l)
+    assert t.shape == (n, R ** (n - 1), 2)
+    for k in range(n):
+        bases = t[k, :, 0].tolist()
+        want = {i for i in range(R ** n) if _digits(i, n, R)[k] == 0}
+        assert len(bases) == len(want) and set(bases) == want
+        for base, psum in t[k].tolist():
+            assert psum == sum(_digits(base, n, R)[:k])
+
+
+@pytest.mark.parametrize("l", [0, 1, 2, 4, 7, 8, 11, 16])
+def test_enclose_lines_three_variables_match_the_kernel_formulas(l):
+    # the three-variable enclosure kernels compute a line's entries from its
+    # index Ln instead of loading them; they must equal the table's
+    R = l + 1
+    t = bern.enclose_lines(3, l)
+    for Ln in range(R * R):
+        q, r = divmod(Ln, R)
+        assert tuple(t[2, Ln]) == (Ln * R, q + r)
+        assert tuple(t[1, Ln]) == (q * R * R + r, q)
+        assert tuple(t[0, Ln]) == (Ln, 0)
+
+
+@pytest.mark.parametrize("n,l", [(1, 6), (2, 5), (3, 6), (4, 2), (4, 5), (5, 3), (6, 2),
+                                 (6, 4), (7, 2), (8, 2)])
+def test_enclose_lines_order(n, l):
+    # below four variables: natural order; from four on, the lines of prefix
+    # sum <= l (C(l+k, k) (l+1)^(n-1-k) of them, the loop bound of the
+    # kernels there) first, then the rest, each part in natural order
+    R = l + 1
+    t = bern.enclose_lines(n, l)
+    for k in range(n):
+        nat = [_natural_index(_digits(b, n, R), k, R) for b in t[k, :, 0].tolist()]
+        psum = t[k, :, 1]
+        if n < 4:
+            assert nat == list(range(R ** (n - 1)))
+            continue
+        cnt = math.comb(l + k, k) * R ** (n - 1 - k)
+        assert np.all(psum[:cnt] <= l) and np.all(psum[cnt:] > l)
+        assert nat[:cnt] == sorted(nat[:cnt]) and nat[cnt:] == sorted(nat[cnt:])
+
+
+def test_enclose_lines_rejects_bad_arguments():
+    lib = bern.load()
+    buf = np.zeros(64, np.int32)
+    assert lib.bern_enclose_lines(3, 2, None, 64) == 1             # BERN_E_INVALID
+    assert lib.bern_enclose_lines(0, 2, buf.ctypes.data, 64) == 1
+    assert lib.bern_enclose_lines(9, 2, buf.ctypes.data, 64) == 1
+    assert lib.bern_enclose_lines(3, -1, buf.ctypes.data, 64) == 1
+    assert lib.bern_enclose_lines(3, 4, buf.ctypes.data, 64) == 1   # needs 2*3*25 = 150
+    assert lib.bern_enclose_lines(3, 2, buf.ctypes.data, 64) == 0   # 2*3*9 = 54 fit
+    assert lib.bern_enclose_lines(2, (1 << 11) + 1, buf.ctypes.data, 64) == 6   # > 2^22 cells
