@@ -258,6 +258,17 @@ int bern_monomials(int n, int D, uint8_t* exps);
  * above 2^22 cells. */
 int bern_enclose_lines(int n, int l, int32_t* out, int64_t cap);
 
+/* The enclosure's reciprocal brackets for order l (Def. 2: the coefficient a_J
+ * enters the Bernstein grid divided by prod_k C(l, j_k)): for each monomial J
+ * of degree <= l in the graded order, two floats lo <= 1 / prod_k C(l, j_k)
+ * <= hi (equal when the product is a power of two, else the two floats
+ * next to the nearest one), which the kernels multiply with the rounding
+ * direction of the bound.
+ *   out: host array of at least cap floats (2 M(n, l) are written).
+ * Host only; no GPU needed.  Returns BERN_OK; BERN_E_INVALID (out NULL, n
+ * outside [1, 8], l outside [0, BERN_MAX_ENCLOSE_ORDER], or cap too small). */
+int bern_enclose_scales(int n, int l, float* out, int64_t cap);
+
 /* ------------------------------------------------------------ hot path */
 
 /* Whole path, Sec. 5.3: input init, then per layer the affine step

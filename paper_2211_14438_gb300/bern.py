@@ -60,6 +60,7 @@ EXPORTS = [
     "bern_bernstein_elevate",
     "bern_bernstein_affine",
     "bern_enclose_lines",
+    "bern_enclose_scales",
 ]
 
 
@@ -135,6 +136,7 @@ def load(build_if_missing: bool = True):
         "bern_num_monomials": (I64, [I, I]),
         "bern_monomials": (I, [I, I, V]),
         "bern_enclose_lines": (I, [I, I, V, I64]),
+        "bern_enclose_scales": (I, [I, I, V, I64]),
         "bern_propagate": (I, [V, ctypes.POINTER(bern_net), V, I64,
                                ctypes.POINTER(bern_degree_plan), ctypes.POINTER(bern_result)]),
         "bern_init_inputs": (I, [V, I, I64, V, V, V, I64, V]),
@@ -207,6 +209,15 @@ def enclose_lines(n: int, l: int) -> np.ndarray:
     nl = (l + 1) ** (n - 1)
     out = np.zeros((n, nl, 2), np.int32)
     _check(load().bern_enclose_lines(n, l, out.ctypes.data, out.size), "bern_enclose_lines")
+    return out
+
+
+def enclose_scales(n: int, l: int) -> np.ndarray:
+    """The enclosure's reciprocal brackets for order l (bern_enclose_scales):
+    array [M(n,l), 2] of float32 (lo, hi) around 1 / prod_k C(l, j_k), in the
+    graded order."""
+    out = np.zeros((num_monomials(n, l), 2), np.float32)
+    _check(load().bern_enclose_scales(n, l, out.ctypes.data, out.size), "bern_enclose_scales")
     return out
 
 

@@ -936,6 +936,15 @@ int bern_enclose_lines(int n, int l, int32_t* out, int64_t cap) {
   return BERN_OK;
 }
 
+int bern_enclose_scales(int n, int l, float* out, int64_t cap) {
+  if (!out || n < 1 || n > kMaxVars || l < 0 || l > kMaxEncloseOrder) return BERN_E_INVALID;
+  if (cap < 2 * num_monomials(n, l)) return BERN_E_INVALID;
+  std::vector<float> rs;
+  build_rscale(n, l, rs);
+  std::memcpy(out, rs.data(), rs.size() * sizeof(float));
+  return BERN_OK;
+}
+
 int bern_init_inputs(bern_ctx* c, int n, int64_t n_boxes, const float* boxes, float* z_up,
                      float* z_lo, int64_t ld, int32_t* nterms) {
   if (!c || n < 1 || n > kMaxVars || n_boxes < 0 || ld < n + 1) return BERN_E_INVALID;

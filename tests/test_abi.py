@@ -144,3 +144,37 @@ def test_enclose_lines_rejects_bad_arguments():
     assert lib.bern_enclose_lines(3, 4, buf.ctypes.data, 64) == 1   # needs 2*3*25 = 150
     assert lib.bern_enclose_lines(3, 2, buf.ctypes.data, 64) == 0   # 2*3*9 = 54 fit
     assert lib.bern_enclose_lines(2, (1 << 11) + 1, buf.ctypes.data, 64) == 6   # > 2^22 cells
+
+
+@pytest.mark.parametrize("n,l", [(1, 0), (1, 16), (1, 24), (2, 8), (3, 4), (3, 8), (3, 16),
+                                 (4, 6), (6, 4), (8, 2)])
+def test_enclose_scales_bracket_the_reciprocals(n, l):
+    # Def. 2 divides a_J by prod_k C(l, j_k); the kernels multiply by a float
+    # bracket of the reciprocal, so each pair must contain it exactly and be
+    # tight (one float when the product is a power of two, else two ulps wide)
+    from fractions import Fraction
+    sc = bern.enclose_scales(n, l).astype(np.float64)
+    ex = bern.monomials(n, l).astype(int)
+    assert sc.shape == (len(ex), 2)
+    for (lo, hi), J in zip(sc, ex):
+        c = 1
+        for j in J:
+            c *= math.comb(l, int(j))
+        exact = Fraction(1, c)
+        assert Fraction(lo) <= exact <= Fraction(hi)
+        if c & (c - 1) == 0:
+            assert lo == hi == float(exact)
+        else:
+            assert Fraction(lo) < exact < Fraction(hi)
+            one = np.float32(1)
+            assert np.nextafter(np.nextafter(np.float32(lo), one), one) == np.float32(hi)
+
+
+def test_enclose_scales_rejects_bad_arguments():
+    lib = bern.load()
+    buf = np.zeros(64, np.float32)
+    assert lib.bern_enclose_scales(3, 2, None, 64) == 1
+    assert lib.bern_enclose_scales(0, 2, buf.ctypes.data, 64) == 1
+    assert lib.bern_enclose_scales(3, 25, buf.ctypes.data, 64) == 1
+    assert lib.bern_enclose_scales(3, 4, buf.ctypes.data, 64) == 1    # needs 2 * 35 = 70
+    assert lib.bern_enclose_scales(3, 2, buf.ctypes.data, 64) == 0    # 2 * 10 = 20 fit
