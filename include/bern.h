@@ -269,6 +269,27 @@ int bern_enclose_lines(int n, int l, int32_t* out, int64_t cap);
  * outside [1, 8], l outside [0, BERN_MAX_ENCLOSE_ORDER], or cap too small). */
 int bern_enclose_scales(int n, int l, float* out, int64_t cap);
 
+/* The composition's row tables for input degree D (Sec. 5.1 Step 3 at ReLU
+ * order 2: s^2 is formed as sums of 1-D convolutions of the rows of s, a row
+ * being the monomials that share the exponents of t_1..t_{n-1}, laid out with
+ * the last exponent running), as the row-convolution kernel reads them.
+ *   sizes[5] receives m_in = M(n, D), the output rows, the row where the
+ *   second half of the work starts, the pairs and the output ranks.
+ *   out (NULL: sizes only) receives, concatenated, int32:
+ *     pos_in[m_in]     row-layout position of each graded input rank;
+ *     hdr[4 per row]   first pair, end of its pairs, first output rank,
+ *                      Lout | in_len << 8 | has_diag << 16 (row length of
+ *                      the square, of the row's own input row, and whether
+ *                      its last pair is a row with itself);
+ *     in_off[per row]  row-layout offset of the row's own input row, or -1;
+ *     pairs[4 per pair] offsets of the shorter and the longer row,
+ *                      L1 << 4 | L2 (L1 <= L2), the dispatch case;
+ *     out_ranks[...]   graded rank (degree <= 2D) of each output row element.
+ * Host only; no GPU needed.  Returns BERN_OK; BERN_E_INVALID (sizes NULL, n
+ * outside [1, 8], D outside [0, 8], or cap too small); BERN_E_UNSUPPORTED
+ * when the input has more than 750 terms (those use the pair-list kernel). */
+int bern_compose_rows(int n, int D, int32_t* out, int64_t cap, int64_t* sizes);
+
 /* ------------------------------------------------------------ hot path */
 
 /* Whole path, Sec. 5.3: input init, then per layer the affine step

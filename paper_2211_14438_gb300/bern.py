@@ -61,6 +61,7 @@ EXPORTS = [
     "bern_bernstein_affine",
     "bern_enclose_lines",
     "bern_enclose_scales",
+    "bern_compose_rows",
 ]
 
 
@@ -137,6 +138,7 @@ def load(build_if_missing: bool = True):
         "bern_monomials": (I, [I, I, V]),
         "bern_enclose_lines": (I, [I, I, V, I64]),
         "bern_enclose_scales": (I, [I, I, V, I64]),
+        "bern_compose_rows": (I, [I, I, V, I64, V]),
         "bern_propagate": (I, [V, ctypes.POINTER(bern_net), V, I64,
                                ctypes.POINTER(bern_degree_plan), ctypes.POINTER(bern_result)]),
         "bern_init_inputs": (I, [V, I, I64, V, V, V, I64, V]),
@@ -219,6 +221,23 @@ def enclose_scales(n: int, l: int) -> np.ndarray:
     out = np.zeros((num_monomials(n, l), 2), np.float32)
     _check(load().bern_enclose_scales(n, l, out.ctypes.data, out.size), "bern_enclose_scales")
     return out
+
+
+def compose_rows(n: int, D: int) -> dict:
+    """The composition's row tables for input degree D (bern_compose_rows):
+    pos_in [M], hdr [rows, 4], in_off [rows], pairs [n_pairs, 4], out_ranks,
+    and row_split."""
+    sizes = np.zeros(5, np.int64)
+    lib = load()
+    _check(lib.bern_compose_rows(n, D, None, 0, sizes.ctypes.data), "bern_compose_rows")
+    m_in, rows, split, npairs, nout = (int(v) for v in sizes)
+    out = np.zeros(m_in + 5 * rows + 4 * npairs + nout, np.int32)
+    _check(lib.bern_compose_rows(n, D, out.ctypes.data, out.size, sizes.ctypes.data),
+           "bern_compose_rows")
+    o = np.cumsum([0, m_in, 4 * rows, rows, 4 * npairs, nout])
+    return {"pos_in": out[o[0]:o[1]], "hdr": out[o[1]:o[2]].reshape(rows, 4),
+            "in_off": out[o[2]:o[3]], "pairs": out[o[3]:o[4]].reshape(npairs, 4),
+            "out_ranks": out[o[4]:o[5]], "row_split": split}
 
 
 def _ptr(t) -> int:

@@ -945,6 +945,29 @@ int bern_enclose_scales(int n, int l, float* out, int64_t cap) {
   return BERN_OK;
 }
 
+int bern_compose_rows(int n, int D, int32_t* out, int64_t cap, int64_t* sizes) {
+  if (!sizes || n < 1 || n > kMaxVars || D < 0 || D > kMaxRowDegree) return BERN_E_INVALID;
+  if (D > row_path_max_degree(n)) return BERN_E_UNSUPPORTED;
+  RowImage im;
+  if (!build_row_table(n, D, im)) return BERN_E_UNSUPPORTED;
+  sizes[0] = im.m_in;
+  sizes[1] = im.n_out_rows;
+  sizes[2] = im.row_split;
+  sizes[3] = (int64_t)im.pairs.size() / 4;
+  sizes[4] = (int64_t)im.out_ranks.size();
+  if (!out) return BERN_OK;
+  const std::vector<int32_t>* parts[] = {&im.pos_in, &im.hdr, &im.in_off, &im.pairs,
+                                         &im.out_ranks};
+  int64_t need = 0;
+  for (const auto* v : parts) need += (int64_t)v->size();
+  if (cap < need) return BERN_E_INVALID;
+  for (const auto* v : parts) {
+    std::memcpy(out, v->data(), v->size() * sizeof(int32_t));
+    out += v->size();
+  }
+  return BERN_OK;
+}
+
 int bern_init_inputs(bern_ctx* c, int n, int64_t n_boxes, const float* boxes, float* z_up,
                      float* z_lo, int64_t ld, int32_t* nterms) {
   if (!c || n < 1 || n > kMaxVars || n_boxes < 0 || ld < n + 1) return BERN_E_INVALID;

@@ -178,3 +178,79 @@ def test_enclose_scales_rejects_bad_arguments():
     assert lib.bern_enclose_scales(3, 25, buf.ctypes.data, 64) == 1
     assert lib.bern_enclose_scales(3, 4, buf.ctypes.data, 64) == 1    # needs 2 * 35 = 70
     assert lib.bern_enclose_scales(3, 2, buf.ctypes.data, 64) == 0    # 2 * 10 = 20 fit
+
+
+# ------------------------------------------------------------ composition row tables
+_CASES = {}
+
+
+@pytest.mark.parametrize("n,D", [(1, 0), (1, 8), (2, 3), (2, 8), (3, 0), (3, 1), (3, 2), (3, 4),
+                                 (3, 8), (4, 5), (5, 4), (6, 3), (8, 2)])
+def test_compose_rows_give_the_exact_square(n, D):
+    # Step 3 at ReLU order 2 forms a1 s + a2 s^2; replay the row kernel's
+    # reading of the tables (off-diagonal row pairs counted twice, the
+    # diagonal pair as a triangle, the row's own input row as the linear
+    # term, each output element to its graded rank) on integer coefficients
+    # and compare with the product expanded monomial by monomial
+    t = bern.compose_rows(n, D)
+    ex_in = bern.monomials(n, D).astype(int)
+    ex_out = bern.monomials(n, 2 * D).astype(int)
+    rank_out = {tuple(e): r for r, e in enumerate(ex_out)}
+    M = len(ex_in)
+    rng = np.random.default_rng(31 * n + D)
+    p = rng.integers(-9, 10, M).astype(np.int64)
+    a1, a2 = 3, 5
+    want = np.zeros(len(ex_out), np.int64)
+    for i in range(M):
+        want[rank_out[tuple(ex_in[i])]] += a1 * p[i]
+        for j in range(M):
+            want[rank_out[tuple(ex_in[i] + ex_in[j])]] += a2 * p[i] * p[j]
+
+    assert sorted(t["pos_in"].tolist()) == list(range(M))
+    s = np.zeros(M, np.int64)
+    s[t["pos_in"]] = p
+    unset = np.iinfo(np.int64).min
+    got = np.full(len(ex_out), unset, np.int64)
+    for P, (pb, pe, rb, w) in enumerate(t["hdr"].tolist()):
+        Lout, in_len, has_diag = w & 0xFF, (w >> 8) & 0xFF, (w >> 16) & 1
+        acc = np.zeros(Lout, np.int64)
+        for k in range(pb, pe - has_diag):
+            op, oq, code, case = t["pairs"][k].tolist()
+            L1, L2 = code >> 4, code & 15
+            assert 1 <= L1 <= L2 <= 9 and op + L1 <= M and oq + L2 <= M
+            assert _CASES.setdefault((L1, L2), case) == case
+            for a in range(L1):
+                for b in range(L2):
+                    acc[a + b] += 2 * s[op + a] * s[oq + b]
+        if has_diag:
+            o, _, code, case = t["pairs"][pe - 1].tolist()
+            L = code & 15
+            assert code >> 4 == L and o + L <= M
+            assert _CASES.setdefault((L, L), case) == case
+            for a in range(L):
+                acc[2 * a] += s[o + a] * s[o + a]
+                for b in range(a + 1, L):
+                    acc[a + b] += 2 * s[o + a] * s[o + b]
+        for c in range(Lout):
+            lin = s[t["in_off"][P] + c] if c < in_len else 0
+            r = t["out_ranks"][rb + c]
+            assert got[r] == unset                       # every rank written once
+            got[r] = a2 * acc[c] + a1 * lin
+    assert np.array_equal(got, want)
+    assert 0 <= t["row_split"] <= len(t["hdr"])
+    # the dispatch cases seen so far: one per pair of row lengths, all distinct
+    # and inside the dense range of the kernel's switch
+    assert len(set(_CASES.values())) == len(_CASES)
+    assert all(0 <= v < 45 for v in _CASES.values())
+
+
+def test_compose_rows_limits():
+    lib = bern.load()
+    sizes = np.zeros(5, np.int64)
+    assert lib.bern_compose_rows(3, 8, None, 0, None) == 1          # sizes NULL
+    assert lib.bern_compose_rows(3, 9, None, 0, sizes.ctypes.data) == 1
+    assert lib.bern_compose_rows(6, 8, None, 0, sizes.ctypes.data) == 6   # 3003 terms
+    assert lib.bern_compose_rows(3, 8, None, 0, sizes.ctypes.data) == 0
+    assert sizes[0] == math.comb(11, 3)
+    buf = np.zeros(8, np.int32)
+    assert lib.bern_compose_rows(3, 8, buf.ctypes.data, buf.size, sizes.ctypes.data) == 1
