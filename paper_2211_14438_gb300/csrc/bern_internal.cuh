@@ -39,9 +39,6 @@ struct PairList {
   int64_t m_in = 0, m_out = 0;
 };
 bool build_square_pairs(int n, int D, PairList& out);
-// Same for the product of a degree-Dq polynomial by a degree-Ds one:
-// pairs (I in q, J in s), packed I | (J << 16)
-bool build_product_pairs(int n, int Dq, int Ds, PairList& out);
 
 // Product table of a degree-Dq polynomial q by a degree-Ds polynomial s, for
 // the Horner kernel: for every output rank K < M(n, Dq + Ds), the pairs

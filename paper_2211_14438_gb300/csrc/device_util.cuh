@@ -17,14 +17,6 @@ template <bool UP>
 __device__ __forceinline__ float dadd(float a, float b) {
   return UP ? __fadd_ru(a, b) : __fadd_rd(a, b);
 }
-template <bool UP>
-__device__ __forceinline__ float dmul(float a, float b) {
-  return UP ? __fmul_ru(a, b) : __fmul_rd(a, b);
-}
-template <bool UP>
-__device__ __forceinline__ float ddiv(float a, float b) {
-  return UP ? __fdiv_ru(a, b) : __fdiv_rd(a, b);
-}
 
 // warp-wide directed sum (fixed tree: deterministic)
 template <bool UP>

@@ -78,10 +78,6 @@ bool build_square_pairs(int n, int D, PairList& out) {
   return build_pairs(n, D, D, true, out);
 }
 
-bool build_product_pairs(int n, int Dq, int Ds, PairList& out) {
-  return build_pairs(n, Dq, Ds, false, out);
-}
-
 bool build_product_table(int n, int Dq, int Ds, int64_t max_pairs, std::vector<int32_t>& ptr,
                          std::vector<int32_t>& pairs) {
   const int64_t mq = num_monomials(n, Dq), ms = num_monomials(n, Ds);
