@@ -76,6 +76,24 @@ def test_custom_split_rule_is_used_and_clipped():
     assert calls and np.allclose(bb.boxes[:, :2, :], root[None, :2, :])
 
 
+def test_widest_split_is_relative_to_the_root():
+    # the fallback split takes the side widest relative to the root's side,
+    # not the widest in absolute terms; ties go to the lowest dimension
+    root = np.array([[-1, 1], [0, 10], [0, 0.5]], np.float32)
+    boxes = np.array([
+        [[0, 1], [0, 4], [0, 0.1]],      # relative sides 0.5, 0.4, 0.2
+        [[0, 0.2], [0, 9], [0, 0.25]],   # 0.1, 0.9, 0.5
+        [[0, 0.2], [0, 1], [0, 0.45]],   # 0.1, 0.1, 0.9
+        [[0, 1], [0, 5], [0, 0.25]],     # 0.5, 0.5, 0.5: a tie
+    ], np.float32)
+    assert bnb.widest_split(boxes, root).tolist() == [0, 1, 2, 0]
+    # a degenerate root side never divides by zero and is never chosen over
+    # a side that is actually wide
+    root0 = np.array([[0, 0], [0, 1]], np.float32)
+    b0 = np.array([[[0, 0], [0, 0.5]]], np.float32)
+    assert bnb.widest_split(b0, root0).tolist() == [1]
+
+
 @pytest.mark.parametrize("active", [[10, 0], [3, 3], [7, 2, 0, 9], [0, 0, 5]])
 def test_plan_moves_balances(active):
     moves = bnb.plan_moves([a + 5 for a in active], active)
