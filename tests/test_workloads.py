@@ -79,3 +79,24 @@ def test_seeds_are_reproducible():
     np.testing.assert_array_equal(a.boxes, b.boxes)
     for x, y in zip(a.net.W, b.net.W):
         np.testing.assert_array_equal(x, y)
+
+
+@pytest.mark.parametrize("world", [1, 2, 4])
+def test_batch_3in_replicas(world):
+    # weak scaling: world replicas of 5120 boxes, replica 0 the benchmark's
+    # own boxes, every replica the same grid cells with its own random boxes,
+    # one network
+    w0 = wl.batch_3in()
+    w = wl.batch_3in_replicas(world)
+    assert w.boxes.shape == (5120 * world, 3, 2)
+    assert np.array_equal(w.boxes[:5120], w0.boxes)
+    for a, b in zip(w.net.W, w0.net.W):
+        assert np.array_equal(a, b)
+    reps = w.boxes.reshape(world, 5120, 3, 2)
+    for r in range(1, world):
+        assert np.array_equal(reps[r, :4096], w0.boxes[:4096])        # the 16^3 grid
+        assert not np.array_equal(reps[r, 4096:], w0.boxes[4096:])    # fresh random boxes
+        side = reps[r, 4096:, :, 1] - reps[r, 4096:, :, 0]
+        assert np.all(side >= 0) and np.all(side <= 0.5 + 1e-6)
+        assert np.all(reps[r, :, :, 0] >= -1) and np.all(reps[r, :, :, 1] <= 1)
+    assert np.array_equal(wl.batch_3in_replicas(world).boxes, w.boxes)   # seeded
