@@ -264,6 +264,32 @@ def test_compose_pointwise(d):
     np.testing.assert_allclose(oracle.eval_poly(lw, n, pts), want - B0, rtol=1e-10, atol=1e-10)
 
 
+@pytest.mark.parametrize("d", [6, 8, 12, 16])
+def test_compose_pointwise_high_orders(d):
+    """The same identity at the high orders of Fig. 1's range (the orders the
+    float64 Horner composition serves): composed polynomial == Def. 1's ReLU
+    polynomial applied to P(t), the lower one shifted by B(0).  The power
+    form's coefficients grow like C(d, d/2) 2^(d/2), so the tolerance scales
+    with the composed polynomial's coefficient mass."""
+    rng = np.random.default_rng(40 + d)
+    n = 2
+    P = random_poly(rng, n, 2)
+    pts = np.vstack([rng.random((150, n)), [[0, 0], [0, 1], [1, 0], [1, 1]]])
+    lo, hi = oracle.enclosure(P, n, 2)
+    lo, hi = lo - 0.05, hi + 0.05
+    if not (lo < 0 < hi):
+        lo, hi = -abs(lo) - 0.1, abs(hi) + 0.1
+    Pv = oracle.eval_poly(P, n, pts)
+    want = np.array([oracle.relu_bern_eval(lo, hi, d, y) for y in Pv])
+    B0 = oracle.relu_bern_eval(lo, hi, d, 0.0)
+    up = oracle.compose(P, n, lo, hi, d, True, cap=64)
+    lw = oracle.compose(P, n, lo, hi, d, False, cap=64)
+    assert max(sum(e) for e in up[0]) <= 2 * d          # no term was truncated
+    tol = 1e-12 * (1 + np.abs(up[1]).sum())
+    assert np.max(np.abs(oracle.eval_poly(up, n, pts) - want)) <= tol
+    assert np.max(np.abs(oracle.eval_poly(lw, n, pts) - (want - B0))) <= tol
+
+
 @pytest.mark.parametrize("cap,tau", [(3, 0.0), (4, 0.0), (6, 1e-2), (64, 5e-2)])
 def test_compose_truncation_sound(cap, tau):
     """Cap truncation and pruning (R4/R5) keep upper >= B(P) >= ... >= lower."""
