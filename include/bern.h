@@ -290,6 +290,23 @@ int bern_enclose_scales(int n, int l, float* out, int64_t cap);
  * when the input has more than 750 terms (those use the pair-list kernel). */
 int bern_compose_rows(int n, int D, int32_t* out, int64_t cap, int64_t* sizes);
 
+/* The output-stationary pair lists of the other composition kernels (Sec.
+ * 5.1 Step 3; the products of Sec. 4.2 over the graded monomial set): for
+ * every output monomial K of degree <= Dq + Ds, the pairs (I, J) of a
+ * degree-Dq and a degree-Ds monomial with I + J = K, pairs[2 ptr[K] ..
+ * 2 ptr[K+1]) as (I, J) int32 in graded ranks.
+ *   square = 1 (Dq == Ds): the square's symmetric list, I <= J (the pair-list
+ *     kernel of order-2 items; it packs each pair as I | J << 16);
+ *   square = 0: the product table of the Horner kernels (orders >= 3).
+ *   sizes[2] receives M(n, Dq + Ds) + 1 and the number of pairs; ptr or pairs
+ *   NULL: sizes only.
+ * Host only; no GPU needed.  Returns BERN_OK; BERN_E_INVALID (sizes NULL, n
+ * outside [1, 8], a degree out of range, square with Dq != Ds, or a cap too
+ * small); BERN_E_UNSUPPORTED beyond the kernels' table limits (square: more
+ * than 65,535 input terms; product: more than 2^24 pairs). */
+int bern_pair_lists(int n, int Dq, int Ds, int square, int32_t* ptr, int64_t cap_ptr,
+                    int32_t* pairs, int64_t cap_pairs, int64_t* sizes);
+
 /* ------------------------------------------------------------ hot path */
 
 /* Whole path, Sec. 5.3: input init, then per layer the affine step

@@ -62,6 +62,7 @@ EXPORTS = [
     "bern_enclose_lines",
     "bern_enclose_scales",
     "bern_compose_rows",
+    "bern_pair_lists",
 ]
 
 
@@ -139,6 +140,7 @@ def load(build_if_missing: bool = True):
         "bern_enclose_lines": (I, [I, I, V, I64]),
         "bern_enclose_scales": (I, [I, I, V, I64]),
         "bern_compose_rows": (I, [I, I, V, I64, V]),
+        "bern_pair_lists": (I, [I, I, I, I, V, I64, V, I64, V]),
         "bern_propagate": (I, [V, ctypes.POINTER(bern_net), V, I64,
                                ctypes.POINTER(bern_degree_plan), ctypes.POINTER(bern_result)]),
         "bern_init_inputs": (I, [V, I, I64, V, V, V, I64, V]),
@@ -238,6 +240,21 @@ def compose_rows(n: int, D: int) -> dict:
     return {"pos_in": out[o[0]:o[1]], "hdr": out[o[1]:o[2]].reshape(rows, 4),
             "in_off": out[o[2]:o[3]], "pairs": out[o[3]:o[4]].reshape(npairs, 4),
             "out_ranks": out[o[4]:o[5]], "row_split": split}
+
+
+def pair_lists(n: int, Dq: int, Ds: int, square: bool):
+    """The composition's output-stationary pair lists (bern_pair_lists):
+    (ptr [M(n, Dq+Ds)+1], pairs [n_pairs, 2] of graded ranks (I, J))."""
+    sizes = np.zeros(2, np.int64)
+    lib = load()
+    _check(lib.bern_pair_lists(n, Dq, Ds, int(square), None, 0, None, 0, sizes.ctypes.data),
+           "bern_pair_lists")
+    ptr = np.zeros(int(sizes[0]), np.int32)
+    pairs = np.zeros((int(sizes[1]), 2), np.int32)
+    _check(lib.bern_pair_lists(n, Dq, Ds, int(square), ptr.ctypes.data, ptr.size,
+                               pairs.ctypes.data, pairs.size, sizes.ctypes.data),
+           "bern_pair_lists")
+    return ptr, pairs
 
 
 def _ptr(t) -> int:

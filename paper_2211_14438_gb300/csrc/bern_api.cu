@@ -968,6 +968,33 @@ int bern_compose_rows(int n, int D, int32_t* out, int64_t cap, int64_t* sizes) {
   return BERN_OK;
 }
 
+int bern_pair_lists(int n, int Dq, int Ds, int square, int32_t* ptr, int64_t cap_ptr,
+                    int32_t* pairs, int64_t cap_pairs, int64_t* sizes) {
+  if (!sizes || n < 1 || n > kMaxVars || Dq < 0 || Ds < 0 || Dq + Ds > kMaxTableDegree ||
+      (square && Dq != Ds))
+    return BERN_E_INVALID;
+  std::vector<int32_t> p, q;
+  if (square) {
+    PairList pl;
+    if (!build_square_pairs(n, Dq, pl)) return BERN_E_UNSUPPORTED;
+    p = pl.ptr;
+    q.resize(2 * pl.pairs.size());
+    for (size_t k = 0; k < pl.pairs.size(); ++k) {
+      q[2 * k] = (int32_t)(pl.pairs[k] & 0xffffu);
+      q[2 * k + 1] = (int32_t)(pl.pairs[k] >> 16);
+    }
+  } else if (!build_product_table(n, Dq, Ds, (int64_t)1 << 24, p, q)) {
+    return BERN_E_UNSUPPORTED;
+  }
+  sizes[0] = (int64_t)p.size();
+  sizes[1] = (int64_t)q.size() / 2;
+  if (!ptr || !pairs) return BERN_OK;
+  if (cap_ptr < (int64_t)p.size() || cap_pairs < (int64_t)q.size()) return BERN_E_INVALID;
+  std::memcpy(ptr, p.data(), p.size() * sizeof(int32_t));
+  std::memcpy(pairs, q.data(), q.size() * sizeof(int32_t));
+  return BERN_OK;
+}
+
 int bern_init_inputs(bern_ctx* c, int n, int64_t n_boxes, const float* boxes, float* z_up,
                      float* z_lo, int64_t ld, int32_t* nterms) {
   if (!c || n < 1 || n > kMaxVars || n_boxes < 0 || ld < n + 1) return BERN_E_INVALID;

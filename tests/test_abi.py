@@ -254,3 +254,55 @@ def test_compose_rows_limits():
     assert sizes[0] == math.comb(11, 3)
     buf = np.zeros(8, np.int32)
     assert lib.bern_compose_rows(3, 8, buf.ctypes.data, buf.size, sizes.ctypes.data) == 1
+
+
+# ------------------------------------------------------------ composition pair lists
+@pytest.mark.parametrize("n,Dq,Ds,square", [
+    (1, 4, 4, True), (2, 3, 3, True), (3, 4, 4, True), (3, 8, 8, True), (6, 2, 2, True),
+    (1, 3, 5, False), (2, 4, 2, False), (3, 8, 2, False), (3, 16, 2, False), (6, 4, 2, False)])
+def test_pair_lists_give_the_exact_product(n, Dq, Ds, square):
+    # every pair of output K's list has I + J = K, every pair of input
+    # monomials (I <= J for the square) appears once, and the products read
+    # off the lists (the square's off-diagonal pairs counted twice) are exact
+    ptr, pairs = bern.pair_lists(n, Dq, Ds, square)
+    ex = bern.monomials(n, Dq + Ds).astype(int)
+    mq, ms, mo = (bern.num_monomials(n, D) for D in (Dq, Ds, Dq + Ds))
+    assert len(ptr) == mo + 1 and ptr[0] == 0 and ptr[-1] == len(pairs)
+    assert np.all(np.diff(ptr) >= 0)
+    seen = set()
+    for K in range(mo):
+        for I, J in pairs[ptr[K]:ptr[K + 1]].tolist():
+            assert I < mq and J < ms and np.array_equal(ex[I] + ex[J], ex[K])
+            assert (I <= J) or not square
+            assert (I, J) not in seen
+            seen.add((I, J))
+    assert len(seen) == (mq * (mq + 1) // 2 if square else mq * ms)
+
+    rng = np.random.default_rng(7 * n + Dq + 3 * Ds)
+    q = rng.integers(-9, 10, mq).astype(np.int64)
+    s = q if square else rng.integers(-9, 10, ms).astype(np.int64)
+    rank = {tuple(e): r for r, e in enumerate(ex)}
+    want = np.zeros(mo, np.int64)
+    for i in range(mq):
+        for j in range(ms):
+            want[rank[tuple(ex[i] + ex[j])]] += q[i] * s[j]
+    got = np.zeros(mo, np.int64)
+    for K in range(mo):
+        for I, J in pairs[ptr[K]:ptr[K + 1]].tolist():
+            got[K] += q[I] * s[J] * (2 if square and I != J else 1)
+    assert np.array_equal(got, want)
+
+
+def test_pair_lists_limits():
+    lib = bern.load()
+    sizes = np.zeros(2, np.int64)
+    assert lib.bern_pair_lists(3, 2, 2, 1, None, 0, None, 0, None) == 1
+    assert lib.bern_pair_lists(3, 2, 3, 1, None, 0, None, 0, sizes.ctypes.data) == 1   # square, Dq != Ds
+    assert lib.bern_pair_lists(9, 2, 2, 1, None, 0, None, 0, sizes.ctypes.data) == 1
+    assert lib.bern_pair_lists(3, 40, 30, 0, None, 0, None, 0, sizes.ctypes.data) == 1  # degree > 64
+    assert lib.bern_pair_lists(3, 2, 2, 1, None, 0, None, 0, sizes.ctypes.data) == 0
+    assert sizes.tolist() == [math.comb(7, 3) + 1, 10 * 11 // 2]
+    assert lib.bern_pair_lists(4, 16, 16, 0, None, 0, None, 0, sizes.ctypes.data) == 6   # > 2^24 pairs
+    p = np.zeros(4, np.int32)
+    assert lib.bern_pair_lists(3, 2, 2, 1, p.ctypes.data, 4, p.ctypes.data, 4,
+                               sizes.ctypes.data) == 1                              # caps too small
