@@ -135,6 +135,10 @@ int upload_tables(DeviceSlot& s, int n, int dmax, int deg_exps, cudaStream_t str
     if (img.size() > kNoAllocTableBytes) return BERN_E_UNSUPPORTED;
   }
   if (img.size() > kNoAllocTableBytes) return BERN_E_UNSUPPORTED;
+  // from here g_tables is being overwritten: until the new view is in place
+  // the slot holds no valid tables, so a failed copy is never taken for them
+  s.table_n = -1;
+  s.table_dmax = -1;
   // the copy is ordered on the caller's stream after every earlier call on it
   if (cudaMemcpyAsync(s.tables, img.data(), img.size(), cudaMemcpyHostToDevice, stream) !=
       cudaSuccess)
