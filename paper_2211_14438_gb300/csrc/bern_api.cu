@@ -140,7 +140,10 @@ int ensure_tables(bern_ctx* c, int n, int dmax, const Tables** out) {
     return BERN_OK;
   }
   if (dmax > kMaxTableDegree) return BERN_E_UNSUPPORTED;
-  // (re)build from scratch; previously captured graphs hold old pointers
+  // (re)build from scratch; previously captured graphs hold old pointers.
+  // Until the rebuild completes the set holds no valid tables (a failed
+  // rebuild leaves it empty, and the next call builds again).
+  ts.dmax = -1;
   for (auto& g : c->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   c->graphs.clear();
@@ -265,36 +268,51 @@ int ensure_prod_tables(bern_ctx* c, int n, int Dmax, int dmax, int cap) {
   int rc = ensure_tables(c, n, 0, &T);
   if (rc) return rc;
   TableSet& ts = c->tables[n];
-  bool changed = false;
+  // Tables added by this call reach the kernels through the device array
+  // prod_arr; it is refreshed on every exit once something was added (also
+  // when a later table fails), and if that copy fails the added tables are
+  // dropped again, so a table the host lists is always one the kernels see.
+  std::vector<std::pair<int, int>> added;
+  auto finish = [&](int rc_in) -> int {
+    if (added.empty()) return rc_in;
+    const cudaError_t e = cudaMemcpy(ts.prod_arr.p, ts.prod_host.data(),
+                                     ts.prod_host.size() * sizeof(ProdTable),
+                                     cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) return rc_in;
+    for (const auto& key : added) {
+      ts.prod_host[(size_t)key.first * kProdStride + key.second] = ProdTable{nullptr, nullptr};
+      auto it = ts.prod.find(key);
+      it->second.first.release();
+      it->second.second.release();
+      ts.prod.erase(it);
+    }
+    return map_cuda(e);
+  };
   for (int D = 0; D <= Dmax; ++D)
     for (int k = 0; k < std::max(1, dmax); ++k) {
       const int Dq = std::min(cap, k * D);
-      if (Dq + D > kMaxTableDegree) return BERN_E_UNSUPPORTED;
+      if (Dq + D > kMaxTableDegree) return finish(BERN_E_UNSUPPORTED);
       const auto key = std::make_pair(Dq, D);
       if (ts.prod.count(key)) continue;
       std::vector<int32_t> ptr, pairs;
-      if (!build_product_table(n, Dq, D, (int64_t)1 << 24, ptr, pairs)) return BERN_E_UNSUPPORTED;
+      if (!build_product_table(n, Dq, D, (int64_t)1 << 24, ptr, pairs))
+        return finish(BERN_E_UNSUPPORTED);
       DevBuf bp, bq;
       cudaError_t e = bp.reserve(ptr.size() * sizeof(int32_t));
       if (e == cudaSuccess) e = bq.reserve(std::max<size_t>(8, pairs.size() * sizeof(int32_t)));
       if (e != cudaSuccess) {
         bp.release();
         bq.release();
-        return map_cuda(e);
+        return finish(map_cuda(e));
       }
       cudaMemcpy(bp.p, ptr.data(), ptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
       if (!pairs.empty())
         cudaMemcpy(bq.p, pairs.data(), pairs.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
       ts.prod[key] = std::make_pair(bp, bq);
       ts.prod_host[(size_t)Dq * kProdStride + D] = ProdTable{(const int32_t*)bp.p, (const int2*)bq.p};
-      changed = true;
+      added.push_back(key);
     }
-  if (changed) {
-    cudaError_t e = cudaMemcpy(ts.prod_arr.p, ts.prod_host.data(),
-                               ts.prod_host.size() * sizeof(ProdTable), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return map_cuda(e);
-  }
-  return BERN_OK;
+  return finish(BERN_OK);
 }
 
 // Composition work queues for up to `items` items.
