@@ -201,8 +201,7 @@ int bern_force_variant(bern_ctx* ctx, const char* kind, int variant);
 /* Largest shared-memory footprint (bytes, at most 200 KB) the Horner
  * composition kernel may use per block before it keeps its buffers in a
  * global workspace instead; the default is 200 KB.  Both placements compute
- * the same values in the same order (a setting for tests and tuning).  A
- * changed limit drops captured graphs. */
+ * the same values in the same order (a setting for tests and tuning). */
 int bern_set_horner_smem_limit(bern_ctx* ctx, int64_t bytes);
 
 /* Use CUDA-graph replay for bern_propagate (default 1).  With graphs on, the

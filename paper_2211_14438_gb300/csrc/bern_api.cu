@@ -96,23 +96,16 @@ struct bern_ctx {
   // reserve the enclosure workspace for grids of (n, order, budget); graphs
   // captured with an older buffer are dropped when it moves
   cudaError_t reserve_enclose(int n, int order, int64_t budget);
-  // Captured graphs hold the addresses of the context's buffers and the
-  // settings they were captured under: drop them (after the work in flight)
-  // before a buffer that is not part of the graph key moves or such a
-  // setting changes.
-  void drop_graphs() {
-    for (auto& g : graphs)
-      if (g.exec) cudaGraphExecDestroy(g.exec);
-    graphs.clear();
-    cudaStreamSynchronize(stream);
-    if (gstream) cudaStreamSynchronize(gstream);
-  }
 };
 
 cudaError_t bern_ctx::reserve_enclose(int n, int order, int64_t budget) {
   const size_t floats = enclose_big_floats(n, order, budget, std::max(1, sms));
   if (floats * sizeof(float) <= ebuf.bytes) return cudaSuccess;
-  drop_graphs();
+  for (auto& g : graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  graphs.clear();
+  cudaStreamSynchronize(stream);
+  if (gstream) cudaStreamSynchronize(gstream);
   return ebuf.reserve(floats * sizeof(float));
 }
 
@@ -325,8 +318,6 @@ int ensure_prod_tables(bern_ctx* c, int n, int Dmax, int dmax, int cap) {
 // Composition work queues for up to `items` items.
 int ensure_queues(bern_ctx* c, int64_t items, ComposeScratch* out, size_t horner_floats = 0) {
   const size_t bytes = 256 + (size_t)kQueueLists * items * sizeof(int);
-  // the queues and the Horner workspace are not part of the graph key
-  if (bytes > c->qbuf.bytes || horner_floats * sizeof(float) > c->hbuf.bytes) c->drop_graphs();
   cudaError_t e = c->qbuf.reserve(bytes);
   if (e != cudaSuccess) return map_cuda(e);
   out->qcount = (int*)c->qbuf.p;
@@ -847,7 +838,6 @@ int bern_force_variant(bern_ctx* c, const char* kind, int variant) {
 
 int bern_set_horner_smem_limit(bern_ctx* c, int64_t bytes) {
   if (!c || bytes < 0) return BERN_E_INVALID;
-  if (bytes != c->horner_smem_limit) c->drop_graphs();   // captured under the old limit
   c->horner_smem_limit = bytes;
   return BERN_OK;
 }
