@@ -317,6 +317,8 @@ int ensure_prod_tables(bern_ctx* c, int n, int Dmax, int dmax, int cap) {
 
 // Composition work queues for up to `items` items.
 int ensure_queues(bern_ctx* c, int64_t items, ComposeScratch* out, size_t horner_floats = 0) {
+  // *out is part of the graph key byte for byte: zero its padding too
+  std::memset(out, 0, sizeof *out);
   const size_t bytes = 256 + (size_t)kQueueLists * items * sizeof(int);
   cudaError_t e = c->qbuf.reserve(bytes);
   if (e != cudaSuccess) return map_cuda(e);
