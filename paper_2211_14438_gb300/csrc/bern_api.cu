@@ -697,8 +697,11 @@ int fill_degrees(bern_ctx* c, const Plan& P, const Chunk& ch, int64_t B) {
     host.resize((size_t)B * l.h_out);
     for (int64_t b = 0; b < B; ++b)
       std::memcpy(&host[(size_t)b * l.h_out], &P.neuron_deg[base], l.h_out);
-    cudaError_t e = cudaMemcpy(ch.at<uint8_t>(l.off_deg), host.data(), host.size(),
-                               cudaMemcpyHostToDevice);
+    // on the context's stream, so the copy is ordered after the previous
+    // chunk's (or call's) kernels that read this workspace, whatever kind of
+    // stream the caller gave (pageable source: staged before the call returns)
+    cudaError_t e = cudaMemcpyAsync(ch.at<uint8_t>(l.off_deg), host.data(), host.size(),
+                                    cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return map_cuda(e);
     base += l.h_out;
   }
